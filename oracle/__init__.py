@@ -1,0 +1,246 @@
+"""Python access to the double-precision CPU oracle (oracle/orc.c).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by the smoke check and by the
+CPU-baseline leg of bench.py, never by the product package.  The oracle shares
+no code with the CUDA library.
+
+Interaction descriptions are plain dicts so that the test code states every
+parameter explicitly:
+    pair = {(ta, tb): ("lj", eps, sigma, rc, shift) | ("wca", eps, sigma)
+                      | ("lj_capped", eps, sigma, rc, shift, caprad)}
+    bond = ("fene", K, R0) or None
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+PAIR_STRIDE = 8
+BOND_STRIDE = 4
+NOBS = 12
+OBS_NAMES = ("ke", "pe_pair", "pe_bond", "virial", "px", "py", "pz",
+             "temperature", "pressure", "mean_bond", "rg2", "nmol")
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        L.orc_num_threads.restype = ctypes.c_int
+        L.orc_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+        L.orc_uniform_centered.argtypes = [ctypes.c_uint32]
+        L.orc_uniform_centered.restype = ctypes.c_double
+        L.orc_uniform_fill.argtypes = [_u32p, ctypes.c_int64, _dp]
+        L.orc_langevin_noise.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, _dp]
+        L.orc_pair_eval.argtypes = [_dp, ctypes.c_double, _dp, _dp]
+        L.orc_bond_eval.argtypes = [_dp, ctypes.c_double, _dp, _dp]
+        L.orc_bond_eval.restype = ctypes.c_int
+        L.orc_forces.argtypes = [ctypes.c_int64, _dp, _dp, _i32p, ctypes.c_int, _dp,
+                                 ctypes.c_int64, _i64p, _dp, _dp, _dp]
+        L.orc_forces.restype = ctypes.c_int
+        for fn in (L.orc_neighbors_brute, L.orc_neighbors_cells):
+            fn.argtypes = [ctypes.c_int64, _dp, _dp, ctypes.c_double, _i64p, _i64p, ctypes.c_int64]
+            fn.restype = ctypes.c_int64
+        L.orc_integrate.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _i32p, _i32p, _dp, ctypes.c_int,
+                                    _dp, ctypes.c_int64, _i64p, _dp, _dp, ctypes.c_int,
+                                    ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64]
+        L.orc_integrate.restype = ctypes.c_int
+        L.orc_observables.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _i32p, _i32p, _dp, ctypes.c_int,
+                                      _dp, ctypes.c_int64, _i64p, _dp, _dp]
+        L.orc_observables.restype = ctypes.c_int
+        L.orc_rdf_counts.argtypes = [ctypes.c_int64, _dp, _dp, ctypes.c_double, ctypes.c_int, _i64p]
+        _lib = L
+    return _lib
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+WCA_RC = 2.0 ** (1.0 / 6.0)
+
+
+def pair_table(pair: dict, ntypes: int) -> np.ndarray:
+    """Flatten a {(ta, tb): spec} dict into the oracle's pair records."""
+    t = np.zeros((ntypes, ntypes, PAIR_STRIDE), dtype=np.float64)
+    for (a, b), spec in pair.items():
+        kind = spec[0]
+        if kind == "lj":
+            _, eps, sig, rc, shift = spec
+            rec = [1, eps, sig, rc, 1.0 if shift else 0.0, 0.0]
+        elif kind == "wca":
+            _, eps, sig = spec
+            rec = [1, eps, sig, WCA_RC * sig, 1.0, 0.0]
+        elif kind == "lj_capped":
+            _, eps, sig, rc, shift, cap = spec
+            rec = [2, eps, sig, rc, 1.0 if shift else 0.0, cap]
+        else:
+            raise ValueError(kind)
+        t[a, b, :6] = rec
+        t[b, a, :6] = rec
+    return t.reshape(-1)
+
+
+def bond_table(bond) -> np.ndarray:
+    b = np.zeros(BOND_STRIDE, dtype=np.float64)
+    if bond is None:
+        return b
+    if bond[0] == "fene":
+        b[:3] = [1, bond[1], bond[2]]
+        return b
+    raise ValueError(bond[0])
+
+
+class Model:
+    """The interaction set of one system as the oracle sees it."""
+
+    def __init__(self, ntypes=1, pair=None, bond=None, masses=None):
+        self.ntypes = ntypes
+        self.pair = pair_table(pair or {}, ntypes)
+        self.bond = bond_table(bond)
+        self.masses = _f64(masses if masses is not None else np.ones(ntypes))
+
+
+def philox(ctr, key):
+    out = np.zeros(4, dtype=np.uint32)
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    lib().orc_philox4x32_10(_p(c, _u32p), _p(k, _u32p), _p(out, _u32p))
+    return out
+
+
+def uniform_centered(words) -> np.ndarray:
+    w = np.ascontiguousarray(words, dtype=np.uint32).reshape(-1)
+    out = np.empty(w.size, dtype=np.float64)
+    lib().orc_uniform_fill(_p(w, _u32p), w.size, _p(out, _dp))
+    return out
+
+
+def langevin_noise(seed: int, step: int, n: int) -> np.ndarray:
+    out = np.empty((n, 3), dtype=np.float64)
+    lib().orc_langevin_noise(seed, step, n, _p(out, _dp))
+    return out
+
+
+def pair_eval(model: Model, ta: int, tb: int, r2: float):
+    u, fr = ctypes.c_double(), ctypes.c_double()
+    rec = model.pair[PAIR_STRIDE * (ta * model.ntypes + tb):][:PAIR_STRIDE].copy()
+    lib().orc_pair_eval(_p(rec, _dp), r2, ctypes.byref(u), ctypes.byref(fr))
+    return u.value, fr.value
+
+
+def bond_eval(model: Model, r2: float):
+    u, fr = ctypes.c_double(), ctypes.c_double()
+    rc = lib().orc_bond_eval(_p(model.bond, _dp), r2, ctypes.byref(u), ctypes.byref(fr))
+    return u.value, fr.value, rc
+
+
+def forces(model: Model, box, x, types, bonds):
+    """Conservative forces and (PE_pair, PE_bond, virial); raises on a broken bond."""
+    x = _f64(x, (-1, 3))
+    n = x.shape[0]
+    L = _f64(box)
+    t = np.ascontiguousarray(types, dtype=np.int32)
+    b = np.ascontiguousarray(bonds, dtype=np.int64).reshape(-1, 2)
+    f = np.zeros((n, 3), dtype=np.float64)
+    en = np.zeros(3, dtype=np.float64)
+    st = lib().orc_forces(n, _p(L, _dp), _p(x, _dp), _p(t, _i32p), model.ntypes,
+                          _p(model.pair, _dp), b.shape[0], _p(b, _i64p),
+                          _p(model.bond, _dp), _p(f, _dp), _p(en, _dp))
+    if st != 0:
+        raise RuntimeError("oracle: bond broken (status %d)" % st)
+    return f, en
+
+
+def neighbors(box, x, rcut, method="cells"):
+    """Neighbour sets as CSR (row_ptr, cols) in id order."""
+    x = _f64(x, (-1, 3))
+    n = x.shape[0]
+    L = _f64(box)
+    cap = max(64, n * 16)
+    fn = lib().orc_neighbors_cells if method == "cells" else lib().orc_neighbors_brute
+    while True:
+        row = np.zeros(n + 1, dtype=np.int64)
+        cols = np.zeros(cap, dtype=np.int64)
+        m = fn(n, _p(L, _dp), _p(x, _dp), rcut, _p(row, _i64p), _p(cols, _i64p), cap)
+        if m >= 0:
+            return row, cols[:m]
+        cap *= 4
+
+
+class State:
+    """Particle state in id order: x, v (n,3) float64, img (n,3) int32."""
+
+    def __init__(self, box, x, v=None, img=None, types=None, bonds=None):
+        self.box = _f64(box).copy()
+        self.x = _f64(x, (-1, 3)).copy()
+        n = self.x.shape[0]
+        self.v = _f64(v, (-1, 3)).copy() if v is not None else np.zeros((n, 3))
+        self.img = (np.ascontiguousarray(img, dtype=np.int32).reshape(-1, 3).copy()
+                    if img is not None else np.zeros((n, 3), dtype=np.int32))
+        self.types = (np.ascontiguousarray(types, dtype=np.int32).copy()
+                      if types is not None else np.zeros(n, dtype=np.int32))
+        self.bonds = (np.ascontiguousarray(bonds, dtype=np.int64).reshape(-1, 2).copy()
+                      if bonds is not None else np.zeros((0, 2), dtype=np.int64))
+        self.f = np.zeros((n, 3), dtype=np.float64)
+        self.f_valid = False
+        self.step = 0
+
+    @property
+    def n(self):
+        return self.x.shape[0]
+
+
+def integrate(model: Model, st: State, nsteps: int, dt: float, gamma: float, kT: float,
+              seed: int):
+    rc = lib().orc_integrate(st.n, _p(st.box, _dp), _p(st.x, _dp), _p(st.v, _dp),
+                             _p(st.img, _i32p), _p(st.types, _i32p), _p(model.masses, _dp),
+                             model.ntypes, _p(model.pair, _dp), st.bonds.shape[0],
+                             _p(st.bonds, _i64p), _p(model.bond, _dp), _p(st.f, _dp),
+                             1 if st.f_valid else 0, dt, gamma, kT, seed, st.step, nsteps)
+    if rc != 0:
+        raise RuntimeError("oracle integrate failed with status %d" % rc)
+    st.f_valid = True
+    st.step += nsteps
+    return st
+
+
+def observables(model: Model, st: State) -> dict:
+    out = np.zeros(NOBS, dtype=np.float64)
+    rc = lib().orc_observables(st.n, _p(st.box, _dp), _p(st.x, _dp), _p(st.v, _dp),
+                               _p(st.img, _i32p), _p(st.types, _i32p), _p(model.masses, _dp),
+                               model.ntypes, _p(model.pair, _dp), st.bonds.shape[0],
+                               _p(st.bonds, _i64p), _p(model.bond, _dp), _p(out, _dp))
+    if rc != 0:
+        raise RuntimeError("oracle observables failed with status %d" % rc)
+    return dict(zip(OBS_NAMES, out.tolist()))
+
+
+def rdf_counts(box, x, rmax, nbins):
+    x = _f64(x, (-1, 3))
+    L = _f64(box)
+    c = np.zeros(nbins, dtype=np.int64)
+    lib().orc_rdf_counts(x.shape[0], _p(L, _dp), _p(x, _dp), rmax, nbins, _p(c, _i64p))
+    return c

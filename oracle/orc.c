@@ -1,0 +1,630 @@
+/*
+ * Oracle implementation: see orc.h.  TEST INFRASTRUCTURE ONLY -- the product
+ * path never loads or calls this code.
+ *
+ * Every function states the definition it writes out.  The paper (ESPResSo++)
+ * names the ingredients but prints no formulas; the formulas here are the
+ * textbook ones for the Kremer-Grest model, and the readings chosen where the
+ * paper is silent are marked "Reading".
+ */
+#include "orc.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10, as defined in Salmon, Moraes, Dror and Shaw, "Parallel     */
+/* random numbers: as easy as 1, 2, 3", SC'11: ten rounds of two 32x32->64   */
+/* multiplies (multipliers 0xD2511F53, 0xCD9E8D57) with the counter words    */
+/* permuted and xor-ed with the key, the key bumped by the Weyl constants    */
+/* 0x9E3779B9, 0xBB67AE85 between rounds.                                    */
+/* ------------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Reading (noise distribution; the paper names only gamma and T for the
+ * Langevin thermostat): the top 24 bits k of a word give the odd integer
+ * 2k+1-2^24, scaled by 2^-25.  The result lies in (-1/2, 1/2), has mean 0 and
+ * variance (1-2^-48)/12, and is exact in binary32 and binary64. */
+double orc_uniform_centered(uint32_t w) {
+    int32_t k = (int32_t)(w >> 8);
+    int32_t odd = 2 * k + 1 - 16777216;
+    return ldexp((double)odd, -25);
+}
+
+void orc_uniform_fill(const uint32_t* w, int64_t n, double* out) {
+    for (int64_t i = 0; i < n; ++i) out[i] = orc_uniform_centered(w[i]);
+}
+
+/* Reading: key = (seed low word, seed high word); counter = (particle id,
+ * step low word, step high word, stream tag 0 = Langevin).  Words 0..2 give
+ * the x, y, z noise of that particle at that step. */
+static void langevin_r(uint64_t seed, int64_t id, int64_t step, double r[3]) {
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint64_t s = (uint64_t)step;
+    uint32_t ctr[4] = {(uint32_t)id, (uint32_t)(s & 0xffffffffu), (uint32_t)(s >> 32), 0u};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    r[0] = orc_uniform_centered(out[0]);
+    r[1] = orc_uniform_centered(out[1]);
+    r[2] = orc_uniform_centered(out[2]);
+}
+
+void orc_langevin_noise(uint64_t seed, int64_t step, int64_t n, double* out) {
+    for (int64_t i = 0; i < n; ++i) langevin_r(seed, i, step, out + 3 * i);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Periodic box                                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Minimum-image convention: the periodic copy of d nearest to zero. */
+static double min_image(double d, double L) { return d - L * nearbyint(d / L); }
+
+static void min_image_vec(const double* xi, const double* xj, const double* L, double d[3]) {
+    for (int c = 0; c < 3; ++c) d[c] = min_image(xi[c] - xj[c], L[c]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Potentials                                                                */
+/* ------------------------------------------------------------------------ */
+
+/* 12-6 Lennard-Jones energy and -dU/dr / r at distance r (r2 = r*r). */
+static void lj_raw(double eps, double sig, double r2, double* u, double* fr) {
+    double s2 = sig * sig / r2;
+    double s6 = s2 * s2 * s2;
+    *u = 4.0 * eps * (s6 * s6 - s6);
+    *fr = 24.0 * eps * (2.0 * s6 * s6 - s6) / r2;
+}
+
+/* Pair record [kind, eps, sigma, rc, shift_flag, caprad].
+ * kind 1: Lennard-Jones cut at rc (r < rc strictly).  With shift_flag the
+ *   energy is lowered by U(rc) so that it is zero at the cutoff; the force is
+ *   not changed (the example script's shift='auto').  WCA is this with
+ *   rc = 2^(1/6) sigma.
+ * kind 2: capped Lennard-Jones (the example's LennardJonesCapped).  Reading:
+ *   for r < caprad the force keeps the direction of r_ij and the magnitude
+ *   |F(caprad)| it has at caprad; the energy continues linearly,
+ *   U(caprad) + |F(caprad)| (caprad - r), so that F = -dU/dr everywhere. */
+void orc_pair_eval(const double* pp, double r2, double* u, double* fr) {
+    *u = 0.0;
+    *fr = 0.0;
+    int kind = (int)pp[0];
+    double eps = pp[1], sig = pp[2], rc = pp[3];
+    if (kind == 0 || r2 >= rc * rc) return;
+    double shift = 0.0;
+    if (pp[4] != 0.0) {
+        double us, fs;
+        lj_raw(eps, sig, rc * rc, &us, &fs);
+        shift = us;
+    }
+    if (kind == 1) {
+        lj_raw(eps, sig, r2, u, fr);
+        *u -= shift;
+    } else if (kind == 2) {
+        double cap = pp[5];
+        if (r2 < cap * cap) {
+            double uc, frc;
+            lj_raw(eps, sig, cap * cap, &uc, &frc);
+            double fmag = frc * cap; /* |F| at the capping radius */
+            double r = sqrt(r2);
+            *u = uc - shift + fmag * (cap - r);
+            *fr = fmag / r;
+        } else {
+            lj_raw(eps, sig, r2, u, fr);
+            *u -= shift;
+        }
+    }
+}
+
+/* Bond record [kind, K, R0].  kind 1: FENE, U = -1/2 K R0^2 ln(1 - r^2/R0^2),
+ * F_i = -K r_ij / (1 - r^2/R0^2).  Reading: r >= R0 is an error (no bond
+ * breaking); returns 1 then. */
+int orc_bond_eval(const double* bp, double r2, double* u, double* fr) {
+    *u = 0.0;
+    *fr = 0.0;
+    int kind = (int)bp[0];
+    if (kind == 0) return 0;
+    if (kind == 1) {
+        double K = bp[1], R0 = bp[2];
+        double q = r2 / (R0 * R0);
+        if (q >= 1.0) return 1;
+        *u = -0.5 * K * R0 * R0 * log(1.0 - q);
+        *fr = -K / (1.0 - q);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Linked cells (textbook head/next lists), used to find all pairs within a  */
+/* cutoff.  When a box edge holds fewer than 3 cells every particle is       */
+/* compared with every other one instead.                                    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int nc[3];
+    int brute;
+    int64_t* head; /* per cell: first particle, or -1 */
+    int64_t* next; /* per particle: next particle in the same cell, or -1 */
+    int64_t* cell_of;
+} cells_t;
+
+static int64_t cell_coord(double xc, double L, int nc) {
+    double w = xc - L * floor(xc / L); /* into [0, L) */
+    int64_t c = (int64_t)floor(w / (L / nc));
+    if (c < 0) c = 0;
+    if (c >= nc) c = nc - 1;
+    return c;
+}
+
+static void cells_build(cells_t* cl, int64_t n, const double* L, const double* x, double rcut) {
+    cl->brute = 0;
+    for (int c = 0; c < 3; ++c) {
+        cl->nc[c] = (rcut > 0.0) ? (int)floor(L[c] / rcut) : 1;
+        if (cl->nc[c] < 3) cl->brute = 1;
+    }
+    cl->head = NULL;
+    cl->next = NULL;
+    cl->cell_of = NULL;
+    if (cl->brute) return;
+    int64_t ncell = (int64_t)cl->nc[0] * cl->nc[1] * cl->nc[2];
+    cl->head = (int64_t*)malloc(sizeof(int64_t) * ncell);
+    cl->next = (int64_t*)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+    cl->cell_of = (int64_t*)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+    for (int64_t c = 0; c < ncell; ++c) cl->head[c] = -1;
+    /* insert in descending id order so each cell's list runs in ascending id */
+    for (int64_t i = n - 1; i >= 0; --i) {
+        int64_t cx = cell_coord(x[3 * i + 0], L[0], cl->nc[0]);
+        int64_t cy = cell_coord(x[3 * i + 1], L[1], cl->nc[1]);
+        int64_t cz = cell_coord(x[3 * i + 2], L[2], cl->nc[2]);
+        int64_t c = (cz * cl->nc[1] + cy) * cl->nc[0] + cx;
+        cl->cell_of[i] = c;
+        cl->next[i] = cl->head[c];
+        cl->head[c] = i;
+    }
+}
+
+static void cells_free(cells_t* cl) {
+    free(cl->head);
+    free(cl->next);
+    free(cl->cell_of);
+}
+
+/* Calls visit(j) for every j != i in the 27 cells around i's cell (or every
+ * j != i when the box is too small for cells).  Expressed as an iterator that
+ * fills a caller buffer to keep the C plain. */
+static int64_t cells_candidates(const cells_t* cl, int64_t n, int64_t i, int64_t* buf) {
+    int64_t m = 0;
+    if (cl->brute) {
+        for (int64_t j = 0; j < n; ++j)
+            if (j != i) buf[m++] = j;
+        return m;
+    }
+    int64_t c = cl->cell_of[i];
+    int64_t cx = c % cl->nc[0];
+    int64_t cy = (c / cl->nc[0]) % cl->nc[1];
+    int64_t cz = c / ((int64_t)cl->nc[0] * cl->nc[1]);
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int64_t ax = (cx + dx + cl->nc[0]) % cl->nc[0];
+                int64_t ay = (cy + dy + cl->nc[1]) % cl->nc[1];
+                int64_t az = (cz + dz + cl->nc[2]) % cl->nc[2];
+                int64_t a = (az * cl->nc[1] + ay) * cl->nc[0] + ax;
+                for (int64_t j = cl->head[a]; j >= 0; j = cl->next[j])
+                    if (j != i) buf[m++] = j;
+            }
+    return m;
+}
+
+static int64_t max_candidates(const cells_t* cl, int64_t n) {
+    if (cl->brute) return n;
+    int64_t ncell = (int64_t)cl->nc[0] * cl->nc[1] * cl->nc[2];
+    int64_t* cnt = (int64_t*)calloc((size_t)ncell, sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i) cnt[cl->cell_of[i]]++;
+    int64_t mx = 0;
+    for (int64_t c = 0; c < ncell; ++c)
+        if (cnt[c] > mx) mx = cnt[c];
+    free(cnt);
+    return 27 * mx + 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Neighbour sets                                                            */
+/* ------------------------------------------------------------------------ */
+static int cmp_i64(const void* a, const void* b) {
+    int64_t x = *(const int64_t*)a, y = *(const int64_t*)b;
+    return (x > y) - (x < y);
+}
+
+/* Definition: all ordered pairs (i, j), j != i, whose minimum-image distance
+ * is below rcut (strict).  O(n^2). */
+int64_t orc_neighbors_brute(int64_t n, const double* L, const double* x, double rcut,
+                            int64_t* row_ptr, int64_t* cols, int64_t cap) {
+    int64_t m = 0;
+    row_ptr[0] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double d[3];
+            min_image_vec(x + 3 * i, x + 3 * j, L, d);
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (r2 < rcut * rcut) {
+                if (m >= cap) return -1;
+                cols[m++] = j;
+            }
+        }
+        row_ptr[i + 1] = m;
+    }
+    return m;
+}
+
+/* The same set found through linked cells of edge >= rcut. */
+int64_t orc_neighbors_cells(int64_t n, const double* L, const double* x, double rcut,
+                            int64_t* row_ptr, int64_t* cols, int64_t cap) {
+    cells_t cl;
+    cells_build(&cl, n, L, x, rcut);
+    int64_t* buf = (int64_t*)malloc(sizeof(int64_t) * (size_t)max_candidates(&cl, n));
+    int64_t m = 0;
+    row_ptr[0] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t nc = cells_candidates(&cl, n, i, buf);
+        int64_t row0 = m;
+        for (int64_t k = 0; k < nc; ++k) {
+            int64_t j = buf[k];
+            double d[3];
+            min_image_vec(x + 3 * i, x + 3 * j, L, d);
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (r2 < rcut * rcut) {
+                if (m >= cap) {
+                    free(buf);
+                    cells_free(&cl);
+                    return -1;
+                }
+                cols[m++] = j;
+            }
+        }
+        qsort(cols + row0, (size_t)(m - row0), sizeof(int64_t), cmp_i64);
+        row_ptr[i + 1] = m;
+    }
+    free(buf);
+    cells_free(&cl);
+    return m;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Forces                                                                    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t* off; /* n+1 */
+    int64_t* nbr; /* partner ids */
+} adj_t;
+
+static void adj_build(adj_t* a, int64_t n, int64_t nbonds, const int64_t* bonds) {
+    a->off = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    a->nbr = (int64_t*)malloc(sizeof(int64_t) * (size_t)(2 * nbonds + 1));
+    for (int64_t b = 0; b < nbonds; ++b) {
+        a->off[bonds[2 * b] + 1]++;
+        a->off[bonds[2 * b + 1] + 1]++;
+    }
+    for (int64_t i = 0; i < n; ++i) a->off[i + 1] += a->off[i];
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    memcpy(fill, a->off, sizeof(int64_t) * (size_t)(n + 1));
+    for (int64_t b = 0; b < nbonds; ++b) {
+        int64_t p = bonds[2 * b], q = bonds[2 * b + 1];
+        a->nbr[fill[p]++] = q;
+        a->nbr[fill[q]++] = p;
+    }
+    free(fill);
+}
+
+static void adj_free(adj_t* a) {
+    free(a->off);
+    free(a->nbr);
+}
+
+/* Definition: F_i = sum over j != i with r_ij < rc(t_i, t_j) of the pair force
+ * plus the sum over bonds (i, p) of the bond force.  There are no exclusions:
+ * bonded beads also interact through the pair potential (Kremer-Grest).
+ * PE_pair = sum over unordered pairs of u, PE_bond = sum over bonds of u,
+ * virial = sum over unordered pairs and bonds of r_ij . F_ij.  Each particle
+ * accumulates its own sum (both orders of every pair are evaluated). */
+int orc_forces(int64_t n, const double* L, const double* x, const int32_t* type,
+               int ntypes, const double* pair_params, int64_t nbonds,
+               const int64_t* bonds, const double* bond_params, double* f,
+               double* energies) {
+    double rmax = 0.0;
+    for (int t = 0; t < ntypes * ntypes; ++t) {
+        const double* pp = pair_params + ORC_PAIR_STRIDE * t;
+        if ((int)pp[0] != 0 && pp[3] > rmax) rmax = pp[3];
+    }
+    cells_t cl;
+    cells_build(&cl, n, L, x, rmax);
+    adj_t adj;
+    adj_build(&adj, n, nbonds, bonds);
+    double* pe_p = (double*)calloc((size_t)n + 1, sizeof(double));
+    double* pe_b = (double*)calloc((size_t)n + 1, sizeof(double));
+    double* vir = (double*)calloc((size_t)n + 1, sizeof(double));
+    int64_t mc = max_candidates(&cl, n);
+    int broken = 0;
+
+#pragma omp parallel reduction(| : broken)
+    {
+        int64_t* buf = (int64_t*)malloc(sizeof(int64_t) * (size_t)mc);
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < n; ++i) {
+            double fi[3] = {0.0, 0.0, 0.0};
+            double ui = 0.0, ub = 0.0, wi = 0.0;
+            if (rmax > 0.0) {
+                int64_t nc = cells_candidates(&cl, n, i, buf);
+                for (int64_t k = 0; k < nc; ++k) {
+                    int64_t j = buf[k];
+                    double d[3];
+                    min_image_vec(x + 3 * i, x + 3 * j, L, d);
+                    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    const double* pp = pair_params + ORC_PAIR_STRIDE * (type[i] * ntypes + type[j]);
+                    double u, fr;
+                    orc_pair_eval(pp, r2, &u, &fr);
+                    for (int c = 0; c < 3; ++c) fi[c] += fr * d[c];
+                    ui += 0.5 * u;
+                    wi += 0.5 * fr * r2;
+                }
+            }
+            for (int64_t k = adj.off[i]; k < adj.off[i + 1]; ++k) {
+                int64_t p = adj.nbr[k];
+                double d[3];
+                min_image_vec(x + 3 * i, x + 3 * p, L, d);
+                double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                double u, fr;
+                if (orc_bond_eval(bond_params, r2, &u, &fr)) broken = 1;
+                for (int c = 0; c < 3; ++c) fi[c] += fr * d[c];
+                ub += 0.5 * u;
+                wi += 0.5 * fr * r2;
+            }
+            for (int c = 0; c < 3; ++c) f[3 * i + c] = fi[c];
+            pe_p[i] = ui;
+            pe_b[i] = ub;
+            vir[i] = wi;
+        }
+        free(buf);
+    }
+    double sp = 0.0, sb = 0.0, sw = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        sp += pe_p[i];
+        sb += pe_b[i];
+        sw += vir[i];
+    }
+    if (energies) {
+        energies[0] = sp;
+        energies[1] = sb;
+        energies[2] = sw;
+    }
+    free(pe_p);
+    free(pe_b);
+    free(vir);
+    adj_free(&adj);
+    cells_free(&cl);
+    return broken ? -4 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Integrator                                                                */
+/* ------------------------------------------------------------------------ */
+
+/* Wrap one coordinate into [0, L), counting crossings in the image counter.
+ * Reading: a coordinate that rounds to exactly L after adding L is set to 0. */
+static void wrap_coord(double* xc, int32_t* im, double L) {
+    if (*xc >= L) {
+        *xc -= L;
+        *im += 1;
+    } else if (*xc < 0.0) {
+        *xc += L;
+        *im -= 1;
+        if (*xc >= L) *xc = 0.0;
+    }
+}
+
+/* Langevin force (added to the conservative force in the force step):
+ * -gamma m v + sqrt(24 gamma m kT / dt) r, r from the Philox stream.
+ * Reading (discretisation; the paper names only gamma and T): the friction
+ * uses the velocity present when the force is evaluated (the half-step
+ * velocity inside a step) and the uniform noise has the variance
+ * 2 gamma m kT / dt of the continuous white noise over one step. */
+static void add_langevin(int64_t n, const double* v, const int32_t* type,
+                         const double* mass_of_type, double* f, double dt, double gamma,
+                         double kT, uint64_t seed, int64_t step) {
+    if (gamma == 0.0) return;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double m = mass_of_type[type[i]];
+        double amp = sqrt(24.0 * gamma * m * kT / dt);
+        double r[3];
+        langevin_r(seed, i, step, r);
+        for (int c = 0; c < 3; ++c) f[3 * i + c] += -gamma * m * v[3 * i + c] + amp * r[c];
+    }
+}
+
+/* Velocity Verlet (the example's VelocityVerlet) with the Langevin extension.
+ * One step from step s-1 to s:
+ *   1. v += dt/2 F/m            (F of step s-1)
+ *   2. x += dt v, wrap into the box, update image counters
+ *   3. F = conservative forces at the new x
+ *   4. F += -gamma m v + sqrt(24 gamma m kT/dt) r(s)
+ *   5. v += dt/2 F/m
+ * Reading: when f is not valid on entry, F of step step0 is first computed
+ * from x, v with the noise of step step0. */
+int orc_integrate(int64_t n, const double* L, double* x, double* v, int32_t* img,
+                  const int32_t* type, const double* mass_of_type, int ntypes,
+                  const double* pair_params, int64_t nbonds, const int64_t* bonds,
+                  const double* bond_params, double* f, int f_valid, double dt,
+                  double gamma, double kT, uint64_t seed, int64_t step0, int64_t nsteps) {
+    double en[3];
+    int st = 0;
+    if (!f_valid) {
+        st = orc_forces(n, L, x, type, ntypes, pair_params, nbonds, bonds, bond_params, f, en);
+        if (st) return st;
+        add_langevin(n, v, type, mass_of_type, f, dt, gamma, kT, seed, step0);
+    }
+    for (int64_t s = step0 + 1; s <= step0 + nsteps; ++s) {
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i) {
+            double m = mass_of_type[type[i]];
+            for (int c = 0; c < 3; ++c) {
+                v[3 * i + c] += 0.5 * dt * f[3 * i + c] / m;
+                x[3 * i + c] += dt * v[3 * i + c];
+                wrap_coord(&x[3 * i + c], &img[3 * i + c], L[c]);
+            }
+        }
+        st = orc_forces(n, L, x, type, ntypes, pair_params, nbonds, bonds, bond_params, f, en);
+        if (st) return st;
+        add_langevin(n, v, type, mass_of_type, f, dt, gamma, kT, seed, s);
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i) {
+            double m = mass_of_type[type[i]];
+            for (int c = 0; c < 3; ++c) v[3 * i + c] += 0.5 * dt * f[3 * i + c] / m;
+        }
+        for (int64_t i = 0; i < 3 * n; ++i)
+            if (!isfinite(x[i]) || !isfinite(v[i])) return -5;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Observables                                                               */
+/* ------------------------------------------------------------------------ */
+static int64_t uf_find(int64_t* parent, int64_t a) {
+    while (parent[a] != a) {
+        parent[a] = parent[parent[a]];
+        a = parent[a];
+    }
+    return a;
+}
+
+/* out[0] KE = sum 1/2 m v^2; out[1] PE_pair; out[2] PE_bond; out[3] virial W;
+ * out[4..6] total momentum; out[7] T = 2 KE / (3 n) (Langevin: no constraint
+ * removes degrees of freedom); out[8] P = (2 KE + W) / (3 V);
+ * out[9] mean bond length; out[10] mean squared radius of gyration over
+ * molecules (connected components of the bond graph with >= 2 beads, from
+ * unwrapped positions x + img L); out[11] number of such molecules. */
+int orc_observables(int64_t n, const double* L, const double* x, const double* v,
+                    const int32_t* img, const int32_t* type, const double* mass_of_type,
+                    int ntypes, const double* pair_params, int64_t nbonds,
+                    const int64_t* bonds, const double* bond_params, double* out) {
+    for (int k = 0; k < ORC_NOBS; ++k) out[k] = 0.0;
+    double* f = (double*)malloc(sizeof(double) * (size_t)(3 * n + 1));
+    double en[3];
+    int st = orc_forces(n, L, x, type, ntypes, pair_params, nbonds, bonds, bond_params, f, en);
+    free(f);
+    double ke = 0.0, p[3] = {0, 0, 0};
+    for (int64_t i = 0; i < n; ++i) {
+        double m = mass_of_type[type[i]];
+        for (int c = 0; c < 3; ++c) {
+            ke += 0.5 * m * v[3 * i + c] * v[3 * i + c];
+            p[c] += m * v[3 * i + c];
+        }
+    }
+    double V = L[0] * L[1] * L[2];
+    out[0] = ke;
+    out[1] = en[0];
+    out[2] = en[1];
+    out[3] = en[2];
+    out[4] = p[0];
+    out[5] = p[1];
+    out[6] = p[2];
+    out[7] = n > 0 ? 2.0 * ke / (3.0 * (double)n) : 0.0;
+    out[8] = (2.0 * ke + en[2]) / (3.0 * V);
+    double bl = 0.0;
+    for (int64_t b = 0; b < nbonds; ++b) {
+        double d[3];
+        min_image_vec(x + 3 * bonds[2 * b], x + 3 * bonds[2 * b + 1], L, d);
+        bl += sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    }
+    out[9] = nbonds > 0 ? bl / (double)nbonds : 0.0;
+
+    int64_t* parent = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    for (int64_t i = 0; i < n; ++i) parent[i] = i;
+    for (int64_t b = 0; b < nbonds; ++b) {
+        int64_t ra = uf_find(parent, bonds[2 * b]), rb = uf_find(parent, bonds[2 * b + 1]);
+        if (ra != rb) parent[ra] = rb;
+    }
+    double* com = (double*)calloc((size_t)(3 * n + 3), sizeof(double));
+    int64_t* cnt = (int64_t*)calloc((size_t)(n + 1), sizeof(int64_t));
+    double* rg = (double*)calloc((size_t)(n + 1), sizeof(double));
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t r = uf_find(parent, i);
+        cnt[r]++;
+        for (int c = 0; c < 3; ++c) com[3 * r + c] += x[3 * i + c] + img[3 * i + c] * L[c];
+    }
+    for (int64_t r = 0; r < n; ++r)
+        if (cnt[r] > 0)
+            for (int c = 0; c < 3; ++c) com[3 * r + c] /= (double)cnt[r];
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t r = uf_find(parent, i);
+        for (int c = 0; c < 3; ++c) {
+            double u = x[3 * i + c] + img[3 * i + c] * L[c] - com[3 * r + c];
+            rg[r] += u * u;
+        }
+    }
+    double rgsum = 0.0;
+    int64_t nmol = 0;
+    for (int64_t r = 0; r < n; ++r)
+        if (cnt[r] >= 2) {
+            rgsum += rg[r] / (double)cnt[r];
+            nmol++;
+        }
+    out[10] = nmol > 0 ? rgsum / (double)nmol : 0.0;
+    out[11] = (double)nmol;
+    free(parent);
+    free(com);
+    free(cnt);
+    free(rg);
+    return st;
+}
+
+/* Unordered pairs with minimum-image distance r < rmax, counted in bin
+ * floor(r / (rmax / nbins)).  O(n^2). */
+void orc_rdf_counts(int64_t n, const double* L, const double* x, double rmax,
+                    int nbins, int64_t* counts) {
+    for (int b = 0; b < nbins; ++b) counts[b] = 0;
+    double dr = rmax / nbins;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = i + 1; j < n; ++j) {
+            double d[3];
+            min_image_vec(x + 3 * i, x + 3 * j, L, d);
+            double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            if (r < rmax) {
+                int b = (int)(r / dr);
+                if (b >= nbins) b = nbins - 1;
+                counts[b]++;
+            }
+        }
+}

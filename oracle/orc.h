@@ -1,0 +1,86 @@
+/*
+ * Oracle for the short-range coarse-grained MD step (ESPResSo++, "Software
+ * design" and "Example usage" sections): plain, slow, double-precision CPU
+ * code written from the definitions of the method.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or helper with the CUDA library, and neither includes the other.
+ *
+ * Conventions (all arrays in particle-id order; particle i has id i):
+ *   x, v, f   : n*3 doubles, row-major (x0,y0,z0,x1,...)
+ *   img       : n*3 int32 periodic image counters (unwrapped = x + img*L)
+ *   L         : 3 box edges of the orthorhombic periodic box
+ *   pair_params: ntypes*ntypes records of ORC_PAIR_STRIDE doubles,
+ *                [kind, eps, sigma, rc, shift_flag, caprad, 0, 0]
+ *                kind: 0 none, 1 Lennard-Jones, 2 capped Lennard-Jones
+ *   bond_params: ORC_BOND_STRIDE doubles [kind, K, R0, 0]; kind 0 none, 1 FENE
+ *   bonds     : nbonds*2 int64 particle ids
+ *
+ * Readings of points the paper leaves open are listed beside each function.
+ */
+#ifndef ORC_H
+#define ORC_H
+#include <stdint.h>
+
+#define ORC_PAIR_STRIDE 8
+#define ORC_BOND_STRIDE 4
+#define ORC_NOBS 12
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+int orc_num_threads(void);
+
+/* Philox4x32-10 counter-based generator (Salmon et al., SC'11). */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* One 32-bit Philox word -> odd multiple of 2^-25 in (-1/2, 1/2). */
+double orc_uniform_centered(uint32_t w);
+void orc_uniform_fill(const uint32_t* w, int64_t n, double* out);
+/* Langevin noise words for particle ids [0,n) at a given step: out n*3. */
+void orc_langevin_noise(uint64_t seed, int64_t step, int64_t n, double* out);
+
+/* Pair and bond potentials at squared distance r2: energy u and scalar fr
+ * such that the force on i is fr * (x_i - x_j). */
+void orc_pair_eval(const double* pp, double r2, double* u, double* fr);
+int orc_bond_eval(const double* bp, double r2, double* u, double* fr);
+
+/* Conservative forces.  energies[0]=PE_pair, [1]=PE_bond, [2]=virial
+ * (sum over pairs and bonds of r_ij . F_ij).  Returns 0, or -4 if a FENE
+ * bond is stretched to r >= R0. */
+int orc_forces(int64_t n, const double* L, const double* x, const int32_t* type,
+               int ntypes, const double* pair_params, int64_t nbonds,
+               const int64_t* bonds, const double* bond_params, double* f,
+               double* energies);
+
+/* Neighbour sets {j != i : |x_i - x_j|_min-image < rcut} in CSR, id order,
+ * columns ascending.  Returns the number of entries (or -1 if cap is short). */
+int64_t orc_neighbors_brute(int64_t n, const double* L, const double* x, double rcut,
+                            int64_t* row_ptr, int64_t* cols, int64_t cap);
+int64_t orc_neighbors_cells(int64_t n, const double* L, const double* x, double rcut,
+                            int64_t* row_ptr, int64_t* cols, int64_t cap);
+
+/* Velocity Verlet with the Langevin thermostat, nsteps steps starting from
+ * step number step0.  f holds the total force of step step0 on entry when
+ * f_valid != 0; otherwise it is computed first.  x, v, img, f are updated. */
+int orc_integrate(int64_t n, const double* L, double* x, double* v, int32_t* img,
+                  const int32_t* type, const double* mass_of_type, int ntypes,
+                  const double* pair_params, int64_t nbonds, const int64_t* bonds,
+                  const double* bond_params, double* f, int f_valid, double dt,
+                  double gamma, double kT, uint64_t seed, int64_t step0, int64_t nsteps);
+
+/* Observables (see orc.c for the definitions). */
+int orc_observables(int64_t n, const double* L, const double* x, const double* v,
+                    const int32_t* img, const int32_t* type, const double* mass_of_type,
+                    int ntypes, const double* pair_params, int64_t nbonds,
+                    const int64_t* bonds, const double* bond_params, double* out);
+
+/* Unique-pair distance histogram for r < rmax in nbins equal bins. */
+void orc_rdf_counts(int64_t n, const double* L, const double* x, double rmax,
+                    int nbins, int64_t* counts);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,399 @@
+"""Pins for the oracle: checks against what the mathematics and the literature
+fix, independent of the oracle's own code (closed forms, known-answer vectors,
+brute force, invariants, limits).  CPU only."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2608_14911_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def golden_values():
+    vals = {}
+    with open(os.path.join(GOLDEN, "literature_values.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            name, value, tol = line.split()[:3]
+            vals[name] = (float(value), float(tol))
+    return vals
+
+
+LIT = golden_values()
+KG = O.Model(1, {(0, 0): ("wca", 1.0, 1.0)}, ("fene", 30.0, 1.5))
+
+
+# --------------------------------------------------------------------------
+# Philox and the noise map
+# --------------------------------------------------------------------------
+def test_philox_known_answers():
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            rows.append([int(t, 16) for t in line.split()])
+    assert len(rows) == 3
+    for r in rows:
+        out = O.philox(r[0:4], r[4:6])
+        assert [int(v) for v in out] == r[6:10]
+
+
+def test_uniform_map_is_the_odd_grid():
+    # every top-24-bit pattern must land on a distinct odd multiple of 2^-25
+    k = np.arange(2 ** 24, dtype=np.uint64)
+    words = ((k << np.uint64(8)) | np.uint64(0xA5)).astype(np.uint32)
+    r = O.uniform_centered(words)
+    j = np.round(r * 2.0 ** 25).astype(np.int64)
+    assert np.all(j.astype(np.float64) * 2.0 ** -25 == r)
+    expect = np.arange(-(2 ** 24 - 1), 2 ** 24, 2, dtype=np.int64)
+    assert np.array_equal(np.sort(j), expect)
+    assert r.max() < 0.5 and r.min() > -0.5
+    # low 8 bits are ignored
+    assert O.uniform_centered(np.array([0x12345600], np.uint32))[0] == \
+        O.uniform_centered(np.array([0x123456ff], np.uint32))[0]
+
+
+def test_langevin_noise_keying():
+    a = O.langevin_noise(42, 7, 5)
+    b = O.langevin_noise(42, 7, 5)
+    c = O.langevin_noise(42, 8, 5)
+    d = O.langevin_noise(43, 7, 5)
+    assert np.array_equal(a, b)
+    assert not np.array_equal(a, c) and not np.array_equal(a, d)
+    # particle i at step s uses counter (i, s_lo, s_hi, 0) under key (seed_lo, seed_hi)
+    out = O.philox([3, 7, 0, 0], [42, 0])
+    assert np.array_equal(a[3], O.uniform_centered(out[:3]))
+    big = (1 << 33) + 5
+    out = O.philox([1, big & 0xffffffff, big >> 32, 0], [(9 << 32 | 11) & 0xffffffff, 9])
+    assert np.array_equal(O.langevin_noise((9 << 32) | 11, big, 2)[1],
+                          O.uniform_centered(out[:3]))
+
+
+# --------------------------------------------------------------------------
+# Potentials
+# --------------------------------------------------------------------------
+def test_lj_closed_forms():
+    m = O.Model(1, {(0, 0): ("lj", 1.0, 1.0, 3.0, False)})
+    rmin, tol = LIT["lj_min_r"]
+    u, fr = O.pair_eval(m, 0, 0, rmin ** 2)
+    assert abs(u - LIT["lj_min_u"][0]) < 1e-12
+    assert abs(fr) < 1e-12
+    u, fr = O.pair_eval(m, 0, 0, 1.0)
+    assert abs(u) < 1e-15 and fr > 0  # U(sigma) = 0, repulsive inside the well
+    u, fr = O.pair_eval(m, 0, 0, 2.5 ** 2)
+    assert abs(u - LIT["lj_u_rc25"][0]) < LIT["lj_u_rc25"][1]
+    # epsilon and sigma both enter: the minimum scales with sigma, depth with eps
+    m2 = O.Model(1, {(0, 0): ("lj", 2.0, 1.5, 5.0, False)})
+    u, fr = O.pair_eval(m2, 0, 0, (rmin * 1.5) ** 2)
+    assert abs(u + 2.0) < 1e-12 and abs(fr) < 1e-12
+    # beyond the cutoff nothing
+    assert O.pair_eval(m, 0, 0, 3.0 ** 2) == (0.0, 0.0)
+
+
+def test_shifted_lj_and_wca_vanish_at_cutoff():
+    m = O.Model(1, {(0, 0): ("lj", 1.0, 1.0, 2.5, True)})
+    u, fr = O.pair_eval(m, 0, 0, (2.5 - 1e-9) ** 2)
+    assert abs(u) < 1e-9
+    u0, _ = O.pair_eval(m, 0, 0, 1.0)
+    assert abs(u0 - (-LIT["lj_u_rc25"][0])) < 1e-11  # U(sigma) = -U_raw(rc)
+    w = O.Model(1, {(0, 0): ("wca", 1.0, 1.0)})
+    rc = 2.0 ** (1.0 / 6.0)
+    u, fr = O.pair_eval(w, 0, 0, (rc * (1 - 1e-9)) ** 2)
+    assert abs(u) < 1e-12 and abs(fr) < 1e-6
+    u, fr = O.pair_eval(w, 0, 0, 1.0)
+    assert abs(u - 1.0) < 1e-14  # WCA U(sigma) = eps
+    assert O.pair_eval(w, 0, 0, rc * rc) == (0.0, 0.0)  # strict r < rc
+
+
+def test_capped_lj_holds_force_magnitude():
+    cap = 0.8
+    capped = O.Model(1, {(0, 0): ("lj_capped", 1.0, 1.0, 2.0 ** (1 / 6), True, cap)})
+    plain = O.Model(1, {(0, 0): ("wca", 1.0, 1.0)})
+    u_c, fr_c = O.pair_eval(plain, 0, 0, cap * cap)
+    fmag = fr_c * cap
+    for r in (0.05, 0.3, 0.79):
+        u, fr = O.pair_eval(capped, 0, 0, r * r)
+        assert abs(fr * r - fmag) < 1e-10 * fmag
+        assert abs(u - (u_c + fmag * (cap - r))) < 1e-9 * fmag
+    for r in (0.81, 1.0, 1.1):
+        assert O.pair_eval(capped, 0, 0, r * r) == O.pair_eval(plain, 0, 0, r * r)
+
+
+def test_fene_limits_and_kg_bond_minimum():
+    # harmonic limit at small r: fr -> -K
+    _, fr, _ = O.bond_eval(KG, 1e-8)
+    assert abs(fr + 30.0) < 1e-6
+    # energy diverges towards R0 and the bond breaks at r >= R0
+    u1, _, _ = O.bond_eval(KG, 1.49 ** 2)
+    u2, _, _ = O.bond_eval(KG, 1.4999 ** 2)
+    assert u2 > u1 > 0
+    assert O.bond_eval(KG, 1.5 ** 2)[2] == 1
+    # the total bonded force (FENE + WCA) changes sign at the KG bond minimum
+    def total(r):
+        _, frb, _ = O.bond_eval(KG, r * r)
+        _, frp = O.pair_eval(KG, 0, 0, r * r)
+        return frb + frp
+    lo, hi = 0.9, 1.05
+    assert total(lo) > 0 > total(hi)
+    for _ in range(80):
+        mid = 0.5 * (lo + hi)
+        if total(mid) > 0:
+            lo = mid
+        else:
+            hi = mid
+    val, tol = LIT["kg_bond_min"]
+    assert abs(lo - val) < tol
+
+
+# --------------------------------------------------------------------------
+# Forces: finite differences, Newton's third law, invariances
+# --------------------------------------------------------------------------
+def _total_energy(model, box, x, types, bonds):
+    _, en = O.forces(model, box, x, types, bonds)
+    return en[0] + en[1]
+
+
+def _small_systems():
+    out = []
+    c = I.kg_lattice(4, 16, density=0.85, seed=3, jitter=0.15)
+    out.append(("kg", KG, c))
+    c = I.lj_fcc(2, 2, 2, density=0.8442)
+    g = np.random.default_rng(5)
+    c.x = np.mod(c.x + g.uniform(-0.2, 0.2, c.x.shape), c.box)
+    out.append(("lj", O.Model(1, {(0, 0): ("lj", 1.0, 1.0, 2.5, True)}), c))
+    c = I.lj_fcc(2, 2, 2, density=0.6)
+    c.types = (np.arange(c.n) % 2).astype(np.int32)
+    c.x = np.mod(c.x + g.uniform(-0.3, 0.3, c.x.shape), c.box)
+    two = O.Model(2, {(0, 0): ("lj", 1.0, 1.0, 2.5, True), (0, 1): ("lj", 1.5, 0.9, 2.2, True),
+                      (1, 1): ("wca", 0.7, 1.1)})
+    out.append(("two-type", two, c))
+    c = I.random_positions(40, (5.0, 5.0, 5.0), seed=9)
+    out.append(("capped", O.Model(1, {(0, 0): ("lj_capped", 1.0, 1.0, 1.12246, True, 0.8)}), c))
+    return out
+
+
+@pytest.mark.parametrize("name,model,cfg", _small_systems(), ids=lambda v: v if isinstance(v, str) else "")
+def test_forces_are_minus_energy_gradient(name, model, cfg):
+    f, _ = O.forces(model, cfg.box, cfg.x, cfg.types, cfg.bonds)
+    h = 1e-6
+    rng = np.random.default_rng(1)
+    idx = rng.choice(cfg.n, size=min(cfg.n, 12), replace=False)
+    scale = np.abs(f).max()
+    for i in idx:
+        for c in range(3):
+            xp = cfg.x.copy()
+            xm = cfg.x.copy()
+            xp[i, c] += h
+            xm[i, c] -= h
+            fd = -(_total_energy(model, cfg.box, xp, cfg.types, cfg.bonds)
+                   - _total_energy(model, cfg.box, xm, cfg.types, cfg.bonds)) / (2 * h)
+            assert abs(fd - f[i, c]) < 2e-6 * max(1.0, scale), (name, i, c, fd, f[i, c])
+
+
+@pytest.mark.parametrize("name,model,cfg", _small_systems(), ids=lambda v: v if isinstance(v, str) else "")
+def test_newton_third_law(name, model, cfg):
+    f, _ = O.forces(model, cfg.box, cfg.x, cfg.types, cfg.bonds)
+    assert np.all(np.abs(f.sum(axis=0)) <= 1e-12 * np.abs(f).sum())
+
+
+def test_translation_and_permutation_invariance():
+    c = I.kg_lattice(10, 20, seed=4, jitter=0.1)
+    f0, e0 = O.forces(KG, c.box, c.x, c.types, c.bonds)
+    shift = np.array([3.3, -1.7, 0.45])
+    xs = np.mod(c.x + shift, c.box)
+    f1, e1 = O.forces(KG, c.box, xs, c.types, c.bonds)
+    rel = np.sqrt(((f1 - f0) ** 2).sum() / (f0 ** 2).sum())
+    assert rel < 1e-12
+    assert np.allclose(e1, e0, rtol=1e-12)
+    perm = np.random.default_rng(2).permutation(c.n)
+    inv = np.argsort(perm)
+    bonds = inv[c.bonds]
+    f2, e2 = O.forces(KG, c.box, c.x[perm], c.types[perm], bonds)
+    rel = np.sqrt(((f2[inv] - f0) ** 2).sum() / (f0 ** 2).sum())
+    assert rel < 1e-14
+    assert np.allclose(e2, e0, rtol=1e-13)
+
+
+def test_two_particle_forces_by_hand():
+    # two beads along x across the periodic boundary: distance 1.0 via the image
+    box = np.array([10.0, 10.0, 10.0])
+    x = np.array([[0.25, 5.0, 5.0], [9.25, 5.0, 5.0]])
+    m = O.Model(1, {(0, 0): ("lj", 1.0, 1.0, 2.5, False)})
+    f, en = O.forces(m, box, x, np.zeros(2, np.int32), np.zeros((0, 2), np.int64))
+    # at r = sigma: U = 0, |F| = 24 eps / sigma, pushing particle 0 towards +x
+    assert abs(en[0]) < 1e-14
+    assert abs(f[0, 0] - 24.0) < 1e-12 and abs(f[1, 0] + 24.0) < 1e-12
+    assert abs(en[2] - 24.0) < 1e-12  # virial r.F = 1 * 24
+
+
+# --------------------------------------------------------------------------
+# Neighbour sets
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", ["random", "lj", "kg", "dense"])
+def test_cell_neighbours_equal_brute_force(kind):
+    if kind == "random":
+        c = I.random_positions(500, (9.0, 7.5, 11.0), seed=1)
+        rcut = 2.3
+    elif kind == "lj":
+        c = I.lj_fcc(4, 4, 3)
+        c.x = np.mod(c.x + np.random.default_rng(0).normal(0, 0.1, c.x.shape), c.box)
+        rcut = 2.8
+    elif kind == "kg":
+        c = I.kg_lattice(20, 50, seed=2, jitter=0.2)
+        rcut = 2.0 ** (1 / 6) + 0.4
+    else:
+        c = I.random_positions(1200, (8.0, 8.0, 8.0), seed=3)
+        rcut = 1.5
+    rb, cb = O.neighbors(c.box, c.x, rcut, method="brute")
+    rc_, cc = O.neighbors(c.box, c.x, rcut, method="cells")
+    assert np.array_equal(rb, rc_) and np.array_equal(cb, cc)
+    assert cb.size > 0
+
+
+def test_neighbour_count_matches_ideal_gas_estimate():
+    # uniform random points: mean neighbour count -> rho * 4/3 pi r^3
+    c = I.random_positions(4000, (15.0, 15.0, 15.0), seed=11)
+    row, cols = O.neighbors(c.box, c.x, 1.5)
+    rho = c.n / np.prod(c.box)
+    expect = rho * 4.0 / 3.0 * math.pi * 1.5 ** 3
+    assert abs(cols.size / c.n - expect) < 0.05 * expect
+
+
+# --------------------------------------------------------------------------
+# Integrator
+# --------------------------------------------------------------------------
+FREE = O.Model(1, {})
+
+
+def _free_variance_closed_form(nsteps, dt, gamma, kT, m=1.0):
+    """Exact variance of one full-step velocity component of a free particle
+    under the scheme (friction on the velocity present at the force step,
+    noise variance 2 gamma m kT / dt), starting from v = 0."""
+    S = 2.0 * gamma * m * kT / dt            # noise force variance
+    vh = (dt / (2 * m)) ** 2 * S             # var v(1/2)
+    var_full = []
+    for s in range(1, nsteps + 1):
+        var_full.append((1 - gamma * dt / 2) ** 2 * vh + (dt / (2 * m)) ** 2 * S)
+        vh = (1 - gamma * dt) ** 2 * vh + (dt / m) ** 2 * S
+    return np.array(var_full)
+
+
+@pytest.mark.parametrize("gamma,dt", [(10.0, 0.05), (1.0, 0.005)])
+def test_free_particle_langevin_closed_form(gamma, dt):
+    n = 200000
+    kT = 1.7
+    nsteps = 12 if gamma * dt > 0.1 else 3
+    st = O.State(np.array([50.0, 50.0, 50.0]), np.full((n, 3), 25.0))
+    expect = _free_variance_closed_form(nsteps, dt, gamma, kT)
+    got = []
+    for s in range(nsteps):
+        O.integrate(FREE, st, 1, dt, gamma, kT, seed=123)
+        got.append((st.v ** 2).mean())
+    got = np.array(got)
+    # sample variance of 3n draws; the uniform noise has kurtosis < 3 so the
+    # Gaussian error bar sqrt(2/3n) is conservative
+    err = expect * np.sqrt(2.0 / (3 * n))
+    assert np.all(np.abs(got - expect) < 5 * err), (got, expect)
+    if gamma * dt > 0.1:
+        # equilibrium: full-step velocities carry exactly kT/m
+        assert abs(expect[-1] - kT) < 1e-6 * kT
+    assert abs(st.v.mean()) < 5 * np.sqrt(expect[-1] / (3 * n))
+
+
+def test_reversibility_without_thermostat():
+    c = I.kg_lattice(5, 20, seed=8, jitter=0.05)
+    st = O.State(c.box, c.x, I.maxwell_velocities(c.n, 1.0, seed=3), c.img, c.types, c.bonds)
+    x0 = st.x + st.img * st.box
+    O.integrate(KG, st, 200, 0.005, 0.0, 0.0, seed=1)
+    st.v = -st.v
+    st.f_valid = False
+    O.integrate(KG, st, 200, 0.005, 0.0, 0.0, seed=1)
+    x1 = st.x + st.img * st.box
+    assert np.abs(x1 - x0).max() < 1e-8
+
+
+def _kg_equilibrated(nsteps=2000, seed=42):
+    c = I.kg_lattice(20, 50, seed=seed, jitter=0.05)
+    st = O.State(c.box, c.x, I.maxwell_velocities(c.n, 1.0, seed=seed), c.img, c.types, c.bonds)
+    O.integrate(KG, st, nsteps, 0.005, 1.0, 1.0, seed=seed)
+    return st
+
+
+def test_nve_energy_drift():
+    st = _kg_equilibrated(1000)
+    st.f_valid = False
+    O.integrate(KG, st, 0, 0.005, 0.0, 0.0, seed=0)
+    es = []
+    for _ in range(40):
+        o = O.observables(KG, st)
+        es.append(o["ke"] + o["pe_pair"] + o["pe_bond"])
+        O.integrate(KG, st, 100, 0.005, 0.0, 0.0, seed=0)
+    es = np.array(es) / st.n
+    assert np.abs(es - es[0]).max() < 1e-3
+    # no secular trend beyond the fluctuation level
+    slope = np.polyfit(np.arange(es.size), es, 1)[0] * es.size
+    assert abs(slope) < 1e-3
+
+
+@pytest.mark.slow
+def test_equipartition_and_kg_bond_length():
+    st = _kg_equilibrated(2000)
+    temps, bonds = [], []
+    for _ in range(50):
+        O.integrate(KG, st, 40, 0.005, 1.0, 1.0, seed=42)
+        o = O.observables(KG, st)
+        temps.append(o["temperature"])
+        bonds.append(o["mean_bond"])
+    temps = np.array(temps)
+    # 50 samples of T with per-sample std ~ sqrt(2/(3N)) = 0.026
+    assert abs(temps.mean() - 1.0) < 0.02
+    val, tol = LIT["kg_mean_bond"]
+    assert abs(np.mean(bonds) - val) < tol
+
+
+# --------------------------------------------------------------------------
+# Observables
+# --------------------------------------------------------------------------
+def test_observables_closed_forms():
+    # a straight rod of 8 beads, spacing 1.0, wrapped across the boundary:
+    # Rg^2 = b^2 (n^2 - 1) / 12
+    box = np.array([6.0, 6.0, 6.0])
+    u = np.stack([np.arange(8) * 1.0 + 2.5, np.full(8, 3.0), np.full(8, 3.0)], axis=1)
+    img = np.floor(u / box).astype(np.int32)
+    x = u - img * box
+    bonds = np.stack([np.arange(7), np.arange(1, 8)], axis=1)
+    v = np.zeros((8, 3))
+    v[:, 0] = 2.0
+    st = O.State(box, x, v, img, None, bonds)
+    o = O.observables(O.Model(1, {}, ("fene", 30.0, 1.5)), st)
+    assert abs(o["rg2"] - (64 - 1) / 12.0) < 1e-12
+    assert abs(o["mean_bond"] - 1.0) < 1e-12
+    assert abs(o["ke"] - 8 * 0.5 * 4.0) < 1e-12
+    assert abs(o["px"] - 16.0) < 1e-12 and o["nmol"] == 1.0
+    # ideal gas pressure P = N kT / V with T from the kinetic energy
+    c = I.random_positions(1000, (10.0, 10.0, 10.0), seed=1)
+    vel = I.maxwell_velocities(1000, 1.3, seed=2)
+    o = O.observables(FREE, O.State(c.box, c.x, vel))
+    assert abs(o["pressure"] - 1000 * o["temperature"] / 1000.0) < 1e-12
+    assert abs(o["temperature"] - 1.3) < 1e-6
+
+
+def test_rdf_counts_small():
+    box = np.array([10.0, 10.0, 10.0])
+    x = np.array([[1.0, 1.0, 1.0], [1.5, 1.0, 1.0], [1.0, 2.2, 1.0], [9.7, 1.0, 1.0]])
+    c = O.rdf_counts(box, x, 2.0, 20)
+    # unique distances: 0.5, 1.2, 1.3 (via image), 1.3 (0-3 is 1.3), ...
+    d = []
+    for i in range(4):
+        for j in range(i + 1, 4):
+            dd = x[i] - x[j]
+            dd -= box * np.round(dd / box)
+            d.append(np.linalg.norm(dd))
+    expect = np.histogram([r for r in d if r < 2.0], bins=20, range=(0, 2.0))[0]
+    assert np.array_equal(c, expect)
