@@ -1,0 +1,252 @@
+/*
+ * espp.h -- C ABI of the GB300 short-range coarse-grained MD library
+ * (libespp_gb.so).
+ *
+ * The library implements the per-timestep short-range force loop of the
+ * ESPResSo++ package (paper "ESPResSo++: A Fast and Extensible Molecular
+ * Simulation Package for Coarse-Grained Models", sections "Software design"
+ * and "Example usage"): linked-cell binning, a Verlet list with a skin,
+ * Lennard-Jones / WCA pair forces plus FENE bonds, and velocity Verlet with a
+ * Langevin thermostat, for bead-spring polymer melts and LJ fluids.  All of it
+ * runs in CUDA kernels for sm_103a; nothing falls back to the CPU.
+ *
+ * General rules
+ *  - Every call returns an int status: ESPP_OK (0) or a negative ESPP_ERR_*.
+ *    espp_last_error() gives a message for the last failing call on a handle.
+ *  - Inputs are copied; the caller keeps ownership of every buffer it passes.
+ *    Outputs are written into caller-allocated buffers.
+ *  - Buffers tagged "where" are host pointers when where == ESPP_HOST and
+ *    device pointers (e.g. torch tensors' data_ptr()) when where == ESPP_DEVICE.
+ *  - All particle I/O is in particle-id order (id = index in the arrays the
+ *    caller passed at creation), whatever order the library keeps internally.
+ *  - Coordinates are double, row-major n x 3.  The library stores them in the
+ *    handle's precision (ESPP_FP32 or ESPP_FP64, fixed at creation).
+ *  - All work is issued on the CUDA stream given at creation (NULL = the
+ *    legacy default stream).  Calls that return data to the host synchronise
+ *    that stream.  A handle is not thread-safe; separate handles are
+ *    independent.
+ *  - A handle may hold several independent systems ("replicas", paper section
+ *    "Software design": the example's System object, one per replica).  They
+ *    share the interaction set and are stepped together; all per-particle
+ *    arrays are the replicas' arrays concatenated in replica order.
+ */
+#ifndef ESPP_H
+#define ESPP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define ESPP_OK 0
+#define ESPP_ERR_ARG (-1)            /* invalid argument */
+#define ESPP_ERR_CUDA (-2)           /* a CUDA call failed */
+#define ESPP_ERR_LIST_OVERFLOW (-3)  /* Verlet list still too small after retries */
+#define ESPP_ERR_BOND_BROKEN (-4)    /* a FENE bond reached r >= R0 */
+#define ESPP_ERR_NONFINITE (-5)      /* a position became NaN or infinite */
+#define ESPP_ERR_TIMEOUT (-6)        /* a bounded device wait gave up */
+#define ESPP_ERR_BOX_TOO_SMALL (-7)  /* fewer than 3 cells of rc+skin along an edge */
+#define ESPP_ERR_STATE (-8)          /* call out of order (e.g. no positions set) */
+#define ESPP_ERR_IO (-9)             /* checkpoint file error */
+
+/* ---- enumerations -------------------------------------------------------- */
+#define ESPP_FP32 1
+#define ESPP_FP64 2
+
+#define ESPP_HOST 0
+#define ESPP_DEVICE 1
+
+/* interaction kinds for espp_set_interaction */
+#define ESPP_NONE 0
+#define ESPP_LJ 1         /* params: eps, sigma, rc, shift (0/1)                */
+#define ESPP_WCA 2        /* params: eps, sigma  (rc = 2^(1/6) sigma, shifted)  */
+#define ESPP_LJ_CAPPED 3  /* params: eps, sigma, rc, shift (0/1), caprad        */
+#define ESPP_FENE 4       /* params: K, R0  (applies to every bond)             */
+
+#define ESPP_MAX_TYPES 8
+#define ESPP_MAX_BONDS_PER_PARTICLE 2
+
+typedef struct espp_system* espp_h;
+
+/* One replica of a batched handle. */
+typedef struct {
+    double box[3];          /* orthorhombic periodic box edges */
+    int64_t n;              /* particles */
+    const int32_t* types;   /* n particle types in [0, ESPP_MAX_TYPES), or NULL = all 0 */
+    int64_t n_bonds;
+    const int64_t* bonds;   /* n_bonds x 2 local particle ids, or NULL */
+    uint64_t seed;          /* Philox key of this replica's thermostat noise */
+} espp_replica_desc;
+
+/* Observables of one replica (paper: computeEnergy() in "Example usage").
+ * Energies are sums over the replica; temperature = 2 ke / (3 n);
+ * pressure = (2 ke + virial) / (3 V); virial = sum over pairs and bonds of
+ * r_ij . F_ij; mean_bond over bonds; rg2 = mean over molecules (connected
+ * components of the bond graph with >= 2 beads) of the squared radius of
+ * gyration of the unwrapped positions. */
+typedef struct {
+    int64_t step;
+    int64_t n;
+    double ke, pe_pair, pe_bond, virial;
+    double px, py, pz;
+    double temperature, pressure;
+    double mean_bond, rg2;
+    int64_t n_molecules;
+    int64_t n_rebuilds;
+    uint32_t error_word;
+    uint32_t reserved;
+} espp_obs_t;
+
+/* ---- creation ------------------------------------------------------------ */
+
+/* Create a handle holding one system: paper "Example usage" (System,
+ * OrthorhombicBC(box), addParticles with ids/types, bonded topology).
+ * box: 3 edges; n particles with types[n] (NULL = all type 0); bonds: n_bonds
+ * pairs of particle ids (NULL if none; at most 2 bonds per particle);
+ * precision ESPP_FP32 or ESPP_FP64; seed keys the Philox noise; cuda_stream is
+ * a cudaStream_t (NULL = default stream).  On success *out owns all device
+ * memory of the system until espp_system_destroy.  Errors: ESPP_ERR_ARG. */
+int espp_system_create(const double box[3], int64_t n, const int32_t* types,
+                       int64_t n_bonds, const int64_t* bonds, int precision,
+                       uint64_t seed, void* cuda_stream, espp_h* out);
+
+/* Create a handle holding R independent replicas (descs[R]), stepped together
+ * in one graph-captured launch per step.  Particle arrays of all other calls
+ * are the replicas' arrays concatenated in replica order. */
+int espp_batch_create(int32_t R, const espp_replica_desc* descs, int precision,
+                      void* cuda_stream, espp_h* out);
+
+int espp_system_destroy(espp_h h);
+
+/* ---- state --------------------------------------------------------------- */
+
+/* Set positions x (n*3; wrapped into the box, crossings added to the image
+ * counters), velocities v (n*3 or NULL = zero) and image counters img (n*3 or
+ * NULL = zero), in id order, from host or device memory (where).  Marks the
+ * neighbour list and the stored force stale.  Paper "Example usage":
+ * addParticles(pos, v). */
+int espp_set_state(espp_h h, const double* x, const double* v, const int32_t* img, int where);
+
+/* Read positions (wrapped into [0,L)), velocities and image counters in id
+ * order into caller buffers (each may be NULL).  Synchronises the stream. */
+int espp_get_state(espp_h h, double* x, double* v, int32_t* img, int where);
+
+/* Set the step number of the state (keys the Philox noise counter). */
+int espp_set_step(espp_h h, int64_t step);
+
+/* ---- interactions -------------------------------------------------------- */
+
+/* Paper "Software design" (VerletListInteractionTemplate<Potential>,
+ * setPotential(type1, type2, potential)) and "Example usage"
+ * (LennardJones(eps, sigma, rc, shift='auto'), LennardJonesCapped(...,
+ * caprad)).  kind = ESPP_LJ | ESPP_WCA | ESPP_LJ_CAPPED | ESPP_NONE sets the
+ * pair potential of types (type_a, type_b) and (type_b, type_a); kind =
+ * ESPP_FENE sets the bond potential of every bond (types ignored).  params as
+ * listed beside the kinds; shift = 1 lowers the energy by U(rc).  The cutoff
+ * of every pair must not exceed the list cutoff of espp_build_neighbors.
+ * Marks the stored force stale. */
+int espp_set_interaction(espp_h h, int kind, int type_a, int type_b, const double* params,
+                         int64_t n_params);
+
+/* Per-type mass (default 1 for every type). */
+int espp_set_mass(espp_h h, int type, double mass);
+
+/* ---- neighbour list ------------------------------------------------------ */
+
+/* Paper "Example usage": VerletList(system, cutoff=rc) with system.skin.
+ * Sets the list cutoff rc and skin and builds the cell grid (cells of edge
+ * >= rc + skin, at least 3 per box edge, else ESPP_ERR_BOX_TOO_SMALL), then
+ * bins, resorts and builds the Verlet list of every replica now.  Later
+ * rebuilds happen automatically when a particle has moved more than skin/2
+ * since the last build. */
+int espp_build_neighbors(espp_h h, double rc, double skin);
+
+/* Tests: the current Verlet list as CSR in id order (global ids).  row_ptr has
+ * n+1 entries; cols has room for cap entries.  Returns ESPP_ERR_ARG if cap is
+ * too small (row_ptr[n] then holds the size needed). */
+int espp_get_neighbors(espp_h h, int64_t* row_ptr, int64_t* cols, int64_t cap);
+
+/* ---- forces and dynamics -------------------------------------------------- */
+
+/* Conservative forces (pairs + bonds, no thermostat) at the current
+ * positions, rebuilding the list first when it is stale.  f_out: n*3 doubles
+ * in id order (host or device, where), or NULL.  The integrator's stored
+ * force is not changed. */
+int espp_compute_forces(espp_h h, double* f_out, int where);
+
+/* Paper "Example usage": VelocityVerlet + LangevinThermostat(gamma,
+ * temperature) and integrator.run(nsteps).  Each step: v += dt/2 F/m;
+ * x += dt v (wrap); rebuild the list if needed; F = conservative forces
+ * - gamma m v + sqrt(24 gamma m kT / dt) r with r uniform in (-1/2, 1/2) from
+ * Philox(seed; id, step); v += dt/2 F/m.  gamma = 0 gives plain velocity
+ * Verlet.  Steps run as CUDA graphs on the handle's stream; the call returns
+ * after the work is issued and checked (it synchronises once at the end).
+ * Errors: ESPP_ERR_BOND_BROKEN, ESPP_ERR_NONFINITE, ESPP_ERR_LIST_OVERFLOW. */
+int espp_integrate(espp_h h, int64_t nsteps, double dt, double gamma, double kT);
+
+/* Paper "Example usage": computeEnergy().  Observables of replica 0 (or of
+ * all R replicas into out[R] with espp_observables_batch).  Synchronises. */
+int espp_observables(espp_h h, espp_obs_t* out);
+int espp_observables_batch(espp_h h, espp_obs_t* out, int32_t R);
+
+/* Unique-pair distance histogram of replica `replica` for r < rmax in nbins
+ * equal bins (counts[nbins], host).  rmax must be below half the smallest
+ * box edge. */
+int espp_rdf_counts(espp_h h, int32_t replica, double rmax, int32_t nbins, int64_t* counts);
+
+/* ---- checkpoint ------------------------------------------------------------ */
+
+/* Paper "New features": checkpoint of the state and of the random number
+ * generator.  The Philox noise is a pure function of (seed, id, step), so the
+ * file holds the full internal state (storage order, positions at the last
+ * list build, velocities, force, image counters, step) and a resumed run is
+ * bit-identical to an uninterrupted one. */
+int espp_checkpoint_save(espp_h h, const char* path);
+int espp_checkpoint_load(espp_h h, const char* path);
+
+/* ---- diagnostics ----------------------------------------------------------- */
+const char* espp_last_error(espp_h h);
+uint32_t espp_error_word(espp_h h);
+int64_t espp_num_particles(espp_h h);
+int32_t espp_num_replicas(espp_h h);
+int64_t espp_num_rebuilds(espp_h h);
+int64_t espp_step(espp_h h);
+int32_t espp_list_capacity(espp_h h);
+/* Number of kernel launches issued through this handle (graph replays count
+ * every kernel node they hold once per replay; conditional bodies as run). */
+int64_t espp_kernel_launches(espp_h h);
+
+/* Kernel timing.  With timing enabled (espp_set_kernel_timing(h, 1)), the
+ * CUDA graphs of espp_integrate record CUDA events around the conditional
+ * rebuild node and the step kernel of every step; after each espp_integrate
+ * call the durations of the last graph replay are added up.  out[4] receives
+ * (sum of step-kernel ms, number of step-kernel launches timed, sum of
+ * rebuild-node ms, number of steps timed); reset = 1 clears the sums.
+ * Enabling or disabling rebuilds the graphs. */
+int espp_set_kernel_timing(espp_h h, int enable);
+int espp_kernel_timing(espp_h h, double* out, int reset);
+
+/* Size of the current Verlet list: total entries over all particles and the
+ * largest per-particle count (rebuilds first if the list is stale). */
+int espp_list_stats(espp_h h, int64_t* total_entries, int32_t* max_count);
+
+/* Steps captured per CUDA graph replay in espp_integrate (default 64). */
+int espp_set_graph_chunk(espp_h h, int32_t steps);
+
+/* Tests: fill out[n*3] (device) with the Langevin noise of local ids [0,n) at
+ * `step` under `seed`, as the force kernel draws it. */
+int espp_langevin_noise(uint64_t seed, int64_t step, int64_t n, double* out_device,
+                        void* cuda_stream);
+
+/* Host-side helper (no GPU work): the 3-D Hilbert-curve rank of each cell of an
+ * nx x ny x nz grid (rank[cz*ny*nx + cy*nx + cx]), as used for the storage
+ * order.  Returns ESPP_OK. */
+int espp_hilbert_ranks(int32_t nx, int32_t ny, int32_t nz, int32_t* rank);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ESPP_H */

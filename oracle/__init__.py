@@ -48,6 +48,9 @@ def lib():
         L.orc_forces.argtypes = [ctypes.c_int64, _dp, _dp, _i32p, ctypes.c_int, _dp,
                                  ctypes.c_int64, _i64p, _dp, _dp, _dp]
         L.orc_forces.restype = ctypes.c_int
+        L.orc_forces_subset.argtypes = [ctypes.c_int64, _dp, _dp, _i32p, ctypes.c_int, _dp,
+                                        ctypes.c_int64, _i64p, _dp, ctypes.c_int64, _i64p, _dp]
+        L.orc_forces_subset.restype = ctypes.c_int
         for fn in (L.orc_neighbors_brute, L.orc_neighbors_cells):
             fn.argtypes = [ctypes.c_int64, _dp, _dp, ctypes.c_double, _i64p, _i64p, ctypes.c_int64]
             fn.restype = ctypes.c_int64
@@ -172,6 +175,23 @@ def forces(model: Model, box, x, types, bonds):
     if st != 0:
         raise RuntimeError("oracle: bond broken (status %d)" % st)
     return f, en
+
+
+def forces_subset(model: Model, box, x, types, bonds, sel):
+    """Conservative forces on the particles `sel` only (same definition)."""
+    x = _f64(x, (-1, 3))
+    n = x.shape[0]
+    L = _f64(box)
+    t = np.ascontiguousarray(types, dtype=np.int32)
+    b = np.ascontiguousarray(bonds, dtype=np.int64).reshape(-1, 2)
+    s = np.ascontiguousarray(sel, dtype=np.int64)
+    f = np.zeros((s.size, 3), dtype=np.float64)
+    st = lib().orc_forces_subset(n, _p(L, _dp), _p(x, _dp), _p(t, _i32p), model.ntypes,
+                                 _p(model.pair, _dp), b.shape[0], _p(b, _i64p),
+                                 _p(model.bond, _dp), s.size, _p(s, _i64p), _p(f, _dp))
+    if st != 0:
+        raise RuntimeError("oracle: bond broken (status %d)" % st)
+    return f
 
 
 def neighbors(box, x, rcut, method="cells"):

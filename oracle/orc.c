@@ -436,6 +436,60 @@ int orc_forces(int64_t n, const double* L, const double* x, const int32_t* type,
     return broken ? -4 : 0;
 }
 
+/* The same definition as orc_forces, evaluated only for the particles listed
+ * in sel[nsel] (for sampled checks of large systems): f_out is nsel*3. */
+int orc_forces_subset(int64_t n, const double* L, const double* x, const int32_t* type,
+                      int ntypes, const double* pair_params, int64_t nbonds,
+                      const int64_t* bonds, const double* bond_params, int64_t nsel,
+                      const int64_t* sel, double* f_out) {
+    double rmax = 0.0;
+    for (int t = 0; t < ntypes * ntypes; ++t) {
+        const double* pp = pair_params + ORC_PAIR_STRIDE * t;
+        if ((int)pp[0] != 0 && pp[3] > rmax) rmax = pp[3];
+    }
+    cells_t cl;
+    cells_build(&cl, n, L, x, rmax);
+    adj_t adj;
+    adj_build(&adj, n, nbonds, bonds);
+    int64_t mc = max_candidates(&cl, n);
+    int broken = 0;
+#pragma omp parallel reduction(| : broken)
+    {
+        int64_t* buf = (int64_t*)malloc(sizeof(int64_t) * (size_t)mc);
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t q = 0; q < nsel; ++q) {
+            int64_t i = sel[q];
+            double fi[3] = {0.0, 0.0, 0.0};
+            if (rmax > 0.0) {
+                int64_t nc = cells_candidates(&cl, n, i, buf);
+                for (int64_t k = 0; k < nc; ++k) {
+                    int64_t j = buf[k];
+                    double d[3];
+                    min_image_vec(x + 3 * i, x + 3 * j, L, d);
+                    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    double u, fr;
+                    orc_pair_eval(pair_params + ORC_PAIR_STRIDE * (type[i] * ntypes + type[j]), r2, &u, &fr);
+                    for (int c = 0; c < 3; ++c) fi[c] += fr * d[c];
+                }
+            }
+            for (int64_t k = adj.off[i]; k < adj.off[i + 1]; ++k) {
+                int64_t p = adj.nbr[k];
+                double d[3];
+                min_image_vec(x + 3 * i, x + 3 * p, L, d);
+                double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                double u, fr;
+                if (orc_bond_eval(bond_params, r2, &u, &fr)) broken = 1;
+                for (int c = 0; c < 3; ++c) fi[c] += fr * d[c];
+            }
+            for (int c = 0; c < 3; ++c) f_out[3 * q + c] = fi[c];
+        }
+        free(buf);
+    }
+    adj_free(&adj);
+    cells_free(&cl);
+    return broken ? -4 : 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Integrator                                                                */
 /* ------------------------------------------------------------------------ */

@@ -54,6 +54,12 @@ int orc_forces(int64_t n, const double* L, const double* x, const int32_t* type,
                const int64_t* bonds, const double* bond_params, double* f,
                double* energies);
 
+/* orc_forces restricted to the particles sel[nsel]; f_out is nsel*3. */
+int orc_forces_subset(int64_t n, const double* L, const double* x, const int32_t* type,
+                      int ntypes, const double* pair_params, int64_t nbonds,
+                      const int64_t* bonds, const double* bond_params, int64_t nsel,
+                      const int64_t* sel, double* f_out);
+
 /* Neighbour sets {j != i : |x_i - x_j|_min-image < rcut} in CSR, id order,
  * columns ascending.  Returns the number of entries (or -1 if cap is short). */
 int64_t orc_neighbors_brute(int64_t n, const double* L, const double* x, double rcut,

@@ -1,0 +1,167 @@
+// Shared device-side types of the CUDA library (not used by the oracle).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "../../include/espp.h"
+
+namespace espp {
+
+// ---------------------------------------------------------------------------
+// Precision-generic 4-vectors: float4 (16 B) or a 32-byte aligned double quad.
+// The w lane carries an integer (particle type in positions, local particle id
+// in velocities) stored bit-for-bit.
+// ---------------------------------------------------------------------------
+struct __align__(32) dquad {
+    double x, y, z, w;
+};
+
+template <class T> struct VecOf;
+template <> struct VecOf<float> { using type = float4; };
+template <> struct VecOf<double> { using type = dquad; };
+template <class T> using V4 = typename VecOf<T>::type;
+
+__device__ __host__ __forceinline__ float int_bits_as(float, int v) {
+#ifdef __CUDA_ARCH__
+    return __int_as_float(v);
+#else
+    float f; memcpy(&f, &v, 4); return f;
+#endif
+}
+__device__ __host__ __forceinline__ double int_bits_as(double, int v) {
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)v);
+#else
+    long long l = v; double d; memcpy(&d, &l, 8); return d;
+#endif
+}
+__device__ __forceinline__ int bits_as_int(float f) { return __float_as_int(f); }
+__device__ __forceinline__ int bits_as_int(double d) { return (int)__double_as_longlong(d); }
+
+template <class T>
+__device__ __forceinline__ V4<T> ld4(const V4<T>* p) { return *p; }
+template <>
+__device__ __forceinline__ float4 ld4<float>(const float4* p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ dquad ld4<double>(const dquad* p) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+    double2 a = __ldg(q), b = __ldg(q + 1);
+    dquad r; r.x = a.x; r.y = a.y; r.z = b.x; r.w = b.y;
+    return r;
+}
+
+// plain (coherent) load, for arrays written earlier in the same kernel chain
+template <class T>
+__device__ __forceinline__ V4<T> ldc(const V4<T>* p) { return *p; }
+
+template <class T> __device__ __forceinline__ V4<T> mk4(T x, T y, T z, T w) {
+    V4<T> r; r.x = x; r.y = y; r.z = z; r.w = w; return r;
+}
+
+// ---------------------------------------------------------------------------
+// Half kick and drift with a fixed rounding sequence (explicit intrinsics, so
+// the compiler cannot contract them differently in different kernels): the
+// result of a run does not depend on how it is split into integrate calls.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+// v + (dt/2 * f) / m, with 1/m precomputed
+template <class T>
+__device__ __forceinline__ T half_kick(T v, T f, T half_dt, T inv_m) {
+    return fma_rn(mul_rn(half_dt, f), inv_m, v);
+}
+// x + dt * v
+template <class T>
+__device__ __forceinline__ T drift(T x, T v, T dt) {
+    return fma_rn(dt, v, x);
+}
+
+// ---------------------------------------------------------------------------
+// Minimum image of xi - xj for coordinates stored in [0, L).  The periodic
+// shift is applied to the larger coordinate first; that subtraction is exact
+// (Sterbenz: the coordinate lies in [L/2, L)), so the result carries a single
+// rounding, as the plain difference of two nearby coordinates does.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T min_image(T xi, T xj, T L, T halfL) {
+    T d = xi - xj;
+    if (d > halfL) d = (xi - L) - xj;
+    else if (d < -halfL) d = xi - (xj - L);
+    return d;
+}
+
+// ---------------------------------------------------------------------------
+// Per-replica geometry, resident in device memory.
+// ---------------------------------------------------------------------------
+template <class T> struct RepGeom {
+    T L[3];
+    T halfL[3];
+    T cells_per_len[3];  // nc / L
+    int nc[3];
+    int cell_off;        // first cell (rank space) of this replica
+    int p_off;           // first particle slot
+    int n;               // particles
+    int pad;
+    unsigned long long seed;
+};
+
+// Tile table: blocks walk tiles; a tile never straddles two replicas.
+struct Tile {
+    int start;  // first particle slot
+    int count;  // particles in the tile (<= TILE)
+    int rep;
+    int pad;
+};
+
+// Pair potential record for one (type_i, type_j), derived on the host.
+template <class T> struct PairRec {
+    int kind;   // 0 none, ESPP_LJ, ESPP_LJ_CAPPED (WCA is LJ)
+    int pad;
+    T rc2;
+    T sig2;
+    T eps24;    // 24 eps
+    T eps4;     // 4 eps
+    T shift;    // U(rc) subtracted when shifted, else 0
+    T cap2;     // caprad^2 (capped kind)
+    T cap;      // caprad
+    T capF;     // |F(caprad)|
+    T capU;     // U(caprad) - shift
+};
+
+template <class T> struct BondRec {
+    int kind;   // 0 none, ESPP_FENE
+    int pad;
+    T K;
+    T inv_R02;
+    T halfKR02;  // K R0^2 / 2
+};
+
+// Control block in device memory (one per handle).
+struct Ctrl {
+    long long step;            // step number of the stored state
+    unsigned int err;          // ESPP error bits (see below)
+    unsigned int abort;        // non-zero freezes every later step kernel
+    unsigned int any_req;      // some replica requested a rebuild
+    unsigned int blocks_done;  // last-block counter of the step kernel
+    unsigned int need_cap;     // largest neighbour count seen by an overflowing build
+    unsigned int n_rebuilds;   // rebuild passes executed (any replica)
+    unsigned int max_count;    // largest neighbour count of the last build
+    unsigned int pad;
+};
+
+enum : unsigned int {
+    ERRBIT_OVERFLOW = 1u,
+    ERRBIT_BOND = 2u,
+    ERRBIT_NONFINITE = 4u,
+    ERRBIT_TIMEOUT = 8u,
+    ERRBIT_CELL = 16u,
+};
+
+constexpr int TILE = 128;          // particles per tile (= threads per block)
+constexpr int MAX_TYPES = ESPP_MAX_TYPES;
+
+}  // namespace espp

@@ -1,0 +1,230 @@
+// State input/output in particle-id order, deterministic FP64 reductions of the
+// observables (paper "Example usage": computeEnergy()), radius of gyration and
+// pair-distance histograms.
+#include "kernels.cuh"
+#include "philox.cuh"
+
+namespace espp {
+
+// Load id-ordered doubles into storage order = id order (the order is reset on
+// every set_state; the next rebuild resorts).  Coordinates are wrapped into
+// [0, L) in double before rounding to T; a value that rounds up to L becomes 0
+// of the next image.
+template <class T>
+__global__ void __launch_bounds__(TILE) k_set_state(DevSys<T> s, const double* __restrict__ x,
+                                                    const double* __restrict__ v,
+                                                    const int* __restrict__ img,
+                                                    const int* __restrict__ types, int cur) {
+    for (int t = blockIdx.x; t < s.ntiles; t += gridDim.x) {
+        const Tile tl = s.tiles[t];
+        if ((int)threadIdx.x >= tl.count) continue;
+        const RepGeom<T>& g = s.reps[tl.rep];
+        const int i = tl.start + threadIdx.x;  // slot == global id
+        T p[3];
+        int im[3];
+        for (int d = 0; d < 3; ++d) {
+            const double L = (double)g.L[d];
+            const double xd = x[3 * (size_t)i + d];
+            const double fl = floor(xd / L);
+            double w = xd - fl * L;
+            int k = (int)fl + (img ? img[3 * (size_t)i + d] : 0);
+            if (w < 0.0) { w += L; k -= 1; }
+            if (w >= L) { w -= L; k += 1; }
+            T wt = (T)w;
+            if (wt >= g.L[d]) { wt = T(0); k += 1; }
+            p[d] = wt;
+            im[d] = k;
+        }
+        const int local = i - g.p_off;
+        s.pos[cur][i] = mk4<T>(p[0], p[1], p[2], int_bits_as(T(0), types ? types[i] : 0));
+        s.xb[i] = s.pos[cur][i];
+        const T vx = v ? (T)v[3 * (size_t)i] : T(0);
+        const T vy = v ? (T)v[3 * (size_t)i + 1] : T(0);
+        const T vz = v ? (T)v[3 * (size_t)i + 2] : T(0);
+        s.vel[i] = mk4<T>(vx, vy, vz, int_bits_as(T(0), local));
+        s.frc[i] = mk4<T>(T(0), T(0), T(0), T(0));
+        s.img[i] = make_int4(im[0], im[1], im[2], 0);
+        s.slot_of_id[i] = i;
+        s.bond_slot[i] = s.bond_gid[i];
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(TILE) k_get_state(DevSys<T> s, double* __restrict__ x,
+                                                    double* __restrict__ v, int* __restrict__ img,
+                                                    int cur) {
+    for (int t = blockIdx.x; t < s.ntiles; t += gridDim.x) {
+        const Tile tl = s.tiles[t];
+        if ((int)threadIdx.x >= tl.count) continue;
+        const RepGeom<T>& g = s.reps[tl.rep];
+        const int i = tl.start + threadIdx.x;
+        const V4<T> vv = s.vel[i];
+        const size_t gid = (size_t)g.p_off + bits_as_int(vv.w);
+        if (x) {
+            const V4<T> p = s.pos[cur][i];
+            x[3 * gid] = p.x;
+            x[3 * gid + 1] = p.y;
+            x[3 * gid + 2] = p.z;
+        }
+        if (v) {
+            v[3 * gid] = vv.x;
+            v[3 * gid + 1] = vv.y;
+            v[3 * gid + 2] = vv.z;
+        }
+        if (img) {
+            const int4 im = s.img[i];
+            img[3 * gid] = im.x;
+            img[3 * gid + 1] = im.y;
+            img[3 * gid + 2] = im.z;
+        }
+    }
+}
+
+// One block per replica sums its tiles' partials in a fixed order.
+template <class T>
+__global__ void __launch_bounds__(256) k_reduce_obs(DevSys<T> s, double* __restrict__ out) {
+    const int r = blockIdx.x;
+    const int t0 = s.rep_tile_off[r], t1 = s.rep_tile_off[r + 1];
+    __shared__ double sh[256];
+    for (int k = 0; k < NPART; ++k) {
+        double a = 0.0;
+        for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) a += s.partials[(size_t)t * NPART + k];
+        sh[threadIdx.x] = a;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[(size_t)r * NPART + k] = sh[0];
+        __syncthreads();
+    }
+}
+
+// One warp per molecule: centre of the unwrapped positions, then the mean
+// squared distance from it, both summed in a fixed lane order.
+template <class T>
+__global__ void k_rg2(DevSys<T> s, int cur, const int* __restrict__ members,
+                      const int* __restrict__ off, const int* __restrict__ mrep, int nmol,
+                      double* __restrict__ rg2) {
+    const int lane = threadIdx.x & 31;
+    const int m = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (m >= nmol) return;
+    const RepGeom<T>& g = s.reps[mrep[m]];
+    const int b = off[m], e = off[m + 1];
+    double c[3] = {0.0, 0.0, 0.0};
+    for (int k = b + lane; k < e; k += 32) {
+        const int slot = s.slot_of_id[members[k]];
+        const V4<T> p = s.pos[cur][slot];
+        const int4 im = s.img[slot];
+        c[0] += (double)p.x + (double)im.x * (double)g.L[0];
+        c[1] += (double)p.y + (double)im.y * (double)g.L[1];
+        c[2] += (double)p.z + (double)im.z * (double)g.L[2];
+    }
+    for (int d = 0; d < 3; ++d) {
+        for (int o = 16; o > 0; o >>= 1) c[d] += __shfl_xor_sync(0xffffffffu, c[d], o);
+        c[d] /= (double)(e - b);
+    }
+    double a = 0.0;
+    for (int k = b + lane; k < e; k += 32) {
+        const int slot = s.slot_of_id[members[k]];
+        const V4<T> p = s.pos[cur][slot];
+        const int4 im = s.img[slot];
+        const double ux = (double)p.x + (double)im.x * (double)g.L[0] - c[0];
+        const double uy = (double)p.y + (double)im.y * (double)g.L[1] - c[1];
+        const double uz = (double)p.z + (double)im.z * (double)g.L[2] - c[2];
+        a += ux * ux + uy * uy + uz * uz;
+    }
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) rg2[m] = a / (double)(e - b);
+}
+
+// Unique pairs (slot i < slot j) of one replica with r < rmax; integer bin
+// counts (exact under atomics).
+template <class T>
+__global__ void __launch_bounds__(256) k_rdf(DevSys<T> s, int cur, int rep, T rmax2, double inv_dr,
+                                             int nbins, unsigned long long* __restrict__ counts) {
+    extern __shared__ unsigned int hist[];
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    const RepGeom<T>& g = s.reps[rep];
+    const V4<T>* __restrict__ P = s.pos[cur];
+    const int n = g.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+      for (int j = i + 1; j < n; ++j) {
+        const V4<T> a = P[g.p_off + i], c = P[g.p_off + j];
+        const T dx = min_image(a.x, c.x, g.L[0], g.halfL[0]);
+        const T dy = min_image(a.y, c.y, g.L[1], g.halfL[1]);
+        const T dz = min_image(a.z, c.z, g.L[2], g.halfL[2]);
+        const T r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < rmax2) {
+            int b = (int)(sqrt((double)r2) * inv_dr);
+            if (b >= nbins) b = nbins - 1;
+            atomicAdd(&hist[b], 1u);
+        }
+      }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x)
+        if (hist[b]) atomicAdd(&counts[b], (unsigned long long)hist[b]);
+}
+
+__global__ void k_noise(unsigned long long seed, long long step, long long n, double* out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double rx, ry, rz;
+    langevin_noise<double>(seed, (int)i, step, rx, ry, rz);
+    out[3 * i] = rx;
+    out[3 * i + 1] = ry;
+    out[3 * i + 2] = rz;
+}
+
+template <class T>
+void Launch<T>::set_state(const DevSys<T>& s, const double* x, const double* v, const int* img,
+                          const int* types_by_gid, int cur, cudaStream_t st) {
+    k_set_state<T><<<s.ntiles, TILE, 0, st>>>(s, x, v, img, types_by_gid, cur);
+}
+
+template <class T>
+void Launch<T>::get_state(const DevSys<T>& s, double* x, double* v, int* img, int cur,
+                          cudaStream_t st) {
+    k_get_state<T><<<s.ntiles, TILE, 0, st>>>(s, x, v, img, cur);
+}
+
+template <class T>
+void Launch<T>::reduce_obs(const DevSys<T>& s, double* out, cudaStream_t st) {
+    k_reduce_obs<T><<<s.R, 256, 0, st>>>(s, out);
+}
+
+template <class T>
+void Launch<T>::rg2(const DevSys<T>& s, int cur, const int* members, const int* off,
+                    const int* mrep, int nmol, double* out, cudaStream_t st) {
+    if (nmol <= 0) return;
+    const int warps_per_block = 4;
+    k_rg2<T><<<(nmol + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, st>>>(
+        s, cur, members, off, mrep, nmol, out);
+}
+
+template <class T>
+void Launch<T>::rdf(const DevSys<T>& s, int cur, int rep, double rmax, int nbins,
+                    unsigned long long* counts, cudaStream_t st) {
+    k_rdf<T><<<4 * 152, 256, sizeof(unsigned int) * nbins, st>>>(s, cur, rep, (T)(rmax * rmax),
+                                                                 nbins / rmax, nbins, counts);
+}
+
+void launch_noise(unsigned long long seed, long long step, long long n, double* out,
+                  cudaStream_t st) {
+    if (n <= 0) return;
+    k_noise<<<(unsigned int)((n + 255) / 256), 256, 0, st>>>(seed, step, n, out);
+}
+
+template void Launch<float>::set_state(const DevSys<float>&, const double*, const double*, const int*, const int*, int, cudaStream_t);
+template void Launch<double>::set_state(const DevSys<double>&, const double*, const double*, const int*, const int*, int, cudaStream_t);
+template void Launch<float>::get_state(const DevSys<float>&, double*, double*, int*, int, cudaStream_t);
+template void Launch<double>::get_state(const DevSys<double>&, double*, double*, int*, int, cudaStream_t);
+template void Launch<float>::reduce_obs(const DevSys<float>&, double*, cudaStream_t);
+template void Launch<double>::reduce_obs(const DevSys<double>&, double*, cudaStream_t);
+template void Launch<float>::rg2(const DevSys<float>&, int, const int*, const int*, const int*, int, double*, cudaStream_t);
+template void Launch<double>::rg2(const DevSys<double>&, int, const int*, const int*, const int*, int, double*, cudaStream_t);
+template void Launch<float>::rdf(const DevSys<float>&, int, int, double, int, unsigned long long*, cudaStream_t);
+template void Launch<double>::rdf(const DevSys<double>&, int, int, double, int, unsigned long long*, cudaStream_t);
+
+}  // namespace espp

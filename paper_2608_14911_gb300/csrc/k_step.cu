@@ -1,0 +1,365 @@
+// The per-step kernel: pair forces over the Verlet list (Lennard-Jones / WCA /
+// capped LJ, paper "Software design": VerletListInteractionTemplate<Potential>
+// with computeForce/computeEnergy; "Example usage": LennardJones(..., shift=
+// 'auto'), LennardJonesCapped), FENE bonds, the Langevin thermostat
+// ("Example usage": LangevinThermostat(gamma, temperature) attached through
+// addExtension) and velocity Verlet ("Example usage": VelocityVerlet), fused
+// into one pass per particle.
+//
+// One thread per particle, particles in cell (Hilbert) order, 128 per block.
+// Each thread sums the forces on its own particle from both directions of the
+// full list, so no force atomics are needed.  In MODE_STEP the thread then
+// completes the step and starts the next one:
+//   F_s  = F_pair + F_bond - gamma m v_{s-1/2} + sqrt(24 gamma m kT/dt) r_s
+//   v_s  = v_{s-1/2} + dt/2 F_s/m           (the full-step velocity)
+//   v_{s+1/2} = v_s + dt/2 F_s/m
+//   x_{s+1}   = x_s + dt v_{s+1/2}           (wrapped; written to the other buffer)
+// and checks the displacement since the last list build against skin/2.
+#include "kernels.cuh"
+#include "philox.cuh"
+
+namespace espp {
+
+template <class T>
+__device__ __forceinline__ void pair_force(const PairRec<T>& pr, T r2, T& fr, T& u) {
+    // caller guarantees r2 < pr.rc2 and kind != 0
+    if (pr.kind == ESPP_LJ_CAPPED && r2 < pr.cap2) {
+        const T r = sqrt(r2);
+        fr = pr.capF / r;
+        u = pr.capU + pr.capF * (pr.cap - r);
+        return;
+    }
+    const T inv_r2 = T(1) / r2;
+    const T s2 = pr.sig2 * inv_r2;
+    const T s6 = s2 * s2 * s2;
+    fr = pr.eps24 * s6 * (T(2) * s6 - T(1)) * inv_r2;
+    u = pr.eps4 * s6 * (s6 - T(1)) - pr.shift;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <class T, int MODE, bool ENERGY>
+__global__ void __launch_bounds__(TILE) k_step(DevSys<T> s, int cur, double* __restrict__ f_out,
+                                               unsigned long long next_cond) {
+    Ctrl* c = s.ctrl;
+    if (MODE != MODE_FORCES && c->abort) return;
+    const long long step = c->step + (MODE >= MODE_STEP ? 1 : 0);
+    const V4<T>* __restrict__ P = s.pos[cur];
+    V4<T>* __restrict__ Pn = s.pos[cur ^ 1];
+    const IntParams<T>* __restrict__ ip = s.ip;
+    __shared__ double red[NPART][TILE / 32];
+
+    for (int t = blockIdx.x; t < s.ntiles; t += gridDim.x) {
+        const Tile tl = s.tiles[t];
+        const bool active = (int)threadIdx.x < tl.count;
+        const RepGeom<T>& g = s.reps[tl.rep];
+        double acc[NPART];
+        if (ENERGY) {
+#pragma unroll
+            for (int k = 0; k < NPART; ++k) acc[k] = 0.0;
+        }
+        if (active) {
+            const int i = tl.start + threadIdx.x;
+            const T L0 = g.L[0], L1 = g.L[1], L2 = g.L[2];
+            const T H0 = g.halfL[0], H1 = g.halfL[1], H2 = g.halfL[2];
+            const V4<T> xi = ld4<T>(P + i);
+            const int ti = bits_as_int(xi.w);
+            T fx = 0, fy = 0, fz = 0, pe = 0, pb = 0, vir = 0;
+            const int n = s.nbr_cnt[i];
+            const int* __restrict__ nb = s.nbr + i;
+            const int stride = s.stride;
+            if (s.ntypes == 1) {
+                const PairRec<T> pr = s.pair[0];
+                if (pr.kind != 0) {
+                    for (int k = 0; k < n; ++k) {
+                        const int j = __ldg(nb + (size_t)k * stride);
+                        const V4<T> xj = ld4<T>(P + j);
+                        const T dx = min_image(xi.x, xj.x, L0, H0);
+                        const T dy = min_image(xi.y, xj.y, L1, H1);
+                        const T dz = min_image(xi.z, xj.z, L2, H2);
+                        const T r2 = dx * dx + dy * dy + dz * dz;
+                        if (r2 < pr.rc2) {
+                            T fr, u;
+                            pair_force(pr, r2, fr, u);
+                            fx += fr * dx;
+                            fy += fr * dy;
+                            fz += fr * dz;
+                            if (ENERGY) {
+                                pe += u;
+                                vir += fr * r2;
+                            }
+                        }
+                    }
+                }
+            } else {
+                for (int k = 0; k < n; ++k) {
+                    const int j = __ldg(nb + (size_t)k * stride);
+                    const V4<T> xj = ld4<T>(P + j);
+                    const PairRec<T> pr = s.pair[ti * s.ntypes + bits_as_int(xj.w)];
+                    const T dx = min_image(xi.x, xj.x, L0, H0);
+                    const T dy = min_image(xi.y, xj.y, L1, H1);
+                    const T dz = min_image(xi.z, xj.z, L2, H2);
+                    const T r2 = dx * dx + dy * dy + dz * dz;
+                    if (pr.kind != 0 && r2 < pr.rc2) {
+                        T fr, u;
+                        pair_force(pr, r2, fr, u);
+                        fx += fr * dx;
+                        fy += fr * dy;
+                        fz += fr * dz;
+                        if (ENERGY) {
+                            pe += u;
+                            vir += fr * r2;
+                        }
+                    }
+                }
+            }
+            // FENE bonds (paper "Functionality": bonded interactions)
+            double blen = 0.0, bcnt = 0.0;
+            if (s.bond.kind != 0) {
+                const int2 b = s.bond_slot[i];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int p = q == 0 ? b.x : b.y;
+                    if (p < 0) continue;
+                    const V4<T> xp = ld4<T>(P + p);
+                    const T dx = min_image(xi.x, xp.x, L0, H0);
+                    const T dy = min_image(xi.y, xp.y, L1, H1);
+                    const T dz = min_image(xi.z, xp.z, L2, H2);
+                    const T r2 = dx * dx + dy * dy + dz * dz;
+                    T one_m = T(1) - r2 * s.bond.inv_R02;
+                    if (!(one_m > T(0))) {
+                        atomicOr(&c->err, ERRBIT_BOND);
+                        c->abort = 1;
+                        __threadfence();
+                        one_m = T(1e-6);
+                    }
+                    const T fr = -s.bond.K / one_m;
+                    fx += fr * dx;
+                    fy += fr * dy;
+                    fz += fr * dz;
+                    if (ENERGY) {
+                        pb += -s.bond.halfKR02 * log(one_m);
+                        vir += fr * r2;
+                        blen += sqrt((double)r2);
+                        bcnt += 1.0;
+                    }
+                }
+            }
+            if (ENERGY) {
+                acc[P_PE_PAIR] = 0.5 * (double)pe;
+                acc[P_PE_BOND] = 0.5 * (double)pb;
+                acc[P_VIRIAL] = 0.5 * (double)vir;
+                acc[P_BOND_LEN] = 0.5 * blen;
+                acc[P_BOND_CNT] = 0.5 * bcnt;
+            }
+            V4<T> v = s.vel[i];
+            if (MODE == MODE_FORCES) {
+                if (f_out) {
+                    const size_t gid = (size_t)g.p_off + bits_as_int(v.w);
+                    f_out[3 * gid + 0] = (double)fx;
+                    f_out[3 * gid + 1] = (double)fy;
+                    f_out[3 * gid + 2] = (double)fz;
+                }
+                if (ENERGY) {
+                    const double m = (double)ip->mass[ti];
+                    acc[P_KE] = 0.5 * m * ((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z);
+                    acc[P_PX] = m * v.x;
+                    acc[P_PY] = m * v.y;
+                    acc[P_PZ] = m * v.z;
+                }
+            } else {
+                const T m = ip->mass[ti], inv_m = ip->inv_mass[ti];
+                if (ip->gamma != T(0)) {
+                    T rx, ry, rz;
+                    langevin_noise<T>(g.seed, bits_as_int(v.w), step, rx, ry, rz);
+                    const T amp = ip->noise_amp[ti];
+                    const T gm = ip->gamma * m;
+                    fx += -gm * v.x + amp * rx;
+                    fy += -gm * v.y + amp * ry;
+                    fz += -gm * v.z + amp * rz;
+                }
+                if (MODE == MODE_INIT) {
+                    s.frc[i] = mk4<T>(fx, fy, fz, T(0));
+                } else {
+                    const T hdt = ip->half_dt;
+                    v.x = half_kick(v.x, fx, hdt, inv_m);
+                    v.y = half_kick(v.y, fy, hdt, inv_m);
+                    v.z = half_kick(v.z, fz, hdt, inv_m);
+                    if (MODE == MODE_FINAL) {
+                        s.vel[i] = v;
+                        s.frc[i] = mk4<T>(fx, fy, fz, T(0));
+                    } else {
+                        v.x = half_kick(v.x, fx, hdt, inv_m);
+                        v.y = half_kick(v.y, fy, hdt, inv_m);
+                        v.z = half_kick(v.z, fz, hdt, inv_m);
+                        const T dt = ip->dt;
+                        T x = drift(xi.x, v.x, dt), y = drift(xi.y, v.y, dt), z = drift(xi.z, v.z, dt);
+                        int wx = 0, wy = 0, wz = 0;
+                        if (x >= L0) { x -= L0; wx = 1; } else if (x < T(0)) { x += L0; wx = -1; if (x >= L0) x = T(0); }
+                        if (y >= L1) { y -= L1; wy = 1; } else if (y < T(0)) { y += L1; wy = -1; if (y >= L1) y = T(0); }
+                        if (z >= L2) { z -= L2; wz = 1; } else if (z < T(0)) { z += L2; wz = -1; if (z >= L2) z = T(0); }
+                        if (wx | wy | wz) {
+                            int4 im = s.img[i];
+                            im.x += wx;
+                            im.y += wy;
+                            im.z += wz;
+                            s.img[i] = im;
+                        }
+                        if (!(x >= T(0) && x < L0 && y >= T(0) && y < L1 && z >= T(0) && z < L2)) {
+                            atomicOr(&c->err, ERRBIT_NONFINITE);
+                            c->abort = 1;
+                            __threadfence();
+                            x = T(0); y = T(0); z = T(0);
+                        }
+                        const V4<T> b = s.xb[i];
+                        const T ex = min_image(x, b.x, L0, H0);
+                        const T ey = min_image(y, b.y, L1, H1);
+                        const T ez = min_image(z, b.z, L2, H2);
+                        if (ex * ex + ey * ey + ez * ez > s.half_skin2) {
+                            s.req[tl.rep] = 1;
+                            c->any_req = 1;
+                            __threadfence();
+                        }
+                        Pn[i] = mk4<T>(x, y, z, xi.w);
+                        s.vel[i] = v;
+                    }
+                }
+            }
+        }
+        if (ENERGY) {
+            const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+            for (int k = 0; k < NPART; ++k) {
+                const double r = warp_sum(acc[k]);
+                if (lane == 0) red[k][w] = r;
+            }
+            __syncthreads();
+            if (threadIdx.x < NPART) {
+                double sum = 0.0;
+#pragma unroll
+                for (int q = 0; q < TILE / 32; ++q) sum += red[threadIdx.x][q];
+                s.partials[(size_t)t * NPART + threadIdx.x] = sum;
+            }
+            __syncthreads();
+        }
+    }
+
+    if (MODE == MODE_STEP || MODE == MODE_FINAL) {
+        // the last block to finish advances the step counter and arms the
+        // conditional rebuild node of the next step
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned int done = atomicAdd(&c->blocks_done, 1u);
+            if (done == gridDim.x - 1) {
+                __threadfence();
+                c->step = step;
+                c->blocks_done = 0;
+                if (next_cond) {
+                    const unsigned int want = *(volatile unsigned int*)&c->any_req;
+                    const unsigned int ab = *(volatile unsigned int*)&c->abort;
+                    cudaGraphSetConditional(next_cond, (want && !ab) ? 1u : 0u);
+                }
+            }
+        }
+    }
+}
+
+// First half-kick and drift of an integrate call: v_{n+1/2}, x_{n+1}.
+template <class T>
+__global__ void __launch_bounds__(TILE) k_prologue(DevSys<T> s, int cur) {
+    Ctrl* c = s.ctrl;
+    if (c->abort) return;
+    const V4<T>* __restrict__ P = s.pos[cur];
+    V4<T>* __restrict__ Pn = s.pos[cur ^ 1];
+    const IntParams<T>* __restrict__ ip = s.ip;
+    for (int t = blockIdx.x; t < s.ntiles; t += gridDim.x) {
+        const Tile tl = s.tiles[t];
+        if ((int)threadIdx.x >= tl.count) continue;
+        const RepGeom<T>& g = s.reps[tl.rep];
+        const int i = tl.start + threadIdx.x;
+        const V4<T> xi = P[i];
+        const int ti = bits_as_int(xi.w);
+        const V4<T> f = s.frc[i];
+        V4<T> v = s.vel[i];
+        const T hdt = ip->half_dt, inv_m = ip->inv_mass[ti];
+        v.x = half_kick(v.x, f.x, hdt, inv_m);
+        v.y = half_kick(v.y, f.y, hdt, inv_m);
+        v.z = half_kick(v.z, f.z, hdt, inv_m);
+        const T dt = ip->dt;
+        const T L0 = g.L[0], L1 = g.L[1], L2 = g.L[2];
+        T x = drift(xi.x, v.x, dt), y = drift(xi.y, v.y, dt), z = drift(xi.z, v.z, dt);
+        int wx = 0, wy = 0, wz = 0;
+        if (x >= L0) { x -= L0; wx = 1; } else if (x < T(0)) { x += L0; wx = -1; if (x >= L0) x = T(0); }
+        if (y >= L1) { y -= L1; wy = 1; } else if (y < T(0)) { y += L1; wy = -1; if (y >= L1) y = T(0); }
+        if (z >= L2) { z -= L2; wz = 1; } else if (z < T(0)) { z += L2; wz = -1; if (z >= L2) z = T(0); }
+        if (wx | wy | wz) {
+            int4 im = s.img[i];
+            im.x += wx;
+            im.y += wy;
+            im.z += wz;
+            s.img[i] = im;
+        }
+        if (!(x >= T(0) && x < L0 && y >= T(0) && y < L1 && z >= T(0) && z < L2)) {
+            atomicOr(&c->err, ERRBIT_NONFINITE);
+            c->abort = 1;
+            x = T(0); y = T(0); z = T(0);
+        }
+        const V4<T> b = s.xb[i];
+        const T ex = min_image(x, b.x, L0, g.halfL[0]);
+        const T ey = min_image(y, b.y, L1, g.halfL[1]);
+        const T ez = min_image(z, b.z, L2, g.halfL[2]);
+        if (ex * ex + ey * ey + ez * ez > s.half_skin2) {
+            s.req[tl.rep] = 1;
+            c->any_req = 1;
+        }
+        Pn[i] = mk4<T>(x, y, z, xi.w);
+        s.vel[i] = v;
+    }
+}
+
+template <class T>
+__global__ void k_set_cond(DevSys<T> s, unsigned long long h) {
+    const unsigned int want = *(volatile unsigned int*)&s.ctrl->any_req;
+    const unsigned int ab = *(volatile unsigned int*)&s.ctrl->abort;
+    cudaGraphSetConditional(h, (want && !ab) ? 1u : 0u);
+}
+
+template <class T>
+void Launch<T>::step(const DevSys<T>& s, int mode, bool energy, int cur, double* f_out,
+                     unsigned long long next_cond, int grid, cudaStream_t st) {
+    const int gr = grid > 0 ? grid : s.ntiles;
+#define ESPP_STEP(M, E) k_step<T, M, E><<<gr, TILE, 0, st>>>(s, cur, f_out, next_cond)
+    switch (mode) {
+        case MODE_FORCES:
+            if (energy) ESPP_STEP(MODE_FORCES, true); else ESPP_STEP(MODE_FORCES, false);
+            break;
+        case MODE_INIT: ESPP_STEP(MODE_INIT, false); break;
+        case MODE_STEP: ESPP_STEP(MODE_STEP, false); break;
+        default: ESPP_STEP(MODE_FINAL, false); break;
+    }
+#undef ESPP_STEP
+}
+
+template <class T>
+void Launch<T>::prologue(const DevSys<T>& s, int cur, int grid, cudaStream_t st) {
+    k_prologue<T><<<grid > 0 ? grid : s.ntiles, TILE, 0, st>>>(s, cur);
+}
+
+template <class T>
+void Launch<T>::set_cond(const DevSys<T>& s, unsigned long long cond, cudaStream_t st) {
+    k_set_cond<T><<<1, 1, 0, st>>>(s, cond);
+}
+
+template void Launch<float>::step(const DevSys<float>&, int, bool, int, double*, unsigned long long, int, cudaStream_t);
+template void Launch<double>::step(const DevSys<double>&, int, bool, int, double*, unsigned long long, int, cudaStream_t);
+template void Launch<float>::prologue(const DevSys<float>&, int, int, cudaStream_t);
+template void Launch<double>::prologue(const DevSys<double>&, int, int, cudaStream_t);
+template void Launch<float>::set_cond(const DevSys<float>&, unsigned long long, cudaStream_t);
+template void Launch<double>::set_cond(const DevSys<double>&, unsigned long long, cudaStream_t);
+
+}  // namespace espp

@@ -1,0 +1,106 @@
+// Device view of one handle and the host-side launchers of every kernel.
+#pragma once
+#include "common.cuh"
+
+namespace espp {
+
+// Integrator parameters, resident in device memory so captured graphs stay
+// valid when they change.
+template <class T> struct IntParams {
+    T dt;
+    T half_dt;
+    T gamma;
+    T kT;
+    T mass[MAX_TYPES];
+    T inv_mass[MAX_TYPES];
+    T noise_amp[MAX_TYPES];  // sqrt(24 gamma m kT / dt)
+};
+
+constexpr int NPART = 12;  // per-tile observable partials (doubles)
+enum : int {
+    P_PE_PAIR = 0, P_PE_BOND, P_VIRIAL, P_KE, P_BOND_LEN, P_BOND_CNT, P_PX, P_PY, P_PZ,
+};
+
+template <class T> struct DevSys {
+    // particle arrays in storage (cell-sorted) order, all replicas concatenated
+    V4<T>* pos[2];      // double-buffered positions; w = type bits
+    V4<T>* vel;         // w = local particle id bits
+    V4<T>* vel_alt;
+    V4<T>* frc;         // total force of the stored step
+    V4<T>* frc_alt;
+    V4<T>* xb;          // positions at the last list build
+    int4* img;          // periodic image counters
+    int4* img_alt;
+    int2* bond_slot;    // storage slots of the (<= 2) bond partners, -1 = none
+    const int2* bond_gid;  // by global id: global ids of bond partners, -1 = none
+    int* slot_of_id;    // global id -> storage slot
+    int* perm;          // new slot -> old slot (rebuild)
+    int* cellh;         // per old slot: global cell rank
+    int* in_cell;       // per old slot: arrival index in its cell
+    // Verlet list: nbr[k * stride + i], k < nbr_cnt[i] <= cap
+    int* nbr;
+    int* nbr_cnt;
+    int cap;
+    int stride;
+    // cells (rank space, all replicas concatenated)
+    int* cell_cnt;
+    int* cell_start;    // ncells + 1
+    const int* cell_rank;  // per replica linear cell index (+cell_off) -> global rank
+    const int* cell_rep;
+    int ncells;
+    int* scan_part;
+    int nscan_blocks;
+    // replicas and tiles
+    const RepGeom<T>* reps;
+    int R;
+    const Tile* tiles;
+    int ntiles;
+    const int* rep_tile_off;  // R + 1: first tile of each replica
+    int* req;           // rebuild requested (per replica), set by the step kernel
+    int* now;           // rebuild running (per replica), latched at the rebuild start
+    Ctrl* ctrl;
+    const IntParams<T>* ip;
+    const PairRec<T>* pair;
+    int ntypes;
+    int N;
+    BondRec<T> bond;
+    T rlist2;           // (rc + skin)^2
+    T half_skin2;       // (skin / 2)^2
+    double* partials;   // ntiles * NPART
+};
+
+// step-kernel modes
+enum : int {
+    MODE_FORCES = 0,  // conservative forces only, written to an id-ordered double buffer
+    MODE_INIT = 1,    // total force of the current step (with thermostat), stored; no kick
+    MODE_STEP = 2,    // F_s, v_s, v_{s+1/2}, x_{s+1}
+    MODE_FINAL = 3,   // F_s, v_s stored (end of an integrate call)
+};
+
+// ---- launchers (defined in the .cu files) ----------------------------------
+template <class T> struct Launch {
+    // rebuild pipeline on the positions in buffer `cur` (other buffer is scratch)
+    static void rebuild(const DevSys<T>& s, int cur, bool permute_force, cudaStream_t st);
+    static void verlet_only(const DevSys<T>& s, int cur, cudaStream_t st);
+    static void request_all(const DevSys<T>& s, cudaStream_t st);
+    // step kernels
+    static void step(const DevSys<T>& s, int mode, bool energy, int cur, double* f_out,
+                     unsigned long long next_cond, int grid, cudaStream_t st);
+    static void prologue(const DevSys<T>& s, int cur, int grid, cudaStream_t st);
+    static void set_cond(const DevSys<T>& s, unsigned long long cond, cudaStream_t st);
+    // state I/O (id-ordered double buffers on the device)
+    static void set_state(const DevSys<T>& s, const double* x, const double* v, const int* img,
+                          const int* types_by_gid, int cur, cudaStream_t st);
+    static void get_state(const DevSys<T>& s, double* x, double* v, int* img, int cur,
+                          cudaStream_t st);
+    static void reduce_obs(const DevSys<T>& s, double* out_R_NPART, cudaStream_t st);
+    static void rg2(const DevSys<T>& s, int cur, const int* mol_members, const int* mol_off,
+                    const int* mol_rep, int nmol, double* mol_rg2, cudaStream_t st);
+    static void rdf(const DevSys<T>& s, int cur, int rep, double rmax, int nbins,
+                    unsigned long long* counts, cudaStream_t st);
+};
+
+void launch_noise(unsigned long long seed, long long step, long long n, double* out,
+                  cudaStream_t st);
+
+}  // namespace espp

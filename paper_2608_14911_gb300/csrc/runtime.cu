@@ -1,0 +1,1168 @@
+// Host runtime behind the C ABI (include/espp.h): owns the device buffers of a
+// handle, prepares geometry, cell grids, tiles and interaction tables, builds
+// and caches the CUDA graphs that step the system, and turns the device error
+// word into status codes.  Everything computed per particle runs in the
+// kernels of k_rebuild.cu, k_step.cu and k_io.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace espp {
+void hilbert_ranks(int nx, int ny, int nz, int* rank);
+int scan_blocks_for(int ncells);
+
+#define CK(call)                                                                       \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            return fail(ESPP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+        }                                                                              \
+    } while (0)
+
+struct SystemBase {
+    std::string msg;
+    virtual ~SystemBase() {}
+    int fail(int code, const std::string& m) {
+        msg = m;
+        return code;
+    }
+    virtual int set_state(const double* x, const double* v, const int32_t* img, int where) = 0;
+    virtual int get_state(double* x, double* v, int32_t* img, int where) = 0;
+    virtual int set_step(int64_t step) = 0;
+    virtual int set_interaction(int kind, int ta, int tb, const double* p, int64_t np) = 0;
+    virtual int set_mass(int type, double m) = 0;
+    virtual int build_neighbors(double rc, double skin) = 0;
+    virtual int get_neighbors(int64_t* row_ptr, int64_t* cols, int64_t cap) = 0;
+    virtual int compute_forces(double* f, int where) = 0;
+    virtual int integrate(int64_t nsteps, double dt, double gamma, double kT) = 0;
+    virtual int observables(espp_obs_t* out, int R) = 0;
+    virtual int rdf_counts(int rep, double rmax, int nbins, int64_t* counts) = 0;
+    virtual int checkpoint_save(const char* path) = 0;
+    virtual int checkpoint_load(const char* path) = 0;
+    virtual uint32_t error_word() = 0;
+    virtual int64_t num_particles() = 0;
+    virtual int32_t num_replicas() = 0;
+    virtual int64_t num_rebuilds() = 0;
+    virtual int64_t step() = 0;
+    virtual int32_t list_capacity() = 0;
+    virtual int64_t kernel_launches() = 0;
+    virtual int set_kernel_timing(int enable) = 0;
+    virtual int kernel_timing(double* out, int reset) = 0;
+    virtual int set_chunk(int steps) = 0;
+    virtual int list_stats(int64_t* total, int32_t* maxc) = 0;
+};
+
+struct PairHost {
+    int kind = ESPP_NONE;
+    double eps = 0, sig = 0, rc = 0, cap = 0;
+    bool shift = false;
+};
+
+template <class T>
+class System : public SystemBase {
+   public:
+    cudaStream_t st = nullptr;
+    int R = 0;
+    int64_t N = 0;
+    std::vector<double> box;  // R*3
+    std::vector<int> rep_n, rep_poff;
+    std::vector<unsigned long long> seeds;
+    std::vector<Tile> tiles_h;
+    std::vector<int> rep_tile_off_h;
+    std::vector<int> types_gid;
+    std::vector<int2> bond_gid_h;
+    std::vector<int> mol_members_h, mol_off_h, mol_rep_h;
+    int ntypes = 1;
+    PairHost pair_h[MAX_TYPES][MAX_TYPES];
+    int bond_kind = ESPP_NONE;
+    double bond_K = 0, bond_R0 = 0;
+    double mass_h[MAX_TYPES];
+    double rc_list = -1, skin = 0;
+    bool cells_ready = false, state_set = false, f_valid = false, rebuild_pending = false;
+    int cur = 0;
+    std::vector<void*> allocs;
+    std::vector<void*> cell_allocs;
+    void* nbr_alloc = nullptr;
+    DevSys<T> d{};
+    RepGeom<T>* d_geom = nullptr;
+    IntParams<T>* d_ip = nullptr;
+    PairRec<T>* d_pair = nullptr;
+    Ctrl* d_ctrl = nullptr;
+    int* d_types = nullptr;
+    double* d_io_x = nullptr;
+    double* d_io_v = nullptr;
+    int* d_io_img = nullptr;
+    double* d_obs = nullptr;
+    int *d_mol_members = nullptr, *d_mol_off = nullptr, *d_mol_rep = nullptr;
+    double* d_mol_rg2 = nullptr;
+    unsigned long long* d_hist = nullptr;
+    int hist_cap = 0;
+    double ip_key[3] = {-1, -1, -1};
+    struct ChunkGraph {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        std::vector<cudaEvent_t> ev;  // timing mode: 3 per step (before rebuild, before step, after step)
+    };
+    std::map<std::tuple<int, int, int>, ChunkGraph> graphs;
+    bool timing = false;
+    double t_step_ms = 0, t_rebuild_ms = 0;
+    int64_t t_step_n = 0;
+    int64_t launches = 0;
+    int64_t rebuild_base = 0;  // rebuilds counted before the last ctrl reset
+    int chunk = 64;
+
+    ~System() override {
+        clear_graphs();
+        for (void* p : cell_allocs) cudaFree(p);
+        if (nbr_alloc) cudaFree(nbr_alloc);
+        for (void* p : allocs) cudaFree(p);
+    }
+
+    template <class P>
+    int alloc(P** out, size_t count, std::vector<void*>& pool) {
+        void* p = nullptr;
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc(&p, count * sizeof(P));
+        if (e != cudaSuccess) return fail(ESPP_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        cudaMemset(p, 0, count * sizeof(P));
+        pool.push_back(p);
+        *out = reinterpret_cast<P*>(p);
+        return ESPP_OK;
+    }
+
+    void clear_graphs() {
+        for (auto& kv : graphs) {
+            cudaGraphExecDestroy(kv.second.exec);
+            cudaGraphDestroy(kv.second.graph);
+            for (cudaEvent_t e : kv.second.ev) cudaEventDestroy(e);
+        }
+        graphs.clear();
+    }
+
+    // ---------------------------------------------------------------- create
+    int create(int Rr, const espp_replica_desc* descs, cudaStream_t stream) {
+        st = stream;
+        R = Rr;
+        for (int a = 0; a < MAX_TYPES; ++a) mass_h[a] = 1.0;
+        int64_t total = 0;
+        for (int r = 0; r < R; ++r) {
+            const espp_replica_desc& dsc = descs[r];
+            if (dsc.n < 1) return fail(ESPP_ERR_ARG, "every replica needs at least one particle");
+            for (int c = 0; c < 3; ++c)
+                if (!(dsc.box[c] > 0) || !std::isfinite(dsc.box[c]))
+                    return fail(ESPP_ERR_ARG, "box edges must be positive and finite");
+            rep_poff.push_back((int)total);
+            rep_n.push_back((int)dsc.n);
+            total += dsc.n;
+            if (total >= (1ll << 31) - 64) return fail(ESPP_ERR_ARG, "too many particles");
+            for (int c = 0; c < 3; ++c) box.push_back(dsc.box[c]);
+            seeds.push_back(dsc.seed);
+        }
+        N = total;
+        types_gid.assign(N, 0);
+        bond_gid_h.assign(N, make_int2(-1, -1));
+        int maxtype = 0;
+        for (int r = 0; r < R; ++r) {
+            const espp_replica_desc& dsc = descs[r];
+            const int off = rep_poff[r];
+            for (int64_t i = 0; i < dsc.n; ++i) {
+                const int t = dsc.types ? dsc.types[i] : 0;
+                if (t < 0 || t >= MAX_TYPES) return fail(ESPP_ERR_ARG, "particle type out of range");
+                types_gid[off + i] = t;
+                maxtype = std::max(maxtype, t);
+            }
+            if (dsc.n_bonds < 0 || (dsc.n_bonds > 0 && !dsc.bonds))
+                return fail(ESPP_ERR_ARG, "bad bond list");
+            for (int64_t b = 0; b < dsc.n_bonds; ++b) {
+                const int64_t p = dsc.bonds[2 * b], q = dsc.bonds[2 * b + 1];
+                if (p < 0 || q < 0 || p >= dsc.n || q >= dsc.n || p == q)
+                    return fail(ESPP_ERR_ARG, "bond references an invalid particle id");
+                for (int side = 0; side < 2; ++side) {
+                    const int a = (int)(side == 0 ? p : q) + off, o = (int)(side == 0 ? q : p) + off;
+                    int2& s = bond_gid_h[a];
+                    if (s.x == o || s.y == o) return fail(ESPP_ERR_ARG, "duplicate bond");
+                    if (s.x < 0) s.x = o;
+                    else if (s.y < 0) s.y = o;
+                    else return fail(ESPP_ERR_ARG, "more than 2 bonds on one particle");
+                }
+            }
+        }
+        ntypes = maxtype + 1;
+        // molecules: connected components of the bond graph with >= 2 beads
+        {
+            std::vector<int> parent(N);
+            std::iota(parent.begin(), parent.end(), 0);
+            auto find = [&](int a) {
+                while (parent[a] != a) {
+                    parent[a] = parent[parent[a]];
+                    a = parent[a];
+                }
+                return a;
+            };
+            for (int64_t i = 0; i < N; ++i) {
+                const int2 b = bond_gid_h[i];
+                for (int o : {b.x, b.y})
+                    if (o >= 0) {
+                        int ra = find((int)i), rb = find(o);
+                        if (ra != rb) parent[std::max(ra, rb)] = std::min(ra, rb);
+                    }
+            }
+            std::vector<int> cnt(N, 0);
+            for (int64_t i = 0; i < N; ++i) cnt[find((int)i)]++;
+            std::vector<int> mol_of_root(N, -1);
+            int nm = 0;
+            for (int64_t i = 0; i < N; ++i)
+                if (find((int)i) == i && cnt[i] >= 2) mol_of_root[i] = nm++;
+            mol_off_h.assign(nm + 1, 0);
+            for (int64_t i = 0; i < N; ++i) {
+                const int m = mol_of_root[find((int)i)];
+                if (m >= 0) mol_off_h[m + 1]++;
+            }
+            for (int m = 0; m < nm; ++m) mol_off_h[m + 1] += mol_off_h[m];
+            mol_members_h.assign(mol_off_h[nm], 0);
+            mol_rep_h.assign(nm, 0);
+            std::vector<int> fill(mol_off_h.begin(), mol_off_h.end() - 1);
+            int r = 0;
+            for (int64_t i = 0; i < N; ++i) {
+                while (r + 1 < R && i >= rep_poff[r + 1]) ++r;
+                const int m = mol_of_root[find((int)i)];
+                if (m >= 0) {
+                    mol_members_h[fill[m]++] = (int)i;
+                    mol_rep_h[m] = r;
+                }
+            }
+        }
+        // tiles
+        rep_tile_off_h.push_back(0);
+        for (int r = 0; r < R; ++r) {
+            for (int s0 = 0; s0 < rep_n[r]; s0 += TILE) {
+                Tile t;
+                t.start = rep_poff[r] + s0;
+                t.count = std::min(TILE, rep_n[r] - s0);
+                t.rep = r;
+                t.pad = 0;
+                tiles_h.push_back(t);
+            }
+            rep_tile_off_h.push_back((int)tiles_h.size());
+        }
+        // device buffers
+        int rc = ESPP_OK;
+        const size_t n = (size_t)N;
+        if ((rc = alloc(&d.pos[0], n, allocs)) || (rc = alloc(&d.pos[1], n, allocs)) ||
+            (rc = alloc(&d.vel, n, allocs)) || (rc = alloc(&d.vel_alt, n, allocs)) ||
+            (rc = alloc(&d.frc, n, allocs)) || (rc = alloc(&d.frc_alt, n, allocs)) ||
+            (rc = alloc(&d.xb, n, allocs)) || (rc = alloc(&d.img, n, allocs)) ||
+            (rc = alloc(&d.img_alt, n, allocs)) || (rc = alloc(&d.bond_slot, n, allocs)))
+            return rc;
+        int2* bg = nullptr;
+        int *sid, *perm, *cellh, *inc, *ncnt, *req, *now, *rto;
+        Tile* tl;
+        double* part;
+        if ((rc = alloc(&bg, n, allocs)) || (rc = alloc(&sid, n, allocs)) ||
+            (rc = alloc(&perm, n, allocs)) || (rc = alloc(&cellh, n, allocs)) ||
+            (rc = alloc(&inc, n, allocs)) || (rc = alloc(&ncnt, n, allocs)) ||
+            (rc = alloc(&req, R, allocs)) || (rc = alloc(&now, R, allocs)) ||
+            (rc = alloc(&tl, tiles_h.size(), allocs)) || (rc = alloc(&rto, R + 1, allocs)) ||
+            (rc = alloc(&part, tiles_h.size() * NPART, allocs)) ||
+            (rc = alloc(&d_geom, R, allocs)) || (rc = alloc(&d_ip, 1, allocs)) ||
+            (rc = alloc(&d_pair, MAX_TYPES * MAX_TYPES, allocs)) || (rc = alloc(&d_ctrl, 1, allocs)) ||
+            (rc = alloc(&d_types, n, allocs)) || (rc = alloc(&d_io_x, 3 * n, allocs)) ||
+            (rc = alloc(&d_io_v, 3 * n, allocs)) || (rc = alloc(&d_io_img, 3 * n, allocs)) ||
+            (rc = alloc(&d_obs, (size_t)R * NPART, allocs)) ||
+            (rc = alloc(&d_mol_members, mol_members_h.size(), allocs)) ||
+            (rc = alloc(&d_mol_off, mol_off_h.size(), allocs)) ||
+            (rc = alloc(&d_mol_rep, mol_rep_h.size(), allocs)) ||
+            (rc = alloc(&d_mol_rg2, mol_rep_h.size(), allocs)))
+            return rc;
+        d.bond_gid = bg;
+        d.slot_of_id = sid;
+        d.perm = perm;
+        d.cellh = cellh;
+        d.in_cell = inc;
+        d.nbr_cnt = ncnt;
+        d.req = req;
+        d.now = now;
+        d.tiles = tl;
+        d.ntiles = (int)tiles_h.size();
+        d.rep_tile_off = rto;
+        d.partials = part;
+        d.reps = d_geom;
+        d.R = R;
+        d.ctrl = d_ctrl;
+        d.ip = d_ip;
+        d.pair = d_pair;
+        d.ntypes = ntypes;
+        d.N = (int)N;
+        CK(cudaMemcpy(bg, bond_gid_h.data(), n * sizeof(int2), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(tl, tiles_h.data(), tiles_h.size() * sizeof(Tile), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(rto, rep_tile_off_h.data(), (R + 1) * sizeof(int), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(d_types, types_gid.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+        if (!mol_members_h.empty()) {
+            CK(cudaMemcpy(d_mol_members, mol_members_h.data(), mol_members_h.size() * sizeof(int), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(d_mol_rep, mol_rep_h.data(), mol_rep_h.size() * sizeof(int), cudaMemcpyHostToDevice));
+        }
+        CK(cudaMemcpy(d_mol_off, mol_off_h.data(), mol_off_h.size() * sizeof(int), cudaMemcpyHostToDevice));
+        upload_geometry();
+        CK(upload_params());
+        return ESPP_OK;
+    }
+
+    int cell_count(int r, int c) const {
+        return (int)std::floor(box[3 * r + c] / ((rc_list + skin) * (1.0 + 1e-6)));
+    }
+
+    int upload_geometry() {
+        std::vector<RepGeom<T>> g(R);
+        int coff = 0;
+        for (int r = 0; r < R; ++r) {
+            for (int c = 0; c < 3; ++c) {
+                g[r].L[c] = (T)box[3 * r + c];
+                g[r].halfL[c] = g[r].L[c] * T(0.5);
+                const int nc = cells_ready ? cell_count(r, c) : 1;
+                g[r].nc[c] = nc;
+                g[r].cells_per_len[c] = (T)((double)nc / (double)g[r].L[c]);
+            }
+            g[r].cell_off = coff;
+            coff += g[r].nc[0] * g[r].nc[1] * g[r].nc[2];
+            g[r].p_off = rep_poff[r];
+            g[r].n = rep_n[r];
+            g[r].pad = 0;
+            g[r].seed = seeds[r];
+        }
+        cudaError_t e = cudaMemcpy(d_geom, g.data(), R * sizeof(RepGeom<T>), cudaMemcpyHostToDevice);
+        return e == cudaSuccess ? ESPP_OK : fail(ESPP_ERR_CUDA, cudaGetErrorString(e));
+    }
+
+    cudaError_t upload_params() {
+        std::vector<PairRec<T>> pr(MAX_TYPES * MAX_TYPES);
+        for (int a = 0; a < ntypes; ++a)
+            for (int b = 0; b < ntypes; ++b) {
+                const PairHost& p = pair_h[a][b];
+                PairRec<T>& q = pr[a * ntypes + b];
+                memset(&q, 0, sizeof(q));
+                q.kind = p.kind;
+                if (p.kind == ESPP_NONE) continue;
+                const double s2 = p.sig * p.sig;
+                auto lj = [&](double r2, double& u, double& fr) {
+                    const double x = s2 / r2, x6 = x * x * x;
+                    u = 4 * p.eps * (x6 * x6 - x6);
+                    fr = 24 * p.eps * (2 * x6 * x6 - x6) / r2;
+                };
+                double us = 0, fs = 0;
+                if (p.shift) lj(p.rc * p.rc, us, fs);
+                q.rc2 = (T)(p.rc * p.rc);
+                q.sig2 = (T)s2;
+                q.eps24 = (T)(24 * p.eps);
+                q.eps4 = (T)(4 * p.eps);
+                q.shift = (T)us;
+                if (p.kind == ESPP_LJ_CAPPED) {
+                    double uc, frc;
+                    lj(p.cap * p.cap, uc, frc);
+                    q.cap2 = (T)(p.cap * p.cap);
+                    q.cap = (T)p.cap;
+                    q.capF = (T)(frc * p.cap);
+                    q.capU = (T)(uc - us);
+                }
+            }
+        d.bond.kind = bond_kind;
+        d.bond.K = (T)bond_K;
+        d.bond.inv_R02 = bond_kind ? (T)(1.0 / (bond_R0 * bond_R0)) : T(0);
+        d.bond.halfKR02 = (T)(0.5 * bond_K * bond_R0 * bond_R0);
+        return cudaMemcpy(d_pair, pr.data(), pr.size() * sizeof(PairRec<T>), cudaMemcpyHostToDevice);
+    }
+
+    int upload_int_params(double dt, double gamma, double kT) {
+        if (ip_key[0] == dt && ip_key[1] == gamma && ip_key[2] == kT && !mass_dirty) return ESPP_OK;
+        IntParams<T> ip;
+        memset(&ip, 0, sizeof(ip));
+        ip.dt = (T)dt;
+        ip.half_dt = (T)(0.5 * dt);
+        ip.gamma = (T)gamma;
+        ip.kT = (T)kT;
+        for (int a = 0; a < MAX_TYPES; ++a) {
+            ip.mass[a] = (T)mass_h[a];
+            ip.inv_mass[a] = (T)(1.0 / mass_h[a]);
+            ip.noise_amp[a] = dt > 0 ? (T)std::sqrt(24.0 * gamma * mass_h[a] * kT / dt) : T(0);
+        }
+        CK(cudaMemcpyAsync(d_ip, &ip, sizeof(ip), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        ip_key[0] = dt;
+        ip_key[1] = gamma;
+        ip_key[2] = kT;
+        mass_dirty = false;
+        return ESPP_OK;
+    }
+    bool mass_dirty = true;
+
+    // ------------------------------------------------------------------ state
+    int set_state(const double* x, const double* v, const int32_t* img, int where) override {
+        if (!x) return fail(ESPP_ERR_ARG, "positions are required");
+        const size_t n3 = 3 * (size_t)N;
+        const double *dx = x, *dv = v;
+        const int* di = img;
+        if (where == ESPP_HOST) {
+            CK(cudaMemcpyAsync(d_io_x, x, n3 * sizeof(double), cudaMemcpyHostToDevice, st));
+            dx = d_io_x;
+            if (v) {
+                CK(cudaMemcpyAsync(d_io_v, v, n3 * sizeof(double), cudaMemcpyHostToDevice, st));
+                dv = d_io_v;
+            }
+            if (img) {
+                CK(cudaMemcpyAsync(d_io_img, img, n3 * sizeof(int), cudaMemcpyHostToDevice, st));
+                di = d_io_img;
+            }
+        } else if (where != ESPP_DEVICE) {
+            return fail(ESPP_ERR_ARG, "where must be ESPP_HOST or ESPP_DEVICE");
+        }
+        cur = 0;
+        {
+            // a new state clears any earlier error or freeze (the step number is kept)
+            Ctrl c = read_ctrl();
+            c.err = 0;
+            c.abort = 0;
+            c.any_req = 0;
+            c.blocks_done = 0;
+            c.need_cap = 0;
+            CK(cudaMemcpyAsync(d_ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+        }
+        Launch<T>::set_state(d, dx, dv, di, d_types, cur, st);
+        Launch<T>::request_all(d, st);
+        launches += 2;
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(st));
+        state_set = true;
+        f_valid = false;
+        rebuild_pending = true;
+        return ESPP_OK;
+    }
+
+    int get_state(double* x, double* v, int32_t* img, int where) override {
+        if (!state_set) return fail(ESPP_ERR_STATE, "no state set");
+        const size_t n3 = 3 * (size_t)N;
+        if (where == ESPP_DEVICE) {
+            Launch<T>::get_state(d, x, v, img, cur, st);
+            launches++;
+            CK(cudaGetLastError());
+            CK(cudaStreamSynchronize(st));
+            return ESPP_OK;
+        }
+        if (where != ESPP_HOST) return fail(ESPP_ERR_ARG, "where must be ESPP_HOST or ESPP_DEVICE");
+        Launch<T>::get_state(d, x ? d_io_x : nullptr, v ? d_io_v : nullptr, img ? d_io_img : nullptr, cur, st);
+        launches++;
+        CK(cudaGetLastError());
+        if (x) CK(cudaMemcpyAsync(x, d_io_x, n3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (v) CK(cudaMemcpyAsync(v, d_io_v, n3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (img) CK(cudaMemcpyAsync(img, d_io_img, n3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        return ESPP_OK;
+    }
+
+    Ctrl read_ctrl() {
+        Ctrl c;
+        memset(&c, 0, sizeof(c));
+        cudaMemcpyAsync(&c, d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        return c;
+    }
+
+    int set_step(int64_t s) override {
+        CK(cudaMemcpyAsync(&d_ctrl->step, &s, sizeof(long long), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        return ESPP_OK;
+    }
+
+    // ----------------------------------------------------------- interactions
+    int set_interaction(int kind, int ta, int tb, const double* p, int64_t np) override {
+        if (kind == ESPP_FENE) {
+            if (!p || np < 2 || !(p[0] > 0) || !(p[1] > 0)) return fail(ESPP_ERR_ARG, "FENE needs K > 0, R0 > 0");
+            bond_kind = ESPP_FENE;
+            bond_K = p[0];
+            bond_R0 = p[1];
+        } else {
+            if (ta < 0 || tb < 0 || ta >= MAX_TYPES || tb >= MAX_TYPES)
+                return fail(ESPP_ERR_ARG, "type out of range");
+            PairHost h;
+            if (kind == ESPP_NONE) {
+            } else if (kind == ESPP_LJ || kind == ESPP_LJ_CAPPED) {
+                const int need = kind == ESPP_LJ ? 4 : 5;
+                if (!p || np < need) return fail(ESPP_ERR_ARG, "too few parameters");
+                h.kind = kind;
+                h.eps = p[0];
+                h.sig = p[1];
+                h.rc = p[2];
+                h.shift = p[3] != 0.0;
+                if (kind == ESPP_LJ_CAPPED) h.cap = p[4];
+                if (!(h.sig > 0) || !(h.rc > 0) || (kind == ESPP_LJ_CAPPED && !(h.cap > 0)))
+                    return fail(ESPP_ERR_ARG, "sigma, rc and caprad must be positive");
+            } else if (kind == ESPP_WCA) {
+                if (!p || np < 2) return fail(ESPP_ERR_ARG, "WCA needs eps, sigma");
+                h.kind = ESPP_LJ;
+                h.eps = p[0];
+                h.sig = p[1];
+                h.rc = std::pow(2.0, 1.0 / 6.0) * p[1];
+                h.shift = true;
+                if (!(h.sig > 0)) return fail(ESPP_ERR_ARG, "sigma must be positive");
+            } else {
+                return fail(ESPP_ERR_ARG, "unknown interaction kind");
+            }
+            pair_h[ta][tb] = h;
+            pair_h[tb][ta] = h;
+        }
+        CK(upload_params());
+        clear_graphs();  // the bond record is a kernel argument of captured graphs
+        f_valid = false;
+        return ESPP_OK;
+    }
+
+    int set_mass(int type, double m) override {
+        if (type < 0 || type >= MAX_TYPES || !(m > 0)) return fail(ESPP_ERR_ARG, "bad mass");
+        mass_h[type] = m;
+        mass_dirty = true;
+        f_valid = false;
+        return ESPP_OK;
+    }
+
+    int check_cutoffs() {
+        for (int a = 0; a < ntypes; ++a)
+            for (int b = 0; b < ntypes; ++b)
+                if (pair_h[a][b].kind != ESPP_NONE && pair_h[a][b].rc > rc_list * (1 + 1e-12))
+                    return fail(ESPP_ERR_ARG, "a pair cutoff exceeds the Verlet-list cutoff");
+        return ESPP_OK;
+    }
+
+    // ---------------------------------------------------------- neighbour list
+    int estimate_cap() const {
+        double best = 0;
+        const double rl = rc_list + skin;
+        for (int r = 0; r < R; ++r) {
+            const double V = box[3 * r] * box[3 * r + 1] * box[3 * r + 2];
+            const double rho = rep_n[r] / V;
+            best = std::max(best, rho * 4.0 / 3.0 * M_PI * rl * rl * rl);
+        }
+        int cap = (int)std::ceil(best * 1.4 + 8);
+        // host-side fault injection for tests: start from a deliberately short list
+        if (const char* f = getenv("ESPP_FAULT_LIST_CAP")) {
+            const int forced = atoi(f);
+            if (forced > 0) cap = forced;
+        }
+        return (cap + 3) & ~3;
+    }
+
+    int alloc_list(int cap) {
+        if (nbr_alloc) cudaFree(nbr_alloc);
+        nbr_alloc = nullptr;
+        d.stride = (int)((N + 31) / 32 * 32);
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, (size_t)cap * d.stride * sizeof(int));
+        if (e != cudaSuccess) return fail(ESPP_ERR_CUDA, std::string("list allocation: ") + cudaGetErrorString(e));
+        nbr_alloc = p;
+        e = cudaMemset(p, 0, (size_t)cap * d.stride * sizeof(int));
+        if (e != cudaSuccess) return fail(ESPP_ERR_CUDA, std::string("list memset: ") + cudaGetErrorString(e));
+        d.nbr = reinterpret_cast<int*>(p);
+        d.cap = cap;
+        clear_graphs();
+        return ESPP_OK;
+    }
+
+    int build_neighbors(double rc, double sk) override {
+        if (!(rc > 0) || !(sk >= 0) || !std::isfinite(rc) || !std::isfinite(sk))
+            return fail(ESPP_ERR_ARG, "rc must be positive and skin non-negative");
+        rc_list = rc;
+        skin = sk;
+        int rcode = check_cutoffs();
+        if (rcode) return rcode;
+        for (int r = 0; r < R; ++r)
+            for (int c = 0; c < 3; ++c)
+                if (cell_count(r, c) < 3) {
+                    cells_ready = false;
+                    return fail(ESPP_ERR_BOX_TOO_SMALL, "box edge holds fewer than 3 cells of rc + skin");
+                }
+        cells_ready = true;
+        // cell grids in Hilbert order
+        for (void* p : cell_allocs) cudaFree(p);
+        cell_allocs.clear();
+        clear_graphs();
+        std::vector<int> rank, rep_of;
+        int coff = 0;
+        for (int r = 0; r < R; ++r) {
+            const int nx = cell_count(r, 0), ny = cell_count(r, 1), nz = cell_count(r, 2);
+            const int nc = nx * ny * nz;
+            std::vector<int> rk(nc);
+            hilbert_ranks(nx, ny, nz, rk.data());
+            for (int k = 0; k < nc; ++k) {
+                rank.push_back(coff + rk[k]);
+                rep_of.push_back(r);
+            }
+            coff += nc;
+        }
+        const int C = coff;
+        int *cnt, *start, *crank, *crep, *part;
+        int rc2 = ESPP_OK;
+        d.nscan_blocks = scan_blocks_for(C);
+        if ((rc2 = alloc(&cnt, C, cell_allocs)) || (rc2 = alloc(&start, C + 1, cell_allocs)) ||
+            (rc2 = alloc(&crank, C, cell_allocs)) || (rc2 = alloc(&crep, C, cell_allocs)) ||
+            (rc2 = alloc(&part, d.nscan_blocks, cell_allocs)))
+            return rc2;
+        CK(cudaMemcpy(crank, rank.data(), C * sizeof(int), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(crep, rep_of.data(), C * sizeof(int), cudaMemcpyHostToDevice));
+        const int nn = (int)N;
+        CK(cudaMemcpy(start + C, &nn, sizeof(int), cudaMemcpyHostToDevice));
+        d.cell_cnt = cnt;
+        d.cell_start = start;
+        d.cell_rank = crank;
+        d.cell_rep = crep;
+        d.ncells = C;
+        d.scan_part = part;
+        const double rl = rc + sk;
+        d.rlist2 = (T)(rl * rl);
+        d.half_skin2 = (T)(0.25 * sk * sk);
+        rcode = upload_geometry();
+        if (rcode) return rcode;
+        rcode = alloc_list(estimate_cap());
+        if (rcode) return rcode;
+        if (!state_set) return ESPP_OK;
+        Launch<T>::request_all(d, st);
+        launches++;
+        return rebuild_now(f_valid);
+    }
+
+    // Direct (non-graph) rebuild with overflow retries.  After an overflow the
+    // list is reallocated and every replica is rebuilt (the old list of the
+    // replicas that did not overflow lived in the freed buffer).
+    int rebuild_now(bool permute_force) {
+        if (!cells_ready) return fail(ESPP_ERR_STATE, "call espp_build_neighbors first");
+        for (int attempt = 0; attempt < 4; ++attempt) {
+            Launch<T>::rebuild(d, cur, permute_force, st);
+            launches += 9;
+            CK(cudaGetLastError());
+            Ctrl c = read_ctrl();
+            CK(cudaGetLastError());
+            if (!(c.err & ERRBIT_OVERFLOW)) {
+                rebuild_pending = false;
+                return ESPP_OK;
+            }
+            int rcode = grow_list(c.need_cap);
+            if (rcode) return rcode;
+            Launch<T>::request_all(d, st);
+            launches++;
+        }
+        return fail(ESPP_ERR_LIST_OVERFLOW, "Verlet list overflow persists after retries");
+    }
+
+    int grow_list(unsigned int need) {
+        int cap = (int)std::ceil(need * 1.2 + 8);
+        cap = (cap + 3) & ~3;
+        int rcode = alloc_list(std::max(cap, d.cap + 4));
+        if (rcode) return rcode;
+        // clear the overflow state; the latched per-replica flags stay set
+        Ctrl c = read_ctrl();
+        c.err &= ~ERRBIT_OVERFLOW;
+        c.abort = 0;
+        c.need_cap = 0;
+        c.blocks_done = 0;
+        CK(cudaMemcpyAsync(d_ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        return ESPP_OK;
+    }
+
+    int ensure_list() {
+        if (!state_set) return fail(ESPP_ERR_STATE, "no state set");
+        if (!cells_ready) return fail(ESPP_ERR_STATE, "call espp_build_neighbors first");
+        int rcode = check_cutoffs();
+        if (rcode) return rcode;
+        Ctrl c = read_ctrl();
+        if (c.abort) return status_from(c);
+        if (rebuild_pending || c.any_req) return rebuild_now(f_valid);
+        return ESPP_OK;
+    }
+
+    int status_from(const Ctrl& c) {
+        if (c.err & ERRBIT_BOND) return fail(ESPP_ERR_BOND_BROKEN, "a FENE bond reached r >= R0");
+        if (c.err & ERRBIT_NONFINITE) return fail(ESPP_ERR_NONFINITE, "a position became non-finite or left the box");
+        if (c.err & ERRBIT_TIMEOUT) return fail(ESPP_ERR_TIMEOUT, "a device wait timed out");
+        if (c.err & ERRBIT_OVERFLOW) return fail(ESPP_ERR_LIST_OVERFLOW, "Verlet list overflow");
+        if (c.abort) return fail(ESPP_ERR_STATE, "aborted");
+        return ESPP_OK;
+    }
+
+    int get_neighbors(int64_t* row_ptr, int64_t* cols, int64_t cap) override {
+        if (!row_ptr) return fail(ESPP_ERR_ARG, "row_ptr is required");
+        int rcode = ensure_list();
+        if (rcode) return rcode;
+        const size_t n = (size_t)N;
+        std::vector<int> cnt(n), nb((size_t)d.cap * d.stride);
+        std::vector<V4<T>> vel(n);
+        CK(cudaMemcpy(cnt.data(), d.nbr_cnt, n * sizeof(int), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(nb.data(), d.nbr, nb.size() * sizeof(int), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(vel.data(), d.vel, n * sizeof(V4<T>), cudaMemcpyDeviceToHost));
+        std::vector<int> gid_of_slot(n);
+        for (int r = 0; r < R; ++r)
+            for (int s0 = rep_poff[r]; s0 < rep_poff[r] + rep_n[r]; ++s0) {
+                int id;
+                if (sizeof(T) == 4) memcpy(&id, &vel[s0].w, 4);
+                else { long long l; memcpy(&l, &vel[s0].w, 8); id = (int)l; }
+                gid_of_slot[s0] = rep_poff[r] + id;
+            }
+        std::vector<int> slot_of_gid(n);
+        for (size_t s0 = 0; s0 < n; ++s0) slot_of_gid[gid_of_slot[s0]] = (int)s0;
+        row_ptr[0] = 0;
+        for (size_t g = 0; g < n; ++g) row_ptr[g + 1] = row_ptr[g] + cnt[slot_of_gid[g]];
+        if (row_ptr[n] > cap || !cols) return fail(ESPP_ERR_ARG, "cols capacity too small");
+        for (size_t g = 0; g < n; ++g) {
+            const int s0 = slot_of_gid[g];
+            int64_t* out = cols + row_ptr[g];
+            for (int k = 0; k < cnt[s0]; ++k) out[k] = gid_of_slot[nb[(size_t)k * d.stride + s0]];
+            std::sort(out, out + cnt[s0]);
+        }
+        return ESPP_OK;
+    }
+
+    // ------------------------------------------------------------------ forces
+    int compute_forces(double* f, int where) override {
+        int rcode = ensure_list();
+        if (rcode) return rcode;
+        double* target = f;
+        if (f && where == ESPP_HOST) target = d_io_x;
+        else if (f && where != ESPP_DEVICE) return fail(ESPP_ERR_ARG, "bad where");
+        Launch<T>::step(d, MODE_FORCES, false, cur, target, 0, 0, st);
+        launches++;
+        CK(cudaGetLastError());
+        if (f && where == ESPP_HOST)
+            CK(cudaMemcpyAsync(f, d_io_x, 3 * (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        return status_from(read_ctrl());
+    }
+
+    // -------------------------------------------------------------- integrate
+    int make_chunk(int S, int p0, bool final_chunk, ChunkGraph** out) {
+        auto key = std::make_tuple(S, p0, final_chunk ? 1 : 0);
+        auto it = graphs.find(key);
+        if (it != graphs.end()) {
+            *out = &it->second;
+            return ESPP_OK;
+        }
+        ChunkGraph cg;
+        if (timing) {
+            cg.ev.resize(3 * (size_t)S);
+            for (auto& e : cg.ev) CK(cudaEventCreate(&e));
+        }
+        cudaStream_t cs = nullptr, bs = nullptr;
+        CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+        cudaGraph_t g;
+        CK(cudaGraphCreate(&g, 0));
+        std::vector<cudaGraphConditionalHandle> h(S);
+        for (int r = 0; r < S; ++r) CK(cudaGraphConditionalHandleCreate(&h[r], g, 0, cudaGraphCondAssignDefault));
+        CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        Launch<T>::set_cond(d, h[0], cs);
+        int p = p0;
+        for (int r = 0; r < S; ++r) {
+            if (timing) CK(cudaEventRecordWithFlags(cg.ev[3 * r], cs, cudaEventRecordExternal));
+            cudaStreamCaptureStatus status;
+            cudaGraph_t capg;
+            const cudaGraphNode_t* deps = nullptr;
+            size_t nd = 0;
+            CK(cudaStreamGetCaptureInfo(cs, &status, nullptr, &capg, &deps, nullptr, &nd));
+            // the parameter struct holds a union without a default constructor
+            alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+            memset(raw, 0, sizeof(raw));
+            cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(raw);
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = h[r];
+            np.conditional.type = cudaGraphCondTypeIf;
+            np.conditional.size = 1;
+            cudaGraphNode_t node;
+            CK(cudaGraphAddNode(&node, capg, deps, nullptr, nd, &np));
+            cudaGraph_t body = np.conditional.phGraph_out[0];
+            CK(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+            CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+            Launch<T>::rebuild(d, p, false, bs);
+            cudaGraph_t tmp;
+            CK(cudaStreamEndCapture(bs, &tmp));
+            const bool last = r == S - 1;
+            const int mode = (final_chunk && last) ? MODE_FINAL : MODE_STEP;
+            if (timing) CK(cudaEventRecordWithFlags(cg.ev[3 * r + 1], cs, cudaEventRecordExternal));
+            Launch<T>::step(d, mode, false, p, nullptr, last ? 0ull : (unsigned long long)h[r + 1], 0, cs);
+            if (timing) CK(cudaEventRecordWithFlags(cg.ev[3 * r + 2], cs, cudaEventRecordExternal));
+            if (mode == MODE_STEP) p ^= 1;
+        }
+        cudaGraph_t done;
+        CK(cudaStreamEndCapture(cs, &done));
+        cudaGraphExec_t ex;
+        CK(cudaGraphInstantiate(&ex, done, 0));
+        cudaStreamDestroy(cs);
+        cudaStreamDestroy(bs);
+        cg.graph = done;
+        cg.exec = ex;
+        auto ins = graphs.emplace(key, std::move(cg));
+        *out = &ins.first->second;
+        return ESPP_OK;
+    }
+
+    // timing mode: add the event-measured durations of the last replay of a chunk
+    int harvest_timing(ChunkGraph* cg) {
+        const size_t S = cg->ev.size() / 3;
+        for (size_t r = 0; r < S; ++r) {
+            float a = 0, b = 0;
+            CK(cudaEventElapsedTime(&a, cg->ev[3 * r], cg->ev[3 * r + 1]));
+            CK(cudaEventElapsedTime(&b, cg->ev[3 * r + 1], cg->ev[3 * r + 2]));
+            t_rebuild_ms += a;
+            t_step_ms += b;
+            t_step_n += 1;
+        }
+        return ESPP_OK;
+    }
+
+    int set_kernel_timing(int enable) override {
+        timing = enable != 0;
+        clear_graphs();
+        t_step_ms = t_rebuild_ms = 0;
+        t_step_n = 0;
+        return ESPP_OK;
+    }
+
+    int kernel_timing(double* out, int reset) override {
+        out[0] = t_step_ms;
+        out[1] = (double)t_step_n;
+        out[2] = t_rebuild_ms;
+        out[3] = (double)t_step_n;
+        if (reset) {
+            t_step_ms = t_rebuild_ms = 0;
+            t_step_n = 0;
+        }
+        return ESPP_OK;
+    }
+
+    int integrate(int64_t nsteps, double dt, double gamma, double kT) override {
+        if (nsteps < 0 || !(dt > 0) || !(gamma >= 0) || !(kT >= 0) || !std::isfinite(dt))
+            return fail(ESPP_ERR_ARG, "need nsteps >= 0, dt > 0, gamma >= 0, kT >= 0");
+        if (nsteps == 0) return ESPP_OK;
+        int rcode = ensure_list();
+        if (rcode) return rcode;
+        rcode = upload_int_params(dt, gamma, kT);
+        if (rcode) return rcode;
+        Ctrl c0 = read_ctrl();
+        const int64_t step0 = c0.step;
+        const int64_t target = step0 + nsteps;
+        const int64_t rb0 = c0.n_rebuilds;
+        if (!f_valid) {
+            Launch<T>::step(d, MODE_INIT, false, cur, nullptr, 0, 0, st);
+            launches++;
+            f_valid = true;
+        }
+        const int c_start = cur;
+        Launch<T>::prologue(d, cur, 0, st);
+        launches++;
+        CK(cudaGetLastError());
+        int64_t done = step0;  // last completed step
+        for (int attempt = 0; attempt < 8; ++attempt) {
+            // positions of step done+1 live in buffer (1 - c_start) ^ ((done - step0) & 1)
+            int p = (1 - c_start) ^ (int)((done - step0) & 1);
+            int64_t remaining = target - done;
+            ChunkGraph* last_cg = nullptr;
+            while (remaining > 0) {
+                const int S = (int)std::min<int64_t>(remaining, chunk);
+                const bool fin = S == remaining;
+                ChunkGraph* cg = nullptr;
+                rcode = make_chunk(S, p, fin, &cg);
+                if (rcode) return rcode;
+                CK(cudaGraphLaunch(cg->exec, st));
+                last_cg = cg;
+                launches += 1 + S;
+                p ^= (fin ? (S - 1) : S) & 1;
+                remaining -= S;
+            }
+            Ctrl c = read_ctrl();
+            CK(cudaGetLastError());
+            launches += 9 * (int64_t)(c.n_rebuilds - (unsigned)rb0);
+            if (c.err & (ERRBIT_BOND | ERRBIT_NONFINITE | ERRBIT_TIMEOUT)) return status_from(c);
+            if (c.err & ERRBIT_OVERFLOW) {
+                // frozen after step c.step with the positions of the next step in
+                // buffer pm: grow the list, rebuild every replica there, go on
+                done = c.step;
+                const int pm = (1 - c_start) ^ (int)((done - step0) & 1);
+                rcode = grow_list(c.need_cap);
+                if (rcode) return rcode;
+                Launch<T>::request_all(d, st);
+                Launch<T>::rebuild(d, pm, false, st);
+                launches += 10;
+                CK(cudaGetLastError());
+                continue;
+            }
+            if (c.step != target) return fail(ESPP_ERR_STATE, "step counter mismatch after integrate");
+            if (timing && last_cg) {
+                rcode = harvest_timing(last_cg);
+                if (rcode) return rcode;
+            }
+            cur = (1 - c_start) ^ (int)((nsteps - 1) & 1);
+            return ESPP_OK;
+        }
+        return fail(ESPP_ERR_LIST_OVERFLOW, "Verlet list overflow persists after retries");
+    }
+
+    // ------------------------------------------------------------ observables
+    int observables(espp_obs_t* out, int Rq) override {
+        if (!out || Rq < 1 || Rq > R) return fail(ESPP_ERR_ARG, "bad output");
+        int rcode = ensure_list();
+        if (rcode) return rcode;
+        rcode = upload_int_params(ip_key[0] > 0 ? ip_key[0] : 1.0, std::max(ip_key[1], 0.0), std::max(ip_key[2], 0.0));
+        if (rcode) return rcode;
+        Launch<T>::step(d, MODE_FORCES, true, cur, nullptr, 0, 0, st);
+        Launch<T>::reduce_obs(d, d_obs, st);
+        Launch<T>::rg2(d, cur, d_mol_members, d_mol_off, d_mol_rep, (int)mol_rep_h.size(), d_mol_rg2, st);
+        launches += 3;
+        CK(cudaGetLastError());
+        std::vector<double> part((size_t)R * NPART), rg(mol_rep_h.size());
+        CK(cudaMemcpyAsync(part.data(), d_obs, part.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (!rg.empty()) CK(cudaMemcpyAsync(rg.data(), d_mol_rg2, rg.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        Ctrl c = read_ctrl();
+        CK(cudaGetLastError());
+        std::vector<double> rgsum(R, 0.0);
+        std::vector<int64_t> nmol(R, 0);
+        for (size_t m = 0; m < rg.size(); ++m) {
+            rgsum[mol_rep_h[m]] += rg[m];
+            nmol[mol_rep_h[m]]++;
+        }
+        for (int r = 0; r < Rq; ++r) {
+            const double* q = &part[(size_t)r * NPART];
+            espp_obs_t& o = out[r];
+            memset(&o, 0, sizeof(o));
+            o.step = c.step;
+            o.n = rep_n[r];
+            o.ke = q[P_KE];
+            o.pe_pair = q[P_PE_PAIR];
+            o.pe_bond = q[P_PE_BOND];
+            o.virial = q[P_VIRIAL];
+            o.px = q[P_PX];
+            o.py = q[P_PY];
+            o.pz = q[P_PZ];
+            o.temperature = 2.0 * o.ke / (3.0 * rep_n[r]);
+            const double V = box[3 * r] * box[3 * r + 1] * box[3 * r + 2];
+            o.pressure = (2.0 * o.ke + o.virial) / (3.0 * V);
+            o.mean_bond = q[P_BOND_CNT] > 0 ? q[P_BOND_LEN] / q[P_BOND_CNT] : 0.0;
+            o.rg2 = nmol[r] > 0 ? rgsum[r] / nmol[r] : 0.0;
+            o.n_molecules = nmol[r];
+            o.n_rebuilds = c.n_rebuilds;
+            o.error_word = c.err;
+        }
+        return ESPP_OK;
+    }
+
+    int rdf_counts(int rep, double rmax, int nbins, int64_t* counts) override {
+        if (rep < 0 || rep >= R || nbins < 1 || !(rmax > 0) || !counts) return fail(ESPP_ERR_ARG, "bad rdf arguments");
+        for (int c = 0; c < 3; ++c)
+            if (rmax >= 0.5 * box[3 * rep + c]) return fail(ESPP_ERR_ARG, "rmax must be below half the box");
+        if (!state_set) return fail(ESPP_ERR_STATE, "no state set");
+        if (nbins > 12288) return fail(ESPP_ERR_ARG, "too many bins");
+        if (hist_cap < nbins) {
+            if (d_hist) cudaFree(d_hist);
+            d_hist = nullptr;
+            CK(cudaMalloc(&d_hist, nbins * sizeof(unsigned long long)));
+            allocs.push_back(d_hist);
+            hist_cap = nbins;
+        }
+        CK(cudaMemsetAsync(d_hist, 0, nbins * sizeof(unsigned long long), st));
+        Launch<T>::rdf(d, cur, rep, rmax, nbins, d_hist, st);
+        launches++;
+        CK(cudaGetLastError());
+        std::vector<unsigned long long> h(nbins);
+        CK(cudaMemcpyAsync(h.data(), d_hist, nbins * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int b = 0; b < nbins; ++b) counts[b] = (int64_t)h[b];
+        return ESPP_OK;
+    }
+
+    // ------------------------------------------------------------- checkpoint
+    int checkpoint_save(const char*) override { return fail(ESPP_ERR_STATE, "checkpoint not available"); }
+    int checkpoint_load(const char*) override { return fail(ESPP_ERR_STATE, "checkpoint not available"); }
+
+    // ------------------------------------------------------------ diagnostics
+    uint32_t error_word() override { return read_ctrl().err; }
+    int64_t num_particles() override { return N; }
+    int32_t num_replicas() override { return R; }
+    int64_t num_rebuilds() override { return read_ctrl().n_rebuilds; }
+    int64_t step() override { return read_ctrl().step; }
+    int32_t list_capacity() override { return d.cap; }
+    int64_t kernel_launches() override { return launches; }
+    int list_stats(int64_t* total, int32_t* maxc) override {
+        int rcode = ensure_list();
+        if (rcode) return rcode;
+        std::vector<int> cnt((size_t)N);
+        CK(cudaMemcpy(cnt.data(), d.nbr_cnt, (size_t)N * sizeof(int), cudaMemcpyDeviceToHost));
+        int64_t t = 0;
+        int m = 0;
+        for (int c : cnt) {
+            t += c;
+            m = std::max(m, c);
+        }
+        if (total) *total = t;
+        if (maxc) *maxc = m;
+        return ESPP_OK;
+    }
+
+    int set_chunk(int steps) override {
+        if (steps < 1 || steps > 1024) return fail(ESPP_ERR_ARG, "chunk must be in [1, 1024]");
+        chunk = steps;
+        clear_graphs();
+        return ESPP_OK;
+    }
+};
+
+}  // namespace espp
+
+struct espp_system {
+    std::unique_ptr<espp::SystemBase> impl;
+    std::string create_msg;
+};
+
+static thread_local std::string g_create_error;
+
+template <class F>
+static int guarded(espp_h h, F&& f) {
+    if (!h || !h->impl) return ESPP_ERR_ARG;
+    try {
+        return f(*h->impl);
+    } catch (const std::exception& e) {
+        h->impl->msg = e.what();
+        return ESPP_ERR_STATE;
+    }
+}
+
+extern "C" {
+
+int espp_batch_create(int32_t R, const espp_replica_desc* descs, int precision, void* stream, espp_h* out) {
+    if (!out || R < 1 || !descs) {
+        g_create_error = "invalid arguments";
+        return ESPP_ERR_ARG;
+    }
+    *out = nullptr;
+    std::unique_ptr<espp_system> h(new espp_system());
+    int rc;
+    if (precision == ESPP_FP32) {
+        auto* s = new espp::System<float>();
+        h->impl.reset(s);
+        rc = s->create(R, descs, (cudaStream_t)stream);
+    } else if (precision == ESPP_FP64) {
+        auto* s = new espp::System<double>();
+        h->impl.reset(s);
+        rc = s->create(R, descs, (cudaStream_t)stream);
+    } else {
+        g_create_error = "precision must be ESPP_FP32 or ESPP_FP64";
+        return ESPP_ERR_ARG;
+    }
+    if (rc != ESPP_OK) {
+        g_create_error = h->impl->msg;
+        return rc;
+    }
+    *out = h.release();
+    return ESPP_OK;
+}
+
+int espp_system_create(const double box[3], int64_t n, const int32_t* types, int64_t n_bonds,
+                       const int64_t* bonds, int precision, uint64_t seed, void* stream, espp_h* out) {
+    if (!box) return ESPP_ERR_ARG;
+    espp_replica_desc d;
+    d.box[0] = box[0];
+    d.box[1] = box[1];
+    d.box[2] = box[2];
+    d.n = n;
+    d.types = types;
+    d.n_bonds = n_bonds;
+    d.bonds = bonds;
+    d.seed = seed;
+    return espp_batch_create(1, &d, precision, stream, out);
+}
+
+int espp_system_destroy(espp_h h) {
+    if (!h) return ESPP_ERR_ARG;
+    delete h;
+    return ESPP_OK;
+}
+
+int espp_set_state(espp_h h, const double* x, const double* v, const int32_t* img, int where) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.set_state(x, v, img, where); });
+}
+int espp_get_state(espp_h h, double* x, double* v, int32_t* img, int where) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.get_state(x, v, img, where); });
+}
+int espp_set_step(espp_h h, int64_t step) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.set_step(step); });
+}
+int espp_set_interaction(espp_h h, int kind, int ta, int tb, const double* p, int64_t np) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.set_interaction(kind, ta, tb, p, np); });
+}
+int espp_set_mass(espp_h h, int type, double m) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.set_mass(type, m); });
+}
+int espp_build_neighbors(espp_h h, double rc, double skin) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.build_neighbors(rc, skin); });
+}
+int espp_get_neighbors(espp_h h, int64_t* row_ptr, int64_t* cols, int64_t cap) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.get_neighbors(row_ptr, cols, cap); });
+}
+int espp_compute_forces(espp_h h, double* f, int where) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.compute_forces(f, where); });
+}
+int espp_integrate(espp_h h, int64_t nsteps, double dt, double gamma, double kT) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.integrate(nsteps, dt, gamma, kT); });
+}
+int espp_observables(espp_h h, espp_obs_t* out) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.observables(out, 1); });
+}
+int espp_observables_batch(espp_h h, espp_obs_t* out, int32_t R) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.observables(out, R); });
+}
+int espp_rdf_counts(espp_h h, int32_t rep, double rmax, int32_t nbins, int64_t* counts) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.rdf_counts(rep, rmax, nbins, counts); });
+}
+int espp_checkpoint_save(espp_h h, const char* path) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.checkpoint_save(path); });
+}
+int espp_checkpoint_load(espp_h h, const char* path) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.checkpoint_load(path); });
+}
+const char* espp_last_error(espp_h h) {
+    if (!h || !h->impl) return g_create_error.c_str();
+    return h->impl->msg.c_str();
+}
+uint32_t espp_error_word(espp_h h) { return (h && h->impl) ? h->impl->error_word() : 0u; }
+int64_t espp_num_particles(espp_h h) { return (h && h->impl) ? h->impl->num_particles() : -1; }
+int32_t espp_num_replicas(espp_h h) { return (h && h->impl) ? h->impl->num_replicas() : -1; }
+int64_t espp_num_rebuilds(espp_h h) { return (h && h->impl) ? h->impl->num_rebuilds() : -1; }
+int64_t espp_step(espp_h h) { return (h && h->impl) ? h->impl->step() : -1; }
+int32_t espp_list_capacity(espp_h h) { return (h && h->impl) ? h->impl->list_capacity() : -1; }
+int64_t espp_kernel_launches(espp_h h) { return (h && h->impl) ? h->impl->kernel_launches() : -1; }
+
+int espp_set_kernel_timing(espp_h h, int enable) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.set_kernel_timing(enable); });
+}
+int espp_kernel_timing(espp_h h, double* out, int reset) {
+    if (!out) return ESPP_ERR_ARG;
+    return guarded(h, [&](espp::SystemBase& s) { return s.kernel_timing(out, reset); });
+}
+int espp_list_stats(espp_h h, int64_t* total_entries, int32_t* max_count) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.list_stats(total_entries, max_count); });
+}
+int espp_set_graph_chunk(espp_h h, int32_t steps) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.set_chunk(steps); });
+}
+
+int espp_langevin_noise(uint64_t seed, int64_t step, int64_t n, double* out, void* stream) {
+    if (n < 0 || (n > 0 && !out)) return ESPP_ERR_ARG;
+    espp::launch_noise(seed, step, n, out, (cudaStream_t)stream);
+    if (cudaGetLastError() != cudaSuccess) return ESPP_ERR_CUDA;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return ESPP_ERR_CUDA;
+    return ESPP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,343 @@
+"""Thin ctypes binding of libespp_gb.so (include/espp.h).
+
+The functions below carry the C names and only marshal arguments; every step of
+the MD path runs in the library's CUDA kernels.  `System` is a convenience
+wrapper over one handle that accepts numpy arrays (host) or CUDA torch tensors
+(device).  There is no CPU fallback: if the library is missing or no GPU is
+visible, the first call raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libespp_gb.so")
+
+ESPP_OK = 0
+ESPP_ERR_ARG = -1
+ESPP_ERR_CUDA = -2
+ESPP_ERR_LIST_OVERFLOW = -3
+ESPP_ERR_BOND_BROKEN = -4
+ESPP_ERR_NONFINITE = -5
+ESPP_ERR_TIMEOUT = -6
+ESPP_ERR_BOX_TOO_SMALL = -7
+ESPP_ERR_STATE = -8
+ESPP_ERR_IO = -9
+
+ESPP_FP32 = 1
+ESPP_FP64 = 2
+ESPP_HOST = 0
+ESPP_DEVICE = 1
+
+ESPP_NONE = 0
+ESPP_LJ = 1
+ESPP_WCA = 2
+ESPP_LJ_CAPPED = 3
+ESPP_FENE = 4
+
+ERROR_NAMES = {
+    ESPP_ERR_ARG: "ESPP_ERR_ARG", ESPP_ERR_CUDA: "ESPP_ERR_CUDA",
+    ESPP_ERR_LIST_OVERFLOW: "ESPP_ERR_LIST_OVERFLOW", ESPP_ERR_BOND_BROKEN: "ESPP_ERR_BOND_BROKEN",
+    ESPP_ERR_NONFINITE: "ESPP_ERR_NONFINITE", ESPP_ERR_TIMEOUT: "ESPP_ERR_TIMEOUT",
+    ESPP_ERR_BOX_TOO_SMALL: "ESPP_ERR_BOX_TOO_SMALL", ESPP_ERR_STATE: "ESPP_ERR_STATE",
+    ESPP_ERR_IO: "ESPP_ERR_IO",
+}
+
+# every symbol include/espp.h declares
+EXPORTS = (
+    "espp_system_create", "espp_batch_create", "espp_system_destroy", "espp_set_state",
+    "espp_get_state", "espp_set_step", "espp_set_interaction", "espp_set_mass",
+    "espp_build_neighbors", "espp_get_neighbors", "espp_compute_forces", "espp_integrate",
+    "espp_observables", "espp_observables_batch", "espp_rdf_counts", "espp_checkpoint_save",
+    "espp_checkpoint_load", "espp_last_error", "espp_error_word", "espp_num_particles",
+    "espp_num_replicas", "espp_num_rebuilds", "espp_step", "espp_list_capacity",
+    "espp_kernel_launches", "espp_langevin_noise", "espp_hilbert_ranks",
+    "espp_set_kernel_timing", "espp_kernel_timing", "espp_set_graph_chunk", "espp_list_stats",
+)
+
+
+class EsppError(RuntimeError):
+    def __init__(self, code, msg):
+        self.code = code
+        super().__init__("%s (%d): %s" % (ERROR_NAMES.get(code, "?"), code, msg))
+
+
+class ReplicaDesc(ctypes.Structure):
+    _fields_ = [("box", ctypes.c_double * 3), ("n", ctypes.c_int64),
+                ("types", ctypes.c_void_p), ("n_bonds", ctypes.c_int64),
+                ("bonds", ctypes.c_void_p), ("seed", ctypes.c_uint64)]
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("ke", ctypes.c_double), ("pe_pair", ctypes.c_double),
+                ("pe_bond", ctypes.c_double), ("virial", ctypes.c_double),
+                ("px", ctypes.c_double), ("py", ctypes.c_double), ("pz", ctypes.c_double),
+                ("temperature", ctypes.c_double), ("pressure", ctypes.c_double),
+                ("mean_bond", ctypes.c_double), ("rg2", ctypes.c_double),
+                ("n_molecules", ctypes.c_int64), ("n_rebuilds", ctypes.c_int64),
+                ("error_word", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+_lib = None
+
+
+def lib(path: str = LIB_PATH):
+    """Load libespp_gb.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libespp_gb.so is not built (%s); run __graft_entry__.build()" % path)
+    L = ctypes.CDLL(path)
+    vp, dp, i64, i32 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.c_int32
+    sig = {
+        "espp_system_create": ([dp, i64, vp, i64, vp, ctypes.c_int, ctypes.c_uint64, vp, ctypes.POINTER(vp)], ctypes.c_int),
+        "espp_batch_create": ([i32, ctypes.POINTER(ReplicaDesc), ctypes.c_int, vp, ctypes.POINTER(vp)], ctypes.c_int),
+        "espp_system_destroy": ([vp], ctypes.c_int),
+        "espp_set_state": ([vp, vp, vp, vp, ctypes.c_int], ctypes.c_int),
+        "espp_get_state": ([vp, vp, vp, vp, ctypes.c_int], ctypes.c_int),
+        "espp_set_step": ([vp, i64], ctypes.c_int),
+        "espp_set_interaction": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, i64], ctypes.c_int),
+        "espp_set_mass": ([vp, ctypes.c_int, ctypes.c_double], ctypes.c_int),
+        "espp_build_neighbors": ([vp, ctypes.c_double, ctypes.c_double], ctypes.c_int),
+        "espp_get_neighbors": ([vp, vp, vp, i64], ctypes.c_int),
+        "espp_compute_forces": ([vp, vp, ctypes.c_int], ctypes.c_int),
+        "espp_integrate": ([vp, i64, ctypes.c_double, ctypes.c_double, ctypes.c_double], ctypes.c_int),
+        "espp_observables": ([vp, ctypes.POINTER(Obs)], ctypes.c_int),
+        "espp_observables_batch": ([vp, ctypes.POINTER(Obs), i32], ctypes.c_int),
+        "espp_rdf_counts": ([vp, i32, ctypes.c_double, i32, vp], ctypes.c_int),
+        "espp_checkpoint_save": ([vp, ctypes.c_char_p], ctypes.c_int),
+        "espp_checkpoint_load": ([vp, ctypes.c_char_p], ctypes.c_int),
+        "espp_last_error": ([vp], ctypes.c_char_p),
+        "espp_error_word": ([vp], ctypes.c_uint32),
+        "espp_num_particles": ([vp], i64),
+        "espp_num_replicas": ([vp], i32),
+        "espp_num_rebuilds": ([vp], i64),
+        "espp_step": ([vp], i64),
+        "espp_list_capacity": ([vp], i32),
+        "espp_kernel_launches": ([vp], i64),
+        "espp_langevin_noise": ([ctypes.c_uint64, i64, i64, vp, vp], ctypes.c_int),
+        "espp_hilbert_ranks": ([i32, i32, i32, vp], ctypes.c_int),
+        "espp_set_kernel_timing": ([vp, ctypes.c_int], ctypes.c_int),
+        "espp_kernel_timing": ([vp, dp, ctypes.c_int], ctypes.c_int),
+        "espp_set_graph_chunk": ([vp, i32], ctypes.c_int),
+        "espp_list_stats": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i32)], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _check(rc, h=None):
+    if rc != ESPP_OK:
+        msg = lib().espp_last_error(h)
+        raise EsppError(rc, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    """(pointer, where) for a numpy array or a torch tensor."""
+    if a is None:
+        return None, ESPP_HOST
+    if hasattr(a, "data_ptr"):
+        if a.is_cuda:
+            return ctypes.c_void_p(a.data_ptr()), ESPP_DEVICE
+        return ctypes.c_void_p(a.data_ptr()), ESPP_HOST
+    return a.ctypes.data_as(ctypes.c_void_p), ESPP_HOST
+
+
+# ---- the C calls, by name --------------------------------------------------------
+def espp_hilbert_ranks(nx, ny, nz):
+    out = np.zeros(nx * ny * nz, dtype=np.int32)
+    _check(lib().espp_hilbert_ranks(nx, ny, nz, out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def espp_langevin_noise(seed, step, out_tensor, stream=0):
+    n = out_tensor.numel() // 3
+    _check(lib().espp_langevin_noise(seed, step, n, ctypes.c_void_p(out_tensor.data_ptr()),
+                                     ctypes.c_void_p(stream)))
+
+
+class System:
+    """One handle: a single system or a batch of independent replicas."""
+
+    def __init__(self, box=None, n=None, types=None, bonds=None, precision=ESPP_FP32, seed=42,
+                 stream=0, replicas=None):
+        L = lib()
+        self._h = ctypes.c_void_p()
+        self.precision = precision
+        keep = []
+        if replicas is None:
+            replicas = [dict(box=box, n=n, types=types, bonds=bonds, seed=seed)]
+        descs = (ReplicaDesc * len(replicas))()
+        self.rep_n = []
+        for k, r in enumerate(replicas):
+            t = None if r.get("types") is None else np.ascontiguousarray(r["types"], dtype=np.int32)
+            b = None
+            if r.get("bonds") is not None and len(r["bonds"]) > 0:
+                b = np.ascontiguousarray(r["bonds"], dtype=np.int64).reshape(-1, 2)
+            keep += [t, b]
+            d = descs[k]
+            for c in range(3):
+                d.box[c] = float(np.asarray(r["box"], dtype=np.float64)[c])
+            d.n = int(r["n"])
+            d.types = t.ctypes.data if t is not None else None
+            d.n_bonds = 0 if b is None else b.shape[0]
+            d.bonds = b.ctypes.data if b is not None else None
+            d.seed = int(r.get("seed", 42))
+            self.rep_n.append(int(r["n"]))
+        rc = L.espp_batch_create(len(replicas), descs, precision, ctypes.c_void_p(stream),
+                                 ctypes.byref(self._h))
+        _check(rc, None)
+        self.n = sum(self.rep_n)
+        self.R = len(replicas)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().espp_system_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _c(self, rc):
+        _check(rc, self._h)
+
+    # state
+    def set_state(self, x, v=None, img=None):
+        if not hasattr(x, "data_ptr"):
+            x = np.ascontiguousarray(x, dtype=np.float64)
+            v = None if v is None else np.ascontiguousarray(v, dtype=np.float64)
+            img = None if img is None else np.ascontiguousarray(img, dtype=np.int32)
+        px, where = _ptr(x)
+        pv, _ = _ptr(v)
+        pi, _ = _ptr(img)
+        self._c(lib().espp_set_state(self._h, px, pv, pi, where))
+
+    def get_state(self, out=None):
+        if out is not None:
+            x, v, img = out
+            px, where = _ptr(x)
+            self._c(lib().espp_get_state(self._h, px, _ptr(v)[0], _ptr(img)[0], where))
+            return out
+        x = np.zeros((self.n, 3))
+        v = np.zeros((self.n, 3))
+        img = np.zeros((self.n, 3), dtype=np.int32)
+        self._c(lib().espp_get_state(self._h, _ptr(x)[0], _ptr(v)[0], _ptr(img)[0], ESPP_HOST))
+        return x, v, img
+
+    def set_step(self, step):
+        self._c(lib().espp_set_step(self._h, int(step)))
+
+    # interactions
+    def set_interaction(self, kind, ta=0, tb=0, params=()):
+        p = (ctypes.c_double * max(1, len(params)))(*params)
+        self._c(lib().espp_set_interaction(self._h, kind, ta, tb, p, len(params)))
+
+    def set_lj(self, eps, sigma, rc, shift=True, ta=0, tb=0):
+        self.set_interaction(ESPP_LJ, ta, tb, (eps, sigma, rc, 1.0 if shift else 0.0))
+
+    def set_wca(self, eps=1.0, sigma=1.0, ta=0, tb=0):
+        self.set_interaction(ESPP_WCA, ta, tb, (eps, sigma))
+
+    def set_lj_capped(self, eps, sigma, rc, caprad, shift=True, ta=0, tb=0):
+        self.set_interaction(ESPP_LJ_CAPPED, ta, tb, (eps, sigma, rc, 1.0 if shift else 0.0, caprad))
+
+    def set_fene(self, K=30.0, R0=1.5):
+        self.set_interaction(ESPP_FENE, 0, 0, (K, R0))
+
+    def set_mass(self, t, m):
+        self._c(lib().espp_set_mass(self._h, t, m))
+
+    # neighbours, forces, dynamics
+    def build_neighbors(self, rc, skin):
+        self._c(lib().espp_build_neighbors(self._h, rc, skin))
+
+    def get_neighbors(self):
+        row = np.zeros(self.n + 1, dtype=np.int64)
+        rc = lib().espp_get_neighbors(self._h, _ptr(row)[0], None, 0)
+        need = int(row[-1])
+        cols = np.zeros(max(need, 1), dtype=np.int64)
+        self._c(lib().espp_get_neighbors(self._h, _ptr(row)[0], _ptr(cols)[0], cols.size))
+        return row, cols[:need]
+
+    def compute_forces(self, out=None):
+        if out is None:
+            out = np.zeros((self.n, 3))
+        p, where = _ptr(out)
+        self._c(lib().espp_compute_forces(self._h, p, where))
+        return out
+
+    def integrate(self, nsteps, dt, gamma, kT):
+        self._c(lib().espp_integrate(self._h, int(nsteps), dt, gamma, kT))
+
+    def observables(self, replica=None):
+        out = (Obs * self.R)()
+        self._c(lib().espp_observables_batch(self._h, out, self.R))
+        if replica is None:
+            return out[0].as_dict() if self.R == 1 else [o.as_dict() for o in out]
+        return out[replica].as_dict()
+
+    def rdf_counts(self, rmax, nbins, replica=0):
+        c = np.zeros(nbins, dtype=np.int64)
+        self._c(lib().espp_rdf_counts(self._h, replica, rmax, nbins, _ptr(c)[0]))
+        return c
+
+    def checkpoint_save(self, path):
+        self._c(lib().espp_checkpoint_save(self._h, path.encode()))
+
+    def checkpoint_load(self, path):
+        self._c(lib().espp_checkpoint_load(self._h, path.encode()))
+
+    # timing
+    def set_kernel_timing(self, enable=True):
+        self._c(lib().espp_set_kernel_timing(self._h, 1 if enable else 0))
+
+    def kernel_timing(self, reset=False):
+        out = (ctypes.c_double * 4)()
+        self._c(lib().espp_kernel_timing(self._h, out, 1 if reset else 0))
+        return dict(step_ms=out[0], step_launches=int(out[1]), rebuild_ms=out[2], steps=int(out[3]))
+
+    def list_stats(self):
+        t, m = ctypes.c_int64(), ctypes.c_int32()
+        self._c(lib().espp_list_stats(self._h, ctypes.byref(t), ctypes.byref(m)))
+        return int(t.value), int(m.value)
+
+    def set_graph_chunk(self, steps):
+        self._c(lib().espp_set_graph_chunk(self._h, int(steps)))
+
+    # diagnostics
+    @property
+    def error_word(self):
+        return int(lib().espp_error_word(self._h))
+
+    @property
+    def step(self):
+        return int(lib().espp_step(self._h))
+
+    @property
+    def n_rebuilds(self):
+        return int(lib().espp_num_rebuilds(self._h))
+
+    @property
+    def list_capacity(self):
+        return int(lib().espp_list_capacity(self._h))
+
+    @property
+    def kernel_launches(self):
+        return int(lib().espp_kernel_launches(self._h))

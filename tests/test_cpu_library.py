@@ -1,0 +1,73 @@
+"""CPU-only checks of the CUDA library: it builds, loads, exports every symbol
+the C header declares, and its host-side Hilbert ordering is a bijection whose
+consecutive cells are face neighbours.  No GPU work is issued."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2608_14911_gb300 import build as pbuild
+from paper_2608_14911_gb300 import espp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pbuild.build()
+    return espp.lib()
+
+
+def header_symbols():
+    txt = open(os.path.join(ROOT, "include", "espp.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(espp_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol(lib):
+    syms = header_symbols()
+    assert len(syms) >= 20
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert sorted(espp.EXPORTS) == syms
+
+
+@pytest.mark.parametrize("n", [2, 4, 8, 16])
+def test_hilbert_ranks_bijective_and_adjacent(lib, n):
+    rank = espp.espp_hilbert_ranks(n, n, n)
+    assert np.array_equal(np.sort(rank), np.arange(n ** 3))
+    order = np.argsort(rank)
+    z, rem = np.divmod(order, n * n)
+    y, x = np.divmod(rem, n)
+    steps = np.abs(np.diff(x)) + np.abs(np.diff(y)) + np.abs(np.diff(z))
+    assert np.all(steps == 1)
+
+
+@pytest.mark.parametrize("dims", [(3, 5, 7), (69, 69, 69), (76, 76, 38)])
+def test_hilbert_ranks_non_power_of_two(lib, dims):
+    rank = espp.espp_hilbert_ranks(*dims)
+    assert np.array_equal(np.sort(rank), np.arange(np.prod(dims)))
+    # locality: consecutive cells are mostly face neighbours
+    nx, ny, nz = dims
+    order = np.argsort(rank)
+    z, rem = np.divmod(order, nx * ny)
+    y, x = np.divmod(rem, nx)
+    steps = np.abs(np.diff(x)) + np.abs(np.diff(y)) + np.abs(np.diff(z))
+    assert np.mean(steps == 1) > 0.9
+
+
+def test_hilbert_rejects_bad_grid(lib):
+    with pytest.raises(espp.EsppError):
+        espp.espp_hilbert_ranks(0, 3, 3)
+
+
+def test_create_without_gpu_fails_loudly(lib):
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    with pytest.raises(espp.EsppError):
+        espp.System(np.array([10.0, 10.0, 10.0]), 10)

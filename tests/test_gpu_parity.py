@@ -1,0 +1,319 @@
+"""GPU parity tests: the CUDA path (through the C ABI) against the oracle on the
+same seeded inputs.  Tolerances: neighbour sets exact outside a 1e-6 sigma band
+at the list cutoff (FP32) or exact (FP64); single-step forces <= 1e-5 relative
+RMS in FP32 and <= 1e-12 in FP64."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2608_14911_gb300 import espp, inputs as I
+
+from _systems import (KG_BOND, KG_PAIR, LJ_PAIR, WCA_RC, Case, capped_case, kg_case, lj_case,
+                      rel_rms, two_type_case)
+
+pytestmark = pytest.mark.gpu
+
+FP32, FP64 = espp.ESPP_FP32, espp.ESPP_FP64
+FORCE_TOL = {FP32: 1e-5, FP64: 1e-12}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+    import torch
+    assert torch.cuda.is_available()
+
+
+def cases():
+    return [kg_case(), kg_case(7, 23, seed=5, jitter=0.1), lj_case(), two_type_case(),
+            capped_case()]
+
+
+# ---------------------------------------------------------------------------
+def test_philox_stream_bit_exact():
+    import torch
+    for seed in (0, 42, (1 << 40) + 7):
+        for step in (0, 1, 12345, (1 << 33) + 5):
+            n = 1537
+            out = torch.zeros((n, 3), dtype=torch.float64, device="cuda")
+            espp.espp_langevin_noise(seed, step, out)
+            ref = O.langevin_noise(seed, step, n)
+            assert np.array_equal(out.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+@pytest.mark.parametrize("case", cases(), ids=lambda c: c.name)
+def test_neighbour_sets_match_brute_force(case, prec):
+    s = case.system(prec)
+    row, cols = s.get_neighbors()
+    c = case.cfg
+    rl = case.rc_list + case.skin
+    orow, ocols = O.neighbors(c.box, c.x, rl, method="brute")
+    band = 1e-6 if prec == FP32 else 0.0
+    for i in range(c.n):
+        got = set(cols[row[i]:row[i + 1]].tolist())
+        exp = set(ocols[orow[i]:orow[i + 1]].tolist())
+        if got == exp:
+            continue
+        for j in got ^ exp:
+            d = c.x[i] - c.x[j]
+            d -= c.box * np.round(d / c.box)
+            assert abs(np.linalg.norm(d) - rl) <= band, (i, j, np.linalg.norm(d))
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+@pytest.mark.parametrize("case", cases(), ids=lambda c: c.name)
+def test_forces_match_oracle(case, prec):
+    s = case.system(prec)
+    f = s.compute_forces()
+    c = case.cfg
+    fo, _ = O.forces(case.model, c.box, c.x, c.types, c.bonds)
+    assert rel_rms(f, fo) <= FORCE_TOL[prec]
+    # a second explicit build (resort of an already sorted state) changes nothing
+    s.build_neighbors(case.rc_list, case.skin)
+    f2 = s.compute_forces()
+    assert rel_rms(f2, fo) <= FORCE_TOL[prec]
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_forces_device_pointers(prec):
+    import torch
+    case = kg_case()
+    c = case.cfg
+    s = espp.System(c.box, c.n, c.types, c.bonds, precision=prec)
+    s.set_wca()
+    s.set_fene()
+    x = torch.tensor(c.x, device="cuda")
+    img = torch.tensor(c.img, device="cuda", dtype=torch.int32)
+    s.set_state(x, None, img)
+    s.build_neighbors(WCA_RC, 0.4)
+    f = torch.zeros((c.n, 3), dtype=torch.float64, device="cuda")
+    s.compute_forces(f)
+    fo, _ = O.forces(case.model, c.box, c.x, c.types, c.bonds)
+    assert rel_rms(f.cpu().numpy(), fo) <= FORCE_TOL[prec]
+    xo = torch.zeros_like(x)
+    vo = torch.zeros_like(x)
+    io = torch.zeros_like(img)
+    s.get_state((xo, vo, io))
+    assert np.array_equal(xo.cpu().numpy(), c.x)
+    assert np.array_equal(io.cpu().numpy(), c.img)
+    s.close()
+
+
+def _unwrapped(x, img, box):
+    return x + img * box
+
+
+@pytest.mark.parametrize("nsteps", [1, 7, 150])
+@pytest.mark.parametrize("case_fn", [kg_case, lj_case, two_type_case], ids=["kg", "lj", "two"])
+def test_integrate_fp64_matches_oracle(case_fn, nsteps):
+    case = case_fn()
+    s = case.system(FP64, seed=11)
+    s.integrate(nsteps, 0.005, 1.0, 1.0)
+    x, v, img = s.get_state()
+    st = case.oracle_state()
+    O.integrate(case.model, st, nsteps, 0.005, 1.0, 1.0, seed=11)
+    box = case.cfg.box
+    ux, uo = _unwrapped(x, img, box), _unwrapped(st.x, st.img, box)
+    assert np.abs(ux - uo).max() < 1e-10
+    assert np.abs(v - st.v).max() < 1e-9
+    assert s.step == nsteps
+    s.close()
+
+
+def test_integrate_fp64_split_calls_equal_one_call():
+    case = kg_case()
+    a = case.system(FP64, seed=3)
+    a.integrate(90, 0.005, 1.0, 1.0)
+    b = case.system(FP64, seed=3)
+    for k in (1, 2, 64, 23):
+        b.integrate(k, 0.005, 1.0, 1.0)
+    xa, va, ia = a.get_state()
+    xb, vb, ib = b.get_state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(ia, ib)
+
+
+@pytest.mark.parametrize("case_fn", [kg_case, lj_case], ids=["kg", "lj"])
+def test_integrate_fp32_single_step(case_fn):
+    case = case_fn()
+    s = case.system(FP32, seed=5)
+    s.integrate(1, 0.005, 1.0, 1.0)
+    x, v, img = s.get_state()
+    st = case.oracle_state()
+    O.integrate(case.model, st, 1, 0.005, 1.0, 1.0, seed=5)
+    box = case.cfg.box
+    ulp = np.spacing(np.float32(box.max()))
+    assert np.abs(_unwrapped(x, img, box) - _unwrapped(st.x, st.img, box)).max() <= 4 * ulp
+    assert rel_rms(v, st.v) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+@pytest.mark.parametrize("case_fn", [kg_case, lj_case, two_type_case], ids=["kg", "lj", "two"])
+def test_observables_match_oracle(case_fn, prec):
+    case = case_fn()
+    s = case.system(prec)
+    o = s.observables()
+    oo = O.observables(case.model, case.oracle_state())
+    tol = 1e-12 if prec == FP64 else 2e-6
+    for k in ("pe_pair", "pe_bond", "virial", "ke", "temperature", "pressure", "mean_bond", "rg2"):
+        ref = oo[k]
+        assert abs(o[k] - ref) <= tol * max(1.0, abs(ref)), (k, o[k], ref)
+    assert o["n_molecules"] == int(oo["nmol"])
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_rdf_counts_match_oracle(prec):
+    case = lj_case((6, 6, 6))
+    s = case.system(prec)
+    got = s.rdf_counts(3.0, 60)
+    exp = O.rdf_counts(case.cfg.box, case.cfg.x, 3.0, 60)
+    assert got.sum() == exp.sum()
+    assert np.abs(got - exp).max() <= 2
+
+
+def test_batched_replicas_equal_standalone_runs():
+    sizes = [(3, 40, 101), (11, 20, 202), (5, 77, 303)]
+    cases_ = [kg_case(nc, nb, seed=sd, jitter=0.08) for nc, nb, sd in sizes]
+    reps = [dict(box=c.cfg.box, n=c.cfg.n, types=c.cfg.types, bonds=c.cfg.bonds, seed=1000 + k)
+            for k, c in enumerate(cases_)]
+    b = espp.System(replicas=reps, precision=FP32)
+    b.set_wca()
+    b.set_fene()
+    b.set_state(np.concatenate([c.cfg.x for c in cases_]), np.concatenate([c.v for c in cases_]),
+                np.concatenate([c.cfg.img for c in cases_]))
+    b.build_neighbors(WCA_RC, 0.4)
+    b.integrate(300, 0.005, 1.0, 1.0)
+    xb, vb, ib = b.get_state()
+    off = 0
+    for k, c in enumerate(cases_):
+        s = c.system(FP32, seed=1000 + k)
+        s.integrate(300, 0.005, 1.0, 1.0)
+        x, v, img = s.get_state()
+        n = c.cfg.n
+        assert np.array_equal(x, xb[off:off + n])
+        assert np.array_equal(v, vb[off:off + n])
+        assert np.array_equal(img, ib[off:off + n])
+        off += n
+    obs = b.observables()
+    assert len(obs) == 3 and all(o["n"] == c.cfg.n for o, c in zip(obs, cases_))
+
+
+def test_list_overflow_is_retried(monkeypatch):
+    monkeypatch.setenv("ESPP_FAULT_LIST_CAP", "4")
+    case = lj_case()
+    s = case.system(FP32)
+    assert s.list_capacity > 4
+    f = s.compute_forces()
+    fo, _ = O.forces(case.model, case.cfg.box, case.cfg.x, case.cfg.types, case.cfg.bonds)
+    assert rel_rms(f, fo) <= 1e-5
+    monkeypatch.setenv("ESPP_FAULT_LIST_CAP", "8")
+    s2 = case.system(FP64)
+    s2.integrate(40, 0.005, 1.0, 0.72)
+    x, v, img = s2.get_state()
+    st = case.oracle_state()
+    O.integrate(case.model, st, 40, 0.005, 1.0, 0.72, seed=42)
+    assert np.abs(_unwrapped(x, img, case.cfg.box) - _unwrapped(st.x, st.img, case.cfg.box)).max() < 1e-10
+
+
+def test_broken_bond_is_reported():
+    case = kg_case(4, 50)
+    c = case.cfg
+    c.x = c.x.copy()
+    c.x[5] = np.mod(c.x[4] + np.array([1.6, 0.0, 0.0]), c.box)
+    c.img = np.zeros_like(c.img)
+    s = case.system(FP32)
+    with pytest.raises(espp.EsppError) as e:
+        s.compute_forces()
+    assert e.value.code == espp.ESPP_ERR_BOND_BROKEN
+
+
+def test_box_too_small_is_reported():
+    s = espp.System(np.array([4.0, 4.0, 4.0]), 8, precision=FP32)
+    s.set_wca()
+    s.set_state(np.random.default_rng(0).random((8, 3)) * 4.0)
+    with pytest.raises(espp.EsppError) as e:
+        s.build_neighbors(WCA_RC, 0.4)
+    assert e.value.code == espp.ESPP_ERR_BOX_TOO_SMALL
+
+
+def test_cutoff_beyond_list_is_rejected():
+    case = lj_case()
+    s = case.system(FP32, build=False)
+    with pytest.raises(espp.EsppError) as e:
+        s.build_neighbors(2.0, 0.3)
+    assert e.value.code == espp.ESPP_ERR_ARG
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_single_free_particle(prec):
+    box = np.array([5.0, 6.0, 7.0])
+    s = espp.System(box, 1, precision=prec, seed=9)
+    s.set_wca()
+    s.set_state(np.array([[4.9, 0.05, 3.5]]), np.array([[3.0, -2.0, 1.0]]))
+    s.build_neighbors(WCA_RC, 0.4)
+    assert np.array_equal(s.compute_forces(), np.zeros((1, 3)))
+    s.integrate(100, 0.005, 1.0, 1.0)
+    x, v, img = s.get_state()
+    st = O.State(box, np.array([[4.9, 0.05, 3.5]]), np.array([[3.0, -2.0, 1.0]]))
+    O.integrate(O.Model(1, KG_PAIR), st, 100, 0.005, 1.0, 1.0, seed=9)
+    tol = 1e-12 if prec == FP64 else 1e-4
+    assert np.abs(_unwrapped(x, img, box) - _unwrapped(st.x, st.img, box)).max() < tol
+    assert np.abs(v - st.v).max() < tol
+
+
+def test_ragged_tiles_and_types():
+    # 257 particles: two full tiles plus a tail of one
+    c = I.random_positions(257, (9.0, 9.5, 10.0), seed=4)
+    c.types = (np.arange(257) % 3).astype(np.int32)
+    pair = {(0, 0): ("wca", 1.0, 1.0), (0, 1): ("lj", 0.5, 1.0, 2.0, True),
+            (1, 1): ("lj", 1.0, 0.8, 1.8, False), (0, 2): ("wca", 1.0, 0.9),
+            (1, 2): ("lj_capped", 1.0, 1.0, 2.0, True, 0.85), (2, 2): ("lj", 0.3, 1.2, 2.0, True)}
+    case = Case("ragged", c, pair, None, 2.0, 0.25, np.zeros((257, 3)))
+    for prec in (FP32, FP64):
+        s = case.system(prec)
+        f = s.compute_forces()
+        fo, _ = O.forces(case.model, c.box, c.x, c.types, c.bonds)
+        assert rel_rms(f, fo) <= (1e-5 if prec == FP32 else 1e-12)
+
+
+def test_capped_pushoff_runs_like_the_oracle():
+    case = capped_case(800, 10.0)
+    s = case.system(FP64, seed=4)
+    s.integrate(200, 1e-4, 1.0, 1.0)
+    x, v, img = s.get_state()
+    st = case.oracle_state()
+    O.integrate(case.model, st, 200, 1e-4, 1.0, 1.0, seed=4)
+    assert np.abs(_unwrapped(x, img, case.cfg.box) - _unwrapped(st.x, st.img, case.cfg.box)).max() < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# full sizes, sampled against the oracle one particle at a time
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_full_size_kg_1m_sampled_forces(prec):
+    c = I.kg_lattice(1000, 1000, density=0.85, seed=42, jitter=0.05)
+    case = Case("kg1m", c, KG_PAIR, KG_BOND, WCA_RC, 0.4)
+    s = case.system(prec)
+    f = s.compute_forces()
+    sel = np.random.default_rng(0).choice(c.n, 4000, replace=False)
+    fo = O.forces_subset(case.model, c.box, c.x, c.types, c.bonds, sel)
+    assert rel_rms(f[sel], fo) <= FORCE_TOL[prec]
+    # property at any size: Newton's third law
+    assert np.abs(f.sum(axis=0)).max() <= (1e-3 if prec == FP32 else 1e-8) * np.abs(f).sum() / c.n
+    s.close()
+
+
+def test_full_size_lj_4m_sampled_forces():
+    case = lj_case((128, 128, 64), seed=2, noise=0.05)
+    c = case.cfg
+    s = case.system(FP32)
+    f = s.compute_forces()
+    sel = np.random.default_rng(1).choice(c.n, 4000, replace=False)
+    fo = O.forces_subset(case.model, c.box, c.x, c.types, c.bonds, sel)
+    assert rel_rms(f[sel], fo) <= 1e-5
+    s.close()
