@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--profile-steps", type=int, default=1024)
+    ap.add_argument("--direct", action="store_true",
+                    help="launch every kernel directly instead of through CUDA graphs (for ncu)")
     ap.add_argument("--quick-start", action="store_true",
                     help="lattice start with a short equilibration (for profiler runs)")
     return ap.parse_args()
@@ -321,6 +323,8 @@ def run_ours(a):
 
     seed = 42 + rank
     s, cfg, start = make_melt(a, seed, espp.ESPP_FP32)
+    if a.direct:
+        s.set_graph_chunk(0)
     n = cfg.n
     assert a.warmup >= 3
     s.integrate(a.warmup, 0.005, 1.0, 1.0)
@@ -341,6 +345,8 @@ def run_ours(a):
     obs = s.observables()
 
     # ---- step-kernel duration by CUDA events inside the graphs -------------
+    if a.direct:
+        s.set_graph_chunk(64)
     s.set_kernel_timing(True)
     prof_steps = max(64, a.profile_steps // 64 * 64)
     for _ in range(prof_steps // 64):

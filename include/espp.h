@@ -65,6 +65,8 @@ extern "C" {
 #define ESPP_WCA 2        /* params: eps, sigma  (rc = 2^(1/6) sigma, shifted)  */
 #define ESPP_LJ_CAPPED 3  /* params: eps, sigma, rc, shift (0/1), caprad        */
 #define ESPP_FENE 4       /* params: K, R0  (applies to every bond)             */
+#define ESPP_TAB_PAIR 5   /* params: rc, n, u[n], F[n] on r_k = k rc / (n-1)    */
+#define ESPP_TAB_BOND 6   /* params: rmax, n, u[n], F[n] on r_k = k rmax / (n-1); every bond */
 
 #define ESPP_MAX_TYPES 8
 #define ESPP_MAX_BONDS_PER_PARTICLE 2
@@ -147,7 +149,10 @@ int espp_set_step(espp_h h, int64_t step);
  * ESPP_FENE sets the bond potential of every bond (types ignored).  params as
  * listed beside the kinds; shift = 1 lowers the energy by U(rc).  The cutoff
  * of every pair must not exceed the list cutoff of espp_build_neighbors.
- * Marks the stored force stale. */
+ * Tabulated kinds (paper "Functionality": tabulated potentials) take the
+ * energy u and the force F = -dU/dr on a uniform grid from r = 0 and
+ * interpolate both linearly in r; a tabulated bond longer than rmax is an
+ * error like a stretched FENE bond.  Marks the stored force stale. */
 int espp_set_interaction(espp_h h, int kind, int type_a, int type_b, const double* params,
                          int64_t n_params);
 
@@ -233,7 +238,15 @@ int espp_kernel_timing(espp_h h, double* out, int reset);
  * largest per-particle count (rebuilds first if the list is stale). */
 int espp_list_stats(espp_h h, int64_t* total_entries, int32_t* max_count);
 
-/* Steps captured per CUDA graph replay in espp_integrate (default 64). */
+/* Steps between Hilbert resorts of the particle storage inside
+ * espp_integrate (default 500; 0 = only on explicit builds).  A resort happens
+ * before every step whose number is a multiple of the interval, so results do
+ * not depend on how a run is split into calls. */
+int espp_set_resort_interval(espp_h h, int64_t steps);
+
+/* Steps captured per CUDA graph replay in espp_integrate (default 64).  0
+ * launches every kernel directly instead (no graphs; for profilers, which do
+ * not see kernels inside conditional graphs). */
 int espp_set_graph_chunk(espp_h h, int32_t steps);
 
 /* Tests: fill out[n*3] (device) with the Langevin noise of local ids [0,n) at

@@ -7,8 +7,10 @@ no code with the CUDA library.
 Interaction descriptions are plain dicts so that the test code states every
 parameter explicitly:
     pair = {(ta, tb): ("lj", eps, sigma, rc, shift) | ("wca", eps, sigma)
-                      | ("lj_capped", eps, sigma, rc, shift, caprad)}
-    bond = ("fene", K, R0) or None
+                      | ("lj_capped", eps, sigma, rc, shift, caprad)
+                      | ("table", slot, rc)}
+    bond = ("fene", K, R0) | ("table", slot) | None
+Tables are registered with set_table(slot, rmax, u, f).
 """
 import ctypes
 import os
@@ -48,6 +50,8 @@ def lib():
         L.orc_forces.argtypes = [ctypes.c_int64, _dp, _dp, _i32p, ctypes.c_int, _dp,
                                  ctypes.c_int64, _i64p, _dp, _dp, _dp]
         L.orc_forces.restype = ctypes.c_int
+        L.orc_set_table.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _dp]
+        L.orc_set_table.restype = ctypes.c_int
         L.orc_forces_subset.argtypes = [ctypes.c_int64, _dp, _dp, _i32p, ctypes.c_int, _dp,
                                         ctypes.c_int64, _i64p, _dp, ctypes.c_int64, _i64p, _dp]
         L.orc_forces_subset.restype = ctypes.c_int
@@ -99,6 +103,9 @@ def pair_table(pair: dict, ntypes: int) -> np.ndarray:
         elif kind == "lj_capped":
             _, eps, sig, rc, shift, cap = spec
             rec = [2, eps, sig, rc, 1.0 if shift else 0.0, cap]
+        elif kind == "table":
+            _, slot, rc = spec
+            rec = [3, slot, 0.0, rc, 0.0, 0.0]
         else:
             raise ValueError(kind)
         t[a, b, :6] = rec
@@ -113,7 +120,18 @@ def bond_table(bond) -> np.ndarray:
     if bond[0] == "fene":
         b[:3] = [1, bond[1], bond[2]]
         return b
+    if bond[0] == "table":
+        b[:2] = [2, bond[1]]
+        return b
     raise ValueError(bond[0])
+
+
+def set_table(slot, rmax, u, f):
+    """Register a table: u and F = -dU/dr at r_k = k rmax / (n - 1)."""
+    u = _f64(u)
+    f = _f64(f)
+    if lib().orc_set_table(slot, rmax, u.size, _p(u, _dp), _p(f, _dp)) != 0:
+        raise ValueError("bad table")
 
 
 class Model:

@@ -107,11 +107,51 @@ static void lj_raw(double eps, double sig, double r2, double* u, double* fr) {
     *fr = 24.0 * eps * (2.0 * s6 * s6 - s6) / r2;
 }
 
+/* Tabulated potentials (paper "Functionality": tabulated potentials).  A
+ * table holds u(r_k) and F(r_k) = -dU/dr at r_k = k * rmax / (n - 1),
+ * k = 0..n-1.  Reading: both are interpolated linearly in r between nodes. */
+#define ORC_MAX_TABLES 16
+static struct {
+    int n;
+    double rmax;
+    double* u;
+    double* f;
+} orc_tables[ORC_MAX_TABLES];
+
+int orc_set_table(int slot, double rmax, int n, const double* u, const double* f) {
+    if (slot < 0 || slot >= ORC_MAX_TABLES || n < 2 || !(rmax > 0)) return -1;
+    free(orc_tables[slot].u);
+    free(orc_tables[slot].f);
+    orc_tables[slot].n = n;
+    orc_tables[slot].rmax = rmax;
+    orc_tables[slot].u = (double*)malloc(sizeof(double) * (size_t)n);
+    orc_tables[slot].f = (double*)malloc(sizeof(double) * (size_t)n);
+    memcpy(orc_tables[slot].u, u, sizeof(double) * (size_t)n);
+    memcpy(orc_tables[slot].f, f, sizeof(double) * (size_t)n);
+    return 0;
+}
+
+/* Table `slot` at distance r (0 <= r < rmax): energy u and force F along r. */
+static void table_eval(int slot, double r, double* u, double* F) {
+    int n = orc_tables[slot].n;
+    double dr = orc_tables[slot].rmax / (n - 1);
+    double x = r / dr;
+    int k = (int)floor(x);
+    if (k > n - 2) k = n - 2;
+    if (k < 0) k = 0;
+    double t = x - k;
+    const double* uu = orc_tables[slot].u;
+    const double* ff = orc_tables[slot].f;
+    *u = uu[k] + t * (uu[k + 1] - uu[k]);
+    *F = ff[k] + t * (ff[k + 1] - ff[k]);
+}
+
 /* Pair record [kind, eps, sigma, rc, shift_flag, caprad].
  * kind 1: Lennard-Jones cut at rc (r < rc strictly).  With shift_flag the
  *   energy is lowered by U(rc) so that it is zero at the cutoff; the force is
  *   not changed (the example script's shift='auto').  WCA is this with
  *   rc = 2^(1/6) sigma.
+ * kind 3: tabulated, record [3, table slot, 0, rc]: u and F from the table.
  * kind 2: capped Lennard-Jones (the example's LennardJonesCapped).  Reading:
  *   for r < caprad the force keeps the direction of r_ij and the magnitude
  *   |F(caprad)| it has at caprad; the energy continues linearly,
@@ -127,6 +167,12 @@ void orc_pair_eval(const double* pp, double r2, double* u, double* fr) {
         double us, fs;
         lj_raw(eps, sig, rc * rc, &us, &fs);
         shift = us;
+    }
+    if (kind == 3) {
+        double r = sqrt(r2), F;
+        table_eval((int)pp[1], r, u, &F);
+        *fr = F / r;
+        return;
     }
     if (kind == 1) {
         lj_raw(eps, sig, r2, u, fr);
@@ -149,12 +195,21 @@ void orc_pair_eval(const double* pp, double r2, double* u, double* fr) {
 
 /* Bond record [kind, K, R0].  kind 1: FENE, U = -1/2 K R0^2 ln(1 - r^2/R0^2),
  * F_i = -K r_ij / (1 - r^2/R0^2).  Reading: r >= R0 is an error (no bond
- * breaking); returns 1 then. */
+ * breaking); returns 1 then.  kind 2: tabulated bond, record [2, table slot]:
+ * u and F from the table; r >= the table's rmax is an error like r >= R0. */
 int orc_bond_eval(const double* bp, double r2, double* u, double* fr) {
     *u = 0.0;
     *fr = 0.0;
     int kind = (int)bp[0];
     if (kind == 0) return 0;
+    if (kind == 2) {
+        int slot = (int)bp[1];
+        double r = sqrt(r2), F;
+        if (r >= orc_tables[slot].rmax) return 1;
+        table_eval(slot, r, u, &F);
+        *fr = r > 0.0 ? F / r : 0.0;
+        return 0;
+    }
     if (kind == 1) {
         double K = bp[1], R0 = bp[2];
         double q = r2 / (R0 * R0);

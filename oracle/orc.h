@@ -13,8 +13,10 @@
  *   L         : 3 box edges of the orthorhombic periodic box
  *   pair_params: ntypes*ntypes records of ORC_PAIR_STRIDE doubles,
  *                [kind, eps, sigma, rc, shift_flag, caprad, 0, 0]
- *                kind: 0 none, 1 Lennard-Jones, 2 capped Lennard-Jones
- *   bond_params: ORC_BOND_STRIDE doubles [kind, K, R0, 0]; kind 0 none, 1 FENE
+ *                kind: 0 none, 1 Lennard-Jones, 2 capped Lennard-Jones,
+ *                3 tabulated [3, slot, 0, rc]
+ *   bond_params: ORC_BOND_STRIDE doubles [kind, K, R0, 0]; kind 0 none, 1 FENE,
+ *                2 tabulated [2, slot]
  *   bonds     : nbonds*2 int64 particle ids
  *
  * Readings of points the paper leaves open are listed beside each function.
@@ -40,6 +42,9 @@ double orc_uniform_centered(uint32_t w);
 void orc_uniform_fill(const uint32_t* w, int64_t n, double* out);
 /* Langevin noise words for particle ids [0,n) at a given step: out n*3. */
 void orc_langevin_noise(uint64_t seed, int64_t step, int64_t n, double* out);
+
+/* Register a table (u, F = -dU/dr at r_k = k rmax/(n-1)) in slot [0, 16). */
+int orc_set_table(int slot, double rmax, int n, const double* u, const double* f);
 
 /* Pair and bond potentials at squared distance r2: energy u and scalar fr
  * such that the force on i is fr * (x_i - x_j). */

@@ -130,15 +130,34 @@ template <class T> struct PairRec {
     T cap;      // caprad
     T capF;     // |F(caprad)|
     T capU;     // U(caprad) - shift
+    int tab_off;  // tabulated kind: u at tab[tab_off + k], F at tab[tab_off + tab_n + k]
+    int tab_n;
+    T inv_dr;     // (tab_n - 1) / rc
 };
 
 template <class T> struct BondRec {
-    int kind;   // 0 none, ESPP_FENE
+    int kind;   // 0 none, ESPP_FENE, ESPP_TAB_BOND
     int pad;
     T K;
     T inv_R02;
     T halfKR02;  // K R0^2 / 2
+    int tab_off;
+    int tab_n;
+    T inv_dr;    // tabulated: (tab_n - 1) / rmax
+    T rmax;
 };
+
+// Linear interpolation in a table of u(r_k) and F(r_k) (k < n) at r = x / inv_dr.
+template <class T>
+__device__ __forceinline__ void table_lookup(const T* __restrict__ tb, int n, T inv_dr, T r, T& u, T& F) {
+    const T x = r * inv_dr;
+    int k = (int)x;
+    k = k > n - 2 ? n - 2 : k;
+    const T t = x - (T)k;
+    const T u0 = tb[k], u1 = tb[k + 1], f0 = tb[n + k], f1 = tb[n + k + 1];
+    u = u0 + t * (u1 - u0);
+    F = f0 + t * (f1 - f0);
+}
 
 // Control block in device memory (one per handle).
 struct Ctrl {
@@ -150,7 +169,7 @@ struct Ctrl {
     unsigned int need_cap;     // largest neighbour count seen by an overflowing build
     unsigned int n_rebuilds;   // rebuild passes executed (any replica)
     unsigned int max_count;    // largest neighbour count of the last build
-    unsigned int pad;
+    unsigned int need_capc;    // largest cell occupancy seen by an overflowing binning
 };
 
 enum : unsigned int {

@@ -21,8 +21,15 @@
 namespace espp {
 
 template <class T>
-__device__ __forceinline__ void pair_force(const PairRec<T>& pr, T r2, T& fr, T& u) {
+__device__ __forceinline__ void pair_force(const PairRec<T>& pr, const T* __restrict__ tab, T r2, T& fr, T& u) {
     // caller guarantees r2 < pr.rc2 and kind != 0
+    if (pr.kind == ESPP_TAB_PAIR) {
+        const T r = sqrt(r2);
+        T F;
+        table_lookup(tab + pr.tab_off, pr.tab_n, pr.inv_dr, r, u, F);
+        fr = F / r;
+        return;
+    }
     if (pr.kind == ESPP_LJ_CAPPED && r2 < pr.cap2) {
         const T r = sqrt(r2);
         fr = pr.capF / r;
@@ -34,6 +41,55 @@ __device__ __forceinline__ void pair_force(const PairRec<T>& pr, T r2, T& fr, T&
     const T s6 = s2 * s2 * s2;
     fr = pr.eps24 * s6 * (T(2) * s6 - T(1)) * inv_r2;
     u = pr.eps4 * s6 * (s6 - T(1)) - pr.shift;
+}
+
+// Sum of the pair forces on particle i over its Verlet list.  The list is
+// read in batches of int4 groups: all indices of a batch first, then all
+// neighbour positions, then the arithmetic, so that each thread keeps several
+// independent loads in flight.
+template <class T, bool ENERGY, bool MULTI>
+__device__ __forceinline__ void pair_loop(const DevSys<T>& s, const V4<T>* __restrict__ P, int i, int n,
+                                          const V4<T>& xi, int ti, const PairRec<T>* pr1,
+                                          T L0, T L1, T L2, T H0, T H1, T H2,
+                                          T& fx, T& fy, T& fz, T& pe, T& vir) {
+    constexpr int GB = sizeof(T) == 4 ? 2 : 1;  // int4 groups per batch
+    const int ng = (n + 3) >> 2;
+    const int4* __restrict__ nb = reinterpret_cast<const int4*>(s.nbr) + i;
+    const size_t stride = (size_t)s.stride;
+    for (int g0 = 0; g0 < ng; g0 += GB) {
+        int jj[4 * GB];
+#pragma unroll
+        for (int q = 0; q < GB; ++q) {
+            const int4 a = (g0 + q < ng) ? __ldg(nb + (g0 + q) * stride) : make_int4(-1, -1, -1, -1);
+            jj[4 * q + 0] = a.x;
+            jj[4 * q + 1] = a.y;
+            jj[4 * q + 2] = a.z;
+            jj[4 * q + 3] = a.w;
+        }
+        V4<T> xj[4 * GB];
+#pragma unroll
+        for (int q = 0; q < 4 * GB; ++q) xj[q] = jj[q] >= 0 ? ld4<T>(P + jj[q]) : xi;
+#pragma unroll
+        for (int q = 0; q < 4 * GB; ++q) {
+            if (jj[q] < 0) continue;
+            const PairRec<T>& pr = MULTI ? s.pair[ti * s.ntypes + bits_as_int(xj[q].w)] : *pr1;
+            const T dx = min_image(xi.x, xj[q].x, L0, H0);
+            const T dy = min_image(xi.y, xj[q].y, L1, H1);
+            const T dz = min_image(xi.z, xj[q].z, L2, H2);
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            if ((!MULTI || pr.kind != 0) && r2 < pr.rc2) {
+                T fr, u;
+                pair_force(pr, s.tab, r2, fr, u);
+                fx += fr * dx;
+                fy += fr * dy;
+                fz += fr * dz;
+                if (ENERGY) {
+                    pe += u;
+                    vir += fr * r2;
+                }
+            }
+        }
+    }
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -70,52 +126,12 @@ __global__ void __launch_bounds__(TILE) k_step(DevSys<T> s, int cur, double* __r
             const int ti = bits_as_int(xi.w);
             T fx = 0, fy = 0, fz = 0, pe = 0, pb = 0, vir = 0;
             const int n = s.nbr_cnt[i];
-            const int* __restrict__ nb = s.nbr + i;
-            const int stride = s.stride;
             if (s.ntypes == 1) {
                 const PairRec<T> pr = s.pair[0];
-                if (pr.kind != 0) {
-                    for (int k = 0; k < n; ++k) {
-                        const int j = __ldg(nb + (size_t)k * stride);
-                        const V4<T> xj = ld4<T>(P + j);
-                        const T dx = min_image(xi.x, xj.x, L0, H0);
-                        const T dy = min_image(xi.y, xj.y, L1, H1);
-                        const T dz = min_image(xi.z, xj.z, L2, H2);
-                        const T r2 = dx * dx + dy * dy + dz * dz;
-                        if (r2 < pr.rc2) {
-                            T fr, u;
-                            pair_force(pr, r2, fr, u);
-                            fx += fr * dx;
-                            fy += fr * dy;
-                            fz += fr * dz;
-                            if (ENERGY) {
-                                pe += u;
-                                vir += fr * r2;
-                            }
-                        }
-                    }
-                }
+                if (pr.kind != 0)
+                    pair_loop<T, ENERGY, false>(s, P, i, n, xi, ti, &pr, L0, L1, L2, H0, H1, H2, fx, fy, fz, pe, vir);
             } else {
-                for (int k = 0; k < n; ++k) {
-                    const int j = __ldg(nb + (size_t)k * stride);
-                    const V4<T> xj = ld4<T>(P + j);
-                    const PairRec<T> pr = s.pair[ti * s.ntypes + bits_as_int(xj.w)];
-                    const T dx = min_image(xi.x, xj.x, L0, H0);
-                    const T dy = min_image(xi.y, xj.y, L1, H1);
-                    const T dz = min_image(xi.z, xj.z, L2, H2);
-                    const T r2 = dx * dx + dy * dy + dz * dz;
-                    if (pr.kind != 0 && r2 < pr.rc2) {
-                        T fr, u;
-                        pair_force(pr, r2, fr, u);
-                        fx += fr * dx;
-                        fy += fr * dy;
-                        fz += fr * dz;
-                        if (ENERGY) {
-                            pe += u;
-                            vir += fr * r2;
-                        }
-                    }
-                }
+                pair_loop<T, ENERGY, true>(s, P, i, n, xi, ti, nullptr, L0, L1, L2, H0, H1, H2, fx, fy, fz, pe, vir);
             }
             // FENE bonds (paper "Functionality": bonded interactions)
             double blen = 0.0, bcnt = 0.0;
@@ -130,19 +146,33 @@ __global__ void __launch_bounds__(TILE) k_step(DevSys<T> s, int cur, double* __r
                     const T dy = min_image(xi.y, xp.y, L1, H1);
                     const T dz = min_image(xi.z, xp.z, L2, H2);
                     const T r2 = dx * dx + dy * dy + dz * dz;
-                    T one_m = T(1) - r2 * s.bond.inv_R02;
-                    if (!(one_m > T(0))) {
-                        atomicOr(&c->err, ERRBIT_BOND);
-                        c->abort = 1;
-                        __threadfence();
-                        one_m = T(1e-6);
+                    T fr, ub = T(0);
+                    if (s.bond.kind == ESPP_FENE) {
+                        T one_m = T(1) - r2 * s.bond.inv_R02;
+                        if (!(one_m > T(0))) {
+                            atomicOr(&c->err, ERRBIT_BOND);
+                            c->abort = 1;
+                            __threadfence();
+                            one_m = T(1e-6);
+                        }
+                        fr = -s.bond.K / one_m;
+                        if (ENERGY) ub = -s.bond.halfKR02 * log(one_m);
+                    } else {
+                        T r = sqrt(r2), F;
+                        if (!(r < s.bond.rmax)) {
+                            atomicOr(&c->err, ERRBIT_BOND);
+                            c->abort = 1;
+                            __threadfence();
+                            r = T(0);
+                        }
+                        table_lookup(s.tab + s.bond.tab_off, s.bond.tab_n, s.bond.inv_dr, r, ub, F);
+                        fr = r > T(0) ? F / r : T(0);
                     }
-                    const T fr = -s.bond.K / one_m;
                     fx += fr * dx;
                     fy += fr * dy;
                     fz += fr * dz;
                     if (ENERGY) {
-                        pb += -s.bond.halfKR02 * log(one_m);
+                        pb += ub;
                         vir += fr * r2;
                         blen += sqrt((double)r2);
                         bcnt += 1.0;

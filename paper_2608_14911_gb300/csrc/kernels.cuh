@@ -37,14 +37,18 @@ template <class T> struct DevSys {
     int* perm;          // new slot -> old slot (rebuild)
     int* cellh;         // per old slot: global cell rank
     int* in_cell;       // per old slot: arrival index in its cell
-    // Verlet list: nbr[k * stride + i], k < nbr_cnt[i] <= cap
+    // Verlet list in groups of four: entry k of particle i sits at
+    // nbr[4 * ((k / 4) * stride + i) + k % 4]; k < nbr_cnt[i] <= cap; the last
+    // group is padded with -1
     int* nbr;
     int* nbr_cnt;
     int cap;
     int stride;
     // cells (rank space, all replicas concatenated)
     int* cell_cnt;
-    int* cell_start;    // ncells + 1
+    int* cell_list;     // ncells * capc member slots, ascending within a cell
+    int capc;
+    int* cell_start;    // ncells + 1 (resort only)
     const int* cell_rank;  // per replica linear cell index (+cell_off) -> global rank
     const int* cell_rep;
     int ncells;
@@ -61,6 +65,7 @@ template <class T> struct DevSys {
     Ctrl* ctrl;
     const IntParams<T>* ip;
     const PairRec<T>* pair;
+    const T* tab;       // concatenated tables (tabulated pair and bond kinds)
     int ntypes;
     int N;
     BondRec<T> bond;
@@ -79,9 +84,9 @@ enum : int {
 
 // ---- launchers (defined in the .cu files) ----------------------------------
 template <class T> struct Launch {
-    // rebuild pipeline on the positions in buffer `cur` (other buffer is scratch)
-    static void rebuild(const DevSys<T>& s, int cur, bool permute_force, cudaStream_t st);
-    static void verlet_only(const DevSys<T>& s, int cur, cudaStream_t st);
+    // rebuild pipeline on the positions in buffer `cur` (other buffer is
+    // scratch); returns the number of kernels launched
+    static int rebuild(const DevSys<T>& s, int cur, bool resort, bool permute_force, cudaStream_t st);
     static void request_all(const DevSys<T>& s, cudaStream_t st);
     // step kernels
     static void step(const DevSys<T>& s, int mode, bool energy, int cur, double* f_out,

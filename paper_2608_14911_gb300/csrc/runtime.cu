@@ -60,12 +60,14 @@ struct SystemBase {
     virtual int kernel_timing(double* out, int reset) = 0;
     virtual int set_chunk(int steps) = 0;
     virtual int list_stats(int64_t* total, int32_t* maxc) = 0;
+    virtual int set_resort_interval(int64_t steps) = 0;
 };
 
 struct PairHost {
     int kind = ESPP_NONE;
     double eps = 0, sig = 0, rc = 0, cap = 0;
     bool shift = false;
+    std::vector<double> tab;  // tabulated: u[n] then F[n]
 };
 
 template <class T>
@@ -86,6 +88,9 @@ class System : public SystemBase {
     PairHost pair_h[MAX_TYPES][MAX_TYPES];
     int bond_kind = ESPP_NONE;
     double bond_K = 0, bond_R0 = 0;
+    std::vector<double> bond_tab;  // tabulated bond: u[n] then F[n] over [0, bond_R0]
+    void* tab_alloc = nullptr;
+    size_t tab_elems = 0;
     double mass_h[MAX_TYPES];
     double rc_list = -1, skin = 0;
     bool cells_ready = false, state_set = false, f_valid = false, rebuild_pending = false;
@@ -118,13 +123,16 @@ class System : public SystemBase {
     double t_step_ms = 0, t_rebuild_ms = 0;
     int64_t t_step_n = 0;
     int64_t launches = 0;
-    int64_t rebuild_base = 0;  // rebuilds counted before the last ctrl reset
     int chunk = 64;
+    int64_t resort_every = 500;  // steps between Hilbert resorts inside integrate (0 = never)
+    void* cell_list_alloc = nullptr;
 
     ~System() override {
         clear_graphs();
         for (void* p : cell_allocs) cudaFree(p);
         if (nbr_alloc) cudaFree(nbr_alloc);
+        if (cell_list_alloc) cudaFree(cell_list_alloc);
+        if (tab_alloc) cudaFree(tab_alloc);
         for (void* p : allocs) cudaFree(p);
     }
 
@@ -344,6 +352,8 @@ class System : public SystemBase {
     }
 
     cudaError_t upload_params() {
+        // concatenated tables in the handle's precision
+        std::vector<T> tab;
         std::vector<PairRec<T>> pr(MAX_TYPES * MAX_TYPES);
         for (int a = 0; a < ntypes; ++a)
             for (int b = 0; b < ntypes; ++b) {
@@ -352,6 +362,15 @@ class System : public SystemBase {
                 memset(&q, 0, sizeof(q));
                 q.kind = p.kind;
                 if (p.kind == ESPP_NONE) continue;
+                if (p.kind == ESPP_TAB_PAIR) {
+                    const int nt = (int)(p.tab.size() / 2);
+                    q.rc2 = (T)(p.rc * p.rc);
+                    q.tab_off = (int)tab.size();
+                    q.tab_n = nt;
+                    q.inv_dr = (T)((nt - 1) / p.rc);
+                    for (double v : p.tab) tab.push_back((T)v);
+                    continue;
+                }
                 const double s2 = p.sig * p.sig;
                 auto lj = [&](double r2, double& u, double& fr) {
                     const double x = s2 / r2, x6 = x * x * x;
@@ -378,6 +397,26 @@ class System : public SystemBase {
         d.bond.K = (T)bond_K;
         d.bond.inv_R02 = bond_kind ? (T)(1.0 / (bond_R0 * bond_R0)) : T(0);
         d.bond.halfKR02 = (T)(0.5 * bond_K * bond_R0 * bond_R0);
+        d.bond.rmax = (T)bond_R0;
+        if (bond_kind == ESPP_TAB_BOND) {
+            const int nt = (int)(bond_tab.size() / 2);
+            d.bond.tab_off = (int)tab.size();
+            d.bond.tab_n = nt;
+            d.bond.inv_dr = (T)((nt - 1) / bond_R0);
+            for (double v : bond_tab) tab.push_back((T)v);
+        }
+        if (tab.size() > tab_elems || !tab_alloc) {
+            if (tab_alloc) cudaFree(tab_alloc);
+            tab_alloc = nullptr;
+            tab_elems = std::max<size_t>(tab.size(), 1);
+            cudaError_t e = cudaMalloc(&tab_alloc, tab_elems * sizeof(T));
+            if (e != cudaSuccess) return e;
+        }
+        d.tab = reinterpret_cast<const T*>(tab_alloc);
+        if (!tab.empty()) {
+            cudaError_t e = cudaMemcpy(tab_alloc, tab.data(), tab.size() * sizeof(T), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return e;
+        }
         return cudaMemcpy(d_pair, pr.data(), pr.size() * sizeof(PairRec<T>), cudaMemcpyHostToDevice);
     }
 
@@ -483,11 +522,31 @@ class System : public SystemBase {
 
     // ----------------------------------------------------------- interactions
     int set_interaction(int kind, int ta, int tb, const double* p, int64_t np) override {
+        auto read_table = [&](double& rmax, std::vector<double>& out) -> int {
+            if (!p || np < 2) return fail(ESPP_ERR_ARG, "a table needs rmax, n, u[n], F[n]");
+            const double nd = p[1];
+            if (!(p[0] > 0) || !(nd >= 2) || nd != std::floor(nd) || np != 2 + 2 * (int64_t)nd)
+                return fail(ESPP_ERR_ARG, "a table needs rmax > 0, n >= 2 and exactly 2n values");
+            rmax = p[0];
+            out.assign(p + 2, p + 2 + 2 * (int64_t)nd);
+            for (double v : out)
+                if (!std::isfinite(v)) return fail(ESPP_ERR_ARG, "non-finite table entry");
+            return ESPP_OK;
+        };
         if (kind == ESPP_FENE) {
             if (!p || np < 2 || !(p[0] > 0) || !(p[1] > 0)) return fail(ESPP_ERR_ARG, "FENE needs K > 0, R0 > 0");
             bond_kind = ESPP_FENE;
             bond_K = p[0];
             bond_R0 = p[1];
+        } else if (kind == ESPP_TAB_BOND) {
+            double rmax;
+            std::vector<double> t;
+            int rc = read_table(rmax, t);
+            if (rc) return rc;
+            bond_kind = ESPP_TAB_BOND;
+            bond_K = 0;
+            bond_R0 = rmax;
+            bond_tab = t;
         } else {
             if (ta < 0 || tb < 0 || ta >= MAX_TYPES || tb >= MAX_TYPES)
                 return fail(ESPP_ERR_ARG, "type out of range");
@@ -504,6 +563,10 @@ class System : public SystemBase {
                 if (kind == ESPP_LJ_CAPPED) h.cap = p[4];
                 if (!(h.sig > 0) || !(h.rc > 0) || (kind == ESPP_LJ_CAPPED && !(h.cap > 0)))
                     return fail(ESPP_ERR_ARG, "sigma, rc and caprad must be positive");
+            } else if (kind == ESPP_TAB_PAIR) {
+                int rc = read_table(h.rc, h.tab);
+                if (rc) return rc;
+                h.kind = ESPP_TAB_PAIR;
             } else if (kind == ESPP_WCA) {
                 if (!p || np < 2) return fail(ESPP_ERR_ARG, "WCA needs eps, sigma");
                 h.kind = ESPP_LJ;
@@ -556,6 +619,33 @@ class System : public SystemBase {
             if (forced > 0) cap = forced;
         }
         return (cap + 3) & ~3;
+    }
+
+    int estimate_capc() const {
+        double best = 0;
+        for (int r = 0; r < R; ++r) {
+            const double nc = (double)cell_count(r, 0) * cell_count(r, 1) * cell_count(r, 2);
+            best = std::max(best, rep_n[r] / nc);
+        }
+        int capc = (int)std::ceil(best * 2.0 + 8);
+        if (const char* f = getenv("ESPP_FAULT_CELL_CAP")) {
+            const int forced = atoi(f);
+            if (forced > 0) capc = forced;
+        }
+        return (capc + 3) & ~3;  // rows of whole int4 groups
+    }
+
+    int alloc_cells(int capc) {
+        if (cell_list_alloc) cudaFree(cell_list_alloc);
+        cell_list_alloc = nullptr;
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, (size_t)capc * d.ncells * sizeof(int));
+        if (e != cudaSuccess) return fail(ESPP_ERR_CUDA, std::string("cell allocation: ") + cudaGetErrorString(e));
+        cell_list_alloc = p;
+        d.cell_list = reinterpret_cast<int*>(p);
+        d.capc = capc;
+        clear_graphs();
+        return ESPP_OK;
     }
 
     int alloc_list(int cap) {
@@ -630,47 +720,58 @@ class System : public SystemBase {
         if (rcode) return rcode;
         rcode = alloc_list(estimate_cap());
         if (rcode) return rcode;
+        rcode = alloc_cells(estimate_capc());
+        if (rcode) return rcode;
         if (!state_set) return ESPP_OK;
         Launch<T>::request_all(d, st);
         launches++;
         return rebuild_now(f_valid);
     }
 
-    // Direct (non-graph) rebuild with overflow retries.  After an overflow the
-    // list is reallocated and every replica is rebuilt (the old list of the
-    // replicas that did not overflow lived in the freed buffer).
+    // Direct (non-graph) rebuild with a resort, with capacity retries.  After
+    // an overflow the list or the cell array is reallocated and every replica
+    // is rebuilt (the old buffers of the other replicas are gone).
     int rebuild_now(bool permute_force) {
         if (!cells_ready) return fail(ESPP_ERR_STATE, "call espp_build_neighbors first");
-        for (int attempt = 0; attempt < 4; ++attempt) {
-            Launch<T>::rebuild(d, cur, permute_force, st);
-            launches += 9;
+        for (int attempt = 0; attempt < 6; ++attempt) {
+            launches += Launch<T>::rebuild(d, cur, true, permute_force, st);
             CK(cudaGetLastError());
             Ctrl c = read_ctrl();
             CK(cudaGetLastError());
-            if (!(c.err & ERRBIT_OVERFLOW)) {
+            if (!(c.err & (ERRBIT_OVERFLOW | ERRBIT_CELL))) {
                 rebuild_pending = false;
                 return ESPP_OK;
             }
-            int rcode = grow_list(c.need_cap);
+            int rcode = grow_capacity(c);
             if (rcode) return rcode;
-            Launch<T>::request_all(d, st);
-            launches++;
         }
-        return fail(ESPP_ERR_LIST_OVERFLOW, "Verlet list overflow persists after retries");
+        return fail(ESPP_ERR_LIST_OVERFLOW, "Verlet list or cell overflow persists after retries");
     }
 
-    int grow_list(unsigned int need) {
-        int cap = (int)std::ceil(need * 1.2 + 8);
-        cap = (cap + 3) & ~3;
-        int rcode = alloc_list(std::max(cap, d.cap + 4));
-        if (rcode) return rcode;
-        // clear the overflow state; the latched per-replica flags stay set
-        Ctrl c = read_ctrl();
-        c.err &= ~ERRBIT_OVERFLOW;
-        c.abort = 0;
-        c.need_cap = 0;
-        c.blocks_done = 0;
-        CK(cudaMemcpyAsync(d_ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+    // grow the list and/or the cell member array after an overflow, clear the
+    // overflow state and request a rebuild of every replica
+    int grow_capacity(const Ctrl& c) {
+        int rcode = ESPP_OK;
+        if (c.err & ERRBIT_OVERFLOW) {
+            int cap = (int)std::ceil(c.need_cap * 1.2 + 8);
+            cap = (cap + 3) & ~3;
+            rcode = alloc_list(std::max(cap, d.cap + 4));
+            if (rcode) return rcode;
+        }
+        if (c.err & ERRBIT_CELL) {
+            const int capc = std::max((int)std::ceil(c.need_capc * 1.3 + 4), d.capc + 4);
+            rcode = alloc_cells((capc + 3) & ~3);
+            if (rcode) return rcode;
+        }
+        Ctrl w = read_ctrl();
+        w.err &= ~(ERRBIT_OVERFLOW | ERRBIT_CELL);
+        w.abort = 0;
+        w.need_cap = 0;
+        w.need_capc = 0;
+        w.blocks_done = 0;
+        CK(cudaMemcpyAsync(d_ctrl, &w, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+        Launch<T>::request_all(d, st);
+        launches++;
         CK(cudaStreamSynchronize(st));
         return ESPP_OK;
     }
@@ -721,7 +822,8 @@ class System : public SystemBase {
         for (size_t g = 0; g < n; ++g) {
             const int s0 = slot_of_gid[g];
             int64_t* out = cols + row_ptr[g];
-            for (int k = 0; k < cnt[s0]; ++k) out[k] = gid_of_slot[nb[(size_t)k * d.stride + s0]];
+            for (int k = 0; k < cnt[s0]; ++k)
+                out[k] = gid_of_slot[nb[4 * ((size_t)(k >> 2) * d.stride + s0) + (k & 3)]];
             std::sort(out, out + cnt[s0]);
         }
         return ESPP_OK;
@@ -786,7 +888,7 @@ class System : public SystemBase {
             cudaGraph_t body = np.conditional.phGraph_out[0];
             CK(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
             CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-            Launch<T>::rebuild(d, p, false, bs);
+            Launch<T>::rebuild(d, p, false, false, bs);
             cudaGraph_t tmp;
             CK(cudaStreamEndCapture(bs, &tmp));
             const bool last = r == S - 1;
@@ -868,34 +970,60 @@ class System : public SystemBase {
         for (int attempt = 0; attempt < 8; ++attempt) {
             // positions of step done+1 live in buffer (1 - c_start) ^ ((done - step0) & 1)
             int p = (1 - c_start) ^ (int)((done - step0) & 1);
-            int64_t remaining = target - done;
+            int64_t next = done + 1;  // step the next graph computes first
             ChunkGraph* last_cg = nullptr;
-            while (remaining > 0) {
-                const int S = (int)std::min<int64_t>(remaining, chunk);
-                const bool fin = S == remaining;
+            int64_t host_rebuilds = 0;  // rebuilds launched here rather than by graph nodes
+            while (next <= target) {
+                // Hilbert resort (with a list rebuild) before every step that is
+                // a multiple of resort_every: a function of the step number only
+                if (resort_every > 0 && next % resort_every == 0) {
+                    Launch<T>::request_all(d, st);
+                    launches += 1 + Launch<T>::rebuild(d, p, true, false, st);
+                    host_rebuilds++;
+                }
+                int64_t S = std::min<int64_t>(target - next + 1, chunk > 0 ? chunk : 64);
+                if (resort_every > 0) {
+                    const int64_t to_resort = resort_every - (next % resort_every);
+                    S = std::min<int64_t>(S, to_resort);
+                }
+                const bool fin = next + S - 1 == target;
+                if (chunk == 0) {
+                    // direct launches (profilers cannot see kernels inside
+                    // conditional graphs): early-exit rebuild kernels + step
+                    host_rebuilds = -1;  // every kernel is counted as launched
+                    for (int64_t r = 0; r < S; ++r) {
+                        launches += Launch<T>::rebuild(d, p, false, false, st);
+                        const int mode = (fin && r == S - 1) ? MODE_FINAL : MODE_STEP;
+                        Launch<T>::step(d, mode, false, p, nullptr, 0ull, 0, st);
+                        launches++;
+                        if (mode == MODE_STEP) p ^= 1;
+                    }
+                    CK(cudaGetLastError());
+                    next += S;
+                    continue;
+                }
                 ChunkGraph* cg = nullptr;
-                rcode = make_chunk(S, p, fin, &cg);
+                rcode = make_chunk((int)S, p, fin, &cg);
                 if (rcode) return rcode;
                 CK(cudaGraphLaunch(cg->exec, st));
                 last_cg = cg;
                 launches += 1 + S;
-                p ^= (fin ? (S - 1) : S) & 1;
-                remaining -= S;
+                p ^= (int)((fin ? (S - 1) : S) & 1);
+                next += S;
             }
             Ctrl c = read_ctrl();
             CK(cudaGetLastError());
-            launches += 9 * (int64_t)(c.n_rebuilds - (unsigned)rb0);
+            if (host_rebuilds >= 0)
+                launches += 4 * ((int64_t)(c.n_rebuilds - (unsigned)rb0) - host_rebuilds);
             if (c.err & (ERRBIT_BOND | ERRBIT_NONFINITE | ERRBIT_TIMEOUT)) return status_from(c);
-            if (c.err & ERRBIT_OVERFLOW) {
+            if (c.err & (ERRBIT_OVERFLOW | ERRBIT_CELL)) {
                 // frozen after step c.step with the positions of the next step in
-                // buffer pm: grow the list, rebuild every replica there, go on
+                // buffer pm: grow, rebuild every replica there, go on
                 done = c.step;
                 const int pm = (1 - c_start) ^ (int)((done - step0) & 1);
-                rcode = grow_list(c.need_cap);
+                rcode = grow_capacity(c);
                 if (rcode) return rcode;
-                Launch<T>::request_all(d, st);
-                Launch<T>::rebuild(d, pm, false, st);
-                launches += 10;
+                launches += Launch<T>::rebuild(d, pm, true, false, st);
                 CK(cudaGetLastError());
                 continue;
             }
@@ -983,8 +1111,158 @@ class System : public SystemBase {
     }
 
     // ------------------------------------------------------------- checkpoint
-    int checkpoint_save(const char*) override { return fail(ESPP_ERR_STATE, "checkpoint not available"); }
-    int checkpoint_load(const char*) override { return fail(ESPP_ERR_STATE, "checkpoint not available"); }
+    // File layout: header, per replica (box, n, seed), then the storage-order
+    // arrays (positions, velocities, force, build positions, images, bond
+    // slots, slot of every id) and the pending rebuild requests.  Loading puts
+    // every array back in the same order and rebuilds the Verlet list from the
+    // build positions, so the list equals the one of the saved run.
+    struct CkptHeader {
+        char magic[8];
+        int32_t version, precision, R, f_valid;
+        int64_t N, step, n_rebuilds;
+        double rc_list, skin;
+    };
+
+    template <class P>
+    int dl(std::vector<P>& h, const P* dptr, size_t n) {
+        h.resize(n);
+        CK(cudaMemcpy(h.data(), dptr, n * sizeof(P), cudaMemcpyDeviceToHost));
+        return ESPP_OK;
+    }
+    template <class P>
+    int ul(P* dptr, const std::vector<P>& h) {
+        CK(cudaMemcpy(dptr, h.data(), h.size() * sizeof(P), cudaMemcpyHostToDevice));
+        return ESPP_OK;
+    }
+
+    int checkpoint_save(const char* path) override {
+        if (!path) return fail(ESPP_ERR_ARG, "path is required");
+        if (!state_set) return fail(ESPP_ERR_STATE, "no state set");
+        CK(cudaStreamSynchronize(st));
+        Ctrl c = read_ctrl();
+        if (c.abort) return status_from(c);
+        CkptHeader hd;
+        memset(&hd, 0, sizeof(hd));
+        memcpy(hd.magic, "ESPPCKP1", 8);
+        hd.version = 1;
+        hd.precision = sizeof(T) == 4 ? ESPP_FP32 : ESPP_FP64;
+        hd.R = R;
+        hd.f_valid = f_valid ? 1 : 0;
+        hd.N = N;
+        hd.step = c.step;
+        hd.n_rebuilds = c.n_rebuilds;
+        hd.rc_list = rc_list;
+        hd.skin = skin;
+        const size_t n = (size_t)N;
+        std::vector<V4<T>> pos, vel, frc, xb;
+        std::vector<int4> img;
+        std::vector<int2> bs;
+        std::vector<int> sid, req;
+        int rcode;
+        if ((rcode = dl(pos, d.pos[cur], n)) || (rcode = dl(vel, d.vel, n)) || (rcode = dl(frc, d.frc, n)) ||
+            (rcode = dl(xb, d.xb, n)) || (rcode = dl(img, d.img, n)) || (rcode = dl(bs, d.bond_slot, n)) ||
+            (rcode = dl(sid, d.slot_of_id, n)) || (rcode = dl(req, d.req, (size_t)R)))
+            return rcode;
+        FILE* fh = fopen(path, "wb");
+        if (!fh) return fail(ESPP_ERR_IO, std::string("cannot open ") + path);
+        bool ok = fwrite(&hd, sizeof(hd), 1, fh) == 1;
+        for (int r = 0; r < R && ok; ++r) {
+            const int64_t nr = rep_n[r];
+            ok = fwrite(&box[3 * r], sizeof(double), 3, fh) == 3 && fwrite(&nr, sizeof(nr), 1, fh) == 1 &&
+                 fwrite(&seeds[r], sizeof(seeds[r]), 1, fh) == 1;
+        }
+        auto wr = [&](const void* p, size_t bytes) { ok = ok && fwrite(p, 1, bytes, fh) == bytes; };
+        wr(pos.data(), n * sizeof(V4<T>));
+        wr(vel.data(), n * sizeof(V4<T>));
+        wr(frc.data(), n * sizeof(V4<T>));
+        wr(xb.data(), n * sizeof(V4<T>));
+        wr(img.data(), n * sizeof(int4));
+        wr(bs.data(), n * sizeof(int2));
+        wr(sid.data(), n * sizeof(int));
+        wr(req.data(), (size_t)R * sizeof(int));
+        ok = (fclose(fh) == 0) && ok;
+        return ok ? ESPP_OK : fail(ESPP_ERR_IO, std::string("write failed: ") + path);
+    }
+
+    int checkpoint_load(const char* path) override {
+        if (!path) return fail(ESPP_ERR_ARG, "path is required");
+        if (!cells_ready) return fail(ESPP_ERR_STATE, "call espp_build_neighbors before loading");
+        FILE* fh = fopen(path, "rb");
+        if (!fh) return fail(ESPP_ERR_IO, std::string("cannot open ") + path);
+        CkptHeader hd;
+        bool ok = fread(&hd, sizeof(hd), 1, fh) == 1 && memcmp(hd.magic, "ESPPCKP1", 8) == 0;
+        if (!ok) {
+            fclose(fh);
+            return fail(ESPP_ERR_IO, "not a checkpoint file");
+        }
+        if (hd.precision != (sizeof(T) == 4 ? ESPP_FP32 : ESPP_FP64) || hd.R != R || hd.N != N) {
+            fclose(fh);
+            return fail(ESPP_ERR_ARG, "checkpoint does not match this handle (precision, replicas, size)");
+        }
+        for (int r = 0; r < R && ok; ++r) {
+            double b[3];
+            int64_t nr;
+            unsigned long long sd;
+            ok = fread(b, sizeof(double), 3, fh) == 3 && fread(&nr, sizeof(nr), 1, fh) == 1 &&
+                 fread(&sd, sizeof(sd), 1, fh) == 1;
+            if (ok && (nr != rep_n[r] || b[0] != box[3 * r] || b[1] != box[3 * r + 1] || b[2] != box[3 * r + 2])) {
+                fclose(fh);
+                return fail(ESPP_ERR_ARG, "checkpoint replica geometry differs from this handle");
+            }
+            if (ok) seeds[r] = sd;
+        }
+        const size_t n = (size_t)N;
+        std::vector<V4<T>> pos(n), vel(n), frc(n), xb(n);
+        std::vector<int4> img(n);
+        std::vector<int2> bs(n);
+        std::vector<int> sid(n), req((size_t)R);
+        auto rd = [&](void* p, size_t bytes) { ok = ok && fread(p, 1, bytes, fh) == bytes; };
+        rd(pos.data(), n * sizeof(V4<T>));
+        rd(vel.data(), n * sizeof(V4<T>));
+        rd(frc.data(), n * sizeof(V4<T>));
+        rd(xb.data(), n * sizeof(V4<T>));
+        rd(img.data(), n * sizeof(int4));
+        rd(bs.data(), n * sizeof(int2));
+        rd(sid.data(), n * sizeof(int));
+        rd(req.data(), (size_t)R * sizeof(int));
+        fclose(fh);
+        if (!ok) return fail(ESPP_ERR_IO, "checkpoint file is truncated");
+        CK(cudaStreamSynchronize(st));
+        int rcode = upload_geometry();  // seeds
+        if (rcode) return rcode;
+        cur = 0;
+        if ((rcode = ul(d.pos[0], pos)) || (rcode = ul(d.pos[1], xb)) || (rcode = ul(d.vel, vel)) ||
+            (rcode = ul(d.frc, frc)) || (rcode = ul(d.xb, xb)) || (rcode = ul(d.img, img)) ||
+            (rcode = ul(d.bond_slot, bs)) || (rcode = ul(d.slot_of_id, sid)))
+            return rcode;
+        Ctrl c = read_ctrl();
+        c.step = hd.step;
+        c.err = 0;
+        c.abort = 0;
+        c.any_req = 0;
+        c.blocks_done = 0;
+        c.need_cap = 0;
+        c.need_capc = 0;
+        CK(cudaMemcpy(d_ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice));
+        // the list of the saved run was built from the build positions: rebuild
+        // it from them (buffer 1 holds a copy), without a resort
+        Launch<T>::request_all(d, st);
+        launches += 1 + Launch<T>::rebuild(d, 1, false, false, st);
+        CK(cudaGetLastError());
+        c = read_ctrl();
+        if (c.err & (ERRBIT_OVERFLOW | ERRBIT_CELL)) return fail(ESPP_ERR_LIST_OVERFLOW, "list capacity too small for the checkpoint");
+        // restore the pending requests and the rebuild counter of the saved run
+        CK(cudaMemcpy(d.req, req.data(), (size_t)R * sizeof(int), cudaMemcpyHostToDevice));
+        int any = 0;
+        for (int v : req) any |= v != 0;
+        c.any_req = any;
+        c.n_rebuilds = (unsigned int)hd.n_rebuilds;
+        CK(cudaMemcpy(d_ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice));
+        state_set = true;
+        f_valid = hd.f_valid != 0;
+        rebuild_pending = false;
+        return ESPP_OK;
+    }
 
     // ------------------------------------------------------------ diagnostics
     uint32_t error_word() override { return read_ctrl().err; }
@@ -1010,8 +1288,14 @@ class System : public SystemBase {
         return ESPP_OK;
     }
 
+    int set_resort_interval(int64_t steps) override {
+        if (steps < 0) return fail(ESPP_ERR_ARG, "resort interval must be >= 0");
+        resort_every = steps;
+        return ESPP_OK;
+    }
+
     int set_chunk(int steps) override {
-        if (steps < 1 || steps > 1024) return fail(ESPP_ERR_ARG, "chunk must be in [1, 1024]");
+        if (steps < 0 || steps > 1024) return fail(ESPP_ERR_ARG, "chunk must be in [0, 1024]");
         chunk = steps;
         clear_graphs();
         return ESPP_OK;
@@ -1152,6 +1436,9 @@ int espp_kernel_timing(espp_h h, double* out, int reset) {
 }
 int espp_list_stats(espp_h h, int64_t* total_entries, int32_t* max_count) {
     return guarded(h, [&](espp::SystemBase& s) { return s.list_stats(total_entries, max_count); });
+}
+int espp_set_resort_interval(espp_h h, int64_t steps) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.set_resort_interval(steps); });
 }
 int espp_set_graph_chunk(espp_h h, int32_t steps) {
     return guarded(h, [&](espp::SystemBase& s) { return s.set_chunk(steps); });

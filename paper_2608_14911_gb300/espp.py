@@ -35,6 +35,8 @@ ESPP_LJ = 1
 ESPP_WCA = 2
 ESPP_LJ_CAPPED = 3
 ESPP_FENE = 4
+ESPP_TAB_PAIR = 5
+ESPP_TAB_BOND = 6
 
 ERROR_NAMES = {
     ESPP_ERR_ARG: "ESPP_ERR_ARG", ESPP_ERR_CUDA: "ESPP_ERR_CUDA",
@@ -54,6 +56,7 @@ EXPORTS = (
     "espp_num_replicas", "espp_num_rebuilds", "espp_step", "espp_list_capacity",
     "espp_kernel_launches", "espp_langevin_noise", "espp_hilbert_ranks",
     "espp_set_kernel_timing", "espp_kernel_timing", "espp_set_graph_chunk", "espp_list_stats",
+    "espp_set_resort_interval",
 )
 
 
@@ -127,6 +130,7 @@ def lib(path: str = LIB_PATH):
         "espp_kernel_timing": ([vp, dp, ctypes.c_int], ctypes.c_int),
         "espp_set_graph_chunk": ([vp, i32], ctypes.c_int),
         "espp_list_stats": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i32)], ctypes.c_int),
+        "espp_set_resort_interval": ([vp, i64], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -261,6 +265,17 @@ class System:
     def set_fene(self, K=30.0, R0=1.5):
         self.set_interaction(ESPP_FENE, 0, 0, (K, R0))
 
+    def set_table_pair(self, rc, u, f, ta=0, tb=0):
+        """Tabulated pair potential: u and F = -dU/dr at r_k = k rc / (n-1)."""
+        u = np.asarray(u, dtype=np.float64)
+        f = np.asarray(f, dtype=np.float64)
+        self.set_interaction(ESPP_TAB_PAIR, ta, tb, [rc, float(u.size)] + u.tolist() + f.tolist())
+
+    def set_table_bond(self, rmax, u, f):
+        u = np.asarray(u, dtype=np.float64)
+        f = np.asarray(f, dtype=np.float64)
+        self.set_interaction(ESPP_TAB_BOND, 0, 0, [rmax, float(u.size)] + u.tolist() + f.tolist())
+
     def set_mass(self, t, m):
         self._c(lib().espp_set_mass(self._h, t, m))
 
@@ -317,6 +332,9 @@ class System:
         t, m = ctypes.c_int64(), ctypes.c_int32()
         self._c(lib().espp_list_stats(self._h, ctypes.byref(t), ctypes.byref(m)))
         return int(t.value), int(m.value)
+
+    def set_resort_interval(self, steps):
+        self._c(lib().espp_set_resort_interval(self._h, int(steps)))
 
     def set_graph_chunk(self, steps):
         self._c(lib().espp_set_graph_chunk(self._h, int(steps)))

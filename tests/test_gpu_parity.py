@@ -220,6 +220,44 @@ def test_list_overflow_is_retried(monkeypatch):
     assert np.abs(_unwrapped(x, img, case.cfg.box) - _unwrapped(st.x, st.img, case.cfg.box)).max() < 1e-10
 
 
+def test_cell_overflow_is_retried(monkeypatch):
+    monkeypatch.setenv("ESPP_FAULT_CELL_CAP", "4")
+    case = lj_case()
+    s = case.system(FP64)
+    s.integrate(30, 0.005, 1.0, 0.72)
+    x, v, img = s.get_state()
+    st = case.oracle_state()
+    O.integrate(case.model, st, 30, 0.005, 1.0, 0.72, seed=42)
+    assert np.abs(_unwrapped(x, img, case.cfg.box) - _unwrapped(st.x, st.img, case.cfg.box)).max() < 1e-10
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_direct_launches_equal_graphs(prec):
+    # the same kernels launched one by one (no CUDA graphs) give the same bits
+    case = kg_case()
+    a = case.system(prec, seed=8)
+    a.integrate(150, 0.005, 1.0, 1.0)
+    b = case.system(prec, seed=8)
+    b.set_graph_chunk(0)
+    b.integrate(150, 0.005, 1.0, 1.0)
+    xa, va, ia = a.get_state()
+    xb, vb, ib = b.get_state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(ia, ib)
+    assert a.n_rebuilds == b.n_rebuilds
+
+
+@pytest.mark.parametrize("every", [0, 7, 40])
+def test_resort_interval_does_not_change_fp64_physics(every):
+    case = lj_case()
+    s = case.system(FP64, seed=2)
+    s.set_resort_interval(every)
+    s.integrate(120, 0.005, 1.0, 0.72)
+    x, v, img = s.get_state()
+    st = case.oracle_state()
+    O.integrate(case.model, st, 120, 0.005, 1.0, 0.72, seed=2)
+    assert np.abs(_unwrapped(x, img, case.cfg.box) - _unwrapped(st.x, st.img, case.cfg.box)).max() < 1e-10
+
+
 def test_broken_bond_is_reported():
     case = kg_case(4, 50)
     c = case.cfg
@@ -289,6 +327,84 @@ def test_capped_pushoff_runs_like_the_oracle():
     st = case.oracle_state()
     O.integrate(case.model, st, 200, 1e-4, 1.0, 1.0, seed=4)
     assert np.abs(_unwrapped(x, img, case.cfg.box) - _unwrapped(st.x, st.img, case.cfg.box)).max() < 1e-9
+
+
+def _tab_case():
+    """KG chains with the WCA pair and the FENE bond given as tables (the
+    table values are inputs: the closed forms sampled on the grid)."""
+    c = I.kg_lattice(20, 50, seed=21, jitter=0.08)
+    n = 2048
+    r = np.linspace(0.0, WCA_RC, n)
+    rs = np.maximum(r, 0.6)
+    u = 4 * (rs ** -12 - rs ** -6) + 1.0
+    f = 24 * (2 * rs ** -13 - rs ** -7)
+    rb = np.linspace(0.0, 1.49, 1024)
+    ub = -0.5 * 30.0 * 2.25 * np.log(1 - rb ** 2 / 2.25)
+    fb = -30.0 * rb / (1 - rb ** 2 / 2.25)
+    O.set_table(3, WCA_RC, u, f)
+    O.set_table(4, 1.49, ub, fb)
+    model = O.Model(1, {(0, 0): ("table", 3, WCA_RC)}, ("table", 4))
+    return c, (WCA_RC, u, f), (1.49, ub, fb), model
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_tabulated_pair_and_bond_match_oracle(prec):
+    c, tp, tb, model = _tab_case()
+    v = I.maxwell_velocities(c.n, 1.0, seed=3)
+    s = espp.System(c.box, c.n, c.types, c.bonds, precision=prec, seed=6)
+    s.set_table_pair(*tp)
+    s.set_table_bond(*tb)
+    s.set_state(c.x, v, c.img)
+    s.build_neighbors(WCA_RC, 0.4)
+    f = s.compute_forces()
+    fo, en = O.forces(model, c.box, c.x, c.types, c.bonds)
+    assert rel_rms(f, fo) <= FORCE_TOL[prec]
+    o = s.observables()
+    oo = O.observables(model, O.State(c.box, c.x, v, c.img, c.types, c.bonds))
+    tol = 1e-12 if prec == FP64 else 2e-6
+    for k in ("pe_pair", "pe_bond", "virial"):
+        assert abs(o[k] - oo[k]) <= tol * max(1.0, abs(oo[k])), k
+    if prec == FP64:
+        s.integrate(60, 0.005, 1.0, 1.0)
+        x1, v1, i1 = s.get_state()
+        st = O.State(c.box, c.x, v, c.img, c.types, c.bonds)
+        O.integrate(model, st, 60, 0.005, 1.0, 1.0, seed=6)
+        assert np.abs(_unwrapped(x1, i1, c.box) - _unwrapped(st.x, st.img, c.box)).max() < 1e-10
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_checkpoint_resume_is_bit_exact(prec, tmp_path):
+    case = kg_case()
+    a = case.system(prec, seed=17)
+    a.integrate(137, 0.005, 1.0, 1.0)
+    path = str(tmp_path / "state.ckpt")
+    a.checkpoint_save(path)
+    a.integrate(300, 0.005, 1.0, 1.0)
+    xa, va, ia = a.get_state()
+    c = case.cfg
+    b = espp.System(c.box, c.n, c.types, c.bonds, precision=prec, seed=999)
+    b.set_wca()
+    b.set_fene()
+    b.build_neighbors(WCA_RC, 0.4)
+    b.checkpoint_load(path)
+    assert b.step == 137
+    b.integrate(300, 0.005, 1.0, 1.0)
+    xb, vb, ib = b.get_state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(ia, ib)
+
+
+def test_checkpoint_rejects_other_handles(tmp_path):
+    case = kg_case()
+    a = case.system(FP32)
+    path = str(tmp_path / "s.ckpt")
+    a.checkpoint_save(path)
+    other = lj_case()
+    b = other.system(FP32)
+    with pytest.raises(espp.EsppError):
+        b.checkpoint_load(path)
+    c64 = case.system(FP64)
+    with pytest.raises(espp.EsppError):
+        c64.checkpoint_load(path)
 
 
 # ---------------------------------------------------------------------------

@@ -397,3 +397,48 @@ def test_rdf_counts_small():
             d.append(np.linalg.norm(dd))
     expect = np.histogram([r for r in d if r < 2.0], bins=20, range=(0, 2.0))[0]
     assert np.array_equal(c, expect)
+
+
+# --------------------------------------------------------------------------
+# Tabulated potentials
+# --------------------------------------------------------------------------
+def test_linear_table_is_interpolated_exactly():
+    # u and F linear in r: linear interpolation reproduces them everywhere
+    rc, n = 3.0, 31
+    r = np.linspace(0.0, rc, n)
+    O.set_table(0, rc, 2.0 - 0.5 * r, 3.0 + 0.25 * r)
+    m = O.Model(1, {(0, 0): ("table", 0, rc)})
+    for rr in (0.013, 0.77, 1.2345, 2.999):
+        u, fr = O.pair_eval(m, 0, 0, rr * rr)
+        assert abs(u - (2.0 - 0.5 * rr)) < 1e-13
+        assert abs(fr * rr - (3.0 + 0.25 * rr)) < 1e-12
+    assert O.pair_eval(m, 0, 0, rc * rc) == (0.0, 0.0)
+
+
+def test_lj_table_within_interpolation_bound():
+    # a table sampled from 12-6 LJ: |F_table - F| <= h^2/8 max|F''| between nodes
+    rc, n = 2.5, 4096
+    r = np.linspace(0.0, rc, n)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        u = np.where(r > 0.5, 4 * (r ** -12 - r ** -6), 0.0)
+        f = np.where(r > 0.5, 24 * (2 * r ** -13 - r ** -7), 0.0)
+    O.set_table(1, rc, u, f)
+    tab = O.Model(1, {(0, 0): ("table", 1, rc)})
+    lj = O.Model(1, {(0, 0): ("lj", 1.0, 1.0, rc, False)})
+    h = rc / (n - 1)
+    for rr in np.linspace(0.9, 2.49, 37):
+        _, fr_t = O.pair_eval(tab, 0, 0, rr * rr)
+        _, fr_a = O.pair_eval(lj, 0, 0, rr * rr)
+        # F'' of LJ is bounded by 24*(2*13*14 r^-15) near r = 0.9
+        bound = h * h / 8 * 24 * 2 * 13 * 14 * 0.9 ** -15
+        assert abs(fr_t * rr - fr_a * rr) <= bound
+
+
+def test_table_bond_breaks_beyond_range():
+    rmax, n = 1.5, 301
+    r = np.linspace(0.0, rmax, n)
+    O.set_table(2, rmax, 15.0 * r * r, -30.0 * r)
+    m = O.Model(1, {}, ("table", 2))
+    u, fr, st = O.bond_eval(m, 0.49)
+    assert st == 0 and abs(fr + 30.0) < 1e-12 and abs(u - 15.0 * 0.49) < 1e-3
+    assert O.bond_eval(m, 1.5 ** 2)[2] == 1
