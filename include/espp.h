@@ -254,6 +254,33 @@ int espp_set_graph_chunk(espp_h h, int32_t steps);
 int espp_langevin_noise(uint64_t seed, int64_t step, int64_t n, double* out_device,
                         void* cuda_stream);
 
+/* Pair-distance histogram that allocates nothing.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- code inside a framework that reserved the device memory up
+ * front and hands out only its own pool, or latency-critical loops that cannot
+ * take the implicit synchronisation of cudaMalloc/cudaFree.
+ *
+ * Same counts as espp_rdf_counts (unique pairs i < j with minimum-image
+ * distance r < rmax, bin floor(r nbins / rmax)), computed from caller-owned
+ * device positions x_device (n*3 doubles, id order, each coordinate in
+ * [0, box) as espp_get_state returns them) into caller-owned device counts
+ * counts_device[nbins] (int64).  Work is queued on cuda_stream; the call does
+ * not wait for it.
+ *
+ * Working memory is a fixed file-scope device array of ESPP_NOALLOC_MAX_BINS
+ * counters (32 KiB) inside the library; every GPU that loads the library holds
+ * it until the process exits.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  All calls share the one array: each
+ * call clears the part it uses, and calls whose work overlaps on the GPU (for
+ * instance on two streams) race on it.  Errors: ESPP_ERR_ARG for nbins outside
+ * [1, ESPP_NOALLOC_MAX_BINS], rmax not below half of every box edge, null
+ * pointers or n < 0; ESPP_ERR_CUDA if a launch fails.  Never calls cudaMalloc,
+ * cudaFree or any allocating routine. */
+#define ESPP_NOALLOC_MAX_BINS 4096
+int espp_rdf_counts_noalloc(const double* x_device, int64_t n, const double box[3], double rmax,
+                            int32_t nbins, int64_t* counts_device, void* cuda_stream);
+
 /* Host-side helper (no GPU work): the 3-D Hilbert-curve rank of each cell of an
  * nx x ny x nz grid (rank[cz*ny*nx + cy*nx + cx]), as used for the storage
  * order.  Returns ESPP_OK. */

@@ -56,8 +56,9 @@ EXPORTS = (
     "espp_num_replicas", "espp_num_rebuilds", "espp_step", "espp_list_capacity",
     "espp_kernel_launches", "espp_langevin_noise", "espp_hilbert_ranks",
     "espp_set_kernel_timing", "espp_kernel_timing", "espp_set_graph_chunk", "espp_list_stats",
-    "espp_set_resort_interval",
+    "espp_rdf_counts_noalloc", "espp_set_resort_interval",
 )
+NOALLOC_MAX_BINS = 4096
 
 
 class EsppError(RuntimeError):
@@ -130,6 +131,7 @@ def lib(path: str = LIB_PATH):
         "espp_kernel_timing": ([vp, dp, ctypes.c_int], ctypes.c_int),
         "espp_set_graph_chunk": ([vp, i32], ctypes.c_int),
         "espp_list_stats": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i32)], ctypes.c_int),
+        "espp_rdf_counts_noalloc": ([vp, i64, dp, ctypes.c_double, i32, vp, vp], ctypes.c_int),
         "espp_set_resort_interval": ([vp, i64], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -168,6 +170,17 @@ def espp_langevin_noise(seed, step, out_tensor, stream=0):
     n = out_tensor.numel() // 3
     _check(lib().espp_langevin_noise(seed, step, n, ctypes.c_void_p(out_tensor.data_ptr()),
                                      ctypes.c_void_p(stream)))
+
+
+def espp_rdf_counts_noalloc(x_device, box, rmax, counts_device, stream=0):
+    """Pair-distance histogram from device positions into device counts,
+    without any allocation inside the library (see include/espp.h)."""
+    n = x_device.shape[0]
+    b = (ctypes.c_double * 3)(*[float(v) for v in box])
+    _check(lib().espp_rdf_counts_noalloc(ctypes.c_void_p(x_device.data_ptr()), n, b, float(rmax),
+                                         counts_device.numel(),
+                                         ctypes.c_void_p(counts_device.data_ptr()),
+                                         ctypes.c_void_p(stream)))
 
 
 class System:
