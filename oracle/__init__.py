@@ -52,6 +52,10 @@ def lib():
         L.orc_forces.restype = ctypes.c_int
         L.orc_set_table.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _dp]
         L.orc_set_table.restype = ctypes.c_int
+        L.orc_set_mlp.argtypes = [_dp, ctypes.c_int64, ctypes.c_double]
+        L.orc_set_mlp.restype = ctypes.c_int
+        L.orc_mlp_pair.argtypes = [ctypes.c_double, _dp, _dp, _dp, _dp]
+        L.orc_set_exclude_bonded.argtypes = [ctypes.c_int]
         L.orc_forces_subset.argtypes = [ctypes.c_int64, _dp, _dp, _i32p, ctypes.c_int, _dp,
                                         ctypes.c_int64, _i64p, _dp, ctypes.c_int64, _i64p, _dp]
         L.orc_forces_subset.restype = ctypes.c_int
@@ -106,6 +110,9 @@ def pair_table(pair: dict, ntypes: int) -> np.ndarray:
         elif kind == "table":
             _, slot, rc = spec
             rec = [3, slot, 0.0, rc, 0.0, 0.0]
+        elif kind == "mlp":
+            _, rc = spec
+            rec = [4, 0.0, 0.0, rc, 0.0, 0.0]
         else:
             raise ValueError(kind)
         t[a, b, :6] = rec
@@ -124,6 +131,33 @@ def bond_table(bond) -> np.ndarray:
         b[:2] = [2, bond[1]]
         return b
     raise ValueError(bond[0])
+
+
+MLP_NPARAMS = 64 * 32 + 64 + 64 * 64 + 64 + 64 + 1
+
+
+def set_mlp(params, rc):
+    """Register the learned pair potential (parameters in double; the caller
+    upcasts BF16 weights)."""
+    p = _f64(params)
+    if lib().orc_set_mlp(_p(p, _dp), p.size, rc) != 0:
+        raise ValueError("bad MLP parameters")
+
+
+def mlp_pair(r, want_grad=False):
+    """u(r), du/dr and (optionally) their gradients w.r.t. the parameters."""
+    u, du = ctypes.c_double(), ctypes.c_double()
+    g = np.zeros(MLP_NPARAMS) if want_grad else None
+    gu = np.zeros(MLP_NPARAMS) if want_grad else None
+    lib().orc_mlp_pair(r, ctypes.byref(u), ctypes.byref(du),
+                       _p(g, _dp) if want_grad else None, _p(gu, _dp) if want_grad else None)
+    if want_grad:
+        return u.value, du.value, g, gu
+    return u.value, du.value
+
+
+def set_exclude_bonded(on):
+    lib().orc_set_exclude_bonded(1 if on else 0)
 
 
 def set_table(slot, rmax, u, f):

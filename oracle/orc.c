@@ -146,12 +146,166 @@ static void table_eval(int slot, double r, double* u, double* F) {
     *F = ff[k] + t * (ff[k + 1] - ff[k]);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Learned radial-basis MLP pair potential (spec learned CG model).     */
+/* Reading (the paper prints no model; the shape is 32 Gaussian bases on     */
+/* [0, rc], two hidden layers of 64 SiLU units, one output):                 */
+/*   phi_k(r) = exp(-(r - mu_k)^2 / (2 w^2)) * fc(r),  mu_k = rc k / 31,    */
+/*   w = rc / 31,  fc(r) = (cos(pi r / rc) + 1) / 2 (smooth cutoff);        */
+/*   h1 = silu(W1 phi + b1), h2 = silu(W2 h1 + b2), u = w3 . h2 + b3.        */
+/* The weights are given in double (the BF16 values upcast).  du/dr is the   */
+/* exact derivative, propagated forward through the same layers.             */
+/* ------------------------------------------------------------------------ */
+#define ORC_MLP_NB 32
+#define ORC_MLP_H 64
+#define ORC_MLP_NPAR (ORC_MLP_H * ORC_MLP_NB + ORC_MLP_H + ORC_MLP_H * ORC_MLP_H + ORC_MLP_H + ORC_MLP_H + 1)
+static double orc_mlp_par[ORC_MLP_NPAR];
+static double orc_mlp_rc = 0.0;
+
+int orc_set_mlp(const double* par, int64_t npar, double rc) {
+    if (npar != ORC_MLP_NPAR || !(rc > 0)) return -1;
+    memcpy(orc_mlp_par, par, sizeof(double) * ORC_MLP_NPAR);
+    orc_mlp_rc = rc;
+    return 0;
+}
+
+static double sigmoid(double z) { return 1.0 / (1.0 + exp(-z)); }
+
+/* Energy of one pair at distance r and its derivative du/dr (r < rc).  If
+ * grad is not NULL it receives d(du/dr)/d(parameters) (ORC_MLP_NPAR values,
+ * same layout as the parameters), and if ugrad is not NULL it receives
+ * du/d(parameters). */
+void orc_mlp_pair(double r, double* u_out, double* dudr_out, double* grad, double* ugrad) {
+    const double rc = orc_mlp_rc;
+    const double* W1 = orc_mlp_par;
+    const double* b1 = W1 + ORC_MLP_H * ORC_MLP_NB;
+    const double* W2 = b1 + ORC_MLP_H;
+    const double* b2 = W2 + ORC_MLP_H * ORC_MLP_H;
+    const double* w3 = b2 + ORC_MLP_H;
+    const double b3 = w3[ORC_MLP_H];
+    double phi[ORC_MLP_NB], dphi[ORC_MLP_NB];
+    const double w = rc / (ORC_MLP_NB - 1);
+    const double fc = 0.5 * (cos(M_PI * r / rc) + 1.0);
+    const double dfc = -0.5 * (M_PI / rc) * sin(M_PI * r / rc);
+    for (int k = 0; k < ORC_MLP_NB; ++k) {
+        const double mu = rc * k / (ORC_MLP_NB - 1);
+        const double g = exp(-(r - mu) * (r - mu) / (2.0 * w * w));
+        phi[k] = g * fc;
+        dphi[k] = g * (-(r - mu) / (w * w)) * fc + g * dfc;
+    }
+    double z1[ORC_MLP_H], dz1[ORC_MLP_H], h1[ORC_MLP_H], dh1[ORC_MLP_H];
+    for (int a = 0; a < ORC_MLP_H; ++a) {
+        double s = b1[a], ds = 0.0;
+        for (int k = 0; k < ORC_MLP_NB; ++k) {
+            s += W1[a * ORC_MLP_NB + k] * phi[k];
+            ds += W1[a * ORC_MLP_NB + k] * dphi[k];
+        }
+        z1[a] = s;
+        dz1[a] = ds;
+        const double sg = sigmoid(s);
+        h1[a] = s * sg;
+        dh1[a] = sg * (1.0 + s * (1.0 - sg)) * ds;
+    }
+    double z2[ORC_MLP_H], dz2[ORC_MLP_H], h2[ORC_MLP_H], dh2[ORC_MLP_H];
+    double u = b3, du = 0.0;
+    for (int a = 0; a < ORC_MLP_H; ++a) {
+        double s = b2[a], ds = 0.0;
+        for (int k = 0; k < ORC_MLP_H; ++k) {
+            s += W2[a * ORC_MLP_H + k] * h1[k];
+            ds += W2[a * ORC_MLP_H + k] * dh1[k];
+        }
+        z2[a] = s;
+        dz2[a] = ds;
+        const double sg = sigmoid(s);
+        h2[a] = s * sg;
+        dh2[a] = sg * (1.0 + s * (1.0 - sg)) * ds;
+        u += w3[a] * h2[a];
+        du += w3[a] * dh2[a];
+    }
+    *u_out = u;
+    *dudr_out = du;
+    if (!grad && !ugrad) return;
+    /* Reverse pass through the pair (primal, tangent).  With s = sigmoid:
+     * silu'(z) = s (1 + z (1 - s)),  silu''(z) = s (1 - s) (2 + z (1 - 2 s)).
+     * Adjoints: for the tangent output du = w3 . dh2 and the primal output
+     * u = w3 . h2 + b3. */
+    double* gW1 = grad;
+    double* gb1 = grad ? grad + ORC_MLP_H * ORC_MLP_NB : NULL;
+    double* gW2 = grad ? gb1 + ORC_MLP_H : NULL;
+    double* gb2 = grad ? gW2 + ORC_MLP_H * ORC_MLP_H : NULL;
+    double* gw3 = grad ? gb2 + ORC_MLP_H : NULL;
+    if (grad) {
+        /* d(du)/d(w3_a) = dh2_a; layer-2 adjoints of the tangent path */
+        double az2[ORC_MLP_H], adz2[ORC_MLP_H];
+        for (int a = 0; a < ORC_MLP_H; ++a) {
+            const double sg = sigmoid(z2[a]);
+            const double s1 = sg * (1.0 + z2[a] * (1.0 - sg));
+            const double s2 = sg * (1.0 - sg) * (2.0 + z2[a] * (1.0 - 2.0 * sg));
+            gw3[a] = dh2[a];
+            adz2[a] = w3[a] * s1;             /* d du / d dz2 */
+            az2[a] = w3[a] * s2 * dz2[a];     /* d du / d z2 */
+        }
+        gw3[ORC_MLP_H] = 0.0; /* b3 */
+        double ah1[ORC_MLP_H], adh1[ORC_MLP_H];
+        for (int k = 0; k < ORC_MLP_H; ++k) {
+            ah1[k] = 0.0;
+            adh1[k] = 0.0;
+        }
+        for (int a = 0; a < ORC_MLP_H; ++a) {
+            gb2[a] = az2[a];
+            for (int k = 0; k < ORC_MLP_H; ++k) {
+                gW2[a * ORC_MLP_H + k] = az2[a] * h1[k] + adz2[a] * dh1[k];
+                ah1[k] += W2[a * ORC_MLP_H + k] * az2[a];
+                adh1[k] += W2[a * ORC_MLP_H + k] * adz2[a];
+            }
+        }
+        for (int a = 0; a < ORC_MLP_H; ++a) {
+            const double sg = sigmoid(z1[a]);
+            const double s1 = sg * (1.0 + z1[a] * (1.0 - sg));
+            const double s2 = sg * (1.0 - sg) * (2.0 + z1[a] * (1.0 - 2.0 * sg));
+            const double adz1 = adh1[a] * s1;
+            const double az1 = ah1[a] * s1 + adh1[a] * s2 * dz1[a];
+            gb1[a] = az1;
+            for (int k = 0; k < ORC_MLP_NB; ++k) gW1[a * ORC_MLP_NB + k] = az1 * phi[k] + adz1 * dphi[k];
+        }
+    }
+    if (ugrad) {
+        double* uW1 = ugrad;
+        double* ub1 = ugrad + ORC_MLP_H * ORC_MLP_NB;
+        double* uW2 = ub1 + ORC_MLP_H;
+        double* ub2 = uW2 + ORC_MLP_H * ORC_MLP_H;
+        double* uw3 = ub2 + ORC_MLP_H;
+        double az2[ORC_MLP_H], ah1[ORC_MLP_H];
+        for (int a = 0; a < ORC_MLP_H; ++a) {
+            const double sg = sigmoid(z2[a]);
+            uw3[a] = h2[a];
+            az2[a] = w3[a] * sg * (1.0 + z2[a] * (1.0 - sg));
+            ah1[a] = 0.0;
+        }
+        uw3[ORC_MLP_H] = 1.0;
+        for (int a = 0; a < ORC_MLP_H; ++a) {
+            ub2[a] = az2[a];
+            for (int k = 0; k < ORC_MLP_H; ++k) {
+                uW2[a * ORC_MLP_H + k] = az2[a] * h1[k];
+                ah1[k] += W2[a * ORC_MLP_H + k] * az2[a];
+            }
+        }
+        for (int a = 0; a < ORC_MLP_H; ++a) {
+            const double sg = sigmoid(z1[a]);
+            const double az1 = ah1[a] * sg * (1.0 + z1[a] * (1.0 - sg));
+            ub1[a] = az1;
+            for (int k = 0; k < ORC_MLP_NB; ++k) uW1[a * ORC_MLP_NB + k] = az1 * phi[k];
+        }
+    }
+}
+
 /* Pair record [kind, eps, sigma, rc, shift_flag, caprad].
  * kind 1: Lennard-Jones cut at rc (r < rc strictly).  With shift_flag the
  *   energy is lowered by U(rc) so that it is zero at the cutoff; the force is
  *   not changed (the example script's shift='auto').  WCA is this with
  *   rc = 2^(1/6) sigma.
  * kind 3: tabulated, record [3, table slot, 0, rc]: u and F from the table.
+ * kind 4: the learned MLP pair potential (orc_set_mlp), record [4, 0, 0, rc].
  * kind 2: capped Lennard-Jones (the example's LennardJonesCapped).  Reading:
  *   for r < caprad the force keeps the direction of r_ij and the magnitude
  *   |F(caprad)| it has at caprad; the energy continues linearly,
@@ -172,6 +326,12 @@ void orc_pair_eval(const double* pp, double r2, double* u, double* fr) {
         double r = sqrt(r2), F;
         table_eval((int)pp[1], r, u, &F);
         *fr = F / r;
+        return;
+    }
+    if (kind == 4) {
+        double r = sqrt(r2), du;
+        orc_mlp_pair(r, u, &du, NULL, NULL);
+        *fr = -du / r;
         return;
     }
     if (kind == 1) {
@@ -407,6 +567,18 @@ static void adj_free(adj_t* a) {
     free(a->nbr);
 }
 
+/* Reading (learned CG model): 1-2 bonded pairs can be excluded from the pair
+ * interactions, so that the bonded (tabulated) potential alone acts between
+ * them.  Off by default (Kremer-Grest keeps WCA between bonded beads). */
+static int orc_exclude_bonded = 0;
+void orc_set_exclude_bonded(int on) { orc_exclude_bonded = on ? 1 : 0; }
+
+static int bonded_to(const adj_t* a, int64_t i, int64_t j) {
+    for (int64_t k = a->off[i]; k < a->off[i + 1]; ++k)
+        if (a->nbr[k] == j) return 1;
+    return 0;
+}
+
 /* Definition: F_i = sum over j != i with r_ij < rc(t_i, t_j) of the pair force
  * plus the sum over bonds (i, p) of the bond force.  There are no exclusions:
  * bonded beads also interact through the pair potential (Kremer-Grest).
@@ -443,6 +615,7 @@ int orc_forces(int64_t n, const double* L, const double* x, const int32_t* type,
                 int64_t nc = cells_candidates(&cl, n, i, buf);
                 for (int64_t k = 0; k < nc; ++k) {
                     int64_t j = buf[k];
+                    if (orc_exclude_bonded && bonded_to(&adj, i, j)) continue;
                     double d[3];
                     min_image_vec(x + 3 * i, x + 3 * j, L, d);
                     double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
@@ -519,6 +692,7 @@ int orc_forces_subset(int64_t n, const double* L, const double* x, const int32_t
                 int64_t nc = cells_candidates(&cl, n, i, buf);
                 for (int64_t k = 0; k < nc; ++k) {
                     int64_t j = buf[k];
+                    if (orc_exclude_bonded && bonded_to(&adj, i, j)) continue;
                     double d[3];
                     min_image_vec(x + 3 * i, x + 3 * j, L, d);
                     double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];

@@ -14,7 +14,7 @@
  *   pair_params: ntypes*ntypes records of ORC_PAIR_STRIDE doubles,
  *                [kind, eps, sigma, rc, shift_flag, caprad, 0, 0]
  *                kind: 0 none, 1 Lennard-Jones, 2 capped Lennard-Jones,
- *                3 tabulated [3, slot, 0, rc]
+ *                3 tabulated [3, slot, 0, rc], 4 learned MLP [4, 0, 0, rc]
  *   bond_params: ORC_BOND_STRIDE doubles [kind, K, R0, 0]; kind 0 none, 1 FENE,
  *                2 tabulated [2, slot]
  *   bonds     : nbonds*2 int64 particle ids
@@ -45,6 +45,16 @@ void orc_langevin_noise(uint64_t seed, int64_t step, int64_t n, double* out);
 
 /* Register a table (u, F = -dU/dr at r_k = k rmax/(n-1)) in slot [0, 16). */
 int orc_set_table(int slot, double rmax, int n, const double* u, const double* f);
+
+/* Learned MLP pair potential: parameters in the order W1 (64x32, row = output
+ * unit), b1 (64), W2 (64x64), b2 (64), w3 (64), b3 (1); cutoff rc. */
+#define ORC_MLP_NPARAMS (64 * 32 + 64 + 64 * 64 + 64 + 64 + 1)
+int orc_set_mlp(const double* par, int64_t npar, double rc);
+/* u(r), du/dr, and optionally d(du/dr)/dparams and du/dparams (NPARAMS each). */
+void orc_mlp_pair(double r, double* u, double* dudr, double* grad_dudr, double* grad_u);
+
+/* Exclude 1-2 bonded pairs from the pair interactions (default off). */
+void orc_set_exclude_bonded(int on);
 
 /* Pair and bond potentials at squared distance r2: energy u and scalar fr
  * such that the force on i is fr * (x_i - x_j). */

@@ -6,16 +6,18 @@
 //
 // Every rebuild (inside the step graphs, when a replica asked for it):
 //   prep      latch the per-replica requests, clear those replicas' cell counts
-//   bin       cell of every particle (Hilbert rank space); atomic slot in a
-//             fixed-capacity member array per cell
-//   cellsort  members of each cell in ascending storage slot, so the list
-//             does not depend on the order of the atomics
-//   verlet    27-cell search, full list (both directions) as groups of four
+//   bin       cell of every particle; the particle's position and storage slot
+//             go to an atomic slot of its cell's fixed-capacity entry array
+//   cellsort  entries of each cell in ascending storage slot, so the list does
+//             not depend on the order of the atomics
+//   verlet    27-cell search from the cell entries (contiguous, no further
+//             indirection), full list (both directions) as groups of four
 //             indices, nbr4[g * stride + i]; records the build positions
 // A resort (launched between step graphs every `resort_every` steps, and on
 // every explicit build) additionally runs, between cellsort and verlet:
-//   scan x3   exclusive scan of the cell counts -> first slot of each cell
-//   scatter   new slot of every member; the member lists switch to new slots
+//   scan x3   exclusive scan of the cell counts in Hilbert-rank order
+//   scatter   new slot of every entry (its cell's first slot + its rank in the
+//             cell); the entries switch to the new slots
 //   gather    permuted copies of positions, velocities, forces, images
 //   copyback  copies back and maps bond partners to their new slots
 // Replicas whose request flag is clear skip every step after `prep`.
@@ -32,6 +34,14 @@ __device__ __forceinline__ int cell_coord(T x, T cpl, int nc) {
     int c = (int)(x * cpl);
     c = c < 0 ? 0 : c;
     return c >= nc ? nc - 1 : c;
+}
+
+template <class T>
+__device__ __forceinline__ int cell_of(const RepGeom<T>& g, const V4<T>& p) {
+    const int cx = cell_coord(p.x, g.cells_per_len[0], g.nc[0]);
+    const int cy = cell_coord(p.y, g.cells_per_len[1], g.nc[1]);
+    const int cz = cell_coord(p.z, g.cells_per_len[2], g.nc[2]);
+    return g.cell_off + (cz * g.nc[1] + cy) * g.nc[0] + cx;
 }
 
 template <class T>
@@ -59,16 +69,13 @@ __global__ void __launch_bounds__(TILE) k_bin(DevSys<T> s, int cur) {
     for (int t = blockIdx.x; t < s.ntiles; t += gridDim.x) {
         const Tile tl = s.tiles[t];
         if (!s.now[tl.rep] || (int)threadIdx.x >= tl.count) continue;
-        const RepGeom<T>& g = s.reps[tl.rep];
         const int i = tl.start + threadIdx.x;
-        const V4<T> p = ld4<T>(P + i);
-        const int cx = cell_coord(p.x, g.cells_per_len[0], g.nc[0]);
-        const int cy = cell_coord(p.y, g.cells_per_len[1], g.nc[1]);
-        const int cz = cell_coord(p.z, g.cells_per_len[2], g.nc[2]);
-        const int h = s.cell_rank[g.cell_off + (cz * g.nc[1] + cy) * g.nc[0] + cx];
+        V4<T> p = ld4<T>(P + i);
+        const int h = cell_of(s.reps[tl.rep], p);
         const int slot = atomicAdd(&s.cell_cnt[h], 1);
         if (slot < s.capc) {
-            s.cell_list[(size_t)h * s.capc + slot] = i;
+            p.w = int_bits_as(T(0), i);
+            s.cell_xyz[(size_t)h * s.capc + slot] = p;
         } else {
             atomicMax(&s.ctrl->need_capc, (unsigned int)(slot + 1));
             atomicOr(&s.ctrl->err, ERRBIT_CELL);
@@ -77,18 +84,19 @@ __global__ void __launch_bounds__(TILE) k_bin(DevSys<T> s, int cur) {
     }
 }
 
-// Members of each cell in ascending storage slot (a handful per cell).
+// Entries of each cell in ascending storage slot (a handful per cell).
 template <class T>
 __global__ void __launch_bounds__(256) k_cellsort(DevSys<T> s) {
     if (s.ctrl->abort) return;
     for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < s.ncells; h += gridDim.x * blockDim.x) {
         if (!s.now[s.cell_rep[h]]) continue;
-        int* p = s.cell_list + (size_t)h * s.capc;
+        V4<T>* p = s.cell_xyz + (size_t)h * s.capc;
         const int e = min(s.cell_cnt[h], s.capc);
         for (int k = 1; k < e; ++k) {
-            const int key = p[k];
+            const V4<T> key = p[k];
+            const int kk = bits_as_int(key.w);
             int q = k - 1;
-            while (q >= 0 && p[q] > key) {
+            while (q >= 0 && bits_as_int(p[q].w) > kk) {
                 p[q + 1] = p[q];
                 --q;
             }
@@ -135,7 +143,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(DevSys<T> s) {
     int sum = 0;
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k)
-        if (base + k < s.ncells) sum += s.cell_cnt[base + k];
+        if (base + k < s.ncells) sum += s.cell_cnt[s.cell_by_rank[base + k]];
     int excl;
     const int total = block_excl_scan(sum, &excl);
     if (threadIdx.x == 0) s.scan_part[blockIdx.x] = total;
@@ -163,7 +171,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(DevSys<T> s) {
     int sum = 0;
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k) {
-        v[k] = base + k < s.ncells ? s.cell_cnt[base + k] : 0;
+        v[k] = base + k < s.ncells ? s.cell_cnt[s.cell_by_rank[base + k]] : 0;
         sum += v[k];
     }
     int excl;
@@ -177,17 +185,18 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(DevSys<T> s) {
 }
 
 // ---- resort ------------------------------------------------------------------
-// Member k of cell h moves to slot start[h] + k; the member list follows.
+// Entry k of the cell of rank h moves to slot start[h] + k; the entry follows.
 template <class T>
 __global__ void __launch_bounds__(256) k_resort_scatter(DevSys<T> s) {
     if (s.ctrl->abort) return;
     for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < s.ncells; h += gridDim.x * blockDim.x) {
-        if (!s.now[s.cell_rep[h]]) continue;
-        int* p = s.cell_list + (size_t)h * s.capc;
-        const int b = s.cell_start[h], e = min(s.cell_cnt[h], s.capc);
+        const int c = s.cell_by_rank[h];
+        if (!s.now[s.cell_rep[c]]) continue;
+        V4<T>* p = s.cell_xyz + (size_t)c * s.capc;
+        const int b = s.cell_start[h], e = min(s.cell_cnt[c], s.capc);
         for (int k = 0; k < e; ++k) {
-            s.perm[b + k] = p[k];
-            p[k] = b + k;
+            s.perm[b + k] = bits_as_int(p[k].w);
+            p[k].w = int_bits_as(T(0), b + k);
         }
     }
 }
@@ -233,11 +242,10 @@ __global__ void __launch_bounds__(TILE) k_copyback(DevSys<T> s, int cur, int per
 
 // ---- Verlet list ----------------------------------------------------------------
 // One thread per particle.  The 27 neighbour cells are visited as three planes
-// of nine: the nine cell ranks and counts of a plane are loaded together
-// (independent loads in flight), then each cell's members are read four at a
-// time (one int4 of the member array, then their positions).  Hits are packed
-// into int4 groups in registers and written as whole 16-byte groups, which
-// makes the stores of a warp contiguous.
+// of nine; the nine counts of a plane are loaded together, then each cell's
+// entries (position and slot, contiguous) are streamed with no further
+// indirection.  Hits are packed into int4 groups in registers and stored as
+// whole 16-byte groups, so the stores of a warp are contiguous.
 template <class T>
 __global__ void __launch_bounds__(TILE) k_verlet(DevSys<T> s, int cur) {
     if (s.ctrl->abort) return;
@@ -257,53 +265,50 @@ __global__ void __launch_bounds__(TILE) k_verlet(DevSys<T> s, int cur) {
             const int cx = cell_coord(xi.x, g.cells_per_len[0], nc0);
             const int cy = cell_coord(xi.y, g.cells_per_len[1], nc1);
             const int cz = cell_coord(xi.z, g.cells_per_len[2], nc2);
+            const int xm = cx == 0 ? nc0 - 1 : cx - 1, xp = cx == nc0 - 1 ? 0 : cx + 1;
+            const int ym = cy == 0 ? nc1 - 1 : cy - 1, yp = cy == nc1 - 1 ? 0 : cy + 1;
             const T L0 = g.L[0], L1 = g.L[1], L2 = g.L[2];
             const T H0 = g.halfL[0], H1 = g.halfL[1], H2 = g.halfL[2];
             const T rl2 = s.rlist2;
             const int cap = s.cap, capc = s.capc;
             const size_t stride = (size_t)s.stride;
             int4* __restrict__ out4 = reinterpret_cast<int4*>(s.nbr) + i;
-            const int* __restrict__ crank = s.cell_rank + g.cell_off;
-            int xs[3] = {cx == 0 ? nc0 - 1 : cx - 1, cx, cx == nc0 - 1 ? 0 : cx + 1};
-            int ys[3] = {cy == 0 ? nc1 - 1 : cy - 1, cy, cy == nc1 - 1 ? 0 : cy + 1};
-            int zs[3] = {cz == 0 ? nc2 - 1 : cz - 1, cz, cz == nc2 - 1 ? 0 : cz + 1};
             int cnt = 0;
             int4 grp = make_int4(-1, -1, -1, -1);
 #pragma unroll 1
             for (int pz = 0; pz < 3; ++pz) {
+                int az = cz + pz - 1;
+                az += az < 0 ? nc2 : 0;
+                az -= az >= nc2 ? nc2 : 0;
                 int hh[9], cn[9];
 #pragma unroll
-                for (int q = 0; q < 9; ++q)
-                    hh[q] = __ldg(crank + (zs[pz] * nc1 + ys[q / 3]) * nc0 + xs[q % 3]);
+                for (int q = 0; q < 9; ++q) {
+                    const int ay = q / 3 == 0 ? ym : (q / 3 == 1 ? cy : yp);
+                    const int ax = q % 3 == 0 ? xm : (q % 3 == 1 ? cx : xp);
+                    hh[q] = g.cell_off + (az * nc1 + ay) * nc0 + ax;
+                }
 #pragma unroll
                 for (int q = 0; q < 9; ++q) cn[q] = min(__ldg(s.cell_cnt + hh[q]), capc);
 #pragma unroll
                 for (int q = 0; q < 9; ++q) {
-                    const int4* __restrict__ row = reinterpret_cast<const int4*>(s.cell_list + (size_t)hh[q] * capc);
-                    for (int k4 = 0; k4 < cn[q]; k4 += 4) {
-                        const int4 m = __ldg(row + (k4 >> 2));
-                        const int mm[4] = {m.x, m.y, m.z, m.w};
-                        V4<T> pj[4];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) pj[u] = (k4 + u < cn[q]) ? ld4<T>(P + mm[u]) : xi;
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            if (k4 + u >= cn[q] || mm[u] == i) continue;
-                            const T ddx = min_image(xi.x, pj[u].x, L0, H0);
-                            const T ddy = min_image(xi.y, pj[u].y, L1, H1);
-                            const T ddz = min_image(xi.z, pj[u].z, L2, H2);
-                            const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                            if (r2 < rl2) {
-                                const int l = cnt & 3;
-                                if (l == 0) grp.x = mm[u];
-                                else if (l == 1) grp.y = mm[u];
-                                else if (l == 2) grp.z = mm[u];
-                                else grp.w = mm[u];
-                                ++cnt;
-                                if ((cnt & 3) == 0) {
-                                    if (cnt <= cap) out4[(size_t)((cnt >> 2) - 1) * stride] = grp;
-                                    grp = make_int4(-1, -1, -1, -1);
-                                }
+                    const V4<T>* __restrict__ ent = s.cell_xyz + (size_t)hh[q] * capc;
+                    for (int k = 0; k < cn[q]; ++k) {
+                        const V4<T> xj = ld4<T>(ent + k);
+                        const int j = bits_as_int(xj.w);
+                        if (j == i) continue;
+                        const T ddx = min_image(xi.x, xj.x, L0, H0);
+                        const T ddy = min_image(xi.y, xj.y, L1, H1);
+                        const T ddz = min_image(xi.z, xj.z, L2, H2);
+                        if (ddx * ddx + ddy * ddy + ddz * ddz < rl2) {
+                            const int l = cnt & 3;
+                            if (l == 0) grp.x = j;
+                            else if (l == 1) grp.y = j;
+                            else if (l == 2) grp.z = j;
+                            else grp.w = j;
+                            ++cnt;
+                            if ((cnt & 3) == 0) {
+                                if (cnt <= cap) out4[(size_t)((cnt >> 2) - 1) * stride] = grp;
+                                grp = make_int4(-1, -1, -1, -1);
                             }
                         }
                     }

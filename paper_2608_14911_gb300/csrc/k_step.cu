@@ -47,7 +47,7 @@ __device__ __forceinline__ void pair_force(const PairRec<T>& pr, const T* __rest
 // read in batches of int4 groups: all indices of a batch first, then all
 // neighbour positions, then the arithmetic, so that each thread keeps several
 // independent loads in flight.
-template <class T, bool ENERGY, bool MULTI>
+template <class T, bool ENERGY, bool MULTI, bool FAST>
 __device__ __forceinline__ void pair_loop(const DevSys<T>& s, const V4<T>* __restrict__ P, int i, int n,
                                           const V4<T>& xi, int ti, const PairRec<T>* pr1,
                                           T L0, T L1, T L2, T H0, T H1, T H2,
@@ -56,15 +56,19 @@ __device__ __forceinline__ void pair_loop(const DevSys<T>& s, const V4<T>* __res
     const int ng = (n + 3) >> 2;
     const int4* __restrict__ nb = reinterpret_cast<const int4*>(s.nbr) + i;
     const size_t stride = (size_t)s.stride;
-    for (int g0 = 0; g0 < ng; g0 += GB) {
+    for (int g0 = 0; g0 < ng || g0 == 0; g0 += GB) {
         int jj[4 * GB];
 #pragma unroll
         for (int q = 0; q < GB; ++q) {
-            const int4 a = (g0 + q < ng) ? __ldg(nb + (g0 + q) * stride) : make_int4(-1, -1, -1, -1);
-            jj[4 * q + 0] = a.x;
-            jj[4 * q + 1] = a.y;
-            jj[4 * q + 2] = a.z;
-            jj[4 * q + 3] = a.w;
+            // the first batch is read without waiting for the count (the list
+            // holds at least GB groups); entries past the count are masked
+            const bool want = g0 == 0 || g0 + q < ng;
+            const int4 a = want ? __ldg(nb + (g0 + q) * stride) : make_int4(-1, -1, -1, -1);
+            const int base = 4 * (g0 + q);
+            jj[4 * q + 0] = base + 0 < n ? a.x : -1;
+            jj[4 * q + 1] = base + 1 < n ? a.y : -1;
+            jj[4 * q + 2] = base + 2 < n ? a.z : -1;
+            jj[4 * q + 3] = base + 3 < n ? a.w : -1;
         }
         V4<T> xj[4 * GB];
 #pragma unroll
@@ -72,6 +76,27 @@ __device__ __forceinline__ void pair_loop(const DevSys<T>& s, const V4<T>* __res
 #pragma unroll
         for (int q = 0; q < 4 * GB; ++q) {
             if (jj[q] < 0) continue;
+            if (FAST) {
+                // one type, plain Lennard-Jones: only rc^2, sigma^2, 24 eps live
+                const T dx = min_image(xi.x, xj[q].x, L0, H0);
+                const T dy = min_image(xi.y, xj[q].y, L1, H1);
+                const T dz = min_image(xi.z, xj[q].z, L2, H2);
+                const T r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 < pr1->rc2) {
+                    const T inv_r2 = T(1) / r2;
+                    const T s2 = pr1->sig2 * inv_r2;
+                    const T s6 = s2 * s2 * s2;
+                    const T fr = pr1->eps24 * s6 * (T(2) * s6 - T(1)) * inv_r2;
+                    fx += fr * dx;
+                    fy += fr * dy;
+                    fz += fr * dz;
+                    if (ENERGY) {
+                        pe += pr1->eps4 * s6 * (s6 - T(1)) - pr1->shift;
+                        vir += fr * r2;
+                    }
+                }
+                continue;
+            }
             const PairRec<T>& pr = MULTI ? s.pair[ti * s.ntypes + bits_as_int(xj[q].w)] : *pr1;
             const T dx = min_image(xi.x, xj[q].x, L0, H0);
             const T dy = min_image(xi.y, xj[q].y, L1, H1);
@@ -98,8 +123,8 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-template <class T, int MODE, bool ENERGY>
-__global__ void __launch_bounds__(TILE) k_step(DevSys<T> s, int cur, double* __restrict__ f_out,
+template <class T, int MODE, bool ENERGY, bool FAST>
+__global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 6 : 4) k_step(DevSys<T> s, int cur, double* __restrict__ f_out,
                                                unsigned long long next_cond) {
     Ctrl* c = s.ctrl;
     if (MODE != MODE_FORCES && c->abort) return;
@@ -122,26 +147,44 @@ __global__ void __launch_bounds__(TILE) k_step(DevSys<T> s, int cur, double* __r
             const int i = tl.start + threadIdx.x;
             const T L0 = g.L[0], L1 = g.L[1], L2 = g.L[2];
             const T H0 = g.halfL[0], H1 = g.halfL[1], H2 = g.halfL[2];
+            // independent loads first: own position, list count, bond slots,
+            // velocity and build position, then the bond partners' positions
             const V4<T> xi = ld4<T>(P + i);
             const int ti = bits_as_int(xi.w);
             T fx = 0, fy = 0, fz = 0, pe = 0, pb = 0, vir = 0;
             const int n = s.nbr_cnt[i];
-            if (s.ntypes == 1) {
+            const bool bonded = s.bond.kind != 0;
+            const int2 b = bonded ? s.bond_slot[i] : make_int2(-1, -1);
+            V4<T> v = s.vel[i];
+            V4<T> xbi;
+            if (MODE == MODE_STEP) xbi = s.xb[i];
+            const V4<T> xp0 = b.x >= 0 ? ld4<T>(P + b.x) : xi;
+            const V4<T> xp1 = b.y >= 0 ? ld4<T>(P + b.y) : xi;
+            if (FAST) {
+                PairRec<T> pr;
+                pr.rc2 = s.pair[0].rc2;
+                pr.sig2 = s.pair[0].sig2;
+                pr.eps24 = s.pair[0].eps24;
+                if (ENERGY) {
+                    pr.eps4 = s.pair[0].eps4;
+                    pr.shift = s.pair[0].shift;
+                }
+                pair_loop<T, ENERGY, false, true>(s, P, i, n, xi, ti, &pr, L0, L1, L2, H0, H1, H2, fx, fy, fz, pe, vir);
+            } else if (s.ntypes == 1) {
                 const PairRec<T> pr = s.pair[0];
                 if (pr.kind != 0)
-                    pair_loop<T, ENERGY, false>(s, P, i, n, xi, ti, &pr, L0, L1, L2, H0, H1, H2, fx, fy, fz, pe, vir);
+                    pair_loop<T, ENERGY, false, false>(s, P, i, n, xi, ti, &pr, L0, L1, L2, H0, H1, H2, fx, fy, fz, pe, vir);
             } else {
-                pair_loop<T, ENERGY, true>(s, P, i, n, xi, ti, nullptr, L0, L1, L2, H0, H1, H2, fx, fy, fz, pe, vir);
+                pair_loop<T, ENERGY, true, false>(s, P, i, n, xi, ti, nullptr, L0, L1, L2, H0, H1, H2, fx, fy, fz, pe, vir);
             }
-            // FENE bonds (paper "Functionality": bonded interactions)
+            // bonds (paper "Functionality": bonded interactions; FENE or tabulated)
             double blen = 0.0, bcnt = 0.0;
-            if (s.bond.kind != 0) {
-                const int2 b = s.bond_slot[i];
+            if (bonded) {
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
                     const int p = q == 0 ? b.x : b.y;
                     if (p < 0) continue;
-                    const V4<T> xp = ld4<T>(P + p);
+                    const V4<T> xp = q == 0 ? xp0 : xp1;
                     const T dx = min_image(xi.x, xp.x, L0, H0);
                     const T dy = min_image(xi.y, xp.y, L1, H1);
                     const T dz = min_image(xi.z, xp.z, L2, H2);
@@ -186,7 +229,6 @@ __global__ void __launch_bounds__(TILE) k_step(DevSys<T> s, int cur, double* __r
                 acc[P_BOND_LEN] = 0.5 * blen;
                 acc[P_BOND_CNT] = 0.5 * bcnt;
             }
-            V4<T> v = s.vel[i];
             if (MODE == MODE_FORCES) {
                 if (f_out) {
                     const size_t gid = (size_t)g.p_off + bits_as_int(v.w);
@@ -245,10 +287,9 @@ __global__ void __launch_bounds__(TILE) k_step(DevSys<T> s, int cur, double* __r
                             __threadfence();
                             x = T(0); y = T(0); z = T(0);
                         }
-                        const V4<T> b = s.xb[i];
-                        const T ex = min_image(x, b.x, L0, H0);
-                        const T ey = min_image(y, b.y, L1, H1);
-                        const T ez = min_image(z, b.z, L2, H2);
+                        const T ex = min_image(x, xbi.x, L0, H0);
+                        const T ey = min_image(y, xbi.y, L1, H1);
+                        const T ez = min_image(z, xbi.z, L2, H2);
                         if (ex * ex + ey * ey + ez * ez > s.half_skin2) {
                             s.req[tl.rep] = 1;
                             c->any_req = 1;
@@ -363,7 +404,11 @@ template <class T>
 void Launch<T>::step(const DevSys<T>& s, int mode, bool energy, int cur, double* f_out,
                      unsigned long long next_cond, int grid, cudaStream_t st) {
     const int gr = grid > 0 ? grid : s.ntiles;
-#define ESPP_STEP(M, E) k_step<T, M, E><<<gr, TILE, 0, st>>>(s, cur, f_out, next_cond)
+#define ESPP_STEP(M, E)                                                                  \
+    do {                                                                                 \
+        if (s.lj_fast) k_step<T, M, E, true><<<gr, TILE, 0, st>>>(s, cur, f_out, next_cond); \
+        else k_step<T, M, E, false><<<gr, TILE, 0, st>>>(s, cur, f_out, next_cond);     \
+    } while (0)
     switch (mode) {
         case MODE_FORCES:
             if (energy) ESPP_STEP(MODE_FORCES, true); else ESPP_STEP(MODE_FORCES, false);

@@ -45,11 +45,13 @@ template <class T> struct DevSys {
     int cap;
     int stride;
     // cells (rank space, all replicas concatenated)
+    // cells are indexed by cell_off + (cz * ny + cy) * nx + cx; each holds up
+    // to capc entries (position, storage slot in the w lane), ascending slot
     int* cell_cnt;
-    int* cell_list;     // ncells * capc member slots, ascending within a cell
+    V4<T>* cell_xyz;
     int capc;
-    int* cell_start;    // ncells + 1 (resort only)
-    const int* cell_rank;  // per replica linear cell index (+cell_off) -> global rank
+    int* cell_start;       // first slot of each cell in Hilbert-rank order (resort only)
+    const int* cell_by_rank;  // global Hilbert rank -> cell index
     const int* cell_rep;
     int ncells;
     int* scan_part;
@@ -67,6 +69,7 @@ template <class T> struct DevSys {
     const PairRec<T>* pair;
     const T* tab;       // concatenated tables (tabulated pair and bond kinds)
     int ntypes;
+    int lj_fast;        // one particle type with a plain Lennard-Jones pair potential
     int N;
     BondRec<T> bond;
     T rlist2;           // (rc + skin)^2

@@ -393,6 +393,7 @@ class System : public SystemBase {
                     q.capU = (T)(uc - us);
                 }
             }
+        d.lj_fast = (ntypes == 1 && pair_h[0][0].kind == ESPP_LJ) ? 1 : 0;
         d.bond.kind = bond_kind;
         d.bond.K = (T)bond_K;
         d.bond.inv_R02 = bond_kind ? (T)(1.0 / (bond_R0 * bond_R0)) : T(0);
@@ -618,7 +619,7 @@ class System : public SystemBase {
             const int forced = atoi(f);
             if (forced > 0) cap = forced;
         }
-        return (cap + 3) & ~3;
+        return std::max(8, (cap + 3) & ~3);  // the step kernel reads two groups ahead
     }
 
     int estimate_capc() const {
@@ -632,17 +633,17 @@ class System : public SystemBase {
             const int forced = atoi(f);
             if (forced > 0) capc = forced;
         }
-        return (capc + 3) & ~3;  // rows of whole int4 groups
+        return capc;
     }
 
     int alloc_cells(int capc) {
         if (cell_list_alloc) cudaFree(cell_list_alloc);
         cell_list_alloc = nullptr;
         void* p = nullptr;
-        cudaError_t e = cudaMalloc(&p, (size_t)capc * d.ncells * sizeof(int));
+        cudaError_t e = cudaMalloc(&p, (size_t)capc * d.ncells * sizeof(V4<T>));
         if (e != cudaSuccess) return fail(ESPP_ERR_CUDA, std::string("cell allocation: ") + cudaGetErrorString(e));
         cell_list_alloc = p;
-        d.cell_list = reinterpret_cast<int*>(p);
+        d.cell_xyz = reinterpret_cast<V4<T>*>(p);
         d.capc = capc;
         clear_graphs();
         return ESPP_OK;
@@ -682,35 +683,36 @@ class System : public SystemBase {
         for (void* p : cell_allocs) cudaFree(p);
         cell_allocs.clear();
         clear_graphs();
-        std::vector<int> rank, rep_of;
+        std::vector<int> rep_of, by_rank;
         int coff = 0;
         for (int r = 0; r < R; ++r) {
             const int nx = cell_count(r, 0), ny = cell_count(r, 1), nz = cell_count(r, 2);
             const int nc = nx * ny * nz;
             std::vector<int> rk(nc);
             hilbert_ranks(nx, ny, nz, rk.data());
+            by_rank.resize(coff + nc);
             for (int k = 0; k < nc; ++k) {
-                rank.push_back(coff + rk[k]);
                 rep_of.push_back(r);
+                by_rank[coff + rk[k]] = coff + k;
             }
             coff += nc;
         }
         const int C = coff;
-        int *cnt, *start, *crank, *crep, *part;
+        int *cnt, *start, *crep, *cbr, *part;
         int rc2 = ESPP_OK;
         d.nscan_blocks = scan_blocks_for(C);
         if ((rc2 = alloc(&cnt, C, cell_allocs)) || (rc2 = alloc(&start, C + 1, cell_allocs)) ||
-            (rc2 = alloc(&crank, C, cell_allocs)) || (rc2 = alloc(&crep, C, cell_allocs)) ||
+            (rc2 = alloc(&crep, C, cell_allocs)) || (rc2 = alloc(&cbr, C, cell_allocs)) ||
             (rc2 = alloc(&part, d.nscan_blocks, cell_allocs)))
             return rc2;
-        CK(cudaMemcpy(crank, rank.data(), C * sizeof(int), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(crep, rep_of.data(), C * sizeof(int), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(cbr, by_rank.data(), C * sizeof(int), cudaMemcpyHostToDevice));
         const int nn = (int)N;
         CK(cudaMemcpy(start + C, &nn, sizeof(int), cudaMemcpyHostToDevice));
         d.cell_cnt = cnt;
         d.cell_start = start;
-        d.cell_rank = crank;
         d.cell_rep = crep;
+        d.cell_by_rank = cbr;
         d.ncells = C;
         d.scan_part = part;
         const double rl = rc + sk;
@@ -759,8 +761,7 @@ class System : public SystemBase {
             if (rcode) return rcode;
         }
         if (c.err & ERRBIT_CELL) {
-            const int capc = std::max((int)std::ceil(c.need_capc * 1.3 + 4), d.capc + 4);
-            rcode = alloc_cells((capc + 3) & ~3);
+            rcode = alloc_cells(std::max((int)std::ceil(c.need_capc * 1.3 + 4), d.capc + 4));
             if (rcode) return rcode;
         }
         Ctrl w = read_ctrl();

@@ -442,3 +442,83 @@ def test_table_bond_breaks_beyond_range():
     u, fr, st = O.bond_eval(m, 0.49)
     assert st == 0 and abs(fr + 30.0) < 1e-12 and abs(u - 15.0 * 0.49) < 1e-3
     assert O.bond_eval(m, 1.5 ** 2)[2] == 1
+
+
+# --------------------------------------------------------------------------
+# Learned MLP pair potential
+# --------------------------------------------------------------------------
+def _mlp_params(seed=0, scale=0.3):
+    return np.random.default_rng(seed).normal(0.0, scale, O.MLP_NPARAMS)
+
+
+def test_mlp_force_is_minus_energy_derivative():
+    O.set_mlp(_mlp_params(1), 3.5)
+    h = 1e-6
+    for r in (0.4, 0.97, 1.5, 2.2, 3.1, 3.45):
+        u, du = O.mlp_pair(r)
+        fd = (O.mlp_pair(r + h)[0] - O.mlp_pair(r - h)[0]) / (2 * h)
+        assert abs(du - fd) < 1e-7 * max(1.0, abs(du))
+
+
+def test_mlp_parameter_gradients_by_finite_differences():
+    p = _mlp_params(2)
+    O.set_mlp(p, 3.5)
+    r = 1.37
+    _, _, g_du, g_u = O.mlp_pair(r, want_grad=True)
+    rng = np.random.default_rng(3)
+    # W1, b1, W2, b2, w3 and b3 blocks
+    blocks = [(0, 2048), (2048, 2112), (2112, 6208), (6208, 6272), (6272, 6336), (6336, 6337)]
+    h = 1e-6
+    for lo, hi in blocks:
+        for k in rng.choice(np.arange(lo, hi), size=min(6, hi - lo), replace=False):
+            q = p.copy()
+            q[k] += h
+            O.set_mlp(q, 3.5)
+            up, dp = O.mlp_pair(r)
+            q[k] -= 2 * h
+            O.set_mlp(q, 3.5)
+            um, dm = O.mlp_pair(r)
+            assert abs(g_du[k] - (dp - dm) / (2 * h)) < 1e-6 * max(1.0, abs(g_du[k])), k
+            assert abs(g_u[k] - (up - um) / (2 * h)) < 1e-6 * max(1.0, abs(g_u[k])), k
+    O.set_mlp(p, 3.5)
+
+
+def test_mlp_envelope_vanishes_at_cutoff():
+    p = _mlp_params(4)
+    O.set_mlp(p, 3.5)
+    # phi and dphi/dr vanish at rc, so u tends to the zero-input value and du/dr to 0
+    u_rc, du_rc = O.mlp_pair(3.5 - 1e-7)
+    assert abs(du_rc) < 1e-6
+    W1 = p[:2048].reshape(64, 32)
+    b1, W2 = p[2048:2112], p[2112:6208].reshape(64, 64)
+    b2, w3, b3 = p[6208:6272], p[6272:6336], p[6336]
+    silu = lambda z: z / (1 + np.exp(-z))
+    u0 = w3 @ silu(W2 @ silu(b1) + b2) + b3
+    assert abs(u_rc - u0) < 1e-9
+    # zero hidden weights: u is the constant w3 . silu(b2) + b3
+    q = p.copy()
+    q[2112:6208] = 0.0
+    O.set_mlp(q, 3.5)
+    u, du = O.mlp_pair(1.0)
+    assert abs(u - (w3 @ silu(b2) + b3)) < 1e-12 and abs(du) < 1e-15
+    O.set_mlp(p, 3.5)
+
+
+def test_bonded_exclusion_removes_exactly_the_bonded_pairs():
+    c = I.kg_lattice(5, 20, seed=6, jitter=0.1)
+    m = O.Model(1, {(0, 0): ("lj", 1.0, 1.0, 2.5, True)})
+    f_all, _ = O.forces(m, c.box, c.x, c.types, np.zeros((0, 2), np.int64))
+    O.set_exclude_bonded(True)
+    try:
+        f_ex, _ = O.forces(O.Model(1, {(0, 0): ("lj", 1.0, 1.0, 2.5, True)}, None), c.box, c.x, c.types, c.bonds)
+    finally:
+        O.set_exclude_bonded(False)
+    # add back the bonded pair forces by hand: F_i += fr d over bonded partners
+    f_back = f_ex.copy()
+    for a, b in c.bonds:
+        d = c.x[a] - c.x[b]
+        d -= c.box * np.round(d / c.box)
+        _, fr = O.pair_eval(m, 0, 0, float(d @ d))
+        f_back[a] += fr * d
+        f_back[b] -= fr * d
+    assert np.abs(f_back - f_all).max() < 1e-10 * np.abs(f_all).max()
