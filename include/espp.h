@@ -67,6 +67,7 @@ extern "C" {
 #define ESPP_FENE 4       /* params: K, R0  (applies to every bond)             */
 #define ESPP_TAB_PAIR 5   /* params: rc, n, u[n], F[n] on r_k = k rc / (n-1)    */
 #define ESPP_TAB_BOND 6   /* params: rmax, n, u[n], F[n] on r_k = k rmax / (n-1); every bond */
+#define ESPP_MLP 7        /* params: rc; learned pair potential, weights by espp_mlp_set_weights */
 
 #define ESPP_MAX_TYPES 8
 #define ESPP_MAX_BONDS_PER_PARTICLE 2
@@ -155,6 +156,23 @@ int espp_set_step(espp_h h, int64_t step);
  * error like a stretched FENE bond.  Marks the stored force stale. */
 int espp_set_interaction(espp_h h, int kind, int type_a, int type_b, const double* params,
                          int64_t n_params);
+
+/* Learned coarse-grained pair potential (the spec learned-CG model; the
+ * paper's "tabulated potentials" are its fallback).  u(r) = w3 . silu(W2
+ * silu(W1 phi(r) + b1) + b2) + b3 with 32 Gaussian radial bases phi_k(r) =
+ * exp(-(r - mu_k)^2 / (2 w^2)) (cos(pi r / rc) + 1) / 2, mu_k = rc k / 31,
+ * w = rc / 31.  Weights: bf16[ESPP_MLP_NPARAMS] bit patterns in the order W1
+ * (64x32, rows = output units), b1 (64), W2 (64x64), b2 (64), w3 (64), b3.
+ * Evaluated on the tensor cores (BF16 operands, FP32 accumulation) with the
+ * force from the exact derivative carried through both layers.  Select it
+ * with espp_set_interaction(h, ESPP_MLP, 0, 0, {rc}, 1) on a single-type
+ * system. */
+#define ESPP_MLP_NPARAMS 6337
+int espp_mlp_set_weights(espp_h h, const uint16_t* bf16, int64_t n);
+
+/* Leave 1-2 bonded pairs out of the Verlet list (and so out of every pair
+ * potential); default off, as Kremer-Grest keeps WCA between bonded beads. */
+int espp_set_exclude_bonded(espp_h h, int on);
 
 /* Per-type mass (default 1 for every type). */
 int espp_set_mass(espp_h h, int type, double mass);

@@ -95,6 +95,46 @@ __device__ __forceinline__ T min_image(T xi, T xj, T L, T halfL) {
 }
 
 // ---------------------------------------------------------------------------
+// Verlet-list entries carry the periodic image of the pair.  Bits 0..24 hold
+// the neighbour's storage slot, bits 25..30 two bits per dimension: 1 = the
+// neighbour lies across the upper face (use x_i - L), 2 = across the lower
+// face (use x_j - L), 0 = no shift.  Positions are wrapped into the box only
+// when the list is rebuilt, so the image fixed at the build stays valid until
+// the next build.  Both shifted subtractions are exact (Sterbenz: the shifted
+// coordinate lies in [L/2, 2L]); the difference carries one rounding, like
+// the minimum image above.
+// ---------------------------------------------------------------------------
+constexpr int NBR_INDEX_BITS = 25;
+constexpr int NBR_INDEX_MASK = (1 << NBR_INDEX_BITS) - 1;
+constexpr int MAX_PARTICLES = 1 << NBR_INDEX_BITS;
+
+__device__ __forceinline__ int nbr_slot(int e) { return e & NBR_INDEX_MASK; }
+__device__ __forceinline__ int nbr_code(int e) { return e >> NBR_INDEX_BITS; }
+
+template <class T>
+__device__ __forceinline__ T shifted_diff(T xi, T xi_minus_L, T xj, T L, int c) {
+    const T a = (c & 1) ? xi_minus_L : xi;
+    const T b = (c & 2) ? xj - L : xj;
+    return a - b;
+}
+
+// Wrap one coordinate into [0, L); returns the image change (-1, 0, +1).  A
+// coordinate that rounds to exactly L after adding L becomes 0.
+template <class T>
+__device__ __forceinline__ int wrap_coord(T& x, T L) {
+    if (x >= L) {
+        x -= L;
+        return 1;
+    }
+    if (x < T(0)) {
+        x += L;
+        if (x >= L) x = T(0);
+        return -1;
+    }
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
 // Per-replica geometry, resident in device memory.
 // ---------------------------------------------------------------------------
 template <class T> struct RepGeom {

@@ -60,11 +60,25 @@ __global__ void __launch_bounds__(TILE) k_get_state(DevSys<T> s, double* __restr
         const int i = tl.start + threadIdx.x;
         const V4<T> vv = s.vel[i];
         const size_t gid = (size_t)g.p_off + bits_as_int(vv.w);
+        // stored positions may lie just outside the box (they are wrapped at
+        // list builds only): report them wrapped, with the image counters to match
+        const V4<T> p = s.pos[cur][i];
+        const double pc[3] = {(double)p.x, (double)p.y, (double)p.z};
+        double wc[3];
+        int sh[3];
+        for (int d = 0; d < 3; ++d) {
+            const double L = (double)g.L[d];
+            double w = pc[d];
+            int k = 0;
+            if (w >= L) { w -= L; k = 1; }
+            else if (w < 0.0) { w += L; k = -1; if (w >= L) w = 0.0; }
+            wc[d] = w;
+            sh[d] = k;
+        }
         if (x) {
-            const V4<T> p = s.pos[cur][i];
-            x[3 * gid] = p.x;
-            x[3 * gid + 1] = p.y;
-            x[3 * gid + 2] = p.z;
+            x[3 * gid] = wc[0];
+            x[3 * gid + 1] = wc[1];
+            x[3 * gid + 2] = wc[2];
         }
         if (v) {
             v[3 * gid] = vv.x;
@@ -73,9 +87,9 @@ __global__ void __launch_bounds__(TILE) k_get_state(DevSys<T> s, double* __restr
         }
         if (img) {
             const int4 im = s.img[i];
-            img[3 * gid] = im.x;
-            img[3 * gid + 1] = im.y;
-            img[3 * gid + 2] = im.z;
+            img[3 * gid] = im.x + sh[0];
+            img[3 * gid + 1] = im.y + sh[1];
+            img[3 * gid + 2] = im.z + sh[2];
         }
     }
 }

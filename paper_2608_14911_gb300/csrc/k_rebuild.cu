@@ -65,13 +65,24 @@ __global__ void __launch_bounds__(TILE) k_bin(DevSys<T> s, int cur) {
         for (int r = threadIdx.x; r < s.R; r += blockDim.x) s.req[r] = 0;
         if (threadIdx.x == 0) s.ctrl->any_req = 0;
     }
-    const V4<T>* __restrict__ P = s.pos[cur];
+    V4<T>* __restrict__ P = s.pos[cur];
     for (int t = blockIdx.x; t < s.ntiles; t += gridDim.x) {
         const Tile tl = s.tiles[t];
         if (!s.now[tl.rep] || (int)threadIdx.x >= tl.count) continue;
         const int i = tl.start + threadIdx.x;
-        V4<T> p = ld4<T>(P + i);
-        const int h = cell_of(s.reps[tl.rep], p);
+        V4<T> p = P[i];
+        // positions are wrapped into the box at list builds only
+        const RepGeom<T>& g = s.reps[tl.rep];
+        const int wx = wrap_coord(p.x, g.L[0]), wy = wrap_coord(p.y, g.L[1]), wz = wrap_coord(p.z, g.L[2]);
+        if (wx | wy | wz) {
+            P[i] = p;
+            int4 im = s.img[i];
+            im.x += wx;
+            im.y += wy;
+            im.z += wz;
+            s.img[i] = im;
+        }
+        const int h = cell_of(g, p);
         const int slot = atomicAdd(&s.cell_cnt[h], 1);
         if (slot < s.capc) {
             p.w = int_bits_as(T(0), i);
@@ -268,18 +279,24 @@ __global__ void __launch_bounds__(TILE) k_verlet(DevSys<T> s, int cur) {
             const int xm = cx == 0 ? nc0 - 1 : cx - 1, xp = cx == nc0 - 1 ? 0 : cx + 1;
             const int ym = cy == 0 ? nc1 - 1 : cy - 1, yp = cy == nc1 - 1 ? 0 : cy + 1;
             const T L0 = g.L[0], L1 = g.L[1], L2 = g.L[2];
-            const T H0 = g.halfL[0], H1 = g.halfL[1], H2 = g.halfL[2];
+            const T xim = xi.x - L0, yim = xi.y - L1, zim = xi.z - L2;
             const T rl2 = s.rlist2;
             const int cap = s.cap, capc = s.capc;
             const size_t stride = (size_t)s.stride;
             int4* __restrict__ out4 = reinterpret_cast<int4*>(s.nbr) + i;
+            // bonded partners left out of the list when 1-2 exclusions are on
+            const int2 ex = s.excl_bonded ? s.bond_slot[i] : make_int2(-1, -1);
+            // image codes of the stencil rows: 1 = across the upper face, 2 = lower
+            const int cxm = cx == 0 ? 2 : 0, cxp = cx == nc0 - 1 ? 1 : 0;
+            const int cym = cy == 0 ? 2 : 0, cyp = cy == nc1 - 1 ? 1 : 0;
             int cnt = 0;
             int4 grp = make_int4(-1, -1, -1, -1);
 #pragma unroll 1
             for (int pz = 0; pz < 3; ++pz) {
                 int az = cz + pz - 1;
-                az += az < 0 ? nc2 : 0;
-                az -= az >= nc2 ? nc2 : 0;
+                int czc = 0;
+                if (az < 0) { az += nc2; czc = 2; }
+                if (az >= nc2) { az -= nc2; czc = 1; }
                 int hh[9], cn[9];
 #pragma unroll
                 for (int q = 0; q < 9; ++q) {
@@ -291,20 +308,25 @@ __global__ void __launch_bounds__(TILE) k_verlet(DevSys<T> s, int cur) {
                 for (int q = 0; q < 9; ++q) cn[q] = min(__ldg(s.cell_cnt + hh[q]), capc);
 #pragma unroll
                 for (int q = 0; q < 9; ++q) {
+                    const int ccx = q % 3 == 0 ? cxm : (q % 3 == 2 ? cxp : 0);
+                    const int ccy = q / 3 == 0 ? cym : (q / 3 == 2 ? cyp : 0);
+                    const int code = ccx | (ccy << 2) | (czc << 4);
+                    const int tag = code << NBR_INDEX_BITS;
                     const V4<T>* __restrict__ ent = s.cell_xyz + (size_t)hh[q] * capc;
                     for (int k = 0; k < cn[q]; ++k) {
                         const V4<T> xj = ld4<T>(ent + k);
                         const int j = bits_as_int(xj.w);
-                        if (j == i) continue;
-                        const T ddx = min_image(xi.x, xj.x, L0, H0);
-                        const T ddy = min_image(xi.y, xj.y, L1, H1);
-                        const T ddz = min_image(xi.z, xj.z, L2, H2);
+                        if (j == i || j == ex.x || j == ex.y) continue;
+                        const T ddx = shifted_diff(xi.x, xim, xj.x, L0, ccx);
+                        const T ddy = shifted_diff(xi.y, yim, xj.y, L1, ccy);
+                        const T ddz = shifted_diff(xi.z, zim, xj.z, L2, czc);
                         if (ddx * ddx + ddy * ddy + ddz * ddz < rl2) {
                             const int l = cnt & 3;
-                            if (l == 0) grp.x = j;
-                            else if (l == 1) grp.y = j;
-                            else if (l == 2) grp.z = j;
-                            else grp.w = j;
+                            const int e = j | tag;
+                            if (l == 0) grp.x = e;
+                            else if (l == 1) grp.y = e;
+                            else if (l == 2) grp.z = e;
+                            else grp.w = e;
                             ++cnt;
                             if ((cnt & 3) == 0) {
                                 if (cnt <= cap) out4[(size_t)((cnt >> 2) - 1) * stride] = grp;

@@ -20,6 +20,15 @@
 
 namespace espp {
 
+// 1/x: the hardware approximation in FP32 (error of order one ulp, far inside
+// the 1e-5 force tolerance), the correctly rounded division in FP64.
+__device__ __forceinline__ float recip(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
 template <class T>
 __device__ __forceinline__ void pair_force(const PairRec<T>& pr, const T* __restrict__ tab, T r2, T& fr, T& u) {
     // caller guarantees r2 < pr.rc2 and kind != 0
@@ -36,7 +45,7 @@ __device__ __forceinline__ void pair_force(const PairRec<T>& pr, const T* __rest
         u = pr.capU + pr.capF * (pr.cap - r);
         return;
     }
-    const T inv_r2 = T(1) / r2;
+    const T inv_r2 = recip(r2);
     const T s2 = pr.sig2 * inv_r2;
     const T s6 = s2 * s2 * s2;
     fr = pr.eps24 * s6 * (T(2) * s6 - T(1)) * inv_r2;
@@ -50,8 +59,8 @@ __device__ __forceinline__ void pair_force(const PairRec<T>& pr, const T* __rest
 template <class T, bool ENERGY, bool MULTI, bool FAST>
 __device__ __forceinline__ void pair_loop(const DevSys<T>& s, const V4<T>* __restrict__ P, int i, int n,
                                           const V4<T>& xi, int ti, const PairRec<T>* pr1,
-                                          T L0, T L1, T L2, T H0, T H1, T H2,
-                                          T& fx, T& fy, T& fz, T& pe, T& vir) {
+                                          T L0, T L1, T L2, T& fx, T& fy, T& fz, T& pe, T& vir) {
+    const T xim = xi.x - L0, yim = xi.y - L1, zim = xi.z - L2;
     constexpr int GB = sizeof(T) == 4 ? 2 : 1;  // int4 groups per batch
     const int ng = (n + 3) >> 2;
     const int4* __restrict__ nb = reinterpret_cast<const int4*>(s.nbr) + i;
@@ -72,18 +81,19 @@ __device__ __forceinline__ void pair_loop(const DevSys<T>& s, const V4<T>* __res
         }
         V4<T> xj[4 * GB];
 #pragma unroll
-        for (int q = 0; q < 4 * GB; ++q) xj[q] = jj[q] >= 0 ? ld4<T>(P + jj[q]) : xi;
+        for (int q = 0; q < 4 * GB; ++q) xj[q] = jj[q] >= 0 ? ld4<T>(P + nbr_slot(jj[q])) : xi;
 #pragma unroll
         for (int q = 0; q < 4 * GB; ++q) {
             if (jj[q] < 0) continue;
+            const int code = nbr_code(jj[q]);
+            const T dx = shifted_diff(xi.x, xim, xj[q].x, L0, code & 3);
+            const T dy = shifted_diff(xi.y, yim, xj[q].y, L1, (code >> 2) & 3);
+            const T dz = shifted_diff(xi.z, zim, xj[q].z, L2, code >> 4);
             if (FAST) {
                 // one type, plain Lennard-Jones: only rc^2, sigma^2, 24 eps live
-                const T dx = min_image(xi.x, xj[q].x, L0, H0);
-                const T dy = min_image(xi.y, xj[q].y, L1, H1);
-                const T dz = min_image(xi.z, xj[q].z, L2, H2);
                 const T r2 = dx * dx + dy * dy + dz * dz;
                 if (r2 < pr1->rc2) {
-                    const T inv_r2 = T(1) / r2;
+                    const T inv_r2 = recip(r2);
                     const T s2 = pr1->sig2 * inv_r2;
                     const T s6 = s2 * s2 * s2;
                     const T fr = pr1->eps24 * s6 * (T(2) * s6 - T(1)) * inv_r2;
@@ -98,9 +108,6 @@ __device__ __forceinline__ void pair_loop(const DevSys<T>& s, const V4<T>* __res
                 continue;
             }
             const PairRec<T>& pr = MULTI ? s.pair[ti * s.ntypes + bits_as_int(xj[q].w)] : *pr1;
-            const T dx = min_image(xi.x, xj[q].x, L0, H0);
-            const T dy = min_image(xi.y, xj[q].y, L1, H1);
-            const T dz = min_image(xi.z, xj[q].z, L2, H2);
             const T r2 = dx * dx + dy * dy + dz * dz;
             if ((!MULTI || pr.kind != 0) && r2 < pr.rc2) {
                 T fr, u;
@@ -160,7 +167,17 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 6 : 4) k_step(DevSys<T>
             if (MODE == MODE_STEP) xbi = s.xb[i];
             const V4<T> xp0 = b.x >= 0 ? ld4<T>(P + b.x) : xi;
             const V4<T> xp1 = b.y >= 0 ? ld4<T>(P + b.y) : xi;
-            if (FAST) {
+            if (s.mlp_on) {
+                // pair forces of the learned potential, computed by k_mlp
+                const float4 fm = s.mlp_f[i];
+                fx = (T)fm.x;
+                fy = (T)fm.y;
+                fz = (T)fm.z;
+                if (ENERGY) {
+                    pe = (T)fm.w;
+                    vir = (T)s.mlp_w[i];
+                }
+            } else if (FAST) {
                 PairRec<T> pr;
                 pr.rc2 = s.pair[0].rc2;
                 pr.sig2 = s.pair[0].sig2;
@@ -169,13 +186,13 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 6 : 4) k_step(DevSys<T>
                     pr.eps4 = s.pair[0].eps4;
                     pr.shift = s.pair[0].shift;
                 }
-                pair_loop<T, ENERGY, false, true>(s, P, i, n, xi, ti, &pr, L0, L1, L2, H0, H1, H2, fx, fy, fz, pe, vir);
+                pair_loop<T, ENERGY, false, true>(s, P, i, n, xi, ti, &pr, L0, L1, L2, fx, fy, fz, pe, vir);
             } else if (s.ntypes == 1) {
                 const PairRec<T> pr = s.pair[0];
                 if (pr.kind != 0)
-                    pair_loop<T, ENERGY, false, false>(s, P, i, n, xi, ti, &pr, L0, L1, L2, H0, H1, H2, fx, fy, fz, pe, vir);
+                    pair_loop<T, ENERGY, false, false>(s, P, i, n, xi, ti, &pr, L0, L1, L2, fx, fy, fz, pe, vir);
             } else {
-                pair_loop<T, ENERGY, true, false>(s, P, i, n, xi, ti, nullptr, L0, L1, L2, H0, H1, H2, fx, fy, fz, pe, vir);
+                pair_loop<T, ENERGY, true, false>(s, P, i, n, xi, ti, nullptr, L0, L1, L2, fx, fy, fz, pe, vir);
             }
             // bonds (paper "Functionality": bonded interactions; FENE or tabulated)
             double blen = 0.0, bcnt = 0.0;
@@ -270,26 +287,15 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 6 : 4) k_step(DevSys<T>
                         v.z = half_kick(v.z, fz, hdt, inv_m);
                         const T dt = ip->dt;
                         T x = drift(xi.x, v.x, dt), y = drift(xi.y, v.y, dt), z = drift(xi.z, v.z, dt);
-                        int wx = 0, wy = 0, wz = 0;
-                        if (x >= L0) { x -= L0; wx = 1; } else if (x < T(0)) { x += L0; wx = -1; if (x >= L0) x = T(0); }
-                        if (y >= L1) { y -= L1; wy = 1; } else if (y < T(0)) { y += L1; wy = -1; if (y >= L1) y = T(0); }
-                        if (z >= L2) { z -= L2; wz = 1; } else if (z < T(0)) { z += L2; wz = -1; if (z >= L2) z = T(0); }
-                        if (wx | wy | wz) {
-                            int4 im = s.img[i];
-                            im.x += wx;
-                            im.y += wy;
-                            im.z += wz;
-                            s.img[i] = im;
-                        }
-                        if (!(x >= T(0) && x < L0 && y >= T(0) && y < L1 && z >= T(0) && z < L2)) {
+                        // no wrap here: positions stay in the image frame of the
+                        // last list build until the next build wraps them
+                        if (!(fabs(x) < T(1e30) && fabs(y) < T(1e30) && fabs(z) < T(1e30))) {
                             atomicOr(&c->err, ERRBIT_NONFINITE);
                             c->abort = 1;
                             __threadfence();
-                            x = T(0); y = T(0); z = T(0);
+                            x = xi.x; y = xi.y; z = xi.z;
                         }
-                        const T ex = min_image(x, xbi.x, L0, H0);
-                        const T ey = min_image(y, xbi.y, L1, H1);
-                        const T ez = min_image(z, xbi.z, L2, H2);
+                        const T ex = x - xbi.x, ey = y - xbi.y, ez = z - xbi.z;
                         if (ex * ex + ey * ey + ez * ez > s.half_skin2) {
                             s.req[tl.rep] = 1;
                             c->any_req = 1;
@@ -351,7 +357,6 @@ __global__ void __launch_bounds__(TILE) k_prologue(DevSys<T> s, int cur) {
     for (int t = blockIdx.x; t < s.ntiles; t += gridDim.x) {
         const Tile tl = s.tiles[t];
         if ((int)threadIdx.x >= tl.count) continue;
-        const RepGeom<T>& g = s.reps[tl.rep];
         const int i = tl.start + threadIdx.x;
         const V4<T> xi = P[i];
         const int ti = bits_as_int(xi.w);
@@ -362,28 +367,14 @@ __global__ void __launch_bounds__(TILE) k_prologue(DevSys<T> s, int cur) {
         v.y = half_kick(v.y, f.y, hdt, inv_m);
         v.z = half_kick(v.z, f.z, hdt, inv_m);
         const T dt = ip->dt;
-        const T L0 = g.L[0], L1 = g.L[1], L2 = g.L[2];
         T x = drift(xi.x, v.x, dt), y = drift(xi.y, v.y, dt), z = drift(xi.z, v.z, dt);
-        int wx = 0, wy = 0, wz = 0;
-        if (x >= L0) { x -= L0; wx = 1; } else if (x < T(0)) { x += L0; wx = -1; if (x >= L0) x = T(0); }
-        if (y >= L1) { y -= L1; wy = 1; } else if (y < T(0)) { y += L1; wy = -1; if (y >= L1) y = T(0); }
-        if (z >= L2) { z -= L2; wz = 1; } else if (z < T(0)) { z += L2; wz = -1; if (z >= L2) z = T(0); }
-        if (wx | wy | wz) {
-            int4 im = s.img[i];
-            im.x += wx;
-            im.y += wy;
-            im.z += wz;
-            s.img[i] = im;
-        }
-        if (!(x >= T(0) && x < L0 && y >= T(0) && y < L1 && z >= T(0) && z < L2)) {
+        if (!(fabs(x) < T(1e30) && fabs(y) < T(1e30) && fabs(z) < T(1e30))) {
             atomicOr(&c->err, ERRBIT_NONFINITE);
             c->abort = 1;
-            x = T(0); y = T(0); z = T(0);
+            x = xi.x; y = xi.y; z = xi.z;
         }
         const V4<T> b = s.xb[i];
-        const T ex = min_image(x, b.x, L0, g.halfL[0]);
-        const T ey = min_image(y, b.y, L1, g.halfL[1]);
-        const T ez = min_image(z, b.z, L2, g.halfL[2]);
+        const T ex = x - b.x, ey = y - b.y, ez = z - b.z;
         if (ex * ex + ey * ey + ez * ez > s.half_skin2) {
             s.req[tl.rep] = 1;
             c->any_req = 1;
@@ -404,6 +395,7 @@ template <class T>
 void Launch<T>::step(const DevSys<T>& s, int mode, bool energy, int cur, double* f_out,
                      unsigned long long next_cond, int grid, cudaStream_t st) {
     const int gr = grid > 0 ? grid : s.ntiles;
+    if (s.mlp_on) Launch<T>::mlp(s, cur, st);
 #define ESPP_STEP(M, E)                                                                  \
     do {                                                                                 \
         if (s.lj_fast) k_step<T, M, E, true><<<gr, TILE, 0, st>>>(s, cur, f_out, next_cond); \

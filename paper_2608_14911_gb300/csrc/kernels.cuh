@@ -1,5 +1,7 @@
 // Device view of one handle and the host-side launchers of every kernel.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace espp {
@@ -14,6 +16,22 @@ template <class T> struct IntParams {
     T mass[MAX_TYPES];
     T inv_mass[MAX_TYPES];
     T noise_amp[MAX_TYPES];  // sqrt(24 gamma m kT / dt)
+};
+
+// Learned pair potential: 32 radial bases -> 64 -> 64 -> 1 (SiLU), weights
+// in BF16 (W1 row-major 64x32, W2 64x64, rows = output units), biases and the
+// output layer as the BF16 values in float.
+constexpr int MLP_NB = 32;
+constexpr int MLP_H = 64;
+constexpr int MLP_NPARAMS = MLP_H * MLP_NB + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1;
+struct MlpWeights {
+    __nv_bfloat16 W1[MLP_H * MLP_NB];
+    __nv_bfloat16 W2[MLP_H * MLP_H];
+    float b1[MLP_H];
+    float b2[MLP_H];
+    float w3[MLP_H];
+    float b3;
+    float rc;
 };
 
 constexpr int NPART = 12;  // per-tile observable partials (doubles)
@@ -70,6 +88,11 @@ template <class T> struct DevSys {
     const T* tab;       // concatenated tables (tabulated pair and bond kinds)
     int ntypes;
     int lj_fast;        // one particle type with a plain Lennard-Jones pair potential
+    int mlp_on;         // pair forces come from the learned MLP (k_mlp) instead
+    int excl_bonded;    // 1-2 bonded pairs are left out of the Verlet list
+    const MlpWeights* mlp;
+    float4* mlp_f;      // per particle: MLP pair force and sum of pair energies
+    float* mlp_w;       // per particle: sum of r_ij . F_ij over its MLP pairs
     int N;
     BondRec<T> bond;
     T rlist2;           // (rc + skin)^2
@@ -96,6 +119,7 @@ template <class T> struct Launch {
                      unsigned long long next_cond, int grid, cudaStream_t st);
     static void prologue(const DevSys<T>& s, int cur, int grid, cudaStream_t st);
     static void set_cond(const DevSys<T>& s, unsigned long long cond, cudaStream_t st);
+    static void mlp(const DevSys<T>& s, int cur, cudaStream_t st);
     // state I/O (id-ordered double buffers on the device)
     static void set_state(const DevSys<T>& s, const double* x, const double* v, const int* img,
                           const int* types_by_gid, int cur, cudaStream_t st);

@@ -41,6 +41,8 @@ struct SystemBase {
     virtual int set_step(int64_t step) = 0;
     virtual int set_interaction(int kind, int ta, int tb, const double* p, int64_t np) = 0;
     virtual int set_mass(int type, double m) = 0;
+    virtual int mlp_set_weights(const uint16_t* bits, int64_t n) = 0;
+    virtual int set_exclude_bonded(int on) = 0;
     virtual int build_neighbors(double rc, double skin) = 0;
     virtual int get_neighbors(int64_t* row_ptr, int64_t* cols, int64_t cap) = 0;
     virtual int compute_forces(double* f, int where) = 0;
@@ -89,6 +91,8 @@ class System : public SystemBase {
     int bond_kind = ESPP_NONE;
     double bond_K = 0, bond_R0 = 0;
     std::vector<double> bond_tab;  // tabulated bond: u[n] then F[n] over [0, bond_R0]
+    std::vector<uint16_t> mlp_bits;  // learned potential, BF16 bit patterns
+    MlpWeights* d_mlp = nullptr;
     void* tab_alloc = nullptr;
     size_t tab_elems = 0;
     double mass_h[MAX_TYPES];
@@ -172,7 +176,7 @@ class System : public SystemBase {
             rep_poff.push_back((int)total);
             rep_n.push_back((int)dsc.n);
             total += dsc.n;
-            if (total >= (1ll << 31) - 64) return fail(ESPP_ERR_ARG, "too many particles");
+            if (total >= MAX_PARTICLES) return fail(ESPP_ERR_ARG, "too many particles (at most 2^25 per handle)");
             for (int c = 0; c < 3; ++c) box.push_back(dsc.box[c]);
             seeds.push_back(dsc.seed);
         }
@@ -290,8 +294,11 @@ class System : public SystemBase {
             (rc = alloc(&d_mol_members, mol_members_h.size(), allocs)) ||
             (rc = alloc(&d_mol_off, mol_off_h.size(), allocs)) ||
             (rc = alloc(&d_mol_rep, mol_rep_h.size(), allocs)) ||
-            (rc = alloc(&d_mol_rg2, mol_rep_h.size(), allocs)))
+            (rc = alloc(&d_mol_rg2, mol_rep_h.size(), allocs)) ||
+            (rc = alloc(&d.mlp_f, n, allocs)) || (rc = alloc(&d.mlp_w, n, allocs)) ||
+            (rc = alloc(&d_mlp, 1, allocs)))
             return rc;
+        d.mlp = d_mlp;
         d.bond_gid = bg;
         d.slot_of_id = sid;
         d.perm = perm;
@@ -362,6 +369,10 @@ class System : public SystemBase {
                 memset(&q, 0, sizeof(q));
                 q.kind = p.kind;
                 if (p.kind == ESPP_NONE) continue;
+                if (p.kind == ESPP_MLP) {
+                    q.rc2 = (T)(p.rc * p.rc);
+                    continue;
+                }
                 if (p.kind == ESPP_TAB_PAIR) {
                     const int nt = (int)(p.tab.size() / 2);
                     q.rc2 = (T)(p.rc * p.rc);
@@ -394,6 +405,30 @@ class System : public SystemBase {
                 }
             }
         d.lj_fast = (ntypes == 1 && pair_h[0][0].kind == ESPP_LJ) ? 1 : 0;
+        d.mlp_on = (pair_h[0][0].kind == ESPP_MLP) ? 1 : 0;
+        if (d.mlp_on && !mlp_bits.empty()) {
+            MlpWeights w;
+            memset(&w, 0, sizeof(w));
+            auto f = [&](int k) {
+                const uint32_t b = (uint32_t)mlp_bits[k] << 16;
+                float v;
+                memcpy(&v, &b, 4);
+                return v;
+            };
+            memcpy(w.W1, mlp_bits.data(), sizeof(w.W1));
+            const int o_b1 = MLP_H * MLP_NB, o_W2 = o_b1 + MLP_H, o_b2 = o_W2 + MLP_H * MLP_H;
+            const int o_w3 = o_b2 + MLP_H, o_b3 = o_w3 + MLP_H;
+            memcpy(w.W2, mlp_bits.data() + o_W2, sizeof(w.W2));
+            for (int a = 0; a < MLP_H; ++a) {
+                w.b1[a] = f(o_b1 + a);
+                w.b2[a] = f(o_b2 + a);
+                w.w3[a] = f(o_w3 + a);
+            }
+            w.b3 = f(o_b3);
+            w.rc = (float)pair_h[0][0].rc;
+            cudaError_t e = cudaMemcpy(d_mlp, &w, sizeof(w), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return e;
+        }
         d.bond.kind = bond_kind;
         d.bond.K = (T)bond_K;
         d.bond.inv_R02 = bond_kind ? (T)(1.0 / (bond_R0 * bond_R0)) : T(0);
@@ -568,6 +603,12 @@ class System : public SystemBase {
                 int rc = read_table(h.rc, h.tab);
                 if (rc) return rc;
                 h.kind = ESPP_TAB_PAIR;
+            } else if (kind == ESPP_MLP) {
+                if (!p || np < 1 || !(p[0] > 0)) return fail(ESPP_ERR_ARG, "the learned potential needs rc > 0");
+                if (ta != 0 || tb != 0 || ntypes != 1)
+                    return fail(ESPP_ERR_ARG, "the learned potential applies to single-type systems (types 0, 0)");
+                h.kind = ESPP_MLP;
+                h.rc = p[0];
             } else if (kind == ESPP_WCA) {
                 if (!p || np < 2) return fail(ESPP_ERR_ARG, "WCA needs eps, sigma");
                 h.kind = ESPP_LJ;
@@ -584,6 +625,26 @@ class System : public SystemBase {
         }
         CK(upload_params());
         clear_graphs();  // the bond record is a kernel argument of captured graphs
+        f_valid = false;
+        return ESPP_OK;
+    }
+
+    int mlp_set_weights(const uint16_t* bits, int64_t n) override {
+        if (!bits || n != MLP_NPARAMS) return fail(ESPP_ERR_ARG, "expected ESPP_MLP_NPARAMS BF16 weights");
+        mlp_bits.assign(bits, bits + n);
+        CK(upload_params());
+        f_valid = false;
+        return ESPP_OK;
+    }
+
+    int set_exclude_bonded(int on) override {
+        d.excl_bonded = on ? 1 : 0;
+        clear_graphs();  // a kernel argument of the captured graphs
+        rebuild_pending = true;
+        if (state_set) {
+            Launch<T>::request_all(d, st);
+            launches++;
+        }
         f_valid = false;
         return ESPP_OK;
     }
@@ -779,6 +840,7 @@ class System : public SystemBase {
 
     int ensure_list() {
         if (!state_set) return fail(ESPP_ERR_STATE, "no state set");
+        if (d.mlp_on && mlp_bits.empty()) return fail(ESPP_ERR_STATE, "learned potential selected but no weights set");
         if (!cells_ready) return fail(ESPP_ERR_STATE, "call espp_build_neighbors first");
         int rcode = check_cutoffs();
         if (rcode) return rcode;
@@ -824,7 +886,7 @@ class System : public SystemBase {
             const int s0 = slot_of_gid[g];
             int64_t* out = cols + row_ptr[g];
             for (int k = 0; k < cnt[s0]; ++k)
-                out[k] = gid_of_slot[nb[4 * ((size_t)(k >> 2) * d.stride + s0) + (k & 3)]];
+                out[k] = gid_of_slot[nb[4 * ((size_t)(k >> 2) * d.stride + s0) + (k & 3)] & NBR_INDEX_MASK];
             std::sort(out, out + cnt[s0]);
         }
         return ESPP_OK;
@@ -1385,6 +1447,12 @@ int espp_set_step(espp_h h, int64_t step) {
 }
 int espp_set_interaction(espp_h h, int kind, int ta, int tb, const double* p, int64_t np) {
     return guarded(h, [&](espp::SystemBase& s) { return s.set_interaction(kind, ta, tb, p, np); });
+}
+int espp_mlp_set_weights(espp_h h, const uint16_t* bf16, int64_t n) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.mlp_set_weights(bf16, n); });
+}
+int espp_set_exclude_bonded(espp_h h, int on) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.set_exclude_bonded(on); });
 }
 int espp_set_mass(espp_h h, int type, double m) {
     return guarded(h, [&](espp::SystemBase& s) { return s.set_mass(type, m); });

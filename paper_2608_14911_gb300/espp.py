@@ -37,6 +37,8 @@ ESPP_LJ_CAPPED = 3
 ESPP_FENE = 4
 ESPP_TAB_PAIR = 5
 ESPP_TAB_BOND = 6
+ESPP_MLP = 7
+MLP_NPARAMS = 6337
 
 ERROR_NAMES = {
     ESPP_ERR_ARG: "ESPP_ERR_ARG", ESPP_ERR_CUDA: "ESPP_ERR_CUDA",
@@ -56,7 +58,8 @@ EXPORTS = (
     "espp_num_replicas", "espp_num_rebuilds", "espp_step", "espp_list_capacity",
     "espp_kernel_launches", "espp_langevin_noise", "espp_hilbert_ranks",
     "espp_set_kernel_timing", "espp_kernel_timing", "espp_set_graph_chunk", "espp_list_stats",
-    "espp_rdf_counts_noalloc", "espp_set_resort_interval",
+    "espp_rdf_counts_noalloc", "espp_set_resort_interval", "espp_mlp_set_weights",
+    "espp_set_exclude_bonded",
 )
 NOALLOC_MAX_BINS = 4096
 
@@ -133,6 +136,8 @@ def lib(path: str = LIB_PATH):
         "espp_list_stats": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i32)], ctypes.c_int),
         "espp_rdf_counts_noalloc": ([vp, i64, dp, ctypes.c_double, i32, vp, vp], ctypes.c_int),
         "espp_set_resort_interval": ([vp, i64], ctypes.c_int),
+        "espp_mlp_set_weights": ([vp, vp, i64], ctypes.c_int),
+        "espp_set_exclude_bonded": ([vp, ctypes.c_int], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -170,6 +175,17 @@ def espp_langevin_noise(seed, step, out_tensor, stream=0):
     n = out_tensor.numel() // 3
     _check(lib().espp_langevin_noise(seed, step, n, ctypes.c_void_p(out_tensor.data_ptr()),
                                      ctypes.c_void_p(stream)))
+
+
+def to_bf16_bits(a):
+    """float -> BF16 bit patterns (round to nearest even), as uint16."""
+    f = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    rounded = (f + 0x7FFF + ((f >> 16) & 1)) >> 16
+    return rounded.astype(np.uint16)
+
+
+def bf16_bits_to_float(b):
+    return (np.asarray(b, dtype=np.uint16).astype(np.uint32) << 16).view(np.float32).astype(np.float64)
 
 
 def espp_rdf_counts_noalloc(x_device, box, rmax, counts_device, stream=0):
@@ -288,6 +304,15 @@ class System:
         u = np.asarray(u, dtype=np.float64)
         f = np.asarray(f, dtype=np.float64)
         self.set_interaction(ESPP_TAB_BOND, 0, 0, [rmax, float(u.size)] + u.tolist() + f.tolist())
+
+    def set_mlp(self, rc, bf16_bits):
+        """Learned pair potential: cutoff rc and ESPP_MLP_NPARAMS BF16 weights."""
+        b = np.ascontiguousarray(bf16_bits, dtype=np.uint16)
+        self._c(lib().espp_mlp_set_weights(self._h, b.ctypes.data_as(ctypes.c_void_p), b.size))
+        self.set_interaction(ESPP_MLP, 0, 0, (rc,))
+
+    def set_exclude_bonded(self, on=True):
+        self._c(lib().espp_set_exclude_bonded(self._h, 1 if on else 0))
 
     def set_mass(self, t, m):
         self._c(lib().espp_set_mass(self._h, t, m))
