@@ -170,6 +170,32 @@ int espp_set_interaction(espp_h h, int kind, int type_a, int type_b, const doubl
 #define ESPP_MLP_NPARAMS 6337
 int espp_mlp_set_weights(espp_h h, const uint16_t* bf16, int64_t n);
 
+/* Current learned-potential weights (BF16 bit patterns, ESPP_MLP_NPARAMS). */
+int espp_mlp_get_weights(espp_h h, uint16_t* bf16, int64_t n);
+
+/* Force-matching training of the learned potential (spec learned CG
+ * model): frames_x and frames_f are device arrays of nframes x n x 3 doubles
+ * in id order, the site positions and the target forces for the pair
+ * potential (the mapped forces minus the bonded forces of this handle's bond
+ * potential).  Loss = mean over frames and sites of |F_pair + F_bond -
+ * F_target|^2.  Each epoch visits the frames in an order shuffled by
+ * shuffle_seed (splitmix64 Fisher-Yates) in batches of batch_frames; per
+ * batch the gradient is computed on the tensor cores (BF16 operands, FP32
+ * accumulation, deterministic reduction) and Adam (beta 0.9, 0.999, eps 1e-8,
+ * step lr) updates FP32 master weights whose BF16 rounding becomes the
+ * handle's weights.  loss_history[epochs] (host) receives the mean loss of
+ * each epoch (computed before each batch's update).  The handle's positions
+ * are overwritten. */
+int espp_mlp_train(espp_h h, const double* frames_x, const double* frames_f, int32_t nframes,
+                   int32_t batch_frames, int32_t epochs, double lr, uint64_t shuffle_seed,
+                   double* loss_history);
+
+/* The loss and its gradient for the current weights over all frames, without
+ * updating them: loss (host, 1 value) and grad (host, ESPP_MLP_NPARAMS - 1
+ * floats, the parameter order of the weights without b3). */
+int espp_mlp_loss_grad(espp_h h, const double* frames_x, const double* frames_f, int32_t nframes,
+                       double* loss, float* grad);
+
 /* Leave 1-2 bonded pairs out of the Verlet list (and so out of every pair
  * potential); default off, as Kremer-Grest keeps WCA between bonded beads. */
 int espp_set_exclude_bonded(espp_h h, int on);

@@ -56,6 +56,9 @@ def lib():
         L.orc_set_mlp.restype = ctypes.c_int
         L.orc_mlp_pair.argtypes = [ctypes.c_double, _dp, _dp, _dp, _dp]
         L.orc_set_exclude_bonded.argtypes = [ctypes.c_int]
+        L.orc_mlp_loss_grad.argtypes = [ctypes.c_int64, _dp, ctypes.c_int64, _dp, _dp, _i32p,
+                                        ctypes.c_int64, _i64p, _dp, _dp, _dp]
+        L.orc_mlp_loss_grad.restype = ctypes.c_int
         L.orc_forces_subset.argtypes = [ctypes.c_int64, _dp, _dp, _i32p, ctypes.c_int, _dp,
                                         ctypes.c_int64, _i64p, _dp, ctypes.c_int64, _i64p, _dp]
         L.orc_forces_subset.restype = ctypes.c_int
@@ -154,6 +157,25 @@ def mlp_pair(r, want_grad=False):
     if want_grad:
         return u.value, du.value, g, gu
     return u.value, du.value
+
+
+def mlp_loss_grad(model, box, frames_x, frames_y, types, bonds):
+    """Force-matching loss and its parameter gradient (pair potential = the
+    registered MLP, bonds as in `model`)."""
+    X = _f64(frames_x)
+    Y = _f64(frames_y)
+    nf = X.shape[0]
+    n = X.shape[1]
+    L = _f64(box)
+    t = np.ascontiguousarray(types, dtype=np.int32)
+    b = np.ascontiguousarray(bonds, dtype=np.int64).reshape(-1, 2)
+    loss = ctypes.c_double()
+    g = np.zeros(MLP_NPARAMS)
+    st = lib().orc_mlp_loss_grad(n, _p(L, _dp), nf, _p(X, _dp), _p(Y, _dp), _p(t, _i32p), b.shape[0],
+                                 _p(b, _i64p), _p(model.bond, _dp), ctypes.byref(loss), _p(g, _dp))
+    if st != 0:
+        raise RuntimeError("oracle loss failed (%d)" % st)
+    return loss.value, g
 
 
 def set_exclude_bonded(on):

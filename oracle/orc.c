@@ -719,6 +719,65 @@ int orc_forces_subset(int64_t n, const double* L, const double* x, const int32_t
     return broken ? -4 : 0;
 }
 
+/* Force-matching loss of the learned pair potential and its gradient
+ * (spec learned CG model; reading: mean squared force error over all
+ * frames and sites, the target being the mapped force minus the bonded
+ * force).  For frame f with positions X_f and targets Y_f:
+ *   e_i = F_pair,i(X_f) + F_bond,i(X_f) - Y_f,i,   loss = sum |e_i|^2 / (F n).
+ * F_pair,i = sum_j -u'(r_ij) r_ij_hat, so
+ *   d loss / d theta = sum_f sum_i sum_j -(2 / (F n)) (e_i . r_ij_hat)
+ *                      d u'(r_ij) / d theta,
+ * summed over ordered pairs with the exact parameter gradient of u'.  The
+ * pair interactions are those of orc_forces (with the current bonded
+ * exclusion setting); grad receives ORC_MLP_NPARAMS values. */
+int orc_mlp_loss_grad(int64_t n, const double* L, int64_t nframes, const double* X, const double* Y,
+                      const int32_t* type, int64_t nbonds, const int64_t* bonds,
+                      const double* bond_params, double* loss_out, double* grad) {
+    double pp[ORC_PAIR_STRIDE] = {4, 0, 0, orc_mlp_rc, 0, 0, 0, 0};
+    for (int k = 0; k < ORC_MLP_NPAR; ++k) grad[k] = 0.0;
+    double loss = 0.0;
+    double* f = (double*)malloc(sizeof(double) * (size_t)(3 * n + 3));
+    double* gtmp = (double*)malloc(sizeof(double) * ORC_MLP_NPAR);
+    adj_t adj;
+    adj_build(&adj, n, nbonds, bonds);
+    for (int64_t fr = 0; fr < nframes; ++fr) {
+        const double* x = X + 3 * n * fr;
+        const double* y = Y + 3 * n * fr;
+        double en[3];
+        int st = orc_forces(n, L, x, type, 1, pp, nbonds, bonds, bond_params, f, en);
+        if (st) {
+            free(f);
+            free(gtmp);
+            adj_free(&adj);
+            return st;
+        }
+        for (int64_t i = 0; i < 3 * n; ++i) {
+            f[i] -= y[i];
+            loss += f[i] * f[i];
+        }
+        /* pairs within the MLP cutoff, both orders, by brute force */
+        const double c = -2.0 / ((double)nframes * (double)n);
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t j = 0; j < n; ++j) {
+                if (j == i) continue;
+                if (orc_exclude_bonded && bonded_to(&adj, i, j)) continue;
+                double d[3];
+                min_image_vec(x + 3 * i, x + 3 * j, L, d);
+                double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                if (r2 >= orc_mlp_rc * orc_mlp_rc) continue;
+                double r = sqrt(r2), u, du;
+                double w = c * (f[3 * i] * d[0] + f[3 * i + 1] * d[1] + f[3 * i + 2] * d[2]) / r;
+                orc_mlp_pair(r, &u, &du, gtmp, NULL);
+                for (int k = 0; k < ORC_MLP_NPAR; ++k) grad[k] += w * gtmp[k];
+            }
+    }
+    *loss_out = loss / ((double)nframes * (double)n);
+    free(f);
+    free(gtmp);
+    adj_free(&adj);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Integrator                                                                */
 /* ------------------------------------------------------------------------ */

@@ -53,6 +53,12 @@ int orc_set_mlp(const double* par, int64_t npar, double rc);
 /* u(r), du/dr, and optionally d(du/dr)/dparams and du/dparams (NPARAMS each). */
 void orc_mlp_pair(double r, double* u, double* dudr, double* grad_dudr, double* grad_u);
 
+/* Force-matching loss of the learned potential over nframes frames
+ * (X, Y: nframes*n*3 positions and target forces) and its gradient. */
+int orc_mlp_loss_grad(int64_t n, const double* L, int64_t nframes, const double* X, const double* Y,
+                      const int32_t* type, int64_t nbonds, const int64_t* bonds,
+                      const double* bond_params, double* loss_out, double* grad);
+
 /* Exclude 1-2 bonded pairs from the pair interactions (default off). */
 void orc_set_exclude_bonded(int on);
 

@@ -17,31 +17,11 @@
 // sums -du/dr r_hat over them (full list, so no atomics) and writes the
 // particle's pair force, its pair-energy sum and its virial sum (each pair
 // counted from both ends, as the step kernel's own pair loop does).
-#include <cuda_bf16.h>
-
-#include "kernels.cuh"
+#include "mlp_common.cuh"
 
 namespace espp {
 
-constexpr int W1_LD = MLP_NB + 8;  // padded smem row strides (conflict-free B loads)
-constexpr int W2_LD = MLP_H + 8;
 constexpr int MLP_WARPS = 4;
-
-__device__ __forceinline__ unsigned int pack_bf16x2(float lo, float hi) {
-    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<const unsigned int*>(&v);
-}
-
-__device__ __forceinline__ void mma_bf16_16816(float c[4], const unsigned int a[4], unsigned int b0,
-                                               unsigned int b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-__device__ __forceinline__ float sigm(float z) { return 1.0f / (1.0f + __expf(-z)); }
 
 template <class T>
 __global__ void __launch_bounds__(32 * MLP_WARPS) k_mlp(DevSys<T> s, int cur) {
@@ -50,22 +30,11 @@ __global__ void __launch_bounds__(32 * MLP_WARPS) k_mlp(DevSys<T> s, int cur) {
     __shared__ float b1s[MLP_H], b2s[MLP_H], w3s[MLP_H];
     __shared__ float4 pairs[MLP_WARPS][32];  // compacted (r, dx, dy, dz) per warp
     const MlpWeights* __restrict__ W = s.mlp;
-    for (int e = threadIdx.x; e < MLP_H * MLP_NB; e += blockDim.x)
-        w1s[(e / MLP_NB) * W1_LD + e % MLP_NB] = W->W1[e];
-    for (int e = threadIdx.x; e < MLP_H * MLP_H; e += blockDim.x)
-        w2s[(e / MLP_H) * W2_LD + e % MLP_H] = W->W2[e];
-    for (int e = threadIdx.x; e < MLP_H; e += blockDim.x) {
-        b1s[e] = W->b1[e];
-        b2s[e] = W->b2[e];
-        w3s[e] = W->w3[e];
-    }
+    load_mlp_weights(W, w1s, w2s, nullptr, b1s, b2s, w3s);
     __syncthreads();
     if (s.ctrl->abort) return;
     const float b3 = W->b3;
     const float rc = W->rc, rc2 = rc * rc;
-    const float wid = rc / (MLP_NB - 1);
-    const float inv2w2 = 0.5f / (wid * wid), invw2 = 1.0f / (wid * wid);
-    const float pirc = 3.14159265358979f / rc;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, tig = lane & 3;
     const V4<T>* __restrict__ P = s.pos[cur];
@@ -115,42 +84,17 @@ __global__ void __launch_bounds__(32 * MLP_WARPS) k_mlp(DevSys<T> s, int cur) {
                     // rows g and g + 8 of the tile
                     const float ra = __shfl_sync(0xffffffffu, rr, g);
                     const float rb = __shfl_sync(0xffffffffu, rr, g + 8);
-                    const float fca = 0.5f * (__cosf(pirc * ra) + 1.f), fcb = 0.5f * (__cosf(pirc * rb) + 1.f);
-                    const float dfca = -0.5f * pirc * __sinf(pirc * ra), dfcb = -0.5f * pirc * __sinf(pirc * rb);
-                    // ---- layer 1 A operands: phi and dphi/dr in BF16 ------------
                     unsigned int aph[2][4], adp[2][4];
-#pragma unroll
-                    for (int kt = 0; kt < 2; ++kt) {
-#pragma unroll
-                        for (int half = 0; half < 2; ++half) {  // columns +0 / +8
-                            const int col = kt * 16 + half * 8 + tig * 2;
-                            float ph[2][2], dp[2][2];  // [row a/b][col, col+1]
-#pragma unroll
-                            for (int q = 0; q < 2; ++q) {
-                                const float mu = wid * (float)(col + q);
-                                const float da = ra - mu, db = rb - mu;
-                                const float ga = __expf(-da * da * inv2w2), gb = __expf(-db * db * inv2w2);
-                                ph[0][q] = ga * fca;
-                                ph[1][q] = gb * fcb;
-                                dp[0][q] = ga * (dfca - da * invw2 * fca);
-                                dp[1][q] = gb * (dfcb - db * invw2 * fcb);
-                            }
-                            aph[kt][2 * half + 0] = pack_bf16x2(ph[0][0], ph[0][1]);
-                            aph[kt][2 * half + 1] = pack_bf16x2(ph[1][0], ph[1][1]);
-                            adp[kt][2 * half + 0] = pack_bf16x2(dp[0][0], dp[0][1]);
-                            adp[kt][2 * half + 1] = pack_bf16x2(dp[1][0], dp[1][1]);
-                        }
-                    }
+                    rbf_fragments(ra, rb, rc, tig, aph, adp);
                     // ---- layer 1 GEMM, SiLU, re-packed as layer 2 A operands ----
                     unsigned int ah[4][4], adh[4][4];
 #pragma unroll
                     for (int nt = 0; nt < 8; ++nt) {
                         float z[4] = {0.f, 0.f, 0.f, 0.f}, dzv[4] = {0.f, 0.f, 0.f, 0.f};
-                        const __nv_bfloat16* wrow = w1s + (nt * 8 + g) * W1_LD + tig * 2;
 #pragma unroll
                         for (int kt = 0; kt < 2; ++kt) {
-                            const unsigned int b0 = *reinterpret_cast<const unsigned int*>(wrow + kt * 16);
-                            const unsigned int b1 = *reinterpret_cast<const unsigned int*>(wrow + kt * 16 + 8);
+                            unsigned int b0, b1;
+                            b_frag(w1s, W1_LD, nt * 8, kt * 16, g, tig, b0, b1);
                             mma_bf16_16816(z, aph[kt], b0, b1);
                             mma_bf16_16816(dzv, adp[kt], b0, b1);
                         }
@@ -174,11 +118,10 @@ __global__ void __launch_bounds__(32 * MLP_WARPS) k_mlp(DevSys<T> s, int cur) {
 #pragma unroll
                     for (int nt = 0; nt < 8; ++nt) {
                         float z[4] = {0.f, 0.f, 0.f, 0.f}, dzv[4] = {0.f, 0.f, 0.f, 0.f};
-                        const __nv_bfloat16* wrow = w2s + (nt * 8 + g) * W2_LD + tig * 2;
 #pragma unroll
                         for (int kt = 0; kt < 4; ++kt) {
-                            const unsigned int b0 = *reinterpret_cast<const unsigned int*>(wrow + kt * 16);
-                            const unsigned int b1 = *reinterpret_cast<const unsigned int*>(wrow + kt * 16 + 8);
+                            unsigned int b0, b1;
+                            b_frag(w2s, W2_LD, nt * 8, kt * 16, g, tig, b0, b1);
                             mma_bf16_16816(z, ah[kt], b0, b1);
                             mma_bf16_16816(dzv, adh[kt], b0, b1);
                         }

@@ -18,6 +18,16 @@
 #include "kernels.cuh"
 #include "philox.cuh"
 
+// Build-time tunables of the step kernel (FP32): int4 neighbour groups read
+// per batch, and the minimum resident blocks per SM the register budget is
+// fitted to.
+#ifndef ESPP_STEP_GB32
+#define ESPP_STEP_GB32 1
+#endif
+#ifndef ESPP_STEP_MINB32
+#define ESPP_STEP_MINB32 10
+#endif
+
 namespace espp {
 
 // 1/x: the hardware approximation in FP32 (error of order one ulp, far inside
@@ -52,6 +62,42 @@ __device__ __forceinline__ void pair_force(const PairRec<T>& pr, const T* __rest
     u = pr.eps4 * s6 * (s6 - T(1)) - pr.shift;
 }
 
+// One pair term: force (and energy, virial) of neighbour j at displacement d.
+template <class T, bool ENERGY, bool MULTI, bool FAST>
+__device__ __forceinline__ void pair_term(const DevSys<T>& s, int ti, const PairRec<T>* pr1, T dx, T dy,
+                                          T dz, int tj, T& fx, T& fy, T& fz, T& pe, T& vir) {
+    const T r2 = dx * dx + dy * dy + dz * dz;
+    if (FAST) {
+        // one type, plain Lennard-Jones: only rc^2, sigma^2, 24 eps live
+        if (r2 < pr1->rc2) {
+            const T inv_r2 = recip(r2);
+            const T s2 = pr1->sig2 * inv_r2;
+            const T s6 = s2 * s2 * s2;
+            const T fr = pr1->eps24 * s6 * (T(2) * s6 - T(1)) * inv_r2;
+            fx += fr * dx;
+            fy += fr * dy;
+            fz += fr * dz;
+            if (ENERGY) {
+                pe += pr1->eps4 * s6 * (s6 - T(1)) - pr1->shift;
+                vir += fr * r2;
+            }
+        }
+        return;
+    }
+    const PairRec<T>& pr = MULTI ? s.pair[ti * s.ntypes + tj] : *pr1;
+    if ((!MULTI || pr.kind != 0) && r2 < pr.rc2) {
+        T fr, u;
+        pair_force(pr, s.tab, r2, fr, u);
+        fx += fr * dx;
+        fy += fr * dy;
+        fz += fr * dz;
+        if (ENERGY) {
+            pe += u;
+            vir += fr * r2;
+        }
+    }
+}
+
 // Sum of the pair forces on particle i over its Verlet list.  The list is
 // read in batches of int4 groups: all indices of a batch first, then all
 // neighbour positions, then the arithmetic, so that each thread keeps several
@@ -61,7 +107,7 @@ __device__ __forceinline__ void pair_loop(const DevSys<T>& s, const V4<T>* __res
                                           const V4<T>& xi, int ti, const PairRec<T>* pr1,
                                           T L0, T L1, T L2, T& fx, T& fy, T& fz, T& pe, T& vir) {
     const T xim = xi.x - L0, yim = xi.y - L1, zim = xi.z - L2;
-    constexpr int GB = sizeof(T) == 4 ? 2 : 1;  // int4 groups per batch
+    constexpr int GB = sizeof(T) == 4 ? ESPP_STEP_GB32 : 1;  // int4 groups per batch
     const int ng = (n + 3) >> 2;
     const int4* __restrict__ nb = reinterpret_cast<const int4*>(s.nbr) + i;
     const size_t stride = (size_t)s.stride;
@@ -70,55 +116,40 @@ __device__ __forceinline__ void pair_loop(const DevSys<T>& s, const V4<T>* __res
 #pragma unroll
         for (int q = 0; q < GB; ++q) {
             // the first batch is read without waiting for the count (the list
-            // holds at least GB groups); entries past the count are masked
+            // holds at least GB groups); the last group is padded with -1 and
+            // groups past the count are dropped whole
             const bool want = g0 == 0 || g0 + q < ng;
-            const int4 a = want ? __ldg(nb + (g0 + q) * stride) : make_int4(-1, -1, -1, -1);
-            const int base = 4 * (g0 + q);
-            jj[4 * q + 0] = base + 0 < n ? a.x : -1;
-            jj[4 * q + 1] = base + 1 < n ? a.y : -1;
-            jj[4 * q + 2] = base + 2 < n ? a.z : -1;
-            jj[4 * q + 3] = base + 3 < n ? a.w : -1;
+            int4 a = want ? __ldg(nb + (g0 + q) * stride) : make_int4(-1, -1, -1, -1);
+            if (g0 + q >= ng) a = make_int4(-1, -1, -1, -1);
+            jj[4 * q + 0] = a.x;
+            jj[4 * q + 1] = a.y;
+            jj[4 * q + 2] = a.z;
+            jj[4 * q + 3] = a.w;
         }
+        int codes = 0;
+#pragma unroll
+        for (int q = 0; q < 4 * GB; ++q) codes |= jj[q] > NBR_INDEX_MASK ? jj[q] : 0;
         V4<T> xj[4 * GB];
 #pragma unroll
         for (int q = 0; q < 4 * GB; ++q) xj[q] = jj[q] >= 0 ? ld4<T>(P + nbr_slot(jj[q])) : xi;
+        if (codes == 0) {
+            // no pair of this batch crosses a face (the common case)
 #pragma unroll
-        for (int q = 0; q < 4 * GB; ++q) {
-            if (jj[q] < 0) continue;
-            const int code = nbr_code(jj[q]);
-            const T dx = shifted_diff(xi.x, xim, xj[q].x, L0, code & 3);
-            const T dy = shifted_diff(xi.y, yim, xj[q].y, L1, (code >> 2) & 3);
-            const T dz = shifted_diff(xi.z, zim, xj[q].z, L2, code >> 4);
-            if (FAST) {
-                // one type, plain Lennard-Jones: only rc^2, sigma^2, 24 eps live
-                const T r2 = dx * dx + dy * dy + dz * dz;
-                if (r2 < pr1->rc2) {
-                    const T inv_r2 = recip(r2);
-                    const T s2 = pr1->sig2 * inv_r2;
-                    const T s6 = s2 * s2 * s2;
-                    const T fr = pr1->eps24 * s6 * (T(2) * s6 - T(1)) * inv_r2;
-                    fx += fr * dx;
-                    fy += fr * dy;
-                    fz += fr * dz;
-                    if (ENERGY) {
-                        pe += pr1->eps4 * s6 * (s6 - T(1)) - pr1->shift;
-                        vir += fr * r2;
-                    }
-                }
-                continue;
+            for (int q = 0; q < 4 * GB; ++q) {
+                if (jj[q] < 0) continue;
+                pair_term<T, ENERGY, MULTI, FAST>(s, ti, pr1, xi.x - xj[q].x, xi.y - xj[q].y, xi.z - xj[q].z,
+                                                  bits_as_int(xj[q].w), fx, fy, fz, pe, vir);
             }
-            const PairRec<T>& pr = MULTI ? s.pair[ti * s.ntypes + bits_as_int(xj[q].w)] : *pr1;
-            const T r2 = dx * dx + dy * dy + dz * dz;
-            if ((!MULTI || pr.kind != 0) && r2 < pr.rc2) {
-                T fr, u;
-                pair_force(pr, s.tab, r2, fr, u);
-                fx += fr * dx;
-                fy += fr * dy;
-                fz += fr * dz;
-                if (ENERGY) {
-                    pe += u;
-                    vir += fr * r2;
-                }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4 * GB; ++q) {
+                if (jj[q] < 0) continue;
+                const int code = nbr_code(jj[q]);
+                const T dx = shifted_diff(xi.x, xim, xj[q].x, L0, code & 3);
+                const T dy = shifted_diff(xi.y, yim, xj[q].y, L1, (code >> 2) & 3);
+                const T dz = shifted_diff(xi.z, zim, xj[q].z, L2, code >> 4);
+                pair_term<T, ENERGY, MULTI, FAST>(s, ti, pr1, dx, dy, dz, bits_as_int(xj[q].w), fx, fy, fz,
+                                                  pe, vir);
             }
         }
     }
@@ -131,7 +162,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 template <class T, int MODE, bool ENERGY, bool FAST>
-__global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 6 : 4) k_step(DevSys<T> s, int cur, double* __restrict__ f_out,
+__global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? ESPP_STEP_MINB32 : 4) k_step(DevSys<T> s, int cur, double* __restrict__ f_out,
                                                unsigned long long next_cond) {
     Ctrl* c = s.ctrl;
     if (MODE != MODE_FORCES && c->abort) return;
@@ -215,7 +246,7 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 6 : 4) k_step(DevSys<T>
                             __threadfence();
                             one_m = T(1e-6);
                         }
-                        fr = -s.bond.K / one_m;
+                        fr = -s.bond.K * recip(one_m);
                         if (ENERGY) ub = -s.bond.halfKR02 * log(one_m);
                     } else {
                         T r = sqrt(r2), F;

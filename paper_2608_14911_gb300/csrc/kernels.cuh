@@ -120,6 +120,12 @@ template <class T> struct Launch {
     static void prologue(const DevSys<T>& s, int cur, int grid, cudaStream_t st);
     static void set_cond(const DevSys<T>& s, unsigned long long cond, cudaStream_t st);
     static void mlp(const DevSys<T>& s, int cur, cudaStream_t st);
+    // force-matching gradient of one frame (errors, tensor-core gradient,
+    // deterministic reduction into grad and the loss)
+    static int train_grad(const DevSys<T>& s, int cur, const double* Y, float4* err, double* loss_part,
+                          float scale, float* partials, int grad_blocks, float* grad, double* loss,
+                          cudaStream_t st);
+    static cudaError_t prepare_train();
     // state I/O (id-ordered double buffers on the device)
     static void set_state(const DevSys<T>& s, const double* x, const double* v, const int* img,
                           const int* types_by_gid, int cur, cudaStream_t st);
@@ -131,6 +137,10 @@ template <class T> struct Launch {
     static void rdf(const DevSys<T>& s, int cur, int rep, double rmax, int nbins,
                     unsigned long long* counts, cudaStream_t st);
 };
+
+void launch_adam(float* theta, float* m, float* v, float* grad, float lr, float b1, float b2, float eps,
+                 int step, MlpWeights* W, cudaStream_t st);
+int mlp_ngrad();
 
 void launch_noise(unsigned long long seed, long long step, long long n, double* out,
                   cudaStream_t st);

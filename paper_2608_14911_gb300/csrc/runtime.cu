@@ -43,6 +43,9 @@ struct SystemBase {
     virtual int set_mass(int type, double m) = 0;
     virtual int mlp_set_weights(const uint16_t* bits, int64_t n) = 0;
     virtual int set_exclude_bonded(int on) = 0;
+    virtual int mlp_get_weights(uint16_t* out, int64_t n) = 0;
+    virtual int mlp_train(const double* X, const double* Y, int nframes, int batch, int epochs, double lr,
+                          uint64_t seed, double* loss_hist, float* grad_out) = 0;
     virtual int build_neighbors(double rc, double skin) = 0;
     virtual int get_neighbors(int64_t* row_ptr, int64_t* cols, int64_t cap) = 0;
     virtual int compute_forces(double* f, int where) = 0;
@@ -633,6 +636,125 @@ class System : public SystemBase {
         if (!bits || n != MLP_NPARAMS) return fail(ESPP_ERR_ARG, "expected ESPP_MLP_NPARAMS BF16 weights");
         mlp_bits.assign(bits, bits + n);
         CK(upload_params());
+        f_valid = false;
+        return ESPP_OK;
+    }
+
+    int mlp_get_weights(uint16_t* out, int64_t n) override {
+        if (!out || n != MLP_NPARAMS) return fail(ESPP_ERR_ARG, "expected room for ESPP_MLP_NPARAMS weights");
+        if (mlp_bits.empty()) return fail(ESPP_ERR_STATE, "no weights set");
+        memcpy(out, mlp_bits.data(), sizeof(uint16_t) * MLP_NPARAMS);
+        return ESPP_OK;
+    }
+
+    // training state (allocated on first use)
+    float4* t_err = nullptr;
+    double* t_loss_part = nullptr;
+    float* t_partials = nullptr;
+    float *t_grad = nullptr, *t_theta = nullptr, *t_m = nullptr, *t_v = nullptr;
+    double* t_loss = nullptr;
+    int t_blocks = 0, t_epochs_alloc = 0, adam_step = 0;
+
+    static uint64_t splitmix64(uint64_t& x) {
+        uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+
+    // Force-matching training (epochs >= 1), or one loss and gradient
+    // evaluation of the current weights over all frames (epochs == 0).
+    int mlp_train(const double* X, const double* Y, int nframes, int batch, int epochs, double lr, uint64_t seed,
+                  double* loss_hist, float* grad_out) override {
+        if (!X || !Y || nframes < 1 || epochs < 0 || (epochs > 0 && (batch < 1 || !(lr > 0))))
+            return fail(ESPP_ERR_ARG, "bad training arguments");
+        if (!d.mlp_on || mlp_bits.empty()) return fail(ESPP_ERR_STATE, "select the learned potential and set weights first");
+        if (!cells_ready) return fail(ESPP_ERR_STATE, "call espp_build_neighbors first");
+        const int ngrad = mlp_ngrad();
+        const int nep = std::max(epochs, 1);
+        if (!t_err) {
+            t_blocks = std::max(1, std::min(d.ntiles, 152));
+            int rc0;
+            if ((rc0 = alloc(&t_err, (size_t)N, allocs)) || (rc0 = alloc(&t_loss_part, (size_t)d.ntiles, allocs)) ||
+                (rc0 = alloc(&t_partials, (size_t)t_blocks * ngrad, allocs)) || (rc0 = alloc(&t_grad, ngrad, allocs)) ||
+                (rc0 = alloc(&t_theta, ngrad, allocs)) || (rc0 = alloc(&t_m, ngrad, allocs)) ||
+                (rc0 = alloc(&t_v, ngrad, allocs)))
+                return rc0;
+            CK(Launch<T>::prepare_train());
+        }
+        if (t_epochs_alloc < nep) {
+            int rc0 = alloc(&t_loss, (size_t)nep, allocs);
+            if (rc0) return rc0;
+            t_epochs_alloc = nep;
+        }
+        // FP32 master weights from the current BF16 weights (all but b3)
+        {
+            std::vector<float> th(ngrad);
+            for (int k = 0; k < ngrad; ++k) {
+                const uint32_t b = (uint32_t)mlp_bits[k] << 16;
+                memcpy(&th[k], &b, 4);
+            }
+            CK(cudaMemcpy(t_theta, th.data(), ngrad * sizeof(float), cudaMemcpyHostToDevice));
+            CK(cudaMemset(t_m, 0, ngrad * sizeof(float)));
+            CK(cudaMemset(t_v, 0, ngrad * sizeof(float)));
+            CK(cudaMemset(t_grad, 0, ngrad * sizeof(float)));
+            CK(cudaMemset(t_loss, 0, nep * sizeof(double)));
+        }
+        adam_step = 0;
+        const size_t n3 = 3 * (size_t)N;
+        std::vector<int> order(nframes);
+        std::iota(order.begin(), order.end(), 0);
+        uint64_t rs = seed;
+        for (int ep = 0; ep < nep; ++ep) {
+            if (epochs > 0)
+                for (int k = nframes - 1; k > 0; --k) std::swap(order[k], order[splitmix64(rs) % (uint64_t)(k + 1)]);
+            const int bsz = epochs > 0 ? batch : nframes;
+            for (int b0 = 0; b0 < nframes; b0 += bsz) {
+                const int nb = std::min(bsz, nframes - b0);
+                const float scale = (float)(-2.0 / ((double)nb * (double)N));
+                for (int q = 0; q < nb; ++q) {
+                    const int f = order[b0 + q];
+                    int rcode = set_state(X + f * n3, nullptr, nullptr, ESPP_DEVICE);
+                    if (rcode) return rcode;
+                    rcode = rebuild_now(false);
+                    if (rcode) return rcode;
+                    Launch<T>::mlp(d, cur, st);
+                    launches += 1 + Launch<T>::train_grad(d, cur, Y + f * n3, t_err, t_loss_part, scale, t_partials,
+                                                          t_blocks, t_grad, t_loss + ep, st);
+                    CK(cudaGetLastError());
+                }
+                if (epochs > 0) {
+                    ++adam_step;
+                    launch_adam(t_theta, t_m, t_v, t_grad, (float)lr, 0.9f, 0.999f, 1e-8f, adam_step, d_mlp, st);
+                    launches++;
+                    CK(cudaGetLastError());
+                }
+            }
+        }
+        std::vector<double> lh(nep);
+        CK(cudaMemcpyAsync(lh.data(), t_loss, nep * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (grad_out && epochs == 0) CK(cudaMemcpyAsync(grad_out, t_grad, ngrad * sizeof(float), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (loss_hist)
+            for (int ep = 0; ep < nep; ++ep) loss_hist[ep] = lh[ep] / ((double)nframes * (double)N);
+        if (epochs > 0) {
+            // the trained BF16 weights become the handle's weights
+            MlpWeights w;
+            CK(cudaMemcpy(&w, d_mlp, sizeof(w), cudaMemcpyDeviceToHost));
+            auto bits = [](float v) {
+                uint32_t b;
+                memcpy(&b, &v, 4);
+                return (uint16_t)(b >> 16);  // these floats are BF16 values
+            };
+            const int o_b1 = MLP_H * MLP_NB, o_W2 = o_b1 + MLP_H, o_b2 = o_W2 + MLP_H * MLP_H, o_w3 = o_b2 + MLP_H;
+            memcpy(mlp_bits.data(), w.W1, sizeof(w.W1));
+            memcpy(mlp_bits.data() + o_W2, w.W2, sizeof(w.W2));
+            for (int a = 0; a < MLP_H; ++a) {
+                mlp_bits[o_b1 + a] = bits(w.b1[a]);
+                mlp_bits[o_b2 + a] = bits(w.b2[a]);
+                mlp_bits[o_w3 + a] = bits(w.w3[a]);
+            }
+        }
         f_valid = false;
         return ESPP_OK;
     }
@@ -1450,6 +1572,21 @@ int espp_set_interaction(espp_h h, int kind, int ta, int tb, const double* p, in
 }
 int espp_mlp_set_weights(espp_h h, const uint16_t* bf16, int64_t n) {
     return guarded(h, [&](espp::SystemBase& s) { return s.mlp_set_weights(bf16, n); });
+}
+int espp_mlp_get_weights(espp_h h, uint16_t* bf16, int64_t n) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.mlp_get_weights(bf16, n); });
+}
+int espp_mlp_train(espp_h h, const double* frames_x, const double* frames_f, int32_t nframes,
+                   int32_t batch_frames, int32_t epochs, double lr, uint64_t shuffle_seed, double* loss_history) {
+    return guarded(h, [&](espp::SystemBase& s) {
+        return s.mlp_train(frames_x, frames_f, nframes, batch_frames, epochs, lr, shuffle_seed, loss_history, nullptr);
+    });
+}
+int espp_mlp_loss_grad(espp_h h, const double* frames_x, const double* frames_f, int32_t nframes, double* loss,
+                       float* grad) {
+    return guarded(h, [&](espp::SystemBase& s) {
+        return s.mlp_train(frames_x, frames_f, nframes, 0, 0, 0.0, 0, loss, grad);
+    });
 }
 int espp_set_exclude_bonded(espp_h h, int on) {
     return guarded(h, [&](espp::SystemBase& s) { return s.set_exclude_bonded(on); });

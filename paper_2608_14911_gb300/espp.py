@@ -59,7 +59,7 @@ EXPORTS = (
     "espp_kernel_launches", "espp_langevin_noise", "espp_hilbert_ranks",
     "espp_set_kernel_timing", "espp_kernel_timing", "espp_set_graph_chunk", "espp_list_stats",
     "espp_rdf_counts_noalloc", "espp_set_resort_interval", "espp_mlp_set_weights",
-    "espp_set_exclude_bonded",
+    "espp_set_exclude_bonded", "espp_mlp_get_weights", "espp_mlp_train", "espp_mlp_loss_grad",
 )
 NOALLOC_MAX_BINS = 4096
 
@@ -138,6 +138,9 @@ def lib(path: str = LIB_PATH):
         "espp_set_resort_interval": ([vp, i64], ctypes.c_int),
         "espp_mlp_set_weights": ([vp, vp, i64], ctypes.c_int),
         "espp_set_exclude_bonded": ([vp, ctypes.c_int], ctypes.c_int),
+        "espp_mlp_get_weights": ([vp, vp, i64], ctypes.c_int),
+        "espp_mlp_train": ([vp, vp, vp, i32, i32, i32, ctypes.c_double, ctypes.c_uint64, vp], ctypes.c_int),
+        "espp_mlp_loss_grad": ([vp, vp, vp, i32, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -310,6 +313,28 @@ class System:
         b = np.ascontiguousarray(bf16_bits, dtype=np.uint16)
         self._c(lib().espp_mlp_set_weights(self._h, b.ctypes.data_as(ctypes.c_void_p), b.size))
         self.set_interaction(ESPP_MLP, 0, 0, (rc,))
+
+    def mlp_weights(self):
+        out = np.zeros(MLP_NPARAMS, dtype=np.uint16)
+        self._c(lib().espp_mlp_get_weights(self._h, out.ctypes.data_as(ctypes.c_void_p), MLP_NPARAMS))
+        return out
+
+    def mlp_train(self, frames_x, frames_f, batch_frames, epochs, lr, seed=4):
+        """frames_x, frames_f: CUDA float64 tensors (nframes, n, 3)."""
+        loss = np.zeros(epochs)
+        self._c(lib().espp_mlp_train(self._h, ctypes.c_void_p(frames_x.data_ptr()),
+                                     ctypes.c_void_p(frames_f.data_ptr()), frames_x.shape[0], batch_frames,
+                                     epochs, lr, seed, loss.ctypes.data_as(ctypes.c_void_p)))
+        return loss
+
+    def mlp_loss_grad(self, frames_x, frames_f):
+        loss = np.zeros(1)
+        grad = np.zeros(MLP_NPARAMS - 1, dtype=np.float32)
+        self._c(lib().espp_mlp_loss_grad(self._h, ctypes.c_void_p(frames_x.data_ptr()),
+                                         ctypes.c_void_p(frames_f.data_ptr()), frames_x.shape[0],
+                                         loss.ctypes.data_as(ctypes.c_void_p),
+                                         grad.ctypes.data_as(ctypes.c_void_p)))
+        return float(loss[0]), grad.astype(np.float64)
 
     def set_exclude_bonded(self, on=True):
         self._c(lib().espp_set_exclude_bonded(self._h, 1 if on else 0))

@@ -96,3 +96,72 @@ def test_mlp_requires_weights():
     s.build_neighbors(RC, SKIN)
     with pytest.raises(espp.EsppError):
         s.compute_forces()
+
+
+def _frames(c, nframes, seed, noise=0.25):
+    g = np.random.default_rng(seed)
+    X = np.stack([I.f32(np.mod(c.x + g.normal(0, noise, c.x.shape), c.box)) for _ in range(nframes)])
+    X[X >= c.box] = 0.0
+    return X
+
+
+def test_mlp_training_gradient_matches_oracle():
+    import torch
+    c = _cg_system(16, 25, seed=21)
+    bits, wd = _weights(3)
+    rmax, ub, fb = _bond_table()
+    X = _frames(c, 2, 22)
+    Y = np.random.default_rng(23).normal(0, 1.0, X.shape)
+    s = espp.System(c.box, c.n, c.types, c.bonds, precision=espp.ESPP_FP32, seed=5)
+    s.set_mlp(RC, bits)
+    s.set_table_bond(rmax, ub, fb)
+    s.set_exclude_bonded(True)
+    s.set_state(X[0], None, None)
+    s.build_neighbors(RC, SKIN)
+    loss, grad = s.mlp_loss_grad(torch.tensor(X, device="cuda"), torch.tensor(Y, device="cuda"))
+    O.set_mlp(wd, RC)
+    O.set_table(8, rmax, ub, fb)
+    O.set_exclude_bonded(True)
+    try:
+        lo, go = O.mlp_loss_grad(O.Model(1, {}, ("table", 8)), c.box, X, Y, c.types, c.bonds)
+    finally:
+        O.set_exclude_bonded(False)
+    go = go[:-1]  # b3 has no gradient
+    assert abs(loss - lo) <= 2e-2 * lo
+    assert np.linalg.norm(grad - go) <= 5e-2 * np.linalg.norm(go), np.linalg.norm(grad - go) / np.linalg.norm(go)
+    # each block of parameters separately
+    for lo_, hi_ in ((0, 2048), (2048, 2112), (2112, 6208), (6208, 6272), (6272, 6336)):
+        ref = go[lo_:hi_]
+        assert np.linalg.norm(grad[lo_:hi_] - ref) <= 8e-2 * np.linalg.norm(ref) + 1e-9, (lo_, hi_)
+
+
+def test_mlp_training_is_deterministic_and_learns_a_known_potential():
+    import torch
+    # targets: forces of a smooth repulsive pair potential (a fine table)
+    c = I.random_positions(500, (13.5, 13.5, 13.5), seed=31)
+    rt = np.linspace(0.0, RC, 4096)
+    fc = 0.5 * (np.cos(np.pi * rt / RC) + 1)
+    ut = 3.0 * np.exp(-1.5 * rt) * fc
+    dfc = -0.5 * np.pi / RC * np.sin(np.pi * rt / RC)
+    ft = -(3.0 * (-1.5) * np.exp(-1.5 * rt) * fc + 3.0 * np.exp(-1.5 * rt) * dfc)
+    O.set_table(10, RC, ut, ft)
+    tmodel = O.Model(1, {(0, 0): ("table", 10, RC)})
+    X = _frames(c, 8, 32, noise=0.6)
+    Y = np.stack([O.forces(tmodel, c.box, x, c.types, c.bonds)[0] for x in X])
+    bits, _ = _weights(4)
+    Xd, Yd = torch.tensor(X, device="cuda"), torch.tensor(Y, device="cuda")
+    runs = []
+    for _ in range(2):
+        s = espp.System(c.box, c.n, c.types, c.bonds, precision=espp.ESPP_FP32, seed=5)
+        s.set_mlp(RC, bits)
+        s.set_state(X[0])
+        s.build_neighbors(RC, SKIN)
+        loss = s.mlp_train(Xd, Yd, batch_frames=4, epochs=150, lr=2e-3, seed=9)
+        runs.append((loss, s.mlp_weights()))
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+    loss = runs[0][0]
+    assert loss[-1] < 0.05 * loss[0], (loss[0], loss[-1])
+    # the trained network reproduces the target forces
+    s.set_state(X[1])
+    f = s.compute_forces()
+    assert rel_rms(f, Y[1]) < 0.25

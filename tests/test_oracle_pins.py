@@ -522,3 +522,33 @@ def test_bonded_exclusion_removes_exactly_the_bonded_pairs():
         f_back[a] += fr * d
         f_back[b] -= fr * d
     assert np.abs(f_back - f_all).max() < 1e-10 * np.abs(f_all).max()
+
+
+def test_force_matching_gradient_by_finite_differences():
+    # the loss gradient equals central differences of the loss itself
+    c = I.kg_lattice(4, 25, density=0.2125, seed=12, jitter=0.3)
+    g = np.random.default_rng(13)
+    X = np.stack([np.mod(c.x + g.normal(0, 0.2, c.x.shape), c.box) for _ in range(2)])
+    Y = g.normal(0, 1.0, X.shape)
+    p = _mlp_params(7, 0.2)
+    O.set_mlp(p, 3.5)
+    rb = np.linspace(0.0, 4.0, 401)
+    O.set_table(9, 4.0, 5.0 * (rb - 2.0) ** 2, -10.0 * (rb - 2.0))
+    model = O.Model(1, {}, ("table", 9))
+    O.set_exclude_bonded(True)
+    try:
+        loss, grad = O.mlp_loss_grad(model, c.box, X, Y, c.types, c.bonds)
+        h = 1e-6
+        for k in (5, 2050, 3000, 6210, 6300):
+            q = p.copy()
+            q[k] += h
+            O.set_mlp(q, 3.5)
+            lp, _ = O.mlp_loss_grad(model, c.box, X, Y, c.types, c.bonds)
+            q[k] -= 2 * h
+            O.set_mlp(q, 3.5)
+            lm, _ = O.mlp_loss_grad(model, c.box, X, Y, c.types, c.bonds)
+            fd = (lp - lm) / (2 * h)
+            assert abs(grad[k] - fd) < 1e-6 * max(1.0, abs(fd)), (k, grad[k], fd)
+    finally:
+        O.set_exclude_bonded(False)
+        O.set_mlp(p, 3.5)
