@@ -46,6 +46,14 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=1024)
     ap.add_argument("--direct", action="store_true",
                     help="launch every kernel directly instead of through CUDA graphs (for ncu)")
+    ap.add_argument("--no-suite", action="store_true",
+                    help="skip the secondary workloads (4M LJ, 512 replicas, learned CG)")
+    ap.add_argument("--suite-steps", type=int, default=1000)
+    ap.add_argument("--cg-frames", type=int, default=32)
+    ap.add_argument("--cg-epochs", type=int, default=10)
+    ap.add_argument("--cg-batch", type=int, default=4)
+    ap.add_argument("--cg-probe", type=int, default=0,
+                    help="only: N-site CG system with the learned potential, a few force evaluations (for ncu)")
     ap.add_argument("--quick-start", action="store_true",
                     help="lattice start with a short equilibration (for profiler runs)")
     return ap.parse_args()
@@ -145,11 +153,13 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # the system
 # ---------------------------------------------------------------------------
-def make_melt(a, seed, precision):
+def make_melt(a, seed, precision, nchains=None, nbeads=None):
     """KG melt: random-walk chains, soft push-off with a growing force cap,
     then plain WCA; falls back to an overlap-free lattice start."""
     from paper_2608_14911_gb300 import espp, inputs
-    cfg = inputs.kg_random_walk(a.nchains, a.nbeads, density=0.85, seed=seed, bond=0.97)
+    nchains = a.nchains if nchains is None else nchains
+    nbeads = a.nbeads if nbeads is None else nbeads
+    cfg = inputs.kg_random_walk(nchains, nbeads, density=0.85, seed=seed, bond=0.97)
     v = inputs.maxwell_velocities(cfg.n, 1.0, seed=seed)
     s = espp.System(cfg.box, cfg.n, cfg.types, cfg.bonds, precision=precision, seed=seed)
     s.set_fene(30.0, 1.5)
@@ -168,7 +178,8 @@ def make_melt(a, seed, precision):
         s.integrate(1000, 0.005, 1.0, 1.0)
     except espp.EsppError:
         start = "lattice"
-        cfg = inputs.kg_lattice(a.nchains, a.nbeads, density=0.85, seed=seed)
+        s.close()
+        cfg = inputs.kg_lattice(nchains, nbeads, density=0.85, seed=seed)
         s = espp.System(cfg.box, cfg.n, cfg.types, cfg.bonds, precision=precision, seed=seed)
         s.set_fene(30.0, 1.5)
         s.set_wca(1.0, 1.0)
@@ -410,6 +421,21 @@ def run_ours(a):
                "sample": "%d oracle steps of the full %d-bead melt, %.1f s" % (k, n, secs),
                "cpu": cpu_model(), "host_cores": host_cores()}
 
+    suite = None
+    if not a.no_suite and world == 1:
+        suite = {}
+        for name, fn in (("lj4m", lambda o: o.update(suite_lj4m(a, barrier, peaks))),
+                         ("batched512", lambda o: o.update(suite_batched(a, barrier))),
+                         ("learned_cg", lambda o: suite_learned_cg(a, barrier, o))):
+            part = {}
+            t0 = time.perf_counter()
+            try:
+                fn(part)
+            except Exception as exc:  # reported, never hidden; partial results kept
+                part["error"] = "%s: %s" % (type(exc).__name__, exc)
+            part["wall_s"] = time.perf_counter() - t0
+            suite[name] = part
+
     ws_mb = alg_bytes / 1e6
     line = {
         "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
@@ -431,6 +457,7 @@ def run_ours(a):
         "e2e": e2e,
         "gpu_launches": gpu_launches,
         "clocks": clocks,
+        "suite": suite,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -440,8 +467,275 @@ def run_ours(a):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# secondary workloads (reported under "suite")
+# ---------------------------------------------------------------------------
+def _timed(s, steps, dt, gamma, kT, sync):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    sync()
+    e0.record()
+    s.integrate(steps, dt, gamma, kT)
+    e1.record()
+    sync()
+    return e0.elapsed_time(e1)
+
+
+def _step_kernel_ms(s, dt, gamma, kT, steps=256):
+    s.set_kernel_timing(True)
+    for _ in range(max(1, steps // 64)):
+        s.integrate(64, dt, gamma, kT)
+    kt = s.kernel_timing(reset=True)
+    s.set_kernel_timing(False)
+    return kt["step_ms"] / max(1, kt["step_launches"]), kt["rebuild_ms"] / max(1, kt["steps"])
+
+
+def suite_lj4m(a, sync, peaks):
+    """4,194,304-particle LJ fluid: fcc 128x128x64 at density 0.8442, Maxwell
+    T = 0.72, rc 2.5 (shifted), skin 0.3, Langevin gamma 1 at T = 0.72."""
+    from paper_2608_14911_gb300 import espp, inputs
+    cfg = inputs.lj_fcc(128, 128, 64, density=0.8442)
+    v = inputs.maxwell_velocities(cfg.n, 0.72, seed=42)
+    out = {"workload": "lj_fluid_4194304_fcc_rho0.8442_T0.72_rc2.5_skin0.3", "n_particles": cfg.n}
+    for prec, steps in ((espp.ESPP_FP32, a.suite_steps), (espp.ESPP_FP64, max(50, a.suite_steps // 10))):
+        s = espp.System(cfg.box, cfg.n, cfg.types, cfg.bonds, precision=prec, seed=42)
+        s.set_lj(1.0, 1.0, 2.5, True)
+        s.set_state(cfg.x, v, cfg.img)
+        s.build_neighbors(2.5, 0.3)
+        s.integrate(100, 0.005, 1.0, 0.72)
+        rb0 = s.n_rebuilds
+        ms = _timed(s, steps, 0.005, 1.0, 0.72, sync)
+        key = "fp32" if prec == espp.ESPP_FP32 else "fp64"
+        out[key] = {"value": cfg.n * steps / (ms / 1e3), "unit": "particle-steps/s", "steps": steps,
+                    "ms_per_step": ms / steps, "rebuilds": s.n_rebuilds - rb0}
+        if prec == espp.ESPP_FP32:
+            total, _ = s.list_stats()
+            k_ms, rb_ms = _step_kernel_ms(s, 0.005, 1.0, 0.72)
+            byt = step_kernel_bytes(cfg.n, total, 1) - 8 * cfg.n  # no bonds
+            out[key]["step_kernel"] = {"avg_launch_ms": k_ms, "algorithmic_bytes": byt,
+                                       "achieved_gbs": byt / (k_ms * 1e-3) / 1e9,
+                                       "frac_of_measured_hbm": byt / (k_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                                       "mean_list_entries": total / cfg.n,
+                                       "rebuild_node_ms_per_step": rb_ms}
+        s.close()
+    out["fp32_speedup_vs_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
+    return out
+
+
+def suite_batched(a, sync):
+    """512 independent KG melts of uneven size (chains uniform 10-400, length
+    uniform 20-200, density 0.85), one seed each, stepped together."""
+    from paper_2608_14911_gb300 import espp, inputs
+    sizes = inputs.replica_sizes(512, seed=42)
+    cfgs = [inputs.kg_random_walk(nc, nb, density=0.85, seed=42 + r) for r, (nc, nb) in enumerate(sizes)]
+    reps = [dict(box=c.box, n=c.n, types=c.types, bonds=c.bonds, seed=42 + r) for r, c in enumerate(cfgs)]
+    s = espp.System(replicas=reps, precision=espp.ESPP_FP32)
+    n = s.n
+    x = np.concatenate([c.x for c in cfgs])
+    img = np.concatenate([c.img for c in cfgs])
+    v = inputs.maxwell_velocities(n, 1.0, seed=7)
+    s.set_fene(30.0, 1.5)
+    s.set_lj_capped(1.0, 1.0, WCA_RC, 1.05)
+    s.set_state(x, v, img)
+    s.build_neighbors(WCA_RC, 0.4)
+    for cap in (1.05, 1.0, 0.95, 0.9, 0.85, 0.8):
+        s.set_lj_capped(1.0, 1.0, WCA_RC, cap)
+        s.integrate(400, 1e-3, 1.0, 1.0)
+    s.set_wca(1.0, 1.0)
+    s.integrate(1000, 0.002, 1.0, 1.0)
+    s.integrate(200, 0.005, 1.0, 1.0)
+    rb0 = s.n_rebuilds
+    l0 = s.kernel_launches
+    steps = a.suite_steps
+    ms = _timed(s, steps, 0.005, 1.0, 1.0, sync)
+    obs = s.observables()
+    temps = np.array([o["temperature"] for o in obs])
+    out = {"workload": "kg_batched_512_replicas_chains10-400_len20-200_rho0.85", "replicas": 512,
+           "n_particles": n, "min_replica": min(s.rep_n), "max_replica": max(s.rep_n),
+           "value": n * steps / (ms / 1e3), "unit": "particle-steps/s", "steps": steps,
+           "ms_per_step": ms / steps, "rebuild_passes": s.n_rebuilds - rb0,
+           "kernel_launches_per_step": (s.kernel_launches - l0) / steps,
+           "temperature_mean_over_replicas": float(temps.mean())}
+    s.close()
+    return out
+
+
+def _bond_table_boltzmann(xs, nchains, sites_per_chain, box, kT=1.0, dr=0.02, rmax=6.0):
+    """Boltzmann-inverted CG bond potential from mapped frames:
+    U(b) = -kT ln(P(b) / b^2), F = -dU/db, linearly extrapolated outside the
+    sampled range, on a grid from 0 to rmax."""
+    b = []
+    for x in xs:
+        x = x.reshape(nchains, sites_per_chain, 3)
+        d = x[:, 1:] - x[:, :-1]
+        d -= box * np.round(d / box)
+        b.append(np.linalg.norm(d, axis=2).ravel())
+    b = np.concatenate(b)
+    edges = np.arange(0.0, rmax + dr, dr)
+    hist, _ = np.histogram(b, bins=edges)
+    centres = 0.5 * (edges[1:] + edges[:-1])
+    ok = hist > 0
+    U = np.full(centres.size, np.nan)
+    U[ok] = -kT * np.log(hist[ok] / (centres[ok] ** 2))
+    idx = np.nonzero(ok)[0]
+    lo, hi = idx[0], idx[-1]
+    U = np.interp(centres, centres[ok], U[ok])
+    # linear extrapolation with the edge slopes (restoring at both ends)
+    sl = min((U[lo + 2] - U[lo]) / (2 * dr), -1.0)
+    sh = max((U[hi] - U[hi - 2]) / (2 * dr), 1.0)
+    U[:lo] = U[lo] + sl * (centres[:lo] - centres[lo])
+    U[hi + 1:] = U[hi] + sh * (centres[hi + 1:] - centres[hi])
+    grid = np.linspace(0.0, rmax, 1201)
+    Ug = np.interp(grid, centres, U, left=U[0] + sl * (0 - centres[0]))
+    Fg = -np.gradient(Ug, grid)
+    return rmax, Ug - Ug.min(), Fg, float(b.mean())
+
+
+def suite_learned_cg(a, sync, out):
+    """Learned CG: a fine KG melt of 2000 chains x 200 beads is mapped 4:1 onto
+    100k sites every 200 steps; the CG bond table comes from Boltzmann
+    inversion; the MLP pair potential is force-matched on the frames; then a
+    4M-site CG melt runs with the MLP on the tensor cores and with the same
+    potential tabulated.  Results go into `out` as they are measured, and
+    `out["stage"]` names the part that ran last."""
+    import torch
+    from paper_2608_14911_gb300 import espp, inputs
+    # ---- fine run and frames --------------------------------------------------
+    out["stage"] = "fine melt"
+    nch, nb, bps = 2000, 200, 4
+    f, cfg, start = make_melt(a, 42, espp.ESPP_FP32, nchains=nch, nbeads=nb)
+    f.integrate(1000, 0.005, 1.0, 1.0)
+    out["fine_start"] = start
+    ns = cfg.n // bps
+    F = a.cg_frames
+    X = torch.zeros((F, ns, 3), dtype=torch.float64, device="cuda")
+    Y = torch.zeros_like(X)
+    for k in range(F):
+        f.integrate(200, 0.005, 1.0, 1.0)
+        f.cg_map(bps, X[k], Y[k])
+    f.close()
+    out["stage"] = "training"
+    sites_per_chain = nb // bps
+    rmax, ub, fb, bmean = _bond_table_boltzmann(X.cpu().numpy(), nch, sites_per_chain, cfg.box)
+    cg_bonds = inputs.chain_bonds(nch, sites_per_chain)
+    # ---- training -------------------------------------------------------------
+    RCM, SKIN = 3.5, 0.5
+    g = np.random.default_rng(4)
+    lim1, lim2, lim3 = np.sqrt(6 / (32 + 64)), np.sqrt(6 / 128), np.sqrt(6 / 65)
+    w0 = np.concatenate([g.uniform(-lim1, lim1, 64 * 32), np.zeros(64), g.uniform(-lim2, lim2, 64 * 64),
+                         np.zeros(64), g.uniform(-lim3, lim3, 64), [0.0]])
+    bits = espp.to_bf16_bits(w0)
+    c = espp.System(cfg.box, ns, None, cg_bonds, precision=espp.ESPP_FP32, seed=43)
+    c.set_mlp(RCM, bits)
+    c.set_table_bond(rmax, ub, fb)
+    c.set_exclude_bonded(True)
+    c.set_state(X[0].cpu().numpy())
+    c.build_neighbors(RCM, SKIN)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    sync()
+    e0.record()
+    loss = c.mlp_train(X, Y, batch_frames=a.cg_batch, epochs=a.cg_epochs, lr=1e-3, seed=4)
+    e1.record()
+    sync()
+    train_ms = e0.elapsed_time(e1)
+    trained = c.mlp_weights()
+    out["training"] = {"workload": "kg_2000x200_mapped_4to1_100000_sites", "frames": F, "frames_spec": 2000,
+                       "epochs": a.cg_epochs, "batch_frames": a.cg_batch,
+                       "adam_steps": a.cg_epochs * (-(-F // a.cg_batch)), "s_per_epoch": train_ms / 1e3 / a.cg_epochs,
+                       "s_per_epoch_per_frame": train_ms / 1e3 / a.cg_epochs / F,
+                       "loss_first_epoch": float(loss[0]), "loss_last_epoch": float(loss[-1]),
+                       "cg_mean_bond": bmean}
+    c.close()
+    # ---- 4M CG sites: MLP on tensor cores vs the same potential tabulated -----
+    out["stage"] = "4M CG melt"
+    cg = inputs.kg_lattice(16000, 250, density=0.2125, seed=44, jitter=0.1)
+    rt = np.linspace(0.0, RCM, 4096)
+    # the trained potential sampled for the table (a function of r only)
+    tab_sys = espp.System(np.array([20.0, 20.0, 20.0]), 2, None, None, precision=espp.ESPP_FP64)
+    tab_sys.set_mlp(RCM, trained)
+    ut, ft = np.zeros(rt.size), np.zeros(rt.size)
+    xs2 = np.zeros((2, 3))
+    for k, r in enumerate(rt):
+        xs2[0] = (5.0, 5.0, 5.0)
+        xs2[1] = (5.0 + max(r, 1e-3), 5.0, 5.0)
+        tab_sys.set_state(xs2)
+        if k == 0:
+            tab_sys.build_neighbors(RCM, SKIN)
+        fr = tab_sys.compute_forces()
+        ft[k] = fr[1, 0]  # F = -dU/dr on the particle at larger x
+        ut[k] = tab_sys.observables()["pe_pair"]
+    tab_sys.close()
+    res = {}
+    forces = {}
+    for mode in ("mlp", "table"):
+        out["stage"] = "4M CG melt, " + mode
+        s = espp.System(cg.box, cg.n, None, cg.bonds, precision=espp.ESPP_FP32, seed=45)
+        if mode == "mlp":
+            s.set_mlp(RCM, trained)
+        else:
+            s.set_table_pair(RCM, ut, ft)
+        s.set_table_bond(rmax, ub, fb)
+        s.set_exclude_bonded(True)
+        s.set_state(cg.x, inputs.maxwell_velocities(cg.n, 1.0, seed=46), cg.img)
+        s.build_neighbors(RCM, SKIN)
+        forces[mode] = s.compute_forces()
+        s.integrate(20, 0.005, 1.0, 1.0)
+        steps = 100 if mode == "mlp" else 500
+        ms = _timed(s, steps, 0.005, 1.0, 1.0, sync)
+        counts = s.rdf_counts(3.5, 175)
+        res[mode] = {"value": cg.n * steps / (ms / 1e3), "unit": "site-steps/s", "steps": steps,
+                     "ms_per_step": ms / steps, "fine_bead_equivalent": 4 * cg.n * steps / (ms / 1e3)}
+        res[mode]["_rdf"] = counts
+        s.close()
+    dr = 0.02
+    def gofr(cnt):
+        rr = (np.arange(cnt.size) + 0.5) * dr
+        shell = 4 * np.pi * rr ** 2 * dr
+        rho = cg.n / np.prod(cg.box)
+        return cnt / (0.5 * cg.n * rho * shell)
+    ga, gb = gofr(res["mlp"].pop("_rdf")), gofr(res["table"].pop("_rdf"))
+    out["cg4m"] = {"workload": "cg_melt_16000x250_4000000_sites_rho0.2125", "n_sites": cg.n,
+                   "mlp": res["mlp"], "table": res["table"],
+                   "force_rel_rms_mlp_vs_table": float(np.sqrt(((forces["mlp"] - forces["table"]) ** 2).sum()
+                                                               / (forces["table"] ** 2).sum())),
+                   "rdf_l2_mlp_vs_table": float(np.sqrt(((ga - gb) ** 2).sum() * dr / 3.5)),
+                   "rdf_note": "after 120 (MLP) / 520 (table) steps from the same start"}
+    out["stage"] = "done"
+
+
+def run_cg_probe(a):
+    """A CG melt of a.cg_probe sites (density 0.2125, chains of 250) with a
+    random learned potential and a tabulated bond: five force evaluations."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2608_14911_gb300 import espp, inputs
+    nch = max(1, a.cg_probe // 250)
+    cg = inputs.kg_lattice(nch, 250, density=0.2125, seed=44, jitter=0.1)
+    rng = np.random.default_rng(4)
+    w = np.concatenate([rng.normal(0, 0.18, 64 * 32), np.zeros(64), rng.normal(0, 0.125, 64 * 64), np.zeros(64),
+                        rng.normal(0, 0.06, 64), [0.0]])
+    s = espp.System(cg.box, cg.n, None, cg.bonds, precision=espp.ESPP_FP32, seed=1)
+    s.set_mlp(3.5, espp.to_bf16_bits(w))
+    rb = np.linspace(0.0, 4.0, 801)
+    s.set_table_bond(4.0, 5.0 * (rb - 2.0) ** 2, -10.0 * (rb - 2.0))
+    s.set_exclude_bonded(True)
+    s.set_state(cg.x, None, cg.img)
+    s.build_neighbors(3.5, 0.5)
+    out = torch.zeros((cg.n, 3), dtype=torch.float64, device="cuda")
+    for _ in range(5):
+        s.compute_forces(out)
+    torch.cuda.synchronize()
+    print(json.dumps({"cg_probe_sites": cg.n}))
+    return 0
+
+
 def main():
     a = parse()
+    if a.cg_probe:
+        return run_cg_probe(a)
     if a.impl == "reference":
         return run_reference(a)
     return run_ours(a)

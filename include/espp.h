@@ -170,6 +170,13 @@ int espp_set_interaction(espp_h h, int kind, int type_a, int type_b, const doubl
 #define ESPP_MLP_NPARAMS 6337
 int espp_mlp_set_weights(espp_h h, const uint16_t* bf16, int64_t n);
 
+/* Coarse-graining map for learned-CG training data: site k is the centre of
+ * mass of beads [b k, b k + b) (b = beads_per_site, consecutive ids; equal
+ * masses) of the unwrapped positions, wrapped into replica 0's box, and its
+ * force is the sum of the beads' conservative forces.  x_sites, f_sites:
+ * device arrays of (n / b) x 3 doubles.  Synchronises. */
+int espp_cg_map(espp_h h, int32_t beads_per_site, double* x_sites, double* f_sites);
+
 /* Current learned-potential weights (BF16 bit patterns, ESPP_MLP_NPARAMS). */
 int espp_mlp_get_weights(espp_h h, uint16_t* bf16, int64_t n);
 
@@ -243,7 +250,9 @@ int espp_observables_batch(espp_h h, espp_obs_t* out, int32_t R);
 
 /* Unique-pair distance histogram of replica `replica` for r < rmax in nbins
  * equal bins (counts[nbins], host).  rmax must be below half the smallest
- * box edge. */
+ * box edge.  Pairs come from the Verlet list when rmax <= rc + skin (with 1-2
+ * exclusions on, bonded pairs are then not counted), else from all pairs of
+ * the replica (limited to 200000 particles). */
 int espp_rdf_counts(espp_h h, int32_t replica, double rmax, int32_t nbins, int64_t* counts);
 
 /* ---- checkpoint ------------------------------------------------------------ */

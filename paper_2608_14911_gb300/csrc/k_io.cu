@@ -181,6 +181,73 @@ __global__ void __launch_bounds__(256) k_rdf(DevSys<T> s, int cur, int rep, T rm
         if (hist[b]) atomicAdd(&counts[b], (unsigned long long)hist[b]);
 }
 
+// Unique pairs within rmax from the Verlet list (rmax <= list cutoff): each
+// pair appears in both lists, counted from the lower storage slot.
+template <class T>
+__global__ void __launch_bounds__(256) k_rdf_list(DevSys<T> s, int cur, int rep, T rmax2, double inv_dr, int nbins,
+                                                  unsigned long long* __restrict__ counts) {
+    extern __shared__ unsigned int hist[];
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    const RepGeom<T>& g = s.reps[rep];
+    const V4<T>* __restrict__ P = s.pos[cur];
+    const size_t stride = (size_t)s.stride;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < g.n; q += gridDim.x * blockDim.x) {
+        const int i = g.p_off + q;
+        const V4<T> xi = P[i];
+        const int n = s.nbr_cnt[i];
+        for (int k = 0; k < n; ++k) {
+            const int e = s.nbr[4 * ((size_t)(k >> 2) * stride + i) + (k & 3)];
+            const int j = nbr_slot(e);
+            if (j < i) continue;
+            const V4<T> xj = P[j];
+            const int code = nbr_code(e);
+            const T dx = shifted_diff(xi.x, xi.x - g.L[0], xj.x, g.L[0], code & 3);
+            const T dy = shifted_diff(xi.y, xi.y - g.L[1], xj.y, g.L[1], (code >> 2) & 3);
+            const T dz = shifted_diff(xi.z, xi.z - g.L[2], xj.z, g.L[2], code >> 4);
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < rmax2) {
+                int b = (int)(sqrt((double)r2) * inv_dr);
+                if (b >= nbins) b = nbins - 1;
+                atomicAdd(&hist[b], 1u);
+            }
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x)
+        if (hist[b]) atomicAdd(&counts[b], (unsigned long long)hist[b]);
+}
+
+// Coarse-graining map (4:1 style): site k is the centre of mass of beads
+// [bps k, bps k + bps) of the id-ordered unwrapped positions, wrapped into the
+// box; its force is the sum of the beads' forces.
+__global__ void k_cg_map(const double* __restrict__ x, const int* __restrict__ img, const double* __restrict__ f,
+                         long long nsites, int bps, double L0, double L1, double L2, double* __restrict__ xs,
+                         double* __restrict__ fs) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nsites) return;
+    const double L[3] = {L0, L1, L2};
+    for (int d = 0; d < 3; ++d) {
+        double c = 0.0, fsum = 0.0;
+        for (int b = 0; b < bps; ++b) {
+            const long long i = k * bps + b;
+            c += x[3 * i + d] + (double)img[3 * i + d] * L[d];
+            fsum += f[3 * i + d];
+        }
+        c /= bps;
+        c -= L[d] * floor(c / L[d]);
+        if (c >= L[d]) c -= L[d];
+        xs[3 * k + d] = c;
+        fs[3 * k + d] = fsum;
+    }
+}
+
+void launch_cg_map(const double* x, const int* img, const double* f, long long nsites, int bps, const double* L,
+                   double* xs, double* fs, cudaStream_t st) {
+    if (nsites <= 0) return;
+    k_cg_map<<<(unsigned int)((nsites + 255) / 256), 256, 0, st>>>(x, img, f, nsites, bps, L[0], L[1], L[2], xs, fs);
+}
+
 __global__ void k_noise(unsigned long long seed, long long step, long long n, double* out) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -223,6 +290,15 @@ void Launch<T>::rdf(const DevSys<T>& s, int cur, int rep, double rmax, int nbins
     k_rdf<T><<<4 * 152, 256, sizeof(unsigned int) * nbins, st>>>(s, cur, rep, (T)(rmax * rmax),
                                                                  nbins / rmax, nbins, counts);
 }
+
+template <class T>
+void Launch<T>::rdf_list(const DevSys<T>& s, int cur, int rep, double rmax, int nbins,
+                         unsigned long long* counts, cudaStream_t st) {
+    k_rdf_list<T><<<8 * 152, 256, sizeof(unsigned int) * nbins, st>>>(s, cur, rep, (T)(rmax * rmax),
+                                                                      nbins / rmax, nbins, counts);
+}
+template void Launch<float>::rdf_list(const DevSys<float>&, int, int, double, int, unsigned long long*, cudaStream_t);
+template void Launch<double>::rdf_list(const DevSys<double>&, int, int, double, int, unsigned long long*, cudaStream_t);
 
 void launch_noise(unsigned long long seed, long long step, long long n, double* out,
                   cudaStream_t st) {

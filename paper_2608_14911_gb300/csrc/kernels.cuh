@@ -136,11 +136,16 @@ template <class T> struct Launch {
                     const int* mol_rep, int nmol, double* mol_rg2, cudaStream_t st);
     static void rdf(const DevSys<T>& s, int cur, int rep, double rmax, int nbins,
                     unsigned long long* counts, cudaStream_t st);
+    static void rdf_list(const DevSys<T>& s, int cur, int rep, double rmax, int nbins,
+                         unsigned long long* counts, cudaStream_t st);
 };
 
 void launch_adam(float* theta, float* m, float* v, float* grad, float lr, float b1, float b2, float eps,
                  int step, MlpWeights* W, cudaStream_t st);
 int mlp_ngrad();
+
+void launch_cg_map(const double* x, const int* img, const double* f, long long nsites, int bps, const double* L,
+                   double* xs, double* fs, cudaStream_t st);
 
 void launch_noise(unsigned long long seed, long long step, long long n, double* out,
                   cudaStream_t st);

@@ -44,6 +44,7 @@ struct SystemBase {
     virtual int mlp_set_weights(const uint16_t* bits, int64_t n) = 0;
     virtual int set_exclude_bonded(int on) = 0;
     virtual int mlp_get_weights(uint16_t* out, int64_t n) = 0;
+    virtual int cg_map(int bps, double* xs, double* fs) = 0;
     virtual int mlp_train(const double* X, const double* Y, int nframes, int batch, int epochs, double lr,
                           uint64_t seed, double* loss_hist, float* grad_out) = 0;
     virtual int build_neighbors(double rc, double skin) = 0;
@@ -140,6 +141,7 @@ class System : public SystemBase {
         if (nbr_alloc) cudaFree(nbr_alloc);
         if (cell_list_alloc) cudaFree(cell_list_alloc);
         if (tab_alloc) cudaFree(tab_alloc);
+        if (d_hist) cudaFree(d_hist);
         for (void* p : allocs) cudaFree(p);
     }
 
@@ -640,6 +642,24 @@ class System : public SystemBase {
         return ESPP_OK;
     }
 
+    // positions and conservative forces mapped onto sites of bps consecutive
+    // beads (device outputs; replica 0's box)
+    int cg_map(int bps, double* xs, double* fs) override {
+        if (bps < 1 || N % bps != 0 || !xs || !fs) return fail(ESPP_ERR_ARG, "bad mapping arguments");
+        double* fdev = nullptr;
+        CK(cudaMalloc(&fdev, 3 * (size_t)N * sizeof(double)));
+        int rcode = compute_forces(fdev, ESPP_DEVICE);
+        if (!rcode) {
+            Launch<T>::get_state(d, d_io_x, nullptr, d_io_img, cur, st);
+            launch_cg_map(d_io_x, d_io_img, fdev, N / bps, bps, box.data(), xs, fs, st);
+            launches += 2;
+            cudaError_t e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) rcode = fail(ESPP_ERR_CUDA, cudaGetErrorString(e));
+        }
+        cudaFree(fdev);
+        return rcode;
+    }
+
     int mlp_get_weights(uint16_t* out, int64_t n) override {
         if (!out || n != MLP_NPARAMS) return fail(ESPP_ERR_ARG, "expected room for ESPP_MLP_NPARAMS weights");
         if (mlp_bits.empty()) return fail(ESPP_ERR_STATE, "no weights set");
@@ -973,7 +993,7 @@ class System : public SystemBase {
     }
 
     int status_from(const Ctrl& c) {
-        if (c.err & ERRBIT_BOND) return fail(ESPP_ERR_BOND_BROKEN, "a FENE bond reached r >= R0");
+        if (c.err & ERRBIT_BOND) return fail(ESPP_ERR_BOND_BROKEN, "a bond reached r >= R0 (FENE) or the end of its table (tabulated)");
         if (c.err & ERRBIT_NONFINITE) return fail(ESPP_ERR_NONFINITE, "a position became non-finite or left the box");
         if (c.err & ERRBIT_TIMEOUT) return fail(ESPP_ERR_TIMEOUT, "a device wait timed out");
         if (c.err & ERRBIT_OVERFLOW) return fail(ESPP_ERR_LIST_OVERFLOW, "Verlet list overflow");
@@ -1280,12 +1300,23 @@ class System : public SystemBase {
         if (hist_cap < nbins) {
             if (d_hist) cudaFree(d_hist);
             d_hist = nullptr;
+            hist_cap = 0;
             CK(cudaMalloc(&d_hist, nbins * sizeof(unsigned long long)));
-            allocs.push_back(d_hist);
             hist_cap = nbins;
         }
         CK(cudaMemsetAsync(d_hist, 0, nbins * sizeof(unsigned long long), st));
-        Launch<T>::rdf(d, cur, rep, rmax, nbins, d_hist, st);
+        // from the Verlet list when it reaches far enough (with 1-2
+        // exclusions on, bonded pairs are then not counted), else all pairs
+        const double rl = rc_list + skin;
+        bool use_list = false;
+        if (cells_ready && rmax <= rl) {
+            int rcode = ensure_list();
+            if (rcode) return rcode;
+            use_list = true;
+        }
+        if (use_list) Launch<T>::rdf_list(d, cur, rep, rmax, nbins, d_hist, st);
+        else if (rep_n[rep] > 200000) return fail(ESPP_ERR_ARG, "all-pairs histogram of a replica this large; use rmax <= rc + skin");
+        else Launch<T>::rdf(d, cur, rep, rmax, nbins, d_hist, st);
         launches++;
         CK(cudaGetLastError());
         std::vector<unsigned long long> h(nbins);
@@ -1499,6 +1530,9 @@ static thread_local std::string g_create_error;
 template <class F>
 static int guarded(espp_h h, F&& f) {
     if (!h || !h->impl) return ESPP_ERR_ARG;
+    // a failed runtime call elsewhere in this thread leaves a non-sticky
+    // "last error" behind; drop it so launch checks see only our launches
+    (void)cudaGetLastError();
     try {
         return f(*h->impl);
     } catch (const std::exception& e) {
@@ -1572,6 +1606,9 @@ int espp_set_interaction(espp_h h, int kind, int ta, int tb, const double* p, in
 }
 int espp_mlp_set_weights(espp_h h, const uint16_t* bf16, int64_t n) {
     return guarded(h, [&](espp::SystemBase& s) { return s.mlp_set_weights(bf16, n); });
+}
+int espp_cg_map(espp_h h, int32_t beads_per_site, double* x_sites, double* f_sites) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.cg_map(beads_per_site, x_sites, f_sites); });
 }
 int espp_mlp_get_weights(espp_h h, uint16_t* bf16, int64_t n) {
     return guarded(h, [&](espp::SystemBase& s) { return s.mlp_get_weights(bf16, n); });

@@ -60,6 +60,7 @@ EXPORTS = (
     "espp_set_kernel_timing", "espp_kernel_timing", "espp_set_graph_chunk", "espp_list_stats",
     "espp_rdf_counts_noalloc", "espp_set_resort_interval", "espp_mlp_set_weights",
     "espp_set_exclude_bonded", "espp_mlp_get_weights", "espp_mlp_train", "espp_mlp_loss_grad",
+    "espp_cg_map",
 )
 NOALLOC_MAX_BINS = 4096
 
@@ -141,6 +142,7 @@ def lib(path: str = LIB_PATH):
         "espp_mlp_get_weights": ([vp, vp, i64], ctypes.c_int),
         "espp_mlp_train": ([vp, vp, vp, i32, i32, i32, ctypes.c_double, ctypes.c_uint64, vp], ctypes.c_int),
         "espp_mlp_loss_grad": ([vp, vp, vp, i32, vp, vp], ctypes.c_int),
+        "espp_cg_map": ([vp, i32, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -313,6 +315,11 @@ class System:
         b = np.ascontiguousarray(bf16_bits, dtype=np.uint16)
         self._c(lib().espp_mlp_set_weights(self._h, b.ctypes.data_as(ctypes.c_void_p), b.size))
         self.set_interaction(ESPP_MLP, 0, 0, (rc,))
+
+    def cg_map(self, beads_per_site, x_out, f_out):
+        """Map onto sites of consecutive beads into CUDA float64 tensors."""
+        self._c(lib().espp_cg_map(self._h, beads_per_site, ctypes.c_void_p(x_out.data_ptr()),
+                                  ctypes.c_void_p(f_out.data_ptr())))
 
     def mlp_weights(self):
         out = np.zeros(MLP_NPARAMS, dtype=np.uint16)

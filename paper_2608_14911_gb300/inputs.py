@@ -90,18 +90,13 @@ def kg_random_walk(nchains: int, nbeads: int, density: float = 0.85, seed: int =
 def snake_sites(m: int) -> np.ndarray:
     """Sites of an m^3 simple cubic grid in boustrophedon order: consecutive
     sites are always face neighbours."""
-    out = np.empty((m * m * m, 3), dtype=np.int64)
-    k = 0
-    row = 0
-    for z in range(m):
-        ys = range(m) if z % 2 == 0 else range(m - 1, -1, -1)
-        for y in ys:
-            xs = range(m) if row % 2 == 0 else range(m - 1, -1, -1)
-            for x in xs:
-                out[k] = (x, y, z)
-                k += 1
-            row += 1
-    return out
+    z = np.repeat(np.arange(m), m * m)
+    yi = np.tile(np.repeat(np.arange(m), m), m)          # row index inside a plane
+    y = np.where(z % 2 == 0, yi, m - 1 - yi)
+    row = z * m + yi                                      # global row counter
+    xi = np.tile(np.arange(m), m * m)
+    x = np.where(row % 2 == 0, xi, m - 1 - xi)
+    return np.stack([x, y, z], axis=1).astype(np.int64)
 
 
 def kg_lattice(nchains: int, nbeads: int, density: float = 0.85, seed: int = 42,

@@ -433,3 +433,32 @@ def test_full_size_lj_4m_sampled_forces():
     fo = O.forces_subset(case.model, c.box, c.x, c.types, c.bonds, sel)
     assert rel_rms(f[sel], fo) <= 1e-5
     s.close()
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_rdf_from_list_equals_all_pairs(prec):
+    case = lj_case((6, 6, 6))
+    s = case.system(prec)
+    a = s.rdf_counts(2.5, 50)  # within rc + skin: from the Verlet list
+    b = s.rdf_counts(4.5, 90)[:50]  # beyond it: all pairs, the same bins below 2.5
+    if prec == FP64:
+        assert np.array_equal(a, b)
+    else:
+        assert np.abs(a - b).max() <= 2 and abs(int(a.sum()) - int(b.sum())) <= 2
+
+
+def test_cg_map_matches_numpy_mapping():
+    import torch
+    case = kg_case(20, 48, seed=3)
+    s = case.system(FP32)
+    s.integrate(50, 0.005, 1.0, 1.0)
+    x, v, img = s.get_state()
+    f = s.compute_forces()
+    xs = torch.zeros((case.cfg.n // 4, 3), dtype=torch.float64, device="cuda")
+    fs = torch.zeros_like(xs)
+    s.cg_map(4, xs, fs)
+    box = case.cfg.box
+    u = (x + img * box).reshape(-1, 4, 3).mean(axis=1)
+    u = np.mod(u, box)
+    assert np.abs(xs.cpu().numpy() - u).max() < 1e-9
+    assert np.abs(fs.cpu().numpy() - f.reshape(-1, 4, 3).sum(axis=1)).max() < 1e-9
