@@ -297,6 +297,18 @@ int espp_list_stats(espp_h h, int64_t* total_entries, int32_t* max_count);
  * not depend on how a run is split into calls. */
 int espp_set_resort_interval(espp_h h, int64_t steps);
 
+/* Cell sub-decomposition for the Verlet build (paper "Performance
+ * optimizations": cells of rc/2 cut the volume searched per particle).
+ * w = 1: cells of edge >= rc + skin and a 3x3x3 stencil; w = 2: cells of edge
+ * >= (rc + skin) / 2 and a 5x5x5 stencil; w = 0 (default): chosen at each
+ * espp_build_neighbors, 2 when a full cell holds ten or more particles on
+ * average (and every edge holds 5 half cells), else 1.  w = 1 needs 3 cells
+ * along every edge of every replica and w = 2 needs 5 (ESPP_ERR_BOX_TOO_SMALL
+ * otherwise).  The list itself (its set of pairs) does not depend on w.
+ * Takes effect at once when a grid exists (the list is rebuilt), else at the
+ * next espp_build_neighbors.  ESPP_ERR_ARG unless 0 <= w <= 2. */
+int espp_set_cell_subdivision(espp_h h, int32_t w);
+
 /* Steps captured per CUDA graph replay in espp_integrate (default 64).  0
  * launches every kernel directly instead (no graphs; for profilers, which do
  * not see kernels inside conditional graphs). */

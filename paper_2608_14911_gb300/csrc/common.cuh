@@ -209,7 +209,7 @@ struct Ctrl {
     unsigned int need_cap;     // largest neighbour count seen by an overflowing build
     unsigned int n_rebuilds;   // rebuild passes executed (any replica)
     unsigned int max_count;    // largest neighbour count of the last build
-    unsigned int need_capc;    // largest cell occupancy seen by an overflowing binning
+    unsigned int pad;
 };
 
 enum : unsigned int {
@@ -217,7 +217,6 @@ enum : unsigned int {
     ERRBIT_BOND = 2u,
     ERRBIT_NONFINITE = 4u,
     ERRBIT_TIMEOUT = 8u,
-    ERRBIT_CELL = 16u,
 };
 
 constexpr int TILE = 128;          // particles per tile (= threads per block)

@@ -6,12 +6,14 @@
 //
 // Every rebuild (inside the step graphs, when a replica asked for it):
 //   prep      latch the per-replica requests, clear those replicas' cell counts
-//   bin       cell of every particle; the particle's position and storage slot
-//             go to an atomic slot of its cell's fixed-capacity entry array
+//   bin       cell of every particle and its arrival index (atomic histogram)
+//   scan x3   exclusive scan of the counts in cell-index order: first entry of
+//             every cell in one compact entry array (no per-cell capacity)
+//   place     every particle's entry (position, storage slot) into its cell
 //   cellsort  entries of each cell in ascending storage slot, so the list does
 //             not depend on the order of the atomics
-//   verlet    27-cell search from the cell entries (contiguous, no further
-//             indirection), full list (both directions) as groups of four
+//   verlet    stencil search from the cell entries, streamed as contiguous
+//             row ranges; full list (both directions) as groups of four
 //             indices, nbr4[g * stride + i]; records the build positions
 // A resort (launched between step graphs every `resort_every` steps, and on
 // every explicit build) additionally runs, between cellsort and verlet:
@@ -20,7 +22,9 @@
 //             cell); the entries switch to the new slots
 //   gather    permuted copies of positions, velocities, forces, images
 //   copyback  copies back and maps bond partners to their new slots
-// Replicas whose request flag is clear skip every step after `prep`.
+// Replicas whose request flag is clear skip every per-particle and per-cell
+// step after `prep`; their counts and entries stay those of their last build,
+// so the global scan keeps every replica's entries in its own slot range.
 #include "kernels.cuh"
 
 namespace espp {
@@ -58,6 +62,9 @@ __global__ void __launch_bounds__(256) k_prep(DevSys<T> s) {
     }
 }
 
+// Cell of every particle of a flagged replica and its arrival index in that
+// cell (counting-sort histogram); positions are wrapped into the box here,
+// at list builds only.
 template <class T>
 __global__ void __launch_bounds__(TILE) k_bin(DevSys<T> s, int cur) {
     if (s.ctrl->abort) return;
@@ -71,7 +78,6 @@ __global__ void __launch_bounds__(TILE) k_bin(DevSys<T> s, int cur) {
         if (!s.now[tl.rep] || (int)threadIdx.x >= tl.count) continue;
         const int i = tl.start + threadIdx.x;
         V4<T> p = P[i];
-        // positions are wrapped into the box at list builds only
         const RepGeom<T>& g = s.reps[tl.rep];
         const int wx = wrap_coord(p.x, g.L[0]), wy = wrap_coord(p.y, g.L[1]), wz = wrap_coord(p.z, g.L[2]);
         if (wx | wy | wz) {
@@ -83,26 +89,36 @@ __global__ void __launch_bounds__(TILE) k_bin(DevSys<T> s, int cur) {
             s.img[i] = im;
         }
         const int h = cell_of(g, p);
-        const int slot = atomicAdd(&s.cell_cnt[h], 1);
-        if (slot < s.capc) {
-            p.w = int_bits_as(T(0), i);
-            s.cell_xyz[(size_t)h * s.capc + slot] = p;
-        } else {
-            atomicMax(&s.ctrl->need_capc, (unsigned int)(slot + 1));
-            atomicOr(&s.ctrl->err, ERRBIT_CELL);
-            s.ctrl->abort = 1;
-        }
+        s.cellh[i] = h;
+        s.in_cell[i] = atomicAdd(&s.cell_cnt[h], 1);
     }
 }
 
-// Entries of each cell in ascending storage slot (a handful per cell).
+// Entry (wrapped position, storage slot in the w lane) of every particle of a
+// flagged replica at its cell's first entry + its arrival index.
+template <class T>
+__global__ void __launch_bounds__(TILE) k_place(DevSys<T> s, int cur) {
+    if (s.ctrl->abort) return;
+    const V4<T>* __restrict__ P = s.pos[cur];
+    for (int t = blockIdx.x; t < s.ntiles; t += gridDim.x) {
+        const Tile tl = s.tiles[t];
+        if (!s.now[tl.rep] || (int)threadIdx.x >= tl.count) continue;
+        const int i = tl.start + threadIdx.x;
+        V4<T> p = ld4<T>(P + i);
+        p.w = int_bits_as(T(0), i);
+        s.cell_ent[s.cell_beg[s.cellh[i]] + s.in_cell[i]] = p;
+    }
+}
+
+// Entries of each cell in ascending storage slot (a handful per cell), so the
+// list does not depend on the order of the atomics.
 template <class T>
 __global__ void __launch_bounds__(256) k_cellsort(DevSys<T> s) {
     if (s.ctrl->abort) return;
     for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < s.ncells; h += gridDim.x * blockDim.x) {
         if (!s.now[s.cell_rep[h]]) continue;
-        V4<T>* p = s.cell_xyz + (size_t)h * s.capc;
-        const int e = min(s.cell_cnt[h], s.capc);
+        V4<T>* p = s.cell_ent + s.cell_beg[h];
+        const int e = s.cell_beg[h + 1] - s.cell_beg[h];
         for (int k = 1; k < e; ++k) {
             const V4<T> key = p[k];
             const int kk = bits_as_int(key.w);
@@ -147,14 +163,20 @@ __device__ __forceinline__ int block_excl_scan(int v, int* excl_out) {
     return total;
 }
 
-template <class T>
+// RANK = false: cells in index order -> cell_beg (every rebuild);
+// RANK = true: cells in Hilbert-rank order -> rank_start (resort only).
+template <class T, bool RANK>
+__device__ __forceinline__ int scan_count(const DevSys<T>& s, int k) {
+    return k < s.ncells ? s.cell_cnt[RANK ? s.cell_by_rank[k] : k] : 0;
+}
+
+template <class T, bool RANK>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(DevSys<T> s) {
     if (s.ctrl->abort) return;
     const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
     int sum = 0;
 #pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; ++k)
-        if (base + k < s.ncells) sum += s.cell_cnt[s.cell_by_rank[base + k]];
+    for (int k = 0; k < SCAN_ITEMS; ++k) sum += scan_count<T, RANK>(s, base + k);
     int excl;
     const int total = block_excl_scan(sum, &excl);
     if (threadIdx.x == 0) s.scan_part[blockIdx.x] = total;
@@ -174,7 +196,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_top(DevSys<T> s) {
     }
 }
 
-template <class T>
+template <class T, bool RANK>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(DevSys<T> s) {
     if (s.ctrl->abort) return;
     const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
@@ -182,29 +204,31 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(DevSys<T> s) {
     int sum = 0;
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k) {
-        v[k] = base + k < s.ncells ? s.cell_cnt[s.cell_by_rank[base + k]] : 0;
+        v[k] = scan_count<T, RANK>(s, base + k);
         sum += v[k];
     }
     int excl;
     block_excl_scan(sum, &excl);
     int run = s.scan_part[blockIdx.x] + excl;
+    int* out = RANK ? s.rank_start : s.cell_beg;
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k) {
-        if (base + k < s.ncells) s.cell_start[base + k] = run;
+        if (base + k < s.ncells) out[base + k] = run;
         run += v[k];
     }
 }
 
 // ---- resort ------------------------------------------------------------------
-// Entry k of the cell of rank h moves to slot start[h] + k; the entry follows.
+// Entry k of the cell of rank h moves to slot rank_start[h] + k; the entry
+// follows.
 template <class T>
 __global__ void __launch_bounds__(256) k_resort_scatter(DevSys<T> s) {
     if (s.ctrl->abort) return;
     for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < s.ncells; h += gridDim.x * blockDim.x) {
         const int c = s.cell_by_rank[h];
         if (!s.now[s.cell_rep[c]]) continue;
-        V4<T>* p = s.cell_xyz + (size_t)c * s.capc;
-        const int b = s.cell_start[h], e = min(s.cell_cnt[c], s.capc);
+        V4<T>* p = s.cell_ent + s.cell_beg[c];
+        const int b = s.rank_start[h], e = s.cell_beg[c + 1] - s.cell_beg[c];
         for (int k = 0; k < e; ++k) {
             s.perm[b + k] = bits_as_int(p[k].w);
             p[k].w = int_bits_as(T(0), b + k);
@@ -252,102 +276,133 @@ __global__ void __launch_bounds__(TILE) k_copyback(DevSys<T> s, int cur, int per
 }
 
 // ---- Verlet list ----------------------------------------------------------------
-// One thread per particle.  The 27 neighbour cells are visited as three planes
-// of nine; the nine counts of a plane are loaded together, then each cell's
-// entries (position and slot, contiguous) are streamed with no further
-// indirection.  Hits are packed into int4 groups in registers and stored as
-// whole 16-byte groups, so the stores of a warp are contiguous.
-template <class T>
-__global__ void __launch_bounds__(TILE) k_verlet(DevSys<T> s, int cur) {
-    if (s.ctrl->abort) return;
-    __shared__ int smax;
-    const V4<T>* __restrict__ P = s.pos[cur];
-    for (int t = blockIdx.x; t < s.ntiles; t += gridDim.x) {
-        const Tile tl = s.tiles[t];
-        if (!s.now[tl.rep]) continue;  // uniform over the block
-        if (threadIdx.x == 0) smax = 0;
-        __syncthreads();
-        if ((int)threadIdx.x < tl.count) {
-            const RepGeom<T>& g = s.reps[tl.rep];
-            const int i = tl.start + threadIdx.x;
-            const V4<T> xi = ld4<T>(P + i);
-            s.xb[i] = xi;
-            const int nc0 = g.nc[0], nc1 = g.nc[1], nc2 = g.nc[2];
-            const int cx = cell_coord(xi.x, g.cells_per_len[0], nc0);
-            const int cy = cell_coord(xi.y, g.cells_per_len[1], nc1);
-            const int cz = cell_coord(xi.z, g.cells_per_len[2], nc2);
-            const int xm = cx == 0 ? nc0 - 1 : cx - 1, xp = cx == nc0 - 1 ? 0 : cx + 1;
-            const int ym = cy == 0 ? nc1 - 1 : cy - 1, yp = cy == nc1 - 1 ? 0 : cy + 1;
-            const T L0 = g.L[0], L1 = g.L[1], L2 = g.L[2];
-            const T xim = xi.x - L0, yim = xi.y - L1, zim = xi.z - L2;
-            const T rl2 = s.rlist2;
-            const int cap = s.cap, capc = s.capc;
-            const size_t stride = (size_t)s.stride;
-            int4* __restrict__ out4 = reinterpret_cast<int4*>(s.nbr) + i;
-            // bonded partners left out of the list when 1-2 exclusions are on
-            const int2 ex = s.excl_bonded ? s.bond_slot[i] : make_int2(-1, -1);
-            // image codes of the stencil rows: 1 = across the upper face, 2 = lower
-            const int cxm = cx == 0 ? 2 : 0, cxp = cx == nc0 - 1 ? 1 : 0;
-            const int cym = cy == 0 ? 2 : 0, cyp = cy == nc1 - 1 ? 1 : 0;
-            int cnt = 0;
-            int4 grp = make_int4(-1, -1, -1, -1);
+// One thread per particle, in cell order.  With cells of edge >= (rc + skin) / W
+// (W = 1, or the sub-cells of W = 2) the stencil is (2W+1)^2 rows of 2W+1 cells.  The
+// cells of a row are consecutive in index order, so a row is one contiguous
+// range of the entry array (two where it wraps around the box in x).  The
+// ranges of one plane of rows are loaded together, then each range is
+// streamed with no further indirection.  Hits are packed into int4 groups in
+// registers and stored as whole 16-byte groups, so the stores of a warp are
+// contiguous.
+template <class T, int W, bool EXCL>
+__device__ __forceinline__ void verlet_stencil(const DevSys<T>& s, const RepGeom<T>& g, int i,
+                                               const V4<T>& xi, int2 ex, int& cnt, int4& grp,
+                                               int4* __restrict__ out4) {
+    constexpr int NR = 2 * W + 1;
+    const V4<T>* __restrict__ E = s.cell_ent;
+    const int* __restrict__ B = s.cell_beg;
+    const int nc0 = g.nc[0], nc1 = g.nc[1], nc2 = g.nc[2];
+    const int cx = cell_coord(xi.x, g.cells_per_len[0], nc0);
+    const int cy = cell_coord(xi.y, g.cells_per_len[1], nc1);
+    const int cz = cell_coord(xi.z, g.cells_per_len[2], nc2);
+    const T L0 = g.L[0], L1 = g.L[1], L2 = g.L[2];
+    const T rl2 = s.rlist2;
+    const int cap = s.cap;
+    const size_t stride = (size_t)s.stride;
+    // the x ranges are the same for every row: [sl0, sh0] and, where the row
+    // wraps, [sl1, sh1] (image codes cxc0, cxc1)
+    int sl0 = cx - W, sh0 = cx + W, cxc0 = 0, sl1 = 0, sh1 = -1, cxc1 = 0;
+    if (sl0 < 0) {
+        sl1 = 0;
+        sh1 = sh0;
+        sl0 += nc0;
+        sh0 = nc0 - 1;
+        cxc0 = 2;
+    } else if (sh0 >= nc0) {
+        sl1 = 0;
+        sh1 = sh0 - nc0;
+        cxc1 = 1;
+        sh0 = nc0 - 1;
+    }
+    const T xo0 = (cxc0 & 1) ? xi.x - L0 : xi.x, xL0 = (cxc0 & 2) ? L0 : T(0);
+    const T xo1 = (cxc1 & 1) ? xi.x - L0 : xi.x, xL1 = (cxc1 & 2) ? L0 : T(0);
 #pragma unroll 1
-            for (int pz = 0; pz < 3; ++pz) {
-                int az = cz + pz - 1;
-                int czc = 0;
-                if (az < 0) { az += nc2; czc = 2; }
-                if (az >= nc2) { az -= nc2; czc = 1; }
-                int hh[9], cn[9];
+    for (int dz = -W; dz <= W; ++dz) {
+        int az = cz + dz, czc = 0;
+        if (az < 0) { az += nc2; czc = 2; }
+        else if (az >= nc2) { az -= nc2; czc = 1; }
+        const T zo = (czc & 1) ? xi.z - L2 : xi.z, zL = (czc & 2) ? L2 : T(0);
+        int pb[NR][2], pe[NR][2], cyc[NR];
 #pragma unroll
-                for (int q = 0; q < 9; ++q) {
-                    const int ay = q / 3 == 0 ? ym : (q / 3 == 1 ? cy : yp);
-                    const int ax = q % 3 == 0 ? xm : (q % 3 == 1 ? cx : xp);
-                    hh[q] = g.cell_off + (az * nc1 + ay) * nc0 + ax;
-                }
+        for (int r = 0; r < NR; ++r) {
+            int ay = cy + r - W, c = 0;
+            if (ay < 0) { ay += nc1; c = 2; }
+            else if (ay >= nc1) { ay -= nc1; c = 1; }
+            cyc[r] = c;
+            const int base = g.cell_off + (az * nc1 + ay) * nc0;
+            pb[r][0] = __ldg(B + base + sl0);
+            pe[r][0] = __ldg(B + base + sh0 + 1);
+            pb[r][1] = sh1 >= 0 ? __ldg(B + base + sl1) : 0;
+            pe[r][1] = sh1 >= 0 ? __ldg(B + base + sh1 + 1) : 0;
+        }
 #pragma unroll
-                for (int q = 0; q < 9; ++q) cn[q] = min(__ldg(s.cell_cnt + hh[q]), capc);
+        for (int r = 0; r < NR; ++r) {
+            const T yo = (cyc[r] & 1) ? xi.y - L1 : xi.y, yL = (cyc[r] & 2) ? L1 : T(0);
 #pragma unroll
-                for (int q = 0; q < 9; ++q) {
-                    const int ccx = q % 3 == 0 ? cxm : (q % 3 == 2 ? cxp : 0);
-                    const int ccy = q / 3 == 0 ? cym : (q / 3 == 2 ? cyp : 0);
-                    const int code = ccx | (ccy << 2) | (czc << 4);
-                    const int tag = code << NBR_INDEX_BITS;
-                    const V4<T>* __restrict__ ent = s.cell_xyz + (size_t)hh[q] * capc;
-                    for (int k = 0; k < cn[q]; ++k) {
-                        const V4<T> xj = ld4<T>(ent + k);
-                        const int j = bits_as_int(xj.w);
-                        if (j == i || j == ex.x || j == ex.y) continue;
-                        const T ddx = shifted_diff(xi.x, xim, xj.x, L0, ccx);
-                        const T ddy = shifted_diff(xi.y, yim, xj.y, L1, ccy);
-                        const T ddz = shifted_diff(xi.z, zim, xj.z, L2, czc);
-                        if (ddx * ddx + ddy * ddy + ddz * ddz < rl2) {
-                            const int l = cnt & 3;
-                            const int e = j | tag;
-                            if (l == 0) grp.x = e;
-                            else if (l == 1) grp.y = e;
-                            else if (l == 2) grp.z = e;
-                            else grp.w = e;
-                            ++cnt;
-                            if ((cnt & 3) == 0) {
-                                if (cnt <= cap) out4[(size_t)((cnt >> 2) - 1) * stride] = grp;
-                                grp = make_int4(-1, -1, -1, -1);
-                            }
+            for (int part = 0; part < 2; ++part) {
+                const T xo = part ? xo1 : xo0, xL = part ? xL1 : xL0;
+                const int tag = ((part ? cxc1 : cxc0) | (cyc[r] << 2) | (czc << 4)) << NBR_INDEX_BITS;
+                const int e = pe[r][part];
+                for (int p = pb[r][part]; p < e; ++p) {
+                    const V4<T> xj = ld4<T>(E + p);
+                    const int j = bits_as_int(xj.w);
+                    const T dx = xo - (xj.x - xL);
+                    const T dy = yo - (xj.y - yL);
+                    const T dz2 = zo - (xj.z - zL);
+                    bool hit = dx * dx + dy * dy + dz2 * dz2 < rl2 && j != i;
+                    if (EXCL) hit = hit && j != ex.x && j != ex.y;
+                    if (hit) {
+                        const int l = cnt & 3;
+                        const int en = j | tag;
+                        if (l == 0) grp.x = en;
+                        else if (l == 1) grp.y = en;
+                        else if (l == 2) grp.z = en;
+                        else grp.w = en;
+                        ++cnt;
+                        if ((cnt & 3) == 0) {
+                            if (cnt <= cap) out4[(size_t)((cnt >> 2) - 1) * stride] = grp;
+                            grp = make_int4(-1, -1, -1, -1);
                         }
                     }
                 }
             }
-            if ((cnt & 3) != 0 && cnt <= cap) out4[(size_t)(cnt >> 2) * stride] = grp;
+        }
+    }
+}
+
+template <class T, int W, bool EXCL>
+__global__ void __launch_bounds__(TILE) k_verlet(DevSys<T> s, int cur) {
+    if (s.ctrl->abort) return;
+    for (int t = blockIdx.x; t < s.ntiles; t += gridDim.x) {
+        const Tile tl = s.tiles[t];
+        if (!s.now[tl.rep]) continue;  // uniform over the block
+        int cnt = 0;
+        if ((int)threadIdx.x < tl.count) {
+            const RepGeom<T>& g = s.reps[tl.rep];
+            // threads follow the entry array (cell order: a warp walks a run of
+            // cells along x, whose stencils share their rows), not the storage
+            // order; a replica's entries fill the same index range as its slots
+            const V4<T> xi = ld4<T>(s.cell_ent + tl.start + threadIdx.x);
+            const int i = bits_as_int(xi.w);
+            s.xb[i] = xi;
+            // bonded partners left out of the list when 1-2 exclusions are on
+            const int2 ex = EXCL ? s.bond_slot[i] : make_int2(-1, -1);
+            int4* __restrict__ out4 = reinterpret_cast<int4*>(s.nbr) + i;
+            int4 grp = make_int4(-1, -1, -1, -1);
+            verlet_stencil<T, W, EXCL>(s, g, i, xi, ex, cnt, grp, out4);
+            const int cap = s.cap;
+            if ((cnt & 3) != 0 && cnt <= cap) out4[(size_t)(cnt >> 2) * s.stride] = grp;
             s.nbr_cnt[i] = cnt < cap ? cnt : cap;
-            atomicMax(&smax, cnt);
             if (cnt > cap) {
                 atomicMax(&s.ctrl->need_cap, (unsigned int)cnt);
                 atomicOr(&s.ctrl->err, ERRBIT_OVERFLOW);
                 s.ctrl->abort = 1;
             }
         }
-        __syncthreads();
-        if (threadIdx.x == 0) atomicMax(&s.ctrl->max_count, (unsigned int)smax);
-        __syncthreads();
+        // largest count: one atomic per warp, no block barrier
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt = max(cnt, __shfl_xor_sync(0xffffffffu, cnt, o));
+        if ((threadIdx.x & 31) == 0 && cnt > 0) atomicMax(&s.ctrl->max_count, (unsigned int)cnt);
     }
 }
 
@@ -367,19 +422,29 @@ int Launch<T>::rebuild(const DevSys<T>& s, int cur, bool resort, bool permute_fo
     const int gc = grid_for(s.ncells, 256);
     k_prep<T><<<gc, 256, 0, st>>>(s);
     k_bin<T><<<gt, TILE, 0, st>>>(s, cur);
+    k_scan_reduce<T, false><<<s.nscan_blocks, SCAN_THREADS, 0, st>>>(s);
+    k_scan_top<T><<<1, SCAN_THREADS, 0, st>>>(s);
+    k_scan_down<T, false><<<s.nscan_blocks, SCAN_THREADS, 0, st>>>(s);
+    k_place<T><<<gt, TILE, 0, st>>>(s, cur);
     k_cellsort<T><<<gc, 256, 0, st>>>(s);
-    int launched = 4;
+    int launched = 7;
     if (resort) {
-        k_scan_reduce<T><<<s.nscan_blocks, SCAN_THREADS, 0, st>>>(s);
+        k_scan_reduce<T, true><<<s.nscan_blocks, SCAN_THREADS, 0, st>>>(s);
         k_scan_top<T><<<1, SCAN_THREADS, 0, st>>>(s);
-        k_scan_down<T><<<s.nscan_blocks, SCAN_THREADS, 0, st>>>(s);
+        k_scan_down<T, true><<<s.nscan_blocks, SCAN_THREADS, 0, st>>>(s);
         k_resort_scatter<T><<<gc, 256, 0, st>>>(s);
         k_gather<T><<<gt, TILE, 0, st>>>(s, cur, permute_force ? 1 : 0);
         k_copyback<T><<<gt, TILE, 0, st>>>(s, cur, permute_force ? 1 : 0);
         launched += 6;
     }
-    k_verlet<T><<<gt, TILE, 0, st>>>(s, cur);
-    return launched;
+    if (s.cell_w == 1) {
+        if (s.excl_bonded) k_verlet<T, 1, true><<<gt, TILE, 0, st>>>(s, cur);
+        else k_verlet<T, 1, false><<<gt, TILE, 0, st>>>(s, cur);
+    } else {
+        if (s.excl_bonded) k_verlet<T, 2, true><<<gt, TILE, 0, st>>>(s, cur);
+        else k_verlet<T, 2, false><<<gt, TILE, 0, st>>>(s, cur);
+    }
+    return launched + 1;
 }
 
 template <class T>

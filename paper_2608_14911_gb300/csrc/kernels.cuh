@@ -62,13 +62,14 @@ template <class T> struct DevSys {
     int* nbr_cnt;
     int cap;
     int stride;
-    // cells (rank space, all replicas concatenated)
-    // cells are indexed by cell_off + (cz * ny + cy) * nx + cx; each holds up
-    // to capc entries (position, storage slot in the w lane), ascending slot
+    // cells, all replicas concatenated; cell index cell_off + (cz * ny + cy) * nx + cx
     int* cell_cnt;
-    V4<T>* cell_xyz;
-    int capc;
-    int* cell_start;       // first slot of each cell in Hilbert-rank order (resort only)
+    // compact entries (position, storage slot in the w lane): those of cell h
+    // are cell_ent[cell_beg[h] .. cell_beg[h + 1]), ascending slot
+    V4<T>* cell_ent;
+    int* cell_beg;          // ncells + 1; cell_beg[ncells] = N
+    int* rank_start;        // first new slot of each cell in Hilbert-rank order (resort only)
+    int cell_w;             // cell subdivision: cells of edge >= (rc + skin) / cell_w (1 or 2)
     const int* cell_by_rank;  // global Hilbert rank -> cell index
     const int* cell_rep;
     int ncells;
@@ -99,6 +100,9 @@ template <class T> struct DevSys {
     T half_skin2;       // (skin / 2)^2
     double* partials;   // ntiles * NPART
 };
+
+// kernels launched by one rebuild without a resort (Launch::rebuild)
+constexpr int REBUILD_LAUNCHES = 8;
 
 // step-kernel modes
 enum : int {

@@ -67,6 +67,7 @@ struct SystemBase {
     virtual int set_chunk(int steps) = 0;
     virtual int list_stats(int64_t* total, int32_t* maxc) = 0;
     virtual int set_resort_interval(int64_t steps) = 0;
+    virtual int set_cell_subdivision(int w) = 0;
 };
 
 struct PairHost {
@@ -133,13 +134,13 @@ class System : public SystemBase {
     int64_t launches = 0;
     int chunk = 64;
     int64_t resort_every = 500;  // steps between Hilbert resorts inside integrate (0 = never)
-    void* cell_list_alloc = nullptr;
+    int cell_sub_req = 0;  // requested cell subdivision (0 = chosen per system)
+    int cell_sub = 1;      // subdivision in use (stencil half width)
 
     ~System() override {
         clear_graphs();
         for (void* p : cell_allocs) cudaFree(p);
         if (nbr_alloc) cudaFree(nbr_alloc);
-        if (cell_list_alloc) cudaFree(cell_list_alloc);
         if (tab_alloc) cudaFree(tab_alloc);
         if (d_hist) cudaFree(d_hist);
         for (void* p : allocs) cudaFree(p);
@@ -279,7 +280,8 @@ class System : public SystemBase {
             (rc = alloc(&d.vel, n, allocs)) || (rc = alloc(&d.vel_alt, n, allocs)) ||
             (rc = alloc(&d.frc, n, allocs)) || (rc = alloc(&d.frc_alt, n, allocs)) ||
             (rc = alloc(&d.xb, n, allocs)) || (rc = alloc(&d.img, n, allocs)) ||
-            (rc = alloc(&d.img_alt, n, allocs)) || (rc = alloc(&d.bond_slot, n, allocs)))
+            (rc = alloc(&d.img_alt, n, allocs)) || (rc = alloc(&d.bond_slot, n, allocs)) ||
+            (rc = alloc(&d.cell_ent, n, allocs)))
             return rc;
         int2* bg = nullptr;
         int *sid, *perm, *cellh, *inc, *ncnt, *req, *now, *rto;
@@ -337,18 +339,47 @@ class System : public SystemBase {
         return ESPP_OK;
     }
 
-    int cell_count(int r, int c) const {
-        return (int)std::floor(box[3 * r + c] / ((rc_list + skin) * (1.0 + 1e-6)));
+    // cells per edge for stencil half width w: edge >= (rc + skin) / w
+    int cell_count(int r, int c, int w) const {
+        return (int)std::floor(w * box[3 * r + c] / ((rc_list + skin) * (1.0 + 1e-6)));
+    }
+
+    // Automatic choice: half cells (w = 2) pay off once a full cell holds about
+    // ten particles (dense LJ: 19), where the 5x5x5 stencil of half cells
+    // searches 42% less volume; for sparse cells (KG melt: 3) the longer
+    // stencil loop costs more than it saves.  w = 2 also needs 5 cells per edge.
+    int choose_subdivision() {
+        if (cell_sub_req > 0) return cell_sub_req;
+        double n = 0, cells = 0;
+        bool fits2 = true;
+        for (int r = 0; r < R; ++r) {
+            double c1 = 1;
+            for (int c = 0; c < 3; ++c) {
+                c1 *= std::max(1, cell_count(r, c, 1));
+                fits2 = fits2 && cell_count(r, c, 2) >= 5;
+            }
+            n += rep_n[r];
+            cells += c1;
+        }
+        return fits2 && n / cells >= 10.0 ? 2 : 1;
+    }
+
+    // every edge of replica r holds 2w + 1 distinct cells of the subdivision
+    bool cells_fit(int r) const {
+        bool ok = true;
+        for (int c = 0; c < 3; ++c) ok = ok && cell_count(r, c, cell_sub) >= 2 * cell_sub + 1;
+        return ok;
     }
 
     int upload_geometry() {
         std::vector<RepGeom<T>> g(R);
         int coff = 0;
         for (int r = 0; r < R; ++r) {
+            const int w = cell_sub;
             for (int c = 0; c < 3; ++c) {
                 g[r].L[c] = (T)box[3 * r + c];
                 g[r].halfL[c] = g[r].L[c] * T(0.5);
-                const int nc = cells_ready ? cell_count(r, c) : 1;
+                const int nc = cells_ready ? cell_count(r, c, w) : 1;
                 g[r].nc[c] = nc;
                 g[r].cells_per_len[c] = (T)((double)nc / (double)g[r].L[c]);
             }
@@ -825,33 +856,6 @@ class System : public SystemBase {
         return std::max(8, (cap + 3) & ~3);  // the step kernel reads two groups ahead
     }
 
-    int estimate_capc() const {
-        double best = 0;
-        for (int r = 0; r < R; ++r) {
-            const double nc = (double)cell_count(r, 0) * cell_count(r, 1) * cell_count(r, 2);
-            best = std::max(best, rep_n[r] / nc);
-        }
-        int capc = (int)std::ceil(best * 2.0 + 8);
-        if (const char* f = getenv("ESPP_FAULT_CELL_CAP")) {
-            const int forced = atoi(f);
-            if (forced > 0) capc = forced;
-        }
-        return capc;
-    }
-
-    int alloc_cells(int capc) {
-        if (cell_list_alloc) cudaFree(cell_list_alloc);
-        cell_list_alloc = nullptr;
-        void* p = nullptr;
-        cudaError_t e = cudaMalloc(&p, (size_t)capc * d.ncells * sizeof(V4<T>));
-        if (e != cudaSuccess) return fail(ESPP_ERR_CUDA, std::string("cell allocation: ") + cudaGetErrorString(e));
-        cell_list_alloc = p;
-        d.cell_xyz = reinterpret_cast<V4<T>*>(p);
-        d.capc = capc;
-        clear_graphs();
-        return ESPP_OK;
-    }
-
     int alloc_list(int cap) {
         if (nbr_alloc) cudaFree(nbr_alloc);
         nbr_alloc = nullptr;
@@ -875,21 +879,23 @@ class System : public SystemBase {
         skin = sk;
         int rcode = check_cutoffs();
         if (rcode) return rcode;
+        cell_sub = choose_subdivision();
         for (int r = 0; r < R; ++r)
-            for (int c = 0; c < 3; ++c)
-                if (cell_count(r, c) < 3) {
-                    cells_ready = false;
-                    return fail(ESPP_ERR_BOX_TOO_SMALL, "box edge holds fewer than 3 cells of rc + skin");
-                }
+            if (!cells_fit(r)) {
+                cells_ready = false;
+                return fail(ESPP_ERR_BOX_TOO_SMALL,
+                            "box edge holds fewer than 2w + 1 cells of (rc + skin) / w (w: cell subdivision)");
+            }
         cells_ready = true;
-        // cell grids in Hilbert order
+        // cell grids; Hilbert ranks for the resort order
         for (void* p : cell_allocs) cudaFree(p);
         cell_allocs.clear();
         clear_graphs();
         std::vector<int> rep_of, by_rank;
         int coff = 0;
         for (int r = 0; r < R; ++r) {
-            const int nx = cell_count(r, 0), ny = cell_count(r, 1), nz = cell_count(r, 2);
+            const int w = cell_sub;
+            const int nx = cell_count(r, 0, w), ny = cell_count(r, 1, w), nz = cell_count(r, 2, w);
             const int nc = nx * ny * nz;
             std::vector<int> rk(nc);
             hilbert_ranks(nx, ny, nz, rk.data());
@@ -901,19 +907,24 @@ class System : public SystemBase {
             coff += nc;
         }
         const int C = coff;
-        int *cnt, *start, *crep, *cbr, *part;
+        int *cnt, *beg, *rstart, *crep, *cbr, *part;
         int rc2 = ESPP_OK;
         d.nscan_blocks = scan_blocks_for(C);
-        if ((rc2 = alloc(&cnt, C, cell_allocs)) || (rc2 = alloc(&start, C + 1, cell_allocs)) ||
-            (rc2 = alloc(&crep, C, cell_allocs)) || (rc2 = alloc(&cbr, C, cell_allocs)) ||
-            (rc2 = alloc(&part, d.nscan_blocks, cell_allocs)))
+        if ((rc2 = alloc(&cnt, C, cell_allocs)) || (rc2 = alloc(&beg, C + 1, cell_allocs)) ||
+            (rc2 = alloc(&rstart, C, cell_allocs)) || (rc2 = alloc(&crep, C, cell_allocs)) ||
+            (rc2 = alloc(&cbr, C, cell_allocs)) || (rc2 = alloc(&part, d.nscan_blocks, cell_allocs)))
             return rc2;
         CK(cudaMemcpy(crep, rep_of.data(), C * sizeof(int), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(cbr, by_rank.data(), C * sizeof(int), cudaMemcpyHostToDevice));
+        // every count starts at zero (a replica's counts sum to its particle
+        // count after its first build); the entry array ends at N
+        CK(cudaMemset(cnt, 0, C * sizeof(int)));
         const int nn = (int)N;
-        CK(cudaMemcpy(start + C, &nn, sizeof(int), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(beg + C, &nn, sizeof(int), cudaMemcpyHostToDevice));
+        d.cell_w = cell_sub;
         d.cell_cnt = cnt;
-        d.cell_start = start;
+        d.cell_beg = beg;
+        d.rank_start = rstart;
         d.cell_rep = crep;
         d.cell_by_rank = cbr;
         d.ncells = C;
@@ -924,8 +935,6 @@ class System : public SystemBase {
         rcode = upload_geometry();
         if (rcode) return rcode;
         rcode = alloc_list(estimate_cap());
-        if (rcode) return rcode;
-        rcode = alloc_cells(estimate_capc());
         if (rcode) return rcode;
         if (!state_set) return ESPP_OK;
         Launch<T>::request_all(d, st);
@@ -943,18 +952,18 @@ class System : public SystemBase {
             CK(cudaGetLastError());
             Ctrl c = read_ctrl();
             CK(cudaGetLastError());
-            if (!(c.err & (ERRBIT_OVERFLOW | ERRBIT_CELL))) {
+            if (!(c.err & ERRBIT_OVERFLOW)) {
                 rebuild_pending = false;
                 return ESPP_OK;
             }
             int rcode = grow_capacity(c);
             if (rcode) return rcode;
         }
-        return fail(ESPP_ERR_LIST_OVERFLOW, "Verlet list or cell overflow persists after retries");
+        return fail(ESPP_ERR_LIST_OVERFLOW, "Verlet list overflow persists after retries");
     }
 
-    // grow the list and/or the cell member array after an overflow, clear the
-    // overflow state and request a rebuild of every replica
+    // grow the list after an overflow, clear the overflow state and request a
+    // rebuild of every replica
     int grow_capacity(const Ctrl& c) {
         int rcode = ESPP_OK;
         if (c.err & ERRBIT_OVERFLOW) {
@@ -963,15 +972,10 @@ class System : public SystemBase {
             rcode = alloc_list(std::max(cap, d.cap + 4));
             if (rcode) return rcode;
         }
-        if (c.err & ERRBIT_CELL) {
-            rcode = alloc_cells(std::max((int)std::ceil(c.need_capc * 1.3 + 4), d.capc + 4));
-            if (rcode) return rcode;
-        }
         Ctrl w = read_ctrl();
-        w.err &= ~(ERRBIT_OVERFLOW | ERRBIT_CELL);
+        w.err &= ~ERRBIT_OVERFLOW;
         w.abort = 0;
         w.need_cap = 0;
-        w.need_capc = 0;
         w.blocks_done = 0;
         CK(cudaMemcpyAsync(d_ctrl, &w, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
         Launch<T>::request_all(d, st);
@@ -1219,9 +1223,9 @@ class System : public SystemBase {
             Ctrl c = read_ctrl();
             CK(cudaGetLastError());
             if (host_rebuilds >= 0)
-                launches += 4 * ((int64_t)(c.n_rebuilds - (unsigned)rb0) - host_rebuilds);
+                launches += REBUILD_LAUNCHES * ((int64_t)(c.n_rebuilds - (unsigned)rb0) - host_rebuilds);
             if (c.err & (ERRBIT_BOND | ERRBIT_NONFINITE | ERRBIT_TIMEOUT)) return status_from(c);
-            if (c.err & (ERRBIT_OVERFLOW | ERRBIT_CELL)) {
+            if (c.err & ERRBIT_OVERFLOW) {
                 // frozen after step c.step with the positions of the next step in
                 // buffer pm: grow, rebuild every replica there, go on
                 done = c.step;
@@ -1458,7 +1462,6 @@ class System : public SystemBase {
         c.any_req = 0;
         c.blocks_done = 0;
         c.need_cap = 0;
-        c.need_capc = 0;
         CK(cudaMemcpy(d_ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice));
         // the list of the saved run was built from the build positions: rebuild
         // it from them (buffer 1 holds a copy), without a resort
@@ -1466,7 +1469,7 @@ class System : public SystemBase {
         launches += 1 + Launch<T>::rebuild(d, 1, false, false, st);
         CK(cudaGetLastError());
         c = read_ctrl();
-        if (c.err & (ERRBIT_OVERFLOW | ERRBIT_CELL)) return fail(ESPP_ERR_LIST_OVERFLOW, "list capacity too small for the checkpoint");
+        if (c.err & ERRBIT_OVERFLOW) return fail(ESPP_ERR_LIST_OVERFLOW, "list capacity too small for the checkpoint");
         // restore the pending requests and the rebuild counter of the saved run
         CK(cudaMemcpy(d.req, req.data(), (size_t)R * sizeof(int), cudaMemcpyHostToDevice));
         int any = 0;
@@ -1508,6 +1511,13 @@ class System : public SystemBase {
         if (steps < 0) return fail(ESPP_ERR_ARG, "resort interval must be >= 0");
         resort_every = steps;
         return ESPP_OK;
+    }
+
+    int set_cell_subdivision(int w) override {
+        if (w < 0 || w > 2) return fail(ESPP_ERR_ARG, "cell subdivision must be 0, 1 or 2");
+        cell_sub_req = w;
+        // an existing grid is rebuilt with the new cells
+        return cells_ready ? build_neighbors(rc_list, skin) : ESPP_OK;
     }
 
     int set_chunk(int steps) override {
@@ -1682,6 +1692,10 @@ int espp_list_stats(espp_h h, int64_t* total_entries, int32_t* max_count) {
 }
 int espp_set_resort_interval(espp_h h, int64_t steps) {
     return guarded(h, [&](espp::SystemBase& s) { return s.set_resort_interval(steps); });
+}
+
+int espp_set_cell_subdivision(espp_h h, int32_t w) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.set_cell_subdivision(w); });
 }
 int espp_set_graph_chunk(espp_h h, int32_t steps) {
     return guarded(h, [&](espp::SystemBase& s) { return s.set_chunk(steps); });

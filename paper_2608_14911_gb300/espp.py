@@ -60,7 +60,7 @@ EXPORTS = (
     "espp_set_kernel_timing", "espp_kernel_timing", "espp_set_graph_chunk", "espp_list_stats",
     "espp_rdf_counts_noalloc", "espp_set_resort_interval", "espp_mlp_set_weights",
     "espp_set_exclude_bonded", "espp_mlp_get_weights", "espp_mlp_train", "espp_mlp_loss_grad",
-    "espp_cg_map",
+    "espp_cg_map", "espp_set_cell_subdivision",
 )
 NOALLOC_MAX_BINS = 4096
 
@@ -137,6 +137,7 @@ def lib(path: str = LIB_PATH):
         "espp_list_stats": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i32)], ctypes.c_int),
         "espp_rdf_counts_noalloc": ([vp, i64, dp, ctypes.c_double, i32, vp, vp], ctypes.c_int),
         "espp_set_resort_interval": ([vp, i64], ctypes.c_int),
+        "espp_set_cell_subdivision": ([vp, ctypes.c_int32], ctypes.c_int),
         "espp_mlp_set_weights": ([vp, vp, i64], ctypes.c_int),
         "espp_set_exclude_bonded": ([vp, ctypes.c_int], ctypes.c_int),
         "espp_mlp_get_weights": ([vp, vp, i64], ctypes.c_int),
@@ -405,6 +406,9 @@ class System:
 
     def set_resort_interval(self, steps):
         self._c(lib().espp_set_resort_interval(self._h, int(steps)))
+
+    def set_cell_subdivision(self, w):
+        self._c(lib().espp_set_cell_subdivision(self._h, int(w)))
 
     def set_graph_chunk(self, steps):
         self._c(lib().espp_set_graph_chunk(self._h, int(steps)))

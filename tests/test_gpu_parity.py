@@ -220,15 +220,53 @@ def test_list_overflow_is_retried(monkeypatch):
     assert np.abs(_unwrapped(x, img, case.cfg.box) - _unwrapped(st.x, st.img, case.cfg.box)).max() < 1e-10
 
 
-def test_cell_overflow_is_retried(monkeypatch):
-    monkeypatch.setenv("ESPP_FAULT_CELL_CAP", "4")
-    case = lj_case()
-    s = case.system(FP64)
-    s.integrate(30, 0.005, 1.0, 0.72)
-    x, v, img = s.get_state()
+@pytest.mark.parametrize("w", [2])
+@pytest.mark.parametrize("case", [kg_case(), lj_case(), two_type_case()], ids=lambda c: c.name)
+def test_cell_subdivision_keeps_the_list(case, w):
+    # sub-cells (paper: cell sub-decomposition) change the search, not the list
+    a = case.system(FP64)
+    b = case.system(FP64, build=False)
+    b.set_cell_subdivision(w)
+    b.build_neighbors(case.rc_list, case.skin)
+    ra, ca = a.get_neighbors()
+    rb, cb = b.get_neighbors()
+    assert np.array_equal(ra, rb)
+    for i in range(case.cfg.n):
+        assert set(ca[ra[i]:ra[i + 1]].tolist()) == set(cb[rb[i]:rb[i + 1]].tolist())
+    assert rel_rms(b.compute_forces(), a.compute_forces()) <= 1e-13
+    # a trajectory with sub-cells (rebuilds and resorts included) follows the oracle
+    b.set_resort_interval(20)
+    b.integrate(60, 0.005, 1.0, 0.72)
+    x, v, img = b.get_state()
     st = case.oracle_state()
-    O.integrate(case.model, st, 30, 0.005, 1.0, 0.72, seed=42)
+    O.integrate(case.model, st, 60, 0.005, 1.0, 0.72, seed=42)
     assert np.abs(_unwrapped(x, img, case.cfg.box) - _unwrapped(st.x, st.img, case.cfg.box)).max() < 1e-10
+    with pytest.raises(espp.EsppError) as e:
+        b.set_cell_subdivision(3)
+    assert e.value.code == espp.ESPP_ERR_ARG
+
+
+def test_cell_subdivision_in_batches():
+    # replicas of different sizes, each with its own sub-cell grid
+    cases_ = [kg_case(), kg_case(4, 30, seed=3, jitter=0.08), kg_case(7, 23, seed=5, jitter=0.1)]
+    reps = [dict(box=c.cfg.box, n=c.cfg.n, types=c.cfg.types, bonds=c.cfg.bonds, seed=42 + k)
+            for k, c in enumerate(cases_)]
+    b = espp.System(replicas=reps, precision=FP64)
+    b.set_wca()
+    b.set_fene()
+    b.set_state(np.concatenate([c.cfg.x for c in cases_]), np.concatenate([c.v for c in cases_]),
+                np.concatenate([c.cfg.img for c in cases_]))
+    b.set_cell_subdivision(2)
+    b.build_neighbors(WCA_RC, 0.4)
+    f3 = b.compute_forces()
+    b.set_cell_subdivision(1)
+    f1 = b.compute_forces()
+    assert rel_rms(f3, f1) <= 1e-13
+    off = 0
+    for c in cases_:
+        fo, _ = O.forces(c.model, c.cfg.box, c.cfg.x, c.cfg.types, c.cfg.bonds)
+        assert rel_rms(f3[off:off + c.cfg.n], fo) <= 1e-12
+        off += c.cfg.n
 
 
 @pytest.mark.parametrize("prec", [FP32, FP64])
