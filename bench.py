@@ -207,7 +207,10 @@ def timed_integrate(s, steps, stream_sync):
     e1 = torch.cuda.Event(enable_timing=True)
     stream_sync()
     e0.record()
+    # NVTX range: profilers can restrict a capture to the timed steps
+    torch.cuda.nvtx.range_push("timed_region")
     s.integrate(steps, 0.005, 1.0, 1.0)
+    torch.cuda.nvtx.range_pop()
     e1.record()
     stream_sync()
     return e0.elapsed_time(e1)
@@ -223,11 +226,18 @@ def step_kernel_bytes(n, list_entries, precision):
     return n * (5 * v4 + 8 + 4) + 4 * list_entries
 
 
+def step_kernel_digest():
+    """Digest of the sources the step kernel is compiled from."""
+    h = hashlib.sha256()
+    for f in ("k_step.cu", "kernels.cuh", "common.cuh", "philox.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2608_14911_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def read_traffic_record():
     """DRAM bytes per step-kernel launch from the committed ncu summary, or
     None when the kernel source changed since the capture."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
-    src = os.path.join(ROOT, "paper_2608_14911_gb300", "csrc", "k_step.cu")
     if not os.path.exists(path):
         return None
     rec = {}
@@ -236,8 +246,7 @@ def read_traffic_record():
             if ":" in line and not line.startswith("#"):
                 k, val = line.split(":", 1)
                 rec[k.strip()] = val.strip()
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if rec.get("k_step_sha") != digest:
+    if rec.get("k_step_sha") != step_kernel_digest():
         return None
     try:
         return float(rec["dram_bytes_per_particle_step"])
