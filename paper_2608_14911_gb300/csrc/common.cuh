@@ -217,6 +217,7 @@ enum : unsigned int {
     ERRBIT_BOND = 2u,
     ERRBIT_NONFINITE = 4u,
     ERRBIT_TIMEOUT = 8u,
+    ERRBIT_ASYM = 16u,  // a list entry without its mirrored entry
 };
 
 constexpr int TILE = 128;          // particles per tile (= threads per block)

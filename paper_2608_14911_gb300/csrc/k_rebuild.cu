@@ -444,7 +444,10 @@ int Launch<T>::rebuild(const DevSys<T>& s, int cur, bool resort, bool permute_fo
         if (s.excl_bonded) k_verlet<T, 2, true><<<gt, TILE, 0, st>>>(s, cur);
         else k_verlet<T, 2, false><<<gt, TILE, 0, st>>>(s, cur);
     }
-    return launched + 1;
+    launched += 1;
+    // mirrored entries for the learned potential's pair-once evaluation
+    if (s.mlp_on && s.mlp_rev) launched += Launch<T>::mlp_rev(s, st);
+    return launched;
 }
 
 template <class T>

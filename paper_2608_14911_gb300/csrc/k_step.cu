@@ -423,10 +423,10 @@ __global__ void k_set_cond(DevSys<T> s, unsigned long long h) {
 }
 
 template <class T>
-void Launch<T>::step(const DevSys<T>& s, int mode, bool energy, int cur, double* f_out,
-                     unsigned long long next_cond, int grid, cudaStream_t st) {
+int Launch<T>::step(const DevSys<T>& s, int mode, bool energy, int cur, double* f_out,
+                    unsigned long long next_cond, int grid, cudaStream_t st) {
     const int gr = grid > 0 ? grid : s.ntiles;
-    if (s.mlp_on) Launch<T>::mlp(s, cur, st);
+    const int extra = s.mlp_on ? Launch<T>::mlp(s, cur, energy, st) : 0;
 #define ESPP_STEP(M, E)                                                                  \
     do {                                                                                 \
         if (s.lj_fast) k_step<T, M, E, true><<<gr, TILE, 0, st>>>(s, cur, f_out, next_cond); \
@@ -441,6 +441,7 @@ void Launch<T>::step(const DevSys<T>& s, int mode, bool energy, int cur, double*
         default: ESPP_STEP(MODE_FINAL, false); break;
     }
 #undef ESPP_STEP
+    return 1 + extra;
 }
 
 template <class T>
@@ -453,8 +454,8 @@ void Launch<T>::set_cond(const DevSys<T>& s, unsigned long long cond, cudaStream
     k_set_cond<T><<<1, 1, 0, st>>>(s, cond);
 }
 
-template void Launch<float>::step(const DevSys<float>&, int, bool, int, double*, unsigned long long, int, cudaStream_t);
-template void Launch<double>::step(const DevSys<double>&, int, bool, int, double*, unsigned long long, int, cudaStream_t);
+template int Launch<float>::step(const DevSys<float>&, int, bool, int, double*, unsigned long long, int, cudaStream_t);
+template int Launch<double>::step(const DevSys<double>&, int, bool, int, double*, unsigned long long, int, cudaStream_t);
 template void Launch<float>::prologue(const DevSys<float>&, int, int, cudaStream_t);
 template void Launch<double>::prologue(const DevSys<double>&, int, int, cudaStream_t);
 template void Launch<float>::set_cond(const DevSys<float>&, unsigned long long, cudaStream_t);

@@ -94,6 +94,11 @@ template <class T> struct DevSys {
     const MlpWeights* mlp;
     float4* mlp_f;      // per particle: MLP pair force and sum of pair energies
     float* mlp_w;       // per particle: sum of r_ij . F_ij over its MLP pairs
+    // per list entry (layout of nbr): -du/dr / r, u, and for entries (i, j)
+    // with j > i the index of the mirrored entry (j, i)
+    float* mlp_pf;
+    float* mlp_pu;
+    int* mlp_rev;
     int N;
     BondRec<T> bond;
     T rlist2;           // (rc + skin)^2
@@ -119,11 +124,14 @@ template <class T> struct Launch {
     static int rebuild(const DevSys<T>& s, int cur, bool resort, bool permute_force, cudaStream_t st);
     static void request_all(const DevSys<T>& s, cudaStream_t st);
     // step kernels
-    static void step(const DevSys<T>& s, int mode, bool energy, int cur, double* f_out,
-                     unsigned long long next_cond, int grid, cudaStream_t st);
+    // one force evaluation (+ the learned potential's kernels); returns the
+    // number of kernels launched
+    static int step(const DevSys<T>& s, int mode, bool energy, int cur, double* f_out,
+                    unsigned long long next_cond, int grid, cudaStream_t st);
     static void prologue(const DevSys<T>& s, int cur, int grid, cudaStream_t st);
     static void set_cond(const DevSys<T>& s, unsigned long long cond, cudaStream_t st);
-    static void mlp(const DevSys<T>& s, int cur, cudaStream_t st);
+    static int mlp(const DevSys<T>& s, int cur, bool energy, cudaStream_t st);
+    static int mlp_rev(const DevSys<T>& s, cudaStream_t st);
     // force-matching gradient of one frame (errors, tensor-core gradient,
     // deterministic reduction into grad and the loss)
     static int train_grad(const DevSys<T>& s, int cur, const double* Y, float4* err, double* loss_part,

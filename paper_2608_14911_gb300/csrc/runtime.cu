@@ -107,6 +107,8 @@ class System : public SystemBase {
     std::vector<void*> allocs;
     std::vector<void*> cell_allocs;
     void* nbr_alloc = nullptr;
+    void* mlp_buf = nullptr;  // per-entry buffers of the learned potential
+    int mlp_buf_cap = 0;
     DevSys<T> d{};
     RepGeom<T>* d_geom = nullptr;
     IntParams<T>* d_ip = nullptr;
@@ -141,6 +143,7 @@ class System : public SystemBase {
         clear_graphs();
         for (void* p : cell_allocs) cudaFree(p);
         if (nbr_alloc) cudaFree(nbr_alloc);
+        if (mlp_buf) cudaFree(mlp_buf);
         if (tab_alloc) cudaFree(tab_alloc);
         if (d_hist) cudaFree(d_hist);
         for (void* p : allocs) cudaFree(p);
@@ -721,6 +724,10 @@ class System : public SystemBase {
             return fail(ESPP_ERR_ARG, "bad training arguments");
         if (!d.mlp_on || mlp_bits.empty()) return fail(ESPP_ERR_STATE, "select the learned potential and set weights first");
         if (!cells_ready) return fail(ESPP_ERR_STATE, "call espp_build_neighbors first");
+        {
+            const int rb = ensure_mlp_buffers();
+            if (rb) return rb;
+        }
         const int ngrad = mlp_ngrad();
         const int nep = std::max(epochs, 1);
         if (!t_err) {
@@ -769,8 +776,8 @@ class System : public SystemBase {
                     if (rcode) return rcode;
                     rcode = rebuild_now(false);
                     if (rcode) return rcode;
-                    Launch<T>::mlp(d, cur, st);
-                    launches += 1 + Launch<T>::train_grad(d, cur, Y + f * n3, t_err, t_loss_part, scale, t_partials,
+                    launches += Launch<T>::mlp(d, cur, false, st);
+                    launches += Launch<T>::train_grad(d, cur, Y + f * n3, t_err, t_loss_part, scale, t_partials,
                                                           t_blocks, t_grad, t_loss + ep, st);
                     CK(cudaGetLastError());
                 }
@@ -869,6 +876,41 @@ class System : public SystemBase {
         d.nbr = reinterpret_cast<int*>(p);
         d.cap = cap;
         clear_graphs();
+        return d.mlp_on ? alloc_mlp_buffers() : ESPP_OK;
+    }
+
+    // per-entry values and mirrored-entry indices of the learned potential,
+    // sized like the list (3 x 4 bytes per list slot)
+    int alloc_mlp_buffers() {
+        if (mlp_buf) cudaFree(mlp_buf);
+        mlp_buf = nullptr;
+        mlp_buf_cap = 0;
+        d.mlp_pf = d.mlp_pu = nullptr;
+        d.mlp_rev = nullptr;
+        const size_t slots = (size_t)d.cap * d.stride;
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, 3 * slots * sizeof(float));
+        if (e != cudaSuccess) return fail(ESPP_ERR_CUDA, std::string("MLP buffers: ") + cudaGetErrorString(e));
+        e = cudaMemset(p, 0, 3 * slots * sizeof(float));
+        if (e != cudaSuccess) return fail(ESPP_ERR_CUDA, std::string("MLP buffers: ") + cudaGetErrorString(e));
+        mlp_buf = p;
+        mlp_buf_cap = d.cap;
+        d.mlp_pf = reinterpret_cast<float*>(p);
+        d.mlp_pu = d.mlp_pf + slots;
+        d.mlp_rev = reinterpret_cast<int*>(d.mlp_pu + slots);
+        clear_graphs();
+        return ESPP_OK;
+    }
+
+    // the learned potential was selected after the list was sized: allocate its
+    // buffers and rebuild every replica so the mirrored entries exist
+    int ensure_mlp_buffers() {
+        if (!d.mlp_on || !d.nbr || (mlp_buf && mlp_buf_cap == d.cap)) return ESPP_OK;
+        int rcode = alloc_mlp_buffers();
+        if (rcode) return rcode;
+        Launch<T>::request_all(d, st);
+        launches++;
+        rebuild_pending = true;
         return ESPP_OK;
     }
 
@@ -990,6 +1032,8 @@ class System : public SystemBase {
         if (!cells_ready) return fail(ESPP_ERR_STATE, "call espp_build_neighbors first");
         int rcode = check_cutoffs();
         if (rcode) return rcode;
+        rcode = ensure_mlp_buffers();
+        if (rcode) return rcode;
         Ctrl c = read_ctrl();
         if (c.abort) return status_from(c);
         if (rebuild_pending || c.any_req) return rebuild_now(f_valid);
@@ -1000,6 +1044,7 @@ class System : public SystemBase {
         if (c.err & ERRBIT_BOND) return fail(ESPP_ERR_BOND_BROKEN, "a bond reached r >= R0 (FENE) or the end of its table (tabulated)");
         if (c.err & ERRBIT_NONFINITE) return fail(ESPP_ERR_NONFINITE, "a position became non-finite or left the box");
         if (c.err & ERRBIT_TIMEOUT) return fail(ESPP_ERR_TIMEOUT, "a device wait timed out");
+        if (c.err & ERRBIT_ASYM) return fail(ESPP_ERR_STATE, "Verlet list is not symmetric");
         if (c.err & ERRBIT_OVERFLOW) return fail(ESPP_ERR_LIST_OVERFLOW, "Verlet list overflow");
         if (c.abort) return fail(ESPP_ERR_STATE, "aborted");
         return ESPP_OK;
@@ -1045,8 +1090,7 @@ class System : public SystemBase {
         double* target = f;
         if (f && where == ESPP_HOST) target = d_io_x;
         else if (f && where != ESPP_DEVICE) return fail(ESPP_ERR_ARG, "bad where");
-        Launch<T>::step(d, MODE_FORCES, false, cur, target, 0, 0, st);
-        launches++;
+        launches += Launch<T>::step(d, MODE_FORCES, false, cur, target, 0, 0, st);
         CK(cudaGetLastError());
         if (f && where == ESPP_HOST)
             CK(cudaMemcpyAsync(f, d_io_x, 3 * (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1167,8 +1211,7 @@ class System : public SystemBase {
         const int64_t target = step0 + nsteps;
         const int64_t rb0 = c0.n_rebuilds;
         if (!f_valid) {
-            Launch<T>::step(d, MODE_INIT, false, cur, nullptr, 0, 0, st);
-            launches++;
+            launches += Launch<T>::step(d, MODE_INIT, false, cur, nullptr, 0, 0, st);
             f_valid = true;
         }
         const int c_start = cur;
@@ -1203,8 +1246,7 @@ class System : public SystemBase {
                     for (int64_t r = 0; r < S; ++r) {
                         launches += Launch<T>::rebuild(d, p, false, false, st);
                         const int mode = (fin && r == S - 1) ? MODE_FINAL : MODE_STEP;
-                        Launch<T>::step(d, mode, false, p, nullptr, 0ull, 0, st);
-                        launches++;
+                        launches += Launch<T>::step(d, mode, false, p, nullptr, 0ull, 0, st);
                         if (mode == MODE_STEP) p ^= 1;
                     }
                     CK(cudaGetLastError());
@@ -1216,14 +1258,15 @@ class System : public SystemBase {
                 if (rcode) return rcode;
                 CK(cudaGraphLaunch(cg->exec, st));
                 last_cg = cg;
-                launches += 1 + S;
+                launches += 1 + S * (d.mlp_on ? 3 : 1);
                 p ^= (int)((fin ? (S - 1) : S) & 1);
                 next += S;
             }
             Ctrl c = read_ctrl();
             CK(cudaGetLastError());
             if (host_rebuilds >= 0)
-                launches += REBUILD_LAUNCHES * ((int64_t)(c.n_rebuilds - (unsigned)rb0) - host_rebuilds);
+                launches += (REBUILD_LAUNCHES + (d.mlp_on ? 1 : 0)) *
+                            ((int64_t)(c.n_rebuilds - (unsigned)rb0) - host_rebuilds);
             if (c.err & (ERRBIT_BOND | ERRBIT_NONFINITE | ERRBIT_TIMEOUT)) return status_from(c);
             if (c.err & ERRBIT_OVERFLOW) {
                 // frozen after step c.step with the positions of the next step in
@@ -1254,10 +1297,10 @@ class System : public SystemBase {
         if (rcode) return rcode;
         rcode = upload_int_params(ip_key[0] > 0 ? ip_key[0] : 1.0, std::max(ip_key[1], 0.0), std::max(ip_key[2], 0.0));
         if (rcode) return rcode;
-        Launch<T>::step(d, MODE_FORCES, true, cur, nullptr, 0, 0, st);
+        launches += Launch<T>::step(d, MODE_FORCES, true, cur, nullptr, 0, 0, st);
         Launch<T>::reduce_obs(d, d_obs, st);
         Launch<T>::rg2(d, cur, d_mol_members, d_mol_off, d_mol_rep, (int)mol_rep_h.size(), d_mol_rg2, st);
-        launches += 3;
+        launches += 2;
         CK(cudaGetLastError());
         std::vector<double> part((size_t)R * NPART), rg(mol_rep_h.size());
         CK(cudaMemcpyAsync(part.data(), d_obs, part.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
