@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--cg-frames", type=int, default=32)
     ap.add_argument("--cg-epochs", type=int, default=10)
     ap.add_argument("--cg-batch", type=int, default=4)
+    ap.add_argument("--cg-warm", type=int, default=200)
+    ap.add_argument("--cg-steps", type=int, default=200)
     ap.add_argument("--cg-probe", type=int, default=0,
                     help="only: N-site CG system with the learned potential, a few force evaluations (for ncu)")
     ap.add_argument("--quick-start", action="store_true",
@@ -678,6 +680,7 @@ def suite_learned_cg(a, sync, out):
     tab_sys.close()
     res = {}
     forces = {}
+    n_snap, snap_every = 5, 40
     for mode in ("mlp", "table"):
         out["stage"] = "4M CG melt, " + mode
         s = espp.System(cg.box, cg.n, None, cg.bonds, precision=espp.ESPP_FP32, seed=45)
@@ -690,12 +693,25 @@ def suite_learned_cg(a, sync, out):
         s.set_state(cg.x, inputs.maxwell_velocities(cg.n, 1.0, seed=46), cg.img)
         s.build_neighbors(RCM, SKIN)
         forces[mode] = s.compute_forces()
-        s.integrate(20, 0.005, 1.0, 1.0)
-        steps = 100 if mode == "mlp" else 500
+        s.integrate(a.cg_warm, 0.005, 1.0, 1.0)
+        steps = a.cg_steps
         ms = _timed(s, steps, 0.005, 1.0, 1.0, sync)
-        counts = s.rdf_counts(3.5, 175)
+        # force-evaluation time per step (the learned potential's kernels and
+        # the step kernel), from events around the graph's step nodes
+        s.set_kernel_timing(True)
+        for _ in range(2):
+            s.integrate(64, 0.005, 1.0, 1.0)
+        kt = s.kernel_timing(reset=True)
+        s.set_kernel_timing(False)
+        # g(r) averaged over snapshots at the same step numbers for both
+        counts = np.zeros(175)
+        for _ in range(n_snap):
+            s.integrate(snap_every, 0.005, 1.0, 1.0)
+            counts += s.rdf_counts(3.5, 175)
+        counts /= n_snap
         res[mode] = {"value": cg.n * steps / (ms / 1e3), "unit": "site-steps/s", "steps": steps,
-                     "ms_per_step": ms / steps, "fine_bead_equivalent": 4 * cg.n * steps / (ms / 1e3)}
+                     "ms_per_step": ms / steps, "fine_bead_equivalent": 4 * cg.n * steps / (ms / 1e3),
+                     "force_eval_ms": kt["step_ms"] / max(1, kt["step_launches"])}
         res[mode]["_rdf"] = counts
         s.close()
     dr = 0.02
@@ -704,13 +720,30 @@ def suite_learned_cg(a, sync, out):
         shell = 4 * np.pi * rr ** 2 * dr
         rho = cg.n / np.prod(cg.box)
         return cnt / (0.5 * cg.n * rho * shell)
-    ga, gb = gofr(res["mlp"].pop("_rdf")), gofr(res["table"].pop("_rdf"))
+    cm = res["mlp"].pop("_rdf")
+    ct = res["table"].pop("_rdf")
+    ga, gb = gofr(cm), gofr(ct)
+    # tensor-core work of the learned potential: unique pairs inside the cutoff
+    # (all pairs of the histogram minus the excluded 1-2 bonds) x 24576 flop
+    # (two 32x64 and two 64x64 multiply-adds per pair: u and its r-derivative)
+    pairs = float(cm.sum()) - len(cg.bonds)
+    flop = 24576.0 * pairs
+    peaks, peak_kind = measured_peaks()
+    fe = res["mlp"]["force_eval_ms"]
+    res["mlp"]["roofline"] = {"bound": "tensor", "unique_pairs": pairs, "flop_per_step": flop,
+                              "achieved": flop / (fe * 1e-3) / 1e12, "unit": "TFLOP/s",
+                              "peak": peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]),
+                              "frac": flop / (fe * 1e-3) / 1e12 / peaks.get("bf16_tflops_sustained",
+                                                                            peaks["bf16_tflops"]),
+                              "peak_kind": peak_kind + " (bf16_tflops_sustained: timed inside a long run)",
+                              "timed": "all force kernels of a step (pairs, gather, step kernel)"}
     out["cg4m"] = {"workload": "cg_melt_16000x250_4000000_sites_rho0.2125", "n_sites": cg.n,
                    "mlp": res["mlp"], "table": res["table"],
                    "force_rel_rms_mlp_vs_table": float(np.sqrt(((forces["mlp"] - forces["table"]) ** 2).sum()
                                                                / (forces["table"] ** 2).sum())),
                    "rdf_l2_mlp_vs_table": float(np.sqrt(((ga - gb) ** 2).sum() * dr / 3.5)),
-                   "rdf_note": "after 120 (MLP) / 520 (table) steps from the same start"}
+                   "rdf_note": "g(r), dr 0.02, averaged over %d snapshots %d steps apart after %d + %d + 128 steps "
+                               "from the same start, for both potentials" % (n_snap, snap_every, a.cg_warm, a.cg_steps)}
     out["stage"] = "done"
 
 

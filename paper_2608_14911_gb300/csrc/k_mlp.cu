@@ -29,12 +29,29 @@ namespace espp {
 
 constexpr int MLP_WARPS = 4;
 constexpr int MLP_STAGE = 48;  // < 16 pending + 32 new
+#ifndef ESPP_MLP_MINB
+#define ESPP_MLP_MINB 4  // resident blocks of k_mlp_pairs per SM the registers must allow
+#endif
 
-// sigmoid from the hardware tanh: s(z) = (1 + tanh(z / 2)) / 2
-__device__ __forceinline__ float sigm_tanh(float z) {
+// The tile works with y = z / 2: the weights and biases are halved when they
+// are staged (exact in BF16 and FP32), so that with t = tanh(y) (one hardware
+// instruction)
+//   silu(z)  = z (1 + tanh(z/2)) / 2      = y (1 + t)
+//   silu'(z) dz = (1 + t)(1 + y (1 - t)) dy     (dz = 2 dy)
+// and the biases start the accumulators instead of being added afterwards.
+__device__ __forceinline__ float tanh_hw(float y) {
     float t;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(0.5f * z));
-    return fmaf(0.5f, t, 0.5f);
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(y));
+    return t;
+}
+
+// four 8x8 BF16 matrices from shared memory (rows given by lanes 8m..8m+7)
+__device__ __forceinline__ void ldsm_x4(const __nv_bfloat16* p, unsigned int& r0, unsigned int& r1,
+                                        unsigned int& r2, unsigned int& r3) {
+    const unsigned int a = (unsigned int)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(a));
 }
 
 __device__ __forceinline__ size_t entry_index(int i, int k, size_t stride) {
@@ -75,7 +92,8 @@ __global__ void __launch_bounds__(TILE) k_mlp_rev(DevSys<T> s) {
 }
 
 // ---- one 16-pair tile ----------------------------------------------------------
-// stage[p] = (r bits, entry, mirrored entry, -) for rows p < cnt.
+// stage[p] = (r bits, entry, mirrored entry, -) for rows p < cnt.  w1s, w2s,
+// b1s, b2s hold the halved first- and second-layer weights and biases.
 template <bool ENERGY>
 __device__ __forceinline__ void mlp_tile(const int4* stage, int cnt, float rc, float b3, const __nv_bfloat16* w1s,
                                          const __nv_bfloat16* w2s, const float* b1s, const float* b2s,
@@ -91,27 +109,29 @@ __device__ __forceinline__ void mlp_tile(const int4* stage, int cnt, float rc, f
     const float rb = __shfl_sync(0xffffffffu, pr, g + 8);
     unsigned int aph[2][4], adp[2][4];
     rbf_fragments(ra, rb, rc, tig, aph, adp);
+    // ldmatrix row address of this lane: matrix lane / 8 covers k + 8 (lane / 8)
+    const int lr = lane & 7, lm = lane >> 3;
     // ---- layer 1 GEMM, SiLU, re-packed as layer 2 A operands ----
     unsigned int ah[4][4], adh[4][4];
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
-        float z[4] = {0.f, 0.f, 0.f, 0.f}, dzv[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int kt = 0; kt < 2; ++kt) {
-            unsigned int b0, b1;
-            b_frag(w1s, W1_LD, nt * 8, kt * 16, g, tig, b0, b1);
-            mma_bf16_16816(z, aph[kt], b0, b1);
-            mma_bf16_16816(dzv, adp[kt], b0, b1);
-        }
         const int ncol = nt * 8 + tig * 2;
         const float2 bb = *reinterpret_cast<const float2*>(b1s + ncol);
+        float y[4] = {bb.x, bb.y, bb.x, bb.y}, dy[4] = {0.f, 0.f, 0.f, 0.f};
+        unsigned int b[4];
+        ldsm_x4(w1s + (nt * 8 + lr) * W1_LD + 8 * lm, b[0], b[1], b[2], b[3]);
+#pragma unroll
+        for (int kt = 0; kt < 2; ++kt) {
+            mma_bf16_16816(y, aph[kt], b[2 * kt], b[2 * kt + 1]);
+            mma_bf16_16816(dy, adp[kt], b[2 * kt], b[2 * kt + 1]);
+        }
         float hv[4], dhv[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const float zz = z[e] + ((e & 1) ? bb.y : bb.x);
-            const float sg = sigm_tanh(zz);
-            hv[e] = zz * sg;
-            dhv[e] = sg * fmaf(zz, 1.f - sg, 1.f) * dzv[e];
+            const float t = tanh_hw(y[e]);
+            hv[e] = fmaf(y[e], t, y[e]);
+            const float a = fmaf(-y[e], t, y[e] + 1.f);
+            dhv[e] = fmaf(t, a, a) * dy[e];
         }
         const int kt2 = nt >> 1, off = (nt & 1) * 2;
         ah[kt2][off + 0] = pack_bf16x2(hv[0], hv[1]);
@@ -123,29 +143,32 @@ __device__ __forceinline__ void mlp_tile(const int4* stage, int cnt, float rc, f
     float ua = 0.f, ub = 0.f, dua = 0.f, dub = 0.f;
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
-        float z[4] = {0.f, 0.f, 0.f, 0.f}, dzv[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int kt = 0; kt < 4; ++kt) {
-            unsigned int b0, b1;
-            b_frag(w2s, W2_LD, nt * 8, kt * 16, g, tig, b0, b1);
-            mma_bf16_16816(z, ah[kt], b0, b1);
-            mma_bf16_16816(dzv, adh[kt], b0, b1);
-        }
         const int ncol = nt * 8 + tig * 2;
         const float2 bb = *reinterpret_cast<const float2*>(b2s + ncol);
         const float2 ww = *reinterpret_cast<const float2*>(w3s + ncol);
+        float y[4] = {bb.x, bb.y, bb.x, bb.y}, dy[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kh = 0; kh < 2; ++kh) {
+            unsigned int b[4];
+            ldsm_x4(w2s + (nt * 8 + lr) * W2_LD + 32 * kh + 8 * lm, b[0], b[1], b[2], b[3]);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                mma_bf16_16816(y, ah[2 * kh + q], b[2 * q], b[2 * q + 1]);
+                mma_bf16_16816(dy, adh[2 * kh + q], b[2 * q], b[2 * q + 1]);
+            }
+        }
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const float zz = z[e] + ((e & 1) ? bb.y : bb.x);
-            const float sg = sigm_tanh(zz);
+            const float t = tanh_hw(y[e]);
             const float w3v = (e & 1) ? ww.y : ww.x;
-            const float dd = w3v * sg * fmaf(zz, 1.f - sg, 1.f) * dzv[e];
+            const float a = fmaf(-y[e], t, y[e] + 1.f);
+            const float dd = fmaf(t, a, a) * dy[e];
             if (e < 2) {
-                if (ENERGY) ua = fmaf(w3v, zz * sg, ua);
-                dua += dd;
+                if (ENERGY) ua = fmaf(w3v, fmaf(y[e], t, y[e]), ua);
+                dua = fmaf(w3v, dd, dua);
             } else {
-                if (ENERGY) ub = fmaf(w3v, zz * sg, ub);
-                dub += dd;
+                if (ENERGY) ub = fmaf(w3v, fmaf(y[e], t, y[e]), ub);
+                dub = fmaf(w3v, dd, dub);
             }
         }
     }
@@ -168,6 +191,8 @@ __device__ __forceinline__ void mlp_tile(const int4* stage, int cnt, float rc, f
         ufb = __shfl_sync(0xffffffffu, ub, rs);
     }
     if (lane < 16 && pvalid) {
+        // dd is silu'(z2) dz2 already (the halving cancels): du/dr = w3 . dd;
+        // the force factor is -du/dr / r
         const float sv = -(p < 8 ? dfa : dfb) / pr;
         pf[st.y] = sv;
         pf[st.z] = sv;
@@ -181,7 +206,7 @@ __device__ __forceinline__ void mlp_tile(const int4* stage, int cnt, float rc, f
 
 // ---- unique pairs -> per-entry values -------------------------------------------
 template <class T, bool ENERGY>
-__global__ void __launch_bounds__(32 * MLP_WARPS) k_mlp_pairs(DevSys<T> s, int cur) {
+__global__ void __launch_bounds__(32 * MLP_WARPS, ESPP_MLP_MINB) k_mlp_pairs(DevSys<T> s, int cur) {
     __shared__ __align__(16) __nv_bfloat16 w1s[MLP_H * W1_LD];
     __shared__ __align__(16) __nv_bfloat16 w2s[MLP_H * W2_LD];
     __shared__ __align__(16) float b1s[MLP_H];
@@ -189,7 +214,16 @@ __global__ void __launch_bounds__(32 * MLP_WARPS) k_mlp_pairs(DevSys<T> s, int c
     __shared__ __align__(16) float w3s[MLP_H];
     __shared__ int4 stage[MLP_WARPS][MLP_STAGE];
     const MlpWeights* __restrict__ W = s.mlp;
-    load_mlp_weights(W, w1s, w2s, nullptr, b1s, b2s, w3s);
+    // halved first- and second-layer weights and biases (exact)
+    for (int e = threadIdx.x; e < MLP_H * MLP_NB; e += blockDim.x)
+        w1s[(e / MLP_NB) * W1_LD + e % MLP_NB] = __float2bfloat16(0.5f * __bfloat162float(W->W1[e]));
+    for (int e = threadIdx.x; e < MLP_H * MLP_H; e += blockDim.x)
+        w2s[(e / MLP_H) * W2_LD + e % MLP_H] = __float2bfloat16(0.5f * __bfloat162float(W->W2[e]));
+    for (int e = threadIdx.x; e < MLP_H; e += blockDim.x) {
+        b1s[e] = 0.5f * W->b1[e];
+        b2s[e] = 0.5f * W->b2[e];
+        w3s[e] = W->w3[e];
+    }
     __syncthreads();
     if (s.ctrl->abort) return;
     const float b3 = W->b3;
