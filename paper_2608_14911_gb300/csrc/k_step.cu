@@ -27,6 +27,9 @@
 #ifndef ESPP_STEP_MINB32
 #define ESPP_STEP_MINB32 10
 #endif
+#ifndef ESPP_STEP_PREFETCH
+#define ESPP_STEP_PREFETCH 1  // request the next batch's list groups early
+#endif
 
 namespace espp {
 
@@ -101,7 +104,7 @@ __device__ __forceinline__ void pair_term(const DevSys<T>& s, int ti, const Pair
 // Sum of the pair forces on particle i over its Verlet list.  The list is
 // read in batches of int4 groups: all indices of a batch first, then all
 // neighbour positions, then the arithmetic, so that each thread keeps several
-// independent loads in flight.
+// independent loads in flight; the next batch's indices are prefetched.
 template <class T, bool ENERGY, bool MULTI, bool FAST>
 __device__ __forceinline__ void pair_loop(const DevSys<T>& s, const V4<T>* __restrict__ P, int i, int n,
                                           const V4<T>& xi, int ti, const PairRec<T>* pr1,
@@ -111,20 +114,30 @@ __device__ __forceinline__ void pair_loop(const DevSys<T>& s, const V4<T>* __res
     const int ng = (n + 3) >> 2;
     const int4* __restrict__ nb = reinterpret_cast<const int4*>(s.nbr) + i;
     const size_t stride = (size_t)s.stride;
+    const int gcap = s.cap >> 2;  // groups allocated per particle (>= 2)
+    // the groups of the next batch are requested before the positions of the
+    // current one, so their latency overlaps the current batch; the first
+    // batch is read without waiting for the count (groups past the count are
+    // allocated, and dropped whole; the last group is padded with -1)
+    int4 nxt[GB];
+#pragma unroll
+    for (int q = 0; q < GB; ++q) nxt[q] = q < gcap ? __ldg(nb + q * stride) : make_int4(-1, -1, -1, -1);
     for (int g0 = 0; g0 < ng || g0 == 0; g0 += GB) {
         int jj[4 * GB];
 #pragma unroll
         for (int q = 0; q < GB; ++q) {
-            // the first batch is read without waiting for the count (the list
-            // holds at least GB groups); the last group is padded with -1 and
-            // groups past the count are dropped whole
-            const bool want = g0 == 0 || g0 + q < ng;
-            int4 a = want ? __ldg(nb + (g0 + q) * stride) : make_int4(-1, -1, -1, -1);
+            if (!ESPP_STEP_PREFETCH && g0 > 0) nxt[q] = __ldg(nb + (g0 + q) * stride);
+            int4 a = nxt[q];
             if (g0 + q >= ng) a = make_int4(-1, -1, -1, -1);
             jj[4 * q + 0] = a.x;
             jj[4 * q + 1] = a.y;
             jj[4 * q + 2] = a.z;
             jj[4 * q + 3] = a.w;
+        }
+#pragma unroll
+        for (int q = 0; q < GB; ++q) {
+            const int gn = g0 + GB + q;
+            if (ESPP_STEP_PREFETCH && gn < gcap) nxt[q] = __ldg(nb + gn * stride);
         }
         int codes = 0;
 #pragma unroll
