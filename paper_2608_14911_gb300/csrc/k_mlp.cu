@@ -1,36 +1,37 @@
 // Learned coarse-grained pair potential on the tensor cores: a radial-basis
 // MLP u(r) (32 Gaussian bases with a cosine cutoff envelope -> 64 SiLU -> 64
 // SiLU -> 1), BF16 weights and activations, FP32 accumulation.  The force
-// needs du/dr; it is carried forward through the same two GEMMs as a second
-// set of 16 rows (the tangent d/dr of every activation), so one pass gives u
-// and du/dr for 16 pairs:
-//   [z1; dz1] = [phi; dphi/dr] W1^T            (2 x 16 x 32 . 32 x 64)
+// needs du/dr; it is carried forward through the same two GEMMs as the
+// tangent d/dr of every activation, in the rows below the values, so one
+// pass gives u and du/dr for 8 pairs (rows 0-7 values, rows 8-15 tangents):
+//   [z1; dz1] = [phi; dphi/dr] W1^T            (16 x 32 . 32 x 64)
 //   h1 = silu(z1 + b1),  dh1 = silu'(z1 + b1) dz1
-//   [z2; dz2] = [h1; dh1] W2^T                 (2 x 16 x 64 . 64 x 64)
+//   [z2; dz2] = [h1; dh1] W2^T                 (16 x 64 . 64 x 64)
 //   u = w3 . silu(z2 + b2) + b3,  du/dr = w3 . (silu'(z2 + b2) dz2)
 // The accumulator fragments of the first GEMM are re-packed in registers as
 // the A operand of the second (the m16n8 accumulator layout of two adjacent
 // n-tiles equals the m16k16 A layout), so activations never touch memory.
 //
-// Each unordered pair is evaluated once.  Three kernels:
+// Each unordered pair is evaluated once.  Kernels:
 //   k_mlp_rev     (list builds) for every list entry (i, j) with j > i, the
-//                 index of the mirrored entry (j, i) in j's list
-//   k_mlp_pairs   warp per 32 particles: their entries with j > i inside the
-//                 MLP cutoff are compacted through a shared staging buffer
-//                 into dense 16-pair tiles; -du/dr / r (and u) of each pair
-//                 go to both entries of the pair (zero beyond the cutoff)
+//                 index of the mirrored entry (j, i) in j's list, and the
+//                 array of all unordered pairs of the list
+//   k_mlp_stage   thread per unordered pair: the pairs inside the MLP cutoff
+//                 go to a dense pair array (r, entry, mirrored entry)
+//   k_mlp_tiles   warps stream the dense array in 8-pair tensor-core tiles;
+//                 -du/dr / r (and u) of each pair go to both of its entries
 //   k_mlp_gather  thread per particle: force, energy and virial sums over
-//                 its full list from the per-entry values, in list order
-// Every entry is written once per evaluation and summed in a fixed order, so
-// the forces do not depend on the order in which warps run.
+//                 its full list from the per-entry values, in list order,
+//                 over the entries inside the cutoff
+// Every entry inside the cutoff is written once per evaluation and summed in
+// a fixed order, so the forces do not depend on the order in which warps run.
 #include "mlp_common.cuh"
 
 namespace espp {
 
 constexpr int MLP_WARPS = 4;
-constexpr int MLP_STAGE = 48;  // < 16 pending + 32 new
 #ifndef ESPP_MLP_MINB
-#define ESPP_MLP_MINB 4  // resident blocks of k_mlp_pairs per SM the registers must allow
+#define ESPP_MLP_MINB 4  // resident blocks of k_mlp_tiles per SM the registers must allow
 #endif
 
 // The tile works with y = z / 2: the weights and biases are halved when they
@@ -58,161 +59,267 @@ __device__ __forceinline__ size_t entry_index(int i, int k, size_t stride) {
     return 4 * ((size_t)(k >> 2) * stride + i) + (k & 3);
 }
 
-// ---- mirrored entries (list builds) -----------------------------------------
+// Squared distance of a list pair as both kernels that decide "inside the
+// cutoff" compute it: the same operations with explicit rounding, so the
+// decision taken from the pair's two entries agrees (the two displacements are
+// exact negatives of each other).
+template <class T>
+__device__ __forceinline__ float mlp_r2(const V4<T>& xi, T xim, T yim, T zim, const V4<T>& xj, T L0, T L1, T L2,
+                                        int code, float& dx, float& dy, float& dz) {
+    dx = (float)shifted_diff(xi.x, xim, xj.x, L0, code & 3);
+    dy = (float)shifted_diff(xi.y, yim, xj.y, L1, (code >> 2) & 3);
+    dz = (float)shifted_diff(xi.z, zim, xj.z, L2, code >> 4);
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+// Per-warp shared buffer of int4 records, flushed to a global array at a
+// warp-aggregated atomic offset (one atomic per ~500 records).
+constexpr int STAGE_BUF = 512;
+
+struct WarpAppender {
+    int4* buf;
+    int4* out;
+    int* count;
+    int cap;
+    unsigned int* err;
+    int fill;
+    __device__ __forceinline__ void push(bool valid, int4 rec) {
+        const int lane = threadIdx.x & 31;
+        const unsigned int m = __ballot_sync(0xffffffffu, valid);
+        if (valid) buf[fill + __popc(m & ((1u << lane) - 1u))] = rec;
+        fill += __popc(m);
+        __syncwarp();
+        if (fill > STAGE_BUF - 32) flush();
+    }
+    __device__ __forceinline__ void flush() {
+        const int lane = threadIdx.x & 31;
+        int base = 0;
+        if (lane == 0 && fill > 0) base = atomicAdd(count, fill);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const int room = cap - base;
+        if (lane == 0 && fill > room) atomicOr(err, ERRBIT_OVERFLOW);  // cannot happen: sized for every pair
+        for (int k = lane; k < fill && k < room; k += 32) out[base + k] = buf[k];
+        __syncwarp();
+        fill = 0;
+    }
+};
+
+// ---- mirrored entries and the upper-pair array (list builds) -------------------
+// Warp per 32 particles, lanes over list entries.  For every entry (i, j)
+// with j > i: the index of the mirrored entry (j, i), searched in j's list for
+// the replicas just rebuilt and kept for the others, and the record (entry,
+// mirrored entry, replica) in the array of all unordered pairs of the list.
 template <class T>
 __global__ void __launch_bounds__(TILE) k_mlp_rev(DevSys<T> s) {
+    __shared__ int4 buf[TILE / 32][STAGE_BUF];
     if (s.ctrl->abort) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const size_t stride = (size_t)s.stride;
     const int4* __restrict__ nbr4 = reinterpret_cast<const int4*>(s.nbr);
+    WarpAppender ap{buf[warp], s.mlp_upper, s.mlp_nupper, s.mlp_upper_cap, &s.ctrl->err, 0};
     for (int t = blockIdx.x; t < s.ntiles; t += gridDim.x) {
         const Tile tl = s.tiles[t];
-        if (!s.now[tl.rep] || (int)threadIdx.x >= tl.count) continue;
-        const int i = tl.start + threadIdx.x;
-        const int n = s.nbr_cnt[i];
-        for (int k = 0; k < n; ++k) {
-            const size_t e = entry_index(i, k, stride);
-            const int j = nbr_slot(s.nbr[e]);
-            if (j <= i) continue;
-            // the list is symmetric: i is in j's list
-            const int nj = s.nbr_cnt[j];
-            size_t found = e;
-            for (int g = 0; 4 * g < nj; ++g) {
-                const int4 q = nbr4[(size_t)g * stride + j];
-                const int hit = nbr_slot(q.x) == i ? 0 : nbr_slot(q.y) == i ? 1 : nbr_slot(q.z) == i ? 2
-                                                                           : nbr_slot(q.w) == i ? 3 : -1;
-                if (hit >= 0 && 4 * g + hit < nj) {
-                    found = entry_index(j, 4 * g + hit, stride);
-                    break;
+        const int p0 = warp * 32;
+        if (p0 >= tl.count) continue;
+        const int p1 = min(tl.count, p0 + 32);
+        const bool fresh = s.now[tl.rep] != 0;
+        for (int pi = p0; pi < p1; ++pi) {
+            const int i = tl.start + pi;
+            const int n = s.nbr_cnt[i];
+            for (int c0 = 0; c0 < n; c0 += 32) {
+                const int c = c0 + lane;
+                bool upper = false;
+                size_t e = 0, found = 0;
+                if (c < n) {
+                    e = entry_index(i, c, stride);
+                    const int j = nbr_slot(s.nbr[e]);
+                    upper = j > i;
+                    if (upper && fresh) {
+                        // the list is symmetric: i is in j's list
+                        const int nj = s.nbr_cnt[j];
+                        found = e;
+                        for (int g = 0; 4 * g < nj; ++g) {
+                            const int4 q = nbr4[(size_t)g * stride + j];
+                            const int hit = nbr_slot(q.x) == i ? 0 : nbr_slot(q.y) == i ? 1
+                                          : nbr_slot(q.z) == i ? 2 : nbr_slot(q.w) == i ? 3 : -1;
+                            if (hit >= 0 && 4 * g + hit < nj) {
+                                found = entry_index(j, 4 * g + hit, stride);
+                                break;
+                            }
+                        }
+                        if (found == e) atomicOr(&s.ctrl->err, ERRBIT_ASYM);  // cannot happen for a symmetric list
+                        s.mlp_rev[e] = (int)found;
+                    } else if (upper) {
+                        found = (size_t)s.mlp_rev[e];
+                    }
                 }
+                ap.push(upper, make_int4((int)e, (int)found, tl.rep, 0));
             }
-            if (found == e) atomicOr(&s.ctrl->err, ERRBIT_ASYM);  // cannot happen for a symmetric list
-            s.mlp_rev[e] = (int)found;
+        }
+    }
+    ap.flush();
+}
+
+// ---- one 8-pair tile ------------------------------------------------------------
+// Rows g and g + 8 of every m16n8k16 operand belong to the same pair g: row g
+// carries the values (features, activations), row g + 8 their derivatives
+// with respect to r.  A lane then holds, for its columns, both z and dz/dr of
+// one pair, so the SiLU and its derivative stay inside the lane, and a tile
+// needs half the registers of two separate 16-row streams.
+//
+// Features of pair g (distance r) for the first layer: phi in row g, dphi/dr
+// in row g + 8, columns 2t, 2t+1 (+8) of both k-tiles.
+__device__ __forceinline__ void rbf_rows(float r, float rc, int t, unsigned int a[2][4]) {
+    const float wid = rc / (MLP_NB - 1);
+    const float inv2w2 = 0.5f / (wid * wid), invw2 = 1.0f / (wid * wid);
+    const float pirc = 3.14159265358979f / rc;
+    const float fc = 0.5f * (__cosf(pirc * r) + 1.f);
+    const float dfc = -0.5f * pirc * __sinf(pirc * r);
+#pragma unroll
+    for (int kt = 0; kt < 2; ++kt) {
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int col = kt * 16 + half * 8 + t * 2;
+            float ph[2], dp[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const float d = r - wid * (float)(col + q);
+                const float gq = __expf(-d * d * inv2w2);
+                ph[q] = gq * fc;
+                dp[q] = gq * (dfc - d * invw2 * fc);
+            }
+            a[kt][2 * half + 0] = pack_bf16x2(ph[0], ph[1]);
+            a[kt][2 * half + 1] = pack_bf16x2(dp[0], dp[1]);
         }
     }
 }
 
-// ---- one 16-pair tile ----------------------------------------------------------
-// stage[p] = (r bits, entry, mirrored entry, -) for rows p < cnt.  w1s, w2s,
-// b1s, b2s hold the halved first- and second-layer weights and biases.
+// stage[p] = (r bits, entry, mirrored entry, -) for pairs p < cnt (global
+// memory).  w1s, w2s, b1s, b2s hold the halved first- and second-layer
+// weights and biases.
 template <bool ENERGY>
-__device__ __forceinline__ void mlp_tile(const int4* stage, int cnt, float rc, float b3, const __nv_bfloat16* w1s,
-                                         const __nv_bfloat16* w2s, const float* b1s, const float* b2s,
-                                         const float* w3s, float* __restrict__ pf, float* __restrict__ pu) {
+__device__ __forceinline__ void mlp_tile8(const int4* stage, int cnt, float rc, float b3, const __nv_bfloat16* w1s,
+                                          const __nv_bfloat16* w2s, const float* b1s, const float* b2s,
+                                          const float* w3s, float* __restrict__ pf, float* __restrict__ pu) {
     const int lane = threadIdx.x & 31;
     const int g = lane >> 2, tig = lane & 3;
-    const int p = lane & 15;
-    const bool pvalid = p < cnt;
-    const int4 st = pvalid ? stage[p] : make_int4(__float_as_int(rc), 0, 0, 0);
-    const float pr = __int_as_float(st.x);
-    // rows g and g + 8 of the tile
-    const float ra = __shfl_sync(0xffffffffu, pr, g);
-    const float rb = __shfl_sync(0xffffffffu, pr, g + 8);
-    unsigned int aph[2][4], adp[2][4];
-    rbf_fragments(ra, rb, rc, tig, aph, adp);
-    // ldmatrix row address of this lane: matrix lane / 8 covers k + 8 (lane / 8)
+    const bool gvalid = g < cnt;
+    const int4 st = gvalid ? stage[g] : make_int4(__float_as_int(rc), 0, 0, 0);
+    const float r = __int_as_float(st.x);
+    unsigned int af[2][4];
+    rbf_rows(r, rc, tig, af);
     const int lr = lane & 7, lm = lane >> 3;
-    // ---- layer 1 GEMM, SiLU, re-packed as layer 2 A operands ----
-    unsigned int ah[4][4], adh[4][4];
+    // ---- layer 1: [y; dy] = [phi; dphi] W1^T / 2 + [b1 / 2; 0] ----
+    unsigned int ah[4][4];
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
         const int ncol = nt * 8 + tig * 2;
         const float2 bb = *reinterpret_cast<const float2*>(b1s + ncol);
-        float y[4] = {bb.x, bb.y, bb.x, bb.y}, dy[4] = {0.f, 0.f, 0.f, 0.f};
+        float c[4] = {bb.x, bb.y, 0.f, 0.f};
         unsigned int b[4];
         ldsm_x4(w1s + (nt * 8 + lr) * W1_LD + 8 * lm, b[0], b[1], b[2], b[3]);
+        mma_bf16_16816(c, af[0], b[0], b[1]);
+        mma_bf16_16816(c, af[1], b[2], b[3]);
+        float h[2], dh[2];
 #pragma unroll
-        for (int kt = 0; kt < 2; ++kt) {
-            mma_bf16_16816(y, aph[kt], b[2 * kt], b[2 * kt + 1]);
-            mma_bf16_16816(dy, adp[kt], b[2 * kt], b[2 * kt + 1]);
-        }
-        float hv[4], dhv[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const float t = tanh_hw(y[e]);
-            hv[e] = fmaf(y[e], t, y[e]);
-            const float a = fmaf(-y[e], t, y[e] + 1.f);
-            dhv[e] = fmaf(t, a, a) * dy[e];
+        for (int e = 0; e < 2; ++e) {
+            const float y = c[e], t = tanh_hw(y);
+            h[e] = fmaf(y, t, y);
+            const float a = fmaf(-y, t, y + 1.f);
+            dh[e] = fmaf(t, a, a) * c[2 + e];
         }
         const int kt2 = nt >> 1, off = (nt & 1) * 2;
-        ah[kt2][off + 0] = pack_bf16x2(hv[0], hv[1]);
-        ah[kt2][off + 1] = pack_bf16x2(hv[2], hv[3]);
-        adh[kt2][off + 0] = pack_bf16x2(dhv[0], dhv[1]);
-        adh[kt2][off + 1] = pack_bf16x2(dhv[2], dhv[3]);
+        ah[kt2][off + 0] = pack_bf16x2(h[0], h[1]);
+        ah[kt2][off + 1] = pack_bf16x2(dh[0], dh[1]);
     }
-    // ---- layer 2 GEMM and the output layer, one n-tile at a time -
-    float ua = 0.f, ub = 0.f, dua = 0.f, dub = 0.f;
+    // ---- layer 2 and the output layer -------------------------------
+    float u = 0.f, du = 0.f;
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
         const int ncol = nt * 8 + tig * 2;
         const float2 bb = *reinterpret_cast<const float2*>(b2s + ncol);
         const float2 ww = *reinterpret_cast<const float2*>(w3s + ncol);
-        float y[4] = {bb.x, bb.y, bb.x, bb.y}, dy[4] = {0.f, 0.f, 0.f, 0.f};
+        float c[4] = {bb.x, bb.y, 0.f, 0.f};
 #pragma unroll
         for (int kh = 0; kh < 2; ++kh) {
             unsigned int b[4];
             ldsm_x4(w2s + (nt * 8 + lr) * W2_LD + 32 * kh + 8 * lm, b[0], b[1], b[2], b[3]);
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                mma_bf16_16816(y, ah[2 * kh + q], b[2 * q], b[2 * q + 1]);
-                mma_bf16_16816(dy, adh[2 * kh + q], b[2 * q], b[2 * q + 1]);
-            }
+            mma_bf16_16816(c, ah[2 * kh], b[0], b[1]);
+            mma_bf16_16816(c, ah[2 * kh + 1], b[2], b[3]);
         }
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const float t = tanh_hw(y[e]);
-            const float w3v = (e & 1) ? ww.y : ww.x;
-            const float a = fmaf(-y[e], t, y[e] + 1.f);
-            const float dd = fmaf(t, a, a) * dy[e];
-            if (e < 2) {
-                if (ENERGY) ua = fmaf(w3v, fmaf(y[e], t, y[e]), ua);
-                dua = fmaf(w3v, dd, dua);
-            } else {
-                if (ENERGY) ub = fmaf(w3v, fmaf(y[e], t, y[e]), ub);
-                dub = fmaf(w3v, dd, dub);
-            }
+        for (int e = 0; e < 2; ++e) {
+            const float y = c[e], t = tanh_hw(y), w3v = e ? ww.y : ww.x;
+            const float a = fmaf(-y, t, y + 1.f);
+            du = fmaf(w3v, fmaf(t, a, a) * c[2 + e], du);
+            if (ENERGY) u = fmaf(w3v, fmaf(y, t, y), u);
         }
     }
-    // sum over the four lanes of a row group
+    // sum over the four lanes of pair g
 #pragma unroll
     for (int o = 1; o < 4; o <<= 1) {
-        if (ENERGY) {
-            ua += __shfl_xor_sync(0xffffffffu, ua, o);
-            ub += __shfl_xor_sync(0xffffffffu, ub, o);
-        }
-        dua += __shfl_xor_sync(0xffffffffu, dua, o);
-        dub += __shfl_xor_sync(0xffffffffu, dub, o);
+        du += __shfl_xor_sync(0xffffffffu, du, o);
+        if (ENERGY) u += __shfl_xor_sync(0xffffffffu, u, o);
     }
-    // row p lives in lane 4 (p mod 8), first (p < 8) or second half
-    const int rs = 4 * (p & 7);
-    const float dfa = __shfl_sync(0xffffffffu, dua, rs), dfb = __shfl_sync(0xffffffffu, dub, rs);
-    float ufa = 0.f, ufb = 0.f;
-    if (ENERGY) {
-        ufa = __shfl_sync(0xffffffffu, ua, rs);
-        ufb = __shfl_sync(0xffffffffu, ub, rs);
-    }
-    if (lane < 16 && pvalid) {
-        // dd is silu'(z2) dz2 already (the halving cancels): du/dr = w3 . dd;
+    if (tig == 0 && gvalid) {
+        // the halving cancels in the tangent: du/dr = w3 . (silu'(z2) dz2);
         // the force factor is -du/dr / r
-        const float sv = -(p < 8 ? dfa : dfb) / pr;
+        const float sv = -du / r;
         pf[st.y] = sv;
         pf[st.z] = sv;
         if (ENERGY) {
-            const float u = (p < 8 ? ufa : ufb) + b3;
-            pu[st.y] = u;
-            pu[st.z] = u;
+            pu[st.y] = u + b3;
+            pu[st.z] = u + b3;
         }
     }
 }
 
-// ---- unique pairs -> per-entry values -------------------------------------------
+// ---- pairs inside the cutoff -> a dense pair array -------------------------------
+// Thread per unordered pair of the list; the pairs inside the cutoff go to the
+// dense array through per-warp shared buffers.  Their order there does not
+// matter: every pair's result depends only on its own distance.
+template <class T>
+__global__ void __launch_bounds__(TILE) k_mlp_stage(DevSys<T> s, int cur) {
+    __shared__ int4 buf[TILE / 32][STAGE_BUF];
+    if (s.ctrl->abort) return;
+    const float rc = s.mlp->rc, rc2 = rc * rc;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const V4<T>* __restrict__ P = s.pos[cur];
+    const int stride = s.stride;
+    const int nu = min(*s.mlp_nupper, s.mlp_upper_cap);
+    WarpAppender ap{buf[warp], s.mlp_pairs, s.mlp_npairs, s.mlp_pairs_cap, &s.ctrl->err, 0};
+    const int nthreads = gridDim.x * blockDim.x;
+    for (int base = (blockIdx.x * blockDim.x + warp * 32); base < nu; base += nthreads) {
+        const int k = base + lane;
+        bool valid = false;
+        int4 rec = make_int4(0, 0, 0, 0);
+        if (k < nu) {
+            const int4 up = s.mlp_upper[k];
+            const int en = s.nbr[up.x];
+            const int i = (up.x >> 2) % stride;
+            const RepGeom<T>& geo = s.reps[up.z];
+            const T L0 = geo.L[0], L1 = geo.L[1], L2 = geo.L[2];
+            const V4<T> xi = ld4<T>(P + i);
+            const V4<T> xj = ld4<T>(P + nbr_slot(en));
+            float dx, dy, dz;
+            const float r2 = mlp_r2(xi, (T)(xi.x - L0), (T)(xi.y - L1), (T)(xi.z - L2), xj, L0, L1, L2,
+                                    nbr_code(en), dx, dy, dz);
+            valid = r2 < rc2;
+            rec = make_int4(__float_as_int(sqrtf(r2)), up.x, up.y, 0);
+        }
+        ap.push(valid, rec);
+    }
+    ap.flush();
+}
+
+// ---- dense pair tiles on the tensor cores -------------------------------------
 template <class T, bool ENERGY>
-__global__ void __launch_bounds__(32 * MLP_WARPS, ESPP_MLP_MINB) k_mlp_pairs(DevSys<T> s, int cur) {
+__global__ void __launch_bounds__(32 * MLP_WARPS, ESPP_MLP_MINB) k_mlp_tiles(DevSys<T> s) {
     __shared__ __align__(16) __nv_bfloat16 w1s[MLP_H * W1_LD];
     __shared__ __align__(16) __nv_bfloat16 w2s[MLP_H * W2_LD];
     __shared__ __align__(16) float b1s[MLP_H];
     __shared__ __align__(16) float b2s[MLP_H];
     __shared__ __align__(16) float w3s[MLP_H];
-    __shared__ int4 stage[MLP_WARPS][MLP_STAGE];
     const MlpWeights* __restrict__ W = s.mlp;
     // halved first- and second-layer weights and biases (exact)
     for (int e = threadIdx.x; e < MLP_H * MLP_NB; e += blockDim.x)
@@ -227,85 +334,20 @@ __global__ void __launch_bounds__(32 * MLP_WARPS, ESPP_MLP_MINB) k_mlp_pairs(Dev
     __syncthreads();
     if (s.ctrl->abort) return;
     const float b3 = W->b3;
-    const float rc = W->rc, rc2 = rc * rc;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned int lt_mask = (1u << lane) - 1u;
-    const V4<T>* __restrict__ P = s.pos[cur];
-    const size_t stride = (size_t)s.stride;
-    float* __restrict__ pf = s.mlp_pf;
-    float* __restrict__ pu = s.mlp_pu;
-    int4* st = stage[warp];
-    const int ntasks = s.ntiles * (TILE / 32);
-    for (int task = blockIdx.x * MLP_WARPS + warp; task < ntasks; task += gridDim.x * MLP_WARPS) {
-        const Tile tl = s.tiles[task / (TILE / 32)];
-        const int p0 = (task % (TILE / 32)) * 32;
-        if (p0 >= tl.count) continue;
-        const int p1 = min(tl.count, p0 + 32);
-        const RepGeom<T>& geo = s.reps[tl.rep];
-        const T L0 = geo.L[0], L1 = geo.L[1], L2 = geo.L[2];
-        int nst = 0;  // staged pairs, uniform over the warp
-        for (int pi = p0; pi < p1; ++pi) {
-            const int i = tl.start + pi;
-            const V4<T> xi = ld4<T>(P + i);
-            const int n = s.nbr_cnt[i];
-            for (int c0 = 0; c0 < n; c0 += 32) {
-                const int c = c0 + lane;
-                bool valid = false, zero = false;
-                float r = 0.f;
-                size_t e = 0;
-                if (c < n) {
-                    e = entry_index(i, c, stride);
-                    const int en = s.nbr[e];
-                    const int j = nbr_slot(en);
-                    if (j > i) {
-                        const V4<T> xj = ld4<T>(P + j);
-                        const int code = nbr_code(en);
-                        const T ddx = shifted_diff(xi.x, (T)(xi.x - L0), xj.x, L0, code & 3);
-                        const T ddy = shifted_diff(xi.y, (T)(xi.y - L1), xj.y, L1, (code >> 2) & 3);
-                        const T ddz = shifted_diff(xi.z, (T)(xi.z - L2), xj.z, L2, code >> 4);
-                        const float r2 = (float)(ddx * ddx + ddy * ddy + ddz * ddz);
-                        if (r2 < rc2) {
-                            valid = true;
-                            r = sqrtf(r2);
-                        } else {
-                            zero = true;
-                        }
-                    }
-                }
-                const int erev = (valid || zero) ? s.mlp_rev[e] : 0;
-                if (zero) {
-                    pf[e] = 0.f;
-                    pf[erev] = 0.f;
-                    if (ENERGY) {
-                        pu[e] = 0.f;
-                        pu[erev] = 0.f;
-                    }
-                }
-                const unsigned int vm = __ballot_sync(0xffffffffu, valid);
-                if (valid) st[nst + __popc(vm & lt_mask)] = make_int4(__float_as_int(r), (int)e, erev, 0);
-                nst += __popc(vm);
-                __syncwarp();
-                while (nst >= 16) {
-                    mlp_tile<ENERGY>(st, 16, rc, b3, w1s, w2s, b1s, b2s, w3s, pf, pu);
-                    const int rem = nst - 16;
-                    int4 keep = make_int4(0, 0, 0, 0);
-                    if (lane < rem) keep = st[16 + lane];
-                    __syncwarp();
-                    if (lane < rem) st[lane] = keep;
-                    __syncwarp();
-                    nst = rem;
-                }
-            }
-        }
-        if (nst > 0) mlp_tile<ENERGY>(st, nst, rc, b3, w1s, w2s, b1s, b2s, w3s, pf, pu);
-        __syncwarp();
-    }
+    const float rc = W->rc;
+    const int np = min(*s.mlp_npairs, s.mlp_pairs_cap);
+    const int ntl = (np + 7) >> 3;
+    const int warp = threadIdx.x >> 5;
+    for (int t = blockIdx.x * MLP_WARPS + warp; t < ntl; t += gridDim.x * MLP_WARPS)
+        mlp_tile8<ENERGY>(s.mlp_pairs + 8 * (size_t)t, min(8, np - 8 * t), rc, b3, w1s, w2s, b1s, b2s, w3s,
+                          s.mlp_pf, s.mlp_pu);
 }
 
 // ---- per-particle sums over the full list -------------------------------------
 template <class T, bool ENERGY>
 __global__ void __launch_bounds__(TILE) k_mlp_gather(DevSys<T> s, int cur) {
     if (s.ctrl->abort) return;
+    const float rc = s.mlp->rc, rc2 = rc * rc;
     const V4<T>* __restrict__ P = s.pos[cur];
     const size_t stride = (size_t)s.stride;
     const int4* __restrict__ nbr4 = reinterpret_cast<const int4*>(s.nbr);
@@ -332,17 +374,17 @@ __global__ void __launch_bounds__(TILE) k_mlp_gather(DevSys<T> s, int cur) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 if (4 * g + k >= n) continue;
-                if (ENERGY) eu += uv[k];
-                if (sv[k] == 0.f) continue;  // beyond the cutoff (or a flat pair)
-                const int code = nbr_code(en[k]);
                 const V4<T> xj = ld4<T>(P + nbr_slot(en[k]));
-                const float dx = (float)shifted_diff(xi.x, xim, xj.x, L0, code & 3);
-                const float dy = (float)shifted_diff(xi.y, yim, xj.y, L1, (code >> 2) & 3);
-                const float dz = (float)shifted_diff(xi.z, zim, xj.z, L2, code >> 4);
+                float dx, dy, dz;
+                const float r2 = mlp_r2(xi, xim, yim, zim, xj, L0, L1, L2, nbr_code(en[k]), dx, dy, dz);
+                if (!(r2 < rc2)) continue;  // beyond the cutoff: the entry holds no value this step
                 fx = fmaf(sv[k], dx, fx);
                 fy = fmaf(sv[k], dy, fy);
                 fz = fmaf(sv[k], dz, fz);
-                if (ENERGY) ew = fmaf(sv[k], dx * dx + dy * dy + dz * dz, ew);
+                if (ENERGY) {
+                    eu += uv[k];
+                    ew = fmaf(sv[k], r2, ew);
+                }
             }
         }
         s.mlp_f[i] = make_float4(fx, fy, fz, eu);
@@ -352,20 +394,22 @@ __global__ void __launch_bounds__(TILE) k_mlp_gather(DevSys<T> s, int cur) {
 
 template <class T>
 int Launch<T>::mlp(const DevSys<T>& s, int cur, bool energy, cudaStream_t st) {
-    const int tasks = s.ntiles * (TILE / 32);
-    const int blocks = std::max(1, std::min((tasks + MLP_WARPS - 1) / MLP_WARPS, 152 * 16));
+    cudaMemsetAsync(s.mlp_npairs, 0, sizeof(int), st);
+    const int tblocks = 152 * ESPP_MLP_MINB;
+    k_mlp_stage<T><<<152 * 8, TILE, 0, st>>>(s, cur);
     if (energy) {
-        k_mlp_pairs<T, true><<<blocks, 32 * MLP_WARPS, 0, st>>>(s, cur);
+        k_mlp_tiles<T, true><<<tblocks, 32 * MLP_WARPS, 0, st>>>(s);
         k_mlp_gather<T, true><<<s.ntiles, TILE, 0, st>>>(s, cur);
     } else {
-        k_mlp_pairs<T, false><<<blocks, 32 * MLP_WARPS, 0, st>>>(s, cur);
+        k_mlp_tiles<T, false><<<tblocks, 32 * MLP_WARPS, 0, st>>>(s);
         k_mlp_gather<T, false><<<s.ntiles, TILE, 0, st>>>(s, cur);
     }
-    return 2;
+    return 3;
 }
 
 template <class T>
 int Launch<T>::mlp_rev(const DevSys<T>& s, cudaStream_t st) {
+    cudaMemsetAsync(s.mlp_nupper, 0, sizeof(int), st);
     k_mlp_rev<T><<<s.ntiles, TILE, 0, st>>>(s);
     return 1;
 }

@@ -99,6 +99,12 @@ template <class T> struct DevSys {
     float* mlp_pf;
     float* mlp_pu;
     int* mlp_rev;
+    int4* mlp_pairs;    // dense pairs inside the cutoff: (r bits, entry, mirrored entry, -)
+    int mlp_pairs_cap;
+    int* mlp_npairs;    // device counter of mlp_pairs
+    int4* mlp_upper;    // every unordered list pair: (entry, mirrored entry, replica, -)
+    int mlp_upper_cap;
+    int* mlp_nupper;    // device counter of mlp_upper
     int N;
     BondRec<T> bond;
     T rlist2;           // (rc + skin)^2

@@ -880,24 +880,42 @@ class System : public SystemBase {
     }
 
     // per-entry values and mirrored-entry indices of the learned potential,
-    // sized like the list (3 x 4 bytes per list slot)
+    // sized like the list (3 x 4 bytes per list slot), and the dense pair
+    // array (16 bytes per unordered pair)
     int alloc_mlp_buffers() {
         if (mlp_buf) cudaFree(mlp_buf);
         mlp_buf = nullptr;
         mlp_buf_cap = 0;
         d.mlp_pf = d.mlp_pu = nullptr;
         d.mlp_rev = nullptr;
+        d.mlp_pairs = nullptr;
+        d.mlp_npairs = nullptr;
+        d.mlp_pairs_cap = 0;
+        d.mlp_upper = nullptr;
+        d.mlp_nupper = nullptr;
+        d.mlp_upper_cap = 0;
         const size_t slots = (size_t)d.cap * d.stride;
+        // the pair arrays hold every unordered pair of the list; entry
+        // indices are 32-bit
+        const size_t npairs = slots / 2 + 64;
+        if (4 * slots > (size_t)INT32_MAX) return fail(ESPP_ERR_ARG, "list too large for the learned potential");
+        const size_t bytes = 3 * slots * sizeof(float) + 2 * npairs * sizeof(int4) + 64;
         void* p = nullptr;
-        cudaError_t e = cudaMalloc(&p, 3 * slots * sizeof(float));
+        cudaError_t e = cudaMalloc(&p, bytes);
         if (e != cudaSuccess) return fail(ESPP_ERR_CUDA, std::string("MLP buffers: ") + cudaGetErrorString(e));
-        e = cudaMemset(p, 0, 3 * slots * sizeof(float));
+        e = cudaMemset(p, 0, bytes);
         if (e != cudaSuccess) return fail(ESPP_ERR_CUDA, std::string("MLP buffers: ") + cudaGetErrorString(e));
         mlp_buf = p;
         mlp_buf_cap = d.cap;
-        d.mlp_pf = reinterpret_cast<float*>(p);
+        d.mlp_pairs = reinterpret_cast<int4*>(p);  // 256-byte aligned (cudaMalloc)
+        d.mlp_pairs_cap = (int)npairs;
+        d.mlp_upper = d.mlp_pairs + npairs;
+        d.mlp_upper_cap = (int)npairs;
+        d.mlp_pf = reinterpret_cast<float*>(d.mlp_upper + npairs);
         d.mlp_pu = d.mlp_pf + slots;
         d.mlp_rev = reinterpret_cast<int*>(d.mlp_pu + slots);
+        d.mlp_npairs = d.mlp_rev + slots;
+        d.mlp_nupper = d.mlp_npairs + 1;
         clear_graphs();
         return ESPP_OK;
     }
@@ -1258,7 +1276,7 @@ class System : public SystemBase {
                 if (rcode) return rcode;
                 CK(cudaGraphLaunch(cg->exec, st));
                 last_cg = cg;
-                launches += 1 + S * (d.mlp_on ? 3 : 1);
+                launches += 1 + S * (d.mlp_on ? 4 : 1);
                 p ^= (int)((fin ? (S - 1) : S) & 1);
                 next += S;
             }
