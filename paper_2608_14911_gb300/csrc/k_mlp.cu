@@ -105,59 +105,65 @@ struct WarpAppender {
 };
 
 // ---- mirrored entries and the upper-pair array (list builds) -------------------
-// Warp per 32 particles, lanes over list entries.  For every entry (i, j)
-// with j > i: the index of the mirrored entry (j, i), searched in j's list for
-// the replicas just rebuilt and kept for the others, and the record (entry,
-// mirrored entry, replica) in the array of all unordered pairs of the list.
+// Thread per particle.  For every entry (i, j) with j > i: the index of the
+// mirrored entry (j, i), searched in j's list for the replicas just rebuilt
+// and kept for the others, and the record (entry, mirrored entry, list entry,
+// replica) in the array of all unordered pairs of the list.  A warp scan of
+// the per-thread counts gives each thread a contiguous run of records at one
+// atomic offset per warp.
 template <class T>
 __global__ void __launch_bounds__(TILE) k_mlp_rev(DevSys<T> s) {
-    __shared__ int4 buf[TILE / 32][STAGE_BUF];
     if (s.ctrl->abort) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const size_t stride = (size_t)s.stride;
     const int4* __restrict__ nbr4 = reinterpret_cast<const int4*>(s.nbr);
-    WarpAppender ap{buf[warp], s.mlp_upper, s.mlp_nupper, s.mlp_upper_cap, &s.ctrl->err, 0};
     for (int t = blockIdx.x; t < s.ntiles; t += gridDim.x) {
         const Tile tl = s.tiles[t];
-        const int p0 = warp * 32;
-        if (p0 >= tl.count) continue;
-        const int p1 = min(tl.count, p0 + 32);
+        const bool active = (int)threadIdx.x < tl.count;
         const bool fresh = s.now[tl.rep] != 0;
-        for (int pi = p0; pi < p1; ++pi) {
-            const int i = tl.start + pi;
-            const int n = s.nbr_cnt[i];
-            for (int c0 = 0; c0 < n; c0 += 32) {
-                const int c = c0 + lane;
-                bool upper = false;
-                size_t e = 0, found = 0;
-                if (c < n) {
-                    e = entry_index(i, c, stride);
-                    const int j = nbr_slot(s.nbr[e]);
-                    upper = j > i;
-                    if (upper && fresh) {
-                        // the list is symmetric: i is in j's list
-                        const int nj = s.nbr_cnt[j];
-                        found = e;
-                        for (int g = 0; 4 * g < nj; ++g) {
-                            const int4 q = nbr4[(size_t)g * stride + j];
-                            const int hit = nbr_slot(q.x) == i ? 0 : nbr_slot(q.y) == i ? 1
-                                          : nbr_slot(q.z) == i ? 2 : nbr_slot(q.w) == i ? 3 : -1;
-                            if (hit >= 0 && 4 * g + hit < nj) {
-                                found = entry_index(j, 4 * g + hit, stride);
-                                break;
-                            }
-                        }
-                        if (found == e) atomicOr(&s.ctrl->err, ERRBIT_ASYM);  // cannot happen for a symmetric list
-                        s.mlp_rev[e] = (int)found;
-                    } else if (upper) {
-                        found = (size_t)s.mlp_rev[e];
+        const int i = tl.start + threadIdx.x;
+        const int n = active ? s.nbr_cnt[i] : 0;
+        int cnt = 0;
+        for (int k = 0; k < n; ++k) cnt += nbr_slot(s.nbr[entry_index(i, k, stride)]) > i ? 1 : 0;
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        int base = 0;
+        if (lane == 31 && incl > 0) base = atomicAdd(s.mlp_nupper, incl);
+        base = __shfl_sync(0xffffffffu, base, 31) + incl - cnt;
+        if (base + cnt > s.mlp_upper_cap) {
+            atomicOr(&s.ctrl->err, ERRBIT_OVERFLOW);  // cannot happen: sized for every pair
+            continue;
+        }
+        for (int k = 0; k < n; ++k) {
+            const size_t e = entry_index(i, k, stride);
+            const int en = s.nbr[e];
+            const int j = nbr_slot(en);
+            if (j <= i) continue;
+            size_t found = e;
+            if (fresh) {
+                // the list is symmetric: i is in j's list
+                const int nj = s.nbr_cnt[j];
+                for (int g = 0; 4 * g < nj; ++g) {
+                    const int4 q = nbr4[(size_t)g * stride + j];
+                    const int hit = nbr_slot(q.x) == i ? 0 : nbr_slot(q.y) == i ? 1 : nbr_slot(q.z) == i ? 2
+                                                                               : nbr_slot(q.w) == i ? 3 : -1;
+                    if (hit >= 0 && 4 * g + hit < nj) {
+                        found = entry_index(j, 4 * g + hit, stride);
+                        break;
                     }
                 }
-                ap.push(upper, make_int4((int)e, (int)found, tl.rep, 0));
+                if (found == e) atomicOr(&s.ctrl->err, ERRBIT_ASYM);  // cannot happen for a symmetric list
+                s.mlp_rev[e] = (int)found;
+            } else {
+                found = (size_t)s.mlp_rev[e];
             }
+            s.mlp_upper[base++] = make_int4((int)e, (int)found, en, tl.rep);
         }
     }
-    ap.flush();
 }
 
 // ---- one 8-pair tile ------------------------------------------------------------
@@ -295,9 +301,9 @@ __global__ void __launch_bounds__(TILE) k_mlp_stage(DevSys<T> s, int cur) {
         int4 rec = make_int4(0, 0, 0, 0);
         if (k < nu) {
             const int4 up = s.mlp_upper[k];
-            const int en = s.nbr[up.x];
+            const int en = up.z;
             const int i = (up.x >> 2) % stride;
-            const RepGeom<T>& geo = s.reps[up.z];
+            const RepGeom<T>& geo = s.reps[up.w];
             const T L0 = geo.L[0], L1 = geo.L[1], L2 = geo.L[2];
             const V4<T> xi = ld4<T>(P + i);
             const V4<T> xj = ld4<T>(P + nbr_slot(en));

@@ -102,7 +102,7 @@ template <class T> struct DevSys {
     int4* mlp_pairs;    // dense pairs inside the cutoff: (r bits, entry, mirrored entry, -)
     int mlp_pairs_cap;
     int* mlp_npairs;    // device counter of mlp_pairs
-    int4* mlp_upper;    // every unordered list pair: (entry, mirrored entry, replica, -)
+    int4* mlp_upper;    // every unordered list pair: (entry, mirrored entry, list entry, replica)
     int mlp_upper_cap;
     int* mlp_nupper;    // device counter of mlp_upper
     int N;
