@@ -2,15 +2,12 @@
 // MLP u(r) (32 Gaussian bases with a cosine cutoff envelope -> 64 SiLU -> 64
 // SiLU -> 1), BF16 weights and activations, FP32 accumulation.  The force
 // needs du/dr; it is carried forward through the same two GEMMs as the
-// tangent d/dr of every activation, in the rows below the values, so one
-// pass gives u and du/dr for 8 pairs (rows 0-7 values, rows 8-15 tangents):
-//   [z1; dz1] = [phi; dphi/dr] W1^T            (16 x 32 . 32 x 64)
-//   h1 = silu(z1 + b1),  dh1 = silu'(z1 + b1) dz1
-//   [z2; dz2] = [h1; dh1] W2^T                 (16 x 64 . 64 x 64)
-//   u = w3 . silu(z2 + b2) + b3,  du/dr = w3 . (silu'(z2 + b2) dz2)
-// The accumulator fragments of the first GEMM are re-packed in registers as
-// the A operand of the second (the m16n8 accumulator layout of two adjacent
-// n-tiles equals the m16k16 A layout), so activations never touch memory.
+// tangent d/dr of every activation, so one pass gives u and du/dr:
+//   [z1; dz1] = [phi; dphi/dr] W1^T + [b1; 0]          (128 pairs x 32 . 32 x 64)
+//   h1 = silu(z1),  dh1 = silu'(z1) dz1
+//   [z2; dz2] = [h1; dh1] W2^T + [b2; 0]               (128 pairs x 64 . 64 x 64)
+//   u = w3 . silu(z2) + b3,  du/dr = w3 . (silu'(z2) dz2)
+// on the tcgen05 tensor cores with the accumulators in tensor memory.
 //
 // Each unordered pair is evaluated once.  Kernels:
 //   k_mlp_rev     (list builds) for every list entry (i, j) with j > i, the
@@ -18,21 +15,21 @@
 //                 array of all unordered pairs of the list
 //   k_mlp_stage   thread per unordered pair: the pairs inside the MLP cutoff
 //                 go to a dense pair array (r, entry, mirrored entry)
-//   k_mlp_tiles   warps stream the dense array in 8-pair tensor-core tiles;
+//   k_mlp_tc      CTAs stream the dense array in 128-pair tiles on the
+//                 tcgen05 tensor cores (accumulators in tensor memory);
 //                 -du/dr / r (and u) of each pair go to both of its entries
 //   k_mlp_gather  thread per particle: force, energy and virial sums over
 //                 its full list from the per-entry values, in list order,
 //                 over the entries inside the cutoff
 // Every entry inside the cutoff is written once per evaluation and summed in
 // a fixed order, so the forces do not depend on the order in which warps run.
+#include <cstring>
+
 #include "mlp_common.cuh"
+#include "tc_ptx.cuh"
 
 namespace espp {
 
-constexpr int MLP_WARPS = 4;
-#ifndef ESPP_MLP_MINB
-#define ESPP_MLP_MINB 4  // resident blocks of k_mlp_tiles per SM the registers must allow
-#endif
 
 // The tile works with y = z / 2: the weights and biases are halved when they
 // are staged (exact in BF16 and FP32), so that with t = tanh(y) (one hardware
@@ -44,15 +41,6 @@ __device__ __forceinline__ float tanh_hw(float y) {
     float t;
     asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(y));
     return t;
-}
-
-// four 8x8 BF16 matrices from shared memory (rows given by lanes 8m..8m+7)
-__device__ __forceinline__ void ldsm_x4(const __nv_bfloat16* p, unsigned int& r0, unsigned int& r1,
-                                        unsigned int& r2, unsigned int& r3) {
-    const unsigned int a = (unsigned int)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(a));
 }
 
 __device__ __forceinline__ size_t entry_index(int i, int k, size_t stride) {
@@ -166,120 +154,6 @@ __global__ void __launch_bounds__(TILE) k_mlp_rev(DevSys<T> s) {
     }
 }
 
-// ---- one 8-pair tile ------------------------------------------------------------
-// Rows g and g + 8 of every m16n8k16 operand belong to the same pair g: row g
-// carries the values (features, activations), row g + 8 their derivatives
-// with respect to r.  A lane then holds, for its columns, both z and dz/dr of
-// one pair, so the SiLU and its derivative stay inside the lane, and a tile
-// needs half the registers of two separate 16-row streams.
-//
-// Features of pair g (distance r) for the first layer: phi in row g, dphi/dr
-// in row g + 8, columns 2t, 2t+1 (+8) of both k-tiles.
-__device__ __forceinline__ void rbf_rows(float r, float rc, int t, unsigned int a[2][4]) {
-    const float wid = rc / (MLP_NB - 1);
-    const float inv2w2 = 0.5f / (wid * wid), invw2 = 1.0f / (wid * wid);
-    const float pirc = 3.14159265358979f / rc;
-    const float fc = 0.5f * (__cosf(pirc * r) + 1.f);
-    const float dfc = -0.5f * pirc * __sinf(pirc * r);
-#pragma unroll
-    for (int kt = 0; kt < 2; ++kt) {
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int col = kt * 16 + half * 8 + t * 2;
-            float ph[2], dp[2];
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const float d = r - wid * (float)(col + q);
-                const float gq = __expf(-d * d * inv2w2);
-                ph[q] = gq * fc;
-                dp[q] = gq * (dfc - d * invw2 * fc);
-            }
-            a[kt][2 * half + 0] = pack_bf16x2(ph[0], ph[1]);
-            a[kt][2 * half + 1] = pack_bf16x2(dp[0], dp[1]);
-        }
-    }
-}
-
-// stage[p] = (r bits, entry, mirrored entry, -) for pairs p < cnt (global
-// memory).  w1s, w2s, b1s, b2s hold the halved first- and second-layer
-// weights and biases.
-template <bool ENERGY>
-__device__ __forceinline__ void mlp_tile8(const int4* stage, int cnt, float rc, float b3, const __nv_bfloat16* w1s,
-                                          const __nv_bfloat16* w2s, const float* b1s, const float* b2s,
-                                          const float* w3s, float* __restrict__ pf, float* __restrict__ pu) {
-    const int lane = threadIdx.x & 31;
-    const int g = lane >> 2, tig = lane & 3;
-    const bool gvalid = g < cnt;
-    const int4 st = gvalid ? stage[g] : make_int4(__float_as_int(rc), 0, 0, 0);
-    const float r = __int_as_float(st.x);
-    unsigned int af[2][4];
-    rbf_rows(r, rc, tig, af);
-    const int lr = lane & 7, lm = lane >> 3;
-    // ---- layer 1: [y; dy] = [phi; dphi] W1^T / 2 + [b1 / 2; 0] ----
-    unsigned int ah[4][4];
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        const int ncol = nt * 8 + tig * 2;
-        const float2 bb = *reinterpret_cast<const float2*>(b1s + ncol);
-        float c[4] = {bb.x, bb.y, 0.f, 0.f};
-        unsigned int b[4];
-        ldsm_x4(w1s + (nt * 8 + lr) * W1_LD + 8 * lm, b[0], b[1], b[2], b[3]);
-        mma_bf16_16816(c, af[0], b[0], b[1]);
-        mma_bf16_16816(c, af[1], b[2], b[3]);
-        float h[2], dh[2];
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const float y = c[e], t = tanh_hw(y);
-            h[e] = fmaf(y, t, y);
-            const float a = fmaf(-y, t, y + 1.f);
-            dh[e] = fmaf(t, a, a) * c[2 + e];
-        }
-        const int kt2 = nt >> 1, off = (nt & 1) * 2;
-        ah[kt2][off + 0] = pack_bf16x2(h[0], h[1]);
-        ah[kt2][off + 1] = pack_bf16x2(dh[0], dh[1]);
-    }
-    // ---- layer 2 and the output layer -------------------------------
-    float u = 0.f, du = 0.f;
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        const int ncol = nt * 8 + tig * 2;
-        const float2 bb = *reinterpret_cast<const float2*>(b2s + ncol);
-        const float2 ww = *reinterpret_cast<const float2*>(w3s + ncol);
-        float c[4] = {bb.x, bb.y, 0.f, 0.f};
-#pragma unroll
-        for (int kh = 0; kh < 2; ++kh) {
-            unsigned int b[4];
-            ldsm_x4(w2s + (nt * 8 + lr) * W2_LD + 32 * kh + 8 * lm, b[0], b[1], b[2], b[3]);
-            mma_bf16_16816(c, ah[2 * kh], b[0], b[1]);
-            mma_bf16_16816(c, ah[2 * kh + 1], b[2], b[3]);
-        }
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const float y = c[e], t = tanh_hw(y), w3v = e ? ww.y : ww.x;
-            const float a = fmaf(-y, t, y + 1.f);
-            du = fmaf(w3v, fmaf(t, a, a) * c[2 + e], du);
-            if (ENERGY) u = fmaf(w3v, fmaf(y, t, y), u);
-        }
-    }
-    // sum over the four lanes of pair g
-#pragma unroll
-    for (int o = 1; o < 4; o <<= 1) {
-        du += __shfl_xor_sync(0xffffffffu, du, o);
-        if (ENERGY) u += __shfl_xor_sync(0xffffffffu, u, o);
-    }
-    if (tig == 0 && gvalid) {
-        // the halving cancels in the tangent: du/dr = w3 . (silu'(z2) dz2);
-        // the force factor is -du/dr / r
-        const float sv = -du / r;
-        pf[st.y] = sv;
-        pf[st.z] = sv;
-        if (ENERGY) {
-            pu[st.y] = u + b3;
-            pu[st.z] = u + b3;
-        }
-    }
-}
-
 // ---- pairs inside the cutoff -> a dense pair array -------------------------------
 // Thread per unordered pair of the list; the pairs inside the cutoff go to the
 // dense array through per-warp shared buffers.  Their order there does not
@@ -318,35 +192,230 @@ __global__ void __launch_bounds__(TILE) k_mlp_stage(DevSys<T> s, int cur) {
     ap.flush();
 }
 
-// ---- dense pair tiles on the tensor cores -------------------------------------
-template <class T, bool ENERGY>
-__global__ void __launch_bounds__(32 * MLP_WARPS, ESPP_MLP_MINB) k_mlp_tiles(DevSys<T> s) {
-    __shared__ __align__(16) __nv_bfloat16 w1s[MLP_H * W1_LD];
-    __shared__ __align__(16) __nv_bfloat16 w2s[MLP_H * W2_LD];
-    __shared__ __align__(16) float b1s[MLP_H];
-    __shared__ __align__(16) float b2s[MLP_H];
-    __shared__ __align__(16) float w3s[MLP_H];
+// ---- dense pair tiles on the 5th-generation tensor cores -------------------------
+// CTA of 128 threads, one pair per thread and tensor-memory lane.  Per tile:
+//   features   each thread writes its pair's phi (row of A0) and dphi/dr
+//              (row of A1) as BF16, plus a constant-1 column that carries the
+//              (halved) first-layer bias through the MMA
+//   layer 1    one thread issues tcgen05.mma: D[0:64) = A0 W1^T / 2 and
+//              D[64:128) = A1 W1^T / 2 (M 128, N 64, K 48), commit to an mbarrier
+//   epilogue   each thread reads its lane of D (y, dy), writes h = y(1+t) and
+//              dh = (1+t)(1+y(1-t)) dy (t = tanh y) as BF16 rows of A0/A1
+//              (K 80: 64 units + the constant column of the second-layer bias)
+//   layer 2    D[0:64) = A0 W2^T / 2, D[64:128) = A1 W2^T / 2
+//   output     du/dr = w3 . ((1+t)(1+y(1-t)) dy), u = w3 . y(1+t) + b3; the
+//              force factor -du/dr / r goes to both entries of the pair
+// The weights are staged once per CTA; the CTA walks tiles with a grid stride.
+constexpr int TC_M = 128;
+constexpr int TC_N = MLP_H;           // 64 hidden units
+constexpr int TC_K1 = 48;             // 32 features, bias column, zero padding
+constexpr int TC_K2 = 80;             // 64 units, bias column, zero padding
+constexpr uint32_t TC_COLS = 128;     // tensor-memory columns: values 0..63, tangents 64..127
+constexpr int TC_WAIT = 1 << 22;      // polls of an mbarrier before giving up
+constexpr int TC_CTAS_PER_SM = 3;     // shared memory (and tensor memory) per CTA allow three
+
+struct __align__(128) TcShared {
+    __nv_bfloat16 a[2 * TC_M * TC_K2];   // A0 | A1, layer 1 (K1) overlaid by layer 2 (K2)
+    __nv_bfloat16 w1[TC_N * TC_K1];      // B operand of layer 1
+    __nv_bfloat16 w2[TC_N * TC_K2];      // B operand of layer 2
+    float w3[TC_N];
+    uint64_t mbar;
+    uint32_t tmem;
+    int stop;
+};
+
+__device__ __forceinline__ void st_row16(__nv_bfloat16* base, int row, int k, int K, uint4 v) {
+    *reinterpret_cast<uint4*>(reinterpret_cast<char*>(base) + tc::core_offset(row, k, K)) = v;
+}
+
+template <bool ENERGY>
+__global__ void __launch_bounds__(TC_M, 1) k_mlp_tc(DevSys<float> s) {
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    TcShared& sh = *reinterpret_cast<TcShared*>(tc_smem);
+    const int tid = threadIdx.x, warp = tid >> 5;
     const MlpWeights* __restrict__ W = s.mlp;
-    // halved first- and second-layer weights and biases (exact)
-    for (int e = threadIdx.x; e < MLP_H * MLP_NB; e += blockDim.x)
-        w1s[(e / MLP_NB) * W1_LD + e % MLP_NB] = __float2bfloat16(0.5f * __bfloat162float(W->W1[e]));
-    for (int e = threadIdx.x; e < MLP_H * MLP_H; e += blockDim.x)
-        w2s[(e / MLP_H) * W2_LD + e % MLP_H] = __float2bfloat16(0.5f * __bfloat162float(W->W2[e]));
-    for (int e = threadIdx.x; e < MLP_H; e += blockDim.x) {
-        b1s[e] = 0.5f * W->b1[e];
-        b2s[e] = 0.5f * W->b2[e];
-        w3s[e] = W->w3[e];
+    // B operands: halved weights, halved bias in the constant column
+    for (int e = tid; e < TC_N * TC_K1; e += TC_M) {
+        const int n = e / TC_K1, k = e % TC_K1;
+        const float v = k < MLP_NB ? __bfloat162float(W->W1[n * MLP_NB + k]) : (k == MLP_NB ? W->b1[n] : 0.f);
+        *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<char*>(sh.w1) + tc::core_offset(n, k, TC_K1)) =
+            __float2bfloat16(0.5f * v);
     }
+    for (int e = tid; e < TC_N * TC_K2; e += TC_M) {
+        const int n = e / TC_K2, k = e % TC_K2;
+        const float v = k < MLP_H ? __bfloat162float(W->W2[n * MLP_H + k]) : (k == MLP_H ? W->b2[n] : 0.f);
+        *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<char*>(sh.w2) + tc::core_offset(n, k, TC_K2)) =
+            __float2bfloat16(0.5f * v);
+    }
+    for (int e = tid; e < TC_N; e += TC_M) sh.w3[e] = W->w3[e];
+    if (tid == 0) {
+        tc::mbar_init(&sh.mbar, 1);
+        sh.stop = s.ctrl->abort;
+    }
+    if (warp == 0) tc::tmem_alloc(&sh.tmem, TC_COLS);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
     __syncthreads();
-    if (s.ctrl->abort) return;
-    const float b3 = W->b3;
-    const float rc = W->rc;
+    tc::fence_after_sync();
+    const uint32_t tmem = sh.tmem;
+    const uint32_t lanes = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's 32 lanes
+    const float rc = W->rc, b3 = W->b3;
+    const float wid = rc / (MLP_NB - 1);
+    const float inv2w2 = 0.5f / (wid * wid), invw2 = 1.0f / (wid * wid);
+    const float pirc = 3.14159265358979f / rc;
     const int np = min(*s.mlp_npairs, s.mlp_pairs_cap);
-    const int ntl = (np + 7) >> 3;
-    const int warp = threadIdx.x >> 5;
-    for (int t = blockIdx.x * MLP_WARPS + warp; t < ntl; t += gridDim.x * MLP_WARPS)
-        mlp_tile8<ENERGY>(s.mlp_pairs + 8 * (size_t)t, min(8, np - 8 * t), rc, b3, w1s, w2s, b1s, b2s, w3s,
-                          s.mlp_pf, s.mlp_pu);
+    const int ntl = (np + TC_M - 1) / TC_M;
+    const uint32_t idesc = tc::idesc_bf16(TC_M, TC_N);
+    const uint32_t a_base = tc::smem_addr(sh.a), w1_base = tc::smem_addr(sh.w1), w2_base = tc::smem_addr(sh.w2);
+    __nv_bfloat16* A0 = sh.a;
+    float* __restrict__ pf = s.mlp_pf;
+    float* __restrict__ pu = s.mlp_pu;
+    uint32_t parity = 0;
+    bool ok = sh.stop == 0;
+    for (int tile = blockIdx.x; ok && tile < ntl; tile += gridDim.x) {
+        const int p = tile * TC_M + tid;
+        const bool valid = p < np;
+        const int4 rec = valid ? s.mlp_pairs[p] : make_int4(__float_as_int(rc), 0, 0, 0);
+        const float r = __int_as_float(rec.x);
+        // ---- features ----------------------------------------------------------
+        {
+            __nv_bfloat16* A1 = A0 + TC_M * TC_K1;
+            const float fc = 0.5f * (__cosf(pirc * r) + 1.f);
+            const float dfc = -0.5f * pirc * __sinf(pirc * r);
+#pragma unroll
+            for (int g = 0; g < MLP_NB / 8; ++g) {
+                unsigned int ph[4], dp[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float v[2], dv[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const float d = r - wid * (float)(8 * g + 2 * q + h);
+                        const float gk = __expf(-d * d * inv2w2);
+                        v[h] = gk * fc;
+                        dv[h] = gk * (dfc - d * invw2 * fc);
+                    }
+                    ph[q] = pack_bf16x2(v[0], v[1]);
+                    dp[q] = pack_bf16x2(dv[0], dv[1]);
+                }
+                st_row16(A0, tid, 8 * g, TC_K1, make_uint4(ph[0], ph[1], ph[2], ph[3]));
+                st_row16(A1, tid, 8 * g, TC_K1, make_uint4(dp[0], dp[1], dp[2], dp[3]));
+            }
+            st_row16(A0, tid, 32, TC_K1, make_uint4(pack_bf16x2(1.f, 0.f), 0u, 0u, 0u));
+            st_row16(A0, tid, 40, TC_K1, make_uint4(0u, 0u, 0u, 0u));
+            st_row16(A1, tid, 32, TC_K1, make_uint4(0u, 0u, 0u, 0u));
+            st_row16(A1, tid, 40, TC_K1, make_uint4(0u, 0u, 0u, 0u));
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0) {
+            constexpr uint32_t sbo = (TC_K1 / 8) * 128;
+#pragma unroll
+            for (int ks = 0; ks < TC_K1 / 16; ++ks) {
+                const uint64_t db = tc::smem_desc(w1_base + ks * 256, 128, sbo);
+                tc::mma(tmem, tc::smem_desc(a_base + ks * 256, 128, sbo), db, idesc, ks > 0);
+                tc::mma(tmem + 64, tc::smem_desc(a_base + TC_M * TC_K1 * 2 + ks * 256, 128, sbo), db, idesc,
+                        ks > 0);
+            }
+            tc::commit(&sh.mbar);
+        }
+        if (!__syncthreads_and(tc::mbar_wait(&sh.mbar, parity, TC_WAIT))) {
+            ok = false;
+            break;
+        }
+        parity ^= 1u;
+        tc::fence_after_sync();
+        // ---- layer-1 epilogue: h and dh rows of the layer-2 A operands -------------
+        {
+            __nv_bfloat16* A1 = A0 + TC_M * TC_K2;
+#pragma unroll
+            for (int c = 0; c < TC_N; c += 16) {
+                float y[16], dy[16];
+                tc::tmem_ld16x2(lanes + c, lanes + 64 + c, y, dy);
+                unsigned int hw[8], dw[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    float h2[2], d2[2];
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const float yy = y[2 * j + q], t = tanh_hw(yy);
+                        h2[q] = fmaf(yy, t, yy);
+                        const float a = fmaf(-yy, t, yy + 1.f);
+                        d2[q] = fmaf(t, a, a) * dy[2 * j + q];
+                    }
+                    hw[j] = pack_bf16x2(h2[0], h2[1]);
+                    dw[j] = pack_bf16x2(d2[0], d2[1]);
+                }
+                st_row16(A0, tid, c, TC_K2, make_uint4(hw[0], hw[1], hw[2], hw[3]));
+                st_row16(A0, tid, c + 8, TC_K2, make_uint4(hw[4], hw[5], hw[6], hw[7]));
+                st_row16(A1, tid, c, TC_K2, make_uint4(dw[0], dw[1], dw[2], dw[3]));
+                st_row16(A1, tid, c + 8, TC_K2, make_uint4(dw[4], dw[5], dw[6], dw[7]));
+            }
+            st_row16(A0, tid, 64, TC_K2, make_uint4(pack_bf16x2(1.f, 0.f), 0u, 0u, 0u));
+            st_row16(A0, tid, 72, TC_K2, make_uint4(0u, 0u, 0u, 0u));
+            st_row16(A1, tid, 64, TC_K2, make_uint4(0u, 0u, 0u, 0u));
+            st_row16(A1, tid, 72, TC_K2, make_uint4(0u, 0u, 0u, 0u));
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0) {
+            constexpr uint32_t sbo = (TC_K2 / 8) * 128;
+#pragma unroll
+            for (int ks = 0; ks < TC_K2 / 16; ++ks) {
+                const uint64_t db = tc::smem_desc(w2_base + ks * 256, 128, sbo);
+                tc::mma(tmem, tc::smem_desc(a_base + ks * 256, 128, sbo), db, idesc, ks > 0);
+                tc::mma(tmem + 64, tc::smem_desc(a_base + TC_M * TC_K2 * 2 + ks * 256, 128, sbo), db, idesc,
+                        ks > 0);
+            }
+            tc::commit(&sh.mbar);
+        }
+        if (!__syncthreads_and(tc::mbar_wait(&sh.mbar, parity, TC_WAIT))) {
+            ok = false;
+            break;
+        }
+        parity ^= 1u;
+        tc::fence_after_sync();
+        // ---- output layer ----------------------------------------------------------
+        float u = 0.f, du = 0.f;
+#pragma unroll
+        for (int c = 0; c < TC_N; c += 16) {
+            float y[16], dy[16];
+            tc::tmem_ld16x2(lanes + c, lanes + 64 + c, y, dy);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float yy = y[j], t = tanh_hw(yy), w3v = sh.w3[c + j];
+                const float a = fmaf(-yy, t, yy + 1.f);
+                du = fmaf(w3v, fmaf(t, a, a) * dy[j], du);
+                if (ENERGY) u = fmaf(w3v, fmaf(yy, t, yy), u);
+            }
+        }
+        if (valid) {
+            const float sv = -du / r;
+            pf[rec.y] = sv;
+            pf[rec.z] = sv;
+            if (ENERGY) {
+                pu[rec.y] = u + b3;
+                pu[rec.z] = u + b3;
+            }
+        }
+        // tensor-memory reads and shared-memory operands of this tile are done
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
+    if (!ok && sh.stop == 0) {
+        // a commit never arrived: record it, give the MMAs in flight one more
+        // bounded wait, then release the tensor memory
+        if (tid == 0) atomicOr(&s.ctrl->err, ERRBIT_TIMEOUT);
+        tc::mbar_wait(&sh.mbar, parity, TC_WAIT);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_free(tmem, TC_COLS);
 }
 
 // ---- per-particle sums over the full list -------------------------------------
@@ -398,16 +467,42 @@ __global__ void __launch_bounds__(TILE) k_mlp_gather(DevSys<T> s, int cur) {
     }
 }
 
+static_assert(sizeof(TcShared) <= 227 * 1024 / TC_CTAS_PER_SM, "tcgen05 tile CTA too large");
+
+// The learned potential's force pass runs in FP32/BF16 for both precisions of
+// the handle: the tensor-core kernel reads only the pair records and writes
+// the per-entry values, so one FP32 instantiation serves both.
+template <class T>
+static DevSys<float> as_float(const DevSys<T>& s) {
+    DevSys<float> f;
+    memset(&f, 0, sizeof(f));
+    f.ctrl = s.ctrl;
+    f.mlp = s.mlp;
+    f.mlp_pf = s.mlp_pf;
+    f.mlp_pu = s.mlp_pu;
+    f.mlp_pairs = s.mlp_pairs;
+    f.mlp_pairs_cap = s.mlp_pairs_cap;
+    f.mlp_npairs = s.mlp_npairs;
+    return f;
+}
+
+cudaError_t prepare_mlp_tc() {
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(TcShared));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_mlp_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcShared));
+}
+
 template <class T>
 int Launch<T>::mlp(const DevSys<T>& s, int cur, bool energy, cudaStream_t st) {
     cudaMemsetAsync(s.mlp_npairs, 0, sizeof(int), st);
-    const int tblocks = 152 * ESPP_MLP_MINB;
+    const int tblocks = 152 * TC_CTAS_PER_SM;
     k_mlp_stage<T><<<152 * 8, TILE, 0, st>>>(s, cur);
     if (energy) {
-        k_mlp_tiles<T, true><<<tblocks, 32 * MLP_WARPS, 0, st>>>(s);
+        k_mlp_tc<true><<<tblocks, TC_M, sizeof(TcShared), st>>>(as_float(s));
         k_mlp_gather<T, true><<<s.ntiles, TILE, 0, st>>>(s, cur);
     } else {
-        k_mlp_tiles<T, false><<<tblocks, 32 * MLP_WARPS, 0, st>>>(s);
+        k_mlp_tc<false><<<tblocks, TC_M, sizeof(TcShared), st>>>(as_float(s));
         k_mlp_gather<T, false><<<s.ntiles, TILE, 0, st>>>(s, cur);
     }
     return 3;

@@ -161,6 +161,8 @@ template <class T> struct Launch {
 void launch_adam(float* theta, float* m, float* v, float* grad, float lr, float b1, float b2, float eps,
                  int step, MlpWeights* W, cudaStream_t st);
 int mlp_ngrad();
+// once per process, before the learned potential's first launch
+cudaError_t prepare_mlp_tc();
 
 void launch_cg_map(const double* x, const int* img, const double* f, long long nsites, int bps, const double* L,
                    double* xs, double* fs, cudaStream_t st);

@@ -883,6 +883,10 @@ class System : public SystemBase {
     // sized like the list (3 x 4 bytes per list slot), and the dense pair
     // array (16 bytes per unordered pair)
     int alloc_mlp_buffers() {
+        {
+            static cudaError_t prep = prepare_mlp_tc();  // kernel attributes, once per process
+            if (prep != cudaSuccess) return fail(ESPP_ERR_CUDA, std::string("MLP kernel setup: ") + cudaGetErrorString(prep));
+        }
         if (mlp_buf) cudaFree(mlp_buf);
         mlp_buf = nullptr;
         mlp_buf_cap = 0;
