@@ -200,25 +200,25 @@ __global__ void __launch_bounds__(TILE) k_mlp_stage(DevSys<T> s, int cur) {
 //   layer 1    one thread issues tcgen05.mma: D[0:64) = A0 W1^T / 2 and
 //              D[64:128) = A1 W1^T / 2 (M 128, N 64, K 48), commit to an mbarrier
 //   epilogue   each thread reads its lane of D (y, dy), writes h = y(1+t) and
-//              dh = (1+t)(1+y(1-t)) dy (t = tanh y) as BF16 rows of A0/A1
-//              (K 80: 64 units + the constant column of the second-layer bias)
+//              dh = (1+t)(1+y(1-t)) dy (t = tanh y) as BF16 rows of A0/A1 (K 64)
 //   layer 2    D[0:64) = A0 W2^T / 2, D[64:128) = A1 W2^T / 2
-//   output     du/dr = w3 . ((1+t)(1+y(1-t)) dy), u = w3 . y(1+t) + b3; the
+//   output     y += b2 / 2; du/dr = w3 . ((1+t)(1+y(1-t)) dy), u = w3 . y(1+t) + b3; the
 //              force factor -du/dr / r goes to both entries of the pair
 // The weights are staged once per CTA; the CTA walks tiles with a grid stride.
 constexpr int TC_M = 128;
 constexpr int TC_N = MLP_H;           // 64 hidden units
 constexpr int TC_K1 = 48;             // 32 features, bias column, zero padding
-constexpr int TC_K2 = 80;             // 64 units, bias column, zero padding
+constexpr int TC_K2 = MLP_H;          // 64 units (the second-layer bias is added after the MMA)
 constexpr uint32_t TC_COLS = 128;     // tensor-memory columns: values 0..63, tangents 64..127
 constexpr int TC_WAIT = 1 << 22;      // polls of an mbarrier before giving up
-constexpr int TC_CTAS_PER_SM = 3;     // shared memory (and tensor memory) per CTA allow three
+constexpr int TC_CTAS_PER_SM = 4;     // tensor memory (4 x 128 columns) and shared memory allow four
 
 struct __align__(128) TcShared {
     __nv_bfloat16 a[2 * TC_M * TC_K2];   // A0 | A1, layer 1 (K1) overlaid by layer 2 (K2)
     __nv_bfloat16 w1[TC_N * TC_K1];      // B operand of layer 1
     __nv_bfloat16 w2[TC_N * TC_K2];      // B operand of layer 2
     float w3[TC_N];
+    float b2h[TC_N];                      // halved second-layer bias
     uint64_t mbar;
     uint32_t tmem;
     int stop;
@@ -229,7 +229,7 @@ __device__ __forceinline__ void st_row16(__nv_bfloat16* base, int row, int k, in
 }
 
 template <bool ENERGY>
-__global__ void __launch_bounds__(TC_M, 1) k_mlp_tc(DevSys<float> s) {
+__global__ void __launch_bounds__(TC_M, TC_CTAS_PER_SM) k_mlp_tc(DevSys<float> s) {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     TcShared& sh = *reinterpret_cast<TcShared*>(tc_smem);
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -243,11 +243,13 @@ __global__ void __launch_bounds__(TC_M, 1) k_mlp_tc(DevSys<float> s) {
     }
     for (int e = tid; e < TC_N * TC_K2; e += TC_M) {
         const int n = e / TC_K2, k = e % TC_K2;
-        const float v = k < MLP_H ? __bfloat162float(W->W2[n * MLP_H + k]) : (k == MLP_H ? W->b2[n] : 0.f);
         *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<char*>(sh.w2) + tc::core_offset(n, k, TC_K2)) =
-            __float2bfloat16(0.5f * v);
+            __float2bfloat16(0.5f * __bfloat162float(W->W2[n * MLP_H + k]));
     }
-    for (int e = tid; e < TC_N; e += TC_M) sh.w3[e] = W->w3[e];
+    for (int e = tid; e < TC_N; e += TC_M) {
+        sh.w3[e] = W->w3[e];
+        sh.b2h[e] = 0.5f * W->b2[e];
+    }
     if (tid == 0) {
         tc::mbar_init(&sh.mbar, 1);
         sh.stop = s.ctrl->abort;
@@ -353,10 +355,6 @@ __global__ void __launch_bounds__(TC_M, 1) k_mlp_tc(DevSys<float> s) {
                 st_row16(A1, tid, c, TC_K2, make_uint4(dw[0], dw[1], dw[2], dw[3]));
                 st_row16(A1, tid, c + 8, TC_K2, make_uint4(dw[4], dw[5], dw[6], dw[7]));
             }
-            st_row16(A0, tid, 64, TC_K2, make_uint4(pack_bf16x2(1.f, 0.f), 0u, 0u, 0u));
-            st_row16(A0, tid, 72, TC_K2, make_uint4(0u, 0u, 0u, 0u));
-            st_row16(A1, tid, 64, TC_K2, make_uint4(0u, 0u, 0u, 0u));
-            st_row16(A1, tid, 72, TC_K2, make_uint4(0u, 0u, 0u, 0u));
         }
         tc::fence_async_smem();
         tc::fence_before_sync();
@@ -387,7 +385,7 @@ __global__ void __launch_bounds__(TC_M, 1) k_mlp_tc(DevSys<float> s) {
             tc::tmem_ld16x2(lanes + c, lanes + 64 + c, y, dy);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const float yy = y[j], t = tanh_hw(yy), w3v = sh.w3[c + j];
+                const float yy = y[j] + sh.b2h[c + j], t = tanh_hw(yy), w3v = sh.w3[c + j];
                 const float a = fmaf(-yy, t, yy + 1.f);
                 du = fmaf(w3v, fmaf(t, a, a) * dy[j], du);
                 if (ENERGY) u = fmaf(w3v, fmaf(yy, t, yy), u);
