@@ -168,26 +168,39 @@ __global__ void __launch_bounds__(TILE) k_mlp_stage(DevSys<T> s, int cur) {
     const int stride = s.stride;
     const int nu = min(*s.mlp_nupper, s.mlp_upper_cap);
     WarpAppender ap{buf[warp], s.mlp_pairs, s.mlp_npairs, s.mlp_pairs_cap, &s.ctrl->err, 0};
+    // four records per thread and pass: four independent gather chains in flight
+    constexpr int U = 4;
     const int nthreads = gridDim.x * blockDim.x;
-    for (int base = (blockIdx.x * blockDim.x + warp * 32); base < nu; base += nthreads) {
-        const int k = base + lane;
-        bool valid = false;
-        int4 rec = make_int4(0, 0, 0, 0);
-        if (k < nu) {
-            const int4 up = s.mlp_upper[k];
-            const int en = up.z;
-            const int i = (up.x >> 2) % stride;
-            const RepGeom<T>& geo = s.reps[up.w];
-            const T L0 = geo.L[0], L1 = geo.L[1], L2 = geo.L[2];
-            const V4<T> xi = ld4<T>(P + i);
-            const V4<T> xj = ld4<T>(P + nbr_slot(en));
-            float dx, dy, dz;
-            const float r2 = mlp_r2(xi, (T)(xi.x - L0), (T)(xi.y - L1), (T)(xi.z - L2), xj, L0, L1, L2,
-                                    nbr_code(en), dx, dy, dz);
-            valid = r2 < rc2;
-            rec = make_int4(__float_as_int(sqrtf(r2)), up.x, up.y, 0);
+    for (int base = (blockIdx.x * blockDim.x + warp * 32) * U; base < nu; base += nthreads * U) {
+        int4 up[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int k = base + 32 * q + lane;
+            up[q] = k < nu ? s.mlp_upper[k] : make_int4(-1, 0, 0, 0);
         }
-        ap.push(valid, rec);
+        V4<T> xi[U], xj[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            if (up[q].x >= 0) {
+                xi[q] = ld4<T>(P + (up[q].x >> 2) % stride);
+                xj[q] = ld4<T>(P + nbr_slot(up[q].z));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            bool valid = false;
+            int4 rec = make_int4(0, 0, 0, 0);
+            if (up[q].x >= 0) {
+                const RepGeom<T>& geo = s.reps[up[q].w];
+                const T L0 = geo.L[0], L1 = geo.L[1], L2 = geo.L[2];
+                float dx, dy, dz;
+                const float r2 = mlp_r2(xi[q], (T)(xi[q].x - L0), (T)(xi[q].y - L1), (T)(xi[q].z - L2), xj[q],
+                                        L0, L1, L2, nbr_code(up[q].z), dx, dy, dz);
+                valid = r2 < rc2;
+                rec = make_int4(__float_as_int(sqrtf(r2)), up[q].x, up[q].y, 0);
+            }
+            ap.push(valid, rec);
+        }
     }
     ap.flush();
 }
