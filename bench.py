@@ -652,12 +652,24 @@ def suite_learned_cg(a, sync, out):
     sync()
     train_ms = e0.elapsed_time(e1)
     trained = c.mlp_weights()
+    # tensor work of one frame: unique pairs inside the cutoff x (24576 flop
+    # forward, values and tangents, + 2 x 24576 backward to the weights)
+    tr_pairs = float(c.rdf_counts(3.5, 175).sum()) - len(cg_bonds)
+    tr_flop = 3 * 24576.0 * tr_pairs
+    tr_s = train_ms / 1e3 / a.cg_epochs / F
+    peaks_t, peak_kind_t = measured_peaks()
+    tr_peak = peaks_t.get("bf16_tflops_sustained", peaks_t["bf16_tflops"])
     out["training"] = {"workload": "kg_2000x200_mapped_4to1_100000_sites", "frames": F, "frames_spec": 2000,
                        "epochs": a.cg_epochs, "batch_frames": a.cg_batch,
                        "adam_steps": a.cg_epochs * (-(-F // a.cg_batch)), "s_per_epoch": train_ms / 1e3 / a.cg_epochs,
                        "s_per_epoch_per_frame": train_ms / 1e3 / a.cg_epochs / F,
                        "loss_first_epoch": float(loss[0]), "loss_last_epoch": float(loss[-1]),
-                       "cg_mean_bond": bmean}
+                       "cg_mean_bond": bmean,
+                       "roofline": {"bound": "tensor", "unique_pairs_per_frame": tr_pairs,
+                                    "flop_per_frame": tr_flop, "achieved": tr_flop / tr_s / 1e12,
+                                    "unit": "TFLOP/s", "peak": tr_peak, "frac": tr_flop / tr_s / 1e12 / tr_peak,
+                                    "peak_kind": peak_kind_t + " (bf16_tflops_sustained)",
+                                    "timed": "whole epochs: state upload, list build, forces, gradient, Adam"}}
     c.close()
     # ---- 4M CG sites: MLP on tensor cores vs the same potential tabulated -----
     out["stage"] = "4M CG melt"

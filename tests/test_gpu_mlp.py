@@ -88,6 +88,82 @@ def test_mlp_dynamics_runs_and_thermalises():
     assert np.isfinite(o["pe_pair"]) and o["error_word"] == 0
 
 
+def _mlp_system(c, bits, prec=espp.ESPP_FP32, seed=5, replicas=None):
+    rmax, ub, fb = _bond_table()
+    if replicas is None:
+        s = espp.System(c.box, c.n, c.types, c.bonds, precision=prec, seed=seed)
+    else:
+        s = espp.System(replicas=replicas, precision=prec)
+    s.set_mlp(RC, bits)
+    s.set_table_bond(rmax, ub, fb)
+    s.set_exclude_bonded(True)
+    return s
+
+
+def test_mlp_batched_replicas_equal_standalone():
+    # pair records carry their replica; each pair is evaluated once and summed
+    # in list order, so a replica in a batch gets the standalone forces exactly
+    cs = [_cg_system(12, 50, seed=31), _cg_system(20, 40, seed=32), _cg_system(9, 60, seed=33)]
+    bits, _ = _weights(4)
+    reps = [dict(box=c.box, n=c.n, types=c.types, bonds=c.bonds, seed=50 + k) for k, c in enumerate(cs)]
+    b = _mlp_system(None, bits, replicas=reps)
+    b.set_state(np.concatenate([c.x for c in cs]), None, np.concatenate([c.img for c in cs]))
+    b.build_neighbors(RC, SKIN)
+    fb = b.compute_forces()
+    off = 0
+    for k, c in enumerate(cs):
+        s = _mlp_system(c, bits, seed=50 + k)
+        s.set_state(c.x, None, c.img)
+        s.build_neighbors(RC, SKIN)
+        assert np.array_equal(s.compute_forces(), fb[off:off + c.n])
+        off += c.n
+
+
+def test_mlp_survives_list_growth(monkeypatch):
+    # a list overflow reallocates the list and the learned potential's
+    # per-entry buffers, then rebuilds: the forces are those of a roomy list
+    c = _cg_system(15, 50, seed=41)
+    bits, _ = _weights(5)
+    ref = _mlp_system(c, bits)
+    ref.set_state(c.x, None, c.img)
+    ref.build_neighbors(RC, SKIN)
+    monkeypatch.setenv("ESPP_FAULT_LIST_CAP", "8")
+    s = _mlp_system(c, bits)
+    s.set_state(c.x, None, c.img)
+    s.build_neighbors(RC, SKIN)
+    assert s.list_capacity > 8
+    assert np.array_equal(s.compute_forces(), ref.compute_forces())
+
+
+def test_mlp_and_table_switch_on_one_handle():
+    # the learned potential, then its own table, then the learned potential again
+    c = _cg_system(12, 50, seed=51)
+    bits, _ = _weights(6)
+    s = _mlp_system(c, bits)
+    s.set_state(c.x, None, c.img)
+    s.build_neighbors(RC, SKIN)
+    f_mlp = s.compute_forces()
+    rt = np.linspace(0.0, RC, 4096)
+    box = np.array([20.0, 20.0, 20.0])
+    probe = espp.System(box, 2, None, None, precision=espp.ESPP_FP64)
+    probe.set_mlp(RC, bits)
+    ut, ft = np.zeros(rt.size), np.zeros(rt.size)
+    xs = np.zeros((2, 3))
+    for k, r in enumerate(rt):
+        xs[0] = (5.0, 5.0, 5.0)
+        xs[1] = (5.0 + max(r, 1e-3), 5.0, 5.0)
+        probe.set_state(xs)
+        if k == 0:
+            probe.build_neighbors(RC, SKIN)
+        ft[k] = probe.compute_forces()[1, 0]
+        ut[k] = probe.observables()["pe_pair"]
+    s.set_table_pair(RC, ut, ft)
+    f_tab = s.compute_forces()
+    assert rel_rms(f_tab, f_mlp) < 2e-2
+    s.set_mlp(RC, bits)
+    assert np.array_equal(s.compute_forces(), f_mlp)
+
+
 def test_mlp_requires_weights():
     c = _cg_system(10, 50)
     s = espp.System(c.box, c.n, c.types, c.bonds, precision=espp.ESPP_FP32)
