@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--cg-frames", type=int, default=32)
     ap.add_argument("--cg-epochs", type=int, default=10)
     ap.add_argument("--cg-batch", type=int, default=4)
-    ap.add_argument("--cg-warm", type=int, default=200)
+    ap.add_argument("--cg-warm", type=int, default=1000)
     ap.add_argument("--cg-steps", type=int, default=200)
     ap.add_argument("--cg-probe", type=int, default=0,
                     help="only: N-site CG system with the learned potential, a few force evaluations (for ncu)")
@@ -692,7 +692,7 @@ def suite_learned_cg(a, sync, out):
     tab_sys.close()
     res = {}
     forces = {}
-    n_snap, snap_every = 5, 40
+    n_snap, snap_every = 10, 40
     for mode in ("mlp", "table"):
         out["stage"] = "4M CG melt, " + mode
         s = espp.System(cg.box, cg.n, None, cg.bonds, precision=espp.ESPP_FP32, seed=45)
