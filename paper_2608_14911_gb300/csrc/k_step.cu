@@ -28,7 +28,7 @@
 #define ESPP_STEP_MINB32 10
 #endif
 #ifndef ESPP_STEP_PREFETCH
-#define ESPP_STEP_PREFETCH 1  // request the next batch's list groups early
+#define ESPP_STEP_PREFETCH 2  // request the next batch's list groups early (see pair_loop)
 #endif
 
 namespace espp {
@@ -137,7 +137,10 @@ __device__ __forceinline__ void pair_loop(const DevSys<T>& s, const V4<T>* __res
 #pragma unroll
         for (int q = 0; q < GB; ++q) {
             const int gn = g0 + GB + q;
-            if (ESPP_STEP_PREFETCH && gn < gcap) nxt[q] = __ldg(nb + gn * stride);
+            // ESPP_STEP_PREFETCH 1: request while the count may be in flight
+            // (reads one group past the list); 2: only groups inside the list
+            if ((ESPP_STEP_PREFETCH == 1 && gn < gcap) || (ESPP_STEP_PREFETCH == 2 && gn < ng))
+                nxt[q] = __ldg(nb + gn * stride);
         }
         int codes = 0;
 #pragma unroll
