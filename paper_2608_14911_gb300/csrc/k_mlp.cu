@@ -10,9 +10,10 @@
 // on the tcgen05 tensor cores with the accumulators in tensor memory.
 //
 // Each unordered pair is evaluated once.  Kernels:
-//   k_mlp_rev     (list builds) for every list entry (i, j) with j > i, the
-//                 index of the mirrored entry (j, i) in j's list, and the
-//                 array of all unordered pairs of the list
+//   k_mlp_rev     (list builds, after a count and a scan) for every list
+//                 entry (i, j) with j > i, the index of the mirrored entry
+//                 (j, i) in j's list, and the array of all unordered pairs of
+//                 the list in an order that depends only on the list
 //   k_mlp_stage   thread per unordered pair: the pairs inside the MLP cutoff
 //                 go to a dense pair array (r, entry, mirrored entry)
 //   k_mlp_tc      CTAs stream the dense array in 128-pair tiles on the
@@ -26,6 +27,7 @@
 #include <cstring>
 
 #include "mlp_common.cuh"
+#include "scan.cuh"
 #include "tc_ptx.cuh"
 
 namespace espp {
@@ -93,36 +95,83 @@ struct WarpAppender {
 };
 
 // ---- mirrored entries and the upper-pair array (list builds) -------------------
-// Thread per particle.  For every entry (i, j) with j > i: the index of the
-// mirrored entry (j, i), searched in j's list for the replicas just rebuilt
-// and kept for the others, and the record (entry, mirrored entry, list entry,
-// replica) in the array of all unordered pairs of the list.  A warp scan of
-// the per-thread counts gives each thread a contiguous run of records at one
-// atomic offset per warp.
+// Every unordered pair of the list gets one record (entry (i, j) with j > i,
+// mirrored entry (j, i), the list entry, replica), at an offset from a scan of
+// the per-particle counts, so the array's order depends only on the list.
+template <class T>
+__global__ void __launch_bounds__(TILE) k_mlp_count(DevSys<T> s) {
+    if (s.ctrl->abort) return;
+    const size_t stride = (size_t)s.stride;
+    for (int t = blockIdx.x; t < s.ntiles; t += gridDim.x) {
+        const Tile tl = s.tiles[t];
+        if ((int)threadIdx.x >= tl.count) continue;
+        const int i = tl.start + threadIdx.x;
+        const int n = s.nbr_cnt[i];
+        int cnt = 0;
+        for (int k = 0; k < n; ++k) cnt += nbr_slot(s.nbr[entry_index(i, k, stride)]) > i ? 1 : 0;
+        s.mlp_ucount[i] = cnt;
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_uscan_reduce(const int* __restrict__ in, int n,
+                                                             int* __restrict__ part) {
+    const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    int sum = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) sum += base + k < n ? in[base + k] : 0;
+    int excl;
+    const int total = block_excl_scan(sum, &excl);
+    if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_uscan_top(int* __restrict__ part, int nb, int* __restrict__ total) {
+    int carry = 0;
+    for (int b0 = 0; b0 < nb; b0 += SCAN_THREADS) {
+        const int b = b0 + threadIdx.x;
+        const int v = b < nb ? part[b] : 0;
+        int excl;
+        const int t = block_excl_scan(v, &excl);
+        if (b < nb) part[b] = carry + excl;
+        carry += t;
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_uscan_down(const int* __restrict__ in, int n,
+                                                           const int* __restrict__ part, int* __restrict__ out) {
+    const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    int v[SCAN_ITEMS];
+    int sum = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        v[k] = base + k < n ? in[base + k] : 0;
+        sum += v[k];
+    }
+    int excl;
+    block_excl_scan(sum, &excl);
+    int run = part[blockIdx.x] + excl;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+}
+
+// Thread per particle: mirrored entries, searched in j's list for the
+// replicas just rebuilt and kept for the others, and the particle's records.
 template <class T>
 __global__ void __launch_bounds__(TILE) k_mlp_rev(DevSys<T> s) {
     if (s.ctrl->abort) return;
-    const int lane = threadIdx.x & 31;
     const size_t stride = (size_t)s.stride;
     const int4* __restrict__ nbr4 = reinterpret_cast<const int4*>(s.nbr);
     for (int t = blockIdx.x; t < s.ntiles; t += gridDim.x) {
         const Tile tl = s.tiles[t];
-        const bool active = (int)threadIdx.x < tl.count;
+        if ((int)threadIdx.x >= tl.count) continue;
         const bool fresh = s.now[tl.rep] != 0;
         const int i = tl.start + threadIdx.x;
-        const int n = active ? s.nbr_cnt[i] : 0;
-        int cnt = 0;
-        for (int k = 0; k < n; ++k) cnt += nbr_slot(s.nbr[entry_index(i, k, stride)]) > i ? 1 : 0;
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int u = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += u;
-        }
-        int base = 0;
-        if (lane == 31 && incl > 0) base = atomicAdd(s.mlp_nupper, incl);
-        base = __shfl_sync(0xffffffffu, base, 31) + incl - cnt;
-        if (base + cnt > s.mlp_upper_cap) {
+        const int n = s.nbr_cnt[i];
+        int base = s.mlp_uoff[i];
+        if (base + s.mlp_ucount[i] > s.mlp_upper_cap) {
             atomicOr(&s.ctrl->err, ERRBIT_OVERFLOW);  // cannot happen: sized for every pair
             continue;
         }
@@ -521,9 +570,13 @@ int Launch<T>::mlp(const DevSys<T>& s, int cur, bool energy, cudaStream_t st) {
 
 template <class T>
 int Launch<T>::mlp_rev(const DevSys<T>& s, cudaStream_t st) {
-    cudaMemsetAsync(s.mlp_nupper, 0, sizeof(int), st);
+    const int nb = s.mlp_nuscan;
+    k_mlp_count<T><<<s.ntiles, TILE, 0, st>>>(s);
+    k_uscan_reduce<<<nb, SCAN_THREADS, 0, st>>>(s.mlp_ucount, s.N, s.mlp_uscan_part);
+    k_uscan_top<<<1, SCAN_THREADS, 0, st>>>(s.mlp_uscan_part, nb, s.mlp_nupper);
+    k_uscan_down<<<nb, SCAN_THREADS, 0, st>>>(s.mlp_ucount, s.N, s.mlp_uscan_part, s.mlp_uoff);
     k_mlp_rev<T><<<s.ntiles, TILE, 0, st>>>(s);
-    return 1;
+    return 5;
 }
 
 template int Launch<float>::mlp(const DevSys<float>&, int, bool, cudaStream_t);

@@ -26,12 +26,10 @@
 // step after `prep`; their counts and entries stay those of their last build,
 // so the global scan keeps every replica's entries in its own slot range.
 #include "kernels.cuh"
+#include "scan.cuh"
 
 namespace espp {
 
-constexpr int SCAN_THREADS = 256;
-constexpr int SCAN_ITEMS = 8;
-constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
 template <class T>
 __device__ __forceinline__ int cell_coord(T x, T cpl, int nc) {
@@ -133,36 +131,6 @@ __global__ void __launch_bounds__(256) k_cellsort(DevSys<T> s) {
 }
 
 // ---- exclusive scan of the cell counts (three phases, no inter-block waits) --
-__device__ __forceinline__ int warp_incl_scan(int v) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int u = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += u;
-    }
-    return v;
-}
-
-// block-wide exclusive scan of one int per thread; returns the block total
-__device__ __forceinline__ int block_excl_scan(int v, int* excl_out) {
-    __shared__ int wsum[SCAN_THREADS / 32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int inc = warp_incl_scan(v);
-    if (lane == 31) wsum[w] = inc;
-    __syncthreads();
-    if (w == 0) {
-        int t = lane < SCAN_THREADS / 32 ? wsum[lane] : 0;
-        t = warp_incl_scan(t);
-        if (lane < SCAN_THREADS / 32) wsum[lane] = t;
-    }
-    __syncthreads();
-    const int base = w > 0 ? wsum[w - 1] : 0;
-    *excl_out = base + inc - v;
-    const int total = wsum[SCAN_THREADS / 32 - 1];
-    __syncthreads();
-    return total;
-}
-
 // RANK = false: cells in index order -> cell_beg (every rebuild);
 // RANK = true: cells in Hilbert-rank order -> rank_start (resort only).
 template <class T, bool RANK>

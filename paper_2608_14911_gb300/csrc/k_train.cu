@@ -2,22 +2,29 @@
 //
 // Loss over a batch of F frames of n sites: L = sum |e_i|^2 / (F n) with
 // e_i = F_pair,i + F_bond,i - Y_i (Y: mapped forces).  Since
-// F_pair,i = sum_j -u'(r_ij) r_ij_hat, the gradient is a sum over ordered
-// pairs of w_ij d u'(r_ij) / d theta with w_ij = -2 (e_i . r_ij_hat) / (F n).
-// For each tile of 16 pairs a warp runs the forward pass of the inference
-// kernel (activations and their r-tangents), then the reverse pass of the
-// tangent output u' (rows scaled by w):
+// F_pair,i = sum_j -u'(r_ij) r_ij_hat, the gradient is a sum over unordered
+// pairs of w_ij d u'(r_ij) / d theta with
+//   w_ij = -2 ((e_i - e_j) . r_ij_hat) / (F n)
+// (the two ordered terms of a pair share u').  The pairs are the records of
+// the list (each unordered pair once, in an order fixed by the list); those
+// beyond the cutoff get w = 0 and contribute exact zeros.
+//
+// A block of 4 warps works in rounds of 4 tiles of 16 pairs.  Each warp runs,
+// for its tile, the forward pass of the inference kernel (activations and
+// their r-tangents) and the reverse pass of the tangent output u' (rows
+// scaled by w):
 //   az2 = w w3 silu''(z2) dz2,  adz2 = w w3 silu'(z2)      (16 x 64)
 //   [ah1; adh1] = [az2; adz2] W2                           (tensor cores)
 //   az1 = ah1 silu'(z1) + adh1 silu''(z1) dz1,  adz1 = adh1 silu'(z1)
-//   dW2 += az2^T h1 + adz2^T dh1,  dW1 += az1^T phi + adz1^T dphi   (tensor cores,
-//          K = the tile's pairs, operands transposed through shared memory)
-//   db2 += sum az2, dw3 += sum w silu'(z2) dz2, db1 += sum az1
-// Every warp accumulates into its own FP32 slab in shared memory; a block
-// adds its warps' slabs in a fixed order and writes one partial per block,
-// and a separate kernel adds the partials in a fixed order, so the gradient
-// is deterministic.  Adam then updates FP32 master weights and refreshes the
-// BF16 copy the kernels read.
+// and stages phi, dphi, h1, dh1 and the reverse rows in shared memory.  Then
+// warp q accumulates rows 16q..16q+15 of
+//   dW2 += az2^T h1 + adz2^T dh1,  dW1 += az1^T phi + adz1^T dphi
+// over the round's 4 tiles in registers (tensor cores, K = 64 pairs), so the
+// weight gradients never go through shared memory until the end.  The bias
+// and output-weight sums collect per warp.  Each block writes one partial in
+// a fixed order and a separate kernel adds the partials in a fixed order:
+// the gradient is deterministic.  Adam then updates FP32 master weights and
+// refreshes the BF16 copy the kernels read.
 #include "mlp_common.cuh"
 
 namespace espp {
@@ -37,8 +44,7 @@ struct __align__(16) TrainWarp {
     __nv_bfloat16 h1[16 * H_LD], dh1[16 * H_LD];
     __nv_bfloat16 az2[16 * H_LD], adz2[16 * H_LD];
     __nv_bfloat16 az1[16 * H_LD], adz1[16 * H_LD];
-    float4 pairs[32];
-    float acc[NGRAD];
+    float sums[3 * MLP_H];               // db1, db2, dw3 of this warp's tiles
 };
 
 struct __align__(16) TrainShared {
@@ -84,7 +90,7 @@ __device__ __forceinline__ float col_sum(float v) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(32 * TR_WARPS, 1) k_mlp_grad(DevSys<T> s, int cur, const float4* __restrict__ err,
+__global__ void __launch_bounds__(32 * TR_WARPS, 2) k_mlp_grad(DevSys<T> s, int cur, const float4* __restrict__ err,
                                                              float scale, float* __restrict__ partials) {
     extern __shared__ __align__(16) unsigned char tsm_raw[];
     TrainShared& sh = *reinterpret_cast<TrainShared*>(tsm_raw);
@@ -92,248 +98,239 @@ __global__ void __launch_bounds__(32 * TR_WARPS, 1) k_mlp_grad(DevSys<T> s, int 
     const int g = lane >> 2, tig = lane & 3;
     TrainWarp& ws = sh.warp[warp];
     load_mlp_weights(s.mlp, sh.w1s, sh.w2s, sh.w2t, sh.b1s, sh.b2s, sh.w3s);
-    for (int k = lane; k < NGRAD; k += 32) ws.acc[k] = 0.f;
+    for (int k = lane; k < 3 * MLP_H; k += 32) ws.sums[k] = 0.f;
     __syncthreads();
     const float rc = s.mlp->rc, rc2 = rc * rc;
     const V4<T>* __restrict__ P = s.pos[cur];
-    const size_t stride = (size_t)s.stride;
+    const int stride = s.stride;
+    const int nu = min(*s.mlp_nupper, s.mlp_upper_cap);
+    const int nrounds = (nu + 16 * TR_WARPS - 1) / (16 * TR_WARPS);
+    // this warp's rows of dW2 (16 x 64) and dW1 (16 x 32), as MMA accumulators
+    float acc2[8][4], acc1[4][4];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc2[a][e] = 0.f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc1[a][e] = 0.f;
 
-    for (int t = blockIdx.x; t < s.ntiles; t += gridDim.x) {
-        const Tile tl = s.tiles[t];
-        const RepGeom<T>& geo = s.reps[tl.rep];
-        const T L0 = geo.L[0], L1 = geo.L[1], L2 = geo.L[2];
-        for (int pi = warp; pi < tl.count; pi += TR_WARPS) {
-            const int i = tl.start + pi;
-            const V4<T> xi = ld4<T>(P + i);
-            const int n = s.nbr_cnt[i];
-            const float4 ei = err[i];
-            for (int c0 = 0; c0 < n; c0 += 32) {
-                const int c = c0 + lane;
-                float r = rc, dx = 0.f, dy = 0.f, dz = 0.f;
-                bool valid = false;
-                if (c < n) {
-                    const int e = s.nbr[4 * ((size_t)(c >> 2) * stride + i) + (c & 3)];
-                    const V4<T> xj = ld4<T>(P + nbr_slot(e));
-                    const int code = nbr_code(e);
-                    const T ddx = shifted_diff(xi.x, (T)(xi.x - L0), xj.x, L0, code & 3);
-                    const T ddy = shifted_diff(xi.y, (T)(xi.y - L1), xj.y, L1, (code >> 2) & 3);
-                    const T ddz = shifted_diff(xi.z, (T)(xi.z - L2), xj.z, L2, code >> 4);
-                    const float r2 = (float)(ddx * ddx + ddy * ddy + ddz * ddz);
-                    if (r2 < rc2) {
-                        valid = true;
-                        r = sqrtf(r2);
-                        dx = (float)ddx;
-                        dy = (float)ddy;
-                        dz = (float)ddz;
-                    }
-                }
-                const unsigned int vm = __ballot_sync(0xffffffffu, valid);
-                const int nv = __popc(vm);
-                if (valid) ws.pairs[__popc(vm & ((1u << lane) - 1u))] = make_float4(r, dx, dy, dz);
-                __syncwarp();
-                for (int k0 = 0; k0 < nv; k0 += 16) {
-                    const int p = lane & 15;
-                    const bool pvalid = k0 + p < nv;
-                    const float4 q4 = pvalid ? ws.pairs[k0 + p] : make_float4(rc, 0.f, 0.f, 0.f);
-                    // row weight: scale (e_i . r_hat); zero for empty rows
-                    const float wrow = pvalid ? scale * (ei.x * q4.y + ei.y * q4.z + ei.z * q4.w) / q4.x : 0.f;
-                    const float rr = pvalid ? q4.x : rc;
-                    const float ra = __shfl_sync(0xffffffffu, rr, g), rb = __shfl_sync(0xffffffffu, rr, g + 8);
-                    const float wa = __shfl_sync(0xffffffffu, wrow, g), wb = __shfl_sync(0xffffffffu, wrow, g + 8);
-                    // ---- features, staged for dW1 ---------------------------------
-                    unsigned int aph[2][4], adp[2][4];
-                    rbf_fragments(ra, rb, rc, tig, aph, adp);
-#pragma unroll
-                    for (int kt = 0; kt < 2; ++kt) {
-                        const int col = kt * 16 + 2 * tig;
-                        *reinterpret_cast<unsigned int*>(ws.phi + g * PHI_LD + col) = aph[kt][0];
-                        *reinterpret_cast<unsigned int*>(ws.phi + (g + 8) * PHI_LD + col) = aph[kt][1];
-                        *reinterpret_cast<unsigned int*>(ws.phi + g * PHI_LD + col + 8) = aph[kt][2];
-                        *reinterpret_cast<unsigned int*>(ws.phi + (g + 8) * PHI_LD + col + 8) = aph[kt][3];
-                        *reinterpret_cast<unsigned int*>(ws.dphi + g * PHI_LD + col) = adp[kt][0];
-                        *reinterpret_cast<unsigned int*>(ws.dphi + (g + 8) * PHI_LD + col) = adp[kt][1];
-                        *reinterpret_cast<unsigned int*>(ws.dphi + g * PHI_LD + col + 8) = adp[kt][2];
-                        *reinterpret_cast<unsigned int*>(ws.dphi + (g + 8) * PHI_LD + col + 8) = adp[kt][3];
-                    }
-                    // ---- layer 1 forward: h1, dh1 as layer-2 operands, staged ---
-                    unsigned int ah[4][4], adh[4][4];
-#pragma unroll
-                    for (int nt = 0; nt < 8; ++nt) {
-                        float z[4] = {0.f, 0.f, 0.f, 0.f}, dzv[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                        for (int kt = 0; kt < 2; ++kt) {
-                            unsigned int b0, b1;
-                            b_frag(sh.w1s, W1_LD, nt * 8, kt * 16, g, tig, b0, b1);
-                            mma_bf16_16816(z, aph[kt], b0, b1);
-                            mma_bf16_16816(dzv, adp[kt], b0, b1);
-                        }
-                        const int col = nt * 8 + 2 * tig;
-                        float hv[4], dhv[4];
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const float zz = z[e] + sh.b1s[col + (e & 1)];
-                            const float sg = sigm(zz);
-                            hv[e] = zz * sg;
-                            dhv[e] = sg * (1.f + zz * (1.f - sg)) * dzv[e];
-                        }
-                        const int kt2 = nt >> 1, off = (nt & 1) * 2;
-                        ah[kt2][off + 0] = pack_bf16x2(hv[0], hv[1]);
-                        ah[kt2][off + 1] = pack_bf16x2(hv[2], hv[3]);
-                        adh[kt2][off + 0] = pack_bf16x2(dhv[0], dhv[1]);
-                        adh[kt2][off + 1] = pack_bf16x2(dhv[2], dhv[3]);
-                        *reinterpret_cast<unsigned int*>(ws.h1 + g * H_LD + col) = ah[kt2][off + 0];
-                        *reinterpret_cast<unsigned int*>(ws.h1 + (g + 8) * H_LD + col) = ah[kt2][off + 1];
-                        *reinterpret_cast<unsigned int*>(ws.dh1 + g * H_LD + col) = adh[kt2][off + 0];
-                        *reinterpret_cast<unsigned int*>(ws.dh1 + (g + 8) * H_LD + col) = adh[kt2][off + 1];
-                    }
-                    // ---- layer 2 forward and the reverse seeds az2, adz2 ---------
-                    unsigned int aaz[4][4], aadz[4][4];
-#pragma unroll
-                    for (int nt = 0; nt < 8; ++nt) {
-                        float z[4] = {0.f, 0.f, 0.f, 0.f}, dzv[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                        for (int kt = 0; kt < 4; ++kt) {
-                            unsigned int b0, b1;
-                            b_frag(sh.w2s, W2_LD, nt * 8, kt * 16, g, tig, b0, b1);
-                            mma_bf16_16816(z, ah[kt], b0, b1);
-                            mma_bf16_16816(dzv, adh[kt], b0, b1);
-                        }
-                        const int col = nt * 8 + 2 * tig;
-                        float az[4], adz[4], gw3[2] = {0.f, 0.f}, gb2[2] = {0.f, 0.f};
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const float zz = z[e] + sh.b2s[col + (e & 1)];
-                            const float sg = sigm(zz);
-                            const float s1 = sg * (1.f + zz * (1.f - sg));
-                            const float s2 = sg * (1.f - sg) * (2.f + zz * (1.f - 2.f * sg));
-                            const float w = e < 2 ? wa : wb;
-                            const float w3v = sh.w3s[col + (e & 1)];
-                            az[e] = w * w3v * s2 * dzv[e];
-                            adz[e] = w * w3v * s1;
-                            gw3[e & 1] += w * s1 * dzv[e];
-                            gb2[e & 1] += az[e];
-                        }
-                        const int kt2 = nt >> 1, off = (nt & 1) * 2;
-                        aaz[kt2][off + 0] = pack_bf16x2(az[0], az[1]);
-                        aaz[kt2][off + 1] = pack_bf16x2(az[2], az[3]);
-                        aadz[kt2][off + 0] = pack_bf16x2(adz[0], adz[1]);
-                        aadz[kt2][off + 1] = pack_bf16x2(adz[2], adz[3]);
-                        *reinterpret_cast<unsigned int*>(ws.az2 + g * H_LD + col) = aaz[kt2][off + 0];
-                        *reinterpret_cast<unsigned int*>(ws.az2 + (g + 8) * H_LD + col) = aaz[kt2][off + 1];
-                        *reinterpret_cast<unsigned int*>(ws.adz2 + g * H_LD + col) = aadz[kt2][off + 0];
-                        *reinterpret_cast<unsigned int*>(ws.adz2 + (g + 8) * H_LD + col) = aadz[kt2][off + 1];
-#pragma unroll
-                        for (int q = 0; q < 2; ++q) {
-                            const float a3 = col_sum(gw3[q]), a2 = col_sum(gb2[q]);
-                            if (g == 0) {
-                                ws.acc[G_W3 + col + q] += a3;
-                                ws.acc[G_B2 + col + q] += a2;
-                            }
-                        }
-                    }
-                    // ---- back through W2 and layer 1: az1, adz1, staged ----------
-#pragma unroll
-                    for (int nt = 0; nt < 8; ++nt) {
-                        float a1[4] = {0.f, 0.f, 0.f, 0.f}, ad1[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                        for (int kt = 0; kt < 4; ++kt) {
-                            unsigned int b0, b1;
-                            b_frag(sh.w2t, W2_LD, nt * 8, kt * 16, g, tig, b0, b1);
-                            mma_bf16_16816(a1, aaz[kt], b0, b1);
-                            mma_bf16_16816(ad1, aadz[kt], b0, b1);
-                        }
-                        float z[4] = {0.f, 0.f, 0.f, 0.f}, dzv[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                        for (int kt = 0; kt < 2; ++kt) {
-                            unsigned int b0, b1;
-                            b_frag(sh.w1s, W1_LD, nt * 8, kt * 16, g, tig, b0, b1);
-                            mma_bf16_16816(z, aph[kt], b0, b1);
-                            mma_bf16_16816(dzv, adp[kt], b0, b1);
-                        }
-                        const int col = nt * 8 + 2 * tig;
-                        float az[4], adz[4], gb1[2] = {0.f, 0.f};
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const float zz = z[e] + sh.b1s[col + (e & 1)];
-                            const float sg = sigm(zz);
-                            const float s1 = sg * (1.f + zz * (1.f - sg));
-                            const float s2 = sg * (1.f - sg) * (2.f + zz * (1.f - 2.f * sg));
-                            az[e] = a1[e] * s1 + ad1[e] * s2 * dzv[e];
-                            adz[e] = ad1[e] * s1;
-                            gb1[e & 1] += az[e];
-                        }
-                        stage2(ws.az1, H_LD, g, col, az[0], az[1]);
-                        stage2(ws.az1, H_LD, g + 8, col, az[2], az[3]);
-                        stage2(ws.adz1, H_LD, g, col, adz[0], adz[1]);
-                        stage2(ws.adz1, H_LD, g + 8, col, adz[2], adz[3]);
-#pragma unroll
-                        for (int q = 0; q < 2; ++q) {
-                            const float a = col_sum(gb1[q]);
-                            if (g == 0) ws.acc[G_B1 + col + q] += a;
-                        }
-                    }
-                    __syncwarp();
-                    // ---- weight gradients: K = the tile's 16 pairs ---------------
-                    {
-                        unsigned int A[4][4], AD[4][4];
-#pragma unroll
-                        for (int mt = 0; mt < 4; ++mt) {
-                            at_frag(ws.az2, H_LD, mt * 16, g, tig, A[mt]);
-                            at_frag(ws.adz2, H_LD, mt * 16, g, tig, AD[mt]);
-                        }
-#pragma unroll
-                        for (int nt = 0; nt < 8; ++nt) {
-                            unsigned int b0, b1, d0, d1;
-                            bk_frag(ws.h1, H_LD, nt * 8, g, tig, b0, b1);
-                            bk_frag(ws.dh1, H_LD, nt * 8, g, tig, d0, d1);
-#pragma unroll
-                            for (int mt = 0; mt < 4; ++mt) {
-                                float cacc[4] = {0.f, 0.f, 0.f, 0.f};
-                                mma_bf16_16816(cacc, A[mt], b0, b1);
-                                mma_bf16_16816(cacc, AD[mt], d0, d1);
-                                float* dst = ws.acc + G_W2 + (mt * 16 + g) * MLP_H + nt * 8 + 2 * tig;
-                                dst[0] += cacc[0];
-                                dst[1] += cacc[1];
-                                dst[8 * MLP_H] += cacc[2];
-                                dst[8 * MLP_H + 1] += cacc[3];
-                            }
-                        }
-#pragma unroll
-                        for (int mt = 0; mt < 4; ++mt) {
-                            at_frag(ws.az1, H_LD, mt * 16, g, tig, A[mt]);
-                            at_frag(ws.adz1, H_LD, mt * 16, g, tig, AD[mt]);
-                        }
-#pragma unroll
-                        for (int nt = 0; nt < 4; ++nt) {
-                            unsigned int b0, b1, d0, d1;
-                            bk_frag(ws.phi, PHI_LD, nt * 8, g, tig, b0, b1);
-                            bk_frag(ws.dphi, PHI_LD, nt * 8, g, tig, d0, d1);
-#pragma unroll
-                            for (int mt = 0; mt < 4; ++mt) {
-                                float cacc[4] = {0.f, 0.f, 0.f, 0.f};
-                                mma_bf16_16816(cacc, A[mt], b0, b1);
-                                mma_bf16_16816(cacc, AD[mt], d0, d1);
-                                float* dst = ws.acc + G_W1 + (mt * 16 + g) * MLP_NB + nt * 8 + 2 * tig;
-                                dst[0] += cacc[0];
-                                dst[1] += cacc[1];
-                                dst[8 * MLP_NB] += cacc[2];
-                                dst[8 * MLP_NB + 1] += cacc[3];
-                            }
-                        }
-                    }
-                    __syncwarp();
-                }
-                __syncwarp();
+    for (int round = blockIdx.x; round < nrounds; round += gridDim.x) {
+        // ---- the pairs of this warp's tile: distance and row weight --------------
+        const int p = lane & 15;
+        const int k = (round * TR_WARPS + warp) * 16 + p;
+        float rr = rc, wrow = 0.f;
+        if (k < nu) {
+            const int4 up = s.mlp_upper[k];
+            const int i = (up.x >> 2) % stride, j = nbr_slot(up.z);
+            const RepGeom<T>& geo = s.reps[up.w];
+            const T L0 = geo.L[0], L1 = geo.L[1], L2 = geo.L[2];
+            const V4<T> xi = ld4<T>(P + i), xj = ld4<T>(P + j);
+            const int code = nbr_code(up.z);
+            const float dx = (float)shifted_diff(xi.x, (T)(xi.x - L0), xj.x, L0, code & 3);
+            const float dy = (float)shifted_diff(xi.y, (T)(xi.y - L1), xj.y, L1, (code >> 2) & 3);
+            const float dz = (float)shifted_diff(xi.z, (T)(xi.z - L2), xj.z, L2, code >> 4);
+            const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+            if (r2 < rc2) {
+                rr = sqrtf(r2);
+                const float4 ei = err[i], ej = err[j];
+                wrow = scale * ((ei.x - ej.x) * dx + (ei.y - ej.y) * dy + (ei.z - ej.z) * dz) / rr;
             }
         }
+        const float ra = __shfl_sync(0xffffffffu, rr, g), rb = __shfl_sync(0xffffffffu, rr, g + 8);
+        const float wa = __shfl_sync(0xffffffffu, wrow, g), wb = __shfl_sync(0xffffffffu, wrow, g + 8);
+        // ---- features, staged for dW1 ---------------------------------
+        unsigned int aph[2][4], adp[2][4];
+        rbf_fragments(ra, rb, rc, tig, aph, adp);
+#pragma unroll
+        for (int kt = 0; kt < 2; ++kt) {
+            const int col = kt * 16 + 2 * tig;
+            *reinterpret_cast<unsigned int*>(ws.phi + g * PHI_LD + col) = aph[kt][0];
+            *reinterpret_cast<unsigned int*>(ws.phi + (g + 8) * PHI_LD + col) = aph[kt][1];
+            *reinterpret_cast<unsigned int*>(ws.phi + g * PHI_LD + col + 8) = aph[kt][2];
+            *reinterpret_cast<unsigned int*>(ws.phi + (g + 8) * PHI_LD + col + 8) = aph[kt][3];
+            *reinterpret_cast<unsigned int*>(ws.dphi + g * PHI_LD + col) = adp[kt][0];
+            *reinterpret_cast<unsigned int*>(ws.dphi + (g + 8) * PHI_LD + col) = adp[kt][1];
+            *reinterpret_cast<unsigned int*>(ws.dphi + g * PHI_LD + col + 8) = adp[kt][2];
+            *reinterpret_cast<unsigned int*>(ws.dphi + (g + 8) * PHI_LD + col + 8) = adp[kt][3];
+        }
+        // ---- layer 1 forward: h1, dh1 as layer-2 operands, staged ---
+        unsigned int ah[4][4], adh[4][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            float z[4] = {0.f, 0.f, 0.f, 0.f}, dzv[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int kt = 0; kt < 2; ++kt) {
+                unsigned int b0, b1;
+                b_frag(sh.w1s, W1_LD, nt * 8, kt * 16, g, tig, b0, b1);
+                mma_bf16_16816(z, aph[kt], b0, b1);
+                mma_bf16_16816(dzv, adp[kt], b0, b1);
+            }
+            const int col = nt * 8 + 2 * tig;
+            float hv[4], dhv[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float zz = z[e] + sh.b1s[col + (e & 1)];
+                const float sg = sigm(zz);
+                hv[e] = zz * sg;
+                dhv[e] = sg * (1.f + zz * (1.f - sg)) * dzv[e];
+            }
+            const int kt2 = nt >> 1, off = (nt & 1) * 2;
+            ah[kt2][off + 0] = pack_bf16x2(hv[0], hv[1]);
+            ah[kt2][off + 1] = pack_bf16x2(hv[2], hv[3]);
+            adh[kt2][off + 0] = pack_bf16x2(dhv[0], dhv[1]);
+            adh[kt2][off + 1] = pack_bf16x2(dhv[2], dhv[3]);
+            *reinterpret_cast<unsigned int*>(ws.h1 + g * H_LD + col) = ah[kt2][off + 0];
+            *reinterpret_cast<unsigned int*>(ws.h1 + (g + 8) * H_LD + col) = ah[kt2][off + 1];
+            *reinterpret_cast<unsigned int*>(ws.dh1 + g * H_LD + col) = adh[kt2][off + 0];
+            *reinterpret_cast<unsigned int*>(ws.dh1 + (g + 8) * H_LD + col) = adh[kt2][off + 1];
+        }
+        // ---- layer 2 forward and the reverse seeds az2, adz2 ---------
+        unsigned int aaz[4][4], aadz[4][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            float z[4] = {0.f, 0.f, 0.f, 0.f}, dzv[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int kt = 0; kt < 4; ++kt) {
+                unsigned int b0, b1;
+                b_frag(sh.w2s, W2_LD, nt * 8, kt * 16, g, tig, b0, b1);
+                mma_bf16_16816(z, ah[kt], b0, b1);
+                mma_bf16_16816(dzv, adh[kt], b0, b1);
+            }
+            const int col = nt * 8 + 2 * tig;
+            float az[4], adz[4], gw3[2] = {0.f, 0.f}, gb2[2] = {0.f, 0.f};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float zz = z[e] + sh.b2s[col + (e & 1)];
+                const float sg = sigm(zz);
+                const float s1 = sg * (1.f + zz * (1.f - sg));
+                const float s2 = sg * (1.f - sg) * (2.f + zz * (1.f - 2.f * sg));
+                const float w = e < 2 ? wa : wb;
+                const float w3v = sh.w3s[col + (e & 1)];
+                az[e] = w * w3v * s2 * dzv[e];
+                adz[e] = w * w3v * s1;
+                gw3[e & 1] += w * s1 * dzv[e];
+                gb2[e & 1] += az[e];
+            }
+            const int kt2 = nt >> 1, off = (nt & 1) * 2;
+            aaz[kt2][off + 0] = pack_bf16x2(az[0], az[1]);
+            aaz[kt2][off + 1] = pack_bf16x2(az[2], az[3]);
+            aadz[kt2][off + 0] = pack_bf16x2(adz[0], adz[1]);
+            aadz[kt2][off + 1] = pack_bf16x2(adz[2], adz[3]);
+            *reinterpret_cast<unsigned int*>(ws.az2 + g * H_LD + col) = aaz[kt2][off + 0];
+            *reinterpret_cast<unsigned int*>(ws.az2 + (g + 8) * H_LD + col) = aaz[kt2][off + 1];
+            *reinterpret_cast<unsigned int*>(ws.adz2 + g * H_LD + col) = aadz[kt2][off + 0];
+            *reinterpret_cast<unsigned int*>(ws.adz2 + (g + 8) * H_LD + col) = aadz[kt2][off + 1];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const float a3 = col_sum(gw3[q]), a2 = col_sum(gb2[q]);
+                if (g == 0) {
+                    ws.sums[2 * MLP_H + col + q] += a3;
+                    ws.sums[MLP_H + col + q] += a2;
+                }
+            }
+        }
+        // ---- back through W2 and layer 1: az1, adz1, staged ----------
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            float a1[4] = {0.f, 0.f, 0.f, 0.f}, ad1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int kt = 0; kt < 4; ++kt) {
+                unsigned int b0, b1;
+                b_frag(sh.w2t, W2_LD, nt * 8, kt * 16, g, tig, b0, b1);
+                mma_bf16_16816(a1, aaz[kt], b0, b1);
+                mma_bf16_16816(ad1, aadz[kt], b0, b1);
+            }
+            float z[4] = {0.f, 0.f, 0.f, 0.f}, dzv[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int kt = 0; kt < 2; ++kt) {
+                unsigned int b0, b1;
+                b_frag(sh.w1s, W1_LD, nt * 8, kt * 16, g, tig, b0, b1);
+                mma_bf16_16816(z, aph[kt], b0, b1);
+                mma_bf16_16816(dzv, adp[kt], b0, b1);
+            }
+            const int col = nt * 8 + 2 * tig;
+            float az[4], adz[4], gb1[2] = {0.f, 0.f};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float zz = z[e] + sh.b1s[col + (e & 1)];
+                const float sg = sigm(zz);
+                const float s1 = sg * (1.f + zz * (1.f - sg));
+                const float s2 = sg * (1.f - sg) * (2.f + zz * (1.f - 2.f * sg));
+                az[e] = a1[e] * s1 + ad1[e] * s2 * dzv[e];
+                adz[e] = ad1[e] * s1;
+                gb1[e & 1] += az[e];
+            }
+            stage2(ws.az1, H_LD, g, col, az[0], az[1]);
+            stage2(ws.az1, H_LD, g + 8, col, az[2], az[3]);
+            stage2(ws.adz1, H_LD, g, col, adz[0], adz[1]);
+            stage2(ws.adz1, H_LD, g + 8, col, adz[2], adz[3]);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const float a = col_sum(gb1[q]);
+                if (g == 0) ws.sums[col + q] += a;
+            }
+        }
+        __syncthreads();
+        // ---- weight gradients: this warp's rows, K = the round's 4 x 16 pairs ----
+        for (int src = 0; src < TR_WARPS; ++src) {
+            const TrainWarp& ts = sh.warp[src];
+            unsigned int A[4], AD[4];
+            at_frag(ts.az2, H_LD, warp * 16, g, tig, A);
+            at_frag(ts.adz2, H_LD, warp * 16, g, tig, AD);
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                unsigned int b0, b1, d0, d1;
+                bk_frag(ts.h1, H_LD, nt * 8, g, tig, b0, b1);
+                bk_frag(ts.dh1, H_LD, nt * 8, g, tig, d0, d1);
+                mma_bf16_16816(acc2[nt], A, b0, b1);
+                mma_bf16_16816(acc2[nt], AD, d0, d1);
+            }
+            at_frag(ts.az1, H_LD, warp * 16, g, tig, A);
+            at_frag(ts.adz1, H_LD, warp * 16, g, tig, AD);
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                unsigned int b0, b1, d0, d1;
+                bk_frag(ts.phi, PHI_LD, nt * 8, g, tig, b0, b1);
+                bk_frag(ts.dphi, PHI_LD, nt * 8, g, tig, d0, d1);
+                mma_bf16_16816(acc1[nt], A, b0, b1);
+                mma_bf16_16816(acc1[nt], AD, d0, d1);
+            }
+        }
+        __syncthreads();
+    }
+    // ---- this block's partial: register rows, then the warps' sums in order -----
+    float* out = partials + (size_t)blockIdx.x * NGRAD;
+    const int row = warp * 16 + g;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        float* dst = out + G_W2 + row * MLP_H + nt * 8 + 2 * tig;
+        dst[0] = acc2[nt][0];
+        dst[1] = acc2[nt][1];
+        dst[8 * MLP_H] = acc2[nt][2];
+        dst[8 * MLP_H + 1] = acc2[nt][3];
+    }
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+        float* dst = out + G_W1 + row * MLP_NB + nt * 8 + 2 * tig;
+        dst[0] = acc1[nt][0];
+        dst[1] = acc1[nt][1];
+        dst[8 * MLP_NB] = acc1[nt][2];
+        dst[8 * MLP_NB + 1] = acc1[nt][3];
     }
     __syncthreads();
-    float* out = partials + (size_t)blockIdx.x * NGRAD;
-    for (int k = threadIdx.x; k < NGRAD; k += blockDim.x) {
-        float a = 0.f;
+    for (int k = threadIdx.x; k < MLP_H; k += blockDim.x) {
+        float b1v = 0.f, b2v = 0.f, w3v = 0.f;
 #pragma unroll
-        for (int w = 0; w < TR_WARPS; ++w) a += sh.warp[w].acc[k];
-        out[k] = a;
+        for (int w = 0; w < TR_WARPS; ++w) {
+            b1v += sh.warp[w].sums[k];
+            b2v += sh.warp[w].sums[MLP_H + k];
+            w3v += sh.warp[w].sums[2 * MLP_H + k];
+        }
+        out[G_B1 + k] = b1v;
+        out[G_B2 + k] = b2v;
+        out[G_W3 + k] = w3v;
     }
 }
 

@@ -104,7 +104,11 @@ template <class T> struct DevSys {
     int* mlp_npairs;    // device counter of mlp_pairs
     int4* mlp_upper;    // every unordered list pair: (entry, mirrored entry, list entry, replica)
     int mlp_upper_cap;
-    int* mlp_nupper;    // device counter of mlp_upper
+    int* mlp_nupper;    // number of records in mlp_upper
+    int* mlp_ucount;    // per particle: its list entries (i, j) with j > i
+    int* mlp_uoff;      // per particle: first record in mlp_upper (scan of mlp_ucount)
+    int* mlp_uscan_part;
+    int mlp_nuscan;     // scan blocks over the particles
     int N;
     BondRec<T> bond;
     T rlist2;           // (rc + skin)^2

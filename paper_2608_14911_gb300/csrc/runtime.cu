@@ -731,7 +731,7 @@ class System : public SystemBase {
         const int ngrad = mlp_ngrad();
         const int nep = std::max(epochs, 1);
         if (!t_err) {
-            t_blocks = std::max(1, std::min(d.ntiles, 152));
+            t_blocks = 2 * 152;  // two blocks of the gradient kernel per SM
             int rc0;
             if ((rc0 = alloc(&t_err, (size_t)N, allocs)) || (rc0 = alloc(&t_loss_part, (size_t)d.ntiles, allocs)) ||
                 (rc0 = alloc(&t_partials, (size_t)t_blocks * ngrad, allocs)) || (rc0 = alloc(&t_grad, ngrad, allocs)) ||
@@ -898,12 +898,15 @@ class System : public SystemBase {
         d.mlp_upper = nullptr;
         d.mlp_nupper = nullptr;
         d.mlp_upper_cap = 0;
+        d.mlp_ucount = d.mlp_uoff = d.mlp_uscan_part = nullptr;
         const size_t slots = (size_t)d.cap * d.stride;
         // the pair arrays hold every unordered pair of the list; entry
         // indices are 32-bit
         const size_t npairs = slots / 2 + 64;
         if (4 * slots > (size_t)INT32_MAX) return fail(ESPP_ERR_ARG, "list too large for the learned potential");
-        const size_t bytes = 3 * slots * sizeof(float) + 2 * npairs * sizeof(int4) + 64;
+        const int nus = scan_blocks_for((int)N);
+        const size_t bytes = 3 * slots * sizeof(float) + 2 * npairs * sizeof(int4) + 64 +
+                             (2 * (size_t)N + nus + 16) * sizeof(int);
         void* p = nullptr;
         cudaError_t e = cudaMalloc(&p, bytes);
         if (e != cudaSuccess) return fail(ESPP_ERR_CUDA, std::string("MLP buffers: ") + cudaGetErrorString(e));
@@ -920,6 +923,10 @@ class System : public SystemBase {
         d.mlp_rev = reinterpret_cast<int*>(d.mlp_pu + slots);
         d.mlp_npairs = d.mlp_rev + slots;
         d.mlp_nupper = d.mlp_npairs + 1;
+        d.mlp_ucount = d.mlp_npairs + 16;
+        d.mlp_uoff = d.mlp_ucount + N;
+        d.mlp_uscan_part = d.mlp_uoff + N;
+        d.mlp_nuscan = nus;
         clear_graphs();
         return ESPP_OK;
     }
@@ -1287,7 +1294,7 @@ class System : public SystemBase {
             Ctrl c = read_ctrl();
             CK(cudaGetLastError());
             if (host_rebuilds >= 0)
-                launches += (REBUILD_LAUNCHES + (d.mlp_on ? 1 : 0)) *
+                launches += (REBUILD_LAUNCHES + (d.mlp_on ? 5 : 0)) *
                             ((int64_t)(c.n_rebuilds - (unsigned)rb0) - host_rebuilds);
             if (c.err & (ERRBIT_BOND | ERRBIT_NONFINITE | ERRBIT_TIMEOUT)) return status_from(c);
             if (c.err & ERRBIT_OVERFLOW) {
