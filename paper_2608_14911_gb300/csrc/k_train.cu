@@ -57,24 +57,29 @@ struct __align__(16) TrainShared {
 
 size_t train_smem_bytes() { return sizeof(TrainShared); }
 
-__device__ __forceinline__ unsigned int pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-    return (unsigned int)__bfloat16_as_ushort(lo) | ((unsigned int)__bfloat16_as_ushort(hi) << 16);
+// four 8x8 BF16 matrices from shared memory, transposed (rows of each source
+// matrix given by lanes 8m..8m+7)
+__device__ __forceinline__ void ldsm_x4_t(const __nv_bfloat16* p, unsigned int r[4]) {
+    const unsigned int a = (unsigned int)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
 }
 
 // A fragment of M^T for a [16 rows = pairs][ld] staging matrix M: rows of the
-// fragment are columns u0.. of M, columns are the 16 pairs.
-__device__ __forceinline__ void at_frag(const __nv_bfloat16* M, int ld, int u0, int g, int t, unsigned int a[4]) {
-    a[0] = pack2(M[(2 * t) * ld + u0 + g], M[(2 * t + 1) * ld + u0 + g]);
-    a[1] = pack2(M[(2 * t) * ld + u0 + g + 8], M[(2 * t + 1) * ld + u0 + g + 8]);
-    a[2] = pack2(M[(2 * t + 8) * ld + u0 + g], M[(2 * t + 9) * ld + u0 + g]);
-    a[3] = pack2(M[(2 * t + 8) * ld + u0 + g + 8], M[(2 * t + 9) * ld + u0 + g + 8]);
+// fragment are columns u0.. of M, columns are the 16 pairs.  Source matrix m
+// of the load covers pairs 8 (m >> 1).. and columns u0 + 8 (m & 1)..
+__device__ __forceinline__ void at_frag(const __nv_bfloat16* M, int ld, int u0, int lane, unsigned int a[4]) {
+    const int m = lane >> 3, r = lane & 7;
+    ldsm_x4_t(M + ((m >> 1) * 8 + r) * ld + u0 + (m & 1) * 8, a);
 }
 
-// B fragment of a [16 pairs (k)][ld] staging matrix M for columns n0..n0+7.
-__device__ __forceinline__ void bk_frag(const __nv_bfloat16* M, int ld, int n0, int g, int t, unsigned int& b0,
-                                        unsigned int& b1) {
-    b0 = pack2(M[(2 * t) * ld + n0 + g], M[(2 * t + 1) * ld + n0 + g]);
-    b1 = pack2(M[(2 * t + 8) * ld + n0 + g], M[(2 * t + 9) * ld + n0 + g]);
+// B fragments of a [16 pairs (k)][ld] staging matrix M for columns n0..n0+7
+// (b[0], b[1]) and n0+8..n0+15 (b[2], b[3]).  Source matrix m covers pairs
+// 8 (m & 1).. and columns n0 + 8 (m >> 1)..
+__device__ __forceinline__ void bk_frag2(const __nv_bfloat16* M, int ld, int n0, int lane, unsigned int b[4]) {
+    const int m = lane >> 3, r = lane & 7;
+    ldsm_x4_t(M + ((m & 1) * 8 + r) * ld + n0 + (m >> 1) * 8, b);
 }
 
 __device__ __forceinline__ void stage2(__nv_bfloat16* M, int ld, int row, int col, float lo, float hi) {
@@ -277,25 +282,29 @@ __global__ void __launch_bounds__(32 * TR_WARPS, 2) k_mlp_grad(DevSys<T> s, int 
         for (int src = 0; src < TR_WARPS; ++src) {
             const TrainWarp& ts = sh.warp[src];
             unsigned int A[4], AD[4];
-            at_frag(ts.az2, H_LD, warp * 16, g, tig, A);
-            at_frag(ts.adz2, H_LD, warp * 16, g, tig, AD);
+            at_frag(ts.az2, H_LD, warp * 16, lane, A);
+            at_frag(ts.adz2, H_LD, warp * 16, lane, AD);
 #pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                unsigned int b0, b1, d0, d1;
-                bk_frag(ts.h1, H_LD, nt * 8, g, tig, b0, b1);
-                bk_frag(ts.dh1, H_LD, nt * 8, g, tig, d0, d1);
-                mma_bf16_16816(acc2[nt], A, b0, b1);
-                mma_bf16_16816(acc2[nt], AD, d0, d1);
+            for (int nt = 0; nt < 8; nt += 2) {
+                unsigned int b[4], d[4];
+                bk_frag2(ts.h1, H_LD, nt * 8, lane, b);
+                bk_frag2(ts.dh1, H_LD, nt * 8, lane, d);
+                mma_bf16_16816(acc2[nt], A, b[0], b[1]);
+                mma_bf16_16816(acc2[nt], AD, d[0], d[1]);
+                mma_bf16_16816(acc2[nt + 1], A, b[2], b[3]);
+                mma_bf16_16816(acc2[nt + 1], AD, d[2], d[3]);
             }
-            at_frag(ts.az1, H_LD, warp * 16, g, tig, A);
-            at_frag(ts.adz1, H_LD, warp * 16, g, tig, AD);
+            at_frag(ts.az1, H_LD, warp * 16, lane, A);
+            at_frag(ts.adz1, H_LD, warp * 16, lane, AD);
 #pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-                unsigned int b0, b1, d0, d1;
-                bk_frag(ts.phi, PHI_LD, nt * 8, g, tig, b0, b1);
-                bk_frag(ts.dphi, PHI_LD, nt * 8, g, tig, d0, d1);
-                mma_bf16_16816(acc1[nt], A, b0, b1);
-                mma_bf16_16816(acc1[nt], AD, d0, d1);
+            for (int nt = 0; nt < 4; nt += 2) {
+                unsigned int b[4], d[4];
+                bk_frag2(ts.phi, PHI_LD, nt * 8, lane, b);
+                bk_frag2(ts.dphi, PHI_LD, nt * 8, lane, d);
+                mma_bf16_16816(acc1[nt], A, b[0], b[1]);
+                mma_bf16_16816(acc1[nt], AD, d[0], d[1]);
+                mma_bf16_16816(acc1[nt + 1], A, b[2], b[3]);
+                mma_bf16_16816(acc1[nt + 1], AD, d[2], d[3]);
             }
         }
         __syncthreads();

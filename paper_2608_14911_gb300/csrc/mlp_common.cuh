@@ -31,7 +31,12 @@ __device__ __forceinline__ void mma_bf16_16816(float c[4], const unsigned int a[
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ float sigm(float z) { return 1.0f / (1.0f + __expf(-z)); }
+// logistic sigmoid from the hardware tanh: s(z) = (1 + tanh(z / 2)) / 2
+__device__ __forceinline__ float sigm(float z) {
+    float t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(0.5f * z));
+    return fmaf(0.5f, t, 0.5f);
+}
 
 // B fragment (two 32-bit registers) of a [n][k] row-major BF16 matrix in
 // shared memory with row stride ld: element (k, n) = M[n][k].
