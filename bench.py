@@ -692,7 +692,7 @@ def suite_learned_cg(a, sync, out):
     tab_sys.close()
     res = {}
     forces = {}
-    n_snap, snap_every = 10, 40
+    n_snap, snap_every = 40, 20
     for mode in ("mlp", "table"):
         out["stage"] = "4M CG melt, " + mode
         s = espp.System(cg.box, cg.n, None, cg.bonds, precision=espp.ESPP_FP32, seed=45)
