@@ -45,6 +45,44 @@ __device__ __forceinline__ float tanh_hw(float y) {
     return t;
 }
 
+// Pairs of FP32 values in one 64-bit register and the packed FP32x2
+// arithmetic of the sm_100 family (two lanes per instruction, the same
+// round-to-nearest results as the scalar operations).
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 f2(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2split(f32x2 v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f32x2 f2fma(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 f2mul(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 f2add(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// For two units at once, with t = tanh(y):
+//   silu'(z) dz = (1 + t)(1 + y (1 - t)) dy, written c dy with
+//   c = a + t a, a = 1 + y (1 - t), 1 - t = t (-1) + 1
+__device__ __forceinline__ f32x2 silu_tangent_factor(f32x2 y, f32x2 t) {
+    const f32x2 one = f2(1.f, 1.f), mone = f2(-1.f, -1.f);
+    const f32x2 omt = f2fma(t, mone, one);
+    const f32x2 a = f2fma(y, omt, one);
+    return f2fma(t, a, a);
+}
+
 __device__ __forceinline__ size_t entry_index(int i, int k, size_t stride) {
     return 4 * ((size_t)(k >> 2) * stride + i) + (k & 3);
 }
@@ -279,8 +317,8 @@ struct __align__(128) TcShared {
     __nv_bfloat16 a[2 * TC_M * TC_K2];   // A0 | A1, layer 1 (K1) overlaid by layer 2 (K2)
     __nv_bfloat16 w1[TC_N * TC_K1];      // B operand of layer 1
     __nv_bfloat16 w2[TC_N * TC_K2];      // B operand of layer 2
-    float w3[TC_N];
-    float b2h[TC_N];                      // halved second-layer bias
+    __align__(16) float w3[TC_N];
+    __align__(16) float b2h[TC_N];        // halved second-layer bias
     uint64_t mbar;
     uint32_t tmem;
     int stop;
@@ -401,16 +439,15 @@ __global__ void __launch_bounds__(TC_M, TC_CTAS_PER_SM) k_mlp_tc(DevSys<float> s
                 unsigned int hw[8], dw[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    float h2[2], d2[2];
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const float yy = y[2 * j + q], t = tanh_hw(yy);
-                        h2[q] = fmaf(yy, t, yy);
-                        const float a = fmaf(-yy, t, yy + 1.f);
-                        d2[q] = fmaf(t, a, a) * dy[2 * j + q];
-                    }
-                    hw[j] = pack_bf16x2(h2[0], h2[1]);
-                    dw[j] = pack_bf16x2(d2[0], d2[1]);
+                    const f32x2 yv = f2(y[2 * j], y[2 * j + 1]);
+                    const f32x2 tv = f2(tanh_hw(y[2 * j]), tanh_hw(y[2 * j + 1]));
+                    const f32x2 hv = f2fma(yv, tv, yv);  // y (1 + t)
+                    const f32x2 dv = f2mul(silu_tangent_factor(yv, tv), f2(dy[2 * j], dy[2 * j + 1]));
+                    float h0, h1, d0, d1;
+                    f2split(hv, h0, h1);
+                    f2split(dv, d0, d1);
+                    hw[j] = pack_bf16x2(h0, h1);
+                    dw[j] = pack_bf16x2(d0, d1);
                 }
                 st_row16(A0, tid, c, TC_K2, make_uint4(hw[0], hw[1], hw[2], hw[3]));
                 st_row16(A0, tid, c + 8, TC_K2, make_uint4(hw[4], hw[5], hw[6], hw[7]));
@@ -440,18 +477,31 @@ __global__ void __launch_bounds__(TC_M, TC_CTAS_PER_SM) k_mlp_tc(DevSys<float> s
         parity ^= 1u;
         tc::fence_after_sync();
         // ---- output layer ----------------------------------------------------------
-        float u = 0.f, du = 0.f;
+        f32x2 u2 = f2(0.f, 0.f), du2 = f2(0.f, 0.f);
 #pragma unroll
         for (int c = 0; c < TC_N; c += 16) {
             float y[16], dy[16];
             tc::tmem_ld16x2(lanes + c, lanes + 64 + c, y, dy);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const float yy = y[j] + sh.b2h[c + j], t = tanh_hw(yy), w3v = sh.w3[c + j];
-                const float a = fmaf(-yy, t, yy + 1.f);
-                du = fmaf(w3v, fmaf(t, a, a) * dy[j], du);
-                if (ENERGY) u = fmaf(w3v, fmaf(yy, t, yy), u);
+            for (int j = 0; j < 8; ++j) {
+                const float2 bb = *reinterpret_cast<const float2*>(sh.b2h + c + 2 * j);
+                const float2 ww = *reinterpret_cast<const float2*>(sh.w3 + c + 2 * j);
+                const f32x2 yv = f2add(f2(y[2 * j], y[2 * j + 1]), f2(bb.x, bb.y));
+                float y0, y1;
+                f2split(yv, y0, y1);
+                const f32x2 tv = f2(tanh_hw(y0), tanh_hw(y1));
+                const f32x2 wv = f2(ww.x, ww.y);
+                du2 = f2fma(wv, f2mul(silu_tangent_factor(yv, tv), f2(dy[2 * j], dy[2 * j + 1])), du2);
+                if (ENERGY) u2 = f2fma(wv, f2fma(yv, tv, yv), u2);
             }
+        }
+        float u, du;
+        {
+            float a, b;
+            f2split(du2, a, b);
+            du = a + b;
+            f2split(u2, a, b);
+            u = a + b;
         }
         if (valid) {
             const float sv = -du / r;
