@@ -400,19 +400,37 @@ __global__ void __launch_bounds__(TILE) k_train_err(DevSys<T> s, int cur, const 
     }
 }
 
-// grad[k] += sum over blocks of partials (fixed order); loss += sum of parts.
-__global__ void k_grad_reduce(const float* __restrict__ partials, int nblocks, float* __restrict__ grad,
+// grad[k] += sum over blocks of partials in a fixed order, in two passes: 16
+// chunks of consecutive blocks (each chunk summed in order) into chunk sums,
+// then the chunk sums in order; loss += sum of parts.
+constexpr int GRED_CHUNKS = 16;
+
+__global__ void k_grad_chunks(const float* __restrict__ partials, int nblocks, float* __restrict__ chunk) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    const int per = (nblocks + GRED_CHUNKS - 1) / GRED_CHUNKS;
+    if (k >= NGRAD) return;
+    float a = 0.f;
+    for (int b = c * per; b < min(nblocks, (c + 1) * per); ++b) a += partials[(size_t)b * NGRAD + k];
+    chunk[(size_t)c * NGRAD + k] = a;
+}
+
+__global__ void k_grad_reduce(const float* __restrict__ chunk, float* __restrict__ grad,
                               const double* __restrict__ loss_part, int nloss, double* __restrict__ loss) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < NGRAD) {
         float a = 0.f;
-        for (int b = 0; b < nblocks; ++b) a += partials[(size_t)b * NGRAD + k];
+#pragma unroll
+        for (int c = 0; c < GRED_CHUNKS; ++c) a += chunk[(size_t)c * NGRAD + k];
         grad[k] += a;
     }
-    if (k == 0) {
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+        // lane q sums parts q, q + 32, ...; the lanes then add in a fixed tree
         double l = 0.0;
-        for (int b = 0; b < nloss; ++b) l += loss_part[b];
-        *loss += l;
+        for (int b = threadIdx.x; b < nloss; b += 32) l += loss_part[b];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
+        if (threadIdx.x == 0) *loss += l;
     }
 }
 
@@ -447,8 +465,11 @@ int Launch<T>::train_grad(const DevSys<T>& s, int cur, const double* Y, float4* 
                           cudaStream_t st) {
     k_train_err<T><<<s.ntiles, TILE, 0, st>>>(s, cur, Y, err, loss_part);
     k_mlp_grad<T><<<grad_blocks, 32 * TR_WARPS, sizeof(TrainShared), st>>>(s, cur, err, scale, partials);
-    k_grad_reduce<<<(NGRAD + 255) / 256, 256, 0, st>>>(partials, grad_blocks, grad, loss_part, s.ntiles, loss);
-    return 3;
+    // the chunk sums sit after the blocks' partials
+    float* chunk = partials + (size_t)grad_blocks * NGRAD;
+    k_grad_chunks<<<dim3((NGRAD + 255) / 256, GRED_CHUNKS), 256, 0, st>>>(partials, grad_blocks, chunk);
+    k_grad_reduce<<<(NGRAD + 255) / 256, 256, 0, st>>>(chunk, grad, loss_part, s.ntiles, loss);
+    return 4;
 }
 
 template <class T>

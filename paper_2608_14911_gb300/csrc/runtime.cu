@@ -734,7 +734,7 @@ class System : public SystemBase {
             t_blocks = 2 * 152;  // two blocks of the gradient kernel per SM
             int rc0;
             if ((rc0 = alloc(&t_err, (size_t)N, allocs)) || (rc0 = alloc(&t_loss_part, (size_t)d.ntiles, allocs)) ||
-                (rc0 = alloc(&t_partials, (size_t)t_blocks * ngrad, allocs)) || (rc0 = alloc(&t_grad, ngrad, allocs)) ||
+                (rc0 = alloc(&t_partials, (size_t)(t_blocks + 16) * ngrad, allocs)) || (rc0 = alloc(&t_grad, ngrad, allocs)) ||
                 (rc0 = alloc(&t_theta, ngrad, allocs)) || (rc0 = alloc(&t_m, ngrad, allocs)) ||
                 (rc0 = alloc(&t_v, ngrad, allocs)))
                 return rc0;
@@ -774,7 +774,8 @@ class System : public SystemBase {
                     const int f = order[b0 + q];
                     int rcode = set_state(X + f * n3, nullptr, nullptr, ESPP_DEVICE);
                     if (rcode) return rcode;
-                    rcode = rebuild_now(false);
+                    // a training frame needs its list, not a new storage order
+                    rcode = rebuild_now(false, false);
                     if (rcode) return rcode;
                     launches += Launch<T>::mlp(d, cur, false, st);
                     launches += Launch<T>::train_grad(d, cur, Y + f * n3, t_err, t_loss_part, scale, t_partials,
@@ -1013,13 +1014,14 @@ class System : public SystemBase {
         return rebuild_now(f_valid);
     }
 
-    // Direct (non-graph) rebuild with a resort, with capacity retries.  After
+    // Direct (non-graph) rebuild, with a resort unless asked not to, with
+    // capacity retries.  After
     // an overflow the list or the cell array is reallocated and every replica
     // is rebuilt (the old buffers of the other replicas are gone).
-    int rebuild_now(bool permute_force) {
+    int rebuild_now(bool permute_force, bool resort = true) {
         if (!cells_ready) return fail(ESPP_ERR_STATE, "call espp_build_neighbors first");
         for (int attempt = 0; attempt < 6; ++attempt) {
-            launches += Launch<T>::rebuild(d, cur, true, permute_force, st);
+            launches += Launch<T>::rebuild(d, cur, resort, permute_force, st);
             CK(cudaGetLastError());
             Ctrl c = read_ctrl();
             CK(cudaGetLastError());
