@@ -68,6 +68,27 @@ def dist_env():
     return rank, world, local
 
 
+# ---- the multi-GPU bookkeeping: one independent melt per rank (replicas only) ----
+def rank_seed(rank):
+    """Each rank steps its own melt, seeded by its rank."""
+    return 42 + rank
+
+
+def reduce_max(pg, x, device):
+    """Largest value over the ranks of process group pg (None: one process)."""
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world, n, steps, ms_max):
+    """Whole-job particle-steps/s: every rank's particles over the slowest rank's time."""
+    return world * n * steps / (ms_max / 1e3)
+
+
 def workload_name(a):
     return "kg_melt_%dx%d_rho0.85_wca_fene_langevin" % (a.nchains, a.nbeads)
 
@@ -337,13 +358,9 @@ def run_ours(a):
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if not pg:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(pg, x, "cuda")
 
-    seed = 42 + rank
+    seed = rank_seed(rank)
     s, cfg, start = make_melt(a, seed, espp.ESPP_FP32)
     if a.direct:
         s.set_graph_chunk(0)
@@ -363,7 +380,7 @@ def run_ours(a):
     clocks = clk.summary()
     gpu_launches = s.kernel_launches - launches0
     rebuilds = s.n_rebuilds - rb0
-    value = world * n * a.steps / (ms / 1e3)
+    value = aggregate_rate(world, n, a.steps, ms)
     obs = s.observables()
 
     # ---- step-kernel duration by CUDA events inside the graphs -------------
