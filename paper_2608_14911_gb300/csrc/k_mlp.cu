@@ -374,6 +374,9 @@ __global__ void __launch_bounds__(TC_M, TC_CTAS_PER_SM) k_mlp_tc(DevSys<float> s
     float* __restrict__ pu = s.mlp_pu;
     uint32_t parity = 0;
     bool ok = sh.stop == 0;
+    // fault injection: no MMA is issued and a short wait limit runs out
+    const bool fault = s.tc_fault != 0;
+    const int wait_limit = fault ? (1 << 12) : TC_WAIT;
     for (int tile = blockIdx.x; ok && tile < ntl; tile += gridDim.x) {
         const int p = tile * TC_M + tid;
         const bool valid = p < np;
@@ -412,7 +415,7 @@ __global__ void __launch_bounds__(TC_M, TC_CTAS_PER_SM) k_mlp_tc(DevSys<float> s
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
-        if (tid == 0) {
+        if (tid == 0 && !fault) {
             constexpr uint32_t sbo = (TC_K1 / 8) * 128;
 #pragma unroll
             for (int ks = 0; ks < TC_K1 / 16; ++ks) {
@@ -423,7 +426,7 @@ __global__ void __launch_bounds__(TC_M, TC_CTAS_PER_SM) k_mlp_tc(DevSys<float> s
             }
             tc::commit(&sh.mbar);
         }
-        if (!__syncthreads_and(tc::mbar_wait(&sh.mbar, parity, TC_WAIT))) {
+        if (!__syncthreads_and(tc::mbar_wait(&sh.mbar, parity, wait_limit))) {
             ok = false;
             break;
         }
@@ -459,7 +462,7 @@ __global__ void __launch_bounds__(TC_M, TC_CTAS_PER_SM) k_mlp_tc(DevSys<float> s
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
-        if (tid == 0) {
+        if (tid == 0 && !fault) {
             constexpr uint32_t sbo = (TC_K2 / 8) * 128;
 #pragma unroll
             for (int ks = 0; ks < TC_K2 / 16; ++ks) {
@@ -470,7 +473,7 @@ __global__ void __launch_bounds__(TC_M, TC_CTAS_PER_SM) k_mlp_tc(DevSys<float> s
             }
             tc::commit(&sh.mbar);
         }
-        if (!__syncthreads_and(tc::mbar_wait(&sh.mbar, parity, TC_WAIT))) {
+        if (!__syncthreads_and(tc::mbar_wait(&sh.mbar, parity, wait_limit))) {
             ok = false;
             break;
         }
@@ -520,8 +523,11 @@ __global__ void __launch_bounds__(TC_M, TC_CTAS_PER_SM) k_mlp_tc(DevSys<float> s
     if (!ok && sh.stop == 0) {
         // a commit never arrived: record it, give the MMAs in flight one more
         // bounded wait, then release the tensor memory
-        if (tid == 0) atomicOr(&s.ctrl->err, ERRBIT_TIMEOUT);
-        tc::mbar_wait(&sh.mbar, parity, TC_WAIT);
+        if (tid == 0) {
+            atomicOr(&s.ctrl->err, ERRBIT_TIMEOUT);
+            s.ctrl->abort = 1;
+        }
+        tc::mbar_wait(&sh.mbar, parity, wait_limit);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -593,6 +599,7 @@ static DevSys<float> as_float(const DevSys<T>& s) {
     f.mlp_pairs = s.mlp_pairs;
     f.mlp_pairs_cap = s.mlp_pairs_cap;
     f.mlp_npairs = s.mlp_npairs;
+    f.tc_fault = s.tc_fault;
     return f;
 }
 

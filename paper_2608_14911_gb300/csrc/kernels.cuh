@@ -109,6 +109,8 @@ template <class T> struct DevSys {
     int* mlp_uoff;      // per particle: first record in mlp_upper (scan of mlp_ucount)
     int* mlp_uscan_part;
     int mlp_nuscan;     // scan blocks over the particles
+    int tc_fault;       // host fault injection: the tensor-core kernel issues no MMA and
+                        // its bounded mbarrier wait runs out (tests of the timeout path)
     int N;
     BondRec<T> bond;
     T rlist2;           // (rc + skin)^2

@@ -309,6 +309,8 @@ class System : public SystemBase {
             (rc = alloc(&d_mlp, 1, allocs)))
             return rc;
         d.mlp = d_mlp;
+        // host-side fault injection for tests: the tensor-core kernel's wait runs out
+        if (const char* f = getenv("ESPP_FAULT_TC_TIMEOUT")) d.tc_fault = atoi(f) > 0 ? 1 : 0;
         d.bond_gid = bg;
         d.slot_of_id = sid;
         d.perm = perm;

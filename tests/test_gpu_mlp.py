@@ -164,6 +164,26 @@ def test_mlp_and_table_switch_on_one_handle():
     assert np.array_equal(s.compute_forces(), f_mlp)
 
 
+def test_tensor_core_wait_timeout_is_reported(monkeypatch):
+    # host-side fault injection: the tensor-core kernel issues no MMA, its
+    # bounded mbarrier wait runs out, it releases its tensor memory and the
+    # host reads ESPP_ERR_TIMEOUT; the GPU context stays usable
+    c = _cg_system(12, 50, seed=61)
+    bits, _ = _weights(7)
+    monkeypatch.setenv("ESPP_FAULT_TC_TIMEOUT", "1")
+    s = _mlp_system(c, bits)
+    s.set_state(c.x, None, c.img)
+    s.build_neighbors(RC, SKIN)
+    with pytest.raises(espp.EsppError) as e:
+        s.compute_forces()
+    assert e.value.code == espp.ESPP_ERR_TIMEOUT
+    monkeypatch.delenv("ESPP_FAULT_TC_TIMEOUT")
+    ok = _mlp_system(c, bits)
+    ok.set_state(c.x, None, c.img)
+    ok.build_neighbors(RC, SKIN)
+    assert np.isfinite(ok.compute_forces()).all()
+
+
 def test_mlp_requires_weights():
     c = _cg_system(10, 50)
     s = espp.System(c.box, c.n, c.types, c.bonds, precision=espp.ESPP_FP32)
