@@ -220,15 +220,21 @@ __global__ void __launch_bounds__(TILE) k_mlp_rev(DevSys<T> s) {
             if (j <= i) continue;
             size_t found = e;
             if (fresh) {
-                // the list is symmetric: i is in j's list
+                // the list is symmetric: i is in j's list; four groups per
+                // probe keep four loads in flight
                 const int nj = s.nbr_cnt[j];
-                for (int g = 0; 4 * g < nj; ++g) {
-                    const int4 q = nbr4[(size_t)g * stride + j];
-                    const int hit = nbr_slot(q.x) == i ? 0 : nbr_slot(q.y) == i ? 1 : nbr_slot(q.z) == i ? 2
-                                                                               : nbr_slot(q.w) == i ? 3 : -1;
-                    if (hit >= 0 && 4 * g + hit < nj) {
-                        found = entry_index(j, 4 * g + hit, stride);
-                        break;
+                const int ngj = (nj + 3) >> 2;
+                for (int g0 = 0; g0 < ngj && found == e; g0 += 4) {
+                    int4 q[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        q[u] = g0 + u < ngj ? nbr4[(size_t)(g0 + u) * stride + j] : make_int4(-1, -1, -1, -1);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int hit = nbr_slot(q[u].x) == i ? 0 : nbr_slot(q[u].y) == i ? 1
+                                      : nbr_slot(q[u].z) == i ? 2 : nbr_slot(q[u].w) == i ? 3 : -1;
+                        const int kk = 4 * (g0 + u) + hit;
+                        if (hit >= 0 && kk < nj && found == e) found = entry_index(j, kk, stride);
                     }
                 }
                 if (found == e) atomicOr(&s.ctrl->err, ERRBIT_ASYM);  // cannot happen for a symmetric list
