@@ -252,6 +252,38 @@ __global__ void __launch_bounds__(TILE) k_copyback(DevSys<T> s, int cur, int per
 // streamed with no further indirection.  Hits are packed into int4 groups in
 // registers and stored as whole 16-byte groups, so the stores of a warp are
 // contiguous.
+// Candidates [p, e) of one contiguous range: distance test, hits packed into
+// int4 groups.  SHIFT: the range lies across a face (the entries' and the
+// particle's coordinates are shifted as the image codes say); without it the
+// difference is the plain one, which equals the shifted form with zero shifts.
+template <class T, bool EXCL, bool SHIFT>
+__device__ __forceinline__ void verlet_range(const V4<T>* __restrict__ E, int p, int e, int i, int2 ex, T xo, T yo,
+                                             T zo, T xL, T yL, T zL, T rl2, int tag, int cap, size_t stride,
+                                             int& cnt, int4& grp, int4* __restrict__ out4) {
+    for (; p < e; ++p) {
+        const V4<T> xj = ld4<T>(E + p);
+        const int j = bits_as_int(xj.w);
+        const T dx = SHIFT ? xo - (xj.x - xL) : xo - xj.x;
+        const T dy = SHIFT ? yo - (xj.y - yL) : yo - xj.y;
+        const T dz = SHIFT ? zo - (xj.z - zL) : zo - xj.z;
+        bool hit = dx * dx + dy * dy + dz * dz < rl2 && j != i;
+        if (EXCL) hit = hit && j != ex.x && j != ex.y;
+        if (hit) {
+            const int l = cnt & 3;
+            const int en = j | tag;
+            if (l == 0) grp.x = en;
+            else if (l == 1) grp.y = en;
+            else if (l == 2) grp.z = en;
+            else grp.w = en;
+            ++cnt;
+            if ((cnt & 3) == 0) {
+                if (cnt <= cap) out4[(size_t)((cnt >> 2) - 1) * stride] = grp;
+                grp = make_int4(-1, -1, -1, -1);
+            }
+        }
+    }
+}
+
 template <class T, int W, bool EXCL>
 __device__ __forceinline__ void verlet_stencil(const DevSys<T>& s, const RepGeom<T>& g, int i,
                                                const V4<T>& xi, int2 ex, int& cnt, int4& grp,
@@ -310,29 +342,13 @@ __device__ __forceinline__ void verlet_stencil(const DevSys<T>& s, const RepGeom
             for (int part = 0; part < 2; ++part) {
                 const T xo = part ? xo1 : xo0, xL = part ? xL1 : xL0;
                 const int tag = ((part ? cxc1 : cxc0) | (cyc[r] << 2) | (czc << 4)) << NBR_INDEX_BITS;
-                const int e = pe[r][part];
-                for (int p = pb[r][part]; p < e; ++p) {
-                    const V4<T> xj = ld4<T>(E + p);
-                    const int j = bits_as_int(xj.w);
-                    const T dx = xo - (xj.x - xL);
-                    const T dy = yo - (xj.y - yL);
-                    const T dz2 = zo - (xj.z - zL);
-                    bool hit = dx * dx + dy * dy + dz2 * dz2 < rl2 && j != i;
-                    if (EXCL) hit = hit && j != ex.x && j != ex.y;
-                    if (hit) {
-                        const int l = cnt & 3;
-                        const int en = j | tag;
-                        if (l == 0) grp.x = en;
-                        else if (l == 1) grp.y = en;
-                        else if (l == 2) grp.z = en;
-                        else grp.w = en;
-                        ++cnt;
-                        if ((cnt & 3) == 0) {
-                            if (cnt <= cap) out4[(size_t)((cnt >> 2) - 1) * stride] = grp;
-                            grp = make_int4(-1, -1, -1, -1);
-                        }
-                    }
-                }
+                // a range that crosses no face (the common case) needs no shift
+                if (tag == 0)
+                    verlet_range<T, EXCL, false>(E, pb[r][part], pe[r][part], i, ex, xo, yo, zo, xL, yL, zL, rl2,
+                                                 tag, cap, stride, cnt, grp, out4);
+                else
+                    verlet_range<T, EXCL, true>(E, pb[r][part], pe[r][part], i, ex, xo, yo, zo, xL, yL, zL, rl2,
+                                                tag, cap, stride, cnt, grp, out4);
             }
         }
     }
