@@ -308,6 +308,44 @@ def test_broken_bond_is_reported():
     assert e.value.code == espp.ESPP_ERR_BOND_BROKEN
 
 
+def test_degenerate_inputs_are_rejected():
+    # no particles, more than the 2^25 slots a handle can address, a bond to
+    # itself, a zero box edge: ESPP_ERR_ARG before anything is allocated
+    box = np.array([10.0, 10.0, 10.0])
+    for n in (0, 1 << 25):
+        with pytest.raises(espp.EsppError) as e:
+            espp.System(box, n, precision=FP32)
+        assert e.value.code == espp.ESPP_ERR_ARG
+    with pytest.raises(espp.EsppError) as e:
+        espp.System(box, 4, bonds=np.array([[1, 1]]), precision=FP32)
+    assert e.value.code == espp.ESPP_ERR_ARG
+    with pytest.raises(espp.EsppError) as e:
+        espp.System(np.array([10.0, 0.0, 10.0]), 4, precision=FP32)
+    assert e.value.code == espp.ESPP_ERR_ARG
+
+
+def test_zero_steps_and_calls_before_setup():
+    case = kg_case()
+    s = espp.System(case.cfg.box, case.cfg.n, case.cfg.types, case.cfg.bonds, precision=FP32)
+    s.set_wca()
+    s.set_fene()
+    with pytest.raises(espp.EsppError) as e:   # no state yet
+        s.compute_forces()
+    assert e.value.code == espp.ESPP_ERR_STATE
+    s.set_state(case.cfg.x, case.v, case.cfg.img)
+    with pytest.raises(espp.EsppError) as e:   # no list yet
+        s.integrate(1, 0.005, 1.0, 1.0)
+    assert e.value.code == espp.ESPP_ERR_STATE
+    s.build_neighbors(WCA_RC, 0.4)
+    x0, v0, i0 = s.get_state()
+    s.integrate(0, 0.005, 1.0, 1.0)            # zero steps: nothing moves
+    x1, v1, i1 = s.get_state()
+    assert np.array_equal(x0, x1) and np.array_equal(v0, v1) and s.step == 0
+    with pytest.raises(espp.EsppError) as e:   # a non-positive time step
+        s.integrate(5, 0.0, 1.0, 1.0)
+    assert e.value.code == espp.ESPP_ERR_ARG
+
+
 def test_box_too_small_is_reported():
     s = espp.System(np.array([4.0, 4.0, 4.0]), 8, precision=FP32)
     s.set_wca()
