@@ -452,7 +452,8 @@ def run_ours(a):
     suite = None
     if not a.no_suite and world == 1:
         suite = {}
-        for name, fn in (("lj4m", lambda o: o.update(suite_lj4m(a, barrier, peaks))),
+        for name, fn in (("kg1m_dpd", lambda o: o.update(suite_dpd(a, barrier, s, cfg, seed, ms / a.steps))),
+                         ("lj4m", lambda o: o.update(suite_lj4m(a, barrier, peaks))),
                          ("batched512", lambda o: o.update(suite_batched(a, barrier))),
                          ("learned_cg", lambda o: suite_learned_cg(a, barrier, o))):
             part = {}
@@ -517,6 +518,30 @@ def _step_kernel_ms(s, dt, gamma, kT, steps=256):
     kt = s.kernel_timing(reset=True)
     s.set_kernel_timing(False)
     return kt["step_ms"] / max(1, kt["step_launches"]), kt["rebuild_ms"] / max(1, kt["steps"])
+
+
+def suite_dpd(a, sync, src, cfg, seed, langevin_ms):
+    """The KG melt of the headline line under the DPD thermostat (pair cutoff
+    2^(1/6), gamma 1, kT 1) in place of Langevin: each step adds a velocity
+    snapshot and a pass over the list for the pair friction and noise."""
+    from paper_2608_14911_gb300 import espp
+    s, _ = copy_system(src, cfg, espp.ESPP_FP32, seed)
+    s.set_thermostat(espp.ESPP_THERMO_DPD, WCA_RC)
+    s.integrate(200, 0.005, 1.0, 1.0)
+    p0 = s.observables()
+    steps = a.suite_steps
+    ms = _timed(s, steps, 0.005, 1.0, 1.0, sync)
+    k_ms, rb_ms = _step_kernel_ms(s, 0.005, 1.0, 1.0)
+    o = s.observables()
+    _, v, _ = s.get_state()
+    out = {"workload": workload_name(a) + "_dpd_rc1.1225_gamma1", "n_particles": cfg.n,
+           "value": cfg.n * steps / (ms / 1e3), "unit": "particle-steps/s", "steps": steps,
+           "ms_per_step": ms / steps, "langevin_ms_per_step": langevin_ms,
+           "step_kernel_avg_launch_ms": k_ms, "rebuild_node_ms_per_step": rb_ms,
+           "temperature_after": o["temperature"], "temperature_before": p0["temperature"],
+           "net_momentum_per_particle": float(abs(v.sum(axis=0)).max() / cfg.n)}
+    s.close()
+    return out
 
 
 def suite_lj4m(a, sync, peaks):

@@ -233,6 +233,25 @@ int espp_get_neighbors(espp_h h, int64_t* row_ptr, int64_t* cols, int64_t cap);
  * force is not changed. */
 int espp_compute_forces(espp_h h, double* f_out, int where);
 
+/* Thermostat of espp_integrate (paper "Functionality": Langevin dynamics and
+ * dissipative particle dynamics).  ESPP_THERMO_LANGEVIN (default; rc
+ * ignored): per particle, as described at espp_integrate.  ESPP_THERMO_DPD:
+ * per pair at distance r < rc (r_ij = x_i - x_j, e = r_ij / r,
+ * v_ij = v_i - v_j, w = 1 - r / rc):
+ *   F_i += [-gamma w^2 (e . v_ij) + sqrt(2 gamma kT) w theta_ij / sqrt(dt)] e,
+ * theta_ij = sqrt(12) u, u uniform in (-1/2, 1/2) from Philox4x32-10 with key
+ * (seed lo, seed hi) and counter (min id, max id | 2^31, step lo, step hi), so
+ * theta_ij = theta_ji and total momentum is conserved.  The velocities are
+ * those present at the force evaluation; ids are the particle ids within the
+ * replica and seed the replica's seed.  The pairs are those of the Verlet
+ * list: bonded pairs removed by espp_set_exclude_bonded get no DPD force.
+ * rc must not exceed the list cutoff
+ * of espp_build_neighbors (checked by espp_integrate: ESPP_ERR_ARG).  The
+ * stored force becomes stale.  ESPP_ERR_ARG for an unknown kind or rc <= 0. */
+#define ESPP_THERMO_LANGEVIN 0
+#define ESPP_THERMO_DPD 1
+int espp_set_thermostat(espp_h h, int32_t kind, double rc);
+
 /* Paper "Example usage": VelocityVerlet + LangevinThermostat(gamma,
  * temperature) and integrator.run(nsteps).  Each step: v += dt/2 F/m;
  * x += dt v (wrap); rebuild the list if needed; F = conservative forces

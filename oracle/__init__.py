@@ -56,6 +56,9 @@ def lib():
         L.orc_set_mlp.restype = ctypes.c_int
         L.orc_mlp_pair.argtypes = [ctypes.c_double, _dp, _dp, _dp, _dp]
         L.orc_set_exclude_bonded.argtypes = [ctypes.c_int]
+        L.orc_set_dpd.argtypes = [ctypes.c_int, ctypes.c_double]
+        L.orc_dpd_theta.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
+        L.orc_dpd_theta.restype = ctypes.c_double
         L.orc_mlp_loss_grad.argtypes = [ctypes.c_int64, _dp, ctypes.c_int64, _dp, _dp, _i32p,
                                         ctypes.c_int64, _i64p, _dp, _dp, _dp]
         L.orc_mlp_loss_grad.restype = ctypes.c_int
@@ -180,6 +183,16 @@ def mlp_loss_grad(model, box, frames_x, frames_y, types, bonds):
 
 def set_exclude_bonded(on):
     lib().orc_set_exclude_bonded(1 if on else 0)
+
+
+def set_dpd(on, rc=0.0):
+    """Use the DPD thermostat (pair cutoff rc) instead of Langevin in integrate."""
+    lib().orc_set_dpd(1 if on else 0, float(rc))
+
+
+def dpd_theta(seed, a, b, step):
+    """The pair noise theta_ab of a step (symmetric in a, b)."""
+    return lib().orc_dpd_theta(int(seed), int(a), int(b), int(step))
 
 
 def set_table(slot, rmax, u, f):

@@ -815,12 +815,71 @@ static void add_langevin(int64_t n, const double* v, const int32_t* type,
     }
 }
 
+/* Dissipative particle dynamics thermostat (paper "Functionality": DPD), the
+ * pairwise alternative to the Langevin extension.  For every pair at
+ * distance r < rc (r_ij = x_i - x_j, e = r_ij / r, v_ij = v_i - v_j):
+ *   F_i += [-gamma w(r)^2 (e . v_ij) + sigma w(r) theta_ij / sqrt(dt)] e,
+ *   w(r) = 1 - r / rc, sigma^2 = 2 gamma kT  (Espanol-Warren fluctuation-
+ *   dissipation relation; Groot-Warren weight functions).
+ * Reading: theta_ij has zero mean and unit variance: sqrt(12) times the
+ * centred uniform of word 0 of Philox4x32-10 with key (seed lo, seed hi) and
+ * counter (min id, max id | 2^31, step lo, step hi), so theta_ij = theta_ji
+ * and the pair forces cancel exactly; the velocity is the one present at the
+ * force evaluation (as for the Langevin friction). */
+static int orc_dpd_on = 0;
+static double orc_dpd_rc = 0.0;
+void orc_set_dpd(int on, double rc) {
+    orc_dpd_on = on ? 1 : 0;
+    orc_dpd_rc = rc;
+}
+
+double orc_dpd_theta(uint64_t seed, int64_t a, int64_t b, int64_t step) {
+    const int64_t lo = a < b ? a : b, hi = a < b ? b : a;
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint64_t s = (uint64_t)step;
+    uint32_t ctr[4] = {(uint32_t)lo, (uint32_t)hi | 0x80000000u, (uint32_t)(s & 0xffffffffu), (uint32_t)(s >> 32)};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return sqrt(12.0) * orc_uniform_centered(out[0]);
+}
+
+static void add_dpd(int64_t n, const double* L, const double* x, const double* v, double* f, double dt,
+                    double gamma, double kT, uint64_t seed, int64_t step) {
+    if (gamma == 0.0 && kT == 0.0) return;
+    const double rc = orc_dpd_rc, sigma = sqrt(2.0 * gamma * kT), inv_sqdt = 1.0 / sqrt(dt);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        double fi[3] = {0.0, 0.0, 0.0};
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double d[3];
+            min_image_vec(x + 3 * i, x + 3 * j, L, d);
+            const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (!(r2 < rc * rc)) continue;
+            const double r = sqrt(r2), w = 1.0 - r / rc;
+            double ev = 0.0;
+            for (int c = 0; c < 3; ++c) ev += d[c] / r * (v[3 * i + c] - v[3 * j + c]);
+            const double mag = -gamma * w * w * ev + sigma * w * orc_dpd_theta(seed, i, j, step) * inv_sqdt;
+            for (int c = 0; c < 3; ++c) fi[c] += mag * d[c] / r;
+        }
+        for (int c = 0; c < 3; ++c) f[3 * i + c] += fi[c];
+    }
+}
+
+/* the thermostat of the force step: DPD when selected, else Langevin */
+static void add_thermostat(int64_t n, const double* L, const double* x, const double* v, const int32_t* type,
+                           const double* mass_of_type, double* f, double dt, double gamma, double kT,
+                           uint64_t seed, int64_t step) {
+    if (orc_dpd_on) add_dpd(n, L, x, v, f, dt, gamma, kT, seed, step);
+    else add_langevin(n, v, type, mass_of_type, f, dt, gamma, kT, seed, step);
+}
+
 /* Velocity Verlet (the example's VelocityVerlet) with the Langevin extension.
  * One step from step s-1 to s:
  *   1. v += dt/2 F/m            (F of step s-1)
  *   2. x += dt v, wrap into the box, update image counters
  *   3. F = conservative forces at the new x
- *   4. F += -gamma m v + sqrt(24 gamma m kT/dt) r(s)
+ *   4. F += -gamma m v + sqrt(24 gamma m kT/dt) r(s)   (or the DPD pair terms)
  *   5. v += dt/2 F/m
  * Reading: when f is not valid on entry, F of step step0 is first computed
  * from x, v with the noise of step step0. */
@@ -834,7 +893,7 @@ int orc_integrate(int64_t n, const double* L, double* x, double* v, int32_t* img
     if (!f_valid) {
         st = orc_forces(n, L, x, type, ntypes, pair_params, nbonds, bonds, bond_params, f, en);
         if (st) return st;
-        add_langevin(n, v, type, mass_of_type, f, dt, gamma, kT, seed, step0);
+        add_thermostat(n, L, x, v, type, mass_of_type, f, dt, gamma, kT, seed, step0);
     }
     for (int64_t s = step0 + 1; s <= step0 + nsteps; ++s) {
 #pragma omp parallel for schedule(static)
@@ -848,7 +907,7 @@ int orc_integrate(int64_t n, const double* L, double* x, double* v, int32_t* img
         }
         st = orc_forces(n, L, x, type, ntypes, pair_params, nbonds, bonds, bond_params, f, en);
         if (st) return st;
-        add_langevin(n, v, type, mass_of_type, f, dt, gamma, kT, seed, s);
+        add_thermostat(n, L, x, v, type, mass_of_type, f, dt, gamma, kT, seed, s);
 #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; ++i) {
             double m = mass_of_type[type[i]];

@@ -43,6 +43,11 @@ void orc_uniform_fill(const uint32_t* w, int64_t n, double* out);
 /* Langevin noise words for particle ids [0,n) at a given step: out n*3. */
 void orc_langevin_noise(uint64_t seed, int64_t step, int64_t n, double* out);
 
+/* DPD thermostat instead of Langevin in orc_integrate (pair cutoff rc), and
+ * the pair noise theta_ij of a step (zero mean, unit variance). */
+void orc_set_dpd(int on, double rc);
+double orc_dpd_theta(uint64_t seed, int64_t a, int64_t b, int64_t step);
+
 /* Register a table (u, F = -dU/dr at r_k = k rmax/(n-1)) in slot [0, 16). */
 int orc_set_table(int slot, double rmax, int n, const double* u, const double* f);
 

@@ -171,13 +171,63 @@ __device__ __forceinline__ void pair_loop(const DevSys<T>& s, const V4<T>* __res
     }
 }
 
+// DPD thermostat forces on particle i (paper "Functionality": dissipative
+// particle dynamics): a second pass over the list, pairs inside the DPD
+// cutoff, neighbour velocities and ids from the step's velocity snapshot.
+template <class T>
+__device__ __forceinline__ void dpd_loop(const DevSys<T>& s, const V4<T>* __restrict__ P, int i, int n,
+                                         const V4<T>& xi, const V4<T>& vi, T L0, T L1, T L2,
+                                         unsigned long long seed, long long step, T& fx, T& fy, T& fz) {
+    const IntParams<T>* __restrict__ ip = s.ip;
+    const T rc2 = ip->dpd_rc2, inv_rc = ip->dpd_inv_rc, gamma = ip->gamma, amp = ip->dpd_amp;
+    const T xim = xi.x - L0, yim = xi.y - L1, zim = xi.z - L2;
+    const int idi = bits_as_int(vi.w);
+    const int4* __restrict__ nb = reinterpret_cast<const int4*>(s.nbr) + i;
+    const V4<T>* __restrict__ VS = s.vsnap;
+    const size_t stride = (size_t)s.stride;
+    for (int g = 0; 4 * g < n; ++g) {
+        const int4 a = __ldg(nb + g * stride);
+        const int jj[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (4 * g + q >= n) continue;
+            const int j = nbr_slot(jj[q]), code = nbr_code(jj[q]);
+            const V4<T> xj = ld4<T>(P + j);
+            const T dx = shifted_diff(xi.x, xim, xj.x, L0, code & 3);
+            const T dy = shifted_diff(xi.y, yim, xj.y, L1, (code >> 2) & 3);
+            const T dz = shifted_diff(xi.z, zim, xj.z, L2, code >> 4);
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            if (!(r2 < rc2)) continue;
+            const V4<T> vj = ld4<T>(VS + j);
+            const T r = sqrt(r2), inv_r = T(1) / r;
+            const T w = T(1) - r * inv_rc;
+            const T ev = (dx * (vi.x - vj.x) + dy * (vi.y - vj.y) + dz * (vi.z - vj.z)) * inv_r;
+            const T th = dpd_theta<T>(seed, idi, bits_as_int(vj.w), step);
+            const T mag = (-gamma * w * w * ev + amp * w * th) * inv_r;
+            fx += mag * dx;
+            fy += mag * dy;
+            fz += mag * dz;
+        }
+    }
+}
+
+// velocities at the force evaluation, read by the DPD pass for the neighbours
+template <class T>
+__global__ void __launch_bounds__(TILE) k_vsnap(DevSys<T> s) {
+    if (s.ctrl->abort) return;
+    for (int t = blockIdx.x; t < s.ntiles; t += gridDim.x) {
+        const Tile tl = s.tiles[t];
+        if ((int)threadIdx.x < tl.count) s.vsnap[tl.start + threadIdx.x] = s.vel[tl.start + threadIdx.x];
+    }
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return v;
 }
 
-template <class T, int MODE, bool ENERGY, bool FAST>
+template <class T, int MODE, bool ENERGY, bool FAST, bool DPD>
 __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? ESPP_STEP_MINB32 : 4) k_step(DevSys<T> s, int cur, double* __restrict__ f_out,
                                                unsigned long long next_cond) {
     Ctrl* c = s.ctrl;
@@ -309,7 +359,9 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? ESPP_STEP_MINB32 : 4) k
                 }
             } else {
                 const T m = ip->mass[ti], inv_m = ip->inv_mass[ti];
-                if (ip->gamma != T(0)) {
+                if (DPD) {
+                    dpd_loop<T>(s, P, i, n, xi, v, L0, L1, L2, g.seed, step, fx, fy, fz);
+                } else if (ip->gamma != T(0)) {
                     T rx, ry, rz;
                     langevin_noise<T>(g.seed, bits_as_int(v.w), step, rx, ry, rz);
                     const T amp = ip->noise_amp[ti];
@@ -442,19 +494,30 @@ template <class T>
 int Launch<T>::step(const DevSys<T>& s, int mode, bool energy, int cur, double* f_out,
                     unsigned long long next_cond, int grid, cudaStream_t st) {
     const int gr = grid > 0 ? grid : s.ntiles;
-    const int extra = s.mlp_on ? Launch<T>::mlp(s, cur, energy, st) : 0;
-#define ESPP_STEP(M, E)                                                                  \
-    do {                                                                                 \
-        if (s.lj_fast) k_step<T, M, E, true><<<gr, TILE, 0, st>>>(s, cur, f_out, next_cond); \
-        else k_step<T, M, E, false><<<gr, TILE, 0, st>>>(s, cur, f_out, next_cond);     \
+    int extra = s.mlp_on ? Launch<T>::mlp(s, cur, energy, st) : 0;
+    const bool dpd = s.dpd && mode != MODE_FORCES;
+    if (dpd) {
+        k_vsnap<T><<<s.ntiles, TILE, 0, st>>>(s);
+        extra += 1;
+    }
+#define ESPP_STEP(M, E, D)                                                                  \
+    do {                                                                                    \
+        if (s.lj_fast) k_step<T, M, E, true, D><<<gr, TILE, 0, st>>>(s, cur, f_out, next_cond); \
+        else k_step<T, M, E, false, D><<<gr, TILE, 0, st>>>(s, cur, f_out, next_cond);     \
     } while (0)
     switch (mode) {
         case MODE_FORCES:
-            if (energy) ESPP_STEP(MODE_FORCES, true); else ESPP_STEP(MODE_FORCES, false);
+            if (energy) ESPP_STEP(MODE_FORCES, true, false); else ESPP_STEP(MODE_FORCES, false, false);
             break;
-        case MODE_INIT: ESPP_STEP(MODE_INIT, false); break;
-        case MODE_STEP: ESPP_STEP(MODE_STEP, false); break;
-        default: ESPP_STEP(MODE_FINAL, false); break;
+        case MODE_INIT:
+            if (dpd) ESPP_STEP(MODE_INIT, false, true); else ESPP_STEP(MODE_INIT, false, false);
+            break;
+        case MODE_STEP:
+            if (dpd) ESPP_STEP(MODE_STEP, false, true); else ESPP_STEP(MODE_STEP, false, false);
+            break;
+        default:
+            if (dpd) ESPP_STEP(MODE_FINAL, false, true); else ESPP_STEP(MODE_FINAL, false, false);
+            break;
     }
 #undef ESPP_STEP
     return 1 + extra;

@@ -16,6 +16,9 @@ template <class T> struct IntParams {
     T mass[MAX_TYPES];
     T inv_mass[MAX_TYPES];
     T noise_amp[MAX_TYPES];  // sqrt(24 gamma m kT / dt)
+    T dpd_rc2;               // DPD thermostat: cutoff^2, 1 / cutoff,
+    T dpd_inv_rc;
+    T dpd_amp;               // sqrt(2 gamma kT) sqrt(12) / sqrt(dt) (times w u gives the random force)
 };
 
 // Learned pair potential: 32 radial bases -> 64 -> 64 -> 1 (SiLU), weights
@@ -109,6 +112,8 @@ template <class T> struct DevSys {
     int* mlp_uoff;      // per particle: first record in mlp_upper (scan of mlp_ucount)
     int* mlp_uscan_part;
     int mlp_nuscan;     // scan blocks over the particles
+    int dpd;            // DPD thermostat instead of Langevin (integration modes)
+    V4<T>* vsnap;       // DPD: velocities at the force evaluation, read for the neighbours
     int tc_fault;       // host fault injection: the tensor-core kernel issues no MMA and
                         // its bounded mbarrier wait runs out (tests of the timeout path)
     int N;

@@ -46,4 +46,16 @@ __device__ __forceinline__ void langevin_noise(unsigned long long seed, int id, 
     rz = uniform_centered<T>(o.z);
 }
 
+// DPD pair noise theta_ij = sqrt(12) u (zero mean, unit variance): word 0 of
+// Philox4x32-10 with key (seed lo, seed hi) and counter (min id, max id | 2^31,
+// step lo, step hi); symmetric in the two ids.
+template <class T>
+__device__ __forceinline__ T dpd_theta(unsigned long long seed, int a, int b, long long step) {
+    const unsigned long long s = (unsigned long long)step;
+    const unsigned int lo = (unsigned int)min(a, b), hi = (unsigned int)max(a, b) | 0x80000000u;
+    const uint4 o = philox4x32_10(make_uint4(lo, hi, (unsigned int)(s & 0xffffffffull), (unsigned int)(s >> 32)),
+                                  make_uint2((unsigned int)(seed & 0xffffffffull), (unsigned int)(seed >> 32)));
+    return uniform_centered<T>(o.x);
+}
+
 }  // namespace espp

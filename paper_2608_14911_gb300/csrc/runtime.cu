@@ -68,6 +68,7 @@ struct SystemBase {
     virtual int list_stats(int64_t* total, int32_t* maxc) = 0;
     virtual int set_resort_interval(int64_t steps) = 0;
     virtual int set_cell_subdivision(int w) = 0;
+    virtual int set_thermostat(int kind, double rc) = 0;
 };
 
 struct PairHost {
@@ -137,6 +138,7 @@ class System : public SystemBase {
     int chunk = 64;
     int64_t resort_every = 500;  // steps between Hilbert resorts inside integrate (0 = never)
     int cell_sub_req = 0;  // requested cell subdivision (0 = chosen per system)
+    double dpd_rc = 0;     // DPD thermostat cutoff (d.dpd set)
     int cell_sub = 1;      // subdivision in use (stencil half width)
 
     ~System() override {
@@ -505,6 +507,11 @@ class System : public SystemBase {
         ip.half_dt = (T)(0.5 * dt);
         ip.gamma = (T)gamma;
         ip.kT = (T)kT;
+        if (d.dpd) {
+            ip.dpd_rc2 = (T)(dpd_rc * dpd_rc);
+            ip.dpd_inv_rc = (T)(1.0 / dpd_rc);
+            ip.dpd_amp = (T)(std::sqrt(2.0 * gamma * kT) * std::sqrt(12.0) / std::sqrt(dt));
+        }
         for (int a = 0; a < MAX_TYPES; ++a) {
             ip.mass[a] = (T)mass_h[a];
             ip.inv_mass[a] = (T)(1.0 / mass_h[a]);
@@ -1237,6 +1244,8 @@ class System : public SystemBase {
         if (nsteps == 0) return ESPP_OK;
         int rcode = ensure_list();
         if (rcode) return rcode;
+        if (d.dpd && !(dpd_rc <= rc_list * (1 + 1e-12)))
+            return fail(ESPP_ERR_ARG, "the DPD cutoff exceeds the list cutoff");
         rcode = upload_int_params(dt, gamma, kT);
         if (rcode) return rcode;
         Ctrl c0 = read_ctrl();
@@ -1291,7 +1300,7 @@ class System : public SystemBase {
                 if (rcode) return rcode;
                 CK(cudaGraphLaunch(cg->exec, st));
                 last_cg = cg;
-                launches += 1 + S * (d.mlp_on ? 4 : 1);
+                launches += 1 + S * (1 + (d.mlp_on ? 3 : 0) + (d.dpd ? 1 : 0));
                 p ^= (int)((fin ? (S - 1) : S) & 1);
                 next += S;
             }
@@ -1589,6 +1598,26 @@ class System : public SystemBase {
         return ESPP_OK;
     }
 
+    int set_thermostat(int kind, double rc) override {
+        if (kind == ESPP_THERMO_LANGEVIN) {
+            d.dpd = 0;
+        } else if (kind == ESPP_THERMO_DPD) {
+            if (!(rc > 0) || !std::isfinite(rc)) return fail(ESPP_ERR_ARG, "the DPD cutoff must be > 0");
+            if (!d.vsnap) {
+                const int rb = alloc(&d.vsnap, (size_t)N, allocs);
+                if (rb) return rb;
+            }
+            d.dpd = 1;
+            dpd_rc = rc;
+        } else {
+            return fail(ESPP_ERR_ARG, "unknown thermostat kind");
+        }
+        clear_graphs();   // the thermostat is a template argument of captured kernels
+        mass_dirty = true;  // the DPD constants live in the integrator parameters
+        f_valid = false;
+        return ESPP_OK;
+    }
+
     int set_cell_subdivision(int w) override {
         if (w < 0 || w > 2) return fail(ESPP_ERR_ARG, "cell subdivision must be 0, 1 or 2");
         cell_sub_req = w;
@@ -1770,6 +1799,9 @@ int espp_set_resort_interval(espp_h h, int64_t steps) {
     return guarded(h, [&](espp::SystemBase& s) { return s.set_resort_interval(steps); });
 }
 
+int espp_set_thermostat(espp_h h, int32_t kind, double rc) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.set_thermostat(kind, rc); });
+}
 int espp_set_cell_subdivision(espp_h h, int32_t w) {
     return guarded(h, [&](espp::SystemBase& s) { return s.set_cell_subdivision(w); });
 }

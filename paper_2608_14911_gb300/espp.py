@@ -39,6 +39,8 @@ ESPP_TAB_PAIR = 5
 ESPP_TAB_BOND = 6
 ESPP_MLP = 7
 MLP_NPARAMS = 6337
+ESPP_THERMO_LANGEVIN = 0
+ESPP_THERMO_DPD = 1
 
 ERROR_NAMES = {
     ESPP_ERR_ARG: "ESPP_ERR_ARG", ESPP_ERR_CUDA: "ESPP_ERR_CUDA",
@@ -60,7 +62,7 @@ EXPORTS = (
     "espp_set_kernel_timing", "espp_kernel_timing", "espp_set_graph_chunk", "espp_list_stats",
     "espp_rdf_counts_noalloc", "espp_set_resort_interval", "espp_mlp_set_weights",
     "espp_set_exclude_bonded", "espp_mlp_get_weights", "espp_mlp_train", "espp_mlp_loss_grad",
-    "espp_cg_map", "espp_set_cell_subdivision",
+    "espp_cg_map", "espp_set_cell_subdivision", "espp_set_thermostat",
 )
 NOALLOC_MAX_BINS = 4096
 
@@ -138,6 +140,7 @@ def lib(path: str = LIB_PATH):
         "espp_rdf_counts_noalloc": ([vp, i64, dp, ctypes.c_double, i32, vp, vp], ctypes.c_int),
         "espp_set_resort_interval": ([vp, i64], ctypes.c_int),
         "espp_set_cell_subdivision": ([vp, ctypes.c_int32], ctypes.c_int),
+        "espp_set_thermostat": ([vp, ctypes.c_int32, ctypes.c_double], ctypes.c_int),
         "espp_mlp_set_weights": ([vp, vp, i64], ctypes.c_int),
         "espp_set_exclude_bonded": ([vp, ctypes.c_int], ctypes.c_int),
         "espp_mlp_get_weights": ([vp, vp, i64], ctypes.c_int),
@@ -409,6 +412,10 @@ class System:
 
     def set_cell_subdivision(self, w):
         self._c(lib().espp_set_cell_subdivision(self._h, int(w)))
+
+    def set_thermostat(self, kind, rc=0.0):
+        """ESPP_THERMO_LANGEVIN, or ESPP_THERMO_DPD with pair cutoff rc."""
+        self._c(lib().espp_set_thermostat(self._h, int(kind), float(rc)))
 
     def set_graph_chunk(self, steps):
         self._c(lib().espp_set_graph_chunk(self._h, int(steps)))

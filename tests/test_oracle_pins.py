@@ -552,3 +552,132 @@ def test_force_matching_gradient_by_finite_differences():
     finally:
         O.set_exclude_bonded(False)
         O.set_mlp(p, 3.5)
+
+
+# --------------------------------------------------------------------------
+# DPD thermostat (paper "Functionality": dissipative particle dynamics)
+# --------------------------------------------------------------------------
+@pytest.fixture
+def dpd_on():
+    def on(rc):
+        O.set_dpd(True, rc)
+    yield on
+    O.set_dpd(False)
+
+
+LJ_FLUID = O.Model(1, {(0, 0): ("lj", 1.0, 1.0, 2.5, True)})
+
+
+def _unwrapped(st):
+    return st.x + st.img * st.box
+
+
+def _ideal_dpd_gas(n, density, seed):
+    side = (n / density) ** (1.0 / 3.0)
+    c = I.random_positions(n, np.array([side] * 3), seed=seed)
+    v = I.maxwell_velocities(n, 1.0, seed=seed)
+    v -= v.mean(axis=0)
+    return O.State(c.box, c.x, v)
+
+
+def test_dpd_theta_keying_and_moments():
+    # symmetric in the pair, keyed by step and seed, word 0 of the Philox
+    # block with counter (min id, max id | 2^31, step lo, step hi)
+    assert O.dpd_theta(7, 3, 11, 5) == O.dpd_theta(7, 11, 3, 5)
+    assert O.dpd_theta(7, 3, 11, 5) != O.dpd_theta(7, 3, 11, 6)
+    assert O.dpd_theta(7, 3, 11, 5) != O.dpd_theta(8, 3, 11, 5)
+    step = (1 << 33) + 9
+    out = O.philox([3, 11 | 0x80000000, step & 0xffffffff, step >> 32], [7, 0])
+    assert O.dpd_theta(7, 11, 3, step) == math.sqrt(12.0) * O.uniform_centered(out[:1])[0]
+    # the pair counter never meets the per-particle one (bit 31 of word 1)
+    assert (11 | 0x80000000) != 11
+    g = I.rng(3, 0)
+    a = g.integers(0, 1 << 20, 20000)
+    b = g.integers(0, 1 << 20, 20000)
+    th = np.array([O.dpd_theta(99, int(x), int(y), 17) for x, y in zip(a, b)])
+    # zero mean, unit variance (uniform: 4th moment 9/5)
+    assert abs(th.mean()) < 5 / math.sqrt(th.size)
+    assert abs(th.var() - 1.0) < 5 * math.sqrt(0.8 / th.size)
+    assert np.abs(th).max() < math.sqrt(3.0)
+
+
+def test_dpd_two_particles_closed_form(dpd_on):
+    # kT = 0, no conservative force: the relative velocity along the pair axis
+    # decays as exp(-2 gamma w^2 t) (reduced mass 1/2), the perpendicular
+    # component is untouched, the centre of mass moves uniformly
+    dpd_on(1.0)
+    gamma, r0, dt, nsteps = 4.5, 0.5, 1e-3, 100
+    x = np.array([[5.0, 5.0, 5.0], [5.0 + r0, 5.0, 5.0]])
+    # equal perpendicular velocities keep the pair axis along x
+    v = np.array([[0.3 + 5e-4, 0.2, -0.1], [0.3 - 5e-4, 0.2, -0.1]])
+    st = O.State(np.array([10.0, 10.0, 10.0]), x, v)
+    O.integrate(FREE, st, nsteps, dt, gamma, 0.0, seed=1)
+    w = 1.0 - r0 / 1.0
+    u = st.v[0, 0] - st.v[1, 0]
+    assert abs(u / 1e-3 - math.exp(-2 * gamma * w * w * nsteps * dt)) < 2e-3
+    assert np.array_equal(st.v[:, 1:], v[:, 1:])
+    assert abs(st.v[:, 0].sum() - v[:, 0].sum()) < 1e-15
+    # beyond the cutoff nothing acts
+    v = np.array([[0.3, 0.2, -0.1], [-0.3, -0.4, 0.7]])
+    st = O.State(np.array([10.0, 10.0, 10.0]), np.array([[5.0, 5.0, 5.0], [7.2, 5.0, 5.0]]), v)
+    O.integrate(FREE, st, 20, dt, gamma, 1.0, seed=1)
+    assert np.array_equal(st.v, v)
+
+
+def test_dpd_conserves_momentum(dpd_on):
+    dpd_on(1.0)
+    c = I.lj_fcc(5, 5, 5, density=0.8442)
+    v = I.maxwell_velocities(c.n, 1.5, seed=4) + np.array([0.02, -0.01, 0.005])
+    st = O.State(c.box, c.x, v)
+    p0 = st.v.sum(axis=0)
+    assert np.abs(p0).max() > 1.0  # a non-trivial total momentum to keep
+    O.integrate(LJ_FLUID, st, 200, 0.005, 4.5, 1.0, seed=4)
+    assert np.abs(st.v.sum(axis=0) - p0).max() < 1e-10
+    # with Langevin the same run loses it to the solvent
+    O.set_dpd(False)
+    st = O.State(c.box, c.x, v)
+    O.integrate(LJ_FLUID, st, 200, 0.005, 4.5, 1.0, seed=4)
+    assert np.abs(st.v.sum(axis=0) - p0).max() > 1.0
+
+
+def test_dpd_galilean_invariance(dpd_on):
+    # only relative velocities enter: a uniform boost u is carried along exactly
+    dpd_on(1.0)
+    c = I.lj_fcc(4, 4, 4, density=0.8442)
+    v = I.maxwell_velocities(c.n, 1.0, seed=6)
+    u = np.array([0.7, -1.3, 0.25])
+    a = O.State(c.box, c.x, v)
+    b = O.State(c.box, c.x, v + u)
+    nsteps, dt = 100, 0.005
+    O.integrate(LJ_FLUID, a, nsteps, dt, 4.5, 1.0, seed=9)
+    O.integrate(LJ_FLUID, b, nsteps, dt, 4.5, 1.0, seed=9)
+    assert np.abs(b.v - a.v - u).max() < 1e-9
+    assert np.abs(_unwrapped(b) - _unwrapped(a) - u * nsteps * dt).max() < 1e-9
+
+
+def test_dpd_dissipates_without_noise(dpd_on):
+    dpd_on(1.0)
+    st = _ideal_dpd_gas(400, 3.0, seed=2)
+    ke = [0.5 * (st.v ** 2).sum()]
+    for _ in range(30):
+        O.integrate(FREE, st, 1, 0.01, 4.5, 0.0, seed=2)
+        ke.append(0.5 * (st.v ** 2).sum())
+    ke = np.array(ke)
+    assert np.all(np.diff(ke) < 0)
+    assert ke[-1] < 0.5 * ke[0]
+    assert np.abs(st.v.sum(axis=0)).max() < 1e-10
+
+
+def test_dpd_equipartition(dpd_on):
+    # fluctuation-dissipation: an ideal DPD gas (density 3, rc 1, gamma 4.5)
+    # settles at the bath temperature
+    dpd_on(1.0)
+    kT = 1.0
+    st = _ideal_dpd_gas(648, 3.0, seed=11)
+    st.v *= math.sqrt(0.3)  # start cold
+    O.integrate(FREE, st, 300, 0.01, 4.5, kT, seed=11)
+    t = []
+    for _ in range(60):
+        O.integrate(FREE, st, 10, 0.01, 4.5, kT, seed=11)
+        t.append((st.v ** 2).sum() / (3 * (st.n - 1)))
+    assert abs(np.mean(t) - kT) < 0.03 * kT, np.mean(t)
