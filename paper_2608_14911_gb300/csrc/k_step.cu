@@ -27,6 +27,9 @@
 #ifndef ESPP_STEP_MINB32
 #define ESPP_STEP_MINB32 10
 #endif
+#ifndef ESPP_STEP_MINB32_DPD  // the same for the DPD variants
+#define ESPP_STEP_MINB32_DPD 10
+#endif
 #ifndef ESPP_STEP_PREFETCH
 #define ESPP_STEP_PREFETCH 2  // request the next batch's list groups early (see pair_loop)
 #endif
@@ -101,14 +104,44 @@ __device__ __forceinline__ void pair_term(const DevSys<T>& s, int ti, const Pair
     }
 }
 
+// What the DPD pair term of particle i needs besides the displacement: its
+// half-step velocity and id, the replica's seed and the step.
+template <class T>
+struct DpdCtx {
+    V4<T> vi;
+    unsigned long long seed;
+    long long step;
+};
+
+// DPD pair term (paper "Functionality": dissipative particle dynamics) of a
+// neighbour at displacement d (r2 = |d|^2 inside the DPD cutoff) whose
+// velocity snapshot is vj: dissipative -gamma w^2 (e . v_ij) and random
+// amp w theta_ij along e, w = 1 - r / rc.  e . v_ij and theta_ij are symmetric
+// in the pair, so both sides add exactly opposite forces.
+template <class T>
+__device__ __forceinline__ void dpd_term(const IntParams<T>* __restrict__ ip, const DpdCtx<T>& c, T dx, T dy,
+                                         T dz, T r2, const V4<T>& vj, T& fx, T& fy, T& fz) {
+    const T r = sqrt(r2), inv_r = T(1) / r;
+    const T w = T(1) - r * ip->dpd_inv_rc;
+    const T ev = (dx * (c.vi.x - vj.x) + dy * (c.vi.y - vj.y) + dz * (c.vi.z - vj.z)) * inv_r;
+    const T th = dpd_theta<T>(c.seed, bits_as_int(c.vi.w), bits_as_int(vj.w), c.step);
+    const T mag = (-ip->gamma * w * w * ev + ip->dpd_amp * w * th) * inv_r;
+    fx += mag * dx;
+    fy += mag * dy;
+    fz += mag * dz;
+}
+
 // Sum of the pair forces on particle i over its Verlet list.  The list is
 // read in batches of int4 groups: all indices of a batch first, then all
 // neighbour positions, then the arithmetic, so that each thread keeps several
 // independent loads in flight; the next batch's indices are prefetched.
-template <class T, bool ENERGY, bool MULTI, bool FAST>
+// With DPD the thermostat's pair term is added in the same pass, for pairs
+// inside the DPD cutoff, from the neighbours' velocity snapshot.
+template <class T, bool ENERGY, bool MULTI, bool FAST, bool DPD>
 __device__ __forceinline__ void pair_loop(const DevSys<T>& s, const V4<T>* __restrict__ P, int i, int n,
                                           const V4<T>& xi, int ti, const PairRec<T>* pr1,
-                                          T L0, T L1, T L2, T& fx, T& fy, T& fz, T& pe, T& vir) {
+                                          T L0, T L1, T L2, T& fx, T& fy, T& fz, T& pe, T& vir,
+                                          const DpdCtx<T>* dc = nullptr) {
     const T xim = xi.x - L0, yim = xi.y - L1, zim = xi.z - L2;
     constexpr int GB = sizeof(T) == 4 ? ESPP_STEP_GB32 : 1;  // int4 groups per batch
     const int ng = (n + 3) >> 2;
@@ -153,8 +186,14 @@ __device__ __forceinline__ void pair_loop(const DevSys<T>& s, const V4<T>* __res
 #pragma unroll
             for (int q = 0; q < 4 * GB; ++q) {
                 if (jj[q] < 0) continue;
-                pair_term<T, ENERGY, MULTI, FAST>(s, ti, pr1, xi.x - xj[q].x, xi.y - xj[q].y, xi.z - xj[q].z,
-                                                  bits_as_int(xj[q].w), fx, fy, fz, pe, vir);
+                const T dx = xi.x - xj[q].x, dy = xi.y - xj[q].y, dz = xi.z - xj[q].z;
+                pair_term<T, ENERGY, MULTI, FAST>(s, ti, pr1, dx, dy, dz, bits_as_int(xj[q].w), fx, fy, fz, pe,
+                                                  vir);
+                if (DPD) {
+                    const T r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 < s.ip->dpd_rc2)
+                        dpd_term<T>(s.ip, *dc, dx, dy, dz, r2, ld4<T>(s.vsnap + nbr_slot(jj[q])), fx, fy, fz);
+                }
             }
         } else {
 #pragma unroll
@@ -166,22 +205,25 @@ __device__ __forceinline__ void pair_loop(const DevSys<T>& s, const V4<T>* __res
                 const T dz = shifted_diff(xi.z, zim, xj[q].z, L2, code >> 4);
                 pair_term<T, ENERGY, MULTI, FAST>(s, ti, pr1, dx, dy, dz, bits_as_int(xj[q].w), fx, fy, fz,
                                                   pe, vir);
+                if (DPD) {
+                    const T r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 < s.ip->dpd_rc2)
+                        dpd_term<T>(s.ip, *dc, dx, dy, dz, r2, ld4<T>(s.vsnap + nbr_slot(jj[q])), fx, fy, fz);
+                }
             }
         }
     }
 }
 
-// DPD thermostat forces on particle i (paper "Functionality": dissipative
-// particle dynamics): a second pass over the list, pairs inside the DPD
-// cutoff, neighbour velocities and ids from the step's velocity snapshot.
+// DPD thermostat forces on particle i as a pass of their own over the list,
+// for the learned potential, whose pair forces come from k_mlp.
 template <class T>
 __device__ __forceinline__ void dpd_loop(const DevSys<T>& s, const V4<T>* __restrict__ P, int i, int n,
-                                         const V4<T>& xi, const V4<T>& vi, T L0, T L1, T L2,
-                                         unsigned long long seed, long long step, T& fx, T& fy, T& fz) {
+                                         const V4<T>& xi, const DpdCtx<T>& c, T L0, T L1, T L2, T& fx, T& fy,
+                                         T& fz) {
     const IntParams<T>* __restrict__ ip = s.ip;
-    const T rc2 = ip->dpd_rc2, inv_rc = ip->dpd_inv_rc, gamma = ip->gamma, amp = ip->dpd_amp;
+    const T rc2 = ip->dpd_rc2;
     const T xim = xi.x - L0, yim = xi.y - L1, zim = xi.z - L2;
-    const int idi = bits_as_int(vi.w);
     const int4* __restrict__ nb = reinterpret_cast<const int4*>(s.nbr) + i;
     const V4<T>* __restrict__ VS = s.vsnap;
     const size_t stride = (size_t)s.stride;
@@ -198,15 +240,7 @@ __device__ __forceinline__ void dpd_loop(const DevSys<T>& s, const V4<T>* __rest
             const T dz = shifted_diff(xi.z, zim, xj.z, L2, code >> 4);
             const T r2 = dx * dx + dy * dy + dz * dz;
             if (!(r2 < rc2)) continue;
-            const V4<T> vj = ld4<T>(VS + j);
-            const T r = sqrt(r2), inv_r = T(1) / r;
-            const T w = T(1) - r * inv_rc;
-            const T ev = (dx * (vi.x - vj.x) + dy * (vi.y - vj.y) + dz * (vi.z - vj.z)) * inv_r;
-            const T th = dpd_theta<T>(seed, idi, bits_as_int(vj.w), step);
-            const T mag = (-gamma * w * w * ev + amp * w * th) * inv_r;
-            fx += mag * dx;
-            fy += mag * dy;
-            fz += mag * dz;
+            dpd_term<T>(ip, c, dx, dy, dz, r2, ld4<T>(VS + j), fx, fy, fz);
         }
     }
 }
@@ -228,7 +262,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 template <class T, int MODE, bool ENERGY, bool FAST, bool DPD>
-__global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? ESPP_STEP_MINB32 : 4) k_step(DevSys<T> s, int cur, double* __restrict__ f_out,
+__global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32_DPD : ESPP_STEP_MINB32) : 4) k_step(DevSys<T> s, int cur, double* __restrict__ f_out,
                                                unsigned long long next_cond) {
     Ctrl* c = s.ctrl;
     if (MODE != MODE_FORCES && c->abort) return;
@@ -264,6 +298,12 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? ESPP_STEP_MINB32 : 4) k
             if (MODE == MODE_STEP) xbi = s.xb[i];
             const V4<T> xp0 = b.x >= 0 ? ld4<T>(P + b.x) : xi;
             const V4<T> xp1 = b.y >= 0 ? ld4<T>(P + b.y) : xi;
+            DpdCtx<T> dc;
+            if (DPD) {
+                dc.vi = v;
+                dc.seed = g.seed;
+                dc.step = step;
+            }
             if (s.mlp_on) {
                 // pair forces of the learned potential, computed by k_mlp
                 const float4 fm = s.mlp_f[i];
@@ -274,6 +314,7 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? ESPP_STEP_MINB32 : 4) k
                     pe = (T)fm.w;
                     vir = (T)s.mlp_w[i];
                 }
+                if (DPD) dpd_loop<T>(s, P, i, n, xi, dc, L0, L1, L2, fx, fy, fz);
             } else if (FAST) {
                 PairRec<T> pr;
                 pr.rc2 = s.pair[0].rc2;
@@ -283,13 +324,16 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? ESPP_STEP_MINB32 : 4) k
                     pr.eps4 = s.pair[0].eps4;
                     pr.shift = s.pair[0].shift;
                 }
-                pair_loop<T, ENERGY, false, true>(s, P, i, n, xi, ti, &pr, L0, L1, L2, fx, fy, fz, pe, vir);
+                pair_loop<T, ENERGY, false, true, DPD>(s, P, i, n, xi, ti, &pr, L0, L1, L2, fx, fy, fz, pe, vir,
+                                                       &dc);
             } else if (s.ntypes == 1) {
                 const PairRec<T> pr = s.pair[0];
-                if (pr.kind != 0)
-                    pair_loop<T, ENERGY, false, false>(s, P, i, n, xi, ti, &pr, L0, L1, L2, fx, fy, fz, pe, vir);
+                if (pr.kind != 0 || DPD)
+                    pair_loop<T, ENERGY, false, false, DPD>(s, P, i, n, xi, ti, &pr, L0, L1, L2, fx, fy, fz, pe,
+                                                            vir, &dc);
             } else {
-                pair_loop<T, ENERGY, true, false>(s, P, i, n, xi, ti, nullptr, L0, L1, L2, fx, fy, fz, pe, vir);
+                pair_loop<T, ENERGY, true, false, DPD>(s, P, i, n, xi, ti, nullptr, L0, L1, L2, fx, fy, fz, pe,
+                                                       vir, &dc);
             }
             // bonds (paper "Functionality": bonded interactions; FENE or tabulated)
             double blen = 0.0, bcnt = 0.0;
@@ -359,9 +403,7 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? ESPP_STEP_MINB32 : 4) k
                 }
             } else {
                 const T m = ip->mass[ti], inv_m = ip->inv_mass[ti];
-                if (DPD) {
-                    dpd_loop<T>(s, P, i, n, xi, v, L0, L1, L2, g.seed, step, fx, fy, fz);
-                } else if (ip->gamma != T(0)) {
+                if (!DPD && ip->gamma != T(0)) {
                     T rx, ry, rz;
                     langevin_noise<T>(g.seed, bits_as_int(v.w), step, rx, ry, rz);
                     const T amp = ip->noise_amp[ti];
