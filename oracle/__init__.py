@@ -23,9 +23,9 @@ _lib = None
 
 PAIR_STRIDE = 8
 BOND_STRIDE = 4
-NOBS = 12
+NOBS = 13
 OBS_NAMES = ("ke", "pe_pair", "pe_bond", "virial", "px", "py", "pz",
-             "temperature", "pressure", "mean_bond", "rg2", "nmol")
+             "temperature", "pressure", "mean_bond", "rg2", "nmol", "pxz")
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -59,6 +59,8 @@ def lib():
         L.orc_set_dpd.argtypes = [ctypes.c_int, ctypes.c_double]
         L.orc_dpd_theta.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
         L.orc_dpd_theta.restype = ctypes.c_double
+        L.orc_set_lees_edwards.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
+        L.orc_le_get_time.restype = ctypes.c_double
         L.orc_mlp_loss_grad.argtypes = [ctypes.c_int64, _dp, ctypes.c_int64, _dp, _dp, _i32p,
                                         ctypes.c_int64, _i64p, _dp, _dp, _dp]
         L.orc_mlp_loss_grad.restype = ctypes.c_int
@@ -165,6 +167,7 @@ def mlp_pair(r, want_grad=False):
 def mlp_loss_grad(model, box, frames_x, frames_y, types, bonds):
     """Force-matching loss and its parameter gradient (pair potential = the
     registered MLP, bonds as in `model`)."""
+    _le(0.0)
     X = _f64(frames_x)
     Y = _f64(frames_y)
     nf = X.shape[0]
@@ -183,6 +186,21 @@ def mlp_loss_grad(model, box, frames_x, frames_y, types, bonds):
 
 def set_exclude_bonded(on):
     lib().orc_set_exclude_bonded(1 if on else 0)
+
+
+# Lees-Edwards setting of the calls below (flow x, gradient z, shear rate)
+_LE = {"on": False, "shear": 0.0}
+
+
+def set_lees_edwards(on, shear=0.0):
+    """Lees-Edwards boundary conditions for the following calls; the offset
+    is shear * Lz * t with t the State's (or the call's) simulated time."""
+    _LE["on"] = bool(on)
+    _LE["shear"] = float(shear)
+
+
+def _le(time):
+    lib().orc_set_lees_edwards(1 if _LE["on"] else 0, _LE["shear"], float(time))
 
 
 def set_dpd(on, rc=0.0):
@@ -247,15 +265,17 @@ def bond_eval(model: Model, r2: float):
     return u.value, fr.value, rc
 
 
-def forces(model: Model, box, x, types, bonds):
-    """Conservative forces and (PE_pair, PE_bond, virial); raises on a broken bond."""
+def forces(model: Model, box, x, types, bonds, time=0.0):
+    """Conservative forces and (PE_pair, PE_bond, virial, virial_xz); raises
+    on a broken bond.  time: simulated time (Lees-Edwards offset)."""
+    _le(time)
     x = _f64(x, (-1, 3))
     n = x.shape[0]
     L = _f64(box)
     t = np.ascontiguousarray(types, dtype=np.int32)
     b = np.ascontiguousarray(bonds, dtype=np.int64).reshape(-1, 2)
     f = np.zeros((n, 3), dtype=np.float64)
-    en = np.zeros(3, dtype=np.float64)
+    en = np.zeros(4, dtype=np.float64)
     st = lib().orc_forces(n, _p(L, _dp), _p(x, _dp), _p(t, _i32p), model.ntypes,
                           _p(model.pair, _dp), b.shape[0], _p(b, _i64p),
                           _p(model.bond, _dp), _p(f, _dp), _p(en, _dp))
@@ -264,8 +284,9 @@ def forces(model: Model, box, x, types, bonds):
     return f, en
 
 
-def forces_subset(model: Model, box, x, types, bonds, sel):
+def forces_subset(model: Model, box, x, types, bonds, sel, time=0.0):
     """Conservative forces on the particles `sel` only (same definition)."""
+    _le(time)
     x = _f64(x, (-1, 3))
     n = x.shape[0]
     L = _f64(box)
@@ -281,8 +302,9 @@ def forces_subset(model: Model, box, x, types, bonds, sel):
     return f
 
 
-def neighbors(box, x, rcut, method="cells"):
+def neighbors(box, x, rcut, method="cells", time=0.0):
     """Neighbour sets as CSR (row_ptr, cols) in id order."""
+    _le(time)
     x = _f64(x, (-1, 3))
     n = x.shape[0]
     L = _f64(box)
@@ -314,6 +336,7 @@ class State:
         self.f = np.zeros((n, 3), dtype=np.float64)
         self.f_valid = False
         self.step = 0
+        self.time = 0.0  # simulated time (Lees-Edwards offset)
 
     @property
     def n(self):
@@ -322,6 +345,7 @@ class State:
 
 def integrate(model: Model, st: State, nsteps: int, dt: float, gamma: float, kT: float,
               seed: int):
+    _le(st.time)
     rc = lib().orc_integrate(st.n, _p(st.box, _dp), _p(st.x, _dp), _p(st.v, _dp),
                              _p(st.img, _i32p), _p(st.types, _i32p), _p(model.masses, _dp),
                              model.ntypes, _p(model.pair, _dp), st.bonds.shape[0],
@@ -331,10 +355,12 @@ def integrate(model: Model, st: State, nsteps: int, dt: float, gamma: float, kT:
         raise RuntimeError("oracle integrate failed with status %d" % rc)
     st.f_valid = True
     st.step += nsteps
+    st.time = lib().orc_le_get_time()
     return st
 
 
 def observables(model: Model, st: State) -> dict:
+    _le(st.time)
     out = np.zeros(NOBS, dtype=np.float64)
     rc = lib().orc_observables(st.n, _p(st.box, _dp), _p(st.x, _dp), _p(st.v, _dp),
                                _p(st.img, _i32p), _p(st.types, _i32p), _p(model.masses, _dp),
@@ -345,7 +371,8 @@ def observables(model: Model, st: State) -> dict:
     return dict(zip(OBS_NAMES, out.tolist()))
 
 
-def rdf_counts(box, x, rmax, nbins):
+def rdf_counts(box, x, rmax, nbins, time=0.0):
+    _le(time)
     x = _f64(x, (-1, 3))
     L = _f64(box)
     c = np.zeros(nbins, dtype=np.int64)

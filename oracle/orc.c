@@ -91,9 +91,45 @@ void orc_langevin_noise(uint64_t seed, int64_t step, int64_t n, double* out) {
 /* Minimum-image convention: the periodic copy of d nearest to zero. */
 static double min_image(double d, double L) { return d - L * nearbyint(d / L); }
 
-static void min_image_vec(const double* xi, const double* xj, const double* L, double d[3]) {
-    for (int c = 0; c < 3; ++c) d[c] = min_image(xi[c] - xj[c], L[c]);
+/* Lees-Edwards boundary conditions (paper "State of the field" and "New
+ * features": Lees-Edwards; Lees & Edwards 1972).  Reading: steady shear with
+ * the flow along x and the gradient along z at shear rate gdot; the periodic
+ * image of the box at z + k Lz is displaced by k delta along x and moves with
+ * velocity k gdot Lz along x, delta(t) = gdot Lz t (t = simulated time).
+ * The state below is set by the callers (orc_set_lees_edwards). */
+static int orc_le_on = 0;
+static double orc_le_shear = 0.0, orc_le_time = 0.0;
+
+void orc_set_lees_edwards(int on, double shear, double time) {
+    orc_le_on = on ? 1 : 0;
+    orc_le_shear = shear;
+    orc_le_time = time;
 }
+double orc_le_get_time(void) { return orc_le_time; }
+
+static double le_delta(const double* L) { return orc_le_on ? orc_le_shear * L[2] * orc_le_time : 0.0; }
+
+/* Minimum image of x_i - x_j; *nz receives the z image index k of the copy
+ * of j used (x_j + k (delta, 0, Lz)).  Under Lees-Edwards the z image is
+ * chosen first, then x and y as in a plain periodic box. */
+static void min_image_le(const double* xi, const double* xj, const double* L, double d[3], int* nz) {
+    const double dz = xi[2] - xj[2];
+    const double k = nearbyint(dz / L[2]);
+    d[2] = dz - L[2] * k;
+    double dx = xi[0] - xj[0];
+    if (orc_le_on) dx -= k * le_delta(L);
+    d[0] = min_image(dx, L[0]);
+    d[1] = min_image(xi[1] - xj[1], L[1]);
+    if (nz) *nz = (int)k;
+}
+
+static void min_image_vec(const double* xi, const double* xj, const double* L, double d[3]) {
+    min_image_le(xi, xj, L, d, NULL);
+}
+
+/* Streaming velocity of the imposed shear at height z (Lees-Edwards):
+ * gdot (z - Lz/2) along x, so that the images at z +- Lz move at +- gdot Lz. */
+static double le_stream(double z, const double* L) { return orc_le_on ? orc_le_shear * (z - 0.5 * L[2]) : 0.0; }
 
 /* ------------------------------------------------------------------------ */
 /* Potentials                                                                */
@@ -448,21 +484,27 @@ static int64_t cells_candidates(const cells_t* cl, int64_t n, int64_t i, int64_t
     int64_t cx = c % cl->nc[0];
     int64_t cy = (c / cl->nc[0]) % cl->nc[1];
     int64_t cz = c / ((int64_t)cl->nc[0] * cl->nc[1]);
-    for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                int64_t ax = (cx + dx + cl->nc[0]) % cl->nc[0];
+    for (int dz = -1; dz <= 1; ++dz) {
+        /* under Lees-Edwards the rows across the z faces are displaced along
+         * x by the shear offset: take the whole x row there */
+        const int across = orc_le_on && (cz + dz < 0 || cz + dz >= cl->nc[2]);
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int x0 = across ? 0 : -1, x1 = across ? cl->nc[0] - 1 : 1;
+            for (int dx = x0; dx <= x1; ++dx) {
+                int64_t ax = across ? dx : (cx + dx + cl->nc[0]) % cl->nc[0];
                 int64_t ay = (cy + dy + cl->nc[1]) % cl->nc[1];
                 int64_t az = (cz + dz + cl->nc[2]) % cl->nc[2];
                 int64_t a = (az * cl->nc[1] + ay) * cl->nc[0] + ax;
                 for (int64_t j = cl->head[a]; j >= 0; j = cl->next[j])
                     if (j != i) buf[m++] = j;
             }
+        }
+    }
     return m;
 }
 
 static int64_t max_candidates(const cells_t* cl, int64_t n) {
-    if (cl->brute) return n;
+    if (cl->brute || orc_le_on) return n;
     int64_t ncell = (int64_t)cl->nc[0] * cl->nc[1] * cl->nc[2];
     int64_t* cnt = (int64_t*)calloc((size_t)ncell, sizeof(int64_t));
     for (int64_t i = 0; i < n; ++i) cnt[cl->cell_of[i]]++;
@@ -583,8 +625,9 @@ static int bonded_to(const adj_t* a, int64_t i, int64_t j) {
  * plus the sum over bonds (i, p) of the bond force.  There are no exclusions:
  * bonded beads also interact through the pair potential (Kremer-Grest).
  * PE_pair = sum over unordered pairs of u, PE_bond = sum over bonds of u,
- * virial = sum over unordered pairs and bonds of r_ij . F_ij.  Each particle
- * accumulates its own sum (both orders of every pair are evaluated). */
+ * virial = sum over unordered pairs and bonds of r_ij . F_ij, and its xz
+ * component W_xz = sum of (r_ij)_x (F_ij)_z.  Each particle accumulates its
+ * own sum (both orders of every pair are evaluated). */
 int orc_forces(int64_t n, const double* L, const double* x, const int32_t* type,
                int ntypes, const double* pair_params, int64_t nbonds,
                const int64_t* bonds, const double* bond_params, double* f,
@@ -601,6 +644,7 @@ int orc_forces(int64_t n, const double* L, const double* x, const int32_t* type,
     double* pe_p = (double*)calloc((size_t)n + 1, sizeof(double));
     double* pe_b = (double*)calloc((size_t)n + 1, sizeof(double));
     double* vir = (double*)calloc((size_t)n + 1, sizeof(double));
+    double* vxz = (double*)calloc((size_t)n + 1, sizeof(double));
     int64_t mc = max_candidates(&cl, n);
     int broken = 0;
 
@@ -610,7 +654,7 @@ int orc_forces(int64_t n, const double* L, const double* x, const int32_t* type,
 #pragma omp for schedule(static)
         for (int64_t i = 0; i < n; ++i) {
             double fi[3] = {0.0, 0.0, 0.0};
-            double ui = 0.0, ub = 0.0, wi = 0.0;
+            double ui = 0.0, ub = 0.0, wi = 0.0, wxz = 0.0;
             if (rmax > 0.0) {
                 int64_t nc = cells_candidates(&cl, n, i, buf);
                 for (int64_t k = 0; k < nc; ++k) {
@@ -625,6 +669,7 @@ int orc_forces(int64_t n, const double* L, const double* x, const int32_t* type,
                     for (int c = 0; c < 3; ++c) fi[c] += fr * d[c];
                     ui += 0.5 * u;
                     wi += 0.5 * fr * r2;
+                    wxz += 0.5 * fr * d[0] * d[2];
                 }
             }
             for (int64_t k = adj.off[i]; k < adj.off[i + 1]; ++k) {
@@ -637,28 +682,33 @@ int orc_forces(int64_t n, const double* L, const double* x, const int32_t* type,
                 for (int c = 0; c < 3; ++c) fi[c] += fr * d[c];
                 ub += 0.5 * u;
                 wi += 0.5 * fr * r2;
+                wxz += 0.5 * fr * d[0] * d[2];
             }
             for (int c = 0; c < 3; ++c) f[3 * i + c] = fi[c];
             pe_p[i] = ui;
             pe_b[i] = ub;
             vir[i] = wi;
+            vxz[i] = wxz;
         }
         free(buf);
     }
-    double sp = 0.0, sb = 0.0, sw = 0.0;
+    double sp = 0.0, sb = 0.0, sw = 0.0, sxz = 0.0;
     for (int64_t i = 0; i < n; ++i) {
         sp += pe_p[i];
         sb += pe_b[i];
         sw += vir[i];
+        sxz += vxz[i];
     }
     if (energies) {
         energies[0] = sp;
         energies[1] = sb;
         energies[2] = sw;
+        energies[3] = sxz;
     }
     free(pe_p);
     free(pe_b);
     free(vir);
+    free(vxz);
     adj_free(&adj);
     cells_free(&cl);
     return broken ? -4 : 0;
@@ -743,7 +793,7 @@ int orc_mlp_loss_grad(int64_t n, const double* L, int64_t nframes, const double*
     for (int64_t fr = 0; fr < nframes; ++fr) {
         const double* x = X + 3 * n * fr;
         const double* y = Y + 3 * n * fr;
-        double en[3];
+        double en[4];
         int st = orc_forces(n, L, x, type, 1, pp, nbonds, bonds, bond_params, f, en);
         if (st) {
             free(f);
@@ -795,13 +845,39 @@ static void wrap_coord(double* xc, int32_t* im, double L) {
     }
 }
 
+/* Wrap under Lees-Edwards: crossing a z face by k boxes moves the particle
+ * to the image it entered, displaced by -k delta along x and slower by
+ * k gdot Lz along x; x and y are then wrapped as usual (x may need several
+ * boxes).  The unwrapped position x + img_x Lx + img_z delta(t) is continuous
+ * in time (delta the offset without reduction). */
+static void le_wrap(double* xi, double* vi, int32_t* im, const double* L, double delta) {
+    const int32_t z0 = im[2];
+    wrap_coord(&xi[2], &im[2], L[2]);
+    const int kz = im[2] - z0;
+    if (kz != 0) {
+        xi[0] -= kz * delta;
+        vi[0] -= kz * orc_le_shear * L[2];
+        double k = floor(xi[0] / L[0]);
+        xi[0] -= k * L[0];
+        if (xi[0] >= L[0]) {
+            xi[0] -= L[0];
+            k += 1.0;
+        }
+        if (xi[0] < 0.0) xi[0] = 0.0;
+        im[0] += (int32_t)k;
+    } else {
+        wrap_coord(&xi[0], &im[0], L[0]);
+    }
+    wrap_coord(&xi[1], &im[1], L[1]);
+}
+
 /* Langevin force (added to the conservative force in the force step):
  * -gamma m v + sqrt(24 gamma m kT / dt) r, r from the Philox stream.
  * Reading (discretisation; the paper names only gamma and T): the friction
  * uses the velocity present when the force is evaluated (the half-step
  * velocity inside a step) and the uniform noise has the variance
  * 2 gamma m kT / dt of the continuous white noise over one step. */
-static void add_langevin(int64_t n, const double* v, const int32_t* type,
+static void add_langevin(int64_t n, const double* L, const double* x, const double* v, const int32_t* type,
                          const double* mass_of_type, double* f, double dt, double gamma,
                          double kT, uint64_t seed, int64_t step) {
     if (gamma == 0.0) return;
@@ -811,7 +887,10 @@ static void add_langevin(int64_t n, const double* v, const int32_t* type,
         double amp = sqrt(24.0 * gamma * m * kT / dt);
         double r[3];
         langevin_r(seed, i, step, r);
-        for (int c = 0; c < 3; ++c) f[3 * i + c] += -gamma * m * v[3 * i + c] + amp * r[c];
+        /* under Lees-Edwards the friction acts on the velocity relative to
+         * the imposed streaming profile (reading) */
+        double vp[3] = {v[3 * i + 0] - le_stream(x[3 * i + 2], L), v[3 * i + 1], v[3 * i + 2]};
+        for (int c = 0; c < 3; ++c) f[3 * i + c] += -gamma * m * vp[c] + amp * r[c];
     }
 }
 
@@ -825,7 +904,9 @@ static void add_langevin(int64_t n, const double* v, const int32_t* type,
  * centred uniform of word 0 of Philox4x32-10 with key (seed lo, seed hi) and
  * counter (min id, max id | 2^31, step lo, step hi), so theta_ij = theta_ji
  * and the pair forces cancel exactly; the velocity is the one present at the
- * force evaluation (as for the Langevin friction). */
+ * force evaluation (as for the Langevin friction).  Under Lees-Edwards the
+ * image of j across the z faces moves at k gdot Lz along x: v_ij is taken
+ * against that image's velocity. */
 static int orc_dpd_on = 0;
 static double orc_dpd_rc = 0.0;
 void orc_set_dpd(int on, double rc) {
@@ -853,12 +934,16 @@ static void add_dpd(int64_t n, const double* L, const double* x, const double* v
         for (int64_t j = 0; j < n; ++j) {
             if (j == i) continue;
             double d[3];
-            min_image_vec(x + 3 * i, x + 3 * j, L, d);
+            int nz;
+            min_image_le(x + 3 * i, x + 3 * j, L, d, &nz);
             const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
             if (!(r2 < rc * rc)) continue;
             const double r = sqrt(r2), w = 1.0 - r / rc;
+            double vij[3];
+            for (int c = 0; c < 3; ++c) vij[c] = v[3 * i + c] - v[3 * j + c];
+            if (orc_le_on) vij[0] -= nz * orc_le_shear * L[2];
             double ev = 0.0;
-            for (int c = 0; c < 3; ++c) ev += d[c] / r * (v[3 * i + c] - v[3 * j + c]);
+            for (int c = 0; c < 3; ++c) ev += d[c] / r * vij[c];
             const double mag = -gamma * w * w * ev + sigma * w * orc_dpd_theta(seed, i, j, step) * inv_sqdt;
             for (int c = 0; c < 3; ++c) fi[c] += mag * d[c] / r;
         }
@@ -871,7 +956,7 @@ static void add_thermostat(int64_t n, const double* L, const double* x, const do
                            const double* mass_of_type, double* f, double dt, double gamma, double kT,
                            uint64_t seed, int64_t step) {
     if (orc_dpd_on) add_dpd(n, L, x, v, f, dt, gamma, kT, seed, step);
-    else add_langevin(n, v, type, mass_of_type, f, dt, gamma, kT, seed, step);
+    else add_langevin(n, L, x, v, type, mass_of_type, f, dt, gamma, kT, seed, step);
 }
 
 /* Velocity Verlet (the example's VelocityVerlet) with the Langevin extension.
@@ -888,21 +973,28 @@ int orc_integrate(int64_t n, const double* L, double* x, double* v, int32_t* img
                   const double* pair_params, int64_t nbonds, const int64_t* bonds,
                   const double* bond_params, double* f, int f_valid, double dt,
                   double gamma, double kT, uint64_t seed, int64_t step0, int64_t nsteps) {
-    double en[3];
+    double en[4];
     int st = 0;
+    const double t0 = orc_le_time;  /* simulated time of step0 (Lees-Edwards offset) */
     if (!f_valid) {
         st = orc_forces(n, L, x, type, ntypes, pair_params, nbonds, bonds, bond_params, f, en);
         if (st) return st;
         add_thermostat(n, L, x, v, type, mass_of_type, f, dt, gamma, kT, seed, step0);
     }
     for (int64_t s = step0 + 1; s <= step0 + nsteps; ++s) {
+        orc_le_time = t0 + (double)(s - step0) * dt;
+        const double delta = le_delta(L);
 #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; ++i) {
             double m = mass_of_type[type[i]];
             for (int c = 0; c < 3; ++c) {
                 v[3 * i + c] += 0.5 * dt * f[3 * i + c] / m;
                 x[3 * i + c] += dt * v[3 * i + c];
-                wrap_coord(&x[3 * i + c], &img[3 * i + c], L[c]);
+            }
+            if (orc_le_on) {
+                le_wrap(x + 3 * i, v + 3 * i, img + 3 * i, L, delta);
+            } else {
+                for (int c = 0; c < 3; ++c) wrap_coord(&x[3 * i + c], &img[3 * i + c], L[c]);
             }
         }
         st = orc_forces(n, L, x, type, ntypes, pair_params, nbonds, bonds, bond_params, f, en);
@@ -935,23 +1027,31 @@ static int64_t uf_find(int64_t* parent, int64_t a) {
  * removes degrees of freedom); out[8] P = (2 KE + W) / (3 V);
  * out[9] mean bond length; out[10] mean squared radius of gyration over
  * molecules (connected components of the bond graph with >= 2 beads, from
- * unwrapped positions x + img L); out[11] number of such molecules. */
+ * unwrapped positions x + img L); out[11] number of such molecules;
+ * out[12] the xz component of the pressure tensor,
+ * P_xz = (sum m v_x v_z + W_xz) / V.  Under Lees-Edwards the kinetic terms
+ * (KE, T, P, P_xz) use the velocity relative to the streaming profile and
+ * the unwrapped x adds img_z delta(t). */
 int orc_observables(int64_t n, const double* L, const double* x, const double* v,
                     const int32_t* img, const int32_t* type, const double* mass_of_type,
                     int ntypes, const double* pair_params, int64_t nbonds,
                     const int64_t* bonds, const double* bond_params, double* out) {
     for (int k = 0; k < ORC_NOBS; ++k) out[k] = 0.0;
     double* f = (double*)malloc(sizeof(double) * (size_t)(3 * n + 1));
-    double en[3];
+    double en[4];
     int st = orc_forces(n, L, x, type, ntypes, pair_params, nbonds, bonds, bond_params, f, en);
     free(f);
-    double ke = 0.0, p[3] = {0, 0, 0};
+    double ke = 0.0, p[3] = {0, 0, 0}, kxz = 0.0;
     for (int64_t i = 0; i < n; ++i) {
         double m = mass_of_type[type[i]];
+        /* kinetic terms from the velocity relative to the Lees-Edwards
+         * streaming profile (the velocity itself without shear) */
+        const double vp[3] = {v[3 * i + 0] - le_stream(x[3 * i + 2], L), v[3 * i + 1], v[3 * i + 2]};
         for (int c = 0; c < 3; ++c) {
-            ke += 0.5 * m * v[3 * i + c] * v[3 * i + c];
+            ke += 0.5 * m * vp[c] * vp[c];
             p[c] += m * v[3 * i + c];
         }
+        kxz += m * vp[0] * vp[2];
     }
     double V = L[0] * L[1] * L[2];
     out[0] = ke;
@@ -963,6 +1063,7 @@ int orc_observables(int64_t n, const double* L, const double* x, const double* v
     out[6] = p[2];
     out[7] = n > 0 ? 2.0 * ke / (3.0 * (double)n) : 0.0;
     out[8] = (2.0 * ke + en[2]) / (3.0 * V);
+    out[12] = (kxz + en[3]) / V;
     double bl = 0.0;
     for (int64_t b = 0; b < nbonds; ++b) {
         double d[3];
@@ -984,6 +1085,7 @@ int orc_observables(int64_t n, const double* L, const double* x, const double* v
         int64_t r = uf_find(parent, i);
         cnt[r]++;
         for (int c = 0; c < 3; ++c) com[3 * r + c] += x[3 * i + c] + img[3 * i + c] * L[c];
+        com[3 * r + 0] += img[3 * i + 2] * le_delta(L);
     }
     for (int64_t r = 0; r < n; ++r)
         if (cnt[r] > 0)
@@ -992,6 +1094,7 @@ int orc_observables(int64_t n, const double* L, const double* x, const double* v
         int64_t r = uf_find(parent, i);
         for (int c = 0; c < 3; ++c) {
             double u = x[3 * i + c] + img[3 * i + c] * L[c] - com[3 * r + c];
+            if (c == 0) u += img[3 * i + 2] * le_delta(L);
             rg[r] += u * u;
         }
     }

@@ -27,7 +27,7 @@
 
 #define ORC_PAIR_STRIDE 8
 #define ORC_BOND_STRIDE 4
-#define ORC_NOBS 12
+#define ORC_NOBS 13
 
 #ifdef __cplusplus
 extern "C" {
@@ -64,6 +64,12 @@ int orc_mlp_loss_grad(int64_t n, const double* L, int64_t nframes, const double*
                       const int32_t* type, int64_t nbonds, const int64_t* bonds,
                       const double* bond_params, double* loss_out, double* grad);
 
+/* Lees-Edwards boundary conditions: shear rate along x with the gradient
+ * along z, and the simulated time t of the state (offset gdot Lz t).  The
+ * time advances with orc_integrate; orc_le_get_time reads it back. */
+void orc_set_lees_edwards(int on, double shear, double time);
+double orc_le_get_time(void);
+
 /* Exclude 1-2 bonded pairs from the pair interactions (default off). */
 void orc_set_exclude_bonded(int on);
 
@@ -73,7 +79,7 @@ void orc_pair_eval(const double* pp, double r2, double* u, double* fr);
 int orc_bond_eval(const double* bp, double r2, double* u, double* fr);
 
 /* Conservative forces.  energies[0]=PE_pair, [1]=PE_bond, [2]=virial
- * (sum over pairs and bonds of r_ij . F_ij).  Returns 0, or -4 if a FENE
+ * (sum over pairs and bonds of r_ij . F_ij), [3]=its xz component.  Returns 0, or -4 if a FENE
  * bond is stretched to r >= R0. */
 int orc_forces(int64_t n, const double* L, const double* x, const int32_t* type,
                int ntypes, const double* pair_params, int64_t nbonds,

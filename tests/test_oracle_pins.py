@@ -681,3 +681,167 @@ def test_dpd_equipartition(dpd_on):
         O.integrate(FREE, st, 10, 0.01, 4.5, kT, seed=11)
         t.append((st.v ** 2).sum() / (3 * (st.n - 1)))
     assert abs(np.mean(t) - kT) < 0.03 * kT, np.mean(t)
+
+
+# --------------------------------------------------------------------------
+# Lees-Edwards boundary conditions (paper "State of the field" and "New
+# features"): flow along x, gradient along z, offset delta = gdot Lz t
+# --------------------------------------------------------------------------
+@pytest.fixture
+def le_on():
+    def on(shear):
+        O.set_lees_edwards(True, shear)
+    yield on
+    O.set_lees_edwards(False)
+    O.set_dpd(False)
+
+
+def _le_images(box, delta, xi, xj, na=3):
+    """Displacements x_i - image(x_j) over the explicit sheared images."""
+    delta = delta % box[0]  # the same set of images, a few boxes to enumerate
+    out = []
+    for b in (-1, 0, 1):
+        for a in range(-na, na + 1):
+            for c in (-1, 0, 1):
+                img = np.array([a * box[0] + b * delta, c * box[1], b * box[2]])
+                out.append(xi - (xj + img))
+    return np.array(out)
+
+
+def test_le_neighbours_match_image_enumeration(le_on):
+    box = np.array([8.0, 9.0, 10.0])
+    shear, t = 0.37, 5.3
+    delta = shear * box[2] * t  # several box lengths along x
+    le_on(shear)
+    c = I.random_positions(500, box, seed=12)
+    rcut = 1.5
+    row, cols = O.neighbors(box, c.x, rcut, time=t)
+    got = set()
+    for i in range(c.n):
+        for j in cols[row[i]:row[i + 1]]:
+            got.add((i, int(j)))
+    want = set()
+    for i in range(c.n):
+        d = c.x[i] - c.x  # (n, 3) plain differences
+        best = np.full(c.n, np.inf)
+        for b in (-1, 0, 1):
+            for a in range(-4, 5):
+                for cc in (-1, 0, 1):
+                    img = np.array([a * box[0] + b * delta, cc * box[1], b * box[2]])
+                    best = np.minimum(best, ((d - img) ** 2).sum(axis=1))
+        for j in np.nonzero(best < rcut * rcut)[0]:
+            if j != i:
+                want.add((i, int(j)))
+    assert got == want and len(want) > 500
+    # with the shear off the same positions give the plain periodic sets
+    O.set_lees_edwards(False)
+    row0, cols0 = O.neighbors(box, c.x, rcut)
+    assert {(i, int(j)) for i in range(c.n) for j in cols0[row0[i]:row0[i + 1]]} != want
+
+
+def test_le_ballistic_motion(le_on):
+    # no forces, no thermostat: seen from the image frame a particle came
+    # from, its velocity never changes (each crossing of a sheared face takes
+    # gdot Lz off v_x per box), and the unwrapped position
+    # x + img_x Lx + img_z delta(t) moves on a straight line
+    shear, dt, nsteps = 0.5, 0.01, 1500
+    le_on(shear)
+    box = np.array([6.0, 6.0, 6.0])
+    c = I.random_positions(300, box, seed=3)
+    v = I.maxwell_velocities(300, 1.0, seed=3)
+    st = O.State(box, c.x, v)
+
+    def frame_velocity(s):
+        p = s.v.copy()
+        p[:, 0] += s.img[:, 2] * shear * box[2]
+        return p
+
+    def unwrapped(s):
+        u = s.x + s.img * box
+        u[:, 0] += s.img[:, 2] * shear * box[2] * s.time
+        return u
+
+    u0 = unwrapped(st)
+    O.integrate(FREE, st, nsteps, dt, 0.0, 0.0, seed=1)
+    assert abs(st.time - nsteps * dt) < 1e-12
+    assert np.abs(st.img[:, 2]).max() >= 2  # particles crossed the sheared faces
+    assert np.abs(frame_velocity(st) - v).max() < 1e-11
+    assert np.array_equal(st.v[:, 1:], v[:, 1:])
+    # each particle moves with its initial velocity seen from its own image frame
+    assert np.abs(unwrapped(st) - (u0 + v * nsteps * dt)).max() < 1e-9
+
+
+def _dpd_shear_run(shear, nsteps, seed=5, box=(5.0, 5.0, 6.0), gamma=4.5):
+    box = np.array(box)
+    n = int(3.0 * box.prod())
+    c = I.random_positions(n, box, seed=seed)
+    v = I.maxwell_velocities(n, 1.0, seed=seed)
+    v[:, 0] += shear * (c.x[:, 2] - box[2] / 2)  # start on the linear profile
+    st = O.State(box, c.x, v)
+    O.set_dpd(True, 1.0)
+    prof, pxz, temp = [], [], []
+    for _ in range(nsteps // 20):
+        O.integrate(FREE, st, 20, 0.01, gamma, 1.0, seed=seed)
+        o = O.observables(FREE, st)
+        pxz.append(o["pxz"])
+        temp.append(o["temperature"])
+        prof.append(np.polyfit(st.x[:, 2] - box[2] / 2, st.v[:, 0], 1)[0])
+    return np.array(prof), np.array(pxz), np.array(temp)
+
+
+def test_le_dpd_keeps_the_linear_profile(le_on):
+    # a DPD fluid sheared through the boundaries keeps the imposed linear
+    # velocity profile, stays at the bath temperature (relative to the
+    # profile) and carries a negative xz pressure (momentum flows down the
+    # gradient)
+    shear = 0.5
+    le_on(shear)
+    prof, pxz, temp = _dpd_shear_run(shear, 2000)
+    assert abs(prof[len(prof) // 2:].mean() - shear) < 0.1 * shear, prof
+    assert abs(temp[len(temp) // 2:].mean() - 1.0) < 0.05, temp.mean()
+    assert pxz.mean() < -3 * pxz.std() / math.sqrt(pxz.size), (pxz.mean(), pxz.std())
+    # without the sheared boundary the same start relaxes the profile away
+    O.set_lees_edwards(False)
+    prof0, _, _ = _dpd_shear_run(shear, 2000)
+    assert prof0[-10:].mean() < 0.5 * shear
+
+
+def test_le_langevin_relative_to_profile(le_on):
+    # an ideal gas under the profile-biased Langevin thermostat follows the
+    # streaming profile, with the bath temperature relative to it
+    shear = 0.5
+    le_on(shear)
+    box = np.array([6.0, 6.0, 6.0])
+    c = I.random_positions(2000, box, seed=8)
+    st = O.State(box, c.x, I.maxwell_velocities(2000, 1.0, seed=8))
+    O.integrate(FREE, st, 600, 0.01, 2.0, 1.0, seed=8)
+    slopes, temps = [], []
+    for _ in range(20):
+        O.integrate(FREE, st, 10, 0.01, 2.0, 1.0, seed=8)
+        slopes.append(np.polyfit(st.x[:, 2] - box[2] / 2, st.v[:, 0], 1)[0])
+        temps.append(O.observables(FREE, st)["temperature"])
+    assert abs(np.mean(slopes) - shear) < 0.1 * shear
+    assert abs(np.mean(temps) - 1.0) < 0.03
+
+
+def test_le_rg2_of_a_chain_across_the_sheared_face(le_on):
+    # radius of gyration from the unwrapped positions equals the one built by
+    # walking the bonds with the sheared minimum image
+    shear = 0.8
+    le_on(shear)
+    c = I.kg_lattice(6, 30, seed=4, jitter=0.05)
+    st = O.State(c.box, c.x, I.maxwell_velocities(c.n, 1.0, seed=4), c.img, c.types, c.bonds)
+    O.integrate(KG, st, 3000, 0.005, 1.0, 1.0, seed=4)
+    assert np.abs(st.img[:, 2]).max() >= 1
+    delta = shear * c.box[2] * st.time
+    rg = []
+    for m in range(6):
+        ids = np.arange(30 * m, 30 * m + 30)
+        pos = [st.x[ids[0]]]
+        for a, b in zip(ids[:-1], ids[1:]):
+            d = _le_images(c.box, delta, st.x[b], st.x[a])
+            pos.append(pos[-1] + d[np.argmin((d ** 2).sum(axis=1))])
+        pos = np.array(pos)
+        rg.append(((pos - pos.mean(axis=0)) ** 2).sum(axis=1).mean())
+    o = O.observables(KG, st)
+    assert abs(o["rg2"] - np.mean(rg)) < 1e-9 * np.mean(rg)
