@@ -89,7 +89,11 @@ typedef struct {
  * pressure = (2 ke + virial) / (3 V); virial = sum over pairs and bonds of
  * r_ij . F_ij; mean_bond over bonds; rg2 = mean over molecules (connected
  * components of the bond graph with >= 2 beads) of the squared radius of
- * gyration of the unwrapped positions. */
+ * gyration of the unwrapped positions; pxz = (sum m v_x v_z + sum over pairs
+ * and bonds of (r_ij)_x (F_ij)_z) / V, the xz component of the pressure
+ * tensor.  Under Lees-Edwards (espp_set_lees_edwards) ke, temperature,
+ * pressure and pxz use the velocity relative to the shear profile and the
+ * unwrapped x adds img_z delta(t). */
 typedef struct {
     int64_t step;
     int64_t n;
@@ -101,6 +105,7 @@ typedef struct {
     int64_t n_rebuilds;
     uint32_t error_word;
     uint32_t reserved;
+    double pxz;
 } espp_obs_t;
 
 /* ---- creation ------------------------------------------------------------ */
@@ -251,6 +256,27 @@ int espp_compute_forces(espp_h h, double* f_out, int where);
 #define ESPP_THERMO_LANGEVIN 0
 #define ESPP_THERMO_DPD 1
 int espp_set_thermostat(espp_h h, int32_t kind, double rc);
+
+/* Lees-Edwards boundary conditions (paper "State of the field" and "New
+ * features": Lees-Edwards): steady shear with the flow along x and the
+ * gradient along z at shear rate gdot (shear_rate).  The periodic image of a
+ * replica's box at z + k Lz is displaced by k delta(t) along x and moves at
+ * k gdot Lz along x, delta(t) = gdot Lz t, where t is the simulated time of
+ * the handle (`time` sets t at the current step; every integrate step adds
+ * its dt).  A particle crossing a z face by k boxes is moved by -k delta
+ * along x and its v_x by -k gdot Lz; image counters count the wraps, so
+ * x + img_x Lx + img_z delta(t) is the continuous unwrapped x.  Pair and bond
+ * vectors take the sheared minimum image; the Langevin friction acts on
+ * v - gdot (z - Lz/2) x; DPD relative velocities include the image velocity.
+ * on = 0 restores the plain periodic box (time is kept).  Positions given to
+ * espp_set_state must lie inside the box along z.  The list is rebuilt on
+ * the next call; the change of delta since a build counts against the skin.
+ * Errors: ESPP_ERR_ARG (non-finite values), ESPP_ERR_STATE (with the learned
+ * potential or the CG mapping, which are not available under shear). */
+int espp_set_lees_edwards(espp_h h, int32_t on, double shear_rate, double time);
+/* Current setting and simulated time t of the handle (any pointer may be
+ * NULL). */
+int espp_get_lees_edwards(espp_h h, int32_t* on, double* shear_rate, double* time);
 
 /* Paper "Example usage": VelocityVerlet + LangevinThermostat(gamma,
  * temperature) and integrator.run(nsteps).  Each step: v += dt/2 F/m;

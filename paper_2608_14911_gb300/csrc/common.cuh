@@ -209,6 +209,10 @@ struct Ctrl {
     unsigned int need_cap;     // largest neighbour count seen by an overflowing build
     unsigned int n_rebuilds;   // rebuild passes executed (any replica)
     unsigned int max_count;    // largest neighbour count of the last build
+    unsigned int pos_ahead;    // 1 while the stored positions are those of step + 1
+                               // (inside an integrate call, after the first drift)
+    unsigned int le_keep;      // the next rebuild keeps the stored Lees-Edwards build
+                               // offsets (a checkpoint load), then clears this
     unsigned int pad;
 };
 

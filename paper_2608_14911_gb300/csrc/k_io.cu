@@ -66,14 +66,24 @@ __global__ void __launch_bounds__(TILE) k_get_state(DevSys<T> s, double* __restr
         const double pc[3] = {(double)p.x, (double)p.y, (double)p.z};
         double wc[3];
         int sh[3];
-        for (int d = 0; d < 3; ++d) {
-            const double L = (double)g.L[d];
-            double w = pc[d];
-            int k = 0;
-            if (w >= L) { w -= L; k = 1; }
-            else if (w < 0.0) { w += L; k = -1; if (w >= L) w = 0.0; }
-            wc[d] = w;
-            sh[d] = k;
+        double vx = (double)vv.x;
+        if (s.le_on) {
+            // Lees-Edwards: a crossing of a sheared face also moves x and v_x
+            const double L[3] = {(double)g.L[0], (double)g.L[1], (double)g.L[2]};
+            wc[0] = pc[0];
+            wc[1] = pc[1];
+            wc[2] = pc[2];
+            le_wrap(wc, vx, sh, L, le_offset(s, g, s.ctrl->step + (long long)s.ctrl->pos_ahead), s.le_shear);
+        } else {
+            for (int d = 0; d < 3; ++d) {
+                const double L = (double)g.L[d];
+                double w = pc[d];
+                int k = 0;
+                if (w >= L) { w -= L; k = 1; }
+                else if (w < 0.0) { w += L; k = -1; if (w >= L) w = 0.0; }
+                wc[d] = w;
+                sh[d] = k;
+            }
         }
         if (x) {
             x[3 * gid] = wc[0];
@@ -81,7 +91,7 @@ __global__ void __launch_bounds__(TILE) k_get_state(DevSys<T> s, double* __restr
             x[3 * gid + 2] = wc[2];
         }
         if (v) {
-            v[3 * gid] = vv.x;
+            v[3 * gid] = vx;
             v[3 * gid + 1] = vv.y;
             v[3 * gid + 2] = vv.z;
         }
@@ -125,12 +135,14 @@ __global__ void k_rg2(DevSys<T> s, int cur, const int* __restrict__ members,
     if (m >= nmol) return;
     const RepGeom<T>& g = s.reps[mrep[m]];
     const int b = off[m], e = off[m + 1];
+    // Lees-Edwards: the unwrapped x adds img_z delta(t) (delta not reduced)
+    const double dle = s.le_on ? le_offset(s, g, s.ctrl->step + (long long)s.ctrl->pos_ahead) : 0.0;
     double c[3] = {0.0, 0.0, 0.0};
     for (int k = b + lane; k < e; k += 32) {
         const int slot = s.slot_of_id[members[k]];
         const V4<T> p = s.pos[cur][slot];
         const int4 im = s.img[slot];
-        c[0] += (double)p.x + (double)im.x * (double)g.L[0];
+        c[0] += (double)p.x + (double)im.x * (double)g.L[0] + (double)im.z * dle;
         c[1] += (double)p.y + (double)im.y * (double)g.L[1];
         c[2] += (double)p.z + (double)im.z * (double)g.L[2];
     }
@@ -143,7 +155,7 @@ __global__ void k_rg2(DevSys<T> s, int cur, const int* __restrict__ members,
         const int slot = s.slot_of_id[members[k]];
         const V4<T> p = s.pos[cur][slot];
         const int4 im = s.img[slot];
-        const double ux = (double)p.x + (double)im.x * (double)g.L[0] - c[0];
+        const double ux = (double)p.x + (double)im.x * (double)g.L[0] + (double)im.z * dle - c[0];
         const double uy = (double)p.y + (double)im.y * (double)g.L[1] - c[1];
         const double uz = (double)p.z + (double)im.z * (double)g.L[2] - c[2];
         a += ux * ux + uy * uy + uz * uz;
@@ -163,12 +175,18 @@ __global__ void __launch_bounds__(256) k_rdf(DevSys<T> s, int cur, int rep, T rm
     const RepGeom<T>& g = s.reps[rep];
     const V4<T>* __restrict__ P = s.pos[cur];
     const int n = g.n;
+    const T dle = s.le_on ? (T)le_reduce(le_offset(s, g, s.ctrl->step + (long long)s.ctrl->pos_ahead),
+                                         (double)g.L[0])
+                          : T(0);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
       for (int j = i + 1; j < n; ++j) {
         const V4<T> a = P[g.p_off + i], c = P[g.p_off + j];
-        const T dx = min_image(a.x, c.x, g.L[0], g.halfL[0]);
-        const T dy = min_image(a.y, c.y, g.L[1], g.halfL[1]);
         const T dz = min_image(a.z, c.z, g.L[2], g.halfL[2]);
+        const T dy = min_image(a.y, c.y, g.L[1], g.halfL[1]);
+        const T zr = a.z - c.z;
+        const T dx = (s.le_on && (zr > g.halfL[2] || zr < -g.halfL[2]))
+                         ? le_dx(a.x, c.x, zr > g.halfL[2] ? 1 : -1, dle, g.L[0], T(1) / g.L[0])
+                         : min_image(a.x, c.x, g.L[0], g.halfL[0]);
         const T r2 = dx * dx + dy * dy + dz * dz;
         if (r2 < rmax2) {
             int b = (int)(sqrt((double)r2) * inv_dr);
@@ -192,6 +210,9 @@ __global__ void __launch_bounds__(256) k_rdf_list(DevSys<T> s, int cur, int rep,
     const RepGeom<T>& g = s.reps[rep];
     const V4<T>* __restrict__ P = s.pos[cur];
     const size_t stride = (size_t)s.stride;
+    const T dle = s.le_on ? (T)le_reduce(le_offset(s, g, s.ctrl->step + (long long)s.ctrl->pos_ahead),
+                                         (double)g.L[0])
+                          : T(0);
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < g.n; q += gridDim.x * blockDim.x) {
         const int i = g.p_off + q;
         const V4<T> xi = P[i];
@@ -202,7 +223,8 @@ __global__ void __launch_bounds__(256) k_rdf_list(DevSys<T> s, int cur, int rep,
             if (j < i) continue;
             const V4<T> xj = P[j];
             const int code = nbr_code(e);
-            const T dx = shifted_diff(xi.x, xi.x - g.L[0], xj.x, g.L[0], code & 3);
+            const T dx = (code & 3) == 3 ? le_dx(xi.x, xj.x, (code >> 4) == 1 ? 1 : -1, dle, g.L[0], T(1) / g.L[0])
+                                         : shifted_diff(xi.x, xi.x - g.L[0], xj.x, g.L[0], code & 3);
             const T dy = shifted_diff(xi.y, xi.y - g.L[1], xj.y, g.L[1], (code >> 2) & 3);
             const T dz = shifted_diff(xi.z, xi.z - g.L[2], xj.z, g.L[2], code >> 4);
             const T r2 = dx * dx + dy * dy + dz * dz;

@@ -52,7 +52,17 @@ __global__ void __launch_bounds__(256) k_prep(DevSys<T> s) {
     for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < s.ncells; h += gridDim.x * blockDim.x)
         if (s.req[s.cell_rep[h]]) s.cell_cnt[h] = 0;
     if (blockIdx.x == 0) {
-        for (int r = threadIdx.x; r < s.R; r += blockDim.x) s.now[r] = s.req[r];
+        // Lees-Edwards: the offset at this build, for the rebuild criterion
+        // and the sheared rows of the search (kept as stored after a
+        // checkpoint load)
+        const long long pstep = s.ctrl->step + (long long)s.ctrl->pos_ahead;
+        const bool keep = s.ctrl->le_keep != 0;
+        for (int r = threadIdx.x; r < s.R; r += blockDim.x) {
+            s.now[r] = s.req[r];
+            if (s.le_on && s.req[r] && !keep) s.le_db[r] = le_offset(s, s.reps[r], pstep);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s.ctrl->le_keep = 0;
         if (threadIdx.x == 0 && s.ctrl->any_req) {
             s.ctrl->n_rebuilds += 1;
             s.ctrl->max_count = 0;
@@ -77,7 +87,31 @@ __global__ void __launch_bounds__(TILE) k_bin(DevSys<T> s, int cur) {
         const int i = tl.start + threadIdx.x;
         V4<T> p = P[i];
         const RepGeom<T>& g = s.reps[tl.rep];
-        const int wx = wrap_coord(p.x, g.L[0]), wy = wrap_coord(p.y, g.L[1]), wz = wrap_coord(p.z, g.L[2]);
+        int wx, wy, wz;
+        if (s.le_on && !(p.z >= T(0) && p.z < g.L[2])) {
+            // across a sheared face: the image entered is displaced and moving
+            const double L[3] = {(double)g.L[0], (double)g.L[1], (double)g.L[2]};
+            double q[3] = {(double)p.x, (double)p.y, (double)p.z};
+            V4<T> v = s.vel[i];
+            double vx = (double)v.x;
+            int k[3];
+            le_wrap(q, vx, k, L, s.le_db[tl.rep], s.le_shear);
+            p.x = (T)q[0];
+            p.y = (T)q[1];
+            p.z = (T)q[2];
+            // a coordinate rounded up to L in the conversion wraps to 0
+            if (!(p.x < g.L[0])) p.x = T(0);
+            if (!(p.z < g.L[2])) p.z = T(0);
+            v.x = (T)vx;
+            s.vel[i] = v;
+            wx = k[0];
+            wy = k[1];
+            wz = k[2];
+        } else {
+            wx = wrap_coord(p.x, g.L[0]);
+            wy = wrap_coord(p.y, g.L[1]);
+            wz = wrap_coord(p.z, g.L[2]);
+        }
         if (wx | wy | wz) {
             P[i] = p;
             int4 im = s.img[i];
@@ -256,14 +290,23 @@ __global__ void __launch_bounds__(TILE) k_copyback(DevSys<T> s, int cur, int per
 // int4 groups.  SHIFT: the range lies across a face (the entries' and the
 // particle's coordinates are shifted as the image codes say); without it the
 // difference is the plain one, which equals the shifted form with zero shifts.
-template <class T, bool EXCL, bool SHIFT>
+// LE: a row across a sheared face (Lees-Edwards): x is the nearest image of
+// x_i - nz delta - x_j (xL holds nz delta, yL/zL the usual shifts).
+template <class T, bool EXCL, bool SHIFT, bool LE = false>
 __device__ __forceinline__ void verlet_range(const V4<T>* __restrict__ E, int p, int e, int i, int2 ex, T xo, T yo,
                                              T zo, T xL, T yL, T zL, T rl2, int tag, int cap, size_t stride,
-                                             int& cnt, int4& grp, int4* __restrict__ out4) {
+                                             int& cnt, int4& grp, int4* __restrict__ out4, T Lx = T(0),
+                                             T inv_Lx = T(0)) {
     for (; p < e; ++p) {
         const V4<T> xj = ld4<T>(E + p);
         const int j = bits_as_int(xj.w);
-        const T dx = SHIFT ? xo - (xj.x - xL) : xo - xj.x;
+        T dx;
+        if (LE) {
+            dx = (xo - xj.x) - xL;
+            dx -= Lx * rint(dx * inv_Lx);
+        } else {
+            dx = SHIFT ? xo - (xj.x - xL) : xo - xj.x;
+        }
         const T dy = SHIFT ? yo - (xj.y - yL) : yo - xj.y;
         const T dz = SHIFT ? zo - (xj.z - zL) : zo - xj.z;
         bool hit = dx * dx + dy * dy + dz * dz < rl2 && j != i;
@@ -284,7 +327,55 @@ __device__ __forceinline__ void verlet_range(const V4<T>* __restrict__ E, int p,
     }
 }
 
+// replica index of a geometry record
+template <class T>
+__device__ __forceinline__ int g_rep(const DevSys<T>& s, const RepGeom<T>& g) {
+    return (int)(&g - s.reps);
+}
+
+// One plane of rows across a sheared face (Lees-Edwards): x cells
+// cxs - W .. cxs + W (cyclic) of rows cy - W .. cy + W, entries tagged with x
+// code 3 (the x image is taken at evaluation time from the current delta).
 template <class T, int W, bool EXCL>
+__device__ __forceinline__ void verlet_le_plane(const DevSys<T>& s, const RepGeom<T>& g, int i, const V4<T>& xi,
+                                             int2 ex, int cxs, int az, int cy, T nd, T zo, T zL, T L0, T inv_L0,
+                                             int czc, int& cnt, int4& grp, int4* __restrict__ out4) {
+    const V4<T>* __restrict__ E = s.cell_ent;
+    const int* __restrict__ B = s.cell_beg;
+    const int nc0 = g.nc[0], nc1 = g.nc[1];
+    const T L1 = g.L[1];
+    for (int r = -W; r <= W; ++r) {
+        int ay = cy + r, c = 0;
+        if (ay < 0) { ay += nc1; c = 2; }
+        else if (ay >= nc1) { ay -= nc1; c = 1; }
+        const T yo = (c & 1) ? xi.y - L1 : xi.y, yL = (c & 2) ? L1 : T(0);
+        const int tag = (3 | (c << 2) | (czc << 4)) << NBR_INDEX_BITS;
+        const int base = g.cell_off + (az * nc1 + ay) * nc0;
+        int lo = cxs - W, hi = cxs + W;
+        // the cyclic x range as up to two contiguous pieces
+        int p0b, p0e, p1b = 0, p1e = 0;
+        if (lo < 0) {
+            p0b = __ldg(B + base + lo + nc0);
+            p0e = __ldg(B + base + nc0);
+            p1b = __ldg(B + base);
+            p1e = __ldg(B + base + hi + 1);
+        } else if (hi >= nc0) {
+            p0b = __ldg(B + base + lo);
+            p0e = __ldg(B + base + nc0);
+            p1b = __ldg(B + base);
+            p1e = __ldg(B + base + hi - nc0 + 1);
+        } else {
+            p0b = __ldg(B + base + lo);
+            p0e = __ldg(B + base + hi + 1);
+        }
+        verlet_range<T, EXCL, true, true>(E, p0b, p0e, i, ex, xi.x, yo, zo, nd, yL, zL, s.rlist2, tag, s.cap,
+                                          (size_t)s.stride, cnt, grp, out4, L0, inv_L0);
+        verlet_range<T, EXCL, true, true>(E, p1b, p1e, i, ex, xi.x, yo, zo, nd, yL, zL, s.rlist2, tag, s.cap,
+                                          (size_t)s.stride, cnt, grp, out4, L0, inv_L0);
+    }
+}
+
+template <class T, int W, bool EXCL, bool LE>
 __device__ __forceinline__ void verlet_stencil(const DevSys<T>& s, const RepGeom<T>& g, int i,
                                                const V4<T>& xi, int2 ex, int& cnt, int4& grp,
                                                int4* __restrict__ out4) {
@@ -316,12 +407,27 @@ __device__ __forceinline__ void verlet_stencil(const DevSys<T>& s, const RepGeom
     }
     const T xo0 = (cxc0 & 1) ? xi.x - L0 : xi.x, xL0 = (cxc0 & 2) ? L0 : T(0);
     const T xo1 = (cxc1 & 1) ? xi.x - L0 : xi.x, xL1 = (cxc1 & 2) ? L0 : T(0);
+    // Lees-Edwards: delta of this build reduced into [0, Lx)
+    const T le_d = LE ? (T)le_reduce(s.le_db[g_rep(s, g)], (double)L0) : T(0);
+    const T inv_L0 = LE ? T(1) / L0 : T(0);
 #pragma unroll 1
     for (int dz = -W; dz <= W; ++dz) {
         int az = cz + dz, czc = 0;
         if (az < 0) { az += nc2; czc = 2; }
         else if (az >= nc2) { az -= nc2; czc = 1; }
         const T zo = (czc & 1) ? xi.z - L2 : xi.z, zL = (czc & 2) ? L2 : T(0);
+        if (LE && czc != 0) {
+            // a plane across a sheared face: the partners' image is displaced
+            // by nz delta along x; its x cells are found around x_i - nz delta
+            const int nz = czc == 1 ? 1 : -1;
+            const T nd = (T)nz * le_d;
+            T xs = xi.x - nd;
+            if (xs < T(0)) xs += L0;
+            if (xs >= L0) xs -= L0;
+            const int cxs = cell_coord(xs, g.cells_per_len[0], nc0);
+            verlet_le_plane<T, W, EXCL>(s, g, i, xi, ex, cxs, az, cy, nd, zo, zL, L0, inv_L0, czc, cnt, grp, out4);
+            continue;
+        }
         int pb[NR][2], pe[NR][2], cyc[NR];
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
@@ -354,7 +460,7 @@ __device__ __forceinline__ void verlet_stencil(const DevSys<T>& s, const RepGeom
     }
 }
 
-template <class T, int W, bool EXCL>
+template <class T, int W, bool EXCL, bool LE>
 __global__ void __launch_bounds__(TILE) k_verlet(DevSys<T> s, int cur) {
     if (s.ctrl->abort) return;
     for (int t = blockIdx.x; t < s.ntiles; t += gridDim.x) {
@@ -373,7 +479,7 @@ __global__ void __launch_bounds__(TILE) k_verlet(DevSys<T> s, int cur) {
             const int2 ex = EXCL ? s.bond_slot[i] : make_int2(-1, -1);
             int4* __restrict__ out4 = reinterpret_cast<int4*>(s.nbr) + i;
             int4 grp = make_int4(-1, -1, -1, -1);
-            verlet_stencil<T, W, EXCL>(s, g, i, xi, ex, cnt, grp, out4);
+            verlet_stencil<T, W, EXCL, LE>(s, g, i, xi, ex, cnt, grp, out4);
             const int cap = s.cap;
             if ((cnt & 3) != 0 && cnt <= cap) out4[(size_t)(cnt >> 2) * s.stride] = grp;
             s.nbr_cnt[i] = cnt < cap ? cnt : cap;
@@ -421,13 +527,19 @@ int Launch<T>::rebuild(const DevSys<T>& s, int cur, bool resort, bool permute_fo
         k_copyback<T><<<gt, TILE, 0, st>>>(s, cur, permute_force ? 1 : 0);
         launched += 6;
     }
+#define ESPP_VERLET(W, E)                                                  \
+    do {                                                                   \
+        if (s.le_on) k_verlet<T, W, E, true><<<gt, TILE, 0, st>>>(s, cur);  \
+        else k_verlet<T, W, E, false><<<gt, TILE, 0, st>>>(s, cur);        \
+    } while (0)
     if (s.cell_w == 1) {
-        if (s.excl_bonded) k_verlet<T, 1, true><<<gt, TILE, 0, st>>>(s, cur);
-        else k_verlet<T, 1, false><<<gt, TILE, 0, st>>>(s, cur);
+        if (s.excl_bonded) ESPP_VERLET(1, true);
+        else ESPP_VERLET(1, false);
     } else {
-        if (s.excl_bonded) k_verlet<T, 2, true><<<gt, TILE, 0, st>>>(s, cur);
-        else k_verlet<T, 2, false><<<gt, TILE, 0, st>>>(s, cur);
+        if (s.excl_bonded) ESPP_VERLET(2, true);
+        else ESPP_VERLET(2, false);
     }
+#undef ESPP_VERLET
     launched += 1;
     // mirrored entries for the learned potential's pair-once evaluation
     if (s.mlp_on && s.mlp_rev) launched += Launch<T>::mlp_rev(s, st);

@@ -71,7 +71,7 @@ __device__ __forceinline__ void pair_force(const PairRec<T>& pr, const T* __rest
 // One pair term: force (and energy, virial) of neighbour j at displacement d.
 template <class T, bool ENERGY, bool MULTI, bool FAST>
 __device__ __forceinline__ void pair_term(const DevSys<T>& s, int ti, const PairRec<T>* pr1, T dx, T dy,
-                                          T dz, int tj, T& fx, T& fy, T& fz, T& pe, T& vir) {
+                                          T dz, int tj, T& fx, T& fy, T& fz, T& pe, T& vir, T& vxz) {
     const T r2 = dx * dx + dy * dy + dz * dz;
     if (FAST) {
         // one type, plain Lennard-Jones: only rc^2, sigma^2, 24 eps live
@@ -86,6 +86,7 @@ __device__ __forceinline__ void pair_term(const DevSys<T>& s, int ti, const Pair
             if (ENERGY) {
                 pe += pr1->eps4 * s6 * (s6 - T(1)) - pr1->shift;
                 vir += fr * r2;
+                vxz += fr * dx * dz;
             }
         }
         return;
@@ -100,9 +101,21 @@ __device__ __forceinline__ void pair_term(const DevSys<T>& s, int ti, const Pair
         if (ENERGY) {
             pe += u;
             vir += fr * r2;
+            vxz += fr * dx * dz;
         }
     }
 }
+
+// Lees-Edwards quantities of the current step, uniform over a tile: delta
+// reduced into [0, Lx), 1 / Lx, the x velocity le_shear Lz of the image
+// above, and le_shear (streaming profile le_shear (z - Lz / 2)).
+template <class T>
+struct LeCtx {
+    T d;
+    T inv_Lx;
+    T vs;
+    T shear;
+};
 
 // What the DPD pair term of particle i needs besides the displacement: its
 // half-step velocity and id, the replica's seed and the step.
@@ -111,19 +124,23 @@ struct DpdCtx {
     V4<T> vi;
     unsigned long long seed;
     long long step;
+    T le_vs;  // Lees-Edwards: x velocity of the image above (0 without shear)
 };
 
 // DPD pair term (paper "Functionality": dissipative particle dynamics) of a
 // neighbour at displacement d (r2 = |d|^2 inside the DPD cutoff) whose
 // velocity snapshot is vj: dissipative -gamma w^2 (e . v_ij) and random
 // amp w theta_ij along e, w = 1 - r / rc.  e . v_ij and theta_ij are symmetric
-// in the pair, so both sides add exactly opposite forces.
+// in the pair, so both sides add exactly opposite forces.  nz: the partner is
+// the image above (+1) or below (-1) a sheared face (Lees-Edwards), whose
+// velocity is vj + nz le_shear Lz along x.
 template <class T>
 __device__ __forceinline__ void dpd_term(const IntParams<T>* __restrict__ ip, const DpdCtx<T>& c, T dx, T dy,
-                                         T dz, T r2, const V4<T>& vj, T& fx, T& fy, T& fz) {
+                                         T dz, T r2, const V4<T>& vj, T& fx, T& fy, T& fz, int nz = 0) {
     const T r = sqrt(r2), inv_r = T(1) / r;
     const T w = T(1) - r * ip->dpd_inv_rc;
-    const T ev = (dx * (c.vi.x - vj.x) + dy * (c.vi.y - vj.y) + dz * (c.vi.z - vj.z)) * inv_r;
+    const T vjx = nz == 0 ? vj.x : vj.x + (T)nz * c.le_vs;
+    const T ev = (dx * (c.vi.x - vjx) + dy * (c.vi.y - vj.y) + dz * (c.vi.z - vj.z)) * inv_r;
     const T th = dpd_theta<T>(c.seed, bits_as_int(c.vi.w), bits_as_int(vj.w), c.step);
     const T mag = (-ip->gamma * w * w * ev + ip->dpd_amp * w * th) * inv_r;
     fx += mag * dx;
@@ -137,11 +154,13 @@ __device__ __forceinline__ void dpd_term(const IntParams<T>* __restrict__ ip, co
 // independent loads in flight; the next batch's indices are prefetched.
 // With DPD the thermostat's pair term is added in the same pass, for pairs
 // inside the DPD cutoff, from the neighbours' velocity snapshot.
+// Entries with x code 3 cross a sheared face (Lees-Edwards): their x
+// difference is taken from the current offset in *le.
 template <class T, bool ENERGY, bool MULTI, bool FAST, bool DPD>
 __device__ __forceinline__ void pair_loop(const DevSys<T>& s, const V4<T>* __restrict__ P, int i, int n,
                                           const V4<T>& xi, int ti, const PairRec<T>* pr1,
-                                          T L0, T L1, T L2, T& fx, T& fy, T& fz, T& pe, T& vir,
-                                          const DpdCtx<T>* dc = nullptr) {
+                                          T L0, T L1, T L2, T& fx, T& fy, T& fz, T& pe, T& vir, T& vxz,
+                                          const LeCtx<T>* le, const DpdCtx<T>* dc = nullptr) {
     const T xim = xi.x - L0, yim = xi.y - L1, zim = xi.z - L2;
     constexpr int GB = sizeof(T) == 4 ? ESPP_STEP_GB32 : 1;  // int4 groups per batch
     const int ng = (n + 3) >> 2;
@@ -188,7 +207,7 @@ __device__ __forceinline__ void pair_loop(const DevSys<T>& s, const V4<T>* __res
                 if (jj[q] < 0) continue;
                 const T dx = xi.x - xj[q].x, dy = xi.y - xj[q].y, dz = xi.z - xj[q].z;
                 pair_term<T, ENERGY, MULTI, FAST>(s, ti, pr1, dx, dy, dz, bits_as_int(xj[q].w), fx, fy, fz, pe,
-                                                  vir);
+                                                  vir, vxz);
                 if (DPD) {
                     const T r2 = dx * dx + dy * dy + dz * dz;
                     if (r2 < s.ip->dpd_rc2)
@@ -200,15 +219,23 @@ __device__ __forceinline__ void pair_loop(const DevSys<T>& s, const V4<T>* __res
             for (int q = 0; q < 4 * GB; ++q) {
                 if (jj[q] < 0) continue;
                 const int code = nbr_code(jj[q]);
-                const T dx = shifted_diff(xi.x, xim, xj[q].x, L0, code & 3);
+                int nz = 0;
+                T dx;
+                if ((code & 3) == 3) {
+                    nz = (code >> 4) == 1 ? 1 : -1;
+                    dx = le_dx(xi.x, xj[q].x, nz, le->d, L0, le->inv_Lx);
+                } else {
+                    dx = shifted_diff(xi.x, xim, xj[q].x, L0, code & 3);
+                }
                 const T dy = shifted_diff(xi.y, yim, xj[q].y, L1, (code >> 2) & 3);
                 const T dz = shifted_diff(xi.z, zim, xj[q].z, L2, code >> 4);
                 pair_term<T, ENERGY, MULTI, FAST>(s, ti, pr1, dx, dy, dz, bits_as_int(xj[q].w), fx, fy, fz,
-                                                  pe, vir);
+                                                  pe, vir, vxz);
                 if (DPD) {
                     const T r2 = dx * dx + dy * dy + dz * dz;
                     if (r2 < s.ip->dpd_rc2)
-                        dpd_term<T>(s.ip, *dc, dx, dy, dz, r2, ld4<T>(s.vsnap + nbr_slot(jj[q])), fx, fy, fz);
+                        dpd_term<T>(s.ip, *dc, dx, dy, dz, r2, ld4<T>(s.vsnap + nbr_slot(jj[q])), fx, fy, fz,
+                                    nz);
                 }
             }
         }
@@ -219,8 +246,8 @@ __device__ __forceinline__ void pair_loop(const DevSys<T>& s, const V4<T>* __res
 // for the learned potential, whose pair forces come from k_mlp.
 template <class T>
 __device__ __forceinline__ void dpd_loop(const DevSys<T>& s, const V4<T>* __restrict__ P, int i, int n,
-                                         const V4<T>& xi, const DpdCtx<T>& c, T L0, T L1, T L2, T& fx, T& fy,
-                                         T& fz) {
+                                         const V4<T>& xi, const DpdCtx<T>& c, const LeCtx<T>& le, T L0, T L1,
+                                         T L2, T& fx, T& fy, T& fz) {
     const IntParams<T>* __restrict__ ip = s.ip;
     const T rc2 = ip->dpd_rc2;
     const T xim = xi.x - L0, yim = xi.y - L1, zim = xi.z - L2;
@@ -235,12 +262,19 @@ __device__ __forceinline__ void dpd_loop(const DevSys<T>& s, const V4<T>* __rest
             if (4 * g + q >= n) continue;
             const int j = nbr_slot(jj[q]), code = nbr_code(jj[q]);
             const V4<T> xj = ld4<T>(P + j);
-            const T dx = shifted_diff(xi.x, xim, xj.x, L0, code & 3);
+            int nz = 0;
+            T dx;
+            if ((code & 3) == 3) {
+                nz = (code >> 4) == 1 ? 1 : -1;
+                dx = le_dx(xi.x, xj.x, nz, le.d, L0, le.inv_Lx);
+            } else {
+                dx = shifted_diff(xi.x, xim, xj.x, L0, code & 3);
+            }
             const T dy = shifted_diff(xi.y, yim, xj.y, L1, (code >> 2) & 3);
             const T dz = shifted_diff(xi.z, zim, xj.z, L2, code >> 4);
             const T r2 = dx * dx + dy * dy + dz * dz;
             if (!(r2 < rc2)) continue;
-            dpd_term<T>(ip, c, dx, dy, dz, r2, ld4<T>(VS + j), fx, fy, fz);
+            dpd_term<T>(ip, c, dx, dy, dz, r2, ld4<T>(VS + j), fx, fy, fz, nz);
         }
     }
 }
@@ -281,6 +315,31 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32
 #pragma unroll
             for (int k = 0; k < NPART; ++k) acc[k] = 0.0;
         }
+        // Lees-Edwards: the tile's offset now and, after the drift, the
+        // displacement bound that keeps the list valid: pairs across a sheared
+        // face also move apart by the change of delta since the build
+        LeCtx<T> le;
+        T skin_thr2 = s.half_skin2;
+        if (s.le_on) {
+            double q[2] = {0.0, 0.0};
+            if ((threadIdx.x & 31) == 0) {
+                const double dnow = le_offset(s, g, step);
+                q[0] = le_reduce(dnow, (double)g.L[0]);
+                if (MODE == MODE_STEP) {
+                    const double h = 0.5 * ((double)s.skin - fabs(le_offset(s, g, step + 1) - s.le_db[tl.rep]));
+                    q[1] = h > 0.0 ? h * h : 0.0;
+                }
+            }
+            q[0] = __shfl_sync(0xffffffffu, q[0], 0);
+            q[1] = __shfl_sync(0xffffffffu, q[1], 0);
+            le.d = (T)q[0];
+            le.inv_Lx = T(1) / g.L[0];
+            le.shear = (T)s.le_shear;
+            le.vs = (T)(s.le_shear * (double)g.L[2]);
+            if (MODE == MODE_STEP) skin_thr2 = (T)q[1];
+        } else {
+            le.d = le.inv_Lx = le.vs = le.shear = T(0);
+        }
         if (active) {
             const int i = tl.start + threadIdx.x;
             const T L0 = g.L[0], L1 = g.L[1], L2 = g.L[2];
@@ -289,7 +348,7 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32
             // velocity and build position, then the bond partners' positions
             const V4<T> xi = ld4<T>(P + i);
             const int ti = bits_as_int(xi.w);
-            T fx = 0, fy = 0, fz = 0, pe = 0, pb = 0, vir = 0;
+            T fx = 0, fy = 0, fz = 0, pe = 0, pb = 0, vir = 0, vxz = 0;
             const int n = s.nbr_cnt[i];
             const bool bonded = s.bond.kind != 0;
             const int2 b = bonded ? s.bond_slot[i] : make_int2(-1, -1);
@@ -303,6 +362,7 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32
                 dc.vi = v;
                 dc.seed = g.seed;
                 dc.step = step;
+                dc.le_vs = le.vs;
             }
             if (s.mlp_on) {
                 // pair forces of the learned potential, computed by k_mlp
@@ -314,7 +374,7 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32
                     pe = (T)fm.w;
                     vir = (T)s.mlp_w[i];
                 }
-                if (DPD) dpd_loop<T>(s, P, i, n, xi, dc, L0, L1, L2, fx, fy, fz);
+                if (DPD) dpd_loop<T>(s, P, i, n, xi, dc, le, L0, L1, L2, fx, fy, fz);
             } else if (FAST) {
                 PairRec<T> pr;
                 pr.rc2 = s.pair[0].rc2;
@@ -325,15 +385,15 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32
                     pr.shift = s.pair[0].shift;
                 }
                 pair_loop<T, ENERGY, false, true, DPD>(s, P, i, n, xi, ti, &pr, L0, L1, L2, fx, fy, fz, pe, vir,
-                                                       &dc);
+                                                       vxz, &le, &dc);
             } else if (s.ntypes == 1) {
                 const PairRec<T> pr = s.pair[0];
                 if (pr.kind != 0 || DPD)
                     pair_loop<T, ENERGY, false, false, DPD>(s, P, i, n, xi, ti, &pr, L0, L1, L2, fx, fy, fz, pe,
-                                                            vir, &dc);
+                                                            vir, vxz, &le, &dc);
             } else {
                 pair_loop<T, ENERGY, true, false, DPD>(s, P, i, n, xi, ti, nullptr, L0, L1, L2, fx, fy, fz, pe,
-                                                       vir, &dc);
+                                                       vir, vxz, &le, &dc);
             }
             // bonds (paper "Functionality": bonded interactions; FENE or tabulated)
             double blen = 0.0, bcnt = 0.0;
@@ -343,9 +403,15 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32
                     const int p = q == 0 ? b.x : b.y;
                     if (p < 0) continue;
                     const V4<T> xp = q == 0 ? xp0 : xp1;
-                    const T dx = min_image(xi.x, xp.x, L0, H0);
-                    const T dy = min_image(xi.y, xp.y, L1, H1);
                     const T dz = min_image(xi.z, xp.z, L2, H2);
+                    const T dy = min_image(xi.y, xp.y, L1, H1);
+                    T dx;
+                    if (s.le_on && (xi.z - xp.z > H2 || xi.z - xp.z < -H2)) {
+                        // bond across a sheared face
+                        dx = le_dx(xi.x, xp.x, xi.z - xp.z > H2 ? 1 : -1, le.d, L0, le.inv_Lx);
+                    } else {
+                        dx = min_image(xi.x, xp.x, L0, H0);
+                    }
                     const T r2 = dx * dx + dy * dy + dz * dz;
                     T fr, ub = T(0);
                     if (s.bond.kind == ESPP_FENE) {
@@ -375,6 +441,7 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32
                     if (ENERGY) {
                         pb += ub;
                         vir += fr * r2;
+                        vxz += fr * dx * dz;
                         blen += sqrt((double)r2);
                         bcnt += 1.0;
                     }
@@ -386,6 +453,7 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32
                 acc[P_VIRIAL] = 0.5 * (double)vir;
                 acc[P_BOND_LEN] = 0.5 * blen;
                 acc[P_BOND_CNT] = 0.5 * bcnt;
+                acc[P_VIR_XZ] = 0.5 * (double)vxz;
             }
             if (MODE == MODE_FORCES) {
                 if (f_out) {
@@ -396,7 +464,10 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32
                 }
                 if (ENERGY) {
                     const double m = (double)ip->mass[ti];
-                    acc[P_KE] = 0.5 * m * ((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z);
+                    // kinetic terms relative to the shear profile (Lees-Edwards)
+                    const double vxp = (double)v.x - (double)le.shear * ((double)xi.z - (double)H2);
+                    acc[P_KE] = 0.5 * m * (vxp * vxp + (double)v.y * v.y + (double)v.z * v.z);
+                    acc[P_KIN_XZ] = m * vxp * (double)v.z;
                     acc[P_PX] = m * v.x;
                     acc[P_PY] = m * v.y;
                     acc[P_PZ] = m * v.z;
@@ -408,7 +479,9 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32
                     langevin_noise<T>(g.seed, bits_as_int(v.w), step, rx, ry, rz);
                     const T amp = ip->noise_amp[ti];
                     const T gm = ip->gamma * m;
-                    fx += -gm * v.x + amp * rx;
+                    // friction relative to the shear profile (Lees-Edwards)
+                    const T vxp = s.le_on ? v.x - le.shear * (xi.z - H2) : v.x;
+                    fx += -gm * vxp + amp * rx;
                     fy += -gm * v.y + amp * ry;
                     fz += -gm * v.z + amp * rz;
                 }
@@ -437,7 +510,7 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32
                             x = xi.x; y = xi.y; z = xi.z;
                         }
                         const T ex = x - xbi.x, ey = y - xbi.y, ez = z - xbi.z;
-                        if (ex * ex + ey * ey + ez * ez > s.half_skin2) {
+                        if (ex * ex + ey * ey + ez * ez > skin_thr2) {
                             s.req[tl.rep] = 1;
                             c->any_req = 1;
                             __threadfence();
@@ -476,6 +549,7 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32
             if (done == gridDim.x - 1) {
                 __threadfence();
                 c->step = step;
+                if (MODE == MODE_FINAL) c->pos_ahead = 0;
                 c->blocks_done = 0;
                 if (next_cond) {
                     const unsigned int want = *(volatile unsigned int*)&c->any_req;
@@ -495,10 +569,19 @@ __global__ void __launch_bounds__(TILE) k_prologue(DevSys<T> s, int cur) {
     const V4<T>* __restrict__ P = s.pos[cur];
     V4<T>* __restrict__ Pn = s.pos[cur ^ 1];
     const IntParams<T>* __restrict__ ip = s.ip;
+    // the stored positions become those of step + 1 (read by the rebuilds)
+    if (blockIdx.x == 0 && threadIdx.x == 0) c->pos_ahead = 1;
+    const long long step = c->step;
     for (int t = blockIdx.x; t < s.ntiles; t += gridDim.x) {
         const Tile tl = s.tiles[t];
         if ((int)threadIdx.x >= tl.count) continue;
         const int i = tl.start + threadIdx.x;
+        T skin_thr2 = s.half_skin2;
+        if (s.le_on) {
+            // Lees-Edwards: the change of delta since the build uses up skin
+            const double h = 0.5 * ((double)s.skin - fabs(le_offset(s, s.reps[tl.rep], step + 1) - s.le_db[tl.rep]));
+            skin_thr2 = h > 0.0 ? (T)(h * h) : T(0);
+        }
         const V4<T> xi = P[i];
         const int ti = bits_as_int(xi.w);
         const V4<T> f = s.frc[i];
@@ -516,7 +599,7 @@ __global__ void __launch_bounds__(TILE) k_prologue(DevSys<T> s, int cur) {
         }
         const V4<T> b = s.xb[i];
         const T ex = x - b.x, ey = y - b.y, ez = z - b.z;
-        if (ex * ex + ey * ey + ez * ez > s.half_skin2) {
+        if (ex * ex + ey * ey + ez * ez > skin_thr2) {
             s.req[tl.rep] = 1;
             c->any_req = 1;
         }

@@ -40,6 +40,18 @@ struct MlpWeights {
 constexpr int NPART = 12;  // per-tile observable partials (doubles)
 enum : int {
     P_PE_PAIR = 0, P_PE_BOND, P_VIRIAL, P_KE, P_BOND_LEN, P_BOND_CNT, P_PX, P_PY, P_PZ,
+    P_VIR_XZ,  // sum over pairs and bonds of (r_ij)_x (F_ij)_z
+    P_KIN_XZ,  // sum of m v_x v_z (velocities relative to the shear profile)
+};
+
+// Lees-Edwards clock in device memory: the simulated time of step s is
+// t0 + (s - s0) dt (rewritten by the host before each integrate call, so
+// captured graphs need no update).
+struct LeClock {
+    double t0;
+    double dt;
+    long long s0;
+    long long pad;
 };
 
 template <class T> struct DevSys {
@@ -116,12 +128,85 @@ template <class T> struct DevSys {
     V4<T>* vsnap;       // DPD: velocities at the force evaluation, read for the neighbours
     int tc_fault;       // host fault injection: the tensor-core kernel issues no MMA and
                         // its bounded mbarrier wait runs out (tests of the timeout path)
+    // Lees-Edwards boundary conditions: flow along x, gradient along z; the
+    // image at z + k Lz is displaced by k delta(t) along x and moves at
+    // k le_shear Lz, delta(t) = le_shear Lz t.  List entries of pairs across
+    // the sheared faces carry x code 3 (x image taken at evaluation time).
+    int le_on;
+    double le_shear;
+    const LeClock* le_clk;
+    double* le_db;      // per replica: delta at the last list build (not reduced)
     int N;
     BondRec<T> bond;
     T rlist2;           // (rc + skin)^2
     T half_skin2;       // (skin / 2)^2
+    T skin;
     double* partials;   // ntiles * NPART
 };
+
+// ---- Lees-Edwards helpers ----------------------------------------------------
+// offset delta of replica g at step `step`, not reduced
+template <class T>
+__device__ __forceinline__ double le_offset(const DevSys<T>& s, const RepGeom<T>& g, long long step) {
+    const LeClock* c = s.le_clk;
+    return s.le_shear * (double)g.L[2] * (c->t0 + (double)(step - c->s0) * c->dt);
+}
+
+// d reduced into [0, L)
+__device__ __forceinline__ double le_reduce(double d, double L) { return d - L * floor(d / L); }
+
+// x displacement of a pair across the sheared faces: nz = +1 when the partner
+// is the image above (z code 1), -1 below (z code 2); delta reduced into
+// [0, Lx); the x image is the nearest one.
+template <class T>
+__device__ __forceinline__ T le_dx(T xi, T xj, int nz, T delta, T Lx, T inv_Lx) {
+    T dx = (xi - xj) - (T)nz * delta;
+    return dx - Lx * rint(dx * inv_Lx);
+}
+
+// Wrap of one position under Lees-Edwards, in double: a crossing of the z
+// faces by k boxes moves x by -k delta and v_x by -k le_shear Lz (the image
+// the particle entered), then x (possibly several boxes) and y are wrapped.
+// k[] receives the image changes.
+__device__ __forceinline__ void le_wrap(double p[3], double& vx, int k[3], const double L[3], double delta,
+                                        double shear) {
+    k[0] = k[1] = k[2] = 0;
+    if (p[2] >= L[2]) {
+        p[2] -= L[2];
+        k[2] = 1;
+    } else if (p[2] < 0.0) {
+        p[2] += L[2];
+        k[2] = -1;
+        if (p[2] >= L[2]) p[2] = 0.0;
+    }
+    if (k[2] != 0) {
+        p[0] -= k[2] * delta;
+        vx -= k[2] * shear * L[2];
+        double q = floor(p[0] / L[0]);
+        p[0] -= q * L[0];
+        if (p[0] >= L[0]) {
+            p[0] -= L[0];
+            q += 1.0;
+        }
+        if (p[0] < 0.0) p[0] = 0.0;
+        k[0] = (int)q;
+    } else if (p[0] >= L[0]) {
+        p[0] -= L[0];
+        k[0] = 1;
+    } else if (p[0] < 0.0) {
+        p[0] += L[0];
+        k[0] = -1;
+        if (p[0] >= L[0]) p[0] = 0.0;
+    }
+    if (p[1] >= L[1]) {
+        p[1] -= L[1];
+        k[1] = 1;
+    } else if (p[1] < 0.0) {
+        p[1] += L[1];
+        k[1] = -1;
+        if (p[1] >= L[1]) p[1] = 0.0;
+    }
+}
 
 // kernels launched by one rebuild without a resort (Launch::rebuild)
 constexpr int REBUILD_LAUNCHES = 8;

@@ -69,6 +69,8 @@ struct SystemBase {
     virtual int set_resort_interval(int64_t steps) = 0;
     virtual int set_cell_subdivision(int w) = 0;
     virtual int set_thermostat(int kind, double rc) = 0;
+    virtual int set_lees_edwards(int on, double shear, double time) = 0;
+    virtual int get_lees_edwards(int* on, double* shear, double* time) = 0;
 };
 
 struct PairHost {
@@ -139,6 +141,10 @@ class System : public SystemBase {
     int64_t resort_every = 500;  // steps between Hilbert resorts inside integrate (0 = never)
     int cell_sub_req = 0;  // requested cell subdivision (0 = chosen per system)
     double dpd_rc = 0;     // DPD thermostat cutoff (d.dpd set)
+    // simulated time t(step) = le_clk_h.t0 + (step - s0) dt, mirrored on the
+    // device for the Lees-Edwards offset
+    LeClock le_clk_h{0.0, 0.0, 0, 0};
+    LeClock* d_le_clk = nullptr;
     int cell_sub = 1;      // subdivision in use (stencil half width)
 
     ~System() override {
@@ -308,8 +314,10 @@ class System : public SystemBase {
             (rc = alloc(&d_mol_rep, mol_rep_h.size(), allocs)) ||
             (rc = alloc(&d_mol_rg2, mol_rep_h.size(), allocs)) ||
             (rc = alloc(&d.mlp_f, n, allocs)) || (rc = alloc(&d.mlp_w, n, allocs)) ||
-            (rc = alloc(&d_mlp, 1, allocs)))
+            (rc = alloc(&d_mlp, 1, allocs)) || (rc = alloc(&d_le_clk, 1, allocs)) ||
+            (rc = alloc(&d.le_db, (size_t)R, allocs)))
             return rc;
+        d.le_clk = d_le_clk;
         d.mlp = d_mlp;
         // host-side fault injection for tests: the tensor-core kernel's wait runs out
         if (const char* f = getenv("ESPP_FAULT_TC_TIMEOUT")) d.tc_fault = atoi(f) > 0 ? 1 : 0;
@@ -599,8 +607,44 @@ class System : public SystemBase {
     }
 
     int set_step(int64_t s) override {
+        // the simulated time stays; the step number it belongs to changes
+        Ctrl c = read_ctrl();
+        const double t = time_at(c.step);
         CK(cudaMemcpyAsync(&d_ctrl->step, &s, sizeof(long long), cudaMemcpyHostToDevice, st));
         CK(cudaStreamSynchronize(st));
+        return set_clock(t, le_clk_h.dt, s);
+    }
+
+    // ---------------------------------------------------- Lees-Edwards clock
+    double time_at(int64_t step) const { return le_clk_h.t0 + (double)(step - le_clk_h.s0) * le_clk_h.dt; }
+    int set_clock(double t0, double dt, int64_t s0) {
+        le_clk_h.t0 = t0;
+        le_clk_h.dt = dt;
+        le_clk_h.s0 = s0;
+        CK(cudaMemcpyAsync(d_le_clk, &le_clk_h, sizeof(LeClock), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        return ESPP_OK;
+    }
+
+    int set_lees_edwards(int on, double shear, double time) override {
+        if (!std::isfinite(shear) || !std::isfinite(time)) return fail(ESPP_ERR_ARG, "shear rate and time must be finite");
+        if (on && d.mlp_on) return fail(ESPP_ERR_STATE, "Lees-Edwards is not available with the learned potential");
+        Ctrl c = read_ctrl();
+        d.le_on = on ? 1 : 0;
+        d.le_shear = on ? shear : 0.0;
+        int rcode = set_clock(time, le_clk_h.dt, c.step);
+        if (rcode) return rcode;
+        clear_graphs();          // the setting is a kernel argument of captured graphs
+        rebuild_pending = true;  // the search across the sheared faces changes
+        f_valid = false;
+        return ESPP_OK;
+    }
+
+    int get_lees_edwards(int* on, double* shear, double* time) override {
+        Ctrl c = read_ctrl();
+        if (on) *on = d.le_on;
+        if (shear) *shear = d.le_shear;
+        if (time) *time = time_at(c.step);
         return ESPP_OK;
     }
 
@@ -689,6 +733,7 @@ class System : public SystemBase {
     // beads (device outputs; replica 0's box)
     int cg_map(int bps, double* xs, double* fs) override {
         if (bps < 1 || N % bps != 0 || !xs || !fs) return fail(ESPP_ERR_ARG, "bad mapping arguments");
+        if (d.le_on) return fail(ESPP_ERR_STATE, "the CG mapping is not available under Lees-Edwards");
         double* fdev = nullptr;
         CK(cudaMalloc(&fdev, 3 * (size_t)N * sizeof(double)));
         int rcode = compute_forces(fdev, ESPP_DEVICE);
@@ -1013,6 +1058,7 @@ class System : public SystemBase {
         const double rl = rc + sk;
         d.rlist2 = (T)(rl * rl);
         d.half_skin2 = (T)(0.25 * sk * sk);
+        d.skin = (T)sk;
         rcode = upload_geometry();
         if (rcode) return rcode;
         rcode = alloc_list(estimate_cap());
@@ -1069,6 +1115,7 @@ class System : public SystemBase {
     int ensure_list() {
         if (!state_set) return fail(ESPP_ERR_STATE, "no state set");
         if (d.mlp_on && mlp_bits.empty()) return fail(ESPP_ERR_STATE, "learned potential selected but no weights set");
+        if (d.mlp_on && d.le_on) return fail(ESPP_ERR_STATE, "Lees-Edwards is not available with the learned potential");
         if (!cells_ready) return fail(ESPP_ERR_STATE, "call espp_build_neighbors first");
         int rcode = check_cutoffs();
         if (rcode) return rcode;
@@ -1252,6 +1299,9 @@ class System : public SystemBase {
         const int64_t step0 = c0.step;
         const int64_t target = step0 + nsteps;
         const int64_t rb0 = c0.n_rebuilds;
+        // the clock of this call: t(step0) carried over, this call's dt
+        rcode = set_clock(time_at(step0), dt, step0);
+        if (rcode) return rcode;
         if (!f_valid) {
             launches += Launch<T>::step(d, MODE_INIT, false, cur, nullptr, 0, 0, st);
             f_valid = true;
@@ -1371,6 +1421,7 @@ class System : public SystemBase {
             o.temperature = 2.0 * o.ke / (3.0 * rep_n[r]);
             const double V = box[3 * r] * box[3 * r + 1] * box[3 * r + 2];
             o.pressure = (2.0 * o.ke + o.virial) / (3.0 * V);
+            o.pxz = (q[P_KIN_XZ] + q[P_VIR_XZ]) / V;
             o.mean_bond = q[P_BOND_CNT] > 0 ? q[P_BOND_LEN] / q[P_BOND_CNT] : 0.0;
             o.rg2 = nmol[r] > 0 ? rgsum[r] / nmol[r] : 0.0;
             o.n_molecules = nmol[r];
@@ -1426,6 +1477,8 @@ class System : public SystemBase {
         int32_t version, precision, R, f_valid;
         int64_t N, step, n_rebuilds;
         double rc_list, skin;
+        int32_t le_on, pad;
+        double le_shear, le_time, le_dt;  // Lees-Edwards setting and the simulated time
     };
 
     template <class P>
@@ -1448,8 +1501,8 @@ class System : public SystemBase {
         if (c.abort) return status_from(c);
         CkptHeader hd;
         memset(&hd, 0, sizeof(hd));
-        memcpy(hd.magic, "ESPPCKP1", 8);
-        hd.version = 1;
+        memcpy(hd.magic, "ESPPCKP2", 8);
+        hd.version = 2;
         hd.precision = sizeof(T) == 4 ? ESPP_FP32 : ESPP_FP64;
         hd.R = R;
         hd.f_valid = f_valid ? 1 : 0;
@@ -1458,15 +1511,21 @@ class System : public SystemBase {
         hd.n_rebuilds = c.n_rebuilds;
         hd.rc_list = rc_list;
         hd.skin = skin;
+        hd.le_on = d.le_on;
+        hd.le_shear = d.le_shear;
+        hd.le_time = time_at(c.step);
+        hd.le_dt = le_clk_h.dt;
         const size_t n = (size_t)N;
         std::vector<V4<T>> pos, vel, frc, xb;
         std::vector<int4> img;
         std::vector<int2> bs;
         std::vector<int> sid, req;
+        std::vector<double> ledb;
         int rcode;
         if ((rcode = dl(pos, d.pos[cur], n)) || (rcode = dl(vel, d.vel, n)) || (rcode = dl(frc, d.frc, n)) ||
             (rcode = dl(xb, d.xb, n)) || (rcode = dl(img, d.img, n)) || (rcode = dl(bs, d.bond_slot, n)) ||
-            (rcode = dl(sid, d.slot_of_id, n)) || (rcode = dl(req, d.req, (size_t)R)))
+            (rcode = dl(sid, d.slot_of_id, n)) || (rcode = dl(req, d.req, (size_t)R)) ||
+            (rcode = dl(ledb, d.le_db, (size_t)R)))
             return rcode;
         FILE* fh = fopen(path, "wb");
         if (!fh) return fail(ESPP_ERR_IO, std::string("cannot open ") + path);
@@ -1485,6 +1544,7 @@ class System : public SystemBase {
         wr(bs.data(), n * sizeof(int2));
         wr(sid.data(), n * sizeof(int));
         wr(req.data(), (size_t)R * sizeof(int));
+        wr(ledb.data(), (size_t)R * sizeof(double));
         ok = (fclose(fh) == 0) && ok;
         return ok ? ESPP_OK : fail(ESPP_ERR_IO, std::string("write failed: ") + path);
     }
@@ -1495,7 +1555,7 @@ class System : public SystemBase {
         FILE* fh = fopen(path, "rb");
         if (!fh) return fail(ESPP_ERR_IO, std::string("cannot open ") + path);
         CkptHeader hd;
-        bool ok = fread(&hd, sizeof(hd), 1, fh) == 1 && memcmp(hd.magic, "ESPPCKP1", 8) == 0;
+        bool ok = fread(&hd, sizeof(hd), 1, fh) == 1 && memcmp(hd.magic, "ESPPCKP2", 8) == 0;
         if (!ok) {
             fclose(fh);
             return fail(ESPP_ERR_IO, "not a checkpoint file");
@@ -1521,6 +1581,7 @@ class System : public SystemBase {
         std::vector<int4> img(n);
         std::vector<int2> bs(n);
         std::vector<int> sid(n), req((size_t)R);
+        std::vector<double> ledb((size_t)R);
         auto rd = [&](void* p, size_t bytes) { ok = ok && fread(p, 1, bytes, fh) == bytes; };
         rd(pos.data(), n * sizeof(V4<T>));
         rd(vel.data(), n * sizeof(V4<T>));
@@ -1530,18 +1591,28 @@ class System : public SystemBase {
         rd(bs.data(), n * sizeof(int2));
         rd(sid.data(), n * sizeof(int));
         rd(req.data(), (size_t)R * sizeof(int));
+        rd(ledb.data(), (size_t)R * sizeof(double));
         fclose(fh);
         if (!ok) return fail(ESPP_ERR_IO, "checkpoint file is truncated");
+        if (hd.le_on && d.mlp_on) return fail(ESPP_ERR_STATE, "Lees-Edwards is not available with the learned potential");
         CK(cudaStreamSynchronize(st));
         int rcode = upload_geometry();  // seeds
         if (rcode) return rcode;
         cur = 0;
         if ((rcode = ul(d.pos[0], pos)) || (rcode = ul(d.pos[1], xb)) || (rcode = ul(d.vel, vel)) ||
             (rcode = ul(d.frc, frc)) || (rcode = ul(d.xb, xb)) || (rcode = ul(d.img, img)) ||
-            (rcode = ul(d.bond_slot, bs)) || (rcode = ul(d.slot_of_id, sid)))
+            (rcode = ul(d.bond_slot, bs)) || (rcode = ul(d.slot_of_id, sid)) || (rcode = ul(d.le_db, ledb)))
             return rcode;
+        // Lees-Edwards setting and clock of the saved run
+        d.le_on = hd.le_on;
+        d.le_shear = hd.le_shear;
+        clear_graphs();
+        rcode = set_clock(hd.le_time, hd.le_dt, hd.step);
+        if (rcode) return rcode;
         Ctrl c = read_ctrl();
         c.step = hd.step;
+        c.pos_ahead = 0;
+        c.le_keep = 1;  // the list below is rebuilt with the saved build offsets
         c.err = 0;
         c.abort = 0;
         c.any_req = 0;
@@ -1799,6 +1870,12 @@ int espp_set_resort_interval(espp_h h, int64_t steps) {
     return guarded(h, [&](espp::SystemBase& s) { return s.set_resort_interval(steps); });
 }
 
+int espp_set_lees_edwards(espp_h h, int32_t on, double shear_rate, double time) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.set_lees_edwards(on, shear_rate, time); });
+}
+int espp_get_lees_edwards(espp_h h, int32_t* on, double* shear_rate, double* time) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.get_lees_edwards(on, shear_rate, time); });
+}
 int espp_set_thermostat(espp_h h, int32_t kind, double rc) {
     return guarded(h, [&](espp::SystemBase& s) { return s.set_thermostat(kind, rc); });
 }

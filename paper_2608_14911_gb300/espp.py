@@ -63,6 +63,7 @@ EXPORTS = (
     "espp_rdf_counts_noalloc", "espp_set_resort_interval", "espp_mlp_set_weights",
     "espp_set_exclude_bonded", "espp_mlp_get_weights", "espp_mlp_train", "espp_mlp_loss_grad",
     "espp_cg_map", "espp_set_cell_subdivision", "espp_set_thermostat",
+    "espp_set_lees_edwards", "espp_get_lees_edwards",
 )
 NOALLOC_MAX_BINS = 4096
 
@@ -87,7 +88,8 @@ class Obs(ctypes.Structure):
                 ("temperature", ctypes.c_double), ("pressure", ctypes.c_double),
                 ("mean_bond", ctypes.c_double), ("rg2", ctypes.c_double),
                 ("n_molecules", ctypes.c_int64), ("n_rebuilds", ctypes.c_int64),
-                ("error_word", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("error_word", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("pxz", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -141,6 +143,8 @@ def lib(path: str = LIB_PATH):
         "espp_set_resort_interval": ([vp, i64], ctypes.c_int),
         "espp_set_cell_subdivision": ([vp, ctypes.c_int32], ctypes.c_int),
         "espp_set_thermostat": ([vp, ctypes.c_int32, ctypes.c_double], ctypes.c_int),
+        "espp_set_lees_edwards": ([vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double], ctypes.c_int),
+        "espp_get_lees_edwards": ([vp, ctypes.POINTER(ctypes.c_int32), dp, dp], ctypes.c_int),
         "espp_mlp_set_weights": ([vp, vp, i64], ctypes.c_int),
         "espp_set_exclude_bonded": ([vp, ctypes.c_int], ctypes.c_int),
         "espp_mlp_get_weights": ([vp, vp, i64], ctypes.c_int),
@@ -416,6 +420,19 @@ class System:
     def set_thermostat(self, kind, rc=0.0):
         """ESPP_THERMO_LANGEVIN, or ESPP_THERMO_DPD with pair cutoff rc."""
         self._c(lib().espp_set_thermostat(self._h, int(kind), float(rc)))
+
+    def set_lees_edwards(self, on, shear_rate=0.0, time=None):
+        """Lees-Edwards shear (flow x, gradient z); time defaults to the
+        handle's current simulated time."""
+        if time is None:
+            time = self.lees_edwards()[2]
+        self._c(lib().espp_set_lees_edwards(self._h, 1 if on else 0, float(shear_rate), float(time)))
+
+    def lees_edwards(self):
+        """(on, shear_rate, simulated time)."""
+        on, sh, t = ctypes.c_int32(), ctypes.c_double(), ctypes.c_double()
+        self._c(lib().espp_get_lees_edwards(self._h, ctypes.byref(on), ctypes.byref(sh), ctypes.byref(t)))
+        return bool(on.value), sh.value, t.value
 
     def set_graph_chunk(self, steps):
         self._c(lib().espp_set_graph_chunk(self._h, int(steps)))
