@@ -453,6 +453,7 @@ def run_ours(a):
     if not a.no_suite and world == 1:
         suite = {}
         for name, fn in (("kg1m_dpd", lambda o: o.update(suite_dpd(a, barrier, s, cfg, seed, ms / a.steps))),
+                         ("dpd_fluid_786k", lambda o: o.update(suite_dpd_fluid(a, barrier))),
                          ("lj4m", lambda o: o.update(suite_lj4m(a, barrier, peaks))),
                          ("batched512", lambda o: o.update(suite_batched(a, barrier))),
                          ("learned_cg", lambda o: suite_learned_cg(a, barrier, o))):
@@ -541,6 +542,46 @@ def suite_dpd(a, sync, src, cfg, seed, langevin_ms):
            "temperature_after": o["temperature"], "temperature_before": p0["temperature"],
            "net_momentum_per_particle": float(abs(v.sum(axis=0)).max() / cfg.n)}
     s.close()
+    return out
+
+
+def suite_dpd_fluid(a, sync):
+    """Groot-Warren DPD fluid: 786,432 particles at density 3 in a 64^3 box,
+    soft repulsion F = 25 (1 - r) (tabulated) and the DPD thermostat (rc 1,
+    gamma 4.5, kT 1, dt 0.04), at rest and under Lees-Edwards shear 0.01."""
+    from paper_2608_14911_gb300 import espp, inputs
+    L, a_rep, n_tab = 64.0, 25.0, 1001
+    box = np.array([L, L, L])
+    n = int(3 * L ** 3)
+    cfg = inputs.random_positions(n, box, seed=11)
+    v = inputs.maxwell_velocities(n, 1.0, seed=11)
+    r = np.linspace(0.0, 1.0, n_tab)
+    u_tab, f_tab = 0.5 * a_rep * (1.0 - r) ** 2, a_rep * (1.0 - r)
+    out = {"workload": "dpd_fluid_786432_rho3_a25_gamma4.5_dt0.04", "n_particles": n}
+    for label, shear in (("rest", None), ("lees_edwards_0.01", 0.01)):
+        s = espp.System(box, n, cfg.types, cfg.bonds, precision=espp.ESPP_FP32, seed=11)
+        s.set_table_pair(1.0, u_tab, f_tab)
+        s.set_state(cfg.x, v, cfg.img)
+        if shear is not None:
+            s.set_lees_edwards(True, shear, 0.0)
+        s.build_neighbors(1.0, 0.4)
+        s.set_thermostat(espp.ESPP_THERMO_DPD, 1.0)
+        s.integrate(300, 0.04, 4.5, 1.0)
+        rb0 = s.n_rebuilds
+        steps = a.suite_steps
+        ms = _timed(s, steps, 0.04, 4.5, 1.0, sync)
+        rb = s.n_rebuilds - rb0
+        obs = []
+        for _ in range(10):  # after the timed region: averages over 10 snapshots
+            s.integrate(20, 0.04, 4.5, 1.0)
+            obs.append(s.observables())
+        mean = {k: float(np.mean([q[k] for q in obs])) for k in ("temperature", "pressure", "pxz")}
+        part = {"value": n * steps / (ms / 1e3), "unit": "particle-steps/s", "steps": steps,
+                "ms_per_step": ms / steps, "rebuilds": rb, **mean}
+        if shear is not None:
+            part["viscosity_estimate"] = -mean["pxz"] / shear
+        out[label] = part
+        s.close()
     return out
 
 

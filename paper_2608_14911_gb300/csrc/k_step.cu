@@ -156,7 +156,7 @@ __device__ __forceinline__ void dpd_term(const IntParams<T>* __restrict__ ip, co
 // inside the DPD cutoff, from the neighbours' velocity snapshot.
 // Entries with x code 3 cross a sheared face (Lees-Edwards): their x
 // difference is taken from the current offset in *le.
-template <class T, bool ENERGY, bool MULTI, bool FAST, bool DPD>
+template <class T, bool ENERGY, bool MULTI, bool FAST, bool DPD, bool LE>
 __device__ __forceinline__ void pair_loop(const DevSys<T>& s, const V4<T>* __restrict__ P, int i, int n,
                                           const V4<T>& xi, int ti, const PairRec<T>* pr1,
                                           T L0, T L1, T L2, T& fx, T& fy, T& fz, T& pe, T& vir, T& vxz,
@@ -221,7 +221,7 @@ __device__ __forceinline__ void pair_loop(const DevSys<T>& s, const V4<T>* __res
                 const int code = nbr_code(jj[q]);
                 int nz = 0;
                 T dx;
-                if ((code & 3) == 3) {
+                if (LE && (code & 3) == 3) {
                     nz = (code >> 4) == 1 ? 1 : -1;
                     dx = le_dx(xi.x, xj[q].x, nz, le->d, L0, le->inv_Lx);
                 } else {
@@ -244,7 +244,7 @@ __device__ __forceinline__ void pair_loop(const DevSys<T>& s, const V4<T>* __res
 
 // DPD thermostat forces on particle i as a pass of their own over the list,
 // for the learned potential, whose pair forces come from k_mlp.
-template <class T>
+template <class T, bool LE>
 __device__ __forceinline__ void dpd_loop(const DevSys<T>& s, const V4<T>* __restrict__ P, int i, int n,
                                          const V4<T>& xi, const DpdCtx<T>& c, const LeCtx<T>& le, T L0, T L1,
                                          T L2, T& fx, T& fy, T& fz) {
@@ -264,7 +264,7 @@ __device__ __forceinline__ void dpd_loop(const DevSys<T>& s, const V4<T>* __rest
             const V4<T> xj = ld4<T>(P + j);
             int nz = 0;
             T dx;
-            if ((code & 3) == 3) {
+            if (LE && (code & 3) == 3) {
                 nz = (code >> 4) == 1 ? 1 : -1;
                 dx = le_dx(xi.x, xj.x, nz, le.d, L0, le.inv_Lx);
             } else {
@@ -295,7 +295,7 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-template <class T, int MODE, bool ENERGY, bool FAST, bool DPD>
+template <class T, int MODE, bool ENERGY, bool FAST, bool DPD, bool LE>
 __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32_DPD : ESPP_STEP_MINB32) : 4) k_step(DevSys<T> s, int cur, double* __restrict__ f_out,
                                                unsigned long long next_cond) {
     Ctrl* c = s.ctrl;
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32
         // face also move apart by the change of delta since the build
         LeCtx<T> le;
         T skin_thr2 = s.half_skin2;
-        if (s.le_on) {
+        if (LE) {
             double q[2] = {0.0, 0.0};
             if ((threadIdx.x & 31) == 0) {
                 const double dnow = le_offset(s, g, step);
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32
                     pe = (T)fm.w;
                     vir = (T)s.mlp_w[i];
                 }
-                if (DPD) dpd_loop<T>(s, P, i, n, xi, dc, le, L0, L1, L2, fx, fy, fz);
+                if (DPD) dpd_loop<T, LE>(s, P, i, n, xi, dc, le, L0, L1, L2, fx, fy, fz);
             } else if (FAST) {
                 PairRec<T> pr;
                 pr.rc2 = s.pair[0].rc2;
@@ -384,15 +384,15 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32
                     pr.eps4 = s.pair[0].eps4;
                     pr.shift = s.pair[0].shift;
                 }
-                pair_loop<T, ENERGY, false, true, DPD>(s, P, i, n, xi, ti, &pr, L0, L1, L2, fx, fy, fz, pe, vir,
+                pair_loop<T, ENERGY, false, true, DPD, LE>(s, P, i, n, xi, ti, &pr, L0, L1, L2, fx, fy, fz, pe, vir,
                                                        vxz, &le, &dc);
             } else if (s.ntypes == 1) {
                 const PairRec<T> pr = s.pair[0];
                 if (pr.kind != 0 || DPD)
-                    pair_loop<T, ENERGY, false, false, DPD>(s, P, i, n, xi, ti, &pr, L0, L1, L2, fx, fy, fz, pe,
+                    pair_loop<T, ENERGY, false, false, DPD, LE>(s, P, i, n, xi, ti, &pr, L0, L1, L2, fx, fy, fz, pe,
                                                             vir, vxz, &le, &dc);
             } else {
-                pair_loop<T, ENERGY, true, false, DPD>(s, P, i, n, xi, ti, nullptr, L0, L1, L2, fx, fy, fz, pe,
+                pair_loop<T, ENERGY, true, false, DPD, LE>(s, P, i, n, xi, ti, nullptr, L0, L1, L2, fx, fy, fz, pe,
                                                        vir, vxz, &le, &dc);
             }
             // bonds (paper "Functionality": bonded interactions; FENE or tabulated)
@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32
                     const T dz = min_image(xi.z, xp.z, L2, H2);
                     const T dy = min_image(xi.y, xp.y, L1, H1);
                     T dx;
-                    if (s.le_on && (xi.z - xp.z > H2 || xi.z - xp.z < -H2)) {
+                    if (LE && (xi.z - xp.z > H2 || xi.z - xp.z < -H2)) {
                         // bond across a sheared face
                         dx = le_dx(xi.x, xp.x, xi.z - xp.z > H2 ? 1 : -1, le.d, L0, le.inv_Lx);
                     } else {
@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32
                 if (ENERGY) {
                     const double m = (double)ip->mass[ti];
                     // kinetic terms relative to the shear profile (Lees-Edwards)
-                    const double vxp = (double)v.x - (double)le.shear * ((double)xi.z - (double)H2);
+                    const double vxp = LE ? (double)v.x - (double)le.shear * ((double)xi.z - (double)H2) : (double)v.x;
                     acc[P_KE] = 0.5 * m * (vxp * vxp + (double)v.y * v.y + (double)v.z * v.z);
                     acc[P_KIN_XZ] = m * vxp * (double)v.z;
                     acc[P_PX] = m * v.x;
@@ -480,7 +480,7 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32
                     const T amp = ip->noise_amp[ti];
                     const T gm = ip->gamma * m;
                     // friction relative to the shear profile (Lees-Edwards)
-                    const T vxp = s.le_on ? v.x - le.shear * (xi.z - H2) : v.x;
+                    const T vxp = LE ? v.x - le.shear * (xi.z - H2) : v.x;
                     fx += -gm * vxp + amp * rx;
                     fy += -gm * v.y + amp * ry;
                     fz += -gm * v.z + amp * rz;
@@ -625,10 +625,15 @@ int Launch<T>::step(const DevSys<T>& s, int mode, bool energy, int cur, double* 
         k_vsnap<T><<<s.ntiles, TILE, 0, st>>>(s);
         extra += 1;
     }
-#define ESPP_STEP(M, E, D)                                                                  \
-    do {                                                                                    \
-        if (s.lj_fast) k_step<T, M, E, true, D><<<gr, TILE, 0, st>>>(s, cur, f_out, next_cond); \
-        else k_step<T, M, E, false, D><<<gr, TILE, 0, st>>>(s, cur, f_out, next_cond);     \
+#define ESPP_STEP_LE(M, E, D, LE)                                                            \
+    do {                                                                                     \
+        if (s.lj_fast) k_step<T, M, E, true, D, LE><<<gr, TILE, 0, st>>>(s, cur, f_out, next_cond); \
+        else k_step<T, M, E, false, D, LE><<<gr, TILE, 0, st>>>(s, cur, f_out, next_cond);     \
+    } while (0)
+#define ESPP_STEP(M, E, D)                            \
+    do {                                              \
+        if (s.le_on) ESPP_STEP_LE(M, E, D, true);     \
+        else ESPP_STEP_LE(M, E, D, false);            \
     } while (0)
     switch (mode) {
         case MODE_FORCES:
@@ -645,6 +650,7 @@ int Launch<T>::step(const DevSys<T>& s, int mode, bool energy, int cur, double* 
             break;
     }
 #undef ESPP_STEP
+#undef ESPP_STEP_LE
     return 1 + extra;
 }
 
@@ -658,11 +664,18 @@ void Launch<T>::set_cond(const DevSys<T>& s, unsigned long long cond, cudaStream
     k_set_cond<T><<<1, 1, 0, st>>>(s, cond);
 }
 
+// The two precisions compile as separate units (k_step_f32.cu, k_step_f64.cu)
+// that include this file with ESPP_STEP_PRECISION set, so they build in
+// parallel; compiled alone, this file instantiates both.
+#if !defined(ESPP_STEP_PRECISION) || ESPP_STEP_PRECISION == 32
 template int Launch<float>::step(const DevSys<float>&, int, bool, int, double*, unsigned long long, int, cudaStream_t);
-template int Launch<double>::step(const DevSys<double>&, int, bool, int, double*, unsigned long long, int, cudaStream_t);
 template void Launch<float>::prologue(const DevSys<float>&, int, int, cudaStream_t);
-template void Launch<double>::prologue(const DevSys<double>&, int, int, cudaStream_t);
 template void Launch<float>::set_cond(const DevSys<float>&, unsigned long long, cudaStream_t);
+#endif
+#if !defined(ESPP_STEP_PRECISION) || ESPP_STEP_PRECISION == 64
+template int Launch<double>::step(const DevSys<double>&, int, bool, int, double*, unsigned long long, int, cudaStream_t);
+template void Launch<double>::prologue(const DevSys<double>&, int, int, cudaStream_t);
 template void Launch<double>::set_cond(const DevSys<double>&, unsigned long long, cudaStream_t);
+#endif
 
 }  // namespace espp
