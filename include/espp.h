@@ -257,6 +257,29 @@ int espp_compute_forces(espp_h h, double* f_out, int where);
 #define ESPP_THERMO_DPD 1
 int espp_set_thermostat(espp_h h, int32_t kind, double rc);
 
+/* Pair-force method (paper "Performance optimizations": Verlet lists with a
+ * skin, and linked cells with the sub-cell decomposition of Yao et al.).
+ * ESPP_FORCES_VERLET (default): the Verlet list of espp_build_neighbors,
+ * rebuilt when a particle moved more than skin/2.  ESPP_FORCES_CELLS: no
+ * list; every step bins the particles into cells of edge rc / w (rc of
+ * espp_build_neighbors; the skin is not used) and sums the pair forces (and
+ * the DPD pair term) over the cell stencil; pays off where a list would be
+ * rebuilt every step or two.  Both give the same forces up to rounding order.
+ * espp_get_neighbors is unavailable, and espp_rdf_counts uses all pairs, in
+ * the cell mode.  The cells are rebuilt for the new method.  Errors:
+ * ESPP_ERR_ARG (unknown method), ESPP_ERR_STATE (the cell mode with the
+ * learned potential). */
+#define ESPP_FORCES_VERLET 0
+#define ESPP_FORCES_CELLS 1
+int espp_set_force_method(espp_h h, int32_t method);
+/* Times nsteps integrate steps (dt, gamma, kT) with each method from the
+ * current state, restores the state (as espp_set_state would, plus the step
+ * and simulated time) and keeps the faster method.  ms_per_step[2] (may be
+ * NULL) receives the times of ESPP_FORCES_VERLET and ESPP_FORCES_CELLS,
+ * *chosen (may be NULL) the method kept.  Synchronises. */
+int espp_tune_force_method(espp_h h, int32_t nsteps, double dt, double gamma, double kT, double* ms_per_step,
+                           int32_t* chosen);
+
 /* Lees-Edwards boundary conditions (paper "State of the field" and "New
  * features": Lees-Edwards): steady shear with the flow along x and the
  * gradient along z at shear rate gdot (shear_rate).  The periodic image of a

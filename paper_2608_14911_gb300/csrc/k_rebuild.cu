@@ -161,6 +161,9 @@ __global__ void __launch_bounds__(256) k_cellsort(DevSys<T> s) {
             }
             p[q + 1] = key;
         }
+        // list-free mode with DPD: the velocities in entry order as well
+        if (s.cells_mode && s.dpd)
+            for (int k = 0; k < e; ++k) s.cell_vel[s.cell_beg[h] + k] = s.vel[bits_as_int(p[k].w)];
     }
 }
 
@@ -527,6 +530,8 @@ int Launch<T>::rebuild(const DevSys<T>& s, int cur, bool resort, bool permute_fo
         k_copyback<T><<<gt, TILE, 0, st>>>(s, cur, permute_force ? 1 : 0);
         launched += 6;
     }
+    // list-free mode: the binning is all that is needed
+    if (s.cells_mode) return launched;
 #define ESPP_VERLET(W, E)                                                  \
     do {                                                                   \
         if (s.le_on) k_verlet<T, W, E, true><<<gt, TILE, 0, st>>>(s, cur);  \

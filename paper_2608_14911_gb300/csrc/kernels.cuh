@@ -125,6 +125,12 @@ template <class T> struct DevSys {
     int* mlp_uscan_part;
     int mlp_nuscan;     // scan blocks over the particles
     int dpd;            // DPD thermostat instead of Langevin (integration modes)
+    // list-free mode: particles binned every step, pair forces (with the DPD
+    // pair term) from the cell stencil into cpf / cpv, read by the step kernel
+    int cells_mode;
+    V4<T>* cpf;         // per slot: pair force and pair energy
+    V4<T>* cpv;         // per slot: pair virial and its xz part (energy pass)
+    V4<T>* cell_vel;    // velocities in cell-entry order (with DPD), written at binning
     V4<T>* vsnap;       // DPD: velocities at the force evaluation, read for the neighbours
     int tc_fault;       // host fault injection: the tensor-core kernel issues no MMA and
                         // its bounded mbarrier wait runs out (tests of the timeout path)
@@ -233,6 +239,8 @@ template <class T> struct Launch {
     static void prologue(const DevSys<T>& s, int cur, int grid, cudaStream_t st);
     static void set_cond(const DevSys<T>& s, unsigned long long cond, cudaStream_t st);
     static int mlp(const DevSys<T>& s, int cur, bool energy, cudaStream_t st);
+    // list-free pair forces from the cell stencil (k_cells.cu)
+    static int cellforce(const DevSys<T>& s, int cur, bool energy, bool dpd, cudaStream_t st);
     static int mlp_rev(const DevSys<T>& s, cudaStream_t st);
     // force-matching gradient of one frame (errors, tensor-core gradient,
     // deterministic reduction into grad and the loss)

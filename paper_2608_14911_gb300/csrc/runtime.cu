@@ -71,6 +71,8 @@ struct SystemBase {
     virtual int set_thermostat(int kind, double rc) = 0;
     virtual int set_lees_edwards(int on, double shear, double time) = 0;
     virtual int get_lees_edwards(int* on, double* shear, double* time) = 0;
+    virtual int set_force_method(int method) = 0;
+    virtual int tune_force_method(int nsteps, double dt, double gamma, double kT, double* ms, int* chosen) = 0;
 };
 
 struct PairHost {
@@ -354,9 +356,13 @@ class System : public SystemBase {
         return ESPP_OK;
     }
 
-    // cells per edge for stencil half width w: edge >= (rc + skin) / w
+    // reach of the cell stencil: the list radius rc + skin, or rc alone in
+    // the list-free mode (no skin: every step is binned)
+    double cell_reach() const { return rc_list + (d.cells_mode ? 0.0 : skin); }
+
+    // cells per edge for stencil half width w: edge >= reach / w
     int cell_count(int r, int c, int w) const {
-        return (int)std::floor(w * box[3 * r + c] / ((rc_list + skin) * (1.0 + 1e-6)));
+        return (int)std::floor(w * box[3 * r + c] / (cell_reach() * (1.0 + 1e-6)));
     }
 
     // Automatic choice: half cells (w = 2) pay off once a full cell holds about
@@ -455,7 +461,9 @@ class System : public SystemBase {
                     q.capU = (T)(uc - us);
                 }
             }
-        d.lj_fast = (ntypes == 1 && pair_h[0][0].kind == ESPP_LJ) ? 1 : 0;
+        // the list-free mode reads its pair forces from the cell kernel, which
+        // the general step-kernel variants take
+        d.lj_fast = (!d.cells_mode && ntypes == 1 && pair_h[0][0].kind == ESPP_LJ) ? 1 : 0;
         d.mlp_on = (pair_h[0][0].kind == ESPP_MLP) ? 1 : 0;
         if (d.mlp_on && !mlp_bits.empty()) {
             MlpWeights w;
@@ -1116,6 +1124,7 @@ class System : public SystemBase {
         if (!state_set) return fail(ESPP_ERR_STATE, "no state set");
         if (d.mlp_on && mlp_bits.empty()) return fail(ESPP_ERR_STATE, "learned potential selected but no weights set");
         if (d.mlp_on && d.le_on) return fail(ESPP_ERR_STATE, "Lees-Edwards is not available with the learned potential");
+        if (d.mlp_on && d.cells_mode) return fail(ESPP_ERR_STATE, "the learned potential needs the Verlet list");
         if (!cells_ready) return fail(ESPP_ERR_STATE, "call espp_build_neighbors first");
         int rcode = check_cutoffs();
         if (rcode) return rcode;
@@ -1139,6 +1148,7 @@ class System : public SystemBase {
 
     int get_neighbors(int64_t* row_ptr, int64_t* cols, int64_t cap) override {
         if (!row_ptr) return fail(ESPP_ERR_ARG, "row_ptr is required");
+        if (d.cells_mode) return fail(ESPP_ERR_STATE, "no Verlet list in the list-free force mode");
         int rcode = ensure_list();
         if (rcode) return rcode;
         const size_t n = (size_t)N;
@@ -1303,6 +1313,11 @@ class System : public SystemBase {
         rcode = set_clock(time_at(step0), dt, step0);
         if (rcode) return rcode;
         if (!f_valid) {
+            if (d.cells_mode && d.dpd) {
+                // the DPD pair term reads the cell-ordered velocities: bin again
+                Launch<T>::request_all(d, st);
+                launches += 1 + Launch<T>::rebuild(d, cur, false, false, st);
+            }
             launches += Launch<T>::step(d, MODE_INIT, false, cur, nullptr, 0, 0, st);
             f_valid = true;
         }
@@ -1350,14 +1365,14 @@ class System : public SystemBase {
                 if (rcode) return rcode;
                 CK(cudaGraphLaunch(cg->exec, st));
                 last_cg = cg;
-                launches += 1 + S * (1 + (d.mlp_on ? 3 : 0) + (d.dpd ? 1 : 0));
+                launches += 1 + S * (1 + (d.mlp_on ? 3 : 0) + ((d.cells_mode || d.dpd) ? 1 : 0));
                 p ^= (int)((fin ? (S - 1) : S) & 1);
                 next += S;
             }
             Ctrl c = read_ctrl();
             CK(cudaGetLastError());
             if (host_rebuilds >= 0)
-                launches += (REBUILD_LAUNCHES + (d.mlp_on ? 5 : 0)) *
+                launches += (REBUILD_LAUNCHES - (d.cells_mode ? 1 : 0) + (d.mlp_on ? 5 : 0)) *
                             ((int64_t)(c.n_rebuilds - (unsigned)rb0) - host_rebuilds);
             if (c.err & (ERRBIT_BOND | ERRBIT_NONFINITE | ERRBIT_TIMEOUT)) return status_from(c);
             if (c.err & ERRBIT_OVERFLOW) {
@@ -1449,7 +1464,7 @@ class System : public SystemBase {
         // exclusions on, bonded pairs are then not counted), else all pairs
         const double rl = rc_list + skin;
         bool use_list = false;
-        if (cells_ready && rmax <= rl) {
+        if (cells_ready && rmax <= rl && !d.cells_mode) {
             int rcode = ensure_list();
             if (rcode) return rcode;
             use_list = true;
@@ -1621,8 +1636,9 @@ class System : public SystemBase {
         CK(cudaMemcpy(d_ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice));
         // the list of the saved run was built from the build positions: rebuild
         // it from them (buffer 1 holds a copy), without a resort
+        // (list-free mode: bin the saved positions, which the last step binned)
         Launch<T>::request_all(d, st);
-        launches += 1 + Launch<T>::rebuild(d, 1, false, false, st);
+        launches += 1 + Launch<T>::rebuild(d, d.cells_mode ? 0 : 1, false, false, st);
         CK(cudaGetLastError());
         c = read_ctrl();
         if (c.err & ERRBIT_OVERFLOW) return fail(ESPP_ERR_LIST_OVERFLOW, "list capacity too small for the checkpoint");
@@ -1648,6 +1664,12 @@ class System : public SystemBase {
     int32_t list_capacity() override { return d.cap; }
     int64_t kernel_launches() override { return launches; }
     int list_stats(int64_t* total, int32_t* maxc) override {
+        if (d.cells_mode) {
+            // no list is built in the list-free mode
+            if (total) *total = 0;
+            if (maxc) *maxc = 0;
+            return ESPP_OK;
+        }
         int rcode = ensure_list();
         if (rcode) return rcode;
         std::vector<int> cnt((size_t)N);
@@ -1686,6 +1708,75 @@ class System : public SystemBase {
         clear_graphs();   // the thermostat is a template argument of captured kernels
         mass_dirty = true;  // the DPD constants live in the integrator parameters
         f_valid = false;
+        return ESPP_OK;
+    }
+
+    // ------------------------------------------------------- force method
+    int set_force_method(int method) override {
+        if (method != ESPP_FORCES_VERLET && method != ESPP_FORCES_CELLS)
+            return fail(ESPP_ERR_ARG, "unknown force method");
+        const int cells = method == ESPP_FORCES_CELLS ? 1 : 0;
+        if (cells && d.mlp_on) return fail(ESPP_ERR_STATE, "the learned potential needs the Verlet list");
+        if (cells == d.cells_mode) return ESPP_OK;
+        if (cells && !d.cpf) {
+            int rc;
+            if ((rc = alloc(&d.cpf, (size_t)N, allocs)) || (rc = alloc(&d.cpv, (size_t)N, allocs)) ||
+                (rc = alloc(&d.cell_vel, (size_t)N, allocs)))
+                return rc;
+        }
+        d.cells_mode = cells;
+        CK(upload_params());  // the fast Lennard-Jones variant is for the list
+        clear_graphs();
+        f_valid = false;
+        // the cells' edge depends on the method (the list's skin is no part of it)
+        return cells_ready ? build_neighbors(rc_list, skin) : ESPP_OK;
+    }
+
+    // Times nsteps steps with each method from the current state and keeps the
+    // faster; the state is then restored through set_state (so the next
+    // integrate recomputes the force of the current step).
+    int tune_force_method(int nsteps, double dt, double gamma, double kT, double* ms, int* chosen) override {
+        if (nsteps < 1) return fail(ESPP_ERR_ARG, "nsteps must be positive");
+        if (!state_set || !cells_ready) return fail(ESPP_ERR_STATE, "set the state and build the cells first");
+        const size_t n3 = 3 * (size_t)N;
+        std::vector<double> x(n3), v(n3);
+        std::vector<int32_t> img(n3);
+        int rcode = get_state(x.data(), v.data(), img.data(), ESPP_HOST);
+        if (rcode) return rcode;
+        const int64_t step0 = read_ctrl().step;
+        const double t0 = time_at(step0), dt0 = le_clk_h.dt;
+        auto restore = [&]() -> int {
+            int rc = set_state(x.data(), v.data(), img.data(), ESPP_HOST);
+            if (rc) return rc;
+            if ((rc = set_step(step0))) return rc;
+            return set_clock(t0, dt0, step0);
+        };
+        double t[2] = {INFINITY, INFINITY};
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        for (int m = 0; m < 2; ++m) {
+            if (m == ESPP_FORCES_CELLS && d.mlp_on) continue;
+            if ((rcode = set_force_method(m)) || (rcode = restore()) || (rcode = integrate(2, dt, gamma, kT))) break;
+            CK(cudaEventRecord(e0, st));
+            rcode = integrate(nsteps, dt, gamma, kT);
+            if (rcode) break;
+            CK(cudaEventRecord(e1, st));
+            CK(cudaEventSynchronize(e1));
+            float el = 0;
+            CK(cudaEventElapsedTime(&el, e0, e1));
+            t[m] = el / nsteps;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rcode) return rcode;
+        const int best = t[ESPP_FORCES_CELLS] < t[ESPP_FORCES_VERLET] ? ESPP_FORCES_CELLS : ESPP_FORCES_VERLET;
+        if ((rcode = set_force_method(best)) || (rcode = restore())) return rcode;
+        if (ms) {
+            ms[0] = t[0];
+            ms[1] = t[1];
+        }
+        if (chosen) *chosen = best;
         return ESPP_OK;
     }
 
@@ -1875,6 +1966,18 @@ int espp_set_lees_edwards(espp_h h, int32_t on, double shear_rate, double time) 
 }
 int espp_get_lees_edwards(espp_h h, int32_t* on, double* shear_rate, double* time) {
     return guarded(h, [&](espp::SystemBase& s) { return s.get_lees_edwards(on, shear_rate, time); });
+}
+int espp_set_force_method(espp_h h, int32_t method) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.set_force_method(method); });
+}
+int espp_tune_force_method(espp_h h, int32_t nsteps, double dt, double gamma, double kT, double* ms_per_step,
+                           int32_t* chosen) {
+    return guarded(h, [&](espp::SystemBase& s) {
+        int c = 0;
+        const int rc = s.tune_force_method(nsteps, dt, gamma, kT, ms_per_step, &c);
+        if (chosen) *chosen = c;
+        return rc;
+    });
 }
 int espp_set_thermostat(espp_h h, int32_t kind, double rc) {
     return guarded(h, [&](espp::SystemBase& s) { return s.set_thermostat(kind, rc); });

@@ -41,6 +41,8 @@ ESPP_MLP = 7
 MLP_NPARAMS = 6337
 ESPP_THERMO_LANGEVIN = 0
 ESPP_THERMO_DPD = 1
+ESPP_FORCES_VERLET = 0
+ESPP_FORCES_CELLS = 1
 
 ERROR_NAMES = {
     ESPP_ERR_ARG: "ESPP_ERR_ARG", ESPP_ERR_CUDA: "ESPP_ERR_CUDA",
@@ -63,7 +65,8 @@ EXPORTS = (
     "espp_rdf_counts_noalloc", "espp_set_resort_interval", "espp_mlp_set_weights",
     "espp_set_exclude_bonded", "espp_mlp_get_weights", "espp_mlp_train", "espp_mlp_loss_grad",
     "espp_cg_map", "espp_set_cell_subdivision", "espp_set_thermostat",
-    "espp_set_lees_edwards", "espp_get_lees_edwards",
+    "espp_set_lees_edwards", "espp_get_lees_edwards", "espp_set_force_method",
+    "espp_tune_force_method",
 )
 NOALLOC_MAX_BINS = 4096
 
@@ -145,6 +148,9 @@ def lib(path: str = LIB_PATH):
         "espp_set_thermostat": ([vp, ctypes.c_int32, ctypes.c_double], ctypes.c_int),
         "espp_set_lees_edwards": ([vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double], ctypes.c_int),
         "espp_get_lees_edwards": ([vp, ctypes.POINTER(ctypes.c_int32), dp, dp], ctypes.c_int),
+        "espp_set_force_method": ([vp, ctypes.c_int32], ctypes.c_int),
+        "espp_tune_force_method": ([vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp,
+                                    ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "espp_mlp_set_weights": ([vp, vp, i64], ctypes.c_int),
         "espp_set_exclude_bonded": ([vp, ctypes.c_int], ctypes.c_int),
         "espp_mlp_get_weights": ([vp, vp, i64], ctypes.c_int),
@@ -433,6 +439,19 @@ class System:
         on, sh, t = ctypes.c_int32(), ctypes.c_double(), ctypes.c_double()
         self._c(lib().espp_get_lees_edwards(self._h, ctypes.byref(on), ctypes.byref(sh), ctypes.byref(t)))
         return bool(on.value), sh.value, t.value
+
+    def set_force_method(self, method):
+        """ESPP_FORCES_VERLET (the list) or ESPP_FORCES_CELLS (list-free)."""
+        self._c(lib().espp_set_force_method(self._h, int(method)))
+
+    def tune_force_method(self, nsteps, dt, gamma, kT):
+        """Time both methods from the current state, keep the faster;
+        returns (ms per step [Verlet, cells], chosen method)."""
+        ms = (ctypes.c_double * 2)()
+        ch = ctypes.c_int32()
+        self._c(lib().espp_tune_force_method(self._h, int(nsteps), float(dt), float(gamma), float(kT), ms,
+                                             ctypes.byref(ch)))
+        return [ms[0], ms[1]], int(ch.value)
 
     def set_graph_chunk(self, steps):
         self._c(lib().espp_set_graph_chunk(self._h, int(steps)))
