@@ -16,6 +16,11 @@
 #include "kernels.cuh"
 #include "pair_terms.cuh"
 
+// minimum resident blocks per SM the FP32 register budget is fitted to
+#ifndef ESPP_CF_MINB32
+#define ESPP_CF_MINB32 8
+#endif
+
 namespace espp {
 
 template <class T>
@@ -59,37 +64,8 @@ __device__ __forceinline__ void cf_range(const DevSys<T>& s, const V4<T>* __rest
     }
 }
 
-// The cyclic x range lo..hi (lo >= -nc, hi < 2 nc) of one row as up to two
-// contiguous pieces of the entry array, with the image code of each piece
-// (1: the piece lies across the upper x face, 2: the lower).
-struct RowPieces {
-    int b0, e0, b1, e1, c0, c1;
-};
-__device__ __forceinline__ RowPieces row_pieces(const int* __restrict__ B, int base, int lo, int hi, int nc) {
-    RowPieces r;
-    r.b1 = r.e1 = 0;
-    r.c0 = r.c1 = 0;
-    if (lo < 0) {
-        r.b0 = __ldg(B + base + lo + nc);
-        r.e0 = __ldg(B + base + nc);
-        r.c0 = 2;
-        r.b1 = __ldg(B + base);
-        r.e1 = __ldg(B + base + hi + 1);
-    } else if (hi >= nc) {
-        r.b0 = __ldg(B + base + lo);
-        r.e0 = __ldg(B + base + nc);
-        r.b1 = __ldg(B + base);
-        r.e1 = __ldg(B + base + hi - nc + 1);
-        r.c1 = 1;
-    } else {
-        r.b0 = __ldg(B + base + lo);
-        r.e0 = __ldg(B + base + hi + 1);
-    }
-    return r;
-}
-
 template <class T, int W, bool ENERGY, bool MULTI, bool DPD, bool LE>
-__global__ void __launch_bounds__(TILE) k_cellforce(DevSys<T> s, int cur) {
+__global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? ESPP_CF_MINB32 : 2) k_cellforce(DevSys<T> s, int cur) {
     if (s.ctrl->abort) return;
     const V4<T>* __restrict__ P = s.pos[cur];  // type bits of the partners (several types)
     const V4<T>* __restrict__ E = s.cell_ent;
@@ -125,7 +101,8 @@ __global__ void __launch_bounds__(TILE) k_cellforce(DevSys<T> s, int cur) {
         const T inv_L0 = LE ? T(1) / L0 : T(0);
         // Lees-Edwards: delta of this step (binned with it) reduced into [0, Lx)
         const T le_d = LE ? (T)le_reduce(s.le_db[tl.rep], (double)L0) : T(0);
-        T fx = 0, fy = 0, fz = 0, pe = 0, vir = 0, vxz = 0;
+        T fx = 0, fy = 0, fz = 0, pe_ = 0, vir = 0, vxz = 0;
+        constexpr int NR = 2 * W + 1;
 #pragma unroll 1
         for (int dz = -W; dz <= W; ++dz) {
             int az = cz + dz, czc = 0;
@@ -144,40 +121,60 @@ __global__ void __launch_bounds__(TILE) k_cellforce(DevSys<T> s, int cur) {
                 if (xs >= L0) xs -= L0;
                 cxr = cf_cell_coord(xs, g.cells_per_len[0], nc0);
             }
-#pragma unroll 1
-            for (int dy = -W; dy <= W; ++dy) {
-                int ay = cy + dy, cyc = 0;
-                if (ay < 0) { ay += nc1; cyc = 2; }
-                else if (ay >= nc1) { ay -= nc1; cyc = 1; }
-                const T yo = (cyc & 1) ? xi.y - L1 : xi.y, yL = (cyc & 2) ? L1 : T(0);
+            // the plane's rows share one cyclic x range: up to two pieces
+            // [x0a, x0b] and [x1a, x1b] with their x image codes
+            int x0a = cxr - W, x0b = cxr + W, x1a = 0, x1b = -1, c0 = 0, c1 = 0;
+            if (x0a < 0) {
+                x1a = 0;
+                x1b = x0b;
+                x0a += nc0;
+                x0b = nc0 - 1;
+                c0 = 2;
+            } else if (x0b >= nc0) {
+                x1a = 0;
+                x1b = x0b - nc0;
+                x0b = nc0 - 1;
+                c1 = 1;
+            }
+            // all row ranges of the plane first, so their loads overlap
+            int pb[NR][2], pe[NR][2], cyc[NR];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                int ay = cy + r - W, c = 0;
+                if (ay < 0) { ay += nc1; c = 2; }
+                else if (ay >= nc1) { ay -= nc1; c = 1; }
+                cyc[r] = c;
                 const int base = g.cell_off + (az * nc1 + ay) * nc0;
-                const RowPieces rp = row_pieces(B, base, cxr - W, cxr + W, nc0);
-                if (sheared) {
-                    cf_range<T, ENERGY, MULTI, DPD, true, true>(s, E, VE, rp.b0, rp.e0, i, ti, ex, pr1, P, xi.x, yo,
-                                                                 zo, nd, yL, zL, L0, inv_L0, nz, &dc, fx, fy, fz, pe,
-                                                                 vir, vxz);
-                    cf_range<T, ENERGY, MULTI, DPD, true, true>(s, E, VE, rp.b1, rp.e1, i, ti, ex, pr1, P, xi.x, yo,
-                                                                 zo, nd, yL, zL, L0, inv_L0, nz, &dc, fx, fy, fz, pe,
-                                                                 vir, vxz);
-                    continue;
-                }
+                pb[r][0] = __ldg(B + base + x0a);
+                pe[r][0] = __ldg(B + base + x0b + 1);
+                pb[r][1] = x1b >= 0 ? __ldg(B + base + x1a) : 0;
+                pe[r][1] = x1b >= 0 ? __ldg(B + base + x1b + 1) : 0;
+            }
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const T yo = (cyc[r] & 1) ? xi.y - L1 : xi.y, yL = (cyc[r] & 2) ? L1 : T(0);
 #pragma unroll
                 for (int part = 0; part < 2; ++part) {
-                    const int pb = part ? rp.b1 : rp.b0, pe_ = part ? rp.e1 : rp.e0;
-                    const int cxc = part ? rp.c1 : rp.c0;
+                    if (sheared) {
+                        cf_range<T, ENERGY, MULTI, DPD, true, true>(s, E, VE, pb[r][part], pe[r][part], i, ti, ex, pr1,
+                                                                     P, xi.x, yo, zo, nd, yL, zL, L0, inv_L0, nz,
+                                                                     &dc, fx, fy, fz, pe_, vir, vxz);
+                        continue;
+                    }
+                    const int cxc = part ? c1 : c0;
                     const T xo = (cxc & 1) ? xi.x - L0 : xi.x, xL = (cxc & 2) ? L0 : T(0);
-                    if ((cxc | cyc | czc) == 0)
-                        cf_range<T, ENERGY, MULTI, DPD, false, false>(s, E, VE, pb, pe_, i, ti, ex, pr1, P, xo, yo,
-                                                                       zo, xL, yL, zL, L0, inv_L0, 0, &dc, fx, fy, fz,
-                                                                       pe, vir, vxz);
+                    if ((cxc | cyc[r] | czc) == 0)
+                        cf_range<T, ENERGY, MULTI, DPD, false, false>(s, E, VE, pb[r][part], pe[r][part], i, ti, ex,
+                                                                       pr1, P, xo, yo, zo, xL, yL, zL, L0, inv_L0, 0,
+                                                                       &dc, fx, fy, fz, pe_, vir, vxz);
                     else
-                        cf_range<T, ENERGY, MULTI, DPD, true, false>(s, E, VE, pb, pe_, i, ti, ex, pr1, P, xo, yo,
-                                                                      zo, xL, yL, zL, L0, inv_L0, 0, &dc, fx, fy, fz,
-                                                                      pe, vir, vxz);
+                        cf_range<T, ENERGY, MULTI, DPD, true, false>(s, E, VE, pb[r][part], pe[r][part], i, ti, ex,
+                                                                      pr1, P, xo, yo, zo, xL, yL, zL, L0, inv_L0, 0,
+                                                                      &dc, fx, fy, fz, pe_, vir, vxz);
                 }
             }
         }
-        s.cpf[i] = mk4<T>(fx, fy, fz, pe);
+        s.cpf[i] = mk4<T>(fx, fy, fz, pe_);
         if (ENERGY) s.cpv[i] = mk4<T>(vir, vxz, T(0), T(0));
     }
 }

@@ -371,6 +371,9 @@ class System : public SystemBase {
     // stencil loop costs more than it saves.  w = 2 also needs 5 cells per edge.
     int choose_subdivision() {
         if (cell_sub_req > 0) return cell_sub_req;
+        // the list-free force kernel streams shorter ranges from half cells
+        // and measured slower with them on every workload tried
+        if (d.cells_mode) return 1;
         double n = 0, cells = 0;
         bool fits2 = true;
         for (int r = 0; r < R; ++r) {
