@@ -548,7 +548,8 @@ def suite_dpd(a, sync, src, cfg, seed, langevin_ms):
 def suite_dpd_fluid(a, sync):
     """Groot-Warren DPD fluid: 786,432 particles at density 3 in a 64^3 box,
     soft repulsion F = 25 (1 - r) (tabulated) and the DPD thermostat (rc 1,
-    gamma 4.5, kT 1, dt 0.04), at rest and under Lees-Edwards shear 0.01."""
+    gamma 4.5, kT 1, dt 0.04), at rest and under Lees-Edwards shear 0.01; the
+    force method (Verlet list or list-free cells) is the tuner's choice."""
     from paper_2608_14911_gb300 import espp, inputs
     L, a_rep, n_tab = 64.0, 25.0, 1001
     box = np.array([L, L, L])
@@ -564,9 +565,12 @@ def suite_dpd_fluid(a, sync):
         s.set_state(cfg.x, v, cfg.img)
         if shear is not None:
             s.set_lees_edwards(True, shear, 0.0)
-        s.build_neighbors(1.0, 0.4)
+        s.build_neighbors(1.0, 0.6)
         s.set_thermostat(espp.ESPP_THERMO_DPD, 1.0)
         s.integrate(300, 0.04, 4.5, 1.0)
+        # Verlet list (skin 0.6) or list-free cells, whichever the tuner times faster
+        tuned_ms, method = s.tune_force_method(100, 0.04, 4.5, 1.0)
+        s.integrate(50, 0.04, 4.5, 1.0)
         rb0 = s.n_rebuilds
         steps = a.suite_steps
         ms = _timed(s, steps, 0.04, 4.5, 1.0, sync)
@@ -577,7 +581,9 @@ def suite_dpd_fluid(a, sync):
             obs.append(s.observables())
         mean = {k: float(np.mean([q[k] for q in obs])) for k in ("temperature", "pressure", "pxz")}
         part = {"value": n * steps / (ms / 1e3), "unit": "particle-steps/s", "steps": steps,
-                "ms_per_step": ms / steps, "rebuilds": rb, **mean}
+                "ms_per_step": ms / steps, "rebuilds": rb,
+                "force_method": "cells" if method == espp.ESPP_FORCES_CELLS else "verlet",
+                "tuner_ms_per_step": {"verlet": tuned_ms[0], "cells": tuned_ms[1]}, **mean}
         if shear is not None:
             part["viscosity_estimate"] = -mean["pxz"] / shear
         out[label] = part
