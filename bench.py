@@ -582,8 +582,9 @@ def suite_dpd_fluid(a, sync):
         mean = {k: float(np.mean([q[k] for q in obs])) for k in ("temperature", "pressure", "pxz")}
         part = {"value": n * steps / (ms / 1e3), "unit": "particle-steps/s", "steps": steps,
                 "ms_per_step": ms / steps, "rebuilds": rb,
-                "force_method": "cells" if method == espp.ESPP_FORCES_CELLS else "verlet",
-                "tuner_ms_per_step": {"verlet": tuned_ms[0], "cells": tuned_ms[1]}, **mean}
+                "force_shape": ("verlet_whole_cells", "verlet_half_cells", "cells")[method],
+                "tuner_ms_per_step": {"verlet_whole_cells": tuned_ms[0], "verlet_half_cells": tuned_ms[1],
+                                      "cells": tuned_ms[2]}, **mean}
         if shear is not None:
             part["viscosity_estimate"] = -mean["pxz"] / shear
         out[label] = part
@@ -645,6 +646,9 @@ def suite_batched(a, sync):
     s.set_wca(1.0, 1.0)
     s.integrate(1000, 0.002, 1.0, 1.0)
     s.integrate(200, 0.005, 1.0, 1.0)
+    # the autotuner picks the force path's shape for this batch
+    tuned_ms, shape = s.tune_force_method(100, 0.005, 1.0, 1.0)
+    s.integrate(50, 0.005, 1.0, 1.0)
     rb0 = s.n_rebuilds
     l0 = s.kernel_launches
     steps = a.suite_steps
@@ -656,6 +660,9 @@ def suite_batched(a, sync):
            "value": n * steps / (ms / 1e3), "unit": "particle-steps/s", "steps": steps,
            "ms_per_step": ms / steps, "rebuild_passes": s.n_rebuilds - rb0,
            "kernel_launches_per_step": (s.kernel_launches - l0) / steps,
+           "force_shape": ("verlet_whole_cells", "verlet_half_cells", "cells")[shape],
+           "tuner_ms_per_step": {"verlet_whole_cells": tuned_ms[0], "verlet_half_cells": tuned_ms[1],
+                                 "cells": tuned_ms[2]},
            "temperature_mean_over_replicas": float(temps.mean())}
     s.close()
     return out

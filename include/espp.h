@@ -272,11 +272,14 @@ int espp_set_thermostat(espp_h h, int32_t kind, double rc);
 #define ESPP_FORCES_VERLET 0
 #define ESPP_FORCES_CELLS 1
 int espp_set_force_method(espp_h h, int32_t method);
-/* Times nsteps integrate steps (dt, gamma, kT) with each method from the
- * current state, restores the state (as espp_set_state would, plus the step
- * and simulated time) and keeps the faster method.  ms_per_step[2] (may be
- * NULL) receives the times of ESPP_FORCES_VERLET and ESPP_FORCES_CELLS,
- * *chosen (may be NULL) the method kept.  Synchronises. */
+/* Autotuner of the force path's shape: times nsteps integrate steps (dt,
+ * gamma, kT) from the current state with each of three shapes, 0 = the
+ * Verlet list over whole cells, 1 = the Verlet list over half cells
+ * (subdivision 2), 2 = the list-free cell forces over whole cells; restores
+ * the state (as espp_set_state would, plus the step and simulated time) and
+ * keeps the fastest shape (method and subdivision).  ms_per_step[3] (may be
+ * NULL) receives the times (INFINITY for a shape whose cells do not fit the
+ * box), *chosen (may be NULL) the shape kept.  Synchronises. */
 int espp_tune_force_method(espp_h h, int32_t nsteps, double dt, double gamma, double kT, double* ms_per_step,
                            int32_t* chosen);
 

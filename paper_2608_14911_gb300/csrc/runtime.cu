@@ -1735,9 +1735,12 @@ class System : public SystemBase {
         return cells_ready ? build_neighbors(rc_list, skin) : ESPP_OK;
     }
 
-    // Times nsteps steps with each method from the current state and keeps the
-    // faster; the state is then restored through set_state (so the next
-    // integrate recomputes the force of the current step).
+    // Times nsteps steps of each candidate shape from the current state and
+    // keeps the fastest: the Verlet list over whole cells, the Verlet list
+    // over half cells, the list-free cell forces (whole cells).  The state is
+    // then restored through set_state (so the next integrate recomputes the
+    // force of the current step); a candidate whose cells do not fit the box
+    // is skipped.  The subdivision request of the caller is replaced.
     int tune_force_method(int nsteps, double dt, double gamma, double kT, double* ms, int* chosen) override {
         if (nsteps < 1) return fail(ESPP_ERR_ARG, "nsteps must be positive");
         if (!state_set || !cells_ready) return fail(ESPP_ERR_STATE, "set the state and build the cells first");
@@ -1754,13 +1757,24 @@ class System : public SystemBase {
             if ((rc = set_step(step0))) return rc;
             return set_clock(t0, dt0, step0);
         };
-        double t[2] = {INFINITY, INFINITY};
+        const int method_of[3] = {ESPP_FORCES_VERLET, ESPP_FORCES_VERLET, ESPP_FORCES_CELLS};
+        const int w_of[3] = {1, 2, 1};
+        auto apply = [&](int k) -> int {
+            // method first (it rebuilds the grid), then the subdivision
+            int rc = set_force_method(method_of[k]);
+            if (rc) return rc;
+            cell_sub_req = w_of[k];
+            return build_neighbors(rc_list, skin);
+        };
+        double t[3] = {INFINITY, INFINITY, INFINITY};
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
-        for (int m = 0; m < 2; ++m) {
-            if (m == ESPP_FORCES_CELLS && d.mlp_on) continue;
-            if ((rcode = set_force_method(m)) || (rcode = restore()) || (rcode = integrate(2, dt, gamma, kT))) break;
+        for (int k = 0; k < 3 && !rcode; ++k) {
+            if (method_of[k] == ESPP_FORCES_CELLS && d.mlp_on) continue;
+            const int rc = apply(k);
+            if (rc == ESPP_ERR_BOX_TOO_SMALL) continue;  // this shape does not fit
+            if ((rcode = rc) || (rcode = restore()) || (rcode = integrate(2, dt, gamma, kT))) break;
             CK(cudaEventRecord(e0, st));
             rcode = integrate(nsteps, dt, gamma, kT);
             if (rcode) break;
@@ -1768,17 +1782,18 @@ class System : public SystemBase {
             CK(cudaEventSynchronize(e1));
             float el = 0;
             CK(cudaEventElapsedTime(&el, e0, e1));
-            t[m] = el / nsteps;
+            t[k] = el / nsteps;
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         if (rcode) return rcode;
-        const int best = t[ESPP_FORCES_CELLS] < t[ESPP_FORCES_VERLET] ? ESPP_FORCES_CELLS : ESPP_FORCES_VERLET;
-        if ((rcode = set_force_method(best)) || (rcode = restore())) return rcode;
-        if (ms) {
-            ms[0] = t[0];
-            ms[1] = t[1];
-        }
+        int best = 0;
+        for (int k = 1; k < 3; ++k)
+            if (t[k] < t[best]) best = k;
+        if (!std::isfinite(t[best])) return fail(ESPP_ERR_BOX_TOO_SMALL, "no cell shape fits the box");
+        if ((rcode = apply(best)) || (rcode = restore())) return rcode;
+        if (ms)
+            for (int k = 0; k < 3; ++k) ms[k] = t[k];
         if (chosen) *chosen = best;
         return ESPP_OK;
     }

@@ -445,13 +445,14 @@ class System:
         self._c(lib().espp_set_force_method(self._h, int(method)))
 
     def tune_force_method(self, nsteps, dt, gamma, kT):
-        """Time both methods from the current state, keep the faster;
-        returns (ms per step [Verlet, cells], chosen method)."""
-        ms = (ctypes.c_double * 2)()
+        """Time the three shapes (Verlet/whole cells, Verlet/half cells,
+        list-free cells) from the current state and keep the fastest;
+        returns (ms per step of each, chosen shape index)."""
+        ms = (ctypes.c_double * 3)()
         ch = ctypes.c_int32()
         self._c(lib().espp_tune_force_method(self._h, int(nsteps), float(dt), float(gamma), float(kT), ms,
                                              ctypes.byref(ch)))
-        return [ms[0], ms[1]], int(ch.value)
+        return [ms[0], ms[1], ms[2]], int(ch.value)
 
     def set_graph_chunk(self, steps):
         self._c(lib().espp_set_graph_chunk(self._h, int(steps)))
