@@ -104,19 +104,26 @@ struct DpdCtx {
 // amp w theta_ij along e, w = 1 - r / rc.  e . v_ij and theta_ij are symmetric
 // in the pair, so both sides add exactly opposite forces.  nz: the partner is
 // the image above (+1) or below (-1) a sheared face (Lees-Edwards), whose
-// velocity is vj + nz le_shear Lz along x.
+// velocity is vj + nz le_shear Lz along x.  dpd_value is the magnitude
+// divided by r (the force on i is dpd_value * d).
 template <class T>
-__device__ __forceinline__ void dpd_term(const IntParams<T>* __restrict__ ip, const DpdCtx<T>& c, T dx, T dy,
-                                         T dz, T r2, const V4<T>& vj, T& fx, T& fy, T& fz, int nz = 0) {
+__device__ __forceinline__ T dpd_value(const IntParams<T>* __restrict__ ip, const DpdCtx<T>& c, T dx, T dy, T dz,
+                                       T r2, const V4<T>& vj, int nz = 0) {
     const T r = sqrt(r2), inv_r = T(1) / r;
     const T w = T(1) - r * ip->dpd_inv_rc;
     const T vjx = nz == 0 ? vj.x : vj.x + (T)nz * c.le_vs;
     const T ev = (dx * (c.vi.x - vjx) + dy * (c.vi.y - vj.y) + dz * (c.vi.z - vj.z)) * inv_r;
     const T th = dpd_theta<T>(c.seed, bits_as_int(c.vi.w), bits_as_int(vj.w), c.step);
-    const T mag = (-ip->gamma * w * w * ev + ip->dpd_amp * w * th) * inv_r;
-    fx += mag * dx;
-    fy += mag * dy;
-    fz += mag * dz;
+    return (-ip->gamma * w * w * ev + ip->dpd_amp * w * th) * inv_r;
+}
+
+template <class T>
+__device__ __forceinline__ void dpd_term(const IntParams<T>* __restrict__ ip, const DpdCtx<T>& c, T dx, T dy,
+                                         T dz, T r2, const V4<T>& vj, T& fx, T& fy, T& fz, int nz = 0) {
+    const T val = dpd_value<T>(ip, c, dx, dy, dz, r2, vj, nz);
+    fx += val * dx;
+    fy += val * dy;
+    fz += val * dz;
 }
 
 }  // namespace espp

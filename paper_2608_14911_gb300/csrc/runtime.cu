@@ -1368,7 +1368,7 @@ class System : public SystemBase {
                 if (rcode) return rcode;
                 CK(cudaGraphLaunch(cg->exec, st));
                 last_cg = cg;
-                launches += 1 + S * (1 + (d.mlp_on ? 3 : 0) + ((d.cells_mode || d.dpd) ? 1 : 0));
+                launches += 1 + S * step_kernels();
                 p ^= (int)((fin ? (S - 1) : S) & 1);
                 next += S;
             }
@@ -1643,6 +1643,7 @@ class System : public SystemBase {
         Launch<T>::request_all(d, st);
         launches += 1 + Launch<T>::rebuild(d, d.cells_mode ? 0 : 1, false, false, st);
         CK(cudaGetLastError());
+        rebuild_pending = false;  // the loaded state is complete
         c = read_ctrl();
         if (c.err & ERRBIT_OVERFLOW) return fail(ESPP_ERR_LIST_OVERFLOW, "list capacity too small for the checkpoint");
         // restore the pending requests and the rebuild counter of the saved run
@@ -1712,6 +1713,14 @@ class System : public SystemBase {
         mass_dirty = true;  // the DPD constants live in the integrator parameters
         f_valid = false;
         return ESPP_OK;
+    }
+
+    // kernels of one step inside the step graphs (Launch::step)
+    int step_kernels() const {
+        int k = 1 + (d.mlp_on ? 3 : 0);
+        if (d.cells_mode) k += 1;  // cell-stencil forces
+        else if (d.dpd) k += 1;    // velocity snapshot
+        return k;
     }
 
     // ------------------------------------------------------- force method
