@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-suite", action="store_true",
                     help="skip the secondary workloads (4M LJ, 512 replicas, learned CG)")
     ap.add_argument("--suite-steps", type=int, default=1000)
+    ap.add_argument("--suite-only", default="",
+                    help="comma-separated names of the suite entries to run (default: all)")
     ap.add_argument("--cg-frames", type=int, default=32)
     ap.add_argument("--cg-epochs", type=int, default=10)
     ap.add_argument("--cg-batch", type=int, default=4)
@@ -252,7 +254,7 @@ def step_kernel_bytes(n, list_entries, precision):
 def step_kernel_digest():
     """Digest of the sources the step kernel is compiled from."""
     h = hashlib.sha256()
-    for f in ("k_step.cu", "kernels.cuh", "common.cuh", "philox.cuh"):
+    for f in ("k_step.cu", "pair_terms.cuh", "kernels.cuh", "common.cuh", "philox.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2608_14911_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -457,6 +459,8 @@ def run_ours(a):
                          ("lj4m", lambda o: o.update(suite_lj4m(a, barrier, peaks))),
                          ("batched512", lambda o: o.update(suite_batched(a, barrier))),
                          ("learned_cg", lambda o: suite_learned_cg(a, barrier, o))):
+            if a.suite_only and name not in a.suite_only.split(","):
+                continue
             part = {}
             t0 = time.perf_counter()
             try:
