@@ -31,6 +31,9 @@
 #ifndef ESPP_STEP_MINB32_DPD  // the same for the DPD variants
 #define ESPP_STEP_MINB32_DPD 10
 #endif
+#ifndef ESPP_STEP_LATE  // loads issued after the pair loop: 1 bond partners, 2 velocity and build position
+#define ESPP_STEP_LATE 1  // KG 1M FP32: 64.0 us (1), 65.8 (0), 66.9 (3) at 10 blocks per SM
+#endif
 #ifndef ESPP_STEP_PREFETCH
 #define ESPP_STEP_PREFETCH 2  // request the next batch's list groups early (see pair_loop)
 #endif
@@ -241,11 +244,19 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32
             const int n = s.nbr_cnt[i];
             const bool bonded = s.bond.kind != 0;
             const int2 b = bonded ? s.bond_slot[i] : make_int2(-1, -1);
-            V4<T> v = s.vel[i];
-            V4<T> xbi;
-            if (MODE == MODE_STEP && (FAST || !s.cells_mode)) xbi = s.xb[i];
-            const V4<T> xp0 = b.x >= 0 ? ld4<T>(P + b.x) : xi;
-            const V4<T> xp1 = b.y >= 0 ? ld4<T>(P + b.y) : xi;
+            // loads the pair loop does not need, issued before it (latency
+            // hidden behind the loop) or after it (fewer registers held)
+            constexpr bool LATE_BOND = (ESPP_STEP_LATE & 1) != 0;
+            constexpr bool LATE_VEL = (ESPP_STEP_LATE & 2) != 0 && !DPD;
+            V4<T> v, xbi, xp0, xp1;
+            if (!LATE_VEL) {
+                v = s.vel[i];
+                if (MODE == MODE_STEP && (FAST || !s.cells_mode)) xbi = s.xb[i];
+            }
+            if (!LATE_BOND) {
+                xp0 = b.x >= 0 ? ld4<T>(P + b.x) : xi;
+                xp1 = b.y >= 0 ? ld4<T>(P + b.y) : xi;
+            }
             DpdCtx<T> dc;
             if (DPD) {
                 dc.vi = v;
@@ -296,6 +307,14 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32
             } else {
                 pair_loop<T, ENERGY, true, false, DPD, LE>(s, P, i, n, xi, ti, nullptr, L0, L1, L2, fx, fy, fz, pe,
                                                        vir, vxz, &le, &dc);
+            }
+            if (LATE_VEL) {
+                v = s.vel[i];
+                if (MODE == MODE_STEP && (FAST || !s.cells_mode)) xbi = s.xb[i];
+            }
+            if (LATE_BOND) {
+                xp0 = b.x >= 0 ? ld4<T>(P + b.x) : xi;
+                xp1 = b.y >= 0 ? ld4<T>(P + b.y) : xi;
             }
             // bonds (paper "Functionality": bonded interactions; FENE or tabulated)
             double blen = 0.0, bcnt = 0.0;
