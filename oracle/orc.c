@@ -906,7 +906,9 @@ static void add_langevin(int64_t n, const double* L, const double* x, const doub
  * and the pair forces cancel exactly; the velocity is the one present at the
  * force evaluation (as for the Langevin friction).  Under Lees-Edwards the
  * image of j across the z faces moves at k gdot Lz along x: v_ij is taken
- * against that image's velocity. */
+ * against that image's velocity.  Reading: the thermostat acts on the pairs
+ * of the pair interaction, so with 1-2 bonded exclusions on (the learned CG
+ * model) bonded pairs get no DPD force either. */
 static int orc_dpd_on = 0;
 static double orc_dpd_rc = 0.0;
 void orc_set_dpd(int on, double rc) {
@@ -924,15 +926,19 @@ double orc_dpd_theta(uint64_t seed, int64_t a, int64_t b, int64_t step) {
     return sqrt(12.0) * orc_uniform_centered(out[0]);
 }
 
-static void add_dpd(int64_t n, const double* L, const double* x, const double* v, double* f, double dt,
-                    double gamma, double kT, uint64_t seed, int64_t step) {
+static void add_dpd(int64_t n, const double* L, const double* x, const double* v, int64_t nbonds,
+                    const int64_t* bonds, double* f, double dt, double gamma, double kT, uint64_t seed,
+                    int64_t step) {
     if (gamma == 0.0 && kT == 0.0) return;
     const double rc = orc_dpd_rc, sigma = sqrt(2.0 * gamma * kT), inv_sqdt = 1.0 / sqrt(dt);
+    adj_t adj;
+    adj_build(&adj, n, nbonds, bonds);
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < n; ++i) {
         double fi[3] = {0.0, 0.0, 0.0};
         for (int64_t j = 0; j < n; ++j) {
             if (j == i) continue;
+            if (orc_exclude_bonded && bonded_to(&adj, i, j)) continue;
             double d[3];
             int nz;
             min_image_le(x + 3 * i, x + 3 * j, L, d, &nz);
@@ -949,13 +955,14 @@ static void add_dpd(int64_t n, const double* L, const double* x, const double* v
         }
         for (int c = 0; c < 3; ++c) f[3 * i + c] += fi[c];
     }
+    adj_free(&adj);
 }
 
 /* the thermostat of the force step: DPD when selected, else Langevin */
 static void add_thermostat(int64_t n, const double* L, const double* x, const double* v, const int32_t* type,
-                           const double* mass_of_type, double* f, double dt, double gamma, double kT,
-                           uint64_t seed, int64_t step) {
-    if (orc_dpd_on) add_dpd(n, L, x, v, f, dt, gamma, kT, seed, step);
+                           const double* mass_of_type, int64_t nbonds, const int64_t* bonds, double* f,
+                           double dt, double gamma, double kT, uint64_t seed, int64_t step) {
+    if (orc_dpd_on) add_dpd(n, L, x, v, nbonds, bonds, f, dt, gamma, kT, seed, step);
     else add_langevin(n, L, x, v, type, mass_of_type, f, dt, gamma, kT, seed, step);
 }
 
@@ -979,7 +986,7 @@ int orc_integrate(int64_t n, const double* L, double* x, double* v, int32_t* img
     if (!f_valid) {
         st = orc_forces(n, L, x, type, ntypes, pair_params, nbonds, bonds, bond_params, f, en);
         if (st) return st;
-        add_thermostat(n, L, x, v, type, mass_of_type, f, dt, gamma, kT, seed, step0);
+        add_thermostat(n, L, x, v, type, mass_of_type, nbonds, bonds, f, dt, gamma, kT, seed, step0);
     }
     for (int64_t s = step0 + 1; s <= step0 + nsteps; ++s) {
         orc_le_time = t0 + (double)(s - step0) * dt;
@@ -999,7 +1006,7 @@ int orc_integrate(int64_t n, const double* L, double* x, double* v, int32_t* img
         }
         st = orc_forces(n, L, x, type, ntypes, pair_params, nbonds, bonds, bond_params, f, en);
         if (st) return st;
-        add_thermostat(n, L, x, v, type, mass_of_type, f, dt, gamma, kT, seed, s);
+        add_thermostat(n, L, x, v, type, mass_of_type, nbonds, bonds, f, dt, gamma, kT, seed, s);
 #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; ++i) {
             double m = mass_of_type[type[i]];

@@ -261,3 +261,56 @@ def test_mlp_training_is_deterministic_and_learns_a_known_potential():
     s.set_state(X[1])
     f = s.compute_forces()
     assert rel_rms(f, Y[1]) < 0.25
+
+
+def test_mlp_with_dpd_matches_oracle():
+    # the learned potential with all-zero weights (no pair force at all) and
+    # the DPD thermostat: the DPD pass over the list (1-2 bonded pairs
+    # excluded, as in the list) and the bonds give the oracle's trajectory
+    c = _cg_system(20, 30, seed=7)
+    zeros = np.zeros(espp.MLP_NPARAMS)
+    s = _mlp_system(c, espp.to_bf16_bits(zeros), prec=espp.ESPP_FP64, seed=9)
+    v = I.maxwell_velocities(c.n, 1.0, seed=9)
+    s.set_state(c.x, v, c.img)
+    s.build_neighbors(RC, SKIN)
+    s.set_thermostat(espp.ESPP_THERMO_DPD, 2.0)
+    s.integrate(60, 0.005, 4.5, 1.0)
+    x, vv, img = s.get_state()
+    rmax, ub, fb = _bond_table()
+    O.set_mlp(zeros, RC)
+    O.set_table(7, rmax, ub, fb)
+    O.set_exclude_bonded(True)
+    O.set_dpd(True, 2.0)
+    try:
+        model = O.Model(1, {(0, 0): ("mlp", RC)}, ("table", 7))
+        st = O.State(c.box, c.x, v, c.img, c.types, c.bonds)
+        O.integrate(model, st, 60, 0.005, 4.5, 1.0, seed=9)
+    finally:
+        O.set_exclude_bonded(False)
+        O.set_dpd(False)
+    box = c.box
+    assert np.abs((x + img * box) - (st.x + st.img * box)).max() < 1e-10
+    assert np.abs(vv - st.v).max() < 1e-9
+    # with real weights the pass conserves momentum as well
+    bits, _ = _weights(3)
+    s2 = _mlp_system(c, bits, seed=4)
+    v2 = v + np.array([0.05, -0.02, 0.01])
+    s2.set_state(c.x, v2, c.img)
+    s2.build_neighbors(RC, SKIN)
+    s2.set_thermostat(espp.ESPP_THERMO_DPD, 2.0)
+    s2.integrate(200, 0.005, 4.5, 1.0)
+    _, v3, _ = s2.get_state()
+    assert np.abs(v3.sum(axis=0) - v2.sum(axis=0)).max() < 1e-3 * c.n ** 0.5
+
+
+def test_mlp_refuses_sheared_and_list_free_modes():
+    c = _cg_system(seed=2)
+    bits, _ = _weights(1)
+    s = _mlp_system(c, bits)
+    s.set_state(c.x, None, c.img)
+    s.build_neighbors(RC, SKIN)
+    for call in (lambda: s.set_lees_edwards(True, 0.1, 0.0), lambda: s.set_force_method(espp.ESPP_FORCES_CELLS)):
+        with pytest.raises(espp.EsppError) as e:
+            call()
+        assert e.value.code == espp.ESPP_ERR_STATE
+    s.compute_forces()

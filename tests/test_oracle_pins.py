@@ -845,3 +845,25 @@ def test_le_rg2_of_a_chain_across_the_sheared_face(le_on):
         rg.append(((pos - pos.mean(axis=0)) ** 2).sum(axis=1).mean())
     o = O.observables(KG, st)
     assert abs(o["rg2"] - np.mean(rg)) < 1e-9 * np.mean(rg)
+
+
+def test_dpd_skips_excluded_bonded_pairs(dpd_on):
+    # with 1-2 exclusions on (the learned CG model) a bonded pair gets no DPD
+    # force: a lone FENE dimer moves exactly as without the thermostat
+    dpd_on(1.2)
+    box = np.array([10.0, 10.0, 10.0])
+    x = np.array([[5.0, 5.0, 5.0], [5.9, 5.2, 5.1]])
+    v = np.array([[0.4, -0.3, 0.1], [-0.2, 0.5, 0.3]])
+    bonds = np.array([[0, 1]])
+    fene = O.Model(1, {}, ("fene", 30.0, 1.5))
+    runs = {}
+    try:
+        for excl, gamma in ((True, 4.5), (True, 0.0), (False, 4.5)):
+            O.set_exclude_bonded(excl)
+            st = O.State(box, x, v, None, None, bonds)
+            O.integrate(fene, st, 50, 0.005, gamma, 0.0, seed=3)
+            runs[(excl, gamma)] = st.v.copy()
+    finally:
+        O.set_exclude_bonded(False)
+    assert np.array_equal(runs[(True, 4.5)], runs[(True, 0.0)])
+    assert np.abs(runs[(False, 4.5)] - runs[(True, 0.0)]).max() > 1e-3
