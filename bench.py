@@ -414,6 +414,8 @@ def run_ours(a):
     fp64 = None
     if not a.no_fp64:
         s64, _ = copy_system(s, cfg, espp.ESPP_FP64, seed)
+        if a.direct:
+            s64.set_graph_chunk(0)
         s64.integrate(max(3, a.warmup // 5), 0.005, 1.0, 1.0)
         barrier()
         ms64 = max_over_ranks(timed_integrate(s64, a.fp64_steps, barrier))
