@@ -1540,8 +1540,11 @@ class System : public SystemBase {
         std::vector<int> sid, req;
         std::vector<double> ledb;
         int rcode;
+        // the list-free mode keeps no build positions: the positions, binned
+        // at this step, serve (a handle with a list rebuilds from them)
         if ((rcode = dl(pos, d.pos[cur], n)) || (rcode = dl(vel, d.vel, n)) || (rcode = dl(frc, d.frc, n)) ||
-            (rcode = dl(xb, d.xb, n)) || (rcode = dl(img, d.img, n)) || (rcode = dl(bs, d.bond_slot, n)) ||
+            (rcode = dl(xb, d.cells_mode ? d.pos[cur] : d.xb, n)) || (rcode = dl(img, d.img, n)) ||
+            (rcode = dl(bs, d.bond_slot, n)) ||
             (rcode = dl(sid, d.slot_of_id, n)) || (rcode = dl(req, d.req, (size_t)R)) ||
             (rcode = dl(ledb, d.le_db, (size_t)R)))
             return rcode;

@@ -214,3 +214,28 @@ def test_cell_mode_errors():
     s.integrate(5, 0.005, 1.0, 0.72)
     assert s.list_stats()[0] > 0
     s.close()
+
+
+def test_checkpoint_moves_between_force_methods(tmp_path):
+    # a state saved in the list-free mode resumes on a Verlet-list handle and
+    # the other way round, with forces equal to the oracle's at the saved state
+    case = kg_case()
+    path = str(tmp_path / "x.ckpt")
+    for src, dst in ((CELLS, VERLET), (VERLET, CELLS)):
+        a = case.system(FP64, seed=12, build=False)
+        a.set_force_method(src)
+        a.build_neighbors(case.rc_list, case.skin)
+        a.integrate(77, 0.005, 1.0, 1.0)
+        a.checkpoint_save(path)
+        x, _, img = a.get_state()
+        b = case.system(FP64, seed=12, build=False)
+        b.set_force_method(dst)
+        b.build_neighbors(case.rc_list, case.skin)
+        b.checkpoint_load(path)
+        f = b.compute_forces()
+        fo, _ = O.forces(case.model, case.cfg.box, x, case.cfg.types, case.cfg.bonds)
+        assert rel_rms(f, fo) <= FORCE_TOL[FP64]
+        b.integrate(30, 0.005, 1.0, 1.0)
+        assert b.error_word == 0
+        a.close()
+        b.close()
