@@ -134,8 +134,9 @@ int espp_system_destroy(espp_h h);
 /* Set positions x (n*3; wrapped into the box, crossings added to the image
  * counters), velocities v (n*3 or NULL = zero) and image counters img (n*3 or
  * NULL = zero), in id order, from host or device memory (where).  Marks the
- * neighbour list and the stored force stale.  Paper "Example usage":
- * addParticles(pos, v). */
+ * neighbour list and the stored force stale.  A non-finite position or
+ * velocity fails the call with ESPP_ERR_ARG and leaves the handle without a
+ * state.  Paper "Example usage": addParticles(pos, v). */
 int espp_set_state(espp_h h, const double* x, const double* v, const int32_t* img, int where);
 
 /* Read positions (wrapped into [0,L)), velocities and image counters in id

@@ -22,9 +22,16 @@ __global__ void __launch_bounds__(TILE) k_set_state(DevSys<T> s, const double* _
         const int i = tl.start + threadIdx.x;  // slot == global id
         T p[3];
         int im[3];
+        bool bad = false;
         for (int d = 0; d < 3; ++d) {
             const double L = (double)g.L[d];
-            const double xd = x[3 * (size_t)i + d];
+            double xd = x[3 * (size_t)i + d];
+            // a non-finite coordinate is reported (the call fails) and kept out
+            // of the arithmetic below
+            if (!isfinite(xd)) {
+                bad = true;
+                xd = 0.0;
+            }
             const double fl = floor(xd / L);
             double w = xd - fl * L;
             int k = (int)fl + (img ? img[3 * (size_t)i + d] : 0);
@@ -38,9 +45,14 @@ __global__ void __launch_bounds__(TILE) k_set_state(DevSys<T> s, const double* _
         const int local = i - g.p_off;
         s.pos[cur][i] = mk4<T>(p[0], p[1], p[2], int_bits_as(T(0), types ? types[i] : 0));
         s.xb[i] = s.pos[cur][i];
-        const T vx = v ? (T)v[3 * (size_t)i] : T(0);
-        const T vy = v ? (T)v[3 * (size_t)i + 1] : T(0);
-        const T vz = v ? (T)v[3 * (size_t)i + 2] : T(0);
+        T vx = v ? (T)v[3 * (size_t)i] : T(0);
+        T vy = v ? (T)v[3 * (size_t)i + 1] : T(0);
+        T vz = v ? (T)v[3 * (size_t)i + 2] : T(0);
+        if (!(isfinite(vx) && isfinite(vy) && isfinite(vz))) {
+            bad = true;
+            vx = vy = vz = T(0);
+        }
+        if (bad) atomicOr(&s.ctrl->err, ERRBIT_NONFINITE);
         s.vel[i] = mk4<T>(vx, vy, vz, int_bits_as(T(0), local));
         s.frc[i] = mk4<T>(T(0), T(0), T(0), T(0));
         s.img[i] = make_int4(im[0], im[1], im[2], 0);

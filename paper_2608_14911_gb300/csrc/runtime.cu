@@ -582,6 +582,16 @@ class System : public SystemBase {
         launches += 2;
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(st));
+        {
+            Ctrl c = read_ctrl();
+            if (c.err & ERRBIT_NONFINITE) {
+                // refuse the state: clear the flag, keep no half-set state
+                c.err = 0;
+                CK(cudaMemcpy(d_ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice));
+                state_set = false;
+                return fail(ESPP_ERR_ARG, "non-finite position or velocity");
+            }
+        }
         state_set = true;
         f_valid = false;
         rebuild_pending = true;

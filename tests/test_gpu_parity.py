@@ -538,3 +538,37 @@ def test_cg_map_matches_numpy_mapping():
     u = np.mod(u, box)
     assert np.abs(xs.cpu().numpy() - u).max() < 1e-9
     assert np.abs(fs.cpu().numpy() - f.reshape(-1, 4, 3).sum(axis=1)).max() < 1e-9
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_non_finite_input_and_runaway_are_reported(prec):
+    case = kg_case()
+    c = case.cfg
+    s = case.system(prec)
+    # a non-finite input is refused and leaves no state behind
+    for bad_x, bad_v in ((True, False), (False, True)):
+        x, v = c.x.copy(), case.v.copy()
+        if bad_x:
+            x[5, 1] = np.nan
+        if bad_v:
+            v[7, 2] = np.inf
+        with pytest.raises(espp.EsppError) as e:
+            s.set_state(x, v, c.img)
+        assert e.value.code == espp.ESPP_ERR_ARG
+        with pytest.raises(espp.EsppError) as e:
+            s.integrate(1, 0.005, 1.0, 1.0)
+        assert e.value.code == espp.ESPP_ERR_STATE
+    # a finite but runaway velocity carries a particle beyond any box in one
+    # step: the step kernels stop and the call reports it
+    v = case.v.copy()
+    v[11] = [1e35, 0.0, 0.0]
+    s.set_state(c.x, v, c.img)
+    s.build_neighbors(case.rc_list, case.skin)
+    with pytest.raises(espp.EsppError) as e:
+        s.integrate(5, 0.005, 1.0, 1.0)
+    assert e.value.code == espp.ESPP_ERR_NONFINITE
+    # a fresh state clears the condition
+    s.set_state(c.x, case.v, c.img)
+    s.integrate(5, 0.005, 1.0, 1.0)
+    assert s.error_word == 0
+    s.close()
