@@ -284,16 +284,17 @@ def _free_variance_closed_form(nsteps, dt, gamma, kT, m=1.0):
     return np.array(var_full)
 
 
-@pytest.mark.parametrize("gamma,dt", [(10.0, 0.05), (1.0, 0.005)])
-def test_free_particle_langevin_closed_form(gamma, dt):
+@pytest.mark.parametrize("gamma,dt,m", [(10.0, 0.05, 1.0), (1.0, 0.005, 1.0), (10.0, 0.05, 2.5)])
+def test_free_particle_langevin_closed_form(gamma, dt, m):
     n = 200000
     kT = 1.7
     nsteps = 12 if gamma * dt > 0.1 else 3
     st = O.State(np.array([50.0, 50.0, 50.0]), np.full((n, 3), 25.0))
-    expect = _free_variance_closed_form(nsteps, dt, gamma, kT)
+    model = O.Model(1, {}, masses=[m])
+    expect = _free_variance_closed_form(nsteps, dt, gamma, kT, m)
     got = []
     for s in range(nsteps):
-        O.integrate(FREE, st, 1, dt, gamma, kT, seed=123)
+        O.integrate(model, st, 1, dt, gamma, kT, seed=123)
         got.append((st.v ** 2).mean())
     got = np.array(got)
     # sample variance of 3n draws; the uniform noise has kurtosis < 3 so the
@@ -302,7 +303,7 @@ def test_free_particle_langevin_closed_form(gamma, dt):
     assert np.all(np.abs(got - expect) < 5 * err), (got, expect)
     if gamma * dt > 0.1:
         # equilibrium: full-step velocities carry exactly kT/m
-        assert abs(expect[-1] - kT) < 1e-6 * kT
+        assert abs(expect[-1] - kT / m) < 1e-6 * kT / m
     assert abs(st.v.mean()) < 5 * np.sqrt(expect[-1] / (3 * n))
 
 
