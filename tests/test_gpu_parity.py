@@ -617,3 +617,31 @@ def test_long_run_statistics_match_oracle():
     # far more than these 60 time units; two oracle seeds differ by 5 block
     # errors)
     s.close()
+
+
+@pytest.mark.parametrize("thermo", ["langevin", "dpd"])
+def test_two_masses_match_oracle(thermo):
+    # a particle type of mass 2.5 next to mass 1: friction, noise amplitude,
+    # kicks and kinetic energy all carry the mass
+    case = two_type_case()
+    c = case.cfg
+    s = case.system(FP64, seed=27)
+    s.set_mass(1, 2.5)
+    if thermo == "dpd":
+        s.set_thermostat(espp.ESPP_THERMO_DPD, 1.2)
+        O.set_dpd(True, 1.2)
+    try:
+        s.integrate(120, 0.005, 1.3, 1.0)
+        x, v, img = s.get_state()
+        model = O.Model(2, case.pair, None, masses=[1.0, 2.5])
+        st = case.oracle_state()
+        O.integrate(model, st, 120, 0.005, 1.3, 1.0, seed=27)
+    finally:
+        O.set_dpd(False)
+    box = c.box
+    assert np.abs(_unwrapped(x, img, box) - _unwrapped(st.x, st.img, box)).max() < 1e-10
+    assert np.abs(v - st.v).max() < 1e-9
+    o, oo = s.observables(), O.observables(model, st)
+    for k in ("ke", "temperature", "px", "pressure"):
+        assert abs(o[k] - oo[k]) <= 1e-9 * max(1.0, abs(oo[k])), (k, o[k], oo[k])
+    s.close()
