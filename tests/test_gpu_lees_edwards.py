@@ -278,3 +278,33 @@ def test_le_errors():
     s.set_lees_edwards(False)
     s.integrate(5, 0.005, 1.0, 0.72)
     s.close()
+
+
+@pytest.mark.parametrize("method", [espp.ESPP_FORCES_VERLET, espp.ESPP_FORCES_CELLS])
+def test_le_two_types_fp64_matches_oracle(method, oracle_le):
+    # the general (several types) step-kernel variant across sheared faces,
+    # over the Verlet list and over the cell stencil
+    from _systems import two_type_case
+    case = two_type_case()
+    box = case.cfg.box
+    # start where the offset is two whole boxes: the lattice start then meets
+    # its sheared images without overlaps
+    shear = 0.35
+    t0 = 2 * box[0] / (shear * box[2])
+    oracle_le(shear)
+    s = case.system(FP64, seed=41, build=False)
+    s.set_force_method(method)
+    s.set_lees_edwards(True, shear, t0)
+    s.build_neighbors(case.rc_list, case.skin)
+    s.integrate(80, 0.005, 1.0, 1.0)
+    x, v, img = s.get_state()
+    st = case.oracle_state()
+    st.time = t0
+    O.integrate(case.model, st, 80, 0.005, 1.0, 1.0, seed=41)
+    delta = shear * box[2] * st.time
+    assert np.abs(le_diff(x, st.x, box, delta)).max() < 1e-10
+    assert np.abs(v - st.v).max() < 1e-9
+    o, oo = s.observables(), O.observables(case.model, st)
+    for k in ("pe_pair", "virial", "pxz", "temperature"):
+        assert abs(o[k] - oo[k]) <= 1e-9 * max(1.0, abs(oo[k])), (k, o[k], oo[k])
+    s.close()
