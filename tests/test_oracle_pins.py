@@ -868,3 +868,30 @@ def test_dpd_skips_excluded_bonded_pairs(dpd_on):
         O.set_exclude_bonded(False)
     assert np.array_equal(runs[(True, 4.5)], runs[(True, 0.0)])
     assert np.abs(runs[(False, 4.5)] - runs[(True, 0.0)]).max() > 1e-3
+
+
+def test_pxz_symmetries():
+    # the xz pressure changes sign under the mirror x -> -x and is unchanged
+    # when the x and z axes are exchanged (a cubic box): a wrong component
+    # (xx, zz) or a missing kinetic or virial part breaks one of the two
+    c = I.lj_fcc(5, 5, 5, density=0.8442)
+    g = np.random.default_rng(7)
+    x = np.mod(c.x + g.normal(0, 0.1, c.x.shape), c.box)
+    v = I.maxwell_velocities(c.n, 1.3, seed=7)
+    st = O.State(c.box, x, v)
+    o = O.observables(LJ_FLUID, st)
+    assert abs(o["pxz"]) > 1e-3
+    xm = x.copy()
+    xm[:, 0] = np.mod(-xm[:, 0], c.box[0])
+    vm = v.copy()
+    vm[:, 0] = -vm[:, 0]
+    om = O.observables(LJ_FLUID, O.State(c.box, xm, vm))
+    assert abs(om["pxz"] + o["pxz"]) < 1e-10 * max(1.0, abs(o["pressure"]))
+    assert abs(om["pressure"] - o["pressure"]) < 1e-10 * abs(o["pressure"])
+    xs, vs = x[:, ::-1].copy(), v[:, ::-1].copy()   # (x, y, z) -> (z, y, x)
+    os_ = O.observables(LJ_FLUID, O.State(c.box, xs, vs))
+    assert abs(os_["pxz"] - o["pxz"]) < 1e-10 * max(1.0, abs(o["pressure"]))
+    # the kinetic part alone: no pair within the cutoff
+    far = O.State(np.array([40.0, 40.0, 40.0]), np.array([[5.0, 5.0, 5.0], [30.0, 30.0, 30.0]]),
+                  np.array([[1.0, 0.0, 2.0], [0.5, 0.0, -1.0]]))
+    assert abs(O.observables(LJ_FLUID, far)["pxz"] - (1.0 * 2.0 + 0.5 * -1.0) / 40.0 ** 3) < 1e-15
