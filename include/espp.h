@@ -316,7 +316,10 @@ int espp_get_lees_edwards(espp_h h, int32_t* on, double* shear_rate, double* tim
 int espp_integrate(espp_h h, int64_t nsteps, double dt, double gamma, double kT);
 
 /* Paper "Example usage": computeEnergy().  Observables of replica 0 (or of
- * all R replicas into out[R] with espp_observables_batch).  Synchronises. */
+ * the first R replicas into out[R] with espp_observables_batch; out is host
+ * memory owned by the caller).  Synchronises.  Errors: ESPP_ERR_ARG (null out,
+ * R outside [1, replica count]), ESPP_ERR_STATE (no state set), the errors of
+ * a list rebuild the call may need (ESPP_ERR_LIST_OVERFLOW, ESPP_ERR_NONFINITE). */
 int espp_observables(espp_h h, espp_obs_t* out);
 int espp_observables_batch(espp_h h, espp_obs_t* out, int32_t R);
 
@@ -324,7 +327,11 @@ int espp_observables_batch(espp_h h, espp_obs_t* out, int32_t R);
  * equal bins (counts[nbins], host).  rmax must be below half the smallest
  * box edge.  Pairs come from the Verlet list when rmax <= rc + skin (with 1-2
  * exclusions on, bonded pairs are then not counted), else from all pairs of
- * the replica (limited to 200000 particles). */
+ * the replica (limited to 200000 particles).  Errors: ESPP_ERR_ARG (replica
+ * out of range, nbins outside [1, 12288], rmax not in (0, half the smallest
+ * edge), null counts, an all-pairs histogram above the particle limit),
+ * ESPP_ERR_STATE
+ * (no state set). */
 int espp_rdf_counts(espp_h h, int32_t replica, double rmax, int32_t nbins, int64_t* counts);
 
 /* ---- checkpoint ------------------------------------------------------------ */
@@ -332,8 +339,19 @@ int espp_rdf_counts(espp_h h, int32_t replica, double rmax, int32_t nbins, int64
 /* Paper "New features": checkpoint of the state and of the random number
  * generator.  The Philox noise is a pure function of (seed, id, step), so the
  * file holds the full internal state (storage order, positions at the last
- * list build, velocities, force, image counters, step) and a resumed run is
- * bit-identical to an uninterrupted one. */
+ * list build, velocities, force, image counters, step, per-replica seeds and
+ * pending rebuild requests, the Lees-Edwards setting, clock and build
+ * offsets) and a resumed run is bit-identical to an uninterrupted one.  The
+ * configuration is not in the file: interactions, masses, thermostat, force
+ * method and list cutoff are set on the loading handle as on the saving one.
+ * path: a NUL-terminated file name, written or read with stdio.
+ * Save errors: ESPP_ERR_ARG (null path), ESPP_ERR_STATE (no state set),
+ * ESPP_ERR_IO (open or write failed), the run's own error if the last step
+ * failed.  Load needs espp_build_neighbors first (ESPP_ERR_STATE) and a handle
+ * of the same precision, replica count, sizes and boxes (ESPP_ERR_ARG);
+ * ESPP_ERR_IO for a file that cannot be opened, is not a checkpoint or is
+ * truncated; ESPP_ERR_LIST_OVERFLOW if the saved list does not fit.  A load
+ * that fails before the upload leaves the handle unchanged. */
 int espp_checkpoint_save(espp_h h, const char* path);
 int espp_checkpoint_load(espp_h h, const char* path);
 

@@ -1497,7 +1497,8 @@ class System : public SystemBase {
     // ------------------------------------------------------------- checkpoint
     // File layout: header, per replica (box, n, seed), then the storage-order
     // arrays (positions, velocities, force, build positions, images, bond
-    // slots, slot of every id) and the pending rebuild requests.  Loading puts
+    // slots, slot of every id), the pending rebuild requests and the
+    // Lees-Edwards build offsets of every replica.  Loading puts
     // every array back in the same order and rebuilds the Verlet list from the
     // build positions, so the list equals the one of the saved run.
     struct CkptHeader {
@@ -1595,17 +1596,17 @@ class System : public SystemBase {
             fclose(fh);
             return fail(ESPP_ERR_ARG, "checkpoint does not match this handle (precision, replicas, size)");
         }
+        // the handle changes only once the whole file has been read and checked
+        std::vector<unsigned long long> sds((size_t)R);
         for (int r = 0; r < R && ok; ++r) {
             double b[3];
             int64_t nr;
-            unsigned long long sd;
             ok = fread(b, sizeof(double), 3, fh) == 3 && fread(&nr, sizeof(nr), 1, fh) == 1 &&
-                 fread(&sd, sizeof(sd), 1, fh) == 1;
+                 fread(&sds[r], sizeof(sds[r]), 1, fh) == 1;
             if (ok && (nr != rep_n[r] || b[0] != box[3 * r] || b[1] != box[3 * r + 1] || b[2] != box[3 * r + 2])) {
                 fclose(fh);
                 return fail(ESPP_ERR_ARG, "checkpoint replica geometry differs from this handle");
             }
-            if (ok) seeds[r] = sd;
         }
         const size_t n = (size_t)N;
         std::vector<V4<T>> pos(n), vel(n), frc(n), xb(n);
@@ -1627,6 +1628,7 @@ class System : public SystemBase {
         if (!ok) return fail(ESPP_ERR_IO, "checkpoint file is truncated");
         if (hd.le_on && d.mlp_on) return fail(ESPP_ERR_STATE, "Lees-Edwards is not available with the learned potential");
         CK(cudaStreamSynchronize(st));
+        for (int r = 0; r < R; ++r) seeds[r] = sds[r];
         int rcode = upload_geometry();  // seeds
         if (rcode) return rcode;
         cur = 0;

@@ -483,6 +483,30 @@ def test_checkpoint_rejects_other_handles(tmp_path):
         c64.checkpoint_load(path)
 
 
+def test_failed_checkpoint_load_leaves_the_handle_unchanged(tmp_path):
+    # a truncated file of a run with another seed: the load fails after the
+    # per-replica records (seeds included) have been read; the handle must
+    # keep its own seed and state
+    case = kg_case()
+    a = case.system(FP32, seed=17)
+    a.integrate(20, 0.005, 1.0, 1.0)
+    full = tmp_path / "full.ckpt"
+    a.checkpoint_save(str(full))
+    data = full.read_bytes()
+    cut = tmp_path / "cut.ckpt"
+    cut.write_bytes(data[: len(data) // 2])
+    b = case.system(FP32, seed=5)
+    ref = case.system(FP32, seed=5)
+    with pytest.raises(espp.EsppError):
+        b.checkpoint_load(str(cut))
+    b.integrate(50, 0.005, 1.0, 1.0)
+    ref.integrate(50, 0.005, 1.0, 1.0)
+    xb, vb, ib = b.get_state()
+    xr, vr, ir = ref.get_state()
+    assert b.step == ref.step == 50
+    assert np.array_equal(xb, xr) and np.array_equal(vb, vr) and np.array_equal(ib, ir)
+
+
 # ---------------------------------------------------------------------------
 # full sizes, sampled against the oracle one particle at a time
 # ---------------------------------------------------------------------------
