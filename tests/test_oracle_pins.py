@@ -202,6 +202,24 @@ def test_newton_third_law(name, model, cfg):
     assert np.all(np.abs(f.sum(axis=0)) <= 1e-12 * np.abs(f).sum())
 
 
+@pytest.mark.parametrize("name,model,cfg", _small_systems(), ids=lambda v: v if isinstance(v, str) else "")
+def test_sampled_forces_equal_the_full_evaluation(name, model, cfg):
+    # the full-size parity tests compare sampled particles with forces_subset:
+    # it must give exactly the rows of the (pinned) full evaluation, also with
+    # bonded exclusions and under a sheared boundary
+    sel = np.random.default_rng(4).permutation(cfg.n)[: max(1, cfg.n // 3)]
+    for excl, shear in ((False, 0.0), (True, 0.0), (False, 0.3)):
+        O.set_exclude_bonded(excl)
+        O.set_lees_edwards(shear != 0.0, shear)
+        try:
+            f, _ = O.forces(model, cfg.box, cfg.x, cfg.types, cfg.bonds, time=2.1)
+            fs = O.forces_subset(model, cfg.box, cfg.x, cfg.types, cfg.bonds, sel, time=2.1)
+        finally:
+            O.set_exclude_bonded(False)
+            O.set_lees_edwards(False)
+        assert np.array_equal(fs, f[sel]), (name, excl, shear)
+
+
 def test_translation_and_permutation_invariance():
     c = I.kg_lattice(10, 20, seed=4, jitter=0.1)
     f0, e0 = O.forces(KG, c.box, c.x, c.types, c.bonds)
