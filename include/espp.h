@@ -163,8 +163,8 @@ int espp_set_step(espp_h h, int64_t step);
 int espp_set_interaction(espp_h h, int kind, int type_a, int type_b, const double* params,
                          int64_t n_params);
 
-/* Learned coarse-grained pair potential (the spec learned-CG model; the
- * paper's "tabulated potentials" are its fallback).  u(r) = w3 . silu(W2
+/* Learned coarse-grained pair potential (a learned CG model; the paper's
+ * "tabulated potentials" are its fallback).  u(r) = w3 . silu(W2
  * silu(W1 phi(r) + b1) + b2) + b3 with 32 Gaussian radial bases phi_k(r) =
  * exp(-(r - mu_k)^2 / (2 w^2)) (cos(pi r / rc) + 1) / 2, mu_k = rc k / 31,
  * w = rc / 31.  Weights: bf16[ESPP_MLP_NPARAMS] bit patterns in the order W1
@@ -186,8 +186,8 @@ int espp_cg_map(espp_h h, int32_t beads_per_site, double* x_sites, double* f_sit
 /* Current learned-potential weights (BF16 bit patterns, ESPP_MLP_NPARAMS). */
 int espp_mlp_get_weights(espp_h h, uint16_t* bf16, int64_t n);
 
-/* Force-matching training of the learned potential (spec learned CG
- * model): frames_x and frames_f are device arrays of nframes x n x 3 doubles
+/* Force-matching training of the learned potential (the learned CG model):
+ * frames_x and frames_f are device arrays of nframes x n x 3 doubles
  * in id order, the site positions and the target forces for the pair
  * potential (the mapped forces minus the bonded forces of this handle's bond
  * potential).  Loss = mean over frames and sites of |F_pair + F_bond -

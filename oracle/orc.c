@@ -183,7 +183,7 @@ static void table_eval(int slot, double r, double* u, double* F) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Learned radial-basis MLP pair potential (spec learned CG model).     */
+/* Learned radial-basis MLP pair potential (the learned CG model).            */
 /* Reading (the paper prints no model; the shape is 32 Gaussian bases on     */
 /* [0, rc], two hidden layers of 64 SiLU units, one output):                 */
 /*   phi_k(r) = exp(-(r - mu_k)^2 / (2 w^2)) * fc(r),  mu_k = rc k / 31,    */
@@ -770,7 +770,7 @@ int orc_forces_subset(int64_t n, const double* L, const double* x, const int32_t
 }
 
 /* Force-matching loss of the learned pair potential and its gradient
- * (spec learned CG model; reading: mean squared force error over all
+ * (the learned CG model; reading: mean squared force error over all
  * frames and sites, the target being the mapped force minus the bonded
  * force).  For frame f with positions X_f and targets Y_f:
  *   e_i = F_pair,i(X_f) + F_bond,i(X_f) - Y_f,i,   loss = sum |e_i|^2 / (F n).
