@@ -159,7 +159,10 @@ int espp_set_step(espp_h h, int64_t step);
  * Tabulated kinds (paper "Functionality": tabulated potentials) take the
  * energy u and the force F = -dU/dr on a uniform grid from r = 0 and
  * interpolate both linearly in r; a tabulated bond longer than rmax is an
- * error like a stretched FENE bond.  Marks the stored force stale. */
+ * error like a stretched FENE bond.  Marks the stored force stale.
+ * Errors (ESPP_ERR_ARG, the handle unchanged): an unknown kind, a type outside
+ * [0, ESPP_MAX_TYPES), too few or non-finite parameters, sigma, rc, caprad,
+ * K or R0 not positive, a malformed table. */
 int espp_set_interaction(espp_h h, int kind, int type_a, int type_b, const double* params,
                          int64_t n_params);
 
@@ -172,7 +175,8 @@ int espp_set_interaction(espp_h h, int kind, int type_a, int type_b, const doubl
  * Evaluated on the tensor cores (BF16 operands, FP32 accumulation) with the
  * force from the exact derivative carried through both layers.  Select it
  * with espp_set_interaction(h, ESPP_MLP, 0, 0, {rc}, 1) on a single-type
- * system. */
+ * system.  ESPP_ERR_ARG for n != ESPP_MLP_NPARAMS or a NaN or infinity
+ * pattern among the weights. */
 #define ESPP_MLP_NPARAMS 6337
 int espp_mlp_set_weights(espp_h h, const uint16_t* bf16, int64_t n);
 
@@ -213,7 +217,8 @@ int espp_mlp_loss_grad(espp_h h, const double* frames_x, const double* frames_f,
  * potential); default off, as Kremer-Grest keeps WCA between bonded beads. */
 int espp_set_exclude_bonded(espp_h h, int on);
 
-/* Per-type mass (default 1 for every type). */
+/* Per-type mass (default 1 for every type).  ESPP_ERR_ARG unless the type is
+ * in range and the mass finite and positive. */
 int espp_set_mass(espp_h h, int type, double mass);
 
 /* ---- neighbour list ------------------------------------------------------ */
@@ -223,7 +228,9 @@ int espp_set_mass(espp_h h, int type, double mass);
  * >= rc + skin, at least 3 per box edge, else ESPP_ERR_BOX_TOO_SMALL), then
  * bins, resorts and builds the Verlet list of every replica now.  Later
  * rebuilds happen automatically when a particle has moved more than skin/2
- * since the last build. */
+ * since the last build.  ESPP_ERR_ARG for rc <= 0, skin < 0, non-finite
+ * values or a pair cutoff above rc; that refusal keeps the earlier cutoff,
+ * skin, grid and list. */
 int espp_build_neighbors(espp_h h, double rc, double skin);
 
 /* Tests: the current Verlet list as CSR in id order (global ids).  row_ptr has

@@ -682,8 +682,14 @@ class System : public SystemBase {
                 if (!std::isfinite(v)) return fail(ESPP_ERR_ARG, "non-finite table entry");
             return ESPP_OK;
         };
+        auto finite = [&](int count) {
+            for (int k = 0; k < count; ++k)
+                if (!std::isfinite(p[k])) return false;
+            return true;
+        };
         if (kind == ESPP_FENE) {
-            if (!p || np < 2 || !(p[0] > 0) || !(p[1] > 0)) return fail(ESPP_ERR_ARG, "FENE needs K > 0, R0 > 0");
+            if (!p || np < 2 || !(p[0] > 0) || !(p[1] > 0) || !finite(2))
+                return fail(ESPP_ERR_ARG, "FENE needs finite K > 0, R0 > 0");
             bond_kind = ESPP_FENE;
             bond_K = p[0];
             bond_R0 = p[1];
@@ -704,6 +710,7 @@ class System : public SystemBase {
             } else if (kind == ESPP_LJ || kind == ESPP_LJ_CAPPED) {
                 const int need = kind == ESPP_LJ ? 4 : 5;
                 if (!p || np < need) return fail(ESPP_ERR_ARG, "too few parameters");
+                if (!finite(need)) return fail(ESPP_ERR_ARG, "non-finite parameter");
                 h.kind = kind;
                 h.eps = p[0];
                 h.sig = p[1];
@@ -717,13 +724,14 @@ class System : public SystemBase {
                 if (rc) return rc;
                 h.kind = ESPP_TAB_PAIR;
             } else if (kind == ESPP_MLP) {
-                if (!p || np < 1 || !(p[0] > 0)) return fail(ESPP_ERR_ARG, "the learned potential needs rc > 0");
+                if (!p || np < 1 || !(p[0] > 0) || !finite(1))
+                    return fail(ESPP_ERR_ARG, "the learned potential needs a finite rc > 0");
                 if (ta != 0 || tb != 0 || ntypes != 1)
                     return fail(ESPP_ERR_ARG, "the learned potential applies to single-type systems (types 0, 0)");
                 h.kind = ESPP_MLP;
                 h.rc = p[0];
             } else if (kind == ESPP_WCA) {
-                if (!p || np < 2) return fail(ESPP_ERR_ARG, "WCA needs eps, sigma");
+                if (!p || np < 2 || !finite(2)) return fail(ESPP_ERR_ARG, "WCA needs finite eps, sigma");
                 h.kind = ESPP_LJ;
                 h.eps = p[0];
                 h.sig = p[1];
@@ -744,6 +752,8 @@ class System : public SystemBase {
 
     int mlp_set_weights(const uint16_t* bits, int64_t n) override {
         if (!bits || n != MLP_NPARAMS) return fail(ESPP_ERR_ARG, "expected ESPP_MLP_NPARAMS BF16 weights");
+        for (int64_t k = 0; k < n; ++k)
+            if ((bits[k] & 0x7F80u) == 0x7F80u) return fail(ESPP_ERR_ARG, "non-finite BF16 weight");
         mlp_bits.assign(bits, bits + n);
         CK(upload_params());
         f_valid = false;
@@ -906,7 +916,7 @@ class System : public SystemBase {
     }
 
     int set_mass(int type, double m) override {
-        if (type < 0 || type >= MAX_TYPES || !(m > 0)) return fail(ESPP_ERR_ARG, "bad mass");
+        if (type < 0 || type >= MAX_TYPES || !(m > 0) || !std::isfinite(m)) return fail(ESPP_ERR_ARG, "bad mass");
         mass_h[type] = m;
         mass_dirty = true;
         f_valid = false;
@@ -1022,10 +1032,15 @@ class System : public SystemBase {
     int build_neighbors(double rc, double sk) override {
         if (!(rc > 0) || !(sk >= 0) || !std::isfinite(rc) || !std::isfinite(sk))
             return fail(ESPP_ERR_ARG, "rc must be positive and skin non-negative");
+        const double rc_old = rc_list, sk_old = skin;
         rc_list = rc;
         skin = sk;
         int rcode = check_cutoffs();
-        if (rcode) return rcode;
+        if (rcode) {
+            rc_list = rc_old;  // refused: the grid and list of the old cutoff stay valid
+            skin = sk_old;
+            return rcode;
+        }
         cell_sub = choose_subdivision();
         for (int r = 0; r < R; ++r)
             if (!cells_fit(r)) {

@@ -363,6 +363,31 @@ def test_cutoff_beyond_list_is_rejected():
     assert e.value.code == espp.ESPP_ERR_ARG
 
 
+def test_refused_settings_leave_the_handle_unchanged():
+    case = kg_case()
+    s = case.system(FP32, seed=3)
+    ref = case.system(FP32, seed=3)
+    bad_bits = espp.to_bf16_bits(np.zeros(espp.MLP_NPARAMS))
+    bad_bits[7] = 0x7FC0  # a BF16 NaN
+    refusals = [
+        lambda: s.set_lj(1.0, 1.0, float("inf")),
+        lambda: s.set_wca(float("nan"), 1.0),
+        lambda: s.set_fene(float("inf"), 1.5),
+        lambda: s.set_mass(0, float("inf")),
+        lambda: s.set_mlp(2.5, bad_bits),
+        lambda: s.build_neighbors(0.5, 0.4),  # below the WCA cutoff
+    ]
+    for call in refusals:
+        with pytest.raises(espp.EsppError) as e:
+            call()
+        assert e.value.code == espp.ESPP_ERR_ARG
+    s.integrate(40, 0.005, 1.0, 1.0)
+    ref.integrate(40, 0.005, 1.0, 1.0)
+    xs, vs, is_ = s.get_state()
+    xr, vr, ir = ref.get_state()
+    assert np.array_equal(xs, xr) and np.array_equal(vs, vr) and np.array_equal(is_, ir)
+
+
 @pytest.mark.parametrize("prec", [FP32, FP64])
 def test_single_free_particle(prec):
     box = np.array([5.0, 6.0, 7.0])
