@@ -319,7 +319,9 @@ int espp_get_lees_edwards(espp_h h, int32_t* on, double* shear_rate, double* tim
  * Philox(seed; id, step); v += dt/2 F/m.  gamma = 0 gives plain velocity
  * Verlet.  Steps run as CUDA graphs on the handle's stream; the call returns
  * after the work is issued and checked (it synchronises once at the end).
- * Errors: ESPP_ERR_BOND_BROKEN, ESPP_ERR_NONFINITE, ESPP_ERR_LIST_OVERFLOW. */
+ * Errors: ESPP_ERR_ARG (nsteps < 0, dt not finite and positive, gamma or kT
+ * negative or not finite), ESPP_ERR_STATE (no state or list),
+ * ESPP_ERR_BOND_BROKEN, ESPP_ERR_NONFINITE, ESPP_ERR_LIST_OVERFLOW. */
 int espp_integrate(espp_h h, int64_t nsteps, double dt, double gamma, double kT);
 
 /* Paper "Example usage": computeEnergy().  Observables of replica 0 (or of

@@ -1324,8 +1324,9 @@ class System : public SystemBase {
     }
 
     int integrate(int64_t nsteps, double dt, double gamma, double kT) override {
-        if (nsteps < 0 || !(dt > 0) || !(gamma >= 0) || !(kT >= 0) || !std::isfinite(dt))
-            return fail(ESPP_ERR_ARG, "need nsteps >= 0, dt > 0, gamma >= 0, kT >= 0");
+        if (nsteps < 0 || !(dt > 0) || !(gamma >= 0) || !(kT >= 0) || !std::isfinite(dt) || !std::isfinite(gamma) ||
+            !std::isfinite(kT))
+            return fail(ESPP_ERR_ARG, "need nsteps >= 0 and finite dt > 0, gamma >= 0, kT >= 0");
         if (nsteps == 0) return ESPP_OK;
         int rcode = ensure_list();
         if (rcode) return rcode;

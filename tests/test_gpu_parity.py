@@ -376,6 +376,8 @@ def test_refused_settings_leave_the_handle_unchanged():
         lambda: s.set_mass(0, float("inf")),
         lambda: s.set_mlp(2.5, bad_bits),
         lambda: s.build_neighbors(0.5, 0.4),  # below the WCA cutoff
+        lambda: s.integrate(5, 0.005, float("inf"), 1.0),
+        lambda: s.integrate(5, 0.005, 1.0, float("nan")),
     ]
     for call in refusals:
         with pytest.raises(espp.EsppError) as e:
