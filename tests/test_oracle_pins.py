@@ -523,6 +523,26 @@ def test_mlp_envelope_vanishes_at_cutoff():
     O.set_mlp(p, 3.5)
 
 
+def test_mlp_radial_basis_centres_and_width():
+    # du/dW1[a, k] = (adjoint of unit a) * phi_k(r), so the ratio of two
+    # neighbouring entries is phi_{k+1}(r) / phi_k(r): the envelope cancels,
+    # and for Gaussians of width w centred a spacing D apart its logarithm is
+    # the straight line (2 r - (2k + 1) D) D / (2 w^2).  The reading's 32
+    # bases on [0, rc] put D = w = rc / 31: slope 1/w, zero midway between
+    # the centres.
+    rc = 3.5
+    O.set_mlp(_mlp_params(6), rc)
+    D = w = rc / 31
+    for r in np.linspace(0.05, rc - 0.05, 29):
+        g_u = O.mlp_pair(r, want_grad=True)[3]
+        row = g_u[:2048].reshape(64, 32)
+        a = int(np.argmax(np.abs(row).max(axis=1)))
+        for k in range(max(0, int(r / D) - 2), min(31, int(r / D) + 3)):
+            got = np.log(row[a, k + 1] / row[a, k])
+            want = (2 * r - (2 * k + 1) * D) * D / (2 * w * w)
+            assert abs(got - want) < 1e-9, (r, k, got, want)
+
+
 def test_bonded_exclusion_removes_exactly_the_bonded_pairs():
     c = I.kg_lattice(5, 20, seed=6, jitter=0.1)
     m = O.Model(1, {(0, 0): ("lj", 1.0, 1.0, 2.5, True)})
