@@ -71,3 +71,20 @@ def test_create_without_gpu_fails_loudly(lib):
         pass
     with pytest.raises(espp.EsppError):
         espp.System(np.array([10.0, 10.0, 10.0]), 10)
+
+
+def test_plain_c_client_builds_and_runs(lib, tmp_path):
+    # the header is valid C99 and the library links and runs from C alone
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    exe = str(tmp_path / "abi_client")
+    libdir = os.path.dirname(pbuild.LIB)
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                    "-I", os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "abi_client.c"),
+                    "-L", libdir, "-lespp_gb", "-Wl,-rpath," + libdir, "-o", exe], check=True)
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, (out.returncode, out.stdout, out.stderr)
+    assert out.stdout.startswith(("create refused:", "ok"))
