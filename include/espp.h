@@ -140,10 +140,13 @@ int espp_system_destroy(espp_h h);
 int espp_set_state(espp_h h, const double* x, const double* v, const int32_t* img, int where);
 
 /* Read positions (wrapped into [0,L)), velocities and image counters in id
- * order into caller buffers (each may be NULL).  Synchronises the stream. */
+ * order into caller buffers (each may be NULL).  Synchronises the stream.
+ * Errors: ESPP_ERR_STATE (no state set), ESPP_ERR_ARG (where is neither
+ * ESPP_HOST nor ESPP_DEVICE). */
 int espp_get_state(espp_h h, double* x, double* v, int32_t* img, int where);
 
-/* Set the step number of the state (keys the Philox noise counter). */
+/* Set the step number of the state (keys the Philox noise counter).  The
+ * simulated time of the handle is kept: it now belongs to this step. */
 int espp_set_step(espp_h h, int64_t step);
 
 /* ---- interactions -------------------------------------------------------- */
@@ -243,7 +246,9 @@ int espp_get_neighbors(espp_h h, int64_t* row_ptr, int64_t* cols, int64_t cap);
 /* Conservative forces (pairs + bonds, no thermostat) at the current
  * positions, rebuilding the list first when it is stale.  f_out: n*3 doubles
  * in id order (host or device, where), or NULL.  The integrator's stored
- * force is not changed. */
+ * force is not changed.  Errors: ESPP_ERR_STATE (no state, no list cutoff,
+ * the learned potential without weights), ESPP_ERR_ARG (a pair cutoff above
+ * the list cutoff, a bad where), ESPP_ERR_LIST_OVERFLOW, ESPP_ERR_BOND_BROKEN. */
 int espp_compute_forces(espp_h h, double* f_out, int where);
 
 /* Thermostat of espp_integrate (paper "Functionality": Langevin dynamics and
