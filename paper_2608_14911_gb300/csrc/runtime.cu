@@ -477,10 +477,10 @@ class System : public SystemBase {
                 memcpy(&v, &b, 4);
                 return v;
             };
-            memcpy(w.W1, mlp_bits.data(), sizeof(w.W1));
+            memcpy(static_cast<void*>(w.W1), mlp_bits.data(), sizeof(w.W1));  // BF16 bit patterns
             const int o_b1 = MLP_H * MLP_NB, o_W2 = o_b1 + MLP_H, o_b2 = o_W2 + MLP_H * MLP_H;
             const int o_w3 = o_b2 + MLP_H, o_b3 = o_w3 + MLP_H;
-            memcpy(w.W2, mlp_bits.data() + o_W2, sizeof(w.W2));
+            memcpy(static_cast<void*>(w.W2), mlp_bits.data() + o_W2, sizeof(w.W2));
             for (int a = 0; a < MLP_H; ++a) {
                 w.b1[a] = f(o_b1 + a);
                 w.b2[a] = f(o_b2 + a);
