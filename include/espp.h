@@ -175,8 +175,12 @@ int espp_set_interaction(espp_h h, int kind, int type_a, int type_b, const doubl
  * exp(-(r - mu_k)^2 / (2 w^2)) (cos(pi r / rc) + 1) / 2, mu_k = rc k / 31,
  * w = rc / 31.  Weights: bf16[ESPP_MLP_NPARAMS] bit patterns in the order W1
  * (64x32, rows = output units), b1 (64), W2 (64x64), b2 (64), w3 (64), b3.
- * Evaluated on the tensor cores (BF16 operands, FP32 accumulation) with the
- * force from the exact derivative carried through both layers.  Select it
+ * On an FP32 handle it is evaluated on the tensor cores (BF16 operands:
+ * the radial features and first-layer activations are rounded to BF16; FP32
+ * accumulation) with the force from the exact derivative carried through
+ * both layers.  On an FP64 handle the same network (the same BF16 weights)
+ * is evaluated in double on the CUDA cores, with no rounding to BF16, as the
+ * reference for the tensor-core path; it is much slower.  Select it
  * with espp_set_interaction(h, ESPP_MLP, 0, 0, {rc}, 1) on a single-type
  * system.  ESPP_ERR_ARG for n != ESPP_MLP_NPARAMS or a NaN or infinity
  * pattern among the weights. */
@@ -429,24 +433,33 @@ int espp_langevin_noise(uint64_t seed, int64_t step, int64_t n, double* out_devi
  * front and hands out only its own pool, or latency-critical loops that cannot
  * take the implicit synchronisation of cudaMalloc/cudaFree.
  *
- * Same counts as espp_rdf_counts (unique pairs i < j with minimum-image
- * distance r < rmax, bin floor(r nbins / rmax)), computed from caller-owned
- * device positions x_device (n*3 doubles, id order, each coordinate in
- * [0, box) as espp_get_state returns them) into caller-owned device counts
- * counts_device[nbins] (int64).  Work is queued on cuda_stream; the call does
- * not wait for it.
+ * Counts every unique pair i < j of the n positions whose plain periodic
+ * minimum-image distance is r < rmax, in bin floor(r nbins / rmax): all
+ * pairs, bonded ones included, with no Lees-Edwards offset.  That equals
+ * espp_rdf_counts only where the handle path also counts all pairs of a
+ * plain periodic box (rmax above the list radius, no shear); below the list
+ * radius the handle path counts from the Verlet list, which leaves out
+ * excluded bonded pairs.  Positions: caller-owned device memory x_device
+ * (n*3 doubles, id order, each coordinate in [0, box) as espp_get_state
+ * returns them); counts: caller-owned device memory counts_device[nbins]
+ * (int64).  Work is queued on cuda_stream; the call does not wait for it.
  *
  * Working memory is a fixed file-scope device array of ESPP_NOALLOC_MAX_BINS
  * counters (32 KiB) inside the library; every GPU that loads the library holds
  * it until the process exits.  The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  All calls share the one array: each
- * call clears the part it uses, and calls whose work overlaps on the GPU (for
- * instance on two streams) race on it.  Errors: ESPP_ERR_ARG for nbins outside
- * [1, ESPP_NOALLOC_MAX_BINS], rmax not below half of every box edge, null
- * pointers or n < 0; ESPP_ERR_CUDA if a launch fails.  Never calls cudaMalloc,
- * cudaFree or any allocating routine. */
+ * first call before any stream capture, and do not reset the device
+ * (cudaDeviceReset) while the library stays loaded, since the looked-up
+ * address is kept.  All calls share the one array: each call clears the part
+ * it uses, and calls whose work overlaps on the GPU (for instance on two
+ * streams) race on it.  Errors (all checked on the host before any GPU work,
+ * counts_device then untouched): ESPP_ERR_ARG for nbins outside
+ * [1, ESPP_NOALLOC_MAX_BINS], n outside [0, ESPP_NOALLOC_MAX_N] (the kernel is
+ * O(n^2)), rmax not in (0, half of every box edge), a box edge not positive,
+ * or a null pointer; ESPP_ERR_CUDA if a launch fails.  Never calls
+ * cudaMalloc, cudaFree or any allocating routine. */
 #define ESPP_NOALLOC_MAX_BINS 4096
+#define ESPP_NOALLOC_MAX_N 200000
 int espp_rdf_counts_noalloc(const double* x_device, int64_t n, const double box[3], double rmax,
                             int32_t nbins, int64_t* counts_device, void* cuda_stream);
 

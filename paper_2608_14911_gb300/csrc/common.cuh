@@ -224,6 +224,21 @@ enum : unsigned int {
     ERRBIT_ASYM = 16u,  // a list entry without its mirrored entry
 };
 
+// Streaming multiprocessors of the current device, for grids sized in whole
+// waves (cached per device; 1 if the query fails, which only shrinks grids
+// that stride over their work).
+inline int sm_count() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (cache[dev] <= 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 1;
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
+
 constexpr int TILE = 128;          // particles per tile (= threads per block)
 constexpr int MAX_TYPES = ESPP_MAX_TYPES;
 

@@ -321,14 +321,14 @@ void Launch<T>::rg2(const DevSys<T>& s, int cur, const int* members, const int* 
 template <class T>
 void Launch<T>::rdf(const DevSys<T>& s, int cur, int rep, double rmax, int nbins,
                     unsigned long long* counts, cudaStream_t st) {
-    k_rdf<T><<<4 * 152, 256, sizeof(unsigned int) * nbins, st>>>(s, cur, rep, (T)(rmax * rmax),
+    k_rdf<T><<<4 * sm_count(), 256, sizeof(unsigned int) * nbins, st>>>(s, cur, rep, (T)(rmax * rmax),
                                                                  nbins / rmax, nbins, counts);
 }
 
 template <class T>
 void Launch<T>::rdf_list(const DevSys<T>& s, int cur, int rep, double rmax, int nbins,
                          unsigned long long* counts, cudaStream_t st) {
-    k_rdf_list<T><<<8 * 152, 256, sizeof(unsigned int) * nbins, st>>>(s, cur, rep, (T)(rmax * rmax),
+    k_rdf_list<T><<<8 * sm_count(), 256, sizeof(unsigned int) * nbins, st>>>(s, cur, rep, (T)(rmax * rmax),
                                                                       nbins / rmax, nbins, counts);
 }
 template void Launch<float>::rdf_list(const DevSys<float>&, int, int, double, int, unsigned long long*, cudaStream_t);

@@ -26,6 +26,8 @@
 // a fixed order, so the forces do not depend on the order in which warps run.
 #include <cstring>
 
+#include <math_constants.h>
+
 #include "mlp_common.cuh"
 #include "scan.cuh"
 #include "tc_ptx.cuh"
@@ -598,6 +600,113 @@ __global__ void __launch_bounds__(TILE) k_mlp_gather(DevSys<T> s, int cur) {
     }
 }
 
+// ---- FP64 handles: the learned potential in double on the CUDA cores --------
+// u(r) and du/dr of one pair in double from the BF16 weights (exact upcast):
+// the same network as the tensor-core tile, without any rounding to BF16 of
+// the features or activations, so an FP64 handle gets the network's exact
+// value (to double rounding), as the reference path for the BF16 one.
+__device__ __forceinline__ double silu_d(double z, double& dsilu) {
+    const double sg = 1.0 / (1.0 + exp(-z));
+    dsilu = sg * (1.0 + z * (1.0 - sg));
+    return z * sg;
+}
+
+__device__ void mlp_pair_f64(const MlpWeights* __restrict__ W, double r, double& u, double& du) {
+    const double rc = (double)W->rc;
+    const double w = rc / (MLP_NB - 1);
+    const double inv_2w2 = 1.0 / (2.0 * w * w);
+    double sn, cs;
+    sincospi(r / rc, &sn, &cs);
+    const double fc = 0.5 * (cs + 1.0);
+    const double dfc = -0.5 * (CUDART_PI / rc) * sn;
+    double phi[MLP_NB], dphi[MLP_NB];
+#pragma unroll 4
+    for (int k = 0; k < MLP_NB; ++k) {
+        const double d = r - rc * k / (MLP_NB - 1);
+        const double g = exp(-d * d * inv_2w2);
+        phi[k] = g * fc;
+        dphi[k] = g * (dfc - 2.0 * d * inv_2w2 * fc);
+    }
+    double h1[MLP_H], dh1[MLP_H];
+    for (int a = 0; a < MLP_H; ++a) {
+        double z = (double)W->b1[a], dz = 0.0;
+        const __nv_bfloat16* row = W->W1 + a * MLP_NB;
+#pragma unroll 8
+        for (int k = 0; k < MLP_NB; ++k) {
+            const double wk = (double)__bfloat162float(row[k]);
+            z = fma(wk, phi[k], z);
+            dz = fma(wk, dphi[k], dz);
+        }
+        double s1;
+        h1[a] = silu_d(z, s1);
+        dh1[a] = s1 * dz;
+    }
+    u = (double)W->b3;
+    du = 0.0;
+    for (int a = 0; a < MLP_H; ++a) {
+        double z = (double)W->b2[a], dz = 0.0;
+        const __nv_bfloat16* row = W->W2 + a * MLP_H;
+#pragma unroll 8
+        for (int k = 0; k < MLP_H; ++k) {
+            const double wk = (double)__bfloat162float(row[k]);
+            z = fma(wk, h1[k], z);
+            dz = fma(wk, dh1[k], dz);
+        }
+        double s1;
+        const double h2 = silu_d(z, s1);
+        u = fma((double)W->w3[a], h2, u);
+        du = fma((double)W->w3[a], s1 * dz, du);
+    }
+}
+
+// Thread per particle over its full list (each pair from both ends with the
+// same arithmetic, so F_ij = -F_ji exactly): force, energy (u per pair, half
+// of it to each end by the energy pass) and virial sums in list order.
+template <bool ENERGY>
+__global__ void __launch_bounds__(TILE) k_mlp_f64(DevSys<double> s, int cur) {
+    if (s.ctrl->abort) return;
+    const MlpWeights* __restrict__ W = s.mlp;
+    const double rc = (double)W->rc, rc2 = rc * rc;
+    const V4<double>* __restrict__ P = s.pos[cur];
+    const int4* __restrict__ nbr4 = reinterpret_cast<const int4*>(s.nbr);
+    const size_t stride = (size_t)s.stride;
+    for (int t = blockIdx.x; t < s.ntiles; t += gridDim.x) {
+        const Tile tl = s.tiles[t];
+        if ((int)threadIdx.x >= tl.count) continue;
+        const RepGeom<double>& g = s.reps[tl.rep];
+        const double L0 = g.L[0], L1 = g.L[1], L2 = g.L[2];
+        const int i = tl.start + threadIdx.x;
+        const V4<double> xi = ld4<double>(P + i);
+        const double xim = xi.x - L0, yim = xi.y - L1, zim = xi.z - L2;
+        const int n = s.nbr_cnt[i];
+        double fx = 0.0, fy = 0.0, fz = 0.0, eu = 0.0, ew = 0.0;
+        for (int k = 0; k < n; ++k) {
+            const int4 q = nbr4[(size_t)(k >> 2) * stride + i];
+            const int e = (k & 3) == 0 ? q.x : (k & 3) == 1 ? q.y : (k & 3) == 2 ? q.z : q.w;
+            const V4<double> xj = ld4<double>(P + nbr_slot(e));
+            const int code = nbr_code(e);
+            const double dx = shifted_diff(xi.x, xim, xj.x, L0, code & 3);
+            const double dy = shifted_diff(xi.y, yim, xj.y, L1, (code >> 2) & 3);
+            const double dz = shifted_diff(xi.z, zim, xj.z, L2, code >> 4);
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            if (!(r2 < rc2)) continue;
+            const double r = sqrt(r2);
+            double u, du;
+            mlp_pair_f64(W, r, u, du);
+            const double fr = -du / r;  // F_i = -du/dr r_ij / r
+            fx = fma(fr, dx, fx);
+            fy = fma(fr, dy, fy);
+            fz = fma(fr, dz, fz);
+            if (ENERGY) {
+                eu += u;
+                ew = fma(fr, r2, ew);
+            }
+        }
+        s.mlp_fT[i] = mk4<double>(fx, fy, fz, eu);
+        if (ENERGY) s.mlp_wT[i] = ew;
+    }
+}
+
 static_assert(sizeof(TcShared) <= 227 * 1024 / TC_CTAS_PER_SM, "tcgen05 tile CTA too large");
 
 // The learned potential's force pass runs in FP32/BF16 for both precisions of
@@ -627,9 +736,20 @@ cudaError_t prepare_mlp_tc() {
 
 template <class T>
 int Launch<T>::mlp(const DevSys<T>& s, int cur, bool energy, cudaStream_t st) {
+    if constexpr (sizeof(T) == 8) {
+        // FP64 handle: the network in double on the CUDA cores
+        if (energy) k_mlp_f64<true><<<s.ntiles, TILE, 0, st>>>(s, cur);
+        else k_mlp_f64<false><<<s.ntiles, TILE, 0, st>>>(s, cur);
+        return 1;
+    }
+    return mlp_tc(s, cur, energy, st);
+}
+
+template <class T>
+int Launch<T>::mlp_tc(const DevSys<T>& s, int cur, bool energy, cudaStream_t st) {
     cudaMemsetAsync(s.mlp_npairs, 0, sizeof(int), st);
-    const int tblocks = 152 * TC_CTAS_PER_SM;
-    k_mlp_stage<T><<<152 * ESPP_STAGE_GRID, TILE, 0, st>>>(s, cur);
+    const int tblocks = sm_count() * TC_CTAS_PER_SM;
+    k_mlp_stage<T><<<sm_count() * ESPP_STAGE_GRID, TILE, 0, st>>>(s, cur);
     if (energy) {
         k_mlp_tc<true><<<tblocks, TC_M, sizeof(TcShared), st>>>(as_float(s));
         k_mlp_gather<T, true><<<s.ntiles, TILE, 0, st>>>(s, cur);
@@ -653,6 +773,8 @@ int Launch<T>::mlp_rev(const DevSys<T>& s, cudaStream_t st) {
 
 template int Launch<float>::mlp(const DevSys<float>&, int, bool, cudaStream_t);
 template int Launch<double>::mlp(const DevSys<double>&, int, bool, cudaStream_t);
+template int Launch<float>::mlp_tc(const DevSys<float>&, int, bool, cudaStream_t);
+template int Launch<double>::mlp_tc(const DevSys<double>&, int, bool, cudaStream_t);
 template int Launch<float>::mlp_rev(const DevSys<float>&, cudaStream_t);
 template int Launch<double>::mlp_rev(const DevSys<double>&, cudaStream_t);
 

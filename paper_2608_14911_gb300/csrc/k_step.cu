@@ -266,13 +266,25 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32
             }
             if (s.mlp_on) {
                 // pair forces of the learned potential, computed by k_mlp
-                const float4 fm = s.mlp_f[i];
-                fx = (T)fm.x;
-                fy = (T)fm.y;
-                fz = (T)fm.z;
-                if (ENERGY) {
-                    pe = (T)fm.w;
-                    vir = (T)s.mlp_w[i];
+                if constexpr (sizeof(T) == 8) {
+                    // FP64 handle: the network evaluated in double (k_mlp_f64)
+                    const V4<T> fm = s.mlp_fT[i];
+                    fx = fm.x;
+                    fy = fm.y;
+                    fz = fm.z;
+                    if (ENERGY) {
+                        pe = fm.w;
+                        vir = s.mlp_wT[i];
+                    }
+                } else {
+                    const float4 fm = s.mlp_f[i];
+                    fx = (T)fm.x;
+                    fy = (T)fm.y;
+                    fz = (T)fm.z;
+                    if (ENERGY) {
+                        pe = (T)fm.w;
+                        vir = (T)s.mlp_w[i];
+                    }
                 }
                 if (DPD) dpd_loop<T, LE>(s, P, i, n, xi, dc, le, L0, L1, L2, fx, fy, fz);
             } else if (!FAST && s.cells_mode) {

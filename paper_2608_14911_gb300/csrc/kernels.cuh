@@ -109,6 +109,8 @@ template <class T> struct DevSys {
     const MlpWeights* mlp;
     float4* mlp_f;      // per particle: MLP pair force and sum of pair energies
     float* mlp_w;       // per particle: sum of r_ij . F_ij over its MLP pairs
+    V4<T>* mlp_fT;      // FP64 handles: the same two sums in double (k_mlp_f64)
+    T* mlp_wT;
     // per list entry (layout of nbr): -du/dr / r, u, and for entries (i, j)
     // with j > i the index of the mirrored entry (j, i)
     float* mlp_pf;
@@ -238,7 +240,11 @@ template <class T> struct Launch {
                     unsigned long long next_cond, int grid, cudaStream_t st);
     static void prologue(const DevSys<T>& s, int cur, int grid, cudaStream_t st);
     static void set_cond(const DevSys<T>& s, unsigned long long cond, cudaStream_t st);
+    // the learned potential's pair forces: the tensor-core path (FP32 handles)
+    // or the network in double (FP64 handles); mlp_tc: the tensor-core path
+    // for either precision (per-entry values, as training reads them)
     static int mlp(const DevSys<T>& s, int cur, bool energy, cudaStream_t st);
+    static int mlp_tc(const DevSys<T>& s, int cur, bool energy, cudaStream_t st);
     // list-free pair forces from the cell stencil (k_cells.cu)
     static int cellforce(const DevSys<T>& s, int cur, bool energy, bool dpd, cudaStream_t st);
     static int mlp_rev(const DevSys<T>& s, cudaStream_t st);

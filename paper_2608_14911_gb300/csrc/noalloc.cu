@@ -77,7 +77,9 @@ static cudaError_t scratch_for_current_device(unsigned long long** out) {
 extern "C" int espp_rdf_counts_noalloc(const double* x_device, int64_t n, const double box[3],
                                        double rmax, int32_t nbins, int64_t* counts_device,
                                        void* cuda_stream) {
-    if (!x_device || !counts_device || !box || n < 0 || n > (int64_t)0x7fffffff) return ESPP_ERR_ARG;
+    // n is bounded like the handle path's all-pairs histogram: the O(n^2)
+    // kernel would otherwise hold the GPU for minutes on a large system
+    if (!x_device || !counts_device || !box || n < 0 || n > ESPP_NOALLOC_MAX_N) return ESPP_ERR_ARG;
     if (nbins < 1 || nbins > ESPP_NOALLOC_MAX_BINS) return ESPP_ERR_ARG;
     for (int c = 0; c < 3; ++c)
         if (!(box[c] > 0) || !(rmax > 0) || !(rmax < 0.5 * box[c])) return ESPP_ERR_ARG;
@@ -88,7 +90,7 @@ extern "C" int espp_rdf_counts_noalloc(const double* x_device, int64_t n, const 
     if (cudaMemsetAsync(scratch, 0, (size_t)nbins * sizeof(unsigned long long), st) != cudaSuccess)
         return ESPP_ERR_CUDA;
     if (n > 1) {
-        espp::k_rdf_noalloc<<<4 * 152, 256, sizeof(unsigned int) * nbins, st>>>(
+        espp::k_rdf_noalloc<<<4 * espp::sm_count(), 256, sizeof(unsigned int) * nbins, st>>>(
             x_device, (int)n, box[0], box[1], box[2], rmax * rmax, nbins / rmax, nbins, scratch);
     }
     espp::k_rdf_noalloc_finish<<<(nbins + 255) / 256, 256, 0, st>>>(scratch, nbins, counts_device);

@@ -316,6 +316,7 @@ class System : public SystemBase {
             (rc = alloc(&d_mol_rep, mol_rep_h.size(), allocs)) ||
             (rc = alloc(&d_mol_rg2, mol_rep_h.size(), allocs)) ||
             (rc = alloc(&d.mlp_f, n, allocs)) || (rc = alloc(&d.mlp_w, n, allocs)) ||
+            (sizeof(T) == 8 && ((rc = alloc(&d.mlp_fT, n, allocs)) || (rc = alloc(&d.mlp_wT, n, allocs)))) ||
             (rc = alloc(&d_mlp, 1, allocs)) || (rc = alloc(&d_le_clk, 1, allocs)) ||
             (rc = alloc(&d.le_db, (size_t)R, allocs)))
             return rc;
@@ -642,6 +643,9 @@ class System : public SystemBase {
         le_clk_h.t0 = t0;
         le_clk_h.dt = dt;
         le_clk_h.s0 = s0;
+        // the kernels read the clock under Lees-Edwards only; switching it on
+        // (or loading a sheared checkpoint) passes through here again
+        if (!d.le_on) return ESPP_OK;
         CK(cudaMemcpyAsync(d_le_clk, &le_clk_h, sizeof(LeClock), cudaMemcpyHostToDevice, st));
         CK(cudaStreamSynchronize(st));
         return ESPP_OK;
@@ -816,7 +820,7 @@ class System : public SystemBase {
         const int ngrad = mlp_ngrad();
         const int nep = std::max(epochs, 1);
         if (!t_err) {
-            t_blocks = 2 * 152;  // two blocks of the gradient kernel per SM
+            t_blocks = 2 * sm_count();  // two blocks of the gradient kernel per SM
             int rc0;
             if ((rc0 = alloc(&t_err, (size_t)N, allocs)) || (rc0 = alloc(&t_loss_part, (size_t)d.ntiles, allocs)) ||
                 (rc0 = alloc(&t_partials, (size_t)(t_blocks + 16) * ngrad, allocs)) || (rc0 = alloc(&t_grad, ngrad, allocs)) ||
@@ -862,7 +866,7 @@ class System : public SystemBase {
                     // a training frame needs its list, not a new storage order
                     rcode = rebuild_now(false, false);
                     if (rcode) return rcode;
-                    launches += Launch<T>::mlp(d, cur, false, st);
+                    launches += Launch<T>::mlp_tc(d, cur, false, st);
                     launches += Launch<T>::train_grad(d, cur, Y + f * n3, t_err, t_loss_part, scale, t_partials,
                                                           t_blocks, t_grad, t_loss + ep, st);
                     CK(cudaGetLastError());
@@ -1148,7 +1152,9 @@ class System : public SystemBase {
         return ESPP_OK;
     }
 
-    int ensure_list() {
+    // Rebuilds the list when it is stale; *out (if given) receives the
+    // control block as it stands afterwards.
+    int ensure_list(Ctrl* out = nullptr) {
         if (!state_set) return fail(ESPP_ERR_STATE, "no state set");
         if (d.mlp_on && mlp_bits.empty()) return fail(ESPP_ERR_STATE, "learned potential selected but no weights set");
         if (d.mlp_on && d.le_on) return fail(ESPP_ERR_STATE, "Lees-Edwards is not available with the learned potential");
@@ -1160,7 +1166,12 @@ class System : public SystemBase {
         if (rcode) return rcode;
         Ctrl c = read_ctrl();
         if (c.abort) return status_from(c);
-        if (rebuild_pending || c.any_req) return rebuild_now(f_valid);
+        if (rebuild_pending || c.any_req) {
+            rcode = rebuild_now(f_valid);
+            if (rcode) return rcode;
+            if (out) c = read_ctrl();
+        }
+        if (out) *out = c;
         return ESPP_OK;
     }
 
@@ -1323,18 +1334,55 @@ class System : public SystemBase {
         return ESPP_OK;
     }
 
+    // Step counts of the captured graphs: the chunk limit itself and every
+    // power of two below it.  Any run splits into these (largest first, cut at
+    // the next resort) plus the final step, so one set of graphs serves every
+    // nsteps and no call captures a graph once prepare_graphs has run.
+    std::vector<int> chunk_sizes() const {
+        std::vector<int> out;
+        if (chunk > 0) out.push_back(chunk);
+        for (int k = 1 << 10; k >= 1; k >>= 1)
+            if (k < chunk) out.push_back(k);
+        return out;
+    }
+    int chunk_size_for(int64_t avail) const {
+        if (avail >= chunk) return chunk;
+        int k = 1;
+        while (2 * (int64_t)k <= avail) k <<= 1;
+        return k;
+    }
+
+    // Capture and instantiate every graph a run can use (both position
+    // buffers, every chunk size, the final step), so that integrate calls
+    // after the first one on a configuration launch cached graphs only.
+    int prepare_graphs() {
+        if (chunk <= 0) return ESPP_OK;
+        for (int p = 0; p < 2; ++p) {
+            ChunkGraph* cg = nullptr;
+            for (int S : chunk_sizes()) {
+                int rcode = make_chunk(S, p, false, &cg);
+                if (rcode) return rcode;
+            }
+            int rcode = make_chunk(1, p, true, &cg);
+            if (rcode) return rcode;
+        }
+        return ESPP_OK;
+    }
+
     int integrate(int64_t nsteps, double dt, double gamma, double kT) override {
         if (nsteps < 0 || !(dt > 0) || !(gamma >= 0) || !(kT >= 0) || !std::isfinite(dt) || !std::isfinite(gamma) ||
             !std::isfinite(kT))
             return fail(ESPP_ERR_ARG, "need nsteps >= 0 and finite dt > 0, gamma >= 0, kT >= 0");
         if (nsteps == 0) return ESPP_OK;
-        int rcode = ensure_list();
+        Ctrl c0;
+        int rcode = ensure_list(&c0);
         if (rcode) return rcode;
         if (d.dpd && !(dpd_rc <= rc_list * (1 + 1e-12)))
             return fail(ESPP_ERR_ARG, "the DPD cutoff exceeds the list cutoff");
         rcode = upload_int_params(dt, gamma, kT);
         if (rcode) return rcode;
-        Ctrl c0 = read_ctrl();
+        rcode = prepare_graphs();
+        if (rcode) return rcode;
         const int64_t step0 = c0.step;
         const int64_t target = step0 + nsteps;
         const int64_t rb0 = c0.n_rebuilds;
@@ -1359,7 +1407,6 @@ class System : public SystemBase {
             // positions of step done+1 live in buffer (1 - c_start) ^ ((done - step0) & 1)
             int p = (1 - c_start) ^ (int)((done - step0) & 1);
             int64_t next = done + 1;  // step the next graph computes first
-            ChunkGraph* last_cg = nullptr;
             int64_t host_rebuilds = 0;  // rebuilds launched here rather than by graph nodes
             while (next <= target) {
                 // Hilbert resort (with a list rebuild) before every step that is
@@ -1369,33 +1416,37 @@ class System : public SystemBase {
                     launches += 1 + Launch<T>::rebuild(d, p, true, false, st);
                     host_rebuilds++;
                 }
-                int64_t S = std::min<int64_t>(target - next + 1, chunk > 0 ? chunk : 64);
-                if (resort_every > 0) {
-                    const int64_t to_resort = resort_every - (next % resort_every);
-                    S = std::min<int64_t>(S, to_resort);
-                }
-                const bool fin = next + S - 1 == target;
+                // steps before the final one, up to the next resort
+                int64_t avail = target - next;
+                if (resort_every > 0) avail = std::min<int64_t>(avail, resort_every - (next % resort_every));
+                const bool fin = avail == 0;  // only the final step is left
                 if (chunk == 0) {
                     // direct launches (profilers cannot see kernels inside
                     // conditional graphs): early-exit rebuild kernels + step
                     host_rebuilds = -1;  // every kernel is counted as launched
+                    const int64_t S = fin ? 1 : avail;
                     for (int64_t r = 0; r < S; ++r) {
                         launches += Launch<T>::rebuild(d, p, false, false, st);
-                        const int mode = (fin && r == S - 1) ? MODE_FINAL : MODE_STEP;
-                        launches += Launch<T>::step(d, mode, false, p, nullptr, 0ull, 0, st);
-                        if (mode == MODE_STEP) p ^= 1;
+                        launches += Launch<T>::step(d, fin ? MODE_FINAL : MODE_STEP, false, p, nullptr, 0ull, 0, st);
+                        if (!fin) p ^= 1;
                     }
                     CK(cudaGetLastError());
                     next += S;
                     continue;
                 }
+                const int S = fin ? 1 : chunk_size_for(avail);
                 ChunkGraph* cg = nullptr;
-                rcode = make_chunk((int)S, p, fin, &cg);
+                rcode = make_chunk(S, p, fin, &cg);
                 if (rcode) return rcode;
                 CK(cudaGraphLaunch(cg->exec, st));
-                last_cg = cg;
-                launches += 1 + S * step_kernels();
-                p ^= (int)((fin ? (S - 1) : S) & 1);
+                launches += 1 + (int64_t)S * step_kernels();
+                if (timing) {
+                    // every replay is read back (a graph's events hold its last replay only)
+                    CK(cudaStreamSynchronize(st));
+                    rcode = harvest_timing(cg);
+                    if (rcode) return rcode;
+                }
+                if (!fin) p ^= S & 1;
                 next += S;
             }
             Ctrl c = read_ctrl();
@@ -1413,13 +1464,11 @@ class System : public SystemBase {
                 if (rcode) return rcode;
                 launches += Launch<T>::rebuild(d, pm, true, false, st);
                 CK(cudaGetLastError());
+                rcode = prepare_graphs();  // the grown list is a new kernel argument
+                if (rcode) return rcode;
                 continue;
             }
             if (c.step != target) return fail(ESPP_ERR_STATE, "step counter mismatch after integrate");
-            if (timing && last_cg) {
-                rcode = harvest_timing(last_cg);
-                if (rcode) return rcode;
-            }
             cur = (1 - c_start) ^ (int)((nsteps - 1) & 1);
             return ESPP_OK;
         }
@@ -1748,7 +1797,8 @@ class System : public SystemBase {
 
     // kernels of one step inside the step graphs (Launch::step)
     int step_kernels() const {
-        int k = 1 + (d.mlp_on ? 3 : 0);
+        // the learned potential: stage + tile + gather (FP32), one kernel (FP64)
+        int k = 1 + (d.mlp_on ? (sizeof(T) == 8 ? 1 : 3) : 0);
         if (d.cells_mode) k += 1;  // cell-stencil forces
         else if (d.dpd) k += 1;    // velocity snapshot
         return k;

@@ -69,6 +69,7 @@ EXPORTS = (
     "espp_tune_force_method",
 )
 NOALLOC_MAX_BINS = 4096
+NOALLOC_MAX_N = 200000
 
 
 class EsppError(RuntimeError):
@@ -209,7 +210,22 @@ def bf16_bits_to_float(b):
 
 def espp_rdf_counts_noalloc(x_device, box, rmax, counts_device, stream=0):
     """Pair-distance histogram from device positions into device counts,
-    without any allocation inside the library (see include/espp.h)."""
+    without any allocation inside the library (see include/espp.h).
+
+    x_device: contiguous CUDA float64 tensor of shape (n, 3); counts_device:
+    contiguous CUDA int64 tensor on the same device, one entry per bin.  The
+    library reads and writes these buffers by raw address, so anything else is
+    refused here (ValueError) before the call."""
+    import torch
+    if not (isinstance(x_device, torch.Tensor) and isinstance(counts_device, torch.Tensor)):
+        raise ValueError("x_device and counts_device must be torch tensors")
+    if not (x_device.is_cuda and counts_device.is_cuda) or x_device.device != counts_device.device:
+        raise ValueError("x_device and counts_device must be CUDA tensors on the same device")
+    if x_device.dtype != torch.float64 or x_device.dim() != 2 or x_device.shape[1] != 3 \
+            or not x_device.is_contiguous():
+        raise ValueError("x_device must be a contiguous float64 tensor of shape (n, 3)")
+    if counts_device.dtype != torch.int64 or counts_device.dim() != 1 or not counts_device.is_contiguous():
+        raise ValueError("counts_device must be a contiguous one-dimensional int64 tensor")
     n = x_device.shape[0]
     b = (ctypes.c_double * 3)(*[float(v) for v in box])
     _check(lib().espp_rdf_counts_noalloc(ctypes.c_void_p(x_device.data_ptr()), n, b, float(rmax),

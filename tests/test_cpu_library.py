@@ -88,3 +88,46 @@ def test_plain_c_client_builds_and_runs(lib, tmp_path):
     out = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert out.returncode == 0, (out.returncode, out.stdout, out.stderr)
     assert out.stdout.startswith(("create refused:", "ok"))
+
+
+# Every documented argument error of the allocation-free histogram is caught
+# on the host before any GPU work, so these calls need no GPU: the pointers
+# are never dereferenced.
+_BOX = (10.0, 10.0, 10.0)
+NOALLOC_REFUSALS = {
+    "n_negative": dict(n=-1),
+    "n_above_limit": dict(n=espp.NOALLOC_MAX_N + 1),
+    "nbins_zero": dict(nbins=0),
+    "nbins_above_limit": dict(nbins=espp.NOALLOC_MAX_BINS + 1),
+    "rmax_zero": dict(rmax=0.0),
+    "rmax_negative": dict(rmax=-1.0),
+    "rmax_half_box": dict(rmax=5.0),
+    "rmax_nan": dict(rmax=float("nan")),
+    "box_edge_zero": dict(box=(10.0, 0.0, 10.0)),
+    "null_positions": dict(x=0),
+    "null_counts": dict(counts=0),
+    "null_box": dict(box=None),
+}
+
+
+def _noalloc_raw(L, n=10, nbins=16, rmax=2.0, box=_BOX, x=0x1000, counts=0x2000):
+    import ctypes
+    b = None if box is None else (ctypes.c_double * 3)(*box)
+    return L.espp_rdf_counts_noalloc(ctypes.c_void_p(x), n, b, rmax, nbins, ctypes.c_void_p(counts),
+                                     ctypes.c_void_p(0))
+
+
+@pytest.mark.parametrize("case", sorted(NOALLOC_REFUSALS))
+def test_noalloc_refuses_bad_arguments_on_the_host(lib, case):
+    assert _noalloc_raw(lib, **NOALLOC_REFUSALS[case]) == espp.ESPP_ERR_ARG
+
+
+def test_noalloc_binding_refuses_wrong_tensors_before_the_call(lib):
+    torch = pytest.importorskip("torch")
+    # host tensors are refused by the binding (the library would read them
+    # as device memory); so are the wrong dtypes and shapes, checked first
+    with pytest.raises(ValueError):
+        espp.espp_rdf_counts_noalloc(torch.zeros((4, 3), dtype=torch.float32), _BOX, 2.0,
+                                     torch.zeros(8, dtype=torch.int64))
+    with pytest.raises(ValueError):
+        espp.espp_rdf_counts_noalloc(np.zeros((4, 3)), _BOX, 2.0, np.zeros(8, dtype=np.int64))

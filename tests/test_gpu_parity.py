@@ -166,14 +166,47 @@ def test_observables_match_oracle(case_fn, prec):
     assert o["n_molecules"] == int(oo["nmol"])
 
 
+def _edge_pairs(box, x, rmax, nbins, band):
+    """Per bin edge k (k = 0..nbins, edge k at k rmax / nbins): the number of
+    unique pairs whose minimum-image distance lies within a relative `band`
+    of that edge.  Only such pairs can land in different bins on two sides
+    that round the distance differently."""
+    n = x.shape[0]
+    near = np.zeros(nbins + 1, dtype=np.int64)
+    dr = rmax / nbins
+    for i in range(n - 1):
+        d = x[i] - x[i + 1:]
+        d -= box * np.round(d / box)
+        r = np.sqrt((d * d).sum(axis=1))
+        r = r[r < rmax * (1 + band)]
+        k = np.rint(r / dr).astype(np.int64)
+        close = np.abs(r - k * dr) <= band * np.maximum(r, dr)
+        np.add.at(near, k[close & (k <= nbins)], 1)
+    return near
+
+
 @pytest.mark.parametrize("prec", [FP32, FP64])
 def test_rdf_counts_match_oracle(prec):
+    # counts equal the oracle's bin by bin, except for pairs the two sides
+    # may round across a bin edge: those are counted and named (for the FP64
+    # path the band is 1e-12 relative, and this seed has none, so the FP64
+    # counts are compared exactly)
     case = lj_case((6, 6, 6))
     s = case.system(prec)
-    got = s.rdf_counts(3.0, 60)
-    exp = O.rdf_counts(case.cfg.box, case.cfg.x, 3.0, 60)
-    assert got.sum() == exp.sum()
-    assert np.abs(got - exp).max() <= 2
+    c = case.cfg
+    for rmax, nbins in ((3.0, 60), (4.5, 90)):   # from the list, then from all pairs
+        got = s.rdf_counts(rmax, nbins)
+        exp = O.rdf_counts(c.box, c.x, rmax, nbins)
+        near = _edge_pairs(c.box, c.x, rmax, nbins, 1e-12 if prec == FP64 else 1e-6)
+        if prec == FP64:
+            assert near.sum() == 0
+            assert np.array_equal(got, exp), np.nonzero(got != exp)
+        else:
+            # a pair near edge k moves between bins k - 1 and k; near the
+            # outer edge it may drop out of the histogram
+            slack = near[:-1] + near[1:]
+            assert np.all(np.abs(got - exp) <= slack), (np.nonzero(np.abs(got - exp) > slack), near.sum())
+            assert abs(int(got.sum()) - int(exp.sum())) <= near[-1]
 
 
 def test_batched_replicas_equal_standalone_runs():
@@ -271,17 +304,22 @@ def test_cell_subdivision_in_batches():
 
 @pytest.mark.parametrize("prec", [FP32, FP64])
 def test_direct_launches_equal_graphs(prec):
-    # the same kernels launched one by one (no CUDA graphs) give the same bits
+    # the same kernels launched one by one (no CUDA graphs), or in graphs of
+    # other step counts (a chunk limit of 5: graphs of 5, 4, 2 and 1 steps),
+    # give the same bits, whatever the split of the run into calls
     case = kg_case()
     a = case.system(prec, seed=8)
     a.integrate(150, 0.005, 1.0, 1.0)
-    b = case.system(prec, seed=8)
-    b.set_graph_chunk(0)
-    b.integrate(150, 0.005, 1.0, 1.0)
     xa, va, ia = a.get_state()
-    xb, vb, ib = b.get_state()
-    assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(ia, ib)
-    assert a.n_rebuilds == b.n_rebuilds
+    for chunk, calls in ((0, (150,)), (5, (150,)), (64, (1, 2, 20, 3, 124)), (7, (33, 117))):
+        b = case.system(prec, seed=8)
+        b.set_graph_chunk(chunk)
+        for k in calls:
+            b.integrate(k, 0.005, 1.0, 1.0)
+        xb, vb, ib = b.get_state()
+        assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(ia, ib), (chunk, calls)
+        assert a.n_rebuilds == b.n_rebuilds
+        b.close()
 
 
 @pytest.mark.parametrize("every", [0, 7, 40])
@@ -548,6 +586,58 @@ def test_full_size_kg_1m_sampled_forces(prec):
     assert rel_rms(f[sel], fo) <= FORCE_TOL[prec]
     # property at any size: Newton's third law
     assert np.abs(f.sum(axis=0)).max() <= (1e-3 if prec == FP32 else 1e-8) * np.abs(f).sum() / c.n
+    s.close()
+
+
+def _bench_melt_1m():
+    """The KG melt as the benchmark runs it: 1000 random-walk chains of 1000
+    beads (seed 42), the capped push-off, then plain WCA at dt 0.002 and
+    0.005 (4400 steps), FP32."""
+    c = I.kg_random_walk(1000, 1000, density=0.85, seed=42, bond=0.97)
+    v = I.maxwell_velocities(c.n, 1.0, seed=42)
+    s = espp.System(c.box, c.n, c.types, c.bonds, precision=FP32, seed=42)
+    s.set_fene(30.0, 1.5)
+    s.set_lj_capped(1.0, 1.0, WCA_RC, 1.05)
+    s.set_state(c.x, v, c.img)
+    s.build_neighbors(WCA_RC, 0.4)
+    for cap in (1.05, 1.0, 0.95, 0.9, 0.85, 0.8):
+        s.set_lj_capped(1.0, 1.0, WCA_RC, cap)
+        s.integrate(400, 1e-3, 1.0, 1.0)
+    s.set_wca(1.0, 1.0)
+    s.integrate(1000, 0.002, 1.0, 1.0)
+    s.integrate(1000, 0.005, 1.0, 1.0)
+    return s, c
+
+
+def test_full_size_kg_1m_in_the_benchmark_state():
+    # the timed workload itself, after the GPU has integrated it: rebuilds
+    # inside the step graphs, list growth and a Hilbert resort (every 500
+    # steps: the run crosses step 4500) have all happened at 1M beads; then
+    # forces and neighbour sets of sampled particles against the oracle on
+    # the stored positions
+    s, c = _bench_melt_1m()
+    rb0 = s.n_rebuilds
+    s.integrate(300, 0.005, 1.0, 1.0)
+    assert s.step == 4700 and s.n_rebuilds - rb0 >= 10
+    x, _, _ = s.get_state()
+    f = s.compute_forces()
+    sel = np.random.default_rng(3).choice(c.n, 4000, replace=False)
+    model = O.Model(1, KG_PAIR, KG_BOND)
+    fo = O.forces_subset(model, c.box, x, c.types, c.bonds, sel)
+    assert rel_rms(f[sel], fo) <= FORCE_TOL[FP32], rel_rms(f[sel], fo)
+    # neighbour sets of a list built now, for the stored positions, against
+    # the oracle's cell search, exact outside the 1e-6 sigma band at rc + skin
+    s.build_neighbors(WCA_RC, 0.4)
+    row, cols = s.get_neighbors()
+    orow, ocols = O.neighbors(c.box, x, WCA_RC + 0.4, method="cells")
+    rl = WCA_RC + 0.4
+    for i in sel[:1000]:
+        got = set(cols[row[i]:row[i + 1]].tolist())
+        exp = set(ocols[orow[i]:orow[i + 1]].tolist())
+        for j in got ^ exp:
+            d = x[i] - x[j]
+            d -= c.box * np.round(d / c.box)
+            assert abs(np.sqrt(d @ d) - rl) < 1e-6, (i, j)
     s.close()
 
 

@@ -593,6 +593,73 @@ def test_force_matching_gradient_by_finite_differences():
         O.set_mlp(p, 3.5)
 
 
+def _loss_by_hand(X, Y, box, bonds, rc, rb_max, ub, fb, variant="right"):
+    """Force-matching loss recomputed outside the oracle's loss routine: pair
+    forces F_i = sum_j -u'(r_ij) (x_i - x_j)/r_ij over unordered pairs
+    (bonded 1-2 pairs excluded) from the per-pair derivative alone, bond
+    forces from a linear interpolation of the bond table, then
+    loss = sum_f sum_i |F_i - Y_fi|^2 / (frames x sites).  `variant` plants
+    one of three plausible mistakes, to show that the pin would see it."""
+    nf, n, _ = X.shape
+    bset = {(min(a, b), max(a, b)) for a, b in bonds}
+    total = 0.0
+    for f in range(nf):
+        x = X[f]
+        F = np.zeros((n, 3))
+        for i in range(n):
+            d = x[i] - x[i + 1:]
+            d -= box * np.round(d / box)
+            r = np.sqrt((d * d).sum(axis=1))
+            for k in np.nonzero(r < rc)[0]:
+                j = i + 1 + k
+                if (i, j) in bset:
+                    continue
+                _, du = O.mlp_pair(float(r[k]))
+                fij = -du * d[k] / r[k]
+                F[i] += fij
+                F[j] -= fij
+                if variant == "pairs_twice":
+                    F[i] += fij
+                    F[j] -= fij
+        Fb = np.zeros((n, 3))
+        for a, b in bonds:
+            d = x[a] - x[b]
+            d -= box * np.round(d / box)
+            r = float(np.sqrt(d @ d))
+            fr = np.interp(r, np.linspace(0.0, rb_max, fb.size), fb)
+            Fb[a] += fr * d / r
+            Fb[b] -= fr * d / r
+        e = (F - Fb if variant == "bond_sign" else F + Fb) - Y[f]
+        total += (e * e).sum()
+    return total / (nf if variant == "frames_only" else nf * n)
+
+
+def test_force_matching_loss_value_recomputed_by_hand():
+    # the loss value itself (not only its gradient) against an independent
+    # evaluation from per-pair derivatives and the bond table
+    c = I.kg_lattice(4, 25, density=0.2125, seed=12, jitter=0.3)
+    g = np.random.default_rng(14)
+    X = np.stack([np.mod(c.x + g.normal(0, 0.2, c.x.shape), c.box) for _ in range(2)])
+    Y = g.normal(0, 1.0, X.shape)
+    p = _mlp_params(8, 0.2)
+    O.set_mlp(p, 3.5)
+    rb = np.linspace(0.0, 4.0, 401)
+    ub, fb = 5.0 * (rb - 2.0) ** 2, -10.0 * (rb - 2.0)
+    O.set_table(9, 4.0, ub, fb)
+    model = O.Model(1, {}, ("table", 9))
+    O.set_exclude_bonded(True)
+    try:
+        loss, _ = O.mlp_loss_grad(model, c.box, X, Y, c.types, c.bonds)
+    finally:
+        O.set_exclude_bonded(False)
+    want = _loss_by_hand(X, Y, c.box, c.bonds, 3.5, 4.0, ub, fb)
+    assert abs(loss - want) < 1e-10 * abs(want), (loss, want)
+    # each planted mistake moves the value far outside that tolerance
+    for variant in ("frames_only", "bond_sign", "pairs_twice"):
+        wrong = _loss_by_hand(X, Y, c.box, c.bonds, 3.5, 4.0, ub, fb, variant)
+        assert abs(wrong - want) > 1e-3 * abs(want), variant
+
+
 # --------------------------------------------------------------------------
 # DPD thermostat (paper "Functionality": dissipative particle dynamics)
 # --------------------------------------------------------------------------
