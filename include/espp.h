@@ -391,7 +391,8 @@ int64_t espp_kernel_launches(espp_h h);
  * call the durations of the last graph replay are added up.  out[4] receives
  * (sum of step-kernel ms, number of step-kernel launches timed, sum of
  * rebuild-node ms, number of steps timed); reset = 1 clears the sums.
- * Enabling or disabling rebuilds the graphs. */
+ * Graphs with and without the timing events are cached side by side, so
+ * switching does not rebuild them after the first use of each. */
 int espp_set_kernel_timing(espp_h h, int enable);
 int espp_kernel_timing(espp_h h, double* out, int reset);
 

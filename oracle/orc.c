@@ -841,7 +841,12 @@ static void wrap_coord(double* xc, int32_t* im, double L) {
     } else if (*xc < 0.0) {
         *xc += L;
         *im -= 1;
-        if (*xc >= L) *xc = 0.0;
+        if (*xc >= L) {
+            /* x lay less than half an ulp of L below 0: it stays at 0 in its
+             * own image, so x + img L is continuous */
+            *xc = 0.0;
+            *im += 1;
+        }
     }
 }
 

@@ -119,7 +119,9 @@ __device__ __forceinline__ T shifted_diff(T xi, T xi_minus_L, T xj, T L, int c) 
 }
 
 // Wrap one coordinate into [0, L); returns the image change (-1, 0, +1).  A
-// coordinate that rounds to exactly L after adding L becomes 0.
+// coordinate that rounds to exactly L after adding L (it lay less than half
+// an ulp of L below 0) becomes 0 in its own image, so that x + img L stays
+// continuous.
 template <class T>
 __device__ __forceinline__ int wrap_coord(T& x, T L) {
     if (x >= L) {
@@ -128,11 +130,19 @@ __device__ __forceinline__ int wrap_coord(T& x, T L) {
     }
     if (x < T(0)) {
         x += L;
-        if (x >= L) x = T(0);
+        if (x >= L) {
+            x = T(0);
+            return 0;
+        }
         return -1;
     }
     return 0;
 }
+
+// The largest value of the type below L: a coordinate wrapped in double that
+// rounds up to L in the stored precision is kept in its image there.
+__device__ __forceinline__ float below(float L) { return nextafterf(L, 0.0f); }
+__device__ __forceinline__ double below(double L) { return nextafter(L, 0.0); }
 
 // ---------------------------------------------------------------------------
 // Per-replica geometry, resident in device memory.

@@ -92,7 +92,11 @@ __global__ void __launch_bounds__(TILE) k_get_state(DevSys<T> s, double* __restr
                 double w = pc[d];
                 int k = 0;
                 if (w >= L) { w -= L; k = 1; }
-                else if (w < 0.0) { w += L; k = -1; if (w >= L) w = 0.0; }
+                else if (w < 0.0) {
+                    w += L;
+                    k = -1;
+                    if (w >= L) { w = 0.0; k = 0; }  // less than half an ulp below 0: its own image
+                }
                 wc[d] = w;
                 sh[d] = k;
             }

@@ -99,9 +99,11 @@ __global__ void __launch_bounds__(TILE) k_bin(DevSys<T> s, int cur) {
             p.x = (T)q[0];
             p.y = (T)q[1];
             p.z = (T)q[2];
-            // a coordinate rounded up to L in the conversion wraps to 0
-            if (!(p.x < g.L[0])) p.x = T(0);
-            if (!(p.z < g.L[2])) p.z = T(0);
+            // a coordinate rounded up to L in the conversion stays in its
+            // image, just below L
+            if (!(p.x < g.L[0])) p.x = below(g.L[0]);
+            if (!(p.y < g.L[1])) p.y = below(g.L[1]);
+            if (!(p.z < g.L[2])) p.z = below(g.L[2]);
             v.x = (T)vx;
             s.vel[i] = v;
             wx = k[0];

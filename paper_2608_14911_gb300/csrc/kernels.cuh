@@ -185,7 +185,10 @@ __device__ __forceinline__ void le_wrap(double p[3], double& vx, int k[3], const
     } else if (p[2] < 0.0) {
         p[2] += L[2];
         k[2] = -1;
-        if (p[2] >= L[2]) p[2] = 0.0;
+        if (p[2] >= L[2]) {  // less than half an ulp below 0: its own image
+            p[2] = 0.0;
+            k[2] = 0;
+        }
     }
     if (k[2] != 0) {
         p[0] -= k[2] * delta;
@@ -204,7 +207,10 @@ __device__ __forceinline__ void le_wrap(double p[3], double& vx, int k[3], const
     } else if (p[0] < 0.0) {
         p[0] += L[0];
         k[0] = -1;
-        if (p[0] >= L[0]) p[0] = 0.0;
+        if (p[0] >= L[0]) {
+            p[0] = 0.0;
+            k[0] = 0;
+        }
     }
     if (p[1] >= L[1]) {
         p[1] -= L[1];
@@ -212,7 +218,10 @@ __device__ __forceinline__ void le_wrap(double p[3], double& vx, int k[3], const
     } else if (p[1] < 0.0) {
         p[1] += L[1];
         k[1] = -1;
-        if (p[1] >= L[1]) p[1] = 0.0;
+        if (p[1] >= L[1]) {
+            p[1] = 0.0;
+            k[1] = 0;
+        }
     }
 }
 

@@ -134,7 +134,8 @@ class System : public SystemBase {
         cudaGraphExec_t exec = nullptr;
         std::vector<cudaEvent_t> ev;  // timing mode: 3 per step (before rebuild, before step, after step)
     };
-    std::map<std::tuple<int, int, int>, ChunkGraph> graphs;
+    // key (steps, first position buffer, final step, timing events)
+    std::map<std::tuple<int, int, int, int>, ChunkGraph> graphs;
     bool timing = false;
     double t_step_ms = 0, t_rebuild_ms = 0;
     int64_t t_step_n = 0;
@@ -1236,7 +1237,7 @@ class System : public SystemBase {
 
     // -------------------------------------------------------------- integrate
     int make_chunk(int S, int p0, bool final_chunk, ChunkGraph** out) {
-        auto key = std::make_tuple(S, p0, final_chunk ? 1 : 0);
+        auto key = std::make_tuple(S, p0, final_chunk ? 1 : 0, timing ? 1 : 0);
         auto it = graphs.find(key);
         if (it != graphs.end()) {
             *out = &it->second;
@@ -1315,8 +1316,8 @@ class System : public SystemBase {
     }
 
     int set_kernel_timing(int enable) override {
+        // the graphs with timing events are cached beside the plain ones
         timing = enable != 0;
-        clear_graphs();
         t_step_ms = t_rebuild_ms = 0;
         t_step_n = 0;
         return ESPP_OK;

@@ -619,7 +619,13 @@ def test_full_size_kg_1m_in_the_benchmark_state():
     rb0 = s.n_rebuilds
     s.integrate(300, 0.005, 1.0, 1.0)
     assert s.step == 4700 and s.n_rebuilds - rb0 >= 10
-    x, _, _ = s.get_state()
+    x, _, img = s.get_state()
+    # image counters: every bond of the unwrapped chains (no minimum image)
+    # is shorter than R0 after hundreds of wraps at list builds
+    u = x + img * c.box
+    b = np.asarray(c.bonds)
+    blen = np.sqrt(((u[b[:, 0]] - u[b[:, 1]]) ** 2).sum(axis=1))
+    assert blen.max() < 1.5, (blen.max(), int((blen >= 1.5).sum()))
     f = s.compute_forces()
     sel = np.random.default_rng(3).choice(c.n, 4000, replace=False)
     model = O.Model(1, KG_PAIR, KG_BOND)
@@ -638,6 +644,49 @@ def test_full_size_kg_1m_in_the_benchmark_state():
             d = x[i] - x[j]
             d -= c.box * np.round(d / c.box)
             assert abs(np.sqrt(d @ d) - rl) < 1e-6, (i, j)
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_wrap_just_below_zero_keeps_the_unwrapped_position(prec):
+    # a particle drifts to just below 0 by less than half an ulp of L in the
+    # stored precision; the wrap at the next list build must keep it in its
+    # own image (x + img L continuous), as the oracle does
+    L = 10.0
+    eps = 1e-7 if prec == FP32 else 1e-17
+    box = np.array([L, L, L])
+    s = espp.System(box, 2, None, None, precision=prec, seed=1)
+    s.set_lj(1.0, 1.0, 2.5, True)
+    x = np.array([[eps / 10, 5.0, 5.0], [5.0, 5.0, 5.0]])
+    v = np.array([[-(eps + eps / 10) / 0.005, 0.0, 0.0], [0.0, 0.0, 0.0]])
+    s.set_state(x, v)
+    s.build_neighbors(2.5, 0.3)
+    s.integrate(1, 0.005, 0.0, 0.0)
+    s.build_neighbors(2.5, 0.3)  # wraps the stored positions
+    xw, _, img = s.get_state()
+    assert 0.0 <= xw[0, 0] < L
+    assert abs(xw[0, 0] + img[0, 0] * L) < 1e-5, (xw[0, 0], img[0, 0])
+    s.close()
+
+
+def test_unwrapped_bonds_stay_short_over_a_long_run():
+    # many wraps of a melt's chains at list builds: the unwrapped chains keep
+    # every bond below R0
+    c = I.kg_random_walk(200, 100, density=0.85, seed=7, bond=0.97)
+    s = espp.System(c.box, c.n, c.types, c.bonds, precision=FP32, seed=7)
+    s.set_fene(30.0, 1.5)
+    s.set_lj_capped(1.0, 1.0, WCA_RC, 1.05)
+    s.set_state(c.x, I.maxwell_velocities(c.n, 1.0, seed=7), c.img)
+    s.build_neighbors(WCA_RC, 0.4)
+    for cap in (1.05, 0.95, 0.85):
+        s.set_lj_capped(1.0, 1.0, WCA_RC, cap)
+        s.integrate(400, 1e-3, 1.0, 1.0)
+    s.set_wca(1.0, 1.0)
+    s.integrate(6000, 0.005, 1.0, 1.0)
+    x, _, img = s.get_state()
+    u = x + img * c.box
+    b = np.asarray(c.bonds)
+    assert np.sqrt(((u[b[:, 0]] - u[b[:, 1]]) ** 2).sum(axis=1)).max() < 1.5
     s.close()
 
 

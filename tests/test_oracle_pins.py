@@ -593,6 +593,21 @@ def test_force_matching_gradient_by_finite_differences():
         O.set_mlp(p, 3.5)
 
 
+def test_wrap_just_below_zero_keeps_the_unwrapped_position():
+    # a free particle drifting from x = 1e-20 to x = -2e-18: x + L rounds to L
+    # in double, so the wrap must leave it at 0 in its own image (the
+    # unwrapped coordinate x + img L stays -2e-18, not -L); the same at the
+    # upper face for comparison
+    free = O.Model(1, {})
+    L = 10.0
+    for x0, v0 in ((1e-20, -4e-16), (L - 1e-6, 4e-4)):
+        st = O.State([L, L, L], [[x0, 5.0, 5.0]], [[v0, 0.0, 0.0]])
+        O.integrate(free, st, 1, 0.005, 0.0, 0.0, seed=1)
+        unwrapped = st.x[0, 0] + st.img[0, 0] * L
+        assert 0.0 <= st.x[0, 0] < L
+        assert abs(unwrapped - (x0 + 0.005 * v0)) < 1e-12, (st.x[0, 0], st.img[0, 0])
+
+
 def _loss_by_hand(X, Y, box, bonds, rc, rb_max, ub, fb, variant="right"):
     """Force-matching loss recomputed outside the oracle's loss routine: pair
     forces F_i = sum_j -u'(r_ij) (x_i - x_j)/r_ij over unordered pairs
