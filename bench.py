@@ -52,9 +52,12 @@ def parse():
     ap.add_argument("--suite-steps", type=int, default=1000)
     ap.add_argument("--suite-only", default="",
                     help="comma-separated names of the suite entries to run (default: all)")
-    ap.add_argument("--cg-frames", type=int, default=32)
+    ap.add_argument("--cg-frames", type=int, default=2000)
     ap.add_argument("--cg-epochs", type=int, default=10)
-    ap.add_argument("--cg-batch", type=int, default=4)
+    ap.add_argument("--cg-batch", type=int, default=16)
+    ap.add_argument("--ibi-iters", type=int, default=8)
+    ap.add_argument("--cg-eq", type=int, default=1000)
+    ap.add_argument("--cg-snap", type=int, default=20)
     ap.add_argument("--cg-warm", type=int, default=1000)
     ap.add_argument("--cg-steps", type=int, default=200)
     ap.add_argument("--cg-probe", type=int, default=0,
@@ -678,10 +681,11 @@ def suite_batched(a, sync):
     return out
 
 
-def _bond_table_boltzmann(xs, nchains, sites_per_chain, box, kT=1.0, dr=0.02, rmax=6.0):
+def _bond_table_boltzmann(xs, nchains, sites_per_chain, box, kT=1.0, dr=0.02, rmax=6.0, min_count=100):
     """Boltzmann-inverted CG bond potential from mapped frames:
-    U(b) = -kT ln(P(b) / b^2), F = -dU/db, linearly extrapolated outside the
-    sampled range, on a grid from 0 to rmax."""
+    U(b) = -kT ln(P(b) / b^2) on the bins holding at least min_count bonds,
+    smoothed over five bins, continued linearly outside them with restoring
+    slopes (at least kT / sigma); F = -dU/db on a grid from 0 to rmax."""
     b = []
     for x in xs:
         x = x.reshape(nchains, sites_per_chain, 3)
@@ -692,15 +696,14 @@ def _bond_table_boltzmann(xs, nchains, sites_per_chain, box, kT=1.0, dr=0.02, rm
     edges = np.arange(0.0, rmax + dr, dr)
     hist, _ = np.histogram(b, bins=edges)
     centres = 0.5 * (edges[1:] + edges[:-1])
-    ok = hist > 0
-    U = np.full(centres.size, np.nan)
-    U[ok] = -kT * np.log(hist[ok] / (centres[ok] ** 2))
-    idx = np.nonzero(ok)[0]
-    lo, hi = idx[0], idx[-1]
-    U = np.interp(centres, centres[ok], U[ok])
-    # linear extrapolation with the edge slopes (restoring at both ends)
-    sl = min((U[lo + 2] - U[lo]) / (2 * dr), -1.0)
-    sh = max((U[hi] - U[hi - 2]) / (2 * dr), 1.0)
+    ok = np.nonzero(hist >= min_count)[0]
+    lo, hi = ok[0], ok[-1]
+    U = np.interp(centres, centres[ok], -kT * np.log(hist[ok] / centres[ok] ** 2))
+    pad = 2
+    U[lo:hi + 1] = np.convolve(np.pad(U[lo:hi + 1], pad, mode="edge"), np.ones(5) / 5.0, mode="valid")
+    # linear continuation with the edge slopes (restoring at both ends)
+    sl = min((U[lo + 3] - U[lo]) / (3 * dr), -1.0)
+    sh = max((U[hi] - U[hi - 3]) / (3 * dr), 1.0)
     U[:lo] = U[lo] + sl * (centres[:lo] - centres[lo])
     U[hi + 1:] = U[hi] + sh * (centres[hi + 1:] - centres[hi])
     grid = np.linspace(0.0, rmax, 1201)
@@ -709,13 +712,119 @@ def _bond_table_boltzmann(xs, nchains, sites_per_chain, box, kT=1.0, dr=0.02, rm
     return rmax, Ug - Ug.min(), Fg, float(b.mean())
 
 
+RCM, SKIN_CG, DR_G = 3.5, 0.5, 0.02
+
+
+def _gofr(counts, n, box, dr=DR_G):
+    """g(r) of unique-pair counts per bin (ideal-gas shell normalisation)."""
+    r0 = np.arange(counts.size) * dr
+    shell = 4.0 / 3.0 * np.pi * ((r0 + dr) ** 3 - r0 ** 3)
+    rho = n / np.prod(box)
+    return counts / (0.5 * n * rho * shell)
+
+
+def _rdf_l2(ga, gb, dr=DR_G, rmax=RCM):
+    """L2 distance of two g(r): sqrt(sum (ga - gb)^2 dr / rmax)."""
+    return float(np.sqrt(((ga - gb) ** 2).sum() * dr / rmax))
+
+
+def _cg_handle(box, n, bonds, bond_tab, pair, seed):
+    """A CG handle: the Boltzmann-inverted bond table, 1-2 bonded pairs out of
+    the pair potential, and pair = ("mlp", bits) | ("table", u, F) | None."""
+    from paper_2608_14911_gb300 import espp
+    h = espp.System(box, n, None, bonds, precision=espp.ESPP_FP32, seed=seed)
+    if pair is not None and pair[0] == "mlp":
+        h.set_mlp(RCM, pair[1])
+    elif pair is not None:
+        h.set_table_pair(RCM, pair[1], pair[2])
+    h.set_table_bond(*bond_tab[:3])
+    h.set_exclude_bonded(True)
+    return h
+
+
+def _sampled_rdf(h, x0, v0, eq, nsnap, every):
+    """Mean unique non-bonded pair counts (bins of DR_G up to RCM) over nsnap
+    snapshots every `every` steps after `eq` steps from (x0, v0)."""
+    h.set_state(x0, v0)
+    h.build_neighbors(RCM, SKIN_CG)
+    h.integrate(eq, 0.005, 1.0, 1.0)
+    counts = np.zeros(int(round(RCM / DR_G)))
+    for _ in range(nsnap):
+        h.integrate(every, 0.005, 1.0, 1.0)
+        counts += h.rdf_counts(RCM, counts.size)
+    return counts / nsnap
+
+
+def _table_from_potential(U_bins, rt):
+    """Pair table (u, F = -du/dr) on the grid rt from a potential on the bin
+    centres: linear interpolation, a cosine taper over the last 0.5 sigma so
+    that u and F reach 0 at the cutoff, F by central differences."""
+    rc_b = (np.arange(U_bins.size) + 0.5) * DR_G
+    U = np.interp(rt, rc_b, U_bins)
+    U = U - np.interp(RCM, rc_b, U_bins)
+    taper = np.where(rt < RCM - 0.5, 1.0, 0.5 * (1.0 + np.cos(np.pi * (rt - (RCM - 0.5)) / 0.5)))
+    U = U * taper
+    F = -np.gradient(U, rt)
+    return U, F
+
+
+def _reliable_from(counts_total, min_count=100):
+    """First bin from which every bin holds at least min_count pairs (summed
+    over the sampled snapshots): below it the core is too sparsely sampled
+    for a logarithm."""
+    ok = counts_total >= min_count
+    bad = np.nonzero(~ok)[0]
+    return 0 if bad.size == 0 else int(bad[-1]) + 1
+
+
+def _core_extrapolate(U, first, min_slope=-2.0):
+    """U below bin `first` continued linearly, repulsive (U grows toward r = 0)
+    with the slope of the first sampled bins, at least |min_slope|."""
+    k = min(first + 5, U.size - 1)
+    slope = min((U[k] - U[first]) / ((k - first) * DR_G), min_slope)
+    idx = np.arange(first)
+    U[:first] = U[first] + slope * (idx - first) * DR_G
+    return U
+
+
+def _smooth(v, width=3):
+    pad = width // 2
+    w = np.pad(v, pad, mode="edge")
+    return np.convolve(w, np.ones(width) / width, mode="valid")
+
+
+def _boltzmann_start(g_t, counts_total, kT=1.0):
+    """U_0(r) = -kT ln g_target(r) where the target is well sampled, smoothed
+    over three bins, continued linearly (repulsive) into the core."""
+    first = _reliable_from(counts_total)
+    U = np.zeros(g_t.size)
+    U[first:] = -kT * np.log(g_t[first:])
+    U[first:] = _smooth(U[first:])
+    return _core_extrapolate(U, first), first
+
+
+def _ibi_update(U, g, g_t, counts_g, first_t, damping=0.3):
+    """One iterative Boltzmann inversion step, U += damping kT ln(g / g_t), on
+    the bins both samples hold well (the correction smoothed over five
+    bins), the core re-extrapolated from the first of them."""
+    first = max(first_t, _reliable_from(counts_g))
+    corr = np.zeros_like(U)
+    corr[first:] = damping * np.log(g[first:] / g_t[first:])
+    corr[first:] = _smooth(corr[first:], 5)
+    U = U + corr
+    return _core_extrapolate(U, first)
+
+
 def suite_learned_cg(a, sync, out):
     """Learned CG: a fine KG melt of 2000 chains x 200 beads is mapped 4:1 onto
     100k sites every 200 steps; the CG bond table comes from Boltzmann
-    inversion; the MLP pair potential is force-matched on the frames; then a
-    4M-site CG melt runs with the MLP on the tensor cores and with the same
-    potential tabulated.  Results go into `out` as they are measured, and
-    `out["stage"]` names the part that ran last."""
+    inversion; the MLP pair potential is force-matched on the frames; its
+    judge is an independent tabulated pair potential made from the mapped
+    g(r) alone (Boltzmann inversion refined by iterative Boltzmann
+    inversion).  Both are compared with the mapped fine melt (g(r) and
+    held-out forces); then a 4M-site CG melt runs with the MLP on the tensor
+    cores and with the judge table.  Results go into `out` as they are
+    measured, and `out["stage"]` names the part that ran last."""
     import torch
     from paper_2608_14911_gb300 import espp, inputs
     # ---- fine run and frames --------------------------------------------------
@@ -728,74 +837,136 @@ def suite_learned_cg(a, sync, out):
     F = a.cg_frames
     X = torch.zeros((F, ns, 3), dtype=torch.float64, device="cuda")
     Y = torch.zeros_like(X)
+    t0 = time.perf_counter()
     for k in range(F):
         f.integrate(200, 0.005, 1.0, 1.0)
         f.cg_map(bps, X[k], Y[k])
+    sync()
+    frames_s = time.perf_counter() - t0
     f.close()
-    out["stage"] = "training"
     sites_per_chain = nb // bps
-    rmax, ub, fb, bmean = _bond_table_boltzmann(X.cpu().numpy(), nch, sites_per_chain, cfg.box)
+    every = max(1, F // 200)
+    bond_tab = _bond_table_boltzmann(X[::every].cpu().numpy(), nch, sites_per_chain, cfg.box)
+    x_start = X[F - max(1, F // 10)].cpu().numpy()  # first held-out frame: the start of the CG runs
     cg_bonds = inputs.chain_bonds(nch, sites_per_chain)
+    n_hold = max(1, F // 10)
+    n_train = F - n_hold
+    out["frames"] = {"frames": F, "frames_spec": 2000, "steps_between": 200, "sites": ns,
+                     "train": n_train, "held_out": n_hold, "generation_s": frames_s}
+    # ---- target: the mapped fine melt's non-bonded g(r) ----------------------
+    out["stage"] = "mapped g(r)"
+    probe = _cg_handle(cfg.box, ns, cg_bonds, bond_tab, None, 43)
+    nbin = int(round(RCM / DR_G))
+    tgt_total = np.zeros(nbin)
+    tframes = list(range(0, F, every))
+    for k in tframes:
+        probe.set_state(X[k])
+        if k == 0:
+            probe.build_neighbors(RCM, SKIN_CG)
+        tgt_total += probe.rdf_counts(RCM, nbin)
+    g_t = _gofr(tgt_total / len(tframes), ns, cfg.box)
+    # ---- judge table: Boltzmann inversion + iterative Boltzmann inversion -----
+    out["stage"] = "judge table (IBI)"
+    rt = np.linspace(0.0, RCM, 4096)
+    U, first_t = _boltzmann_start(g_t, tgt_total)
+    vmax = inputs.maxwell_velocities(ns, 1.0, seed=47)
+    ibi_l2, ibi_fmax, best = [], [], None
+    for it in range(a.ibi_iters):
+        ut, ft = _table_from_potential(U, rt)
+        ibi_fmax.append(float(np.abs(ft).max()))
+        h = _cg_handle(cfg.box, ns, cg_bonds, bond_tab, ("table", ut, ft), 100 + it)
+        c = _sampled_rdf(h, x_start, vmax, a.cg_eq, a.cg_snap, 25)
+        h.close()
+        g = _gofr(c, ns, cfg.box)
+        l2 = _rdf_l2(g, g_t)
+        ibi_l2.append(l2)
+        if best is None or l2 < best[0]:
+            best = (l2, ut.copy(), ft.copy(), U.copy())
+        U = _ibi_update(U, g, g_t, c * a.cg_snap, first_t)
+    _, ut, ft, _ = best
+    out["judge_table"] = {"method": "Boltzmann inversion of the mapped non-bonded g(r) (bins with >= 100 sampled "
+                                    "pairs; the core continued linearly), then %d iterations of iterative Boltzmann "
+                                    "inversion (damping 0.3), the best kept" % a.ibi_iters,
+                          "rdf_l2_per_iteration": ibi_l2, "max_abs_force_per_iteration": ibi_fmax,
+                          "core_below_r": first_t * DR_G}
+    probe.close()
     # ---- training -------------------------------------------------------------
-    RCM, SKIN = 3.5, 0.5
+    out["stage"] = "training"
     g = np.random.default_rng(4)
     lim1, lim2, lim3 = np.sqrt(6 / (32 + 64)), np.sqrt(6 / 128), np.sqrt(6 / 65)
     w0 = np.concatenate([g.uniform(-lim1, lim1, 64 * 32), np.zeros(64), g.uniform(-lim2, lim2, 64 * 64),
                          np.zeros(64), g.uniform(-lim3, lim3, 64), [0.0]])
     bits = espp.to_bf16_bits(w0)
-    c = espp.System(cfg.box, ns, None, cg_bonds, precision=espp.ESPP_FP32, seed=43)
-    c.set_mlp(RCM, bits)
-    c.set_table_bond(rmax, ub, fb)
-    c.set_exclude_bonded(True)
-    c.set_state(X[0].cpu().numpy())
-    c.build_neighbors(RCM, SKIN)
+    c = _cg_handle(cfg.box, ns, cg_bonds, bond_tab, ("mlp", bits), 43)
+    c.set_state(X[0])
+    c.build_neighbors(RCM, SKIN_CG)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     sync()
     e0.record()
-    loss = c.mlp_train(X, Y, batch_frames=a.cg_batch, epochs=a.cg_epochs, lr=1e-3, seed=4)
+    loss = c.mlp_train(X[:n_train], Y[:n_train], batch_frames=a.cg_batch, epochs=a.cg_epochs, lr=1e-3, seed=4)
     e1.record()
     sync()
     train_ms = e0.elapsed_time(e1)
     trained = c.mlp_weights()
     # tensor work of one frame: unique pairs inside the cutoff x (24576 flop
     # forward, values and tangents, + 2 x 24576 backward to the weights)
-    tr_pairs = float(c.rdf_counts(3.5, 175).sum()) - len(cg_bonds)
+    tr_pairs = float(c.rdf_counts(RCM, nbin).sum())
     tr_flop = 3 * 24576.0 * tr_pairs
-    tr_s = train_ms / 1e3 / a.cg_epochs / F
+    tr_s = train_ms / 1e3 / a.cg_epochs / n_train
     peaks_t, peak_kind_t = measured_peaks()
     tr_peak = peaks_t.get("bf16_tflops_sustained", peaks_t["bf16_tflops"])
-    out["training"] = {"workload": "kg_2000x200_mapped_4to1_100000_sites", "frames": F, "frames_spec": 2000,
-                       "epochs": a.cg_epochs, "batch_frames": a.cg_batch,
-                       "adam_steps": a.cg_epochs * (-(-F // a.cg_batch)), "s_per_epoch": train_ms / 1e3 / a.cg_epochs,
-                       "s_per_epoch_per_frame": train_ms / 1e3 / a.cg_epochs / F,
-                       "loss_first_epoch": float(loss[0]), "loss_last_epoch": float(loss[-1]),
-                       "cg_mean_bond": bmean,
+    c.close()
+    # ---- held-out forces and losses: zero pair force, judge table, MLP ------
+    out["stage"] = "held-out forces"
+    models = {"zero_pair": None, "judge_table": ("table", ut, ft), "mlp": ("mlp", trained)}
+    held = {}
+    for name, pair in models.items():
+        h = _cg_handle(cfg.box, ns, cg_bonds, bond_tab, pair, 44)
+        se = den = 0.0
+        fq = torch.zeros((ns, 3), dtype=torch.float64, device="cuda")
+        for q in range(n_hold):
+            h.set_state(X[n_train + q])
+            if q == 0:
+                h.build_neighbors(RCM, SKIN_CG)
+            h.compute_forces(fq)
+            yq = Y[n_train + q]
+            se += float(((fq - yq) ** 2).sum())
+            den += float((yq ** 2).sum())
+        h.close()
+        held[name] = {"loss": se / (n_hold * ns), "force_rel_rms": float(np.sqrt(se / den))}
+    out["training"] = {"workload": "kg_2000x200_mapped_4to1_100000_sites", "frames_train": n_train,
+                       "frames_spec": 2000, "epochs": a.cg_epochs, "epochs_spec": 50, "batch_frames": a.cg_batch,
+                       "adam_steps": a.cg_epochs * (-(-n_train // a.cg_batch)),
+                       "s_per_epoch": train_ms / 1e3 / a.cg_epochs,
+                       "s_per_epoch_per_frame": tr_s,
+                       "loss_per_epoch": [float(v) for v in loss],
+                       "held_out": held,
+                       "loss_note": "force-matching loss = mean over frames and sites of |F_pair + F_bond - F_mapped|^2; "
+                                    "training loss per epoch on the training frames, held-out losses on the last "
+                                    "%d frames; zero_pair = bonds only (the floor any pair model must beat)" % n_hold,
+                       "cg_mean_bond": bond_tab[3],
                        "roofline": {"bound": "tensor", "unique_pairs_per_frame": tr_pairs,
                                     "flop_per_frame": tr_flop, "achieved": tr_flop / tr_s / 1e12,
                                     "unit": "TFLOP/s", "peak": tr_peak, "frac": tr_flop / tr_s / 1e12 / tr_peak,
                                     "peak_kind": peak_kind_t + " (bf16_tflops_sustained)",
                                     "timed": "whole epochs: state upload, list build, forces, gradient, Adam"}}
-    c.close()
-    # ---- 4M CG sites: MLP on tensor cores vs the same potential tabulated -----
+    # ---- structure: MLP and judge table against the mapped g(r) ---------------
+    out["stage"] = "structure at 100k sites"
+    gs = {}
+    for name in ("mlp", "judge_table"):
+        h = _cg_handle(cfg.box, ns, cg_bonds, bond_tab, models[name], 61)
+        gs[name] = _gofr(_sampled_rdf(h, x_start, vmax, a.cg_eq, 2 * a.cg_snap, 25), ns, cfg.box)
+        h.close()
+    out["structure"] = {"rdf_l2_mlp_vs_mapped": _rdf_l2(gs["mlp"], g_t),
+                        "rdf_l2_table_vs_mapped": _rdf_l2(gs["judge_table"], g_t),
+                        "rdf_l2_mlp_vs_table": _rdf_l2(gs["mlp"], gs["judge_table"]),
+                        "protocol": "100k CG sites from a held-out mapped frame, Langevin T 1, %d steps, then g(r) "
+                                    "(non-bonded pairs, dr %.2f to %.1f) over %d snapshots 25 steps apart; target: "
+                                    "the mapped g(r) of %d frames" % (a.cg_eq, DR_G, RCM, 2 * a.cg_snap, len(tframes))}
+    # ---- 4M CG sites: MLP on tensor cores vs the judge table -------------------
     out["stage"] = "4M CG melt"
     cg = inputs.kg_lattice(16000, 250, density=0.2125, seed=44, jitter=0.1)
-    rt = np.linspace(0.0, RCM, 4096)
-    # the trained potential sampled for the table (a function of r only)
-    tab_sys = espp.System(np.array([20.0, 20.0, 20.0]), 2, None, None, precision=espp.ESPP_FP64)
-    tab_sys.set_mlp(RCM, trained)
-    ut, ft = np.zeros(rt.size), np.zeros(rt.size)
-    xs2 = np.zeros((2, 3))
-    for k, r in enumerate(rt):
-        xs2[0] = (5.0, 5.0, 5.0)
-        xs2[1] = (5.0 + max(r, 1e-3), 5.0, 5.0)
-        tab_sys.set_state(xs2)
-        if k == 0:
-            tab_sys.build_neighbors(RCM, SKIN)
-        fr = tab_sys.compute_forces()
-        ft[k] = fr[1, 0]  # F = -dU/dr on the particle at larger x
-        ut[k] = tab_sys.observables()["pe_pair"]
-    tab_sys.close()
     res = {}
     forces = {}
     n_snap, snap_every = 40, 20
@@ -806,10 +977,10 @@ def suite_learned_cg(a, sync, out):
             s.set_mlp(RCM, trained)
         else:
             s.set_table_pair(RCM, ut, ft)
-        s.set_table_bond(rmax, ub, fb)
+        s.set_table_bond(*bond_tab[:3])
         s.set_exclude_bonded(True)
         s.set_state(cg.x, inputs.maxwell_velocities(cg.n, 1.0, seed=46), cg.img)
-        s.build_neighbors(RCM, SKIN)
+        s.build_neighbors(RCM, SKIN_CG)
         forces[mode] = s.compute_forces()
         s.integrate(a.cg_warm, 0.005, 1.0, 1.0)
         steps = a.cg_steps
@@ -821,30 +992,24 @@ def suite_learned_cg(a, sync, out):
             s.integrate(64, 0.005, 1.0, 1.0)
         kt = s.kernel_timing(reset=True)
         s.set_kernel_timing(False)
-        # g(r) averaged over snapshots at the same step numbers for both
-        counts = np.zeros(175)
+        counts = np.zeros(nbin)
         for _ in range(n_snap):
             s.integrate(snap_every, 0.005, 1.0, 1.0)
-            counts += s.rdf_counts(3.5, 175)
+            counts += s.rdf_counts(RCM, nbin)
         counts /= n_snap
         res[mode] = {"value": cg.n * steps / (ms / 1e3), "unit": "site-steps/s", "steps": steps,
-                     "ms_per_step": ms / steps, "fine_bead_equivalent": 4 * cg.n * steps / (ms / 1e3),
+                     "steps_spec": 10000, "ms_per_step": ms / steps,
+                     "fine_bead_equivalent": 4 * cg.n * steps / (ms / 1e3),
                      "force_eval_ms": kt["step_ms"] / max(1, kt["step_launches"])}
         res[mode]["_rdf"] = counts
         s.close()
-    dr = 0.02
-    def gofr(cnt):
-        rr = (np.arange(cnt.size) + 0.5) * dr
-        shell = 4 * np.pi * rr ** 2 * dr
-        rho = cg.n / np.prod(cg.box)
-        return cnt / (0.5 * cg.n * rho * shell)
     cm = res["mlp"].pop("_rdf")
     ct = res["table"].pop("_rdf")
-    ga, gb = gofr(cm), gofr(ct)
-    # tensor-core work of the learned potential: unique pairs inside the cutoff
-    # (all pairs of the histogram minus the excluded 1-2 bonds) x 24576 flop
-    # (two 32x64 and two 64x64 multiply-adds per pair: u and its r-derivative)
-    pairs = float(cm.sum()) - len(cg.bonds)
+    ga, gb = _gofr(cm, cg.n, cg.box), _gofr(ct, cg.n, cg.box)
+    # tensor-core work of the learned potential: unique non-bonded pairs inside
+    # the cutoff x 24576 flop (two 32x64 and two 64x64 multiply-adds per pair:
+    # u and its r-derivative)
+    pairs = float(cm.sum())
     flop = 24576.0 * pairs
     peaks, peak_kind = measured_peaks()
     fe = res["mlp"]["force_eval_ms"]
@@ -859,9 +1024,10 @@ def suite_learned_cg(a, sync, out):
                    "mlp": res["mlp"], "table": res["table"],
                    "force_rel_rms_mlp_vs_table": float(np.sqrt(((forces["mlp"] - forces["table"]) ** 2).sum()
                                                                / (forces["table"] ** 2).sum())),
-                   "rdf_l2_mlp_vs_table": float(np.sqrt(((ga - gb) ** 2).sum() * dr / 3.5)),
+                   "rdf_l2_mlp_vs_table": _rdf_l2(ga, gb),
                    "rdf_note": "g(r), dr 0.02, averaged over %d snapshots %d steps apart after %d + %d + 128 steps "
-                               "from the same start, for both potentials" % (n_snap, snap_every, a.cg_warm, a.cg_steps)}
+                               "from the same lattice start, for both potentials" % (n_snap, snap_every, a.cg_warm,
+                                                                                     a.cg_steps)}
     out["stage"] = "done"
 
 
