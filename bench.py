@@ -55,8 +55,8 @@ def parse():
     ap.add_argument("--cg-frames", type=int, default=2000)
     ap.add_argument("--cg-epochs", type=int, default=10)
     ap.add_argument("--cg-batch", type=int, default=16)
-    ap.add_argument("--ibi-iters", type=int, default=8)
-    ap.add_argument("--cg-eq", type=int, default=1000)
+    ap.add_argument("--ibi-iters", type=int, default=20)
+    ap.add_argument("--cg-eq", type=int, default=2000)
     ap.add_argument("--cg-snap", type=int, default=20)
     ap.add_argument("--cg-warm", type=int, default=1000)
     ap.add_argument("--cg-steps", type=int, default=200)

@@ -19,12 +19,15 @@
 #include "pair_terms.cuh"
 #include "philox.cuh"
 
-// Build-time tunables of the step kernel (FP32): int4 neighbour groups read
-// per batch, and the minimum resident blocks per SM the register budget is
-// fitted to.
-#ifndef ESPP_STEP_GB32
-#define ESPP_STEP_GB32 1
-#endif
+// Launch shapes of the FP32 step kernel on the plain list path, chosen at run
+// time by the autotuner (espp_tune_step_shape): int4 neighbour groups read per
+// batch and the minimum resident blocks per SM the register budget is fitted
+// to.  Shape 0 is the default.
+struct StepShape {
+    int groups;  // list groups per batch
+    int minb;    // minimum resident blocks of TILE threads per SM
+};
+constexpr StepShape STEP_SHAPES[ESPP_STEP_SHAPES] = {{1, 10}, {2, 8}, {1, 12}, {1, 8}};
 #ifndef ESPP_STEP_MINB32
 #define ESPP_STEP_MINB32 10
 #endif
@@ -48,13 +51,13 @@ namespace espp {
 // inside the DPD cutoff, from the neighbours' velocity snapshot.
 // Entries with x code 3 cross a sheared face (Lees-Edwards): their x
 // difference is taken from the current offset in *le.
-template <class T, bool ENERGY, bool MULTI, bool FAST, bool DPD, bool LE>
+template <class T, bool ENERGY, bool MULTI, bool FAST, bool DPD, bool LE, int GB32 = 1>
 __device__ __forceinline__ void pair_loop(const DevSys<T>& s, const V4<T>* __restrict__ P, int i, int n,
                                           const V4<T>& xi, int ti, const PairRec<T>* pr1,
                                           T L0, T L1, T L2, T& fx, T& fy, T& fz, T& pe, T& vir, T& vxz,
                                           const LeCtx<T>* le, const DpdCtx<T>* dc = nullptr) {
     const T xim = xi.x - L0, yim = xi.y - L1, zim = xi.z - L2;
-    constexpr int GB = sizeof(T) == 4 ? ESPP_STEP_GB32 : 1;  // int4 groups per batch
+    constexpr int GB = sizeof(T) == 4 ? GB32 : 1;  // int4 groups per batch
     const int ng = (n + 3) >> 2;
     const int4* __restrict__ nb = reinterpret_cast<const int4*>(s.nbr) + i;
     const size_t stride = (size_t)s.stride;
@@ -187,9 +190,12 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-template <class T, int MODE, bool ENERGY, bool FAST, bool DPD, bool LE>
-__global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32_DPD : ESPP_STEP_MINB32) : 4) k_step(DevSys<T> s, int cur, double* __restrict__ f_out,
-                                               unsigned long long next_cond) {
+// SH: launch shape (STEP_SHAPES) of the plain FP32 list path.
+template <class T, int MODE, bool ENERGY, bool FAST, bool DPD, bool LE, int SH = 0>
+__global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32_DPD
+                                                              : (SH == 0 ? ESPP_STEP_MINB32 : STEP_SHAPES[SH].minb))
+                                                       : 4)
+    k_step(DevSys<T> s, int cur, double* __restrict__ f_out, unsigned long long next_cond) {
     Ctrl* c = s.ctrl;
     if (MODE != MODE_FORCES && c->abort) return;
     const long long step = c->step + (MODE >= MODE_STEP ? 1 : 0);
@@ -309,8 +315,8 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32
                     pr.eps4 = s.pair[0].eps4;
                     pr.shift = s.pair[0].shift;
                 }
-                pair_loop<T, ENERGY, false, true, DPD, LE>(s, P, i, n, xi, ti, &pr, L0, L1, L2, fx, fy, fz, pe, vir,
-                                                       vxz, &le, &dc);
+                pair_loop<T, ENERGY, false, true, DPD, LE, STEP_SHAPES[SH].groups>(s, P, i, n, xi, ti, &pr, L0, L1, L2,
+                                                                                   fx, fy, fz, pe, vir, vxz, &le, &dc);
             } else if (s.ntypes == 1) {
                 const PairRec<T> pr = s.pair[0];
                 if (pr.kind != 0 || DPD)
@@ -576,10 +582,22 @@ int Launch<T>::step(const DevSys<T>& s, int mode, bool energy, int cur, double* 
         k_vsnap<T><<<s.ntiles, TILE, 0, st>>>(s);
         extra += 1;
     }
-#define ESPP_STEP_LE(M, E, D, LE)                                                            \
-    do {                                                                                     \
-        if (s.lj_fast) k_step<T, M, E, true, D, LE><<<gr, TILE, 0, st>>>(s, cur, f_out, next_cond); \
-        else k_step<T, M, E, false, D, LE><<<gr, TILE, 0, st>>>(s, cur, f_out, next_cond);     \
+    // the plain FP32 list path of a step takes the tuned launch shape
+    const int sh = (sizeof(T) == 4 && s.lj_fast && !s.le_on && !s.cells_mode && !s.mlp_on &&
+                    (mode == MODE_STEP || mode == MODE_FINAL) && !dpd) ? s.step_shape : 0;
+#define ESPP_STEP_SH(M, E, D, LE)                                                                          \
+    do {                                                                                                   \
+        if constexpr (sizeof(T) == 4 && !(D) && !(LE) && ((M) == MODE_STEP || (M) == MODE_FINAL)) {        \
+            if (sh == 1) { k_step<T, M, E, true, D, LE, 1><<<gr, TILE, 0, st>>>(s, cur, f_out, next_cond); break; } \
+            if (sh == 2) { k_step<T, M, E, true, D, LE, 2><<<gr, TILE, 0, st>>>(s, cur, f_out, next_cond); break; } \
+            if (sh == 3) { k_step<T, M, E, true, D, LE, 3><<<gr, TILE, 0, st>>>(s, cur, f_out, next_cond); break; } \
+        }                                                                                                  \
+        k_step<T, M, E, true, D, LE><<<gr, TILE, 0, st>>>(s, cur, f_out, next_cond);                       \
+    } while (0)
+#define ESPP_STEP_LE(M, E, D, LE)                                                                \
+    do {                                                                                         \
+        if (s.lj_fast) ESPP_STEP_SH(M, E, D, LE);                                                \
+        else k_step<T, M, E, false, D, LE><<<gr, TILE, 0, st>>>(s, cur, f_out, next_cond);         \
     } while (0)
 #define ESPP_STEP(M, E, D)                            \
     do {                                              \
@@ -602,6 +620,7 @@ int Launch<T>::step(const DevSys<T>& s, int mode, bool energy, int cur, double* 
     }
 #undef ESPP_STEP
 #undef ESPP_STEP_LE
+#undef ESPP_STEP_SH
     return 1 + extra;
 }
 

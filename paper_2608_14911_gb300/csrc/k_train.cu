@@ -9,29 +9,16 @@
 // the list (each unordered pair once, in an order fixed by the list); those
 // beyond the cutoff get w = 0 and contribute exact zeros.
 //
-// A block of 4 warps works in rounds of 4 tiles of 16 pairs.  Each warp runs,
-// for its tile, the forward pass of the inference kernel (activations and
-// their r-tangents) and the reverse pass of the tangent output u' (rows
-// scaled by w):
-//   az2 = w w3 silu''(z2) dz2,  adz2 = w w3 silu'(z2)      (16 x 64)
-//   [ah1; adh1] = [az2; adz2] W2                           (tensor cores)
-//   az1 = ah1 silu'(z1) + adh1 silu''(z1) dz1,  adz1 = adh1 silu'(z1)
-// and stages phi, dphi, h1, dh1 and the reverse rows in shared memory.  Then
-// warp q accumulates rows 16q..16q+15 of
-//   dW2 += az2^T h1 + adz2^T dh1,  dW1 += az1^T phi + adz1^T dphi
-// over the round's 4 tiles in registers (tensor cores, K = 64 pairs), so the
-// weight gradients never go through shared memory until the end.  The bias
-// and output-weight sums collect per warp.  Each block writes one partial in
-// a fixed order and a separate kernel adds the partials in a fixed order:
-// the gradient is deterministic.  Adam then updates FP32 master weights and
+// The gradient runs on the tcgen05 tensor cores (k_mlp_grad below: tiles of
+// 128 pairs, accumulators in tensor memory).  Each CTA writes one partial in
+// a fixed order and two small kernels add the partials in a fixed order: the
+// gradient is deterministic.  Adam then updates FP32 master weights and
 // refreshes the BF16 copy the kernels read.
 #include "mlp_common.cuh"
+#include "tc_ptx.cuh"
 
 namespace espp {
 
-constexpr int TR_WARPS = 4;
-constexpr int PHI_LD = MLP_NB + 8;  // bf16 staging row strides
-constexpr int H_LD = MLP_H + 8;
 constexpr int G_W1 = 0;
 constexpr int G_B1 = MLP_H * MLP_NB;
 constexpr int G_W2 = G_B1 + MLP_H;
@@ -39,93 +26,144 @@ constexpr int G_B2 = G_W2 + MLP_H * MLP_H;
 constexpr int G_W3 = G_B2 + MLP_H;
 constexpr int NGRAD = G_W3 + MLP_H;  // every parameter but b3 (whose gradient is 0)
 
-struct __align__(16) TrainWarp {
-    __nv_bfloat16 phi[16 * PHI_LD], dphi[16 * PHI_LD];
-    __nv_bfloat16 h1[16 * H_LD], dh1[16 * H_LD];
-    __nv_bfloat16 az2[16 * H_LD], adz2[16 * H_LD];
-    __nv_bfloat16 az1[16 * H_LD], adz1[16 * H_LD];
-    float sums[3 * MLP_H];               // db1, db2, dw3 of this warp's tiles
+// ---- the gradient tile on the tcgen05 tensor cores -------------------------------
+// A CTA of 128 threads (one pair per thread and tensor-memory lane) walks
+// tiles of 128 pair records.  Per tile, with y = z / 2 and t = tanh(y) as in
+// the inference tile (halved weights, the first-layer bias carried by a
+// constant feature):
+//   L1    [y1 | dy1] = [phi | dphi] W1^T / 2                  D1, tensor memory
+//   epi1  h1 = y1 (1 + t1), dh1 = (1 + t1)(1 + y1 (1 - t1)) dy1   (BF16 rows)
+//   L2    [y2 | dy2] = [h1 | dh1] W2^T / 2                      D2
+//   epi2  with y2 += b2 / 2, dz2 = 2 dy2, s1 = silu'(z2), s2 = silu''(z2):
+//         az2 = w w3 s2 dz2, adz2 = w w3 s1, w dh2 = w s1 dz2  (w: the row weight)
+//   BW    [ah1 | adh1] = [az2 | adz2] W2                        D2 again
+//   G2    dW2 += az2^T h1 + adz2^T dh1, db2 += az2^T 1, dw3 += (w dh2)^T 1
+//   epi3  az1 = ah1 silu'(z1) + adh1 silu''(z1) dz1, adz1 = adh1 silu'(z1)
+//   G1    dW1 += az1^T phi + adz1^T dphi, db1 += az1^T 1
+// The G products contract over the tile's 128 pairs (K = pairs) and stay in
+// tensor memory for all of the CTA's tiles; their operands are the pair-major
+// quantities written column by column (thread p writes column p) in a K-major
+// layout whose core matrices along K sit 144 bytes apart, so a warp's 16-bit
+// column stores hit distinct banks.  Bias and output-weight sums ride along
+// as a constant-1 row of the B operands.  M is 128 throughout: dW2 is the top
+// half of one product (rows az2^T, w dh2^T against [h1 | 1]) plus the bottom
+// half of another (rows w dh2^T, adz2^T against dh1), dW1 likewise.  Each CTA
+// writes one partial in a fixed order: the gradient is deterministic.
+constexpr int GT_M = 128;
+constexpr int GT_K1 = 48;
+constexpr int GT_H = MLP_H;
+constexpr uint32_t GT_COLS = 512;
+constexpr uint32_t GT_D1 = 0, GT_D2 = 128, GT_G2A = 256, GT_G2B = 336, GT_G1A = 400, GT_G1B = 448;
+constexpr uint32_t TLBO = 144, TSBO = 16 * TLBO;  // transposed (K = pairs) layout
+constexpr int A2T_ROWS = 192;  // az2 (0..63), w dh2 (64..127), adz2 (128..191); A1T: az1, adz1
+constexpr int BHT_ROWS = 144;  // h1 (0..63), ones (64), zeros (65..79), dh1 (80..143)
+constexpr int BPT_ROWS = 80;   // phi (0..31), ones (32), zeros (33..47), dphi (48..79)
+constexpr int GT_WAIT = 1 << 22;
+
+__host__ __device__ constexpr uint32_t toff(int r, int k) {
+    return (uint32_t)((r >> 3) * TSBO + (k >> 3) * TLBO + (r & 7) * 16 + (k & 7) * 2);
+}
+
+struct __align__(1024) GradShared {
+    unsigned char a2t[A2T_ROWS / 8 * TSBO];  // A operand of G2; then of G1 (az1, adz1)
+    unsigned char bht[BHT_ROWS / 8 * TSBO];  // B operands of G2
+    unsigned char bpt[BPT_ROWS / 8 * TSBO];  // B operands of G1
+    unsigned char ra[2 * GT_M * GT_H * 2];   // row-major A operands: phi|dphi, then h1|dh1, then az2|adz2
+    unsigned char w1h[GT_H * GT_K1 * 2];     // W1 / 2 with the bias column
+    unsigned char w2h[GT_H * GT_H * 2];      // W2 / 2
+    unsigned char w2t[GT_H * GT_H * 2];      // W2^T
+    float b2h[GT_H];
+    float w3[GT_H];
+    uint64_t mbar;
+    uint32_t tmem;
+    int stop;
 };
 
-struct __align__(16) TrainShared {
-    __nv_bfloat16 w1s[MLP_H * W1_LD];
-    __nv_bfloat16 w2s[MLP_H * W2_LD];
-    __nv_bfloat16 w2t[MLP_H * W2_LD];
-    float b1s[MLP_H], b2s[MLP_H], w3s[MLP_H];
-    TrainWarp warp[TR_WARPS];
-};
 
-size_t train_smem_bytes() { return sizeof(TrainShared); }
-
-// four 8x8 BF16 matrices from shared memory, transposed (rows of each source
-// matrix given by lanes 8m..8m+7)
-__device__ __forceinline__ void ldsm_x4_t(const __nv_bfloat16* p, unsigned int r[4]) {
-    const unsigned int a = (unsigned int)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(a));
+__device__ __forceinline__ void st_bf(unsigned char* base, uint32_t off, float v) {
+    *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16(v);
 }
-
-// A fragment of M^T for a [16 rows = pairs][ld] staging matrix M: rows of the
-// fragment are columns u0.. of M, columns are the 16 pairs.  Source matrix m
-// of the load covers pairs 8 (m >> 1).. and columns u0 + 8 (m & 1)..
-__device__ __forceinline__ void at_frag(const __nv_bfloat16* M, int ld, int u0, int lane, unsigned int a[4]) {
-    const int m = lane >> 3, r = lane & 7;
-    ldsm_x4_t(M + ((m >> 1) * 8 + r) * ld + u0 + (m & 1) * 8, a);
+__device__ __forceinline__ float gt_tanh(float y) {
+    float t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(y));
+    return t;
 }
-
-// B fragments of a [16 pairs (k)][ld] staging matrix M for columns n0..n0+7
-// (b[0], b[1]) and n0+8..n0+15 (b[2], b[3]).  Source matrix m covers pairs
-// 8 (m & 1).. and columns n0 + 8 (m >> 1)..
-__device__ __forceinline__ void bk_frag2(const __nv_bfloat16* M, int ld, int n0, int lane, unsigned int b[4]) {
-    const int m = lane >> 3, r = lane & 7;
-    ldsm_x4_t(M + ((m & 1) * 8 + r) * ld + n0 + (m >> 1) * 8, b);
-}
-
-__device__ __forceinline__ void stage2(__nv_bfloat16* M, int ld, int row, int col, float lo, float hi) {
-    *reinterpret_cast<unsigned int*>(M + row * ld + col) = pack_bf16x2(lo, hi);
-}
-
-// sum over the 8 lanes of equal t (rows of a C fragment), result in lanes 0..3
-__device__ __forceinline__ float col_sum(float v) {
-    v += __shfl_xor_sync(0xffffffffu, v, 4);
-    v += __shfl_xor_sync(0xffffffffu, v, 8);
-    v += __shfl_xor_sync(0xffffffffu, v, 16);
-    return v;
+__device__ __forceinline__ void gt_row16(unsigned char* base, int row, int k, int K, uint4 v) {
+    *reinterpret_cast<uint4*>(base + tc::core_offset(row, k, K)) = v;
 }
 
 template <class T>
-__global__ void __launch_bounds__(32 * TR_WARPS, 2) k_mlp_grad(DevSys<T> s, int cur, const float4* __restrict__ err,
-                                                             float scale, float* __restrict__ partials) {
-    extern __shared__ __align__(16) unsigned char tsm_raw[];
-    TrainShared& sh = *reinterpret_cast<TrainShared*>(tsm_raw);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, tig = lane & 3;
-    TrainWarp& ws = sh.warp[warp];
-    load_mlp_weights(s.mlp, sh.w1s, sh.w2s, sh.w2t, sh.b1s, sh.b2s, sh.w3s);
-    for (int k = lane; k < 3 * MLP_H; k += 32) ws.sums[k] = 0.f;
+__global__ void __launch_bounds__(GT_M, 1) k_mlp_grad(DevSys<T> s, int cur, const float4* __restrict__ err,
+                                                    float scale, float* __restrict__ partials) {
+    extern __shared__ __align__(1024) unsigned char gsm_raw[];
+    GradShared& sh = *reinterpret_cast<GradShared*>(gsm_raw);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const MlpWeights* __restrict__ W = s.mlp;
+    for (int e = tid; e < GT_H * GT_K1; e += GT_M) {
+        const int n = e / GT_K1, k = e % GT_K1;
+        const float v = k < MLP_NB ? __bfloat162float(W->W1[n * MLP_NB + k]) : (k == MLP_NB ? W->b1[n] : 0.f);
+        st_bf(sh.w1h, tc::core_offset(n, k, GT_K1), 0.5f * v);
+    }
+    for (int e = tid; e < GT_H * GT_H; e += GT_M) {
+        const int n = e / GT_H, k = e % GT_H;
+        st_bf(sh.w2h, tc::core_offset(n, k, GT_H), 0.5f * __bfloat162float(W->W2[n * GT_H + k]));
+        st_bf(sh.w2t, tc::core_offset(n, k, GT_H), __bfloat162float(W->W2[k * GT_H + n]));  // (i, o) = W2[o][i]
+    }
+    for (int e = tid; e < GT_H; e += GT_M) {
+        sh.w3[e] = W->w3[e];
+        sh.b2h[e] = 0.5f * W->b2[e];
+    }
+    // the constant rows of this thread's column (pair slot tid)
+    st_bf(sh.bht, toff(64, tid), 1.f);
+    for (int r = 65; r < 80; ++r) st_bf(sh.bht, toff(r, tid), 0.f);
+    st_bf(sh.bpt, toff(32, tid), 1.f);
+    for (int r = 33; r < 48; ++r) st_bf(sh.bpt, toff(r, tid), 0.f);
+    if (tid == 0) {
+        tc::mbar_init(&sh.mbar, 1);
+        sh.stop = s.ctrl->abort;
+    }
+    if (warp == 0) tc::tmem_alloc(&sh.tmem, GT_COLS);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
     __syncthreads();
-    const float rc = s.mlp->rc, rc2 = rc * rc;
+    tc::fence_after_sync();
+    const uint32_t tmem = sh.tmem;
+    const uint32_t lanes = tmem + ((uint32_t)(warp * 32) << 16);
+    const float rc = W->rc, rc2 = rc * rc;
+    const float wid = rc / (MLP_NB - 1);
+    const float inv2w2 = 0.5f / (wid * wid), invw2 = 1.0f / (wid * wid);
+    const float pirc = 3.14159265358979f / rc;
     const V4<T>* __restrict__ P = s.pos[cur];
     const int stride = s.stride;
     const int nu = min(*s.mlp_nupper, s.mlp_upper_cap);
-    const int nrounds = (nu + 16 * TR_WARPS - 1) / (16 * TR_WARPS);
-    // this warp's rows of dW2 (16 x 64) and dW1 (16 x 32), as MMA accumulators
-    float acc2[8][4], acc1[4][4];
-#pragma unroll
-    for (int a = 0; a < 8; ++a)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) acc2[a][e] = 0.f;
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) acc1[a][e] = 0.f;
-
-    for (int round = blockIdx.x; round < nrounds; round += gridDim.x) {
-        // ---- the pairs of this warp's tile: distance and row weight --------------
-        const int p = lane & 15;
-        const int k = (round * TR_WARPS + warp) * 16 + p;
-        float rr = rc, wrow = 0.f;
+    const int ntl = (nu + GT_M - 1) / GT_M;
+    const uint32_t ra = tc::smem_addr(sh.ra), w1 = tc::smem_addr(sh.w1h), w2 = tc::smem_addr(sh.w2h),
+                   w2t = tc::smem_addr(sh.w2t), a2t = tc::smem_addr(sh.a2t), bht = tc::smem_addr(sh.bht),
+                   bpt = tc::smem_addr(sh.bpt);
+    const uint32_t id64 = tc::idesc_bf16(GT_M, 64), id80 = tc::idesc_bf16(GT_M, 80),
+                   id48 = tc::idesc_bf16(GT_M, 48), id32 = tc::idesc_bf16(GT_M, 32);
+    const bool fault = s.tc_fault != 0;
+    const int wait_limit = fault ? (1 << 12) : GT_WAIT;
+    uint32_t parity = 0;
+    bool ok = sh.stop == 0, acc = false;
+    // one commit of the MMAs issued by thread 0, waited for by the whole CTA
+    auto sync_mma = [&]() -> bool {
+        if (tid == 0) tc::commit(&sh.mbar);
+        const bool done = __syncthreads_and(tc::mbar_wait(&sh.mbar, parity, wait_limit));
+        parity ^= 1u;
+        tc::fence_after_sync();
+        return done;
+    };
+    auto sync_smem = [&]() {
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    };
+    for (int tile = blockIdx.x; ok && tile < ntl; tile += gridDim.x) {
+        // ---- this thread's pair: distance and row weight ------------------------
+        const int k = tile * GT_M + tid;
+        float r = rc, wrow = 0.f;
         if (k < nu) {
             const int4 up = s.mlp_upper[k];
             const int i = (up.x >> 2) % stride, j = nbr_slot(up.z);
@@ -138,209 +176,281 @@ __global__ void __launch_bounds__(32 * TR_WARPS, 2) k_mlp_grad(DevSys<T> s, int 
             const float dz = (float)shifted_diff(xi.z, (T)(xi.z - L2), xj.z, L2, code >> 4);
             const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
             if (r2 < rc2) {
-                rr = sqrtf(r2);
+                r = sqrtf(r2);
                 const float4 ei = err[i], ej = err[j];
-                wrow = scale * ((ei.x - ej.x) * dx + (ei.y - ej.y) * dy + (ei.z - ej.z) * dz) / rr;
+                wrow = scale * ((ei.x - ej.x) * dx + (ei.y - ej.y) * dy + (ei.z - ej.z) * dz) / r;
             }
         }
-        const float ra = __shfl_sync(0xffffffffu, rr, g), rb = __shfl_sync(0xffffffffu, rr, g + 8);
-        const float wa = __shfl_sync(0xffffffffu, wrow, g), wb = __shfl_sync(0xffffffffu, wrow, g + 8);
-        // ---- features, staged for dW1 ---------------------------------
-        unsigned int aph[2][4], adp[2][4];
-        rbf_fragments(ra, rb, rc, tig, aph, adp);
+        // ---- features: phi / dphi rows (layer-1 A) and columns (G1 B) ------------
+        {
+            const float fc = 0.5f * (__cosf(pirc * r) + 1.f);
+            const float dfc = -0.5f * pirc * __sinf(pirc * r);
+            unsigned char* fa = sh.ra;
+            unsigned char* fd = sh.ra + GT_M * GT_K1 * 2;
 #pragma unroll
-        for (int kt = 0; kt < 2; ++kt) {
-            const int col = kt * 16 + 2 * tig;
-            *reinterpret_cast<unsigned int*>(ws.phi + g * PHI_LD + col) = aph[kt][0];
-            *reinterpret_cast<unsigned int*>(ws.phi + (g + 8) * PHI_LD + col) = aph[kt][1];
-            *reinterpret_cast<unsigned int*>(ws.phi + g * PHI_LD + col + 8) = aph[kt][2];
-            *reinterpret_cast<unsigned int*>(ws.phi + (g + 8) * PHI_LD + col + 8) = aph[kt][3];
-            *reinterpret_cast<unsigned int*>(ws.dphi + g * PHI_LD + col) = adp[kt][0];
-            *reinterpret_cast<unsigned int*>(ws.dphi + (g + 8) * PHI_LD + col) = adp[kt][1];
-            *reinterpret_cast<unsigned int*>(ws.dphi + g * PHI_LD + col + 8) = adp[kt][2];
-            *reinterpret_cast<unsigned int*>(ws.dphi + (g + 8) * PHI_LD + col + 8) = adp[kt][3];
+            for (int g = 0; g < MLP_NB / 8; ++g) {
+                unsigned int ph[4], dp[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float v[2], dv[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int kk = 8 * g + 2 * q + h;
+                        const float d = r - wid * (float)kk;
+                        const float gk = __expf(-d * d * inv2w2);
+                        v[h] = gk * fc;
+                        dv[h] = gk * (dfc - d * invw2 * fc);
+                    }
+                    ph[q] = pack_bf16x2(v[0], v[1]);
+                    dp[q] = pack_bf16x2(dv[0], dv[1]);
+                    const __nv_bfloat162 pv = *reinterpret_cast<const __nv_bfloat162*>(&ph[q]);
+                    const __nv_bfloat162 dq = *reinterpret_cast<const __nv_bfloat162*>(&dp[q]);
+                    *reinterpret_cast<__nv_bfloat16*>(sh.bpt + toff(8 * g + 2 * q, tid)) = pv.x;
+                    *reinterpret_cast<__nv_bfloat16*>(sh.bpt + toff(8 * g + 2 * q + 1, tid)) = pv.y;
+                    *reinterpret_cast<__nv_bfloat16*>(sh.bpt + toff(48 + 8 * g + 2 * q, tid)) = dq.x;
+                    *reinterpret_cast<__nv_bfloat16*>(sh.bpt + toff(48 + 8 * g + 2 * q + 1, tid)) = dq.y;
+                }
+                gt_row16(fa, tid, 8 * g, GT_K1, make_uint4(ph[0], ph[1], ph[2], ph[3]));
+                gt_row16(fd, tid, 8 * g, GT_K1, make_uint4(dp[0], dp[1], dp[2], dp[3]));
+            }
+            gt_row16(fa, tid, 32, GT_K1, make_uint4(pack_bf16x2(1.f, 0.f), 0u, 0u, 0u));
+            gt_row16(fa, tid, 40, GT_K1, make_uint4(0u, 0u, 0u, 0u));
+            gt_row16(fd, tid, 32, GT_K1, make_uint4(0u, 0u, 0u, 0u));
+            gt_row16(fd, tid, 40, GT_K1, make_uint4(0u, 0u, 0u, 0u));
         }
-        // ---- layer 1 forward: h1, dh1 as layer-2 operands, staged ---
-        unsigned int ah[4][4], adh[4][4];
+        sync_smem();
+        if (tid == 0 && !fault) {
+            constexpr uint32_t sbo = (GT_K1 / 8) * 128;
 #pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            float z[4] = {0.f, 0.f, 0.f, 0.f}, dzv[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int kt = 0; kt < 2; ++kt) {
-                unsigned int b0, b1;
-                b_frag(sh.w1s, W1_LD, nt * 8, kt * 16, g, tig, b0, b1);
-                mma_bf16_16816(z, aph[kt], b0, b1);
-                mma_bf16_16816(dzv, adp[kt], b0, b1);
+            for (int ks = 0; ks < GT_K1 / 16; ++ks) {
+                const uint64_t db = tc::smem_desc(w1 + ks * 256, 128, sbo);
+                tc::mma(tmem + GT_D1, tc::smem_desc(ra + ks * 256, 128, sbo), db, id64, ks > 0);
+                tc::mma(tmem + GT_D1 + 64, tc::smem_desc(ra + GT_M * GT_K1 * 2 + ks * 256, 128, sbo), db, id64,
+                        ks > 0);
             }
-            const int col = nt * 8 + 2 * tig;
-            float hv[4], dhv[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float zz = z[e] + sh.b1s[col + (e & 1)];
-                const float sg = sigm(zz);
-                hv[e] = zz * sg;
-                dhv[e] = sg * (1.f + zz * (1.f - sg)) * dzv[e];
-            }
-            const int kt2 = nt >> 1, off = (nt & 1) * 2;
-            ah[kt2][off + 0] = pack_bf16x2(hv[0], hv[1]);
-            ah[kt2][off + 1] = pack_bf16x2(hv[2], hv[3]);
-            adh[kt2][off + 0] = pack_bf16x2(dhv[0], dhv[1]);
-            adh[kt2][off + 1] = pack_bf16x2(dhv[2], dhv[3]);
-            *reinterpret_cast<unsigned int*>(ws.h1 + g * H_LD + col) = ah[kt2][off + 0];
-            *reinterpret_cast<unsigned int*>(ws.h1 + (g + 8) * H_LD + col) = ah[kt2][off + 1];
-            *reinterpret_cast<unsigned int*>(ws.dh1 + g * H_LD + col) = adh[kt2][off + 0];
-            *reinterpret_cast<unsigned int*>(ws.dh1 + (g + 8) * H_LD + col) = adh[kt2][off + 1];
         }
-        // ---- layer 2 forward and the reverse seeds az2, adz2 ---------
-        unsigned int aaz[4][4], aadz[4][4];
+        if (!sync_mma()) {
+            ok = false;
+            break;
+        }
+        // ---- epilogue 1: h1, dh1 rows (layer-2 A) and columns (G2 B) -------------
+        {
+            unsigned char* ha = sh.ra;
+            unsigned char* hd = sh.ra + GT_M * GT_H * 2;
+#pragma unroll 1
+            for (int c = 0; c < GT_H; c += 16) {
+                float y[16], dy[16];
+                tc::tmem_ld16x2(lanes + GT_D1 + c, lanes + GT_D1 + 64 + c, y, dy);
+                unsigned int hw[8], dw[8];
 #pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            float z[4] = {0.f, 0.f, 0.f, 0.f}, dzv[4] = {0.f, 0.f, 0.f, 0.f};
+                for (int j = 0; j < 8; ++j) {
+                    float hv[2], dv[2];
 #pragma unroll
-            for (int kt = 0; kt < 4; ++kt) {
-                unsigned int b0, b1;
-                b_frag(sh.w2s, W2_LD, nt * 8, kt * 16, g, tig, b0, b1);
-                mma_bf16_16816(z, ah[kt], b0, b1);
-                mma_bf16_16816(dzv, adh[kt], b0, b1);
+                    for (int h = 0; h < 2; ++h) {
+                        const float yy = y[2 * j + h], t = gt_tanh(yy);
+                        hv[h] = yy * (1.f + t);
+                        dv[h] = (1.f + t) * (1.f + yy * (1.f - t)) * dy[2 * j + h];
+                    }
+                    hw[j] = pack_bf16x2(hv[0], hv[1]);
+                    dw[j] = pack_bf16x2(dv[0], dv[1]);
+                    const __nv_bfloat162 hb = *reinterpret_cast<const __nv_bfloat162*>(&hw[j]);
+                    const __nv_bfloat162 db = *reinterpret_cast<const __nv_bfloat162*>(&dw[j]);
+                    *reinterpret_cast<__nv_bfloat16*>(sh.bht + toff(c + 2 * j, tid)) = hb.x;
+                    *reinterpret_cast<__nv_bfloat16*>(sh.bht + toff(c + 2 * j + 1, tid)) = hb.y;
+                    *reinterpret_cast<__nv_bfloat16*>(sh.bht + toff(80 + c + 2 * j, tid)) = db.x;
+                    *reinterpret_cast<__nv_bfloat16*>(sh.bht + toff(80 + c + 2 * j + 1, tid)) = db.y;
+                }
+                gt_row16(ha, tid, c, GT_H, make_uint4(hw[0], hw[1], hw[2], hw[3]));
+                gt_row16(ha, tid, c + 8, GT_H, make_uint4(hw[4], hw[5], hw[6], hw[7]));
+                gt_row16(hd, tid, c, GT_H, make_uint4(dw[0], dw[1], dw[2], dw[3]));
+                gt_row16(hd, tid, c + 8, GT_H, make_uint4(dw[4], dw[5], dw[6], dw[7]));
             }
-            const int col = nt * 8 + 2 * tig;
-            float az[4], adz[4], gw3[2] = {0.f, 0.f}, gb2[2] = {0.f, 0.f};
+        }
+        sync_smem();
+        if (tid == 0 && !fault) {
+            constexpr uint32_t sbo = (GT_H / 8) * 128;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float zz = z[e] + sh.b2s[col + (e & 1)];
-                const float sg = sigm(zz);
-                const float s1 = sg * (1.f + zz * (1.f - sg));
-                const float s2 = sg * (1.f - sg) * (2.f + zz * (1.f - 2.f * sg));
-                const float w = e < 2 ? wa : wb;
-                const float w3v = sh.w3s[col + (e & 1)];
-                az[e] = w * w3v * s2 * dzv[e];
-                adz[e] = w * w3v * s1;
-                gw3[e & 1] += w * s1 * dzv[e];
-                gb2[e & 1] += az[e];
+            for (int ks = 0; ks < GT_H / 16; ++ks) {
+                const uint64_t db = tc::smem_desc(w2 + ks * 256, 128, sbo);
+                tc::mma(tmem + GT_D2, tc::smem_desc(ra + ks * 256, 128, sbo), db, id64, ks > 0);
+                tc::mma(tmem + GT_D2 + 64, tc::smem_desc(ra + GT_M * GT_H * 2 + ks * 256, 128, sbo), db, id64,
+                        ks > 0);
             }
-            const int kt2 = nt >> 1, off = (nt & 1) * 2;
-            aaz[kt2][off + 0] = pack_bf16x2(az[0], az[1]);
-            aaz[kt2][off + 1] = pack_bf16x2(az[2], az[3]);
-            aadz[kt2][off + 0] = pack_bf16x2(adz[0], adz[1]);
-            aadz[kt2][off + 1] = pack_bf16x2(adz[2], adz[3]);
-            *reinterpret_cast<unsigned int*>(ws.az2 + g * H_LD + col) = aaz[kt2][off + 0];
-            *reinterpret_cast<unsigned int*>(ws.az2 + (g + 8) * H_LD + col) = aaz[kt2][off + 1];
-            *reinterpret_cast<unsigned int*>(ws.adz2 + g * H_LD + col) = aadz[kt2][off + 0];
-            *reinterpret_cast<unsigned int*>(ws.adz2 + (g + 8) * H_LD + col) = aadz[kt2][off + 1];
+        }
+        if (!sync_mma()) {
+            ok = false;
+            break;
+        }
+        // ---- epilogue 2: reverse seeds, rows (BW A) and columns (G2 A) -----------
+        {
+            unsigned char* za = sh.ra;
+            unsigned char* zd = sh.ra + GT_M * GT_H * 2;
+#pragma unroll 1
+            for (int c = 0; c < GT_H; c += 16) {
+                float y[16], dy[16];
+                tc::tmem_ld16x2(lanes + GT_D2 + c, lanes + GT_D2 + 64 + c, y, dy);
+                unsigned int aw[8], dw[8];
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const float a3 = col_sum(gw3[q]), a2 = col_sum(gb2[q]);
-                if (g == 0) {
-                    ws.sums[2 * MLP_H + col + q] += a3;
-                    ws.sums[MLP_H + col + q] += a2;
+                for (int j = 0; j < 8; ++j) {
+                    float av[2], adv[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int o = c + 2 * j + h;
+                        const float yy = y[2 * j + h] + sh.b2h[o], t = gt_tanh(yy);
+                        const float s1 = 0.5f * (1.f + t) * (1.f + yy * (1.f - t));
+                        const float s2 = 0.5f * (1.f - t * t) * (1.f - yy * t);
+                        const float dz = 2.f * dy[2 * j + h];
+                        const float ww = wrow * sh.w3[o];
+                        av[h] = ww * s2 * dz;
+                        adv[h] = ww * s1;
+                        st_bf(sh.a2t, toff(64 + o, tid), wrow * s1 * dz);
+                    }
+                    aw[j] = pack_bf16x2(av[0], av[1]);
+                    dw[j] = pack_bf16x2(adv[0], adv[1]);
+                    const __nv_bfloat162 ab = *reinterpret_cast<const __nv_bfloat162*>(&aw[j]);
+                    const __nv_bfloat162 db = *reinterpret_cast<const __nv_bfloat162*>(&dw[j]);
+                    *reinterpret_cast<__nv_bfloat16*>(sh.a2t + toff(c + 2 * j, tid)) = ab.x;
+                    *reinterpret_cast<__nv_bfloat16*>(sh.a2t + toff(c + 2 * j + 1, tid)) = ab.y;
+                    *reinterpret_cast<__nv_bfloat16*>(sh.a2t + toff(128 + c + 2 * j, tid)) = db.x;
+                    *reinterpret_cast<__nv_bfloat16*>(sh.a2t + toff(128 + c + 2 * j + 1, tid)) = db.y;
+                }
+                gt_row16(za, tid, c, GT_H, make_uint4(aw[0], aw[1], aw[2], aw[3]));
+                gt_row16(za, tid, c + 8, GT_H, make_uint4(aw[4], aw[5], aw[6], aw[7]));
+                gt_row16(zd, tid, c, GT_H, make_uint4(dw[0], dw[1], dw[2], dw[3]));
+                gt_row16(zd, tid, c + 8, GT_H, make_uint4(dw[4], dw[5], dw[6], dw[7]));
+            }
+        }
+        sync_smem();
+        if (tid == 0 && !fault) {
+            constexpr uint32_t sbo = (GT_H / 8) * 128;
+#pragma unroll
+            for (int ks = 0; ks < GT_H / 16; ++ks) {
+                const uint64_t db = tc::smem_desc(w2t + ks * 256, 128, sbo);
+                tc::mma(tmem + GT_D2, tc::smem_desc(ra + ks * 256, 128, sbo), db, id64, ks > 0);
+                tc::mma(tmem + GT_D2 + 64, tc::smem_desc(ra + GT_M * GT_H * 2 + ks * 256, 128, sbo), db, id64,
+                        ks > 0);
+            }
+#pragma unroll
+            for (int ks = 0; ks < GT_M / 16; ++ks) {
+                const uint32_t kb = ks * 2 * TLBO;
+                tc::mma(tmem + GT_G2A, tc::smem_desc(a2t + kb, TLBO, TSBO), tc::smem_desc(bht + kb, TLBO, TSBO), id80,
+                        acc || ks > 0);
+                tc::mma(tmem + GT_G2B, tc::smem_desc(a2t + 8 * TSBO + kb, TLBO, TSBO),
+                        tc::smem_desc(bht + 10 * TSBO + kb, TLBO, TSBO), id64, acc || ks > 0);
+            }
+        }
+        if (!sync_mma()) {
+            ok = false;
+            break;
+        }
+        // ---- epilogue 3: layer-1 adjoints, columns (G1 A, over G2's A) -----------
+#pragma unroll 1
+        for (int c = 0; c < GT_H; c += 16) {
+            float ah[16], adh[16], y[16], dy[16];
+            tc::tmem_ld16x2(lanes + GT_D2 + c, lanes + GT_D2 + 64 + c, ah, adh);
+            tc::tmem_ld16x2(lanes + GT_D1 + c, lanes + GT_D1 + 64 + c, y, dy);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float yy = y[j], t = gt_tanh(yy);
+                const float s1 = 0.5f * (1.f + t) * (1.f + yy * (1.f - t));
+                const float s2 = 0.5f * (1.f - t * t) * (1.f - yy * t);
+                st_bf(sh.a2t, toff(c + j, tid), ah[j] * s1 + adh[j] * s2 * (2.f * dy[j]));
+                st_bf(sh.a2t, toff(64 + c + j, tid), adh[j] * s1);
+            }
+        }
+        sync_smem();
+        if (tid == 0 && !fault) {
+#pragma unroll
+            for (int ks = 0; ks < GT_M / 16; ++ks) {
+                const uint32_t kb = ks * 2 * TLBO;
+                const uint64_t da = tc::smem_desc(a2t + kb, TLBO, TSBO);
+                tc::mma(tmem + GT_G1A, da, tc::smem_desc(bpt + kb, TLBO, TSBO), id48, acc || ks > 0);
+                tc::mma(tmem + GT_G1B, da, tc::smem_desc(bpt + 6 * TSBO + kb, TLBO, TSBO), id32, acc || ks > 0);
+            }
+        }
+        // the next tile rewrites the operands of these products
+        if (!sync_mma()) {
+            ok = false;
+            break;
+        }
+        acc = true;
+    }
+    if (!ok && sh.stop == 0) {
+        // a commit never arrived: record it, give the MMAs in flight one more
+        // bounded wait, then release the tensor memory
+        if (tid == 0) {
+            atomicOr(&s.ctrl->err, ERRBIT_TIMEOUT);
+            s.ctrl->abort = 1;
+        }
+        tc::mbar_wait(&sh.mbar, parity, wait_limit);
+    }
+    // ---- this CTA's partial: rows 64..127 of the products hold the second
+    //      halves (through shared memory), rows 0..63 the first ---------------
+    float* out = partials + (size_t)blockIdx.x * NGRAD;
+    float* part2 = reinterpret_cast<float*>(sh.ra);  // dW2 part 2 [64][64], dW1 part 2 [64][32], dw3 [64]
+    if (ok && acc && tid >= 64) {
+        const int o = tid - 64;
+#pragma unroll 1
+        for (int c = 0; c < 64; c += 32) {
+            float a[16], b[16];
+            tc::tmem_ld16x2(lanes + GT_G2B + c, lanes + GT_G2B + c + 16, a, b);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                part2[o * 64 + c + j] = a[j];
+                part2[o * 64 + c + 16 + j] = b[j];
+            }
+        }
+        {
+            float a[16], b[16];
+            tc::tmem_ld16x2(lanes + GT_G1B, lanes + GT_G1B + 16, a, b);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                part2[4096 + o * 32 + j] = a[j];
+                part2[4096 + o * 32 + 16 + j] = b[j];
+            }
+            tc::tmem_ld16x2(lanes + GT_G2A + 64, lanes + GT_G1A + 32, a, b);
+            part2[6144 + o] = a[0];
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (tid < 64) {
+        const int o = tid;
+        if (ok && acc) {
+#pragma unroll 1
+            for (int c = 0; c < 64; c += 32) {
+                float a[16], b[16];
+                tc::tmem_ld16x2(lanes + GT_G2A + c, lanes + GT_G2A + c + 16, a, b);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    out[G_W2 + o * 64 + c + j] = a[j] + part2[o * 64 + c + j];
+                    out[G_W2 + o * 64 + c + 16 + j] = b[j] + part2[o * 64 + c + 16 + j];
                 }
             }
+            float a[16], b[16];
+            tc::tmem_ld16x2(lanes + GT_G1A, lanes + GT_G1A + 16, a, b);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                out[G_W1 + o * 32 + j] = a[j] + part2[4096 + o * 32 + j];
+                out[G_W1 + o * 32 + 16 + j] = b[j] + part2[4096 + o * 32 + 16 + j];
+            }
+            tc::tmem_ld16x2(lanes + GT_G2A + 64, lanes + GT_G1A + 32, a, b);
+            out[G_B2 + o] = a[0];
+            out[G_B1 + o] = b[0];
+            out[G_W3 + o] = part2[6144 + o];
+        } else {
+            // no tile (or a failed wait): a zero partial
+            for (int c = 0; c < 64; ++c) out[G_W2 + o * 64 + c] = 0.f;
+            for (int c = 0; c < 32; ++c) out[G_W1 + o * 32 + c] = 0.f;
+            out[G_B2 + o] = 0.f;
+            out[G_B1 + o] = 0.f;
+            out[G_W3 + o] = 0.f;
         }
-        // ---- back through W2 and layer 1: az1, adz1, staged ----------
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            float a1[4] = {0.f, 0.f, 0.f, 0.f}, ad1[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int kt = 0; kt < 4; ++kt) {
-                unsigned int b0, b1;
-                b_frag(sh.w2t, W2_LD, nt * 8, kt * 16, g, tig, b0, b1);
-                mma_bf16_16816(a1, aaz[kt], b0, b1);
-                mma_bf16_16816(ad1, aadz[kt], b0, b1);
-            }
-            float z[4] = {0.f, 0.f, 0.f, 0.f}, dzv[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int kt = 0; kt < 2; ++kt) {
-                unsigned int b0, b1;
-                b_frag(sh.w1s, W1_LD, nt * 8, kt * 16, g, tig, b0, b1);
-                mma_bf16_16816(z, aph[kt], b0, b1);
-                mma_bf16_16816(dzv, adp[kt], b0, b1);
-            }
-            const int col = nt * 8 + 2 * tig;
-            float az[4], adz[4], gb1[2] = {0.f, 0.f};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float zz = z[e] + sh.b1s[col + (e & 1)];
-                const float sg = sigm(zz);
-                const float s1 = sg * (1.f + zz * (1.f - sg));
-                const float s2 = sg * (1.f - sg) * (2.f + zz * (1.f - 2.f * sg));
-                az[e] = a1[e] * s1 + ad1[e] * s2 * dzv[e];
-                adz[e] = ad1[e] * s1;
-                gb1[e & 1] += az[e];
-            }
-            stage2(ws.az1, H_LD, g, col, az[0], az[1]);
-            stage2(ws.az1, H_LD, g + 8, col, az[2], az[3]);
-            stage2(ws.adz1, H_LD, g, col, adz[0], adz[1]);
-            stage2(ws.adz1, H_LD, g + 8, col, adz[2], adz[3]);
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const float a = col_sum(gb1[q]);
-                if (g == 0) ws.sums[col + q] += a;
-            }
-        }
-        __syncthreads();
-        // ---- weight gradients: this warp's rows, K = the round's 4 x 16 pairs ----
-        for (int src = 0; src < TR_WARPS; ++src) {
-            const TrainWarp& ts = sh.warp[src];
-            unsigned int A[4], AD[4];
-            at_frag(ts.az2, H_LD, warp * 16, lane, A);
-            at_frag(ts.adz2, H_LD, warp * 16, lane, AD);
-#pragma unroll
-            for (int nt = 0; nt < 8; nt += 2) {
-                unsigned int b[4], d[4];
-                bk_frag2(ts.h1, H_LD, nt * 8, lane, b);
-                bk_frag2(ts.dh1, H_LD, nt * 8, lane, d);
-                mma_bf16_16816(acc2[nt], A, b[0], b[1]);
-                mma_bf16_16816(acc2[nt], AD, d[0], d[1]);
-                mma_bf16_16816(acc2[nt + 1], A, b[2], b[3]);
-                mma_bf16_16816(acc2[nt + 1], AD, d[2], d[3]);
-            }
-            at_frag(ts.az1, H_LD, warp * 16, lane, A);
-            at_frag(ts.adz1, H_LD, warp * 16, lane, AD);
-#pragma unroll
-            for (int nt = 0; nt < 4; nt += 2) {
-                unsigned int b[4], d[4];
-                bk_frag2(ts.phi, PHI_LD, nt * 8, lane, b);
-                bk_frag2(ts.dphi, PHI_LD, nt * 8, lane, d);
-                mma_bf16_16816(acc1[nt], A, b[0], b[1]);
-                mma_bf16_16816(acc1[nt], AD, d[0], d[1]);
-                mma_bf16_16816(acc1[nt + 1], A, b[2], b[3]);
-                mma_bf16_16816(acc1[nt + 1], AD, d[2], d[3]);
-            }
-        }
-        __syncthreads();
     }
-    // ---- this block's partial: register rows, then the warps' sums in order -----
-    float* out = partials + (size_t)blockIdx.x * NGRAD;
-    const int row = warp * 16 + g;
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        float* dst = out + G_W2 + row * MLP_H + nt * 8 + 2 * tig;
-        dst[0] = acc2[nt][0];
-        dst[1] = acc2[nt][1];
-        dst[8 * MLP_H] = acc2[nt][2];
-        dst[8 * MLP_H + 1] = acc2[nt][3];
-    }
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-        float* dst = out + G_W1 + row * MLP_NB + nt * 8 + 2 * tig;
-        dst[0] = acc1[nt][0];
-        dst[1] = acc1[nt][1];
-        dst[8 * MLP_NB] = acc1[nt][2];
-        dst[8 * MLP_NB + 1] = acc1[nt][3];
-    }
+    tc::fence_before_sync();
     __syncthreads();
-    for (int k = threadIdx.x; k < MLP_H; k += blockDim.x) {
-        float b1v = 0.f, b2v = 0.f, w3v = 0.f;
-#pragma unroll
-        for (int w = 0; w < TR_WARPS; ++w) {
-            b1v += sh.warp[w].sums[k];
-            b2v += sh.warp[w].sums[MLP_H + k];
-            w3v += sh.warp[w].sums[2 * MLP_H + k];
-        }
-        out[G_B1 + k] = b1v;
-        out[G_B2 + k] = b2v;
-        out[G_W3 + k] = w3v;
-    }
+    if (warp == 0) tc::tmem_free(tmem, GT_COLS);
 }
 
 // e_i = F_pair,i + F_bond,i - Y_id(i); per-block sums of |e|^2 in double.
@@ -464,7 +574,7 @@ int Launch<T>::train_grad(const DevSys<T>& s, int cur, const double* Y, float4* 
                           float scale, float* partials, int grad_blocks, float* grad, double* loss,
                           cudaStream_t st) {
     k_train_err<T><<<s.ntiles, TILE, 0, st>>>(s, cur, Y, err, loss_part);
-    k_mlp_grad<T><<<grad_blocks, 32 * TR_WARPS, sizeof(TrainShared), st>>>(s, cur, err, scale, partials);
+    k_mlp_grad<T><<<grad_blocks, GT_M, sizeof(GradShared), st>>>(s, cur, err, scale, partials);
     // the chunk sums sit after the blocks' partials
     float* chunk = partials + (size_t)grad_blocks * NGRAD;
     k_grad_chunks<<<dim3((NGRAD + 255) / 256, GRED_CHUNKS), 256, 0, st>>>(partials, grad_blocks, chunk);
@@ -475,7 +585,7 @@ int Launch<T>::train_grad(const DevSys<T>& s, int cur, const double* Y, float4* 
 template <class T>
 cudaError_t Launch<T>::prepare_train() {
     return cudaFuncSetAttribute(k_mlp_grad<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sizeof(TrainShared));
+                                (int)sizeof(GradShared));
 }
 
 void launch_adam(float* theta, float* m, float* v, float* grad, float lr, float b1, float b2, float eps,

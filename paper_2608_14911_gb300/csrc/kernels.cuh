@@ -104,6 +104,7 @@ template <class T> struct DevSys {
     const T* tab;       // concatenated tables (tabulated pair and bond kinds)
     int ntypes;
     int lj_fast;        // one particle type with a plain Lennard-Jones pair potential
+    int step_shape;     // launch shape of the FP32 step kernel on the plain list path (autotuned)
     int mlp_on;         // pair forces come from the learned MLP (k_mlp) instead
     int excl_bonded;    // 1-2 bonded pairs are left out of the Verlet list
     const MlpWeights* mlp;

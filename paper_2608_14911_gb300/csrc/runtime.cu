@@ -73,6 +73,8 @@ struct SystemBase {
     virtual int get_lees_edwards(int* on, double* shear, double* time) = 0;
     virtual int set_force_method(int method) = 0;
     virtual int tune_force_method(int nsteps, double dt, double gamma, double kT, double* ms, int* chosen) = 0;
+    virtual int set_step_shape(int shape) = 0;
+    virtual int tune_step_shape(int nsteps, double dt, double gamma, double kT, double* ms, int* chosen) = 0;
 };
 
 struct PairHost {
@@ -821,7 +823,7 @@ class System : public SystemBase {
         const int ngrad = mlp_ngrad();
         const int nep = std::max(epochs, 1);
         if (!t_err) {
-            t_blocks = 2 * sm_count();  // two blocks of the gradient kernel per SM
+            t_blocks = sm_count();  // one gradient CTA per SM (tensor memory: 480 of 512 columns)
             int rc0;
             if ((rc0 = alloc(&t_err, (size_t)N, allocs)) || (rc0 = alloc(&t_loss_part, (size_t)d.ntiles, allocs)) ||
                 (rc0 = alloc(&t_partials, (size_t)(t_blocks + 16) * ngrad, allocs)) || (rc0 = alloc(&t_grad, ngrad, allocs)) ||
@@ -1889,6 +1891,83 @@ class System : public SystemBase {
         return ESPP_OK;
     }
 
+    // ---- launch shape of the step kernel and the resort interval ----------
+    int set_step_shape(int shape) override {
+        if (shape < 0 || shape >= ESPP_STEP_SHAPES) return fail(ESPP_ERR_ARG, "unknown step shape");
+        d.step_shape = shape;
+        clear_graphs();  // a kernel argument of the captured graphs
+        return ESPP_OK;
+    }
+
+    // Times the step-kernel shapes, then the resort intervals, from the
+    // current state (restored after each trial and at the end), keeping the
+    // fastest of each.
+    int tune_step_shape(int nsteps, double dt, double gamma, double kT, double* ms, int* chosen) override {
+        if (nsteps < 1) return fail(ESPP_ERR_ARG, "nsteps must be positive");
+        if (!state_set || !cells_ready) return fail(ESPP_ERR_STATE, "set the state and build the cells first");
+        const size_t n3 = 3 * (size_t)N;
+        std::vector<double> x(n3), v(n3);
+        std::vector<int32_t> img(n3);
+        int rcode = get_state(x.data(), v.data(), img.data(), ESPP_HOST);
+        if (rcode) return rcode;
+        const int64_t step0 = read_ctrl().step;
+        const double t0 = time_at(step0), dt0 = le_clk_h.dt;
+        auto restore = [&]() -> int {
+            int rc = set_state(x.data(), v.data(), img.data(), ESPP_HOST);
+            if (rc) return rc;
+            if ((rc = set_step(step0))) return rc;
+            return set_clock(t0, dt0, step0);
+        };
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        auto timed = [&](int steps, double* out) -> int {
+            int rc;
+            if ((rc = restore()) || (rc = integrate(2, dt, gamma, kT))) return rc;
+            CK(cudaEventRecord(e0, st));
+            if ((rc = integrate(steps, dt, gamma, kT))) return rc;
+            CK(cudaEventRecord(e1, st));
+            CK(cudaEventSynchronize(e1));
+            float el = 0;
+            CK(cudaEventElapsedTime(&el, e0, e1));
+            *out = el / steps;
+            return ESPP_OK;
+        };
+        const int resort_of[3] = {250, 500, 1000};
+        double t[ESPP_STEP_SHAPES + 3];
+        for (double& q : t) q = INFINITY;
+        int best = 0, best_r = 1;
+        for (int k = 0; k < ESPP_STEP_SHAPES && !rcode; ++k)
+            if (!(rcode = set_step_shape(k))) rcode = timed(nsteps, &t[k]);
+        if (!rcode) {
+            for (int k = 1; k < ESPP_STEP_SHAPES; ++k)
+                if (t[k] < t[best]) best = k;
+            rcode = set_step_shape(best);
+        }
+        const int64_t resort0 = resort_every;
+        for (int k = 0; k < 3 && !rcode; ++k) {
+            resort_every = resort_of[k];
+            rcode = timed(std::max(nsteps, 1000), &t[ESPP_STEP_SHAPES + k]);
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rcode) {
+            resort_every = resort0;
+            return rcode;
+        }
+        for (int k = 1; k < 3; ++k)
+            if (t[ESPP_STEP_SHAPES + k] < t[ESPP_STEP_SHAPES + best_r]) best_r = k;
+        resort_every = resort_of[best_r];
+        if ((rcode = restore())) return rcode;
+        if (ms)
+            for (int k = 0; k < ESPP_STEP_SHAPES + 3; ++k) ms[k] = t[k];
+        if (chosen) {
+            chosen[0] = best;
+            chosen[1] = resort_of[best_r];
+        }
+        return ESPP_OK;
+    }
+
     int set_cell_subdivision(int w) override {
         if (w < 0 || w > 2) return fail(ESPP_ERR_ARG, "cell subdivision must be 0, 1 or 2");
         cell_sub_req = w;
@@ -2085,6 +2164,21 @@ int espp_tune_force_method(espp_h h, int32_t nsteps, double dt, double gamma, do
         int c = 0;
         const int rc = s.tune_force_method(nsteps, dt, gamma, kT, ms_per_step, &c);
         if (chosen) *chosen = c;
+        return rc;
+    });
+}
+int espp_set_step_shape(espp_h h, int32_t shape) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.set_step_shape(shape); });
+}
+int espp_tune_step_shape(espp_h h, int32_t nsteps, double dt, double gamma, double kT, double* ms,
+                         int32_t* chosen) {
+    return guarded(h, [&](espp::SystemBase& s) {
+        int c[2] = {0, 0};
+        const int rc = s.tune_step_shape(nsteps, dt, gamma, kT, ms, c);
+        if (rc == ESPP_OK && chosen) {
+            chosen[0] = c[0];
+            chosen[1] = c[1];
+        }
         return rc;
     });
 }

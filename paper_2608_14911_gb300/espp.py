@@ -43,6 +43,7 @@ ESPP_THERMO_LANGEVIN = 0
 ESPP_THERMO_DPD = 1
 ESPP_FORCES_VERLET = 0
 ESPP_FORCES_CELLS = 1
+STEP_SHAPES = 4
 
 ERROR_NAMES = {
     ESPP_ERR_ARG: "ESPP_ERR_ARG", ESPP_ERR_CUDA: "ESPP_ERR_CUDA",
@@ -66,7 +67,7 @@ EXPORTS = (
     "espp_set_exclude_bonded", "espp_mlp_get_weights", "espp_mlp_train", "espp_mlp_loss_grad",
     "espp_cg_map", "espp_set_cell_subdivision", "espp_set_thermostat",
     "espp_set_lees_edwards", "espp_get_lees_edwards", "espp_set_force_method",
-    "espp_tune_force_method",
+    "espp_tune_force_method", "espp_set_step_shape", "espp_tune_step_shape",
 )
 NOALLOC_MAX_BINS = 4096
 NOALLOC_MAX_N = 200000
@@ -152,6 +153,9 @@ def lib(path: str = LIB_PATH):
         "espp_set_force_method": ([vp, ctypes.c_int32], ctypes.c_int),
         "espp_tune_force_method": ([vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp,
                                     ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "espp_set_step_shape": ([vp, ctypes.c_int32], ctypes.c_int),
+        "espp_tune_step_shape": ([vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp,
+                                  ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "espp_mlp_set_weights": ([vp, vp, i64], ctypes.c_int),
         "espp_set_exclude_bonded": ([vp, ctypes.c_int], ctypes.c_int),
         "espp_mlp_get_weights": ([vp, vp, i64], ctypes.c_int),
@@ -469,6 +473,19 @@ class System:
         self._c(lib().espp_tune_force_method(self._h, int(nsteps), float(dt), float(gamma), float(kT), ms,
                                              ctypes.byref(ch)))
         return [ms[0], ms[1], ms[2]], int(ch.value)
+
+    def set_step_shape(self, shape):
+        self._c(lib().espp_set_step_shape(self._h, int(shape)))
+
+    def tune_step_shape(self, nsteps, dt, gamma, kT):
+        """Time the step kernel's launch shapes, then the resort intervals
+        (250, 500, 1000 steps), from the current state and keep the fastest;
+        returns (ms per step of each shape, ms per step of each interval,
+        (shape kept, interval kept))."""
+        ms = (ctypes.c_double * (STEP_SHAPES + 3))()
+        ch = (ctypes.c_int32 * 2)()
+        self._c(lib().espp_tune_step_shape(self._h, int(nsteps), float(dt), float(gamma), float(kT), ms, ch))
+        return list(ms)[:STEP_SHAPES], list(ms)[STEP_SHAPES:], (int(ch[0]), int(ch[1]))
 
     def set_graph_chunk(self, steps):
         self._c(lib().espp_set_graph_chunk(self._h, int(steps)))
