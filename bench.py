@@ -371,6 +371,9 @@ def run_ours(a):
 
     seed = rank_seed(rank)
     s, cfg, start = make_melt(a, seed, espp.ESPP_FP32)
+    # the autotuner picks the step kernel's launch shape and the resort
+    # interval for this melt (untimed; the state is restored afterwards)
+    shape_ms, resort_ms, (shape, resort) = s.tune_step_shape(200, 0.005, 1.0, 1.0)
     if a.direct:
         s.set_graph_chunk(0)
     n = cfg.n
@@ -463,7 +466,8 @@ def run_ours(a):
     suite = None
     if not a.no_suite and world == 1:
         suite = {}
-        for name, fn in (("kg1m_dpd", lambda o: o.update(suite_dpd(a, barrier, s, cfg, seed, ms / a.steps))),
+        for name, fn in (("cfg0_fp64", lambda o: o.update(suite_cfg0(a, barrier))),
+                         ("kg1m_dpd", lambda o: o.update(suite_dpd(a, barrier, s, cfg, seed, ms / a.steps))),
                          ("dpd_fluid_786k", lambda o: o.update(suite_dpd_fluid(a, barrier))),
                          ("lj4m", lambda o: o.update(suite_lj4m(a, barrier, peaks))),
                          ("batched512", lambda o: o.update(suite_batched(a, barrier))),
@@ -491,6 +495,9 @@ def run_ours(a):
                    "l2": "inputs larger than L2: per-step working set %.0f MB > %.0f MB L2, no flush"
                          % (ws_mb, L2_MB),
                    "rebuilds_in_timed_region": rebuilds,
+                   "step_shape": {"chosen": shape, "groups_per_batch": (1, 2, 1, 1)[shape],
+                                  "min_blocks_per_sm": (10, 8, 12, 8)[shape], "resort_interval": resort,
+                                  "tuner_ms_per_step": {"shapes": shape_ms, "resort_250_500_1000": resort_ms}},
                    "mean_list_entries_per_particle": mean_entries / n, "max_list_entries": max_count,
                    "observables_after_run": {k: obs[k] for k in ("temperature", "mean_bond", "rg2", "pe_pair")},
                    "force_error_gate": "FP32 <= 1e-5 relative RMS vs the FP64 oracle (tests/test_gpu_parity.py)"},
@@ -532,6 +539,23 @@ def _step_kernel_ms(s, dt, gamma, kT, steps=256):
     kt = s.kernel_timing(reset=True)
     s.set_kernel_timing(False)
     return kt["step_ms"] / max(1, kt["step_launches"]), kt["rebuild_ms"] / max(1, kt["steps"])
+
+
+def suite_cfg0(a, sync):
+    """The FP64 sanity workload: a Kremer-Grest melt of 20 chains x 50 beads
+    at density 0.85 (random walks, capped push-off, seed 42), 1000 timed
+    Langevin steps in FP64 (its parity with the oracle is checked by the
+    tests, not here)."""
+    from paper_2608_14911_gb300 import espp
+    s, cfg, start = make_melt(a, 42, espp.ESPP_FP64, nchains=20, nbeads=50)
+    steps = 1000
+    ms = _timed(s, steps, 0.005, 1.0, 1.0, sync)
+    o = s.observables()
+    s.close()
+    return {"workload": "kg_melt_20x50_rho0.85_fp64", "n_particles": cfg.n, "start": start, "steps": steps,
+            "value": cfg.n * steps / (ms / 1e3), "unit": "particle-steps/s", "ms_per_step": ms / steps,
+            "dtype": "f64", "temperature": o["temperature"], "mean_bond": o["mean_bond"],
+            "note": "launch-bound at 1000 beads; FP64 parity with the oracle: tests/test_gpu_parity.py"}
 
 
 def suite_dpd(a, sync, src, cfg, seed, langevin_ms):

@@ -27,10 +27,9 @@ constexpr int G_W3 = G_B2 + MLP_H;
 constexpr int NGRAD = G_W3 + MLP_H;  // every parameter but b3 (whose gradient is 0)
 
 // ---- the gradient tile on the tcgen05 tensor cores -------------------------------
-// A CTA of 128 threads (one pair per thread and tensor-memory lane) walks
-// tiles of 128 pair records.  Per tile, with y = z / 2 and t = tanh(y) as in
-// the inference tile (halved weights, the first-layer bias carried by a
-// constant feature):
+// A CTA walks tiles of 128 pair records, one pair per tensor-memory lane.
+// Per tile, with y = z / 2 and t = tanh(y) as in the inference tile (halved
+// weights, the first-layer bias carried by a constant feature):
 //   L1    [y1 | dy1] = [phi | dphi] W1^T / 2                  D1, tensor memory
 //   epi1  h1 = y1 (1 + t1), dh1 = (1 + t1)(1 + y1 (1 - t1)) dy1   (BF16 rows)
 //   L2    [y2 | dy2] = [h1 | dh1] W2^T / 2                      D2
@@ -40,45 +39,49 @@ constexpr int NGRAD = G_W3 + MLP_H;  // every parameter but b3 (whose gradient i
 //   G2    dW2 += az2^T h1 + adz2^T dh1, db2 += az2^T 1, dw3 += (w dh2)^T 1
 //   epi3  az1 = ah1 silu'(z1) + adh1 silu''(z1) dz1, adz1 = adh1 silu'(z1)
 //   G1    dW1 += az1^T phi + adz1^T dphi, db1 += az1^T 1
-// The G products contract over the tile's 128 pairs (K = pairs) and stay in
-// tensor memory for all of the CTA's tiles; their operands are the pair-major
-// quantities written column by column (thread p writes column p) in a K-major
-// layout whose core matrices along K sit 144 bytes apart, so a warp's 16-bit
-// column stores hit distinct banks.  Bias and output-weight sums ride along
-// as a constant-1 row of the B operands.  M is 128 throughout: dW2 is the top
-// half of one product (rows az2^T, w dh2^T against [h1 | 1]) plus the bottom
-// half of another (rows w dh2^T, adz2^T against dh1), dW1 likewise.  Each CTA
-// writes one partial in a fixed order: the gradient is deterministic.
-constexpr int GT_M = 128;
+// Each pair's quantities are written once, as 16-byte pieces of its row, into
+// row buffers that serve twice: as K-major operands of the forward and
+// backward products (rows = pairs) and, read through MN-major descriptors, as
+// the operands of the G products, which contract over the tile's 128 pairs
+// (K = pairs) and accumulate in tensor memory over all of the CTA's tiles.
+// Bias and output-weight sums ride as a constant-1 column of the rows.  M is
+// 128 throughout: dW2 is the top half of one product (rows az2, w dh2
+// against [h1 | 1]) plus the bottom half of another (rows w dh2, adz2
+// against dh1), dW1 likewise.  The CTA's 16 warps split the 64 units of
+// every row four ways (warps w, w + 4, w + 8, w + 12 share the tensor-memory
+// lanes of pairs 32 (w % 4) ..).  Each CTA writes one partial in a fixed
+// order: the gradient is deterministic.
+constexpr int GT_M = 128;                 // pairs per tile
+constexpr int GT_NG = 4;                  // warps per tensor-memory lane quadrant (column groups)
+constexpr int GT_THREADS = GT_M * GT_NG;
+constexpr int GT_CW = MLP_H / GT_NG;      // units per thread in the epilogues (16)
 constexpr int GT_K1 = 48;
 constexpr int GT_H = MLP_H;
 constexpr uint32_t GT_COLS = 512;
 constexpr uint32_t GT_D1 = 0, GT_D2 = 128, GT_G2A = 256, GT_G2B = 336, GT_G1A = 400, GT_G1B = 448;
-constexpr uint32_t TLBO = 144, TSBO = 16 * TLBO;  // transposed (K = pairs) layout
-constexpr int A2T_ROWS = 192;  // az2 (0..63), w dh2 (64..127), adz2 (128..191); A1T: az1, adz1
-constexpr int BHT_ROWS = 144;  // h1 (0..63), ones (64), zeros (65..79), dh1 (80..143)
-constexpr int BPT_ROWS = 80;   // phi (0..31), ones (32), zeros (33..47), dphi (48..79)
+// row buffers, one row per pair (bf16 columns):
+//   F  phi (0..31), 1 (32), 0 (33..47), dphi (48..79), 0 (80..95)
+//   H  h1 (0..63), 1 (64), 0 (65..79), dh1 (80..143)
+//   Z  az2 (0..63), w dh2 (64..127), adz2 (128..191)
+//   A1 az1 (0..63), adz1 (64..127)
+constexpr int F_COLS = 96, H_COLS = 144, Z_COLS = 192, A1_COLS = 128;
+__host__ __device__ constexpr uint32_t rsbo(int cols) { return (uint32_t)(cols / 8) * 128; }  // stride of 8-pair groups
 constexpr int GT_WAIT = 1 << 22;
 
-__host__ __device__ constexpr uint32_t toff(int r, int k) {
-    return (uint32_t)((r >> 3) * TSBO + (k >> 3) * TLBO + (r & 7) * 16 + (k & 7) * 2);
-}
-
 struct __align__(1024) GradShared {
-    unsigned char a2t[A2T_ROWS / 8 * TSBO];  // A operand of G2; then of G1 (az1, adz1)
-    unsigned char bht[BHT_ROWS / 8 * TSBO];  // B operands of G2
-    unsigned char bpt[BPT_ROWS / 8 * TSBO];  // B operands of G1
-    unsigned char ra[2 * GT_M * GT_H * 2];   // row-major A operands: phi|dphi, then h1|dh1, then az2|adz2
-    unsigned char w1h[GT_H * GT_K1 * 2];     // W1 / 2 with the bias column
-    unsigned char w2h[GT_H * GT_H * 2];      // W2 / 2
-    unsigned char w2t[GT_H * GT_H * 2];      // W2^T
+    unsigned char f[GT_M * F_COLS * 2];
+    unsigned char h[GT_M * H_COLS * 2];
+    unsigned char z[GT_M * Z_COLS * 2];
+    unsigned char a1[GT_M * A1_COLS * 2];
+    unsigned char w1h[GT_H * GT_K1 * 2];  // W1 / 2 with the bias column
+    unsigned char w2h[GT_H * GT_H * 2];   // W2 / 2
+    unsigned char w2t[GT_H * GT_H * 2];   // W2^T
     float b2h[GT_H];
     float w3[GT_H];
     uint64_t mbar;
     uint32_t tmem;
     int stop;
 };
-
 
 __device__ __forceinline__ void st_bf(unsigned char* base, uint32_t off, float v) {
     *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16(v);
@@ -88,36 +91,52 @@ __device__ __forceinline__ float gt_tanh(float y) {
     asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(y));
     return t;
 }
-__device__ __forceinline__ void gt_row16(unsigned char* base, int row, int k, int K, uint4 v) {
-    *reinterpret_cast<uint4*>(base + tc::core_offset(row, k, K)) = v;
+// eight consecutive columns c.. of pair p's row in a buffer of `cols` columns
+__device__ __forceinline__ void st_row8(unsigned char* base, int p, int c, int cols, uint4 v) {
+    *reinterpret_cast<uint4*>(base + tc::core_offset(p, c, cols)) = v;
+}
+// a K-major descriptor (rows = pairs, K = columns) at column c0
+__device__ __forceinline__ uint64_t row_desc(uint32_t base, int c0, int cols) {
+    return tc::smem_desc(base + (c0 / 8) * 128, 128, rsbo(cols));
+}
+// an MN-major descriptor (M or N = columns from c0, K = the pairs of K-step ks)
+__device__ __forceinline__ uint64_t col_desc(uint32_t base, int c0, int cols, int ks) {
+    return tc::smem_desc(base + (c0 / 8) * 128 + ks * 2 * rsbo(cols), rsbo(cols), 128);
 }
 
 template <class T>
-__global__ void __launch_bounds__(GT_M, 1) k_mlp_grad(DevSys<T> s, int cur, const float4* __restrict__ err,
-                                                    float scale, float* __restrict__ partials) {
+__global__ void __launch_bounds__(GT_THREADS, 1) k_mlp_grad(DevSys<T> s, int cur, const float4* __restrict__ err,
+                                                          float scale, float* __restrict__ partials) {
     extern __shared__ __align__(1024) unsigned char gsm_raw[];
     GradShared& sh = *reinterpret_cast<GradShared*>(gsm_raw);
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int p = 32 * (warp & 3) + (tid & 31);  // this thread's pair slot (tensor-memory lane)
+    const int grp = warp >> 2;                   // its column group
     const MlpWeights* __restrict__ W = s.mlp;
-    for (int e = tid; e < GT_H * GT_K1; e += GT_M) {
+    for (int e = tid; e < GT_H * GT_K1; e += GT_THREADS) {
         const int n = e / GT_K1, k = e % GT_K1;
         const float v = k < MLP_NB ? __bfloat162float(W->W1[n * MLP_NB + k]) : (k == MLP_NB ? W->b1[n] : 0.f);
         st_bf(sh.w1h, tc::core_offset(n, k, GT_K1), 0.5f * v);
     }
-    for (int e = tid; e < GT_H * GT_H; e += GT_M) {
+    for (int e = tid; e < GT_H * GT_H; e += GT_THREADS) {
         const int n = e / GT_H, k = e % GT_H;
         st_bf(sh.w2h, tc::core_offset(n, k, GT_H), 0.5f * __bfloat162float(W->W2[n * GT_H + k]));
         st_bf(sh.w2t, tc::core_offset(n, k, GT_H), __bfloat162float(W->W2[k * GT_H + n]));  // (i, o) = W2[o][i]
     }
-    for (int e = tid; e < GT_H; e += GT_M) {
+    for (int e = tid; e < GT_H; e += GT_THREADS) {
         sh.w3[e] = W->w3[e];
         sh.b2h[e] = 0.5f * W->b2[e];
     }
-    // the constant rows of this thread's column (pair slot tid)
-    st_bf(sh.bht, toff(64, tid), 1.f);
-    for (int r = 65; r < 80; ++r) st_bf(sh.bht, toff(r, tid), 0.f);
-    st_bf(sh.bpt, toff(32, tid), 1.f);
-    for (int r = 33; r < 48; ++r) st_bf(sh.bpt, toff(r, tid), 0.f);
+    // the constant columns of this pair's rows
+    if (grp == 0) {
+        st_row8(sh.f, p, 32, F_COLS, make_uint4(pack_bf16x2(1.f, 0.f), 0u, 0u, 0u));
+        st_row8(sh.f, p, 40, F_COLS, make_uint4(0u, 0u, 0u, 0u));
+        st_row8(sh.f, p, 80, F_COLS, make_uint4(0u, 0u, 0u, 0u));
+        st_row8(sh.f, p, 88, F_COLS, make_uint4(0u, 0u, 0u, 0u));
+    } else if (grp == 1) {
+        st_row8(sh.h, p, 64, H_COLS, make_uint4(pack_bf16x2(1.f, 0.f), 0u, 0u, 0u));
+        st_row8(sh.h, p, 72, H_COLS, make_uint4(0u, 0u, 0u, 0u));
+    }
     if (tid == 0) {
         tc::mbar_init(&sh.mbar, 1);
         sh.stop = s.ctrl->abort;
@@ -128,7 +147,7 @@ __global__ void __launch_bounds__(GT_M, 1) k_mlp_grad(DevSys<T> s, int cur, cons
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = sh.tmem;
-    const uint32_t lanes = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t lanes = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
     const float rc = W->rc, rc2 = rc * rc;
     const float wid = rc / (MLP_NB - 1);
     const float inv2w2 = 0.5f / (wid * wid), invw2 = 1.0f / (wid * wid);
@@ -137,11 +156,14 @@ __global__ void __launch_bounds__(GT_M, 1) k_mlp_grad(DevSys<T> s, int cur, cons
     const int stride = s.stride;
     const int nu = min(*s.mlp_nupper, s.mlp_upper_cap);
     const int ntl = (nu + GT_M - 1) / GT_M;
-    const uint32_t ra = tc::smem_addr(sh.ra), w1 = tc::smem_addr(sh.w1h), w2 = tc::smem_addr(sh.w2h),
-                   w2t = tc::smem_addr(sh.w2t), a2t = tc::smem_addr(sh.a2t), bht = tc::smem_addr(sh.bht),
-                   bpt = tc::smem_addr(sh.bpt);
-    const uint32_t id64 = tc::idesc_bf16(GT_M, 64), id80 = tc::idesc_bf16(GT_M, 80),
-                   id48 = tc::idesc_bf16(GT_M, 48), id32 = tc::idesc_bf16(GT_M, 32);
+    const uint32_t fb = tc::smem_addr(sh.f), hb = tc::smem_addr(sh.h), zb = tc::smem_addr(sh.z),
+                   ab = tc::smem_addr(sh.a1), w1 = tc::smem_addr(sh.w1h), w2 = tc::smem_addr(sh.w2h),
+                   w2t = tc::smem_addr(sh.w2t);
+    const uint32_t id64 = tc::idesc_bf16(GT_M, 64);
+    // G products: both operands MN-major (transpose bits 15 and 16)
+    const uint32_t gt = (1u << 15) | (1u << 16);
+    const uint32_t id80t = tc::idesc_bf16(GT_M, 80) | gt, id64t = id64 | gt, id48t = tc::idesc_bf16(GT_M, 48) | gt,
+                   id32t = tc::idesc_bf16(GT_M, 32) | gt;
     const bool fault = s.tc_fault != 0;
     const int wait_limit = fault ? (1 << 12) : GT_WAIT;
     uint32_t parity = 0;
@@ -160,9 +182,10 @@ __global__ void __launch_bounds__(GT_M, 1) k_mlp_grad(DevSys<T> s, int cur, cons
         __syncthreads();
         tc::fence_after_sync();
     };
+    const int c0 = grp * GT_CW;  // this thread's 16 units of each layer
     for (int tile = blockIdx.x; ok && tile < ntl; tile += gridDim.x) {
-        // ---- this thread's pair: distance and row weight ------------------------
-        const int k = tile * GT_M + tid;
+        // ---- the pair: distance and row weight ----------------------------------
+        const int k = tile * GT_M + p;
         float r = rc, wrow = 0.f;
         if (k < nu) {
             const int4 up = s.mlp_upper[k];
@@ -181,191 +204,159 @@ __global__ void __launch_bounds__(GT_M, 1) k_mlp_grad(DevSys<T> s, int cur, cons
                 wrow = scale * ((ei.x - ej.x) * dx + (ei.y - ej.y) * dy + (ei.z - ej.z) * dz) / r;
             }
         }
-        // ---- features: phi / dphi rows (layer-1 A) and columns (G1 B) ------------
+        // ---- features 8 grp .. 8 grp + 7 of phi and dphi ---------------------------
         {
             const float fc = 0.5f * (__cosf(pirc * r) + 1.f);
             const float dfc = -0.5f * pirc * __sinf(pirc * r);
-            unsigned char* fa = sh.ra;
-            unsigned char* fd = sh.ra + GT_M * GT_K1 * 2;
+            unsigned int ph[4], dp[4];
 #pragma unroll
-            for (int g = 0; g < MLP_NB / 8; ++g) {
-                unsigned int ph[4], dp[4];
+            for (int q = 0; q < 4; ++q) {
+                float v[2], dv[2];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    float v[2], dv[2];
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int kk = 8 * g + 2 * q + h;
-                        const float d = r - wid * (float)kk;
-                        const float gk = __expf(-d * d * inv2w2);
-                        v[h] = gk * fc;
-                        dv[h] = gk * (dfc - d * invw2 * fc);
-                    }
-                    ph[q] = pack_bf16x2(v[0], v[1]);
-                    dp[q] = pack_bf16x2(dv[0], dv[1]);
-                    const __nv_bfloat162 pv = *reinterpret_cast<const __nv_bfloat162*>(&ph[q]);
-                    const __nv_bfloat162 dq = *reinterpret_cast<const __nv_bfloat162*>(&dp[q]);
-                    *reinterpret_cast<__nv_bfloat16*>(sh.bpt + toff(8 * g + 2 * q, tid)) = pv.x;
-                    *reinterpret_cast<__nv_bfloat16*>(sh.bpt + toff(8 * g + 2 * q + 1, tid)) = pv.y;
-                    *reinterpret_cast<__nv_bfloat16*>(sh.bpt + toff(48 + 8 * g + 2 * q, tid)) = dq.x;
-                    *reinterpret_cast<__nv_bfloat16*>(sh.bpt + toff(48 + 8 * g + 2 * q + 1, tid)) = dq.y;
+                for (int hh = 0; hh < 2; ++hh) {
+                    const float d = r - wid * (float)(8 * grp + 2 * q + hh);
+                    const float gk = __expf(-d * d * inv2w2);
+                    v[hh] = gk * fc;
+                    dv[hh] = gk * (dfc - d * invw2 * fc);
                 }
-                gt_row16(fa, tid, 8 * g, GT_K1, make_uint4(ph[0], ph[1], ph[2], ph[3]));
-                gt_row16(fd, tid, 8 * g, GT_K1, make_uint4(dp[0], dp[1], dp[2], dp[3]));
+                ph[q] = pack_bf16x2(v[0], v[1]);
+                dp[q] = pack_bf16x2(dv[0], dv[1]);
             }
-            gt_row16(fa, tid, 32, GT_K1, make_uint4(pack_bf16x2(1.f, 0.f), 0u, 0u, 0u));
-            gt_row16(fa, tid, 40, GT_K1, make_uint4(0u, 0u, 0u, 0u));
-            gt_row16(fd, tid, 32, GT_K1, make_uint4(0u, 0u, 0u, 0u));
-            gt_row16(fd, tid, 40, GT_K1, make_uint4(0u, 0u, 0u, 0u));
+            st_row8(sh.f, p, 8 * grp, F_COLS, make_uint4(ph[0], ph[1], ph[2], ph[3]));
+            st_row8(sh.f, p, 48 + 8 * grp, F_COLS, make_uint4(dp[0], dp[1], dp[2], dp[3]));
         }
         sync_smem();
         if (tid == 0 && !fault) {
-            constexpr uint32_t sbo = (GT_K1 / 8) * 128;
 #pragma unroll
             for (int ks = 0; ks < GT_K1 / 16; ++ks) {
-                const uint64_t db = tc::smem_desc(w1 + ks * 256, 128, sbo);
-                tc::mma(tmem + GT_D1, tc::smem_desc(ra + ks * 256, 128, sbo), db, id64, ks > 0);
-                tc::mma(tmem + GT_D1 + 64, tc::smem_desc(ra + GT_M * GT_K1 * 2 + ks * 256, 128, sbo), db, id64,
-                        ks > 0);
+                const uint64_t db = tc::smem_desc(w1 + ks * 256, 128, (GT_K1 / 8) * 128);
+                tc::mma(tmem + GT_D1, row_desc(fb, 16 * ks, F_COLS), db, id64, ks > 0);
+                tc::mma(tmem + GT_D1 + 64, row_desc(fb, 48 + 16 * ks, F_COLS), db, id64, ks > 0);
             }
         }
         if (!sync_mma()) {
             ok = false;
             break;
         }
-        // ---- epilogue 1: h1, dh1 rows (layer-2 A) and columns (G2 B) -------------
+        // ---- epilogue 1: h1, dh1 --------------------------------------------------
         {
-            unsigned char* ha = sh.ra;
-            unsigned char* hd = sh.ra + GT_M * GT_H * 2;
-#pragma unroll 1
-            for (int c = 0; c < GT_H; c += 16) {
-                float y[16], dy[16];
-                tc::tmem_ld16x2(lanes + GT_D1 + c, lanes + GT_D1 + 64 + c, y, dy);
-                unsigned int hw[8], dw[8];
+            float y[16], dy[16];
+            tc::tmem_ld16x2(lanes + GT_D1 + c0, lanes + GT_D1 + 64 + c0, y, dy);
+            unsigned int hw[8], dw[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    float hv[2], dv[2];
+            for (int j = 0; j < 8; ++j) {
+                float hv[2], dv[2];
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const float yy = y[2 * j + h], t = gt_tanh(yy);
-                        hv[h] = yy * (1.f + t);
-                        dv[h] = (1.f + t) * (1.f + yy * (1.f - t)) * dy[2 * j + h];
-                    }
-                    hw[j] = pack_bf16x2(hv[0], hv[1]);
-                    dw[j] = pack_bf16x2(dv[0], dv[1]);
-                    const __nv_bfloat162 hb = *reinterpret_cast<const __nv_bfloat162*>(&hw[j]);
-                    const __nv_bfloat162 db = *reinterpret_cast<const __nv_bfloat162*>(&dw[j]);
-                    *reinterpret_cast<__nv_bfloat16*>(sh.bht + toff(c + 2 * j, tid)) = hb.x;
-                    *reinterpret_cast<__nv_bfloat16*>(sh.bht + toff(c + 2 * j + 1, tid)) = hb.y;
-                    *reinterpret_cast<__nv_bfloat16*>(sh.bht + toff(80 + c + 2 * j, tid)) = db.x;
-                    *reinterpret_cast<__nv_bfloat16*>(sh.bht + toff(80 + c + 2 * j + 1, tid)) = db.y;
+                for (int hh = 0; hh < 2; ++hh) {
+                    const float yy = y[2 * j + hh], t = gt_tanh(yy);
+                    hv[hh] = yy * (1.f + t);
+                    dv[hh] = (1.f + t) * (1.f + yy * (1.f - t)) * dy[2 * j + hh];
                 }
-                gt_row16(ha, tid, c, GT_H, make_uint4(hw[0], hw[1], hw[2], hw[3]));
-                gt_row16(ha, tid, c + 8, GT_H, make_uint4(hw[4], hw[5], hw[6], hw[7]));
-                gt_row16(hd, tid, c, GT_H, make_uint4(dw[0], dw[1], dw[2], dw[3]));
-                gt_row16(hd, tid, c + 8, GT_H, make_uint4(dw[4], dw[5], dw[6], dw[7]));
+                hw[j] = pack_bf16x2(hv[0], hv[1]);
+                dw[j] = pack_bf16x2(dv[0], dv[1]);
             }
+            st_row8(sh.h, p, c0, H_COLS, make_uint4(hw[0], hw[1], hw[2], hw[3]));
+            st_row8(sh.h, p, c0 + 8, H_COLS, make_uint4(hw[4], hw[5], hw[6], hw[7]));
+            st_row8(sh.h, p, 80 + c0, H_COLS, make_uint4(dw[0], dw[1], dw[2], dw[3]));
+            st_row8(sh.h, p, 88 + c0, H_COLS, make_uint4(dw[4], dw[5], dw[6], dw[7]));
         }
         sync_smem();
         if (tid == 0 && !fault) {
-            constexpr uint32_t sbo = (GT_H / 8) * 128;
 #pragma unroll
             for (int ks = 0; ks < GT_H / 16; ++ks) {
-                const uint64_t db = tc::smem_desc(w2 + ks * 256, 128, sbo);
-                tc::mma(tmem + GT_D2, tc::smem_desc(ra + ks * 256, 128, sbo), db, id64, ks > 0);
-                tc::mma(tmem + GT_D2 + 64, tc::smem_desc(ra + GT_M * GT_H * 2 + ks * 256, 128, sbo), db, id64,
-                        ks > 0);
+                const uint64_t db = tc::smem_desc(w2 + ks * 256, 128, (GT_H / 8) * 128);
+                tc::mma(tmem + GT_D2, row_desc(hb, 16 * ks, H_COLS), db, id64, ks > 0);
+                tc::mma(tmem + GT_D2 + 64, row_desc(hb, 80 + 16 * ks, H_COLS), db, id64, ks > 0);
             }
         }
         if (!sync_mma()) {
             ok = false;
             break;
         }
-        // ---- epilogue 2: reverse seeds, rows (BW A) and columns (G2 A) -----------
+        // ---- epilogue 2: the reverse seeds ------------------------------------------
         {
-            unsigned char* za = sh.ra;
-            unsigned char* zd = sh.ra + GT_M * GT_H * 2;
-#pragma unroll 1
-            for (int c = 0; c < GT_H; c += 16) {
-                float y[16], dy[16];
-                tc::tmem_ld16x2(lanes + GT_D2 + c, lanes + GT_D2 + 64 + c, y, dy);
-                unsigned int aw[8], dw[8];
+            float y[16], dy[16];
+            tc::tmem_ld16x2(lanes + GT_D2 + c0, lanes + GT_D2 + 64 + c0, y, dy);
+            unsigned int aw[8], ww[8], dw[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    float av[2], adv[2];
+            for (int j = 0; j < 8; ++j) {
+                float av[2], wv[2], adv[2];
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int o = c + 2 * j + h;
-                        const float yy = y[2 * j + h] + sh.b2h[o], t = gt_tanh(yy);
-                        const float s1 = 0.5f * (1.f + t) * (1.f + yy * (1.f - t));
-                        const float s2 = 0.5f * (1.f - t * t) * (1.f - yy * t);
-                        const float dz = 2.f * dy[2 * j + h];
-                        const float ww = wrow * sh.w3[o];
-                        av[h] = ww * s2 * dz;
-                        adv[h] = ww * s1;
-                        st_bf(sh.a2t, toff(64 + o, tid), wrow * s1 * dz);
-                    }
-                    aw[j] = pack_bf16x2(av[0], av[1]);
-                    dw[j] = pack_bf16x2(adv[0], adv[1]);
-                    const __nv_bfloat162 ab = *reinterpret_cast<const __nv_bfloat162*>(&aw[j]);
-                    const __nv_bfloat162 db = *reinterpret_cast<const __nv_bfloat162*>(&dw[j]);
-                    *reinterpret_cast<__nv_bfloat16*>(sh.a2t + toff(c + 2 * j, tid)) = ab.x;
-                    *reinterpret_cast<__nv_bfloat16*>(sh.a2t + toff(c + 2 * j + 1, tid)) = ab.y;
-                    *reinterpret_cast<__nv_bfloat16*>(sh.a2t + toff(128 + c + 2 * j, tid)) = db.x;
-                    *reinterpret_cast<__nv_bfloat16*>(sh.a2t + toff(128 + c + 2 * j + 1, tid)) = db.y;
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int o = c0 + 2 * j + hh;
+                    const float yy = y[2 * j + hh] + sh.b2h[o], t = gt_tanh(yy);
+                    const float s1 = 0.5f * (1.f + t) * (1.f + yy * (1.f - t));
+                    const float s2 = 0.5f * (1.f - t * t) * (1.f - yy * t);
+                    const float dz = 2.f * dy[2 * j + hh];
+                    const float wo = wrow * sh.w3[o];
+                    av[hh] = wo * s2 * dz;
+                    adv[hh] = wo * s1;
+                    wv[hh] = wrow * s1 * dz;
                 }
-                gt_row16(za, tid, c, GT_H, make_uint4(aw[0], aw[1], aw[2], aw[3]));
-                gt_row16(za, tid, c + 8, GT_H, make_uint4(aw[4], aw[5], aw[6], aw[7]));
-                gt_row16(zd, tid, c, GT_H, make_uint4(dw[0], dw[1], dw[2], dw[3]));
-                gt_row16(zd, tid, c + 8, GT_H, make_uint4(dw[4], dw[5], dw[6], dw[7]));
+                aw[j] = pack_bf16x2(av[0], av[1]);
+                ww[j] = pack_bf16x2(wv[0], wv[1]);
+                dw[j] = pack_bf16x2(adv[0], adv[1]);
             }
+            st_row8(sh.z, p, c0, Z_COLS, make_uint4(aw[0], aw[1], aw[2], aw[3]));
+            st_row8(sh.z, p, c0 + 8, Z_COLS, make_uint4(aw[4], aw[5], aw[6], aw[7]));
+            st_row8(sh.z, p, 64 + c0, Z_COLS, make_uint4(ww[0], ww[1], ww[2], ww[3]));
+            st_row8(sh.z, p, 72 + c0, Z_COLS, make_uint4(ww[4], ww[5], ww[6], ww[7]));
+            st_row8(sh.z, p, 128 + c0, Z_COLS, make_uint4(dw[0], dw[1], dw[2], dw[3]));
+            st_row8(sh.z, p, 136 + c0, Z_COLS, make_uint4(dw[4], dw[5], dw[6], dw[7]));
         }
         sync_smem();
         if (tid == 0 && !fault) {
-            constexpr uint32_t sbo = (GT_H / 8) * 128;
 #pragma unroll
             for (int ks = 0; ks < GT_H / 16; ++ks) {
-                const uint64_t db = tc::smem_desc(w2t + ks * 256, 128, sbo);
-                tc::mma(tmem + GT_D2, tc::smem_desc(ra + ks * 256, 128, sbo), db, id64, ks > 0);
-                tc::mma(tmem + GT_D2 + 64, tc::smem_desc(ra + GT_M * GT_H * 2 + ks * 256, 128, sbo), db, id64,
-                        ks > 0);
+                const uint64_t db = tc::smem_desc(w2t + ks * 256, 128, (GT_H / 8) * 128);
+                tc::mma(tmem + GT_D2, row_desc(zb, 16 * ks, Z_COLS), db, id64, ks > 0);
+                tc::mma(tmem + GT_D2 + 64, row_desc(zb, 128 + 16 * ks, Z_COLS), db, id64, ks > 0);
             }
 #pragma unroll
             for (int ks = 0; ks < GT_M / 16; ++ks) {
-                const uint32_t kb = ks * 2 * TLBO;
-                tc::mma(tmem + GT_G2A, tc::smem_desc(a2t + kb, TLBO, TSBO), tc::smem_desc(bht + kb, TLBO, TSBO), id80,
+                tc::mma(tmem + GT_G2A, col_desc(zb, 0, Z_COLS, ks), col_desc(hb, 0, H_COLS, ks), id80t,
                         acc || ks > 0);
-                tc::mma(tmem + GT_G2B, tc::smem_desc(a2t + 8 * TSBO + kb, TLBO, TSBO),
-                        tc::smem_desc(bht + 10 * TSBO + kb, TLBO, TSBO), id64, acc || ks > 0);
+                tc::mma(tmem + GT_G2B, col_desc(zb, 64, Z_COLS, ks), col_desc(hb, 80, H_COLS, ks), id64t,
+                        acc || ks > 0);
             }
         }
         if (!sync_mma()) {
             ok = false;
             break;
         }
-        // ---- epilogue 3: layer-1 adjoints, columns (G1 A, over G2's A) -----------
-#pragma unroll 1
-        for (int c = 0; c < GT_H; c += 16) {
+        // ---- epilogue 3: layer-1 adjoints ---------------------------------------------
+        {
             float ah[16], adh[16], y[16], dy[16];
-            tc::tmem_ld16x2(lanes + GT_D2 + c, lanes + GT_D2 + 64 + c, ah, adh);
-            tc::tmem_ld16x2(lanes + GT_D1 + c, lanes + GT_D1 + 64 + c, y, dy);
+            tc::tmem_ld16x2(lanes + GT_D2 + c0, lanes + GT_D2 + 64 + c0, ah, adh);
+            tc::tmem_ld16x2(lanes + GT_D1 + c0, lanes + GT_D1 + 64 + c0, y, dy);
+            unsigned int aw[8], dw[8];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const float yy = y[j], t = gt_tanh(yy);
-                const float s1 = 0.5f * (1.f + t) * (1.f + yy * (1.f - t));
-                const float s2 = 0.5f * (1.f - t * t) * (1.f - yy * t);
-                st_bf(sh.a2t, toff(c + j, tid), ah[j] * s1 + adh[j] * s2 * (2.f * dy[j]));
-                st_bf(sh.a2t, toff(64 + c + j, tid), adh[j] * s1);
+            for (int j = 0; j < 8; ++j) {
+                float av[2], dv[2];
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int q = 2 * j + hh;
+                    const float yy = y[q], t = gt_tanh(yy);
+                    const float s1 = 0.5f * (1.f + t) * (1.f + yy * (1.f - t));
+                    const float s2 = 0.5f * (1.f - t * t) * (1.f - yy * t);
+                    av[hh] = ah[q] * s1 + adh[q] * s2 * (2.f * dy[q]);
+                    dv[hh] = adh[q] * s1;
+                }
+                aw[j] = pack_bf16x2(av[0], av[1]);
+                dw[j] = pack_bf16x2(dv[0], dv[1]);
             }
+            st_row8(sh.a1, p, c0, A1_COLS, make_uint4(aw[0], aw[1], aw[2], aw[3]));
+            st_row8(sh.a1, p, c0 + 8, A1_COLS, make_uint4(aw[4], aw[5], aw[6], aw[7]));
+            st_row8(sh.a1, p, 64 + c0, A1_COLS, make_uint4(dw[0], dw[1], dw[2], dw[3]));
+            st_row8(sh.a1, p, 72 + c0, A1_COLS, make_uint4(dw[4], dw[5], dw[6], dw[7]));
         }
         sync_smem();
         if (tid == 0 && !fault) {
 #pragma unroll
             for (int ks = 0; ks < GT_M / 16; ++ks) {
-                const uint32_t kb = ks * 2 * TLBO;
-                const uint64_t da = tc::smem_desc(a2t + kb, TLBO, TSBO);
-                tc::mma(tmem + GT_G1A, da, tc::smem_desc(bpt + kb, TLBO, TSBO), id48, acc || ks > 0);
-                tc::mma(tmem + GT_G1B, da, tc::smem_desc(bpt + 6 * TSBO + kb, TLBO, TSBO), id32, acc || ks > 0);
+                const uint64_t da = col_desc(ab, 0, A1_COLS, ks);
+                tc::mma(tmem + GT_G1A, da, col_desc(fb, 0, F_COLS, ks), id48t, acc || ks > 0);
+                tc::mma(tmem + GT_G1B, da, col_desc(fb, 48, F_COLS, ks), id32t, acc || ks > 0);
             }
         }
         // the next tile rewrites the operands of these products
@@ -387,65 +378,53 @@ __global__ void __launch_bounds__(GT_M, 1) k_mlp_grad(DevSys<T> s, int cur, cons
     // ---- this CTA's partial: rows 64..127 of the products hold the second
     //      halves (through shared memory), rows 0..63 the first ---------------
     float* out = partials + (size_t)blockIdx.x * NGRAD;
-    float* part2 = reinterpret_cast<float*>(sh.ra);  // dW2 part 2 [64][64], dW1 part 2 [64][32], dw3 [64]
-    if (ok && acc && tid >= 64) {
-        const int o = tid - 64;
-#pragma unroll 1
-        for (int c = 0; c < 64; c += 32) {
-            float a[16], b[16];
-            tc::tmem_ld16x2(lanes + GT_G2B + c, lanes + GT_G2B + c + 16, a, b);
+    float* part2 = reinterpret_cast<float*>(sh.z);  // dW2 part 2 [64][64], dW1 part 2 [64][32], dw3 [64]
+    const bool lower = p >= 64;                      // uniform per warp
+    if (ok && acc && lower) {
+        const int o = p - 64;
+        float a[16], b[16];
+        tc::tmem_ld16x2(lanes + GT_G2B + c0, lanes + GT_G1B + (c0 & 16), a, b);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                part2[o * 64 + c + j] = a[j];
-                part2[o * 64 + c + 16 + j] = b[j];
-            }
-        }
-        {
-            float a[16], b[16];
-            tc::tmem_ld16x2(lanes + GT_G1B, lanes + GT_G1B + 16, a, b);
+        for (int j = 0; j < 16; ++j) part2[o * 64 + c0 + j] = a[j];
+        if (grp < 2)
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                part2[4096 + o * 32 + j] = a[j];
-                part2[4096 + o * 32 + 16 + j] = b[j];
-            }
-            tc::tmem_ld16x2(lanes + GT_G2A + 64, lanes + GT_G1A + 32, a, b);
+            for (int j = 0; j < 16; ++j) part2[4096 + o * 32 + c0 + j] = b[j];
+        if (grp == 0) {
+            tc::tmem_ld16x2(lanes + GT_G2A + 64, lanes + GT_G2A + 64, a, b);
             part2[6144 + o] = a[0];
+        } else {
+            tc::tmem_ld16x2(lanes + GT_G2A + 64, lanes + GT_G2A + 64, a, b);  // the warp's collective read
         }
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (tid < 64) {
-        const int o = tid;
+    if (!lower) {
+        const int o = p;
         if (ok && acc) {
-#pragma unroll 1
-            for (int c = 0; c < 64; c += 32) {
-                float a[16], b[16];
-                tc::tmem_ld16x2(lanes + GT_G2A + c, lanes + GT_G2A + c + 16, a, b);
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    out[G_W2 + o * 64 + c + j] = a[j] + part2[o * 64 + c + j];
-                    out[G_W2 + o * 64 + c + 16 + j] = b[j] + part2[o * 64 + c + 16 + j];
-                }
-            }
             float a[16], b[16];
-            tc::tmem_ld16x2(lanes + GT_G1A, lanes + GT_G1A + 16, a, b);
+            tc::tmem_ld16x2(lanes + GT_G2A + c0, lanes + GT_G1A + (c0 & 16), a, b);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                out[G_W1 + o * 32 + j] = a[j] + part2[4096 + o * 32 + j];
-                out[G_W1 + o * 32 + 16 + j] = b[j] + part2[4096 + o * 32 + 16 + j];
-            }
+            for (int j = 0; j < 16; ++j) out[G_W2 + o * 64 + c0 + j] = a[j] + part2[o * 64 + c0 + j];
+            if (grp < 2)
+#pragma unroll
+                for (int j = 0; j < 16; ++j) out[G_W1 + o * 32 + c0 + j] = b[j] + part2[4096 + o * 32 + c0 + j];
             tc::tmem_ld16x2(lanes + GT_G2A + 64, lanes + GT_G1A + 32, a, b);
-            out[G_B2 + o] = a[0];
-            out[G_B1 + o] = b[0];
-            out[G_W3 + o] = part2[6144 + o];
+            if (grp == 0) {
+                out[G_B2 + o] = a[0];
+                out[G_B1 + o] = b[0];
+                out[G_W3 + o] = part2[6144 + o];
+            }
         } else {
             // no tile (or a failed wait): a zero partial
-            for (int c = 0; c < 64; ++c) out[G_W2 + o * 64 + c] = 0.f;
-            for (int c = 0; c < 32; ++c) out[G_W1 + o * 32 + c] = 0.f;
-            out[G_B2 + o] = 0.f;
-            out[G_B1 + o] = 0.f;
-            out[G_W3 + o] = 0.f;
+            for (int c = 0; c < GT_CW; ++c) out[G_W2 + o * 64 + c0 + c] = 0.f;
+            if (grp < 2)
+                for (int c = 0; c < GT_CW; ++c) out[G_W1 + o * 32 + c0 + c] = 0.f;
+            if (grp == 0) {
+                out[G_B2 + o] = 0.f;
+                out[G_B1 + o] = 0.f;
+                out[G_W3 + o] = 0.f;
+            }
         }
     }
     tc::fence_before_sync();
@@ -574,7 +553,7 @@ int Launch<T>::train_grad(const DevSys<T>& s, int cur, const double* Y, float4* 
                           float scale, float* partials, int grad_blocks, float* grad, double* loss,
                           cudaStream_t st) {
     k_train_err<T><<<s.ntiles, TILE, 0, st>>>(s, cur, Y, err, loss_part);
-    k_mlp_grad<T><<<grad_blocks, GT_M, sizeof(GradShared), st>>>(s, cur, err, scale, partials);
+    k_mlp_grad<T><<<grad_blocks, GT_THREADS, sizeof(GradShared), st>>>(s, cur, err, scale, partials);
     // the chunk sums sit after the blocks' partials
     float* chunk = partials + (size_t)grad_blocks * NGRAD;
     k_grad_chunks<<<dim3((NGRAD + 255) / 256, GRED_CHUNKS), 256, 0, st>>>(partials, grad_blocks, chunk);
