@@ -78,6 +78,8 @@ struct __align__(1024) GradShared {
     unsigned char w2t[GT_H * GT_H * 2];   // W2^T
     float b2h[GT_H];
     float w3[GT_H];
+    float pr[2][GT_M];  // distance and row weight of each pair slot, this tile and the next
+    float pw[2][GT_M];
     uint64_t mbar;
     uint32_t tmem;
     int stop;
@@ -102,6 +104,30 @@ __device__ __forceinline__ uint64_t row_desc(uint32_t base, int c0, int cols) {
 // an MN-major descriptor (M or N = columns from c0, K = the pairs of K-step ks)
 __device__ __forceinline__ uint64_t col_desc(uint32_t base, int c0, int cols, int ks) {
     return tc::smem_desc(base + (c0 / 8) * 128 + ks * 2 * rsbo(cols), rsbo(cols), 128);
+}
+
+// Distance and row weight of pair record k (r = rc and w = 0 past the end or
+// beyond the cutoff): w = scale ((e_i - e_j) . r_ij) / r.
+template <class T>
+__device__ __forceinline__ void pair_weight(const DevSys<T>& s, const V4<T>* __restrict__ P,
+                                            const float4* __restrict__ err, int4 up, bool valid, float rc2,
+                                            float scale, float& r, float& w) {
+    if (!valid) return;
+    const int stride = s.stride;
+    const int i = (up.x >> 2) % stride, j = nbr_slot(up.z);
+    const RepGeom<T>& geo = s.reps[up.w];
+    const T L0 = geo.L[0], L1 = geo.L[1], L2 = geo.L[2];
+    const V4<T> xi = ld4<T>(P + i), xj = ld4<T>(P + j);
+    const float4 ei = err[i], ej = err[j];
+    const int code = nbr_code(up.z);
+    const float dx = (float)shifted_diff(xi.x, (T)(xi.x - L0), xj.x, L0, code & 3);
+    const float dy = (float)shifted_diff(xi.y, (T)(xi.y - L1), xj.y, L1, (code >> 2) & 3);
+    const float dz = (float)shifted_diff(xi.z, (T)(xi.z - L2), xj.z, L2, code >> 4);
+    const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    if (r2 < rc2) {
+        r = sqrtf(r2);
+        w = scale * ((ei.x - ej.x) * dx + (ei.y - ej.y) * dy + (ei.z - ej.z) * dz) / r;
+    }
 }
 
 template <class T>
@@ -153,7 +179,6 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_mlp_grad(DevSys<T> s, int cur
     const float inv2w2 = 0.5f / (wid * wid), invw2 = 1.0f / (wid * wid);
     const float pirc = 3.14159265358979f / rc;
     const V4<T>* __restrict__ P = s.pos[cur];
-    const int stride = s.stride;
     const int nu = min(*s.mlp_nupper, s.mlp_upper_cap);
     const int ntl = (nu + GT_M - 1) / GT_M;
     const uint32_t fb = tc::smem_addr(sh.f), hb = tc::smem_addr(sh.h), zb = tc::smem_addr(sh.z),
@@ -183,27 +208,23 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_mlp_grad(DevSys<T> s, int cur
         tc::fence_after_sync();
     };
     const int c0 = grp * GT_CW;  // this thread's 16 units of each layer
+    // the pair data of the first tile (column group 0 loads and shares it)
+    if (grp == 0) {
+        const int k = blockIdx.x * GT_M + p;
+        float r = rc, w = 0.f;
+        pair_weight<T>(s, P, err, k < nu ? s.mlp_upper[k] : make_int4(0, 0, 0, 0), k < nu, rc2, scale, r, w);
+        sh.pr[0][p] = r;
+        sh.pw[0][p] = w;
+    }
+    __syncthreads();
+    int buf = 0;
     for (int tile = blockIdx.x; ok && tile < ntl; tile += gridDim.x) {
-        // ---- the pair: distance and row weight ----------------------------------
-        const int k = tile * GT_M + p;
-        float r = rc, wrow = 0.f;
-        if (k < nu) {
-            const int4 up = s.mlp_upper[k];
-            const int i = (up.x >> 2) % stride, j = nbr_slot(up.z);
-            const RepGeom<T>& geo = s.reps[up.w];
-            const T L0 = geo.L[0], L1 = geo.L[1], L2 = geo.L[2];
-            const V4<T> xi = ld4<T>(P + i), xj = ld4<T>(P + j);
-            const int code = nbr_code(up.z);
-            const float dx = (float)shifted_diff(xi.x, (T)(xi.x - L0), xj.x, L0, code & 3);
-            const float dy = (float)shifted_diff(xi.y, (T)(xi.y - L1), xj.y, L1, (code >> 2) & 3);
-            const float dz = (float)shifted_diff(xi.z, (T)(xi.z - L2), xj.z, L2, code >> 4);
-            const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-            if (r2 < rc2) {
-                r = sqrtf(r2);
-                const float4 ei = err[i], ej = err[j];
-                wrow = scale * ((ei.x - ej.x) * dx + (ei.y - ej.y) * dy + (ei.z - ej.z) * dz) / r;
-            }
-        }
+        // ---- the pair: distance and row weight (shared by its four threads) ------
+        const float r = sh.pr[buf][p], wrow = sh.pw[buf][p];
+        // the next tile's record, requested now and used after epilogue 2
+        const int kn = (tile + gridDim.x) * GT_M + p;
+        const bool next_valid = grp == 0 && kn < nu;
+        const int4 up_next = next_valid ? s.mlp_upper[kn] : make_int4(0, 0, 0, 0);
         // ---- features 8 grp .. 8 grp + 7 of phi and dphi ---------------------------
         {
             const float fc = 0.5f * (__cosf(pirc * r) + 1.f);
@@ -238,22 +259,20 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_mlp_grad(DevSys<T> s, int cur
             ok = false;
             break;
         }
-        // ---- epilogue 1: h1, dh1 --------------------------------------------------
+        // ---- epilogue 1: h1, dh1 (two units per packed instruction) -----------------
         {
             float y[16], dy[16];
             tc::tmem_ld16x2(lanes + GT_D1 + c0, lanes + GT_D1 + 64 + c0, y, dy);
             unsigned int hw[8], dw[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                float hv[2], dv[2];
-#pragma unroll
-                for (int hh = 0; hh < 2; ++hh) {
-                    const float yy = y[2 * j + hh], t = gt_tanh(yy);
-                    hv[hh] = yy * (1.f + t);
-                    dv[hh] = (1.f + t) * (1.f + yy * (1.f - t)) * dy[2 * j + hh];
-                }
-                hw[j] = pack_bf16x2(hv[0], hv[1]);
-                dw[j] = pack_bf16x2(dv[0], dv[1]);
+                const f32x2 yv = f2(y[2 * j], y[2 * j + 1]);
+                const f32x2 tv = f2(gt_tanh(y[2 * j]), gt_tanh(y[2 * j + 1]));
+                float h0, h1, d0, d1;
+                f2split(f2fma(yv, tv, yv), h0, h1);  // y (1 + t)
+                f2split(f2mul(silu_tangent_factor(yv, tv), f2(dy[2 * j], dy[2 * j + 1])), d0, d1);
+                hw[j] = pack_bf16x2(h0, h1);
+                dw[j] = pack_bf16x2(d0, d1);
             }
             st_row8(sh.h, p, c0, H_COLS, make_uint4(hw[0], hw[1], hw[2], hw[3]));
             st_row8(sh.h, p, c0 + 8, H_COLS, make_uint4(hw[4], hw[5], hw[6], hw[7]));
@@ -273,29 +292,37 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_mlp_grad(DevSys<T> s, int cur
             ok = false;
             break;
         }
-        // ---- epilogue 2: the reverse seeds ------------------------------------------
+        // ---- epilogue 2: the reverse seeds (two units per packed instruction) ---------
+        // with z = 2 y, t = tanh(y): silu'(z) = (1 + t)(1 + y (1 - t)) / 2,
+        // silu''(z) = (1 + t)(1 - t)(1 - y t) / 2
         {
             float y[16], dy[16];
             tc::tmem_ld16x2(lanes + GT_D2 + c0, lanes + GT_D2 + 64 + c0, y, dy);
             unsigned int aw[8], ww[8], dw[8];
+            const f32x2 one = f2(1.f, 1.f), mone = f2(-1.f, -1.f), half = f2(0.5f, 0.5f);
+            const f32x2 wv2 = f2(wrow, wrow);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                float av[2], wv[2], adv[2];
-#pragma unroll
-                for (int hh = 0; hh < 2; ++hh) {
-                    const int o = c0 + 2 * j + hh;
-                    const float yy = y[2 * j + hh] + sh.b2h[o], t = gt_tanh(yy);
-                    const float s1 = 0.5f * (1.f + t) * (1.f + yy * (1.f - t));
-                    const float s2 = 0.5f * (1.f - t * t) * (1.f - yy * t);
-                    const float dz = 2.f * dy[2 * j + hh];
-                    const float wo = wrow * sh.w3[o];
-                    av[hh] = wo * s2 * dz;
-                    adv[hh] = wo * s1;
-                    wv[hh] = wrow * s1 * dz;
-                }
-                aw[j] = pack_bf16x2(av[0], av[1]);
-                ww[j] = pack_bf16x2(wv[0], wv[1]);
-                dw[j] = pack_bf16x2(adv[0], adv[1]);
+                const int o = c0 + 2 * j;
+                const float2 bb = *reinterpret_cast<const float2*>(sh.b2h + o);
+                const float2 w3v = *reinterpret_cast<const float2*>(sh.w3 + o);
+                const f32x2 yv = f2add(f2(y[2 * j], y[2 * j + 1]), f2(bb.x, bb.y));
+                float ya, yb;
+                f2split(yv, ya, yb);
+                const f32x2 tv = f2(gt_tanh(ya), gt_tanh(yb));
+                const f32x2 opt = f2add(tv, one), omt = f2fma(tv, mone, one);
+                const f32x2 hopt = f2mul(half, opt);
+                const f32x2 s1 = f2mul(hopt, f2fma(yv, omt, one));
+                const f32x2 s2 = f2mul(f2mul(hopt, omt), f2fma(f2mul(yv, tv), mone, one));
+                const f32x2 dz = f2(2.f * dy[2 * j], 2.f * dy[2 * j + 1]);
+                const f32x2 wo = f2mul(wv2, f2(w3v.x, w3v.y));
+                float a0, a1, w0, w1, d0, d1;
+                f2split(f2mul(f2mul(wo, s2), dz), a0, a1);   // az2
+                f2split(f2mul(f2mul(wv2, s1), dz), w0, w1);  // w dh2
+                f2split(f2mul(wo, s1), d0, d1);              // adz2
+                aw[j] = pack_bf16x2(a0, a1);
+                ww[j] = pack_bf16x2(w0, w1);
+                dw[j] = pack_bf16x2(d0, d1);
             }
             st_row8(sh.z, p, c0, Z_COLS, make_uint4(aw[0], aw[1], aw[2], aw[3]));
             st_row8(sh.z, p, c0 + 8, Z_COLS, make_uint4(aw[4], aw[5], aw[6], aw[7]));
@@ -303,6 +330,13 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_mlp_grad(DevSys<T> s, int cur
             st_row8(sh.z, p, 72 + c0, Z_COLS, make_uint4(ww[4], ww[5], ww[6], ww[7]));
             st_row8(sh.z, p, 128 + c0, Z_COLS, make_uint4(dw[0], dw[1], dw[2], dw[3]));
             st_row8(sh.z, p, 136 + c0, Z_COLS, make_uint4(dw[4], dw[5], dw[6], dw[7]));
+        }
+        if (grp == 0) {
+            // the next tile's pair data, into the other buffer
+            float rn = rc, wn = 0.f;
+            pair_weight<T>(s, P, err, up_next, next_valid, rc2, scale, rn, wn);
+            sh.pr[buf ^ 1][p] = rn;
+            sh.pw[buf ^ 1][p] = wn;
         }
         sync_smem();
         if (tid == 0 && !fault) {
@@ -330,20 +364,22 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_mlp_grad(DevSys<T> s, int cur
             tc::tmem_ld16x2(lanes + GT_D2 + c0, lanes + GT_D2 + 64 + c0, ah, adh);
             tc::tmem_ld16x2(lanes + GT_D1 + c0, lanes + GT_D1 + 64 + c0, y, dy);
             unsigned int aw[8], dw[8];
+            const f32x2 one = f2(1.f, 1.f), mone = f2(-1.f, -1.f), half = f2(0.5f, 0.5f);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                float av[2], dv[2];
-#pragma unroll
-                for (int hh = 0; hh < 2; ++hh) {
-                    const int q = 2 * j + hh;
-                    const float yy = y[q], t = gt_tanh(yy);
-                    const float s1 = 0.5f * (1.f + t) * (1.f + yy * (1.f - t));
-                    const float s2 = 0.5f * (1.f - t * t) * (1.f - yy * t);
-                    av[hh] = ah[q] * s1 + adh[q] * s2 * (2.f * dy[q]);
-                    dv[hh] = adh[q] * s1;
-                }
-                aw[j] = pack_bf16x2(av[0], av[1]);
-                dw[j] = pack_bf16x2(dv[0], dv[1]);
+                const f32x2 yv = f2(y[2 * j], y[2 * j + 1]);
+                const f32x2 tv = f2(gt_tanh(y[2 * j]), gt_tanh(y[2 * j + 1]));
+                const f32x2 opt = f2add(tv, one), omt = f2fma(tv, mone, one);
+                const f32x2 hopt = f2mul(half, opt);
+                const f32x2 s1 = f2mul(hopt, f2fma(yv, omt, one));
+                const f32x2 s2 = f2mul(f2mul(hopt, omt), f2fma(f2mul(yv, tv), mone, one));
+                const f32x2 adh2 = f2(adh[2 * j], adh[2 * j + 1]);
+                const f32x2 dz = f2(2.f * dy[2 * j], 2.f * dy[2 * j + 1]);
+                float a0, a1, d0, d1;
+                f2split(f2fma(f2(ah[2 * j], ah[2 * j + 1]), s1, f2mul(f2mul(adh2, s2), dz)), a0, a1);  // az1
+                f2split(f2mul(adh2, s1), d0, d1);                                                      // adz1
+                aw[j] = pack_bf16x2(a0, a1);
+                dw[j] = pack_bf16x2(d0, d1);
             }
             st_row8(sh.a1, p, c0, A1_COLS, make_uint4(aw[0], aw[1], aw[2], aw[3]));
             st_row8(sh.a1, p, c0 + 8, A1_COLS, make_uint4(aw[4], aw[5], aw[6], aw[7]));
@@ -365,6 +401,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_mlp_grad(DevSys<T> s, int cur
             break;
         }
         acc = true;
+        buf ^= 1;
     }
     if (!ok && sh.stop == 0) {
         // a commit never arrived: record it, give the MMAs in flight one more
