@@ -394,6 +394,34 @@ int espp_rdf_counts(espp_h h, int32_t replica, double rmax, int32_t nbins, int64
 int espp_checkpoint_save(espp_h h, const char* path);
 int espp_checkpoint_load(espp_h h, const char* path);
 
+/* Paper "New features": H5MD output and the checkpoint of the random number
+ * generator.  espp_h5md_write writes the handle's state as an H5MD 1.1 file
+ * (HDF5 format; no HDF5 library is used): /h5md (version 1.1, author,
+ * creator), per replica /particles/<g>/{box (dimension 3, periodic
+ * boundary, edges), position, velocity, image, force (one frame each: step,
+ * time, value [1][n][3]), species [n]}, /connectivity/<g>/bonds [n_bonds][2] and
+ * /parameters/espp (step, simulated time, precision, Lees-Edwards setting,
+ * the replicas' Philox seeds [R]); <g> = "all" for a single system,
+ * "replica_<r>" for a batch.  Particle data are in id order, positions
+ * wrapped into the box with their image counters; force is the total force
+ * the next velocity-Verlet step starts from (thermostat terms included),
+ * written once the handle has one (after an integrate call).  Because the Philox noise
+ * is a function of (seed, id, step), the seeds and the step restore the
+ * random stream.  espp_h5md_read loads such a file into a handle of the same
+ * replicas, sizes, boxes, types and Lees-Edwards setting (ESPP_ERR_ARG
+ * otherwise, the handle unchanged): it takes the file's Philox seeds, step
+ * and simulated time, then the positions, velocities and images as
+ * espp_set_state does, and the force where the file holds one; the
+ * interactions, thermostat and list are those of the loading handle.  A run resumed from it continues the same trajectory up to
+ * rounding (the binary espp_checkpoint_* files resume bit for bit).  It reads
+ * the HDF5 subset the writer produces (version-2 superblock and object
+ * headers, compact groups, contiguous datasets) and refuses other files with
+ * ESPP_ERR_IO, as it does a file that cannot be opened or fails a checksum.
+ * Errors: ESPP_ERR_ARG (null path, a mismatched handle), ESPP_ERR_STATE
+ * (write without a state), ESPP_ERR_IO. */
+int espp_h5md_write(espp_h h, const char* path);
+int espp_h5md_read(espp_h h, const char* path);
+
 /* ---- diagnostics ----------------------------------------------------------- */
 const char* espp_last_error(espp_h h);
 uint32_t espp_error_word(espp_h h);

@@ -15,7 +15,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libespp_gb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = ["k_rebuild.cu", "k_step_f32.cu", "k_step_f64.cu", "k_cells.cu", "k_mlp.cu", "k_train.cu", "k_io.cu", "runtime.cu", "noalloc.cu",
-         "hilbert.cpp"]
+         "hilbert.cpp", "h5md.cpp", "h5md_layout.cpp"]
 
 
 def nvcc():

@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(TILE) k_set_state(DevSys<T> s, const double* _
 template <class T>
 __global__ void __launch_bounds__(TILE) k_get_state(DevSys<T> s, double* __restrict__ x,
                                                     double* __restrict__ v, int* __restrict__ img,
-                                                    int cur) {
+                                                    double* __restrict__ f, int cur) {
     for (int t = blockIdx.x; t < s.ntiles; t += gridDim.x) {
         const Tile tl = s.tiles[t];
         if ((int)threadIdx.x >= tl.count) continue;
@@ -117,6 +117,25 @@ __global__ void __launch_bounds__(TILE) k_get_state(DevSys<T> s, double* __restr
             img[3 * gid + 1] = im.y + sh[1];
             img[3 * gid + 2] = im.z + sh[2];
         }
+        if (f) {
+            const V4<T> fi = s.frc[i];
+            f[3 * gid] = fi.x;
+            f[3 * gid + 1] = fi.y;
+            f[3 * gid + 2] = fi.z;
+        }
+    }
+}
+
+// The stored total force of the current step (id-ordered doubles) back into
+// its slots.
+template <class T>
+__global__ void __launch_bounds__(TILE) k_set_force(DevSys<T> s, const double* __restrict__ f) {
+    for (int t = blockIdx.x; t < s.ntiles; t += gridDim.x) {
+        const Tile tl = s.tiles[t];
+        if ((int)threadIdx.x >= tl.count) continue;
+        const int gid = tl.start + threadIdx.x;
+        const int i = s.slot_of_id[gid];
+        s.frc[i] = mk4<T>((T)f[3 * (size_t)gid], (T)f[3 * (size_t)gid + 1], (T)f[3 * (size_t)gid + 2], T(0));
     }
 }
 
@@ -303,9 +322,14 @@ void Launch<T>::set_state(const DevSys<T>& s, const double* x, const double* v, 
 }
 
 template <class T>
-void Launch<T>::get_state(const DevSys<T>& s, double* x, double* v, int* img, int cur,
+void Launch<T>::get_state(const DevSys<T>& s, double* x, double* v, int* img, double* f, int cur,
                           cudaStream_t st) {
-    k_get_state<T><<<s.ntiles, TILE, 0, st>>>(s, x, v, img, cur);
+    k_get_state<T><<<s.ntiles, TILE, 0, st>>>(s, x, v, img, f, cur);
+}
+
+template <class T>
+void Launch<T>::set_force(const DevSys<T>& s, const double* f, cudaStream_t st) {
+    k_set_force<T><<<s.ntiles, TILE, 0, st>>>(s, f);
 }
 
 template <class T>
@@ -346,8 +370,10 @@ void launch_noise(unsigned long long seed, long long step, long long n, double* 
 
 template void Launch<float>::set_state(const DevSys<float>&, const double*, const double*, const int*, const int*, int, cudaStream_t);
 template void Launch<double>::set_state(const DevSys<double>&, const double*, const double*, const int*, const int*, int, cudaStream_t);
-template void Launch<float>::get_state(const DevSys<float>&, double*, double*, int*, int, cudaStream_t);
-template void Launch<double>::get_state(const DevSys<double>&, double*, double*, int*, int, cudaStream_t);
+template void Launch<float>::get_state(const DevSys<float>&, double*, double*, int*, double*, int, cudaStream_t);
+template void Launch<double>::get_state(const DevSys<double>&, double*, double*, int*, double*, int, cudaStream_t);
+template void Launch<float>::set_force(const DevSys<float>&, const double*, cudaStream_t);
+template void Launch<double>::set_force(const DevSys<double>&, const double*, cudaStream_t);
 template void Launch<float>::reduce_obs(const DevSys<float>&, double*, cudaStream_t);
 template void Launch<double>::reduce_obs(const DevSys<double>&, double*, cudaStream_t);
 template void Launch<float>::rg2(const DevSys<float>&, int, const int*, const int*, const int*, int, double*, cudaStream_t);

@@ -267,8 +267,10 @@ template <class T> struct Launch {
     // state I/O (id-ordered double buffers on the device)
     static void set_state(const DevSys<T>& s, const double* x, const double* v, const int* img,
                           const int* types_by_gid, int cur, cudaStream_t st);
-    static void get_state(const DevSys<T>& s, double* x, double* v, int* img, int cur,
+    // f: the stored total force of the current step (thermostat terms included)
+    static void get_state(const DevSys<T>& s, double* x, double* v, int* img, double* f, int cur,
                           cudaStream_t st);
+    static void set_force(const DevSys<T>& s, const double* f, cudaStream_t st);
     static void reduce_obs(const DevSys<T>& s, double* out_R_NPART, cudaStream_t st);
     static void rg2(const DevSys<T>& s, int cur, const int* mol_members, const int* mol_off,
                     const int* mol_rep, int nmol, double* mol_rg2, cudaStream_t st);

@@ -15,6 +15,7 @@
 #include <tuple>
 #include <vector>
 
+#include "h5md.h"
 #include "kernels.cuh"
 
 namespace espp {
@@ -74,6 +75,8 @@ struct SystemBase {
     virtual int set_force_method(int method) = 0;
     virtual int tune_force_method(int nsteps, double dt, double gamma, double kT, double* ms, int* chosen) = 0;
     virtual int set_step_shape(int shape) = 0;
+    virtual int h5md_write(const char* path) = 0;
+    virtual int h5md_read(const char* path) = 0;
     virtual int tune_step_shape(int nsteps, double dt, double gamma, double kT, double* ms, int* chosen) = 0;
 };
 
@@ -606,14 +609,15 @@ class System : public SystemBase {
         if (!state_set) return fail(ESPP_ERR_STATE, "no state set");
         const size_t n3 = 3 * (size_t)N;
         if (where == ESPP_DEVICE) {
-            Launch<T>::get_state(d, x, v, img, cur, st);
+            Launch<T>::get_state(d, x, v, img, nullptr, cur, st);
             launches++;
             CK(cudaGetLastError());
             CK(cudaStreamSynchronize(st));
             return ESPP_OK;
         }
         if (where != ESPP_HOST) return fail(ESPP_ERR_ARG, "where must be ESPP_HOST or ESPP_DEVICE");
-        Launch<T>::get_state(d, x ? d_io_x : nullptr, v ? d_io_v : nullptr, img ? d_io_img : nullptr, cur, st);
+        Launch<T>::get_state(d, x ? d_io_x : nullptr, v ? d_io_v : nullptr, img ? d_io_img : nullptr, nullptr, cur,
+                             st);
         launches++;
         CK(cudaGetLastError());
         if (x) CK(cudaMemcpyAsync(x, d_io_x, n3 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -776,7 +780,7 @@ class System : public SystemBase {
         CK(cudaMalloc(&fdev, 3 * (size_t)N * sizeof(double)));
         int rcode = compute_forces(fdev, ESPP_DEVICE);
         if (!rcode) {
-            Launch<T>::get_state(d, d_io_x, nullptr, d_io_img, cur, st);
+            Launch<T>::get_state(d, d_io_x, nullptr, d_io_img, nullptr, cur, st);
             launch_cg_map(d_io_x, d_io_img, fdev, N / bps, bps, box.data(), xs, fs, st);
             launches += 2;
             cudaError_t e = cudaStreamSynchronize(st);
@@ -1891,6 +1895,111 @@ class System : public SystemBase {
         return ESPP_OK;
     }
 
+    // ---- H5MD files ----------------------------------------------------------
+    int h5md_write(const char* path) override {
+        if (!path) return fail(ESPP_ERR_ARG, "path is required");
+        if (!state_set) return fail(ESPP_ERR_STATE, "no state set");
+        const size_t n3 = 3 * (size_t)N;
+        std::vector<double> x(n3), v(n3);
+        std::vector<int32_t> img(n3);
+        int rcode = get_state(x.data(), v.data(), img.data(), ESPP_HOST);
+        if (rcode) return rcode;
+        // the stored total force of this step, when there is one: velocity
+        // Verlet starts the next step from it (its Langevin friction was taken
+        // at the half-step velocity, which the file does not hold otherwise)
+        std::vector<double> f;
+        if (f_valid) {
+            f.resize(n3);
+            Launch<T>::get_state(d, nullptr, nullptr, nullptr, d_io_x, cur, st);
+            launches++;
+            CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(f.data(), d_io_x, n3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+        }
+        const Ctrl c = read_ctrl();
+        H5mdState hs;
+        hs.step = c.step;
+        hs.time = time_at(c.step);
+        hs.precision = sizeof(T) == 4 ? ESPP_FP32 : ESPP_FP64;
+        hs.lees_edwards = d.le_on;
+        hs.shear_rate = d.le_shear;
+        hs.reps.resize(R);
+        for (int r = 0; r < R; ++r) {
+            H5mdReplica& rp = hs.reps[r];
+            const int off = rep_poff[r], n = rep_n[r];
+            for (int k = 0; k < 3; ++k) rp.box[k] = box[3 * r + k];
+            rp.n = n;
+            rp.x.assign(x.begin() + 3 * (size_t)off, x.begin() + 3 * (size_t)(off + n));
+            rp.v.assign(v.begin() + 3 * (size_t)off, v.begin() + 3 * (size_t)(off + n));
+            rp.img.assign(img.begin() + 3 * (size_t)off, img.begin() + 3 * (size_t)(off + n));
+            if (f_valid) rp.f.assign(f.begin() + 3 * (size_t)off, f.begin() + 3 * (size_t)(off + n));
+            rp.species.assign(types_gid.begin() + off, types_gid.begin() + off + n);
+            for (int a = 0; a < n; ++a) {
+                const int2 b = bond_gid_h[off + a];
+                for (int o : {b.x, b.y})
+                    if (o > off + a) {
+                        rp.bonds.push_back(a);
+                        rp.bonds.push_back(o - off);
+                    }
+            }
+            rp.seed = seeds[r];
+        }
+        std::string err;
+        if (espp::h5md_write(path, hs, err)) return fail(ESPP_ERR_IO, "H5MD write: " + err);
+        return ESPP_OK;
+    }
+
+    int h5md_read(const char* path) override {
+        if (!path) return fail(ESPP_ERR_ARG, "path is required");
+        H5mdState hs;
+        std::string err;
+        if (espp::h5md_read(path, hs, err)) return fail(ESPP_ERR_IO, "H5MD read: " + err);
+        if ((int)hs.reps.size() != R) return fail(ESPP_ERR_ARG, "the file holds another number of replicas");
+        const size_t n3 = 3 * (size_t)N;
+        std::vector<double> x, v, f;
+        std::vector<int32_t> img;
+        x.reserve(n3);
+        v.reserve(n3);
+        img.reserve(n3);
+        const bool with_f = !hs.reps.empty() && !hs.reps[0].f.empty();
+        for (int r = 0; r < R; ++r) {
+            const H5mdReplica& rp = hs.reps[r];
+            if (rp.f.empty() == with_f) return fail(ESPP_ERR_IO, "H5MD read: a force element in some replicas only");
+            f.insert(f.end(), rp.f.begin(), rp.f.end());
+            if (rp.n != rep_n[r]) return fail(ESPP_ERR_ARG, "a replica of the file has another particle count");
+            for (int k = 0; k < 3; ++k)
+                if (rp.box[k] != box[3 * r + k]) return fail(ESPP_ERR_ARG, "a replica of the file has another box");
+            for (int a = 0; a < rep_n[r]; ++a)
+                if (rp.species[a] != types_gid[rep_poff[r] + a])
+                    return fail(ESPP_ERR_ARG, "the file's particle types differ from the handle's");
+            x.insert(x.end(), rp.x.begin(), rp.x.end());
+            v.insert(v.end(), rp.v.begin(), rp.v.end());
+            img.insert(img.end(), rp.img.begin(), rp.img.end());
+        }
+        if (hs.lees_edwards != d.le_on || (d.le_on && hs.shear_rate != d.le_shear))
+            return fail(ESPP_ERR_ARG, "the file's Lees-Edwards setting differs from the handle's");
+        // the Philox seeds, step and clock of the file, then the particles
+        // (wrapped under the clock of the saved step)
+        CK(cudaStreamSynchronize(st));
+        for (int r = 0; r < R; ++r) seeds[r] = hs.reps[r].seed;
+        int rcode = upload_geometry();
+        if (rcode) return rcode;
+        const long long step = hs.step;
+        CK(cudaMemcpyAsync(&d_ctrl->step, &step, sizeof(long long), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        if ((rcode = set_clock(hs.time, le_clk_h.dt, hs.step))) return rcode;
+        if ((rcode = set_state(x.data(), v.data(), img.data(), ESPP_HOST))) return rcode;
+        if (with_f) {
+            CK(cudaMemcpyAsync(d_io_x, f.data(), n3 * sizeof(double), cudaMemcpyHostToDevice, st));
+            Launch<T>::set_force(d, d_io_x, st);
+            launches++;
+            CK(cudaGetLastError());
+            CK(cudaStreamSynchronize(st));
+            f_valid = true;
+        }
+        return ESPP_OK;
+    }
+
     // ---- launch shape of the step kernel and the resort interval ----------
     int set_step_shape(int shape) override {
         if (shape < 0 || shape >= ESPP_STEP_SHAPES) return fail(ESPP_ERR_ARG, "unknown step shape");
@@ -2166,6 +2275,12 @@ int espp_tune_force_method(espp_h h, int32_t nsteps, double dt, double gamma, do
         if (chosen) *chosen = c;
         return rc;
     });
+}
+int espp_h5md_write(espp_h h, const char* path) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.h5md_write(path); });
+}
+int espp_h5md_read(espp_h h, const char* path) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.h5md_read(path); });
 }
 int espp_set_step_shape(espp_h h, int32_t shape) {
     return guarded(h, [&](espp::SystemBase& s) { return s.set_step_shape(shape); });

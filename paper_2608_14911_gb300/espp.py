@@ -68,6 +68,7 @@ EXPORTS = (
     "espp_cg_map", "espp_set_cell_subdivision", "espp_set_thermostat",
     "espp_set_lees_edwards", "espp_get_lees_edwards", "espp_set_force_method",
     "espp_tune_force_method", "espp_set_step_shape", "espp_tune_step_shape",
+    "espp_h5md_write", "espp_h5md_read",
 )
 NOALLOC_MAX_BINS = 4096
 NOALLOC_MAX_N = 200000
@@ -154,6 +155,8 @@ def lib(path: str = LIB_PATH):
         "espp_tune_force_method": ([vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp,
                                     ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "espp_set_step_shape": ([vp, ctypes.c_int32], ctypes.c_int),
+        "espp_h5md_write": ([vp, ctypes.c_char_p], ctypes.c_int),
+        "espp_h5md_read": ([vp, ctypes.c_char_p], ctypes.c_int),
         "espp_tune_step_shape": ([vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp,
                                   ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "espp_mlp_set_weights": ([vp, vp, i64], ctypes.c_int),
@@ -416,6 +419,13 @@ class System:
         c = np.zeros(nbins, dtype=np.int64)
         self._c(lib().espp_rdf_counts(self._h, replica, rmax, nbins, _ptr(c)[0]))
         return c
+
+    def h5md_write(self, path):
+        """The state as an H5MD file (see include/espp.h)."""
+        self._c(lib().espp_h5md_write(self._h, os.fspath(path).encode()))
+
+    def h5md_read(self, path):
+        self._c(lib().espp_h5md_read(self._h, os.fspath(path).encode()))
 
     def checkpoint_save(self, path):
         self._c(lib().espp_checkpoint_save(self._h, path.encode()))
