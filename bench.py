@@ -495,8 +495,9 @@ def run_ours(a):
                    "l2": "inputs larger than L2: per-step working set %.0f MB > %.0f MB L2, no flush"
                          % (ws_mb, L2_MB),
                    "rebuilds_in_timed_region": rebuilds,
-                   "step_shape": {"chosen": shape, "groups_per_batch": (1, 2, 1, 1)[shape],
-                                  "min_blocks_per_sm": (10, 8, 12, 8)[shape], "resort_interval": resort,
+                   "step_shape": {"chosen": shape, "groups_per_batch": espp.STEP_SHAPE_TABLE[shape][0],
+                                  "min_blocks_per_sm": espp.STEP_SHAPE_TABLE[shape][1],
+                                  "tiles_per_block": espp.STEP_SHAPE_TABLE[shape][2], "resort_interval": resort,
                                   "tuner_ms_per_step": {"shapes": shape_ms, "resort_250_500_1000": resort_ms}},
                    "mean_list_entries_per_particle": mean_entries / n, "max_list_entries": max_count,
                    "observables_after_run": {k: obs[k] for k in ("temperature", "mean_bond", "rg2", "pe_pair")},
@@ -642,6 +643,13 @@ def suite_lj4m(a, sync, peaks):
         s.set_state(cfg.x, v, cfg.img)
         s.build_neighbors(2.5, 0.3)
         s.integrate(100, 0.005, 1.0, 0.72)
+        tuned = None
+        if prec == espp.ESPP_FP32:
+            # the autotuner picks the step kernel's launch shape and the resort interval
+            shape_ms, resort_ms, (shape, resort) = s.tune_step_shape(200, 0.005, 1.0, 0.72)
+            tuned = {"chosen": shape, "shape": espp.STEP_SHAPE_TABLE[shape], "resort_interval": resort,
+                     "tuner_ms_per_step": {"shapes": shape_ms, "resort_250_500_1000": resort_ms}}
+            s.integrate(20, 0.005, 1.0, 0.72)
         rb0 = s.n_rebuilds
         ms = _timed(s, steps, 0.005, 1.0, 0.72, sync)
         key = "fp32" if prec == espp.ESPP_FP32 else "fp64"
@@ -656,6 +664,7 @@ def suite_lj4m(a, sync, peaks):
                                        "frac_of_measured_hbm": byt / (k_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
                                        "mean_list_entries": total / cfg.n,
                                        "rebuild_node_ms_per_step": rb_ms}
+            out[key]["step_shape"] = tuned
         s.close()
     out["fp32_speedup_vs_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
     return out
@@ -683,8 +692,10 @@ def suite_batched(a, sync):
     s.set_wca(1.0, 1.0)
     s.integrate(1000, 0.002, 1.0, 1.0)
     s.integrate(200, 0.005, 1.0, 1.0)
-    # the autotuner picks the force path's shape for this batch
+    # the autotuner picks the force path for this batch, then the step
+    # kernel's launch shape and the resort interval
     tuned_ms, shape = s.tune_force_method(100, 0.005, 1.0, 1.0)
+    shape_ms, resort_ms, (step_shape, resort) = s.tune_step_shape(200, 0.005, 1.0, 1.0)
     s.integrate(50, 0.005, 1.0, 1.0)
     rb0 = s.n_rebuilds
     l0 = s.kernel_launches
@@ -700,6 +711,9 @@ def suite_batched(a, sync):
            "force_shape": ("verlet_whole_cells", "verlet_half_cells", "cells")[shape],
            "tuner_ms_per_step": {"verlet_whole_cells": tuned_ms[0], "verlet_half_cells": tuned_ms[1],
                                  "cells": tuned_ms[2]},
+           "step_shape": {"chosen": step_shape, "shape": espp.STEP_SHAPE_TABLE[step_shape],
+                          "resort_interval": resort,
+                          "tuner_ms_per_step": {"shapes": shape_ms, "resort_250_500_1000": resort_ms}},
            "temperature_mean_over_replicas": float(temps.mean())}
     s.close()
     return out

@@ -304,11 +304,11 @@ int espp_tune_force_method(espp_h h, int32_t nsteps, double dt, double gamma, do
  * (the batching pattern's "tile and list shapes picked by an autotuner"; the
  * paper's "Performance optimizations" name data sorting).  Shapes of the
  * FP32 step kernel on the plain list path (one particle type, Lennard-Jones,
- * no Lees-Edwards or DPD): 0 = one int4 list group per batch and registers
- * fitted to 10 resident blocks of 128 threads per SM (the default), 1 = two
- * groups per batch, 8 blocks, 2 = one group, 12 blocks, 3 = one group, 8
- * blocks.  Every shape computes the same forces bit for bit; they differ in
- * speed only.  espp_set_step_shape selects one (ESPP_ERR_ARG outside
+ * no Lees-Edwards or DPD), as (int4 list groups per batch, resident blocks per
+ * SM the registers are fitted to, 128-particle tiles per block): 0 = (1, 10,
+ * 1) (the default), 1 = (2, 8, 1), 2 = (1, 12, 1), 3 = (1, 8, 1), 4 = (1, 5,
+ * 2), 5 = (1, 3, 3), 6 = (1, 2, 4), 7 = (1, 2, 5).  Every shape computes the
+ * same forces bit for bit; they differ in speed only.  espp_set_step_shape selects one (ESPP_ERR_ARG outside
  * [0, ESPP_STEP_SHAPES)).  espp_tune_step_shape times nsteps integrate steps
  * (dt, gamma, kT) from the current state with each shape, keeps the fastest,
  * then times max(nsteps, 1000) steps with each resort interval of 250, 500
@@ -316,7 +316,7 @@ int espp_tune_force_method(espp_h h, int32_t nsteps, double dt, double gamma, do
  * espp_tune_force_method does).  ms_per_step[ESPP_STEP_SHAPES + 3] (may be
  * NULL) receives the times (shapes, then intervals), chosen[2] (may be NULL)
  * the shape and the interval kept.  Synchronises. */
-#define ESPP_STEP_SHAPES 4
+#define ESPP_STEP_SHAPES 8
 int espp_set_step_shape(espp_h h, int32_t shape);
 int espp_tune_step_shape(espp_h h, int32_t nsteps, double dt, double gamma, double kT, double* ms_per_step,
                          int32_t* chosen);

@@ -21,13 +21,18 @@
 
 // Launch shapes of the FP32 step kernel on the plain list path, chosen at run
 // time by the autotuner (espp_tune_step_shape): int4 neighbour groups read per
-// batch and the minimum resident blocks per SM the register budget is fitted
-// to.  Shape 0 is the default.
+// batch, the minimum resident blocks per SM the register budget is fitted to,
+// and the tiles one block takes.  A block of several consecutive tiles holds
+// a larger compact piece of the Hilbert order, so more of its neighbours'
+// positions are shared in the SM's L1 (the halo of a piece shrinks relative
+// to its volume).  Shape 0 is the default.
 struct StepShape {
     int groups;  // list groups per batch
-    int minb;    // minimum resident blocks of TILE threads per SM
+    int minb;    // minimum resident blocks per SM
+    int tpb;     // tiles (of TILE particles) per block
 };
-constexpr StepShape STEP_SHAPES[ESPP_STEP_SHAPES] = {{1, 10}, {2, 8}, {1, 12}, {1, 8}};
+constexpr StepShape STEP_SHAPES[ESPP_STEP_SHAPES] = {{1, 10, 1}, {2, 8, 1}, {1, 12, 1}, {1, 8, 1},
+                                                     {1, 5, 2},  {1, 3, 3}, {1, 2, 4},  {1, 2, 5}};
 #ifndef ESPP_STEP_MINB32
 #define ESPP_STEP_MINB32 10
 #endif
@@ -192,10 +197,16 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // SH: launch shape (STEP_SHAPES) of the plain FP32 list path.
 template <class T, int MODE, bool ENERGY, bool FAST, bool DPD, bool LE, int SH = 0>
-__global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32_DPD
-                                                              : (SH == 0 ? ESPP_STEP_MINB32 : STEP_SHAPES[SH].minb))
-                                                       : 4)
+__global__ void __launch_bounds__(TILE * STEP_SHAPES[SH].tpb,
+                                  sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32_DPD
+                                                        : (SH == 0 ? ESPP_STEP_MINB32 : STEP_SHAPES[SH].minb))
+                                                 : 4)
     k_step(DevSys<T> s, int cur, double* __restrict__ f_out, unsigned long long next_cond) {
+    // TPB consecutive tiles per block; the block-wide energy reduction below
+    // is written for one
+    constexpr int TPB = STEP_SHAPES[SH].tpb;
+    static_assert(TPB == 1 || !ENERGY, "energy reductions take one tile per block");
+    const int lt = TPB > 1 ? (int)threadIdx.x % TILE : (int)threadIdx.x;  // index inside the tile
     Ctrl* c = s.ctrl;
     if (MODE != MODE_FORCES && c->abort) return;
     const long long step = c->step + (MODE >= MODE_STEP ? 1 : 0);
@@ -204,9 +215,9 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32
     const IntParams<T>* __restrict__ ip = s.ip;
     __shared__ double red[NPART][TILE / 32];
 
-    for (int t = blockIdx.x; t < s.ntiles; t += gridDim.x) {
+    for (int t = blockIdx.x * TPB + (TPB > 1 ? (int)threadIdx.x / TILE : 0); t < s.ntiles; t += gridDim.x * TPB) {
         const Tile tl = s.tiles[t];
-        const bool active = (int)threadIdx.x < tl.count;
+        const bool active = lt < tl.count;
         const RepGeom<T>& g = s.reps[tl.rep];
         double acc[NPART];
         if (ENERGY) {
@@ -239,7 +250,7 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32
             le.d = le.inv_Lx = le.vs = le.shear = T(0);
         }
         if (active) {
-            const int i = tl.start + threadIdx.x;
+            const int i = tl.start + lt;
             const T L0 = g.L[0], L1 = g.L[1], L2 = g.L[2];
             const T H0 = g.halfL[0], H1 = g.halfL[1], H2 = g.halfL[2];
             // independent loads first: own position, list count, bond slots,
@@ -450,7 +461,7 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (DPD ? ESPP_STEP_MINB32
                         }
                         if (!FAST && s.cells_mode) {
                             // list-free mode: every step is binned again
-                            if (threadIdx.x == 0) {
+                            if (lt == 0) {
                                 s.req[tl.rep] = 1;
                                 c->any_req = 1;
                                 __threadfence();
@@ -585,12 +596,23 @@ int Launch<T>::step(const DevSys<T>& s, int mode, bool energy, int cur, double* 
     // the plain FP32 list path of a step takes the tuned launch shape
     const int sh = (sizeof(T) == 4 && s.lj_fast && !s.le_on && !s.cells_mode && !s.mlp_on &&
                     (mode == MODE_STEP || mode == MODE_FINAL) && !dpd) ? s.step_shape : 0;
+#define ESPP_STEP_SHAPED(M, E, D, LE, K)                                                                   \
+    k_step<T, M, E, true, D, LE, K>                                                                        \
+        <<<(gr + STEP_SHAPES[K].tpb - 1) / STEP_SHAPES[K].tpb, TILE * STEP_SHAPES[K].tpb, 0, st>>>(s, cur, f_out, next_cond)
 #define ESPP_STEP_SH(M, E, D, LE)                                                                          \
     do {                                                                                                   \
         if constexpr (sizeof(T) == 4 && !(D) && !(LE) && ((M) == MODE_STEP || (M) == MODE_FINAL)) {        \
-            if (sh == 1) { k_step<T, M, E, true, D, LE, 1><<<gr, TILE, 0, st>>>(s, cur, f_out, next_cond); break; } \
-            if (sh == 2) { k_step<T, M, E, true, D, LE, 2><<<gr, TILE, 0, st>>>(s, cur, f_out, next_cond); break; } \
-            if (sh == 3) { k_step<T, M, E, true, D, LE, 3><<<gr, TILE, 0, st>>>(s, cur, f_out, next_cond); break; } \
+            switch (sh) {                                                                                  \
+                case 1: ESPP_STEP_SHAPED(M, E, D, LE, 1); break;                                           \
+                case 2: ESPP_STEP_SHAPED(M, E, D, LE, 2); break;                                           \
+                case 3: ESPP_STEP_SHAPED(M, E, D, LE, 3); break;                                           \
+                case 4: ESPP_STEP_SHAPED(M, E, D, LE, 4); break;                                           \
+                case 5: ESPP_STEP_SHAPED(M, E, D, LE, 5); break;                                           \
+                case 6: ESPP_STEP_SHAPED(M, E, D, LE, 6); break;                                           \
+                case 7: ESPP_STEP_SHAPED(M, E, D, LE, 7); break;                                           \
+                default: break;                                                                            \
+            }                                                                                              \
+            if (sh != 0) break;                                                                            \
         }                                                                                                  \
         k_step<T, M, E, true, D, LE><<<gr, TILE, 0, st>>>(s, cur, f_out, next_cond);                       \
     } while (0)
@@ -621,6 +643,7 @@ int Launch<T>::step(const DevSys<T>& s, int mode, bool energy, int cur, double* 
 #undef ESPP_STEP
 #undef ESPP_STEP_LE
 #undef ESPP_STEP_SH
+#undef ESPP_STEP_SHAPED
     return 1 + extra;
 }
 

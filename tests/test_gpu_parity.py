@@ -831,3 +831,47 @@ def test_two_masses_match_oracle(thermo):
     for k in ("ke", "temperature", "px", "pressure"):
         assert abs(o[k] - oo[k]) <= 1e-9 * max(1.0, abs(oo[k])), (k, o[k], oo[k])
     s.close()
+
+
+# ---------------------------------------------------------------------------
+# launch shapes of the step kernel (autotuned): the same trajectory bit for bit
+# ---------------------------------------------------------------------------
+def test_every_step_shape_gives_the_same_trajectory():
+    # 1000 + 1288 + 333 beads in three replicas: tile counts 8 + 11 + 3 = 22, so
+    # blocks of 2, 3, 4 and 5 tiles end on a partial block and mix replicas
+    sizes = [(20, 50, 11), (23, 56, 12), (9, 37, 13)]
+    cases_ = [kg_case(nc, nb, seed=sd, jitter=0.06) for nc, nb, sd in sizes]
+    reps = [dict(box=c.cfg.box, n=c.cfg.n, types=c.cfg.types, bonds=c.cfg.bonds, seed=70 + k)
+            for k, c in enumerate(cases_)]
+    out = []
+    for shape in range(espp.STEP_SHAPES):
+        b = espp.System(replicas=reps, precision=FP32)
+        b.set_wca()
+        b.set_fene()
+        b.set_state(np.concatenate([c.cfg.x for c in cases_]), np.concatenate([c.v for c in cases_]),
+                    np.concatenate([c.cfg.img for c in cases_]))
+        b.build_neighbors(WCA_RC, 0.4)
+        b.set_step_shape(shape)
+        b.integrate(150, 0.005, 1.0, 1.0)
+        out.append(b.get_state())
+        b.close()
+    for shape in range(1, espp.STEP_SHAPES):
+        for a, c in zip(out[0], out[shape]):
+            assert np.array_equal(a, c), shape
+
+
+def test_step_shape_tuner_restores_the_state():
+    case = kg_case()
+    s = case.system(FP32, seed=8)
+    ref = case.system(FP32, seed=8)
+    shape_ms, resort_ms, (shape, resort) = s.tune_step_shape(20, 0.005, 1.0, 1.0)
+    assert len(shape_ms) == espp.STEP_SHAPES and len(resort_ms) == 3
+    assert all(np.isfinite(shape_ms)) and 0 <= shape < espp.STEP_SHAPES and resort in (250, 500, 1000)
+    assert s.step == 0
+    s.set_step_shape(0)
+    s.integrate(50, 0.005, 1.0, 1.0)
+    ref.integrate(50, 0.005, 1.0, 1.0)
+    for a, b in zip(s.get_state(), ref.get_state()):
+        assert np.array_equal(a, b)
+    with pytest.raises(espp.EsppError):
+        s.set_step_shape(espp.STEP_SHAPES)
