@@ -380,8 +380,11 @@ __device__ __forceinline__ void verlet_le_plane(const DevSys<T>& s, const RepGeo
     }
 }
 
+// The full stencil of particle i: every row over the same x cells cx - W ..
+// cx + W (whole cells: the trimmed form below costs more in registers and
+// per-row work than the quarter of the candidates it saves).
 template <class T, int W, bool EXCL, bool LE>
-__device__ __forceinline__ void verlet_stencil(const DevSys<T>& s, const RepGeom<T>& g, int i,
+__device__ __forceinline__ void verlet_stencil_full(const DevSys<T>& s, const RepGeom<T>& g, int i,
                                                const V4<T>& xi, int2 ex, int& cnt, int4& grp,
                                                int4* __restrict__ out4) {
     constexpr int NR = 2 * W + 1;
@@ -465,8 +468,132 @@ __device__ __forceinline__ void verlet_stencil(const DevSys<T>& s, const RepGeom
     }
 }
 
+// The stencil of particle i, trimmed to the list sphere: a row of cells (one
+// y, one z) is searched only over the x cells that the sphere's chord at the
+// row's nearest point reaches, and rows the sphere misses are skipped.  The
+// nearest point of a row lies dmin_y, dmin_z away (cell units: the particle's
+// offset inside its own cell to the row's slab), the chord's half-width is
+// sqrt(rl^2 - dmin_y^2 - dmin_z^2).  Margins of 1e-4 cell widened every range
+// against rounding, so no pair inside rl is missed (the distance test itself
+// is unchanged); about a quarter (whole cells) to a third (half cells) of the
+// candidates of the full stencil go.  Used with sub-cells (W >= 2), where
+// rows are many and short; with whole cells the full stencil is faster.
 template <class T, int W, bool EXCL, bool LE>
-__global__ void __launch_bounds__(TILE) k_verlet(DevSys<T> s, int cur) {
+__device__ __forceinline__ void verlet_stencil_trim(const DevSys<T>& s, const RepGeom<T>& g, int i,
+                                               const V4<T>& xi, int2 ex, int& cnt, int4& grp,
+                                               int4* __restrict__ out4) {
+    constexpr int NR = 2 * W + 1;
+    const V4<T>* __restrict__ E = s.cell_ent;
+    const int* __restrict__ B = s.cell_beg;
+    const int nc0 = g.nc[0], nc1 = g.nc[1], nc2 = g.nc[2];
+    const int cx = cell_coord(xi.x, g.cells_per_len[0], nc0);
+    const int cy = cell_coord(xi.y, g.cells_per_len[1], nc1);
+    const int cz = cell_coord(xi.z, g.cells_per_len[2], nc2);
+    const T L0 = g.L[0], L1 = g.L[1], L2 = g.L[2];
+    const T rl2 = s.rlist2;
+    const int cap = s.cap;
+    const size_t stride = (size_t)s.stride;
+    // position in cell units, offsets inside the own cell, cell edges
+    const T ux = xi.x * g.cells_per_len[0];
+    const T fy = xi.y * g.cells_per_len[1] - (T)cy, fz = xi.z * g.cells_per_len[2] - (T)cz;
+    const T ey = L1 / (T)nc1, ez = L2 / (T)nc2;
+    const T margin = T(1e-4);
+    // Lees-Edwards: delta of this build reduced into [0, Lx)
+    const T le_d = LE ? (T)le_reduce(s.le_db[g_rep(s, g)], (double)L0) : T(0);
+    const T inv_L0 = LE ? T(1) / L0 : T(0);
+#pragma unroll 1
+    for (int dz = -W; dz <= W; ++dz) {
+        int az = cz + dz, czc = 0;
+        if (az < 0) { az += nc2; czc = 2; }
+        else if (az >= nc2) { az -= nc2; czc = 1; }
+        const T zo = (czc & 1) ? xi.z - L2 : xi.z, zL = (czc & 2) ? L2 : T(0);
+        if (LE && czc != 0) {
+            // a plane across a sheared face: the partners' image is displaced
+            // by nz delta along x; its x cells are found around x_i - nz delta
+            const int nz = czc == 1 ? 1 : -1;
+            const T nd = (T)nz * le_d;
+            T xs = xi.x - nd;
+            if (xs < T(0)) xs += L0;
+            if (xs >= L0) xs -= L0;
+            const int cxs = cell_coord(xs, g.cells_per_len[0], nc0);
+            verlet_le_plane<T, W, EXCL>(s, g, i, xi, ex, cxs, az, cy, nd, zo, zL, L0, inv_L0, czc, cnt, grp, out4);
+            continue;
+        }
+        T dmz = dz > 0 ? (T)dz - fz : (dz < 0 ? fz + (T)(-dz - 1) : T(0));
+        dmz = dmz > margin ? (dmz - margin) * ez : T(0);
+        const T dz2 = dmz * dmz;
+        int pb[NR][2], pe[NR][2], cyc[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int dy = r - W;
+            int ay = cy + dy, c = 0;
+            if (ay < 0) { ay += nc1; c = 2; }
+            else if (ay >= nc1) { ay -= nc1; c = 1; }
+            T dmy = dy > 0 ? (T)dy - fy : (dy < 0 ? fy + (T)(-dy - 1) : T(0));
+            dmy = dmy > margin ? (dmy - margin) * ey : T(0);
+            const T d2 = dmy * dmy + dz2;
+            // x cells of the chord, unwrapped, inside cx - W .. cx + W
+            int lo = cx + 1, hi = cx;  // empty when the sphere misses the row
+            if (d2 < rl2) {
+                const T wc = sqrt(rl2 - d2) * g.cells_per_len[0] + margin;
+                lo = max(cx - W, (int)floor(ux - wc));
+                hi = min(cx + W, (int)floor(ux + wc));
+            }
+            // the chord as up to two contiguous ranges of the row
+            int s0 = lo, h0 = hi, c0 = 0, s1 = 0, h1 = -1, c1 = 0;
+            if (lo < 0) {
+                if (hi < 0) {
+                    s0 = lo + nc0;
+                    h0 = hi + nc0;
+                } else {
+                    s0 = lo + nc0;
+                    h0 = nc0 - 1;
+                    s1 = 0;
+                    h1 = hi;
+                }
+                c0 = 2;
+            } else if (hi >= nc0) {
+                if (lo >= nc0) {
+                    s0 = lo - nc0;
+                    h0 = hi - nc0;
+                    c0 = 1;
+                } else {
+                    h0 = nc0 - 1;
+                    s1 = 0;
+                    h1 = hi - nc0;
+                    c1 = 1;
+                }
+            }
+            cyc[r] = c | (c0 << 2) | (c1 << 4);  // y code, then the x codes of both ranges
+            const int base = g.cell_off + (az * nc1 + ay) * nc0;
+            pb[r][0] = h0 >= s0 ? __ldg(B + base + s0) : 0;
+            pe[r][0] = h0 >= s0 ? __ldg(B + base + h0 + 1) : 0;
+            pb[r][1] = h1 >= s1 ? __ldg(B + base + s1) : 0;
+            pe[r][1] = h1 >= s1 ? __ldg(B + base + h1 + 1) : 0;
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int cyr = cyc[r] & 3;
+            const T yo = (cyr & 1) ? xi.y - L1 : xi.y, yL = (cyr & 2) ? L1 : T(0);
+#pragma unroll
+            for (int part = 0; part < 2; ++part) {
+                const int cxc = (cyc[r] >> (2 + 2 * part)) & 3;
+                const T xo = (cxc & 1) ? xi.x - L0 : xi.x, xL = (cxc & 2) ? L0 : T(0);
+                const int tag = (cxc | (cyr << 2) | (czc << 4)) << NBR_INDEX_BITS;
+                // a range that crosses no face (the common case) needs no shift
+                if (tag == 0)
+                    verlet_range<T, EXCL, false>(E, pb[r][part], pe[r][part], i, ex, xo, yo, zo, xL, yL, zL, rl2,
+                                                 tag, cap, stride, cnt, grp, out4);
+                else
+                    verlet_range<T, EXCL, true>(E, pb[r][part], pe[r][part], i, ex, xo, yo, zo, xL, yL, zL, rl2,
+                                                tag, cap, stride, cnt, grp, out4);
+            }
+        }
+    }
+}
+
+template <class T, int W, bool EXCL, bool LE>
+__global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (W > 1 ? 8 : (EXCL || LE ? 7 : 9)) : 5) k_verlet(DevSys<T> s, int cur) {
     if (s.ctrl->abort) return;
     for (int t = blockIdx.x; t < s.ntiles; t += gridDim.x) {
         const Tile tl = s.tiles[t];
@@ -484,7 +611,8 @@ __global__ void __launch_bounds__(TILE) k_verlet(DevSys<T> s, int cur) {
             const int2 ex = EXCL ? s.bond_slot[i] : make_int2(-1, -1);
             int4* __restrict__ out4 = reinterpret_cast<int4*>(s.nbr) + i;
             int4 grp = make_int4(-1, -1, -1, -1);
-            verlet_stencil<T, W, EXCL, LE>(s, g, i, xi, ex, cnt, grp, out4);
+            if constexpr (W == 1) verlet_stencil_full<T, W, EXCL, LE>(s, g, i, xi, ex, cnt, grp, out4);
+            else verlet_stencil_trim<T, W, EXCL, LE>(s, g, i, xi, ex, cnt, grp, out4);
             const int cap = s.cap;
             if ((cnt & 3) != 0 && cnt <= cap) out4[(size_t)(cnt >> 2) * s.stride] = grp;
             s.nbr_cnt[i] = cnt < cap ? cnt : cap;
