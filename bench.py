@@ -55,7 +55,13 @@ def parse():
     ap.add_argument("--cg-frames", type=int, default=2000)
     ap.add_argument("--cg-epochs", type=int, default=10)
     ap.add_argument("--cg-batch", type=int, default=16)
-    ap.add_argument("--ibi-iters", type=int, default=20)
+    ap.add_argument("--ibi-iters", type=int, default=40)
+    ap.add_argument("--ibi-damping", type=float, default=0.5)
+    ap.add_argument("--refine-damping", type=float, default=0.5)
+    ap.add_argument("--refine-iters", type=int, default=40,
+                    help="structure refinement iterations of the learned potential (0: force matching alone)")
+    ap.add_argument("--refine-frames", type=int, default=64)
+    ap.add_argument("--refine-epochs", type=int, default=10)
     ap.add_argument("--cg-eq", type=int, default=2000)
     ap.add_argument("--cg-snap", type=int, default=20)
     ap.add_argument("--cg-warm", type=int, default=1000)
@@ -853,6 +859,38 @@ def _ibi_update(U, g, g_t, counts_g, first_t, damping=0.3):
     return _core_extrapolate(U, first)
 
 
+def _correction_update(C, g, g_t, counts_g, first_t, damping=0.3):
+    """The structural correction of the learned potential, one iterative
+    Boltzmann inversion step: C += damping kT ln(g / g_t) on the bins both
+    samples hold well (smoothed over five bins); below them C is held at its
+    first reliable value (no force: the core stays the learned one)."""
+    first = max(first_t, _reliable_from(counts_g))
+    corr = np.zeros_like(C)
+    corr[first:] = damping * np.log(g[first:] / g_t[first:])
+    corr[first:] = _smooth(corr[first:], 5)
+    C = C + corr
+    C[:first] = C[first]
+    return C
+
+
+def _pair_forces_of_table(box, n, bonds, ut, ft, frames):
+    """Pair forces (1-2 bonded pairs excluded, no bond term) of a tabulated
+    potential on each frame, through the library."""
+    import torch
+    from paper_2608_14911_gb300 import espp
+    h = espp.System(box, n, None, bonds, precision=espp.ESPP_FP32, seed=5)
+    h.set_table_pair(RCM, ut, ft)
+    h.set_exclude_bonded(True)
+    out = torch.zeros_like(frames)
+    for k in range(frames.shape[0]):
+        h.set_state(frames[k])
+        if k == 0:
+            h.build_neighbors(RCM, SKIN_CG)
+        h.compute_forces(out[k])
+    h.close()
+    return out
+
+
 def suite_learned_cg(a, sync, out):
     """Learned CG: a fine KG melt of 2000 chains x 200 beads is mapped 4:1 onto
     100k sites every 200 steps; the CG bond table comes from Boltzmann
@@ -920,11 +958,11 @@ def suite_learned_cg(a, sync, out):
         ibi_l2.append(l2)
         if best is None or l2 < best[0]:
             best = (l2, ut.copy(), ft.copy(), U.copy())
-        U = _ibi_update(U, g, g_t, c * a.cg_snap, first_t)
+        U = _ibi_update(U, g, g_t, c * a.cg_snap, first_t, damping=a.ibi_damping)
     _, ut, ft, _ = best
     out["judge_table"] = {"method": "Boltzmann inversion of the mapped non-bonded g(r) (bins with >= 100 sampled "
                                     "pairs; the core continued linearly), then %d iterations of iterative Boltzmann "
-                                    "inversion (damping 0.3), the best kept" % a.ibi_iters,
+                                    "inversion (damping %.2f), the best kept" % (a.ibi_iters, a.ibi_damping),
                           "rdf_l2_per_iteration": ibi_l2, "max_abs_force_per_iteration": ibi_fmax,
                           "core_below_r": first_t * DR_G}
     probe.close()
@@ -1002,6 +1040,84 @@ def suite_learned_cg(a, sync, out):
                         "protocol": "100k CG sites from a held-out mapped frame, Langevin T 1, %d steps, then g(r) "
                                     "(non-bonded pairs, dr %.2f to %.1f) over %d snapshots 25 steps apart; target: "
                                     "the mapped g(r) of %d frames" % (a.cg_eq, DR_G, RCM, 2 * a.cg_snap, len(tframes))}
+    # ---- structure refinement of the learned potential ------------------------
+    # Force matching fixes the potential of mean force only as far as a pair
+    # potential can project the mapped forces; the structure it gives is off
+    # by the many-body part.  Each refinement iteration simulates the current
+    # MLP, turns its g(r) error into a pair correction (one iterative
+    # Boltzmann inversion step) and trains the MLP, from its current weights,
+    # to the forces of the current MLP plus the correction's pair forces on
+    # mapped training frames (targets free of the mapped forces' noise, so the
+    # fit takes the correction up exactly).  The best iteration (g(r) against
+    # the mapped one) is kept.
+    refined = trained
+    if a.refine_iters > 0:
+        out["stage"] = "structure refinement"
+        n_ref = min(n_train, a.refine_frames)
+        idx = torch.linspace(0, n_train - 1, n_ref).round().long().to(X.device)
+        Xr, Yr = X[idx].contiguous(), Y[idx].contiguous()
+        C = np.zeros(nbin)
+        w = trained
+        ref_l2, ref_loss, best_r = [], [], None
+        t0 = time.perf_counter()
+        for it in range(a.refine_iters):
+            h = _cg_handle(cfg.box, ns, cg_bonds, bond_tab, ("mlp", w), 300 + it)
+            cnt = _sampled_rdf(h, x_start, vmax, a.cg_eq, a.cg_snap, 25)
+            h.close()
+            gk = _gofr(cnt, ns, cfg.box)
+            l2 = _rdf_l2(gk, g_t)
+            ref_l2.append(l2)
+            if best_r is None or l2 < best_r[0]:
+                best_r = (l2, w, it)
+            if it == a.refine_iters - 1:
+                break
+            dC = _correction_update(np.zeros(nbin), gk, g_t, cnt * a.cg_snap, first_t, damping=a.refine_damping)
+            C = C + dC
+            uc, fc = _table_from_potential(dC, rt)
+            h = _cg_handle(cfg.box, ns, cg_bonds, bond_tab, ("mlp", w), 43)
+            Yc = _pair_forces_of_table(cfg.box, ns, cg_bonds, uc, fc, Xr)
+            fk = torch.zeros((ns, 3), dtype=torch.float64, device="cuda")
+            for k in range(n_ref):
+                h.set_state(Xr[k])
+                if k == 0:
+                    h.build_neighbors(RCM, SKIN_CG)
+                h.compute_forces(fk)
+                Yc[k] += fk
+            lh = h.mlp_train(Xr, Yc, batch_frames=a.cg_batch, epochs=a.refine_epochs, lr=1e-3, seed=5 + it)
+            ref_loss.append(float(lh[-1]))
+            w = h.mlp_weights()
+            h.close()
+        refined = best_r[1]
+        out["refinement"] = {"iterations": a.refine_iters, "frames": n_ref, "epochs_per_iteration": a.refine_epochs,
+                             "rdf_l2_per_iteration": ref_l2, "fine_tune_loss_per_iteration": ref_loss,
+                             "kept_iteration": best_r[2], "wall_s": time.perf_counter() - t0,
+                             "correction_max_abs": float(np.abs(C).max()),
+                             "method": "iteration k: g(r) of the current MLP (100k sites, %d steps, %d snapshots); "
+                                       "correction dC = %.2f kT ln(g / g_mapped) (IBI step on the well-sampled "
+                                       "bins); target forces on %d mapped training frames = the current MLP's "
+                                       "forces + dC's pair forces; %d epochs of force matching on them from the "
+                                       "current weights (Adam, lr 1e-3)" % (a.cg_eq, a.cg_snap, a.refine_damping,
+                                                                          n_ref, a.refine_epochs)}
+        # held-out forces and structure of the refined model
+        h = _cg_handle(cfg.box, ns, cg_bonds, bond_tab, ("mlp", refined), 44)
+        se = den = 0.0
+        fq = torch.zeros((ns, 3), dtype=torch.float64, device="cuda")
+        for q in range(n_hold):
+            h.set_state(X[n_train + q])
+            if q == 0:
+                h.build_neighbors(RCM, SKIN_CG)
+            h.compute_forces(fq)
+            yq = Y[n_train + q]
+            se += float(((fq - yq) ** 2).sum())
+            den += float((yq ** 2).sum())
+        h.close()
+        out["training"]["held_out"]["mlp_refined"] = {"loss": se / (n_hold * ns),
+                                                      "force_rel_rms": float(np.sqrt(se / den))}
+        h = _cg_handle(cfg.box, ns, cg_bonds, bond_tab, ("mlp", refined), 61)
+        g_ref = _gofr(_sampled_rdf(h, x_start, vmax, a.cg_eq, 2 * a.cg_snap, 25), ns, cfg.box)
+        h.close()
+        out["structure"]["rdf_l2_mlp_refined_vs_mapped"] = _rdf_l2(g_ref, g_t)
+        out["structure"]["rdf_l2_mlp_refined_vs_table"] = _rdf_l2(g_ref, gs["judge_table"])
     # ---- 4M CG sites: MLP on tensor cores vs the judge table -------------------
     out["stage"] = "4M CG melt"
     cg = inputs.kg_lattice(16000, 250, density=0.2125, seed=44, jitter=0.1)
@@ -1012,7 +1128,7 @@ def suite_learned_cg(a, sync, out):
         out["stage"] = "4M CG melt, " + mode
         s = espp.System(cg.box, cg.n, None, cg.bonds, precision=espp.ESPP_FP32, seed=45)
         if mode == "mlp":
-            s.set_mlp(RCM, trained)
+            s.set_mlp(RCM, refined)
         else:
             s.set_table_pair(RCM, ut, ft)
         s.set_table_bond(*bond_tab[:3])

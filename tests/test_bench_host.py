@@ -61,3 +61,22 @@ def test_traffic_record_holds_only_for_its_sources(tmp_path, monkeypatch):
     assert bench.read_traffic_record() is None
     (prof / "step_kernel_traffic.txt").unlink()
     assert bench.read_traffic_record() is None
+
+
+def test_structure_correction_is_an_ibi_step_that_keeps_the_core():
+    np = pytest.importorskip("numpy")
+    n = 175
+    g_t = np.ones(n)
+    g = np.ones(n)
+    g[60:80] = 1.2           # too many pairs there: the correction must rise
+    g[100:120] = 0.8         # too few: it must fall
+    counts = np.full(n, 1e4)
+    counts[:20] = 0          # an unsampled core
+    C = bench._correction_update(np.zeros(n), g, g_t, counts, first_t=10)
+    assert np.all(C[:20] == C[20])                     # held below the first reliable bin
+    assert C[70] == pytest.approx(0.3 * np.log(1.2), rel=1e-12)
+    assert C[110] == pytest.approx(0.3 * np.log(0.8), rel=1e-12)
+    assert np.all(np.abs(C[30:50]) < 1e-15)            # no error, no correction
+    # corrections accumulate over iterations
+    C2 = bench._correction_update(C, g, g_t, counts, first_t=10)
+    assert C2[70] == pytest.approx(2 * C[70], rel=1e-12)
