@@ -272,19 +272,26 @@ __global__ void __launch_bounds__(TILE) k_mlp_stage(DevSys<T> s, int cur) {
 }
 
 // ---- dense pair tiles on the 5th-generation tensor cores -------------------------
-// CTA of 128 threads, one pair per thread and tensor-memory lane.  Per tile:
-//   features   each thread writes its pair's phi (row of A0) and dphi/dr
-//              (row of A1) as BF16, plus a constant-1 column that carries the
-//              (halved) first-layer bias through the MMA
+// CTA of 256 threads, two per pair: pair (row) p of a 128-pair tile belongs to
+// tensor-memory lane p, read by warps p / 32 and 4 + p / 32; the first half
+// of the CTA takes columns 0..31 of every 64-column block, the second half
+// columns 32..63 (tensor memory caps the tiles in flight at four per SM, so
+// the second thread per pair is what fills the SM with warps).  Per tile:
+//   features   each half writes 16 of its pair's 32 phi (row of A0) and
+//              dphi/dr (row of A1) as BF16; the first half adds a constant-1
+//              column that carries the (halved) first-layer bias through the MMA
 //   layer 1    one thread issues tcgen05.mma: D[0:64) = A0 W1^T / 2 and
 //              D[64:128) = A1 W1^T / 2 (M 128, N 64, K 48), commit to an mbarrier
-//   epilogue   each thread reads its lane of D (y, dy), writes h = y(1+t) and
-//              dh = (1+t)(1+y(1-t)) dy (t = tanh y) as BF16 rows of A0/A1 (K 64)
+//   epilogue   each thread reads its 32 columns of its lane of D (y, dy), writes
+//              h = y(1+t) and dh = (1+t)(1+y(1-t)) dy (t = tanh y) as BF16 into
+//              the rows of A0/A1 (K 64)
 //   layer 2    D[0:64) = A0 W2^T / 2, D[64:128) = A1 W2^T / 2
-//   output     y += b2 / 2; du/dr = w3 . ((1+t)(1+y(1-t)) dy), u = w3 . y(1+t) + b3; the
+//   output     y += b2 / 2; du/dr = w3 . ((1+t)(1+y(1-t)) dy), u = w3 . y(1+t) + b3,
+//              each half over its 32 units, summed through shared memory; the
 //              force factor -du/dr / r goes to both entries of the pair
 // The weights are staged once per CTA; the CTA walks tiles with a grid stride.
 constexpr int TC_M = 128;
+constexpr int TC_THREADS = 2 * TC_M;  // two threads per pair
 constexpr int TC_N = MLP_H;           // 64 hidden units
 constexpr int TC_K1 = 48;             // 32 features, bias column, zero padding
 constexpr int TC_K2 = MLP_H;          // 64 units (the second-layer bias is added after the MMA)
@@ -298,6 +305,7 @@ struct __align__(128) TcShared {
     __nv_bfloat16 w2[TC_N * TC_K2];      // B operand of layer 2
     __align__(16) float w3[TC_N];
     __align__(16) float b2h[TC_N];        // halved second-layer bias
+    __align__(8) float2 part[TC_M];       // second half's (u, du/dr) partial sums
     uint64_t mbar;
     uint32_t tmem;
     int stop;
@@ -308,24 +316,25 @@ __device__ __forceinline__ void st_row16(__nv_bfloat16* base, int row, int k, in
 }
 
 template <bool ENERGY>
-__global__ void __launch_bounds__(TC_M, TC_CTAS_PER_SM) k_mlp_tc(DevSys<float> s) {
+__global__ void __launch_bounds__(TC_THREADS, TC_CTAS_PER_SM) k_mlp_tc(DevSys<float> s) {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     TcShared& sh = *reinterpret_cast<TcShared*>(tc_smem);
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int row = tid & (TC_M - 1), half = tid >> 7;
     const MlpWeights* __restrict__ W = s.mlp;
     // B operands: halved weights, halved bias in the constant column
-    for (int e = tid; e < TC_N * TC_K1; e += TC_M) {
+    for (int e = tid; e < TC_N * TC_K1; e += TC_THREADS) {
         const int n = e / TC_K1, k = e % TC_K1;
         const float v = k < MLP_NB ? __bfloat162float(W->W1[n * MLP_NB + k]) : (k == MLP_NB ? W->b1[n] : 0.f);
         *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<char*>(sh.w1) + tc::core_offset(n, k, TC_K1)) =
             __float2bfloat16(0.5f * v);
     }
-    for (int e = tid; e < TC_N * TC_K2; e += TC_M) {
+    for (int e = tid; e < TC_N * TC_K2; e += TC_THREADS) {
         const int n = e / TC_K2, k = e % TC_K2;
         *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<char*>(sh.w2) + tc::core_offset(n, k, TC_K2)) =
             __float2bfloat16(0.5f * __bfloat162float(W->W2[n * MLP_H + k]));
     }
-    for (int e = tid; e < TC_N; e += TC_M) {
+    for (int e = tid; e < TC_N; e += TC_THREADS) {
         sh.w3[e] = W->w3[e];
         sh.b2h[e] = 0.5f * W->b2[e];
     }
@@ -339,10 +348,11 @@ __global__ void __launch_bounds__(TC_M, TC_CTAS_PER_SM) k_mlp_tc(DevSys<float> s
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = sh.tmem;
-    const uint32_t lanes = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's 32 lanes
+    const uint32_t lanes = tmem + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's 32 lanes
+    const int c0 = 32 * half;                                           // this half's columns
     const float rc = W->rc, b3 = W->b3;
     const float wid = rc / (MLP_NB - 1);
-    const float inv2w2 = 0.5f / (wid * wid), invw2 = 1.0f / (wid * wid);
+    const float invw2 = 1.0f / (wid * wid), inv_w = 1.0f / wid;
     const float pirc = 3.14159265358979f / rc;
     const int np = min(*s.mlp_npairs, s.mlp_pairs_cap);
     const int ntl = (np + TC_M - 1) / TC_M;
@@ -357,7 +367,7 @@ __global__ void __launch_bounds__(TC_M, TC_CTAS_PER_SM) k_mlp_tc(DevSys<float> s
     const bool fault = s.tc_fault != 0;
     const int wait_limit = fault ? (1 << 12) : TC_WAIT;
     for (int tile = blockIdx.x; ok && tile < ntl; tile += gridDim.x) {
-        const int p = tile * TC_M + tid;
+        const int p = tile * TC_M + row;
         const bool valid = p < np;
         const int4 rec = valid ? s.mlp_pairs[p] : make_int4(__float_as_int(rc), 0, 0, 0);
         const float r = __int_as_float(rec.x);
@@ -366,29 +376,47 @@ __global__ void __launch_bounds__(TC_M, TC_CTAS_PER_SM) k_mlp_tc(DevSys<float> s
             __nv_bfloat16* A1 = A0 + TC_M * TC_K1;
             const float fc = 0.5f * (__cosf(pirc * r) + 1.f);
             const float dfc = -0.5f * pirc * __sinf(pirc * r);
+            // g_k = exp(-(t - k)^2 / 2), t = r / w, by the product recurrence
+            // g_{k+2} = g_k exp(2 (t - k) - 2) (two exponentials per block of
+            // eight bases instead of eight); dphi_k/dr = g_k (A + k B) with
+            // A = dfc - r fc / w^2, B = fc / w.  Pairs of bases in packed FP32x2.
+            const float t = r * inv_w;
+            const float B = fc * inv_w;
+            const f32x2 fc2 = f2(fc, fc);
+            const f32x2 twoB = f2(2.f * B, 2.f * B);
+            const float A = dfc - r * invw2 * fc;
+            const f32x2 em4 = f2(0.018315638888734179f, 0.018315638888734179f);  // e^-4
 #pragma unroll
-            for (int g = 0; g < MLP_NB / 8; ++g) {
+            for (int gg = 0; gg < 2; ++gg) {
+                const int g = 2 * half + gg;  // block of eight bases
                 unsigned int ph[4], dp[4];
+                const float u = t - (float)(8 * g);
+                const float g0 = __expf(-0.5f * u * u);
+                const float e1 = __expf(u - 0.5f);                  // g_{k+1} / g_k at k = 8g
+                const float R0 = e1 * e1 * 0.36787944117144233f;    // g_{k+2} / g_k
+                f32x2 gv = f2(g0, g0 * e1);
+                f32x2 rv = f2(R0, R0 * 0.1353352832366127f);        // (g_{k+2}/g_k, g_{k+3}/g_{k+1})
+                f32x2 cv = f2(A + (float)(8 * g) * B, A + (float)(8 * g + 1) * B);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    float v[2], dv[2];
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const float d = r - wid * (float)(8 * g + 2 * q + h);
-                        const float gk = __expf(-d * d * inv2w2);
-                        v[h] = gk * fc;
-                        dv[h] = gk * (dfc - d * invw2 * fc);
-                    }
-                    ph[q] = pack_bf16x2(v[0], v[1]);
-                    dp[q] = pack_bf16x2(dv[0], dv[1]);
+                    float v0, v1, d0, d1;
+                    f2split(f2mul(gv, fc2), v0, v1);
+                    f2split(f2mul(gv, cv), d0, d1);
+                    ph[q] = pack_bf16x2(v0, v1);
+                    dp[q] = pack_bf16x2(d0, d1);
+                    gv = f2mul(gv, rv);
+                    rv = f2mul(rv, em4);
+                    cv = f2add(cv, twoB);
                 }
-                st_row16(A0, tid, 8 * g, TC_K1, make_uint4(ph[0], ph[1], ph[2], ph[3]));
-                st_row16(A1, tid, 8 * g, TC_K1, make_uint4(dp[0], dp[1], dp[2], dp[3]));
+                st_row16(A0, row, 8 * g, TC_K1, make_uint4(ph[0], ph[1], ph[2], ph[3]));
+                st_row16(A1, row, 8 * g, TC_K1, make_uint4(dp[0], dp[1], dp[2], dp[3]));
             }
-            st_row16(A0, tid, 32, TC_K1, make_uint4(pack_bf16x2(1.f, 0.f), 0u, 0u, 0u));
-            st_row16(A0, tid, 40, TC_K1, make_uint4(0u, 0u, 0u, 0u));
-            st_row16(A1, tid, 32, TC_K1, make_uint4(0u, 0u, 0u, 0u));
-            st_row16(A1, tid, 40, TC_K1, make_uint4(0u, 0u, 0u, 0u));
+            if (half == 0) {
+                st_row16(A0, row, 32, TC_K1, make_uint4(pack_bf16x2(1.f, 0.f), 0u, 0u, 0u));
+                st_row16(A0, row, 40, TC_K1, make_uint4(0u, 0u, 0u, 0u));
+                st_row16(A1, row, 32, TC_K1, make_uint4(0u, 0u, 0u, 0u));
+                st_row16(A1, row, 40, TC_K1, make_uint4(0u, 0u, 0u, 0u));
+            }
         }
         tc::fence_async_smem();
         tc::fence_before_sync();
@@ -415,12 +443,12 @@ __global__ void __launch_bounds__(TC_M, TC_CTAS_PER_SM) k_mlp_tc(DevSys<float> s
         {
             __nv_bfloat16* A1 = A0 + TC_M * TC_K2;
 #pragma unroll
-            for (int c = 0; c < TC_N; c += 16) {
-                float y[16], dy[16];
-                tc::tmem_ld16x2(lanes + c, lanes + 64 + c, y, dy);
-                unsigned int hw[8], dw[8];
+            for (int c = c0; c < c0 + 32; c += 8) {
+                float y[8], dy[8];
+                tc::tmem_ld8x2(lanes + c, lanes + 64 + c, y, dy);
+                unsigned int hw[4], dw[4];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
+                for (int j = 0; j < 4; ++j) {
                     const f32x2 yv = f2(y[2 * j], y[2 * j + 1]);
                     const f32x2 tv = f2(tanh_hw(y[2 * j]), tanh_hw(y[2 * j + 1]));
                     const f32x2 hv = f2fma(yv, tv, yv);  // y (1 + t)
@@ -431,10 +459,8 @@ __global__ void __launch_bounds__(TC_M, TC_CTAS_PER_SM) k_mlp_tc(DevSys<float> s
                     hw[j] = pack_bf16x2(h0, h1);
                     dw[j] = pack_bf16x2(d0, d1);
                 }
-                st_row16(A0, tid, c, TC_K2, make_uint4(hw[0], hw[1], hw[2], hw[3]));
-                st_row16(A0, tid, c + 8, TC_K2, make_uint4(hw[4], hw[5], hw[6], hw[7]));
-                st_row16(A1, tid, c, TC_K2, make_uint4(dw[0], dw[1], dw[2], dw[3]));
-                st_row16(A1, tid, c + 8, TC_K2, make_uint4(dw[4], dw[5], dw[6], dw[7]));
+                st_row16(A0, row, c, TC_K2, make_uint4(hw[0], hw[1], hw[2], hw[3]));
+                st_row16(A1, row, c, TC_K2, make_uint4(dw[0], dw[1], dw[2], dw[3]));
             }
         }
         tc::fence_async_smem();
@@ -458,14 +484,14 @@ __global__ void __launch_bounds__(TC_M, TC_CTAS_PER_SM) k_mlp_tc(DevSys<float> s
         }
         parity ^= 1u;
         tc::fence_after_sync();
-        // ---- output layer ----------------------------------------------------------
+        // ---- output layer: this half's 32 units --------------------------------------
         f32x2 u2 = f2(0.f, 0.f), du2 = f2(0.f, 0.f);
 #pragma unroll
-        for (int c = 0; c < TC_N; c += 16) {
-            float y[16], dy[16];
-            tc::tmem_ld16x2(lanes + c, lanes + 64 + c, y, dy);
+        for (int c = c0; c < c0 + 32; c += 8) {
+            float y[8], dy[8];
+            tc::tmem_ld8x2(lanes + c, lanes + 64 + c, y, dy);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
+            for (int j = 0; j < 4; ++j) {
                 const float2 bb = *reinterpret_cast<const float2*>(sh.b2h + c + 2 * j);
                 const float2 ww = *reinterpret_cast<const float2*>(sh.w3 + c + 2 * j);
                 const f32x2 yv = f2add(f2(y[2 * j], y[2 * j + 1]), f2(bb.x, bb.y));
@@ -485,19 +511,21 @@ __global__ void __launch_bounds__(TC_M, TC_CTAS_PER_SM) k_mlp_tc(DevSys<float> s
             f2split(u2, a, b);
             u = a + b;
         }
-        if (valid) {
-            const float sv = -du / r;
-            pf[rec.y] = sv;
-            pf[rec.z] = sv;
-            if (ENERGY) {
-                pu[rec.y] = u + b3;
-                pu[rec.z] = u + b3;
-            }
-        }
+        if (half == 1) sh.part[row] = make_float2(u, du);
         // tensor-memory reads and shared-memory operands of this tile are done
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
+        if (half == 0 && valid) {
+            const float2 o = sh.part[row];
+            const float sv = -(du + o.y) / r;
+            pf[rec.y] = sv;
+            pf[rec.z] = sv;
+            if (ENERGY) {
+                pu[rec.y] = u + o.x + b3;
+                pu[rec.z] = u + o.x + b3;
+            }
+        }
     }
     if (!ok && sh.stop == 0) {
         // a commit never arrived: record it, give the MMAs in flight one more
@@ -713,10 +741,10 @@ int Launch<T>::mlp_tc(const DevSys<T>& s, int cur, bool energy, cudaStream_t st)
     const int tblocks = sm_count() * TC_CTAS_PER_SM;
     k_mlp_stage<T><<<sm_count() * ESPP_STAGE_GRID, TILE, 0, st>>>(s, cur);
     if (energy) {
-        k_mlp_tc<true><<<tblocks, TC_M, sizeof(TcShared), st>>>(as_float(s));
+        k_mlp_tc<true><<<tblocks, TC_THREADS, sizeof(TcShared), st>>>(as_float(s));
         k_mlp_gather<T, true><<<s.ntiles, TILE, 0, st>>>(s, cur);
     } else {
-        k_mlp_tc<false><<<tblocks, TC_M, sizeof(TcShared), st>>>(as_float(s));
+        k_mlp_tc<false><<<tblocks, TC_THREADS, sizeof(TcShared), st>>>(as_float(s));
         k_mlp_gather<T, false><<<s.ntiles, TILE, 0, st>>>(s, cur);
     }
     return 3;
