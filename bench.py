@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--cg-steps", type=int, default=200)
     ap.add_argument("--cg-probe", type=int, default=0,
                     help="only: N-site CG system with the learned potential, a few force evaluations (for ncu)")
+    ap.add_argument("--train-probe", type=int, default=0,
+                    help="time force-matching training on this many CG sites and exit (for ncu)")
     ap.add_argument("--quick-start", action="store_true",
                     help="lattice start with a short equilibration (for profiler runs)")
     return ap.parse_args()
@@ -1212,10 +1214,49 @@ def run_cg_probe(a):
     return 0
 
 
+def run_train_probe(a):
+    """Force-matching training on a.train_probe CG sites (chains of 50 at
+    density 0.2125, 8 jittered frames with random target forces, random
+    BF16 weights): one warm-up epoch, then two timed epochs."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2608_14911_gb300 import espp, inputs
+    c = inputs.kg_lattice(max(1, a.train_probe // 50), 50, density=0.2125, seed=44, jitter=0.3)
+    rng = np.random.default_rng(4)
+    w = np.concatenate([rng.normal(0, 0.18, 64 * 32), np.zeros(64), rng.normal(0, 0.125, 64 * 64), np.zeros(64),
+                        rng.normal(0, 0.06, 64), [0.0]])
+    nf = 8
+    X = np.stack([inputs.f32(np.mod(c.x + rng.normal(0, 0.3, c.x.shape), c.box)) for _ in range(nf)])
+    X[X >= c.box] = 0.0
+    Xd = torch.tensor(X, device="cuda")
+    Yd = torch.tensor(rng.normal(0, 1.0, X.shape), device="cuda")
+    s = espp.System(c.box, c.n, None, c.bonds, precision=espp.ESPP_FP32, seed=1)
+    s.set_mlp(RCM, espp.to_bf16_bits(w))
+    rb = np.linspace(0.0, 6.0, 1201)
+    s.set_table_bond(6.0, 2.0 * (rb - 2.0) ** 2, -4.0 * (rb - 2.0))
+    s.set_exclude_bonded(True)
+    s.set_state(X[0])
+    s.build_neighbors(RCM, SKIN_CG)
+    s.mlp_train(Xd, Yd, batch_frames=4, epochs=1, lr=1e-3, seed=1)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    loss = s.mlp_train(Xd, Yd, batch_frames=4, epochs=2, lr=1e-3, seed=1)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"train_probe_sites": c.n, "ms_per_frame_epoch": e0.elapsed_time(e1) / (2 * nf),
+                      "loss": [float(v) for v in loss]}))
+    return 0
+
+
 def main():
     a = parse()
     if a.cg_probe:
         return run_cg_probe(a)
+    if a.train_probe:
+        return run_train_probe(a)
     if a.impl == "reference":
         return run_reference(a)
     return run_ours(a)

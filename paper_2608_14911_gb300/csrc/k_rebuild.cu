@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(TILE) k_copyback(DevSys<T> s, int cur, int per
 template <class T, bool EXCL, bool SHIFT, bool LE = false>
 __device__ __forceinline__ void verlet_range(const V4<T>* __restrict__ E, int p, int e, int i, int2 ex, T xo, T yo,
                                              T zo, T xL, T yL, T zL, T rl2, int tag, int cap, size_t stride,
-                                             int& cnt, int4& grp, int4* __restrict__ out4, T Lx = T(0),
+                                             int pad, int& cnt, int4& grp, int4* __restrict__ out4, T Lx = T(0),
                                              T inv_Lx = T(0)) {
     for (; p < e; ++p) {
         const V4<T> xj = ld4<T>(E + p);
@@ -326,7 +326,7 @@ __device__ __forceinline__ void verlet_range(const V4<T>* __restrict__ E, int p,
             ++cnt;
             if ((cnt & 3) == 0) {
                 if (cnt <= cap) out4[(size_t)((cnt >> 2) - 1) * stride] = grp;
-                grp = make_int4(-1, -1, -1, -1);
+                grp = make_int4(pad, pad, pad, pad);
             }
         }
     }
@@ -374,9 +374,9 @@ __device__ __forceinline__ void verlet_le_plane(const DevSys<T>& s, const RepGeo
             p0e = __ldg(B + base + hi + 1);
         }
         verlet_range<T, EXCL, true, true>(E, p0b, p0e, i, ex, xi.x, yo, zo, nd, yL, zL, s.rlist2, tag, s.cap,
-                                          (size_t)s.stride, cnt, grp, out4, L0, inv_L0);
+                                          (size_t)s.stride, s.nbr_pad, cnt, grp, out4, L0, inv_L0);
         verlet_range<T, EXCL, true, true>(E, p1b, p1e, i, ex, xi.x, yo, zo, nd, yL, zL, s.rlist2, tag, s.cap,
-                                          (size_t)s.stride, cnt, grp, out4, L0, inv_L0);
+                                          (size_t)s.stride, s.nbr_pad, cnt, grp, out4, L0, inv_L0);
     }
 }
 
@@ -459,10 +459,10 @@ __device__ __forceinline__ void verlet_stencil_full(const DevSys<T>& s, const Re
                 // a range that crosses no face (the common case) needs no shift
                 if (tag == 0)
                     verlet_range<T, EXCL, false>(E, pb[r][part], pe[r][part], i, ex, xo, yo, zo, xL, yL, zL, rl2,
-                                                 tag, cap, stride, cnt, grp, out4);
+                                                 tag, cap, stride, s.nbr_pad, cnt, grp, out4);
                 else
                     verlet_range<T, EXCL, true>(E, pb[r][part], pe[r][part], i, ex, xo, yo, zo, xL, yL, zL, rl2,
-                                                tag, cap, stride, cnt, grp, out4);
+                                                tag, cap, stride, s.nbr_pad, cnt, grp, out4);
             }
         }
     }
@@ -583,10 +583,10 @@ __device__ __forceinline__ void verlet_stencil_trim(const DevSys<T>& s, const Re
                 // a range that crosses no face (the common case) needs no shift
                 if (tag == 0)
                     verlet_range<T, EXCL, false>(E, pb[r][part], pe[r][part], i, ex, xo, yo, zo, xL, yL, zL, rl2,
-                                                 tag, cap, stride, cnt, grp, out4);
+                                                 tag, cap, stride, s.nbr_pad, cnt, grp, out4);
                 else
                     verlet_range<T, EXCL, true>(E, pb[r][part], pe[r][part], i, ex, xo, yo, zo, xL, yL, zL, rl2,
-                                                tag, cap, stride, cnt, grp, out4);
+                                                tag, cap, stride, s.nbr_pad, cnt, grp, out4);
             }
         }
     }
@@ -610,7 +610,7 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (W > 1 ? 8 : (EXCL || L
             // bonded partners left out of the list when 1-2 exclusions are on
             const int2 ex = EXCL ? s.bond_slot[i] : make_int2(-1, -1);
             int4* __restrict__ out4 = reinterpret_cast<int4*>(s.nbr) + i;
-            int4 grp = make_int4(-1, -1, -1, -1);
+            int4 grp = make_int4(s.nbr_pad, s.nbr_pad, s.nbr_pad, s.nbr_pad);
             if constexpr (W == 1) verlet_stencil_full<T, W, EXCL, LE>(s, g, i, xi, ex, cnt, grp, out4);
             else verlet_stencil_trim<T, W, EXCL, LE>(s, g, i, xi, ex, cnt, grp, out4);
             const int cap = s.cap;

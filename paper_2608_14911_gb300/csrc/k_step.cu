@@ -71,16 +71,21 @@ __device__ __forceinline__ void pair_loop(const DevSys<T>& s, const V4<T>* __res
     // current one, so their latency overlaps the current batch; the first
     // batch is read without waiting for the count (groups past the count are
     // allocated, and dropped whole; the last group is padded with -1)
+    // padding entries (the rest of the last group, and whole groups past the
+    // count) name the padding slot, whose position is far outside the box:
+    // every entry is loaded and evaluated without a test of its own
+    const int pad = s.nbr_pad;
+    const int4 pad4 = make_int4(pad, pad, pad, pad);
     int4 nxt[GB];
 #pragma unroll
-    for (int q = 0; q < GB; ++q) nxt[q] = q < gcap ? __ldg(nb + q * stride) : make_int4(-1, -1, -1, -1);
+    for (int q = 0; q < GB; ++q) nxt[q] = q < gcap ? __ldg(nb + q * stride) : pad4;
     for (int g0 = 0; g0 < ng || g0 == 0; g0 += GB) {
         int jj[4 * GB];
 #pragma unroll
         for (int q = 0; q < GB; ++q) {
             if (!ESPP_STEP_PREFETCH && g0 > 0) nxt[q] = __ldg(nb + (g0 + q) * stride);
             int4 a = nxt[q];
-            if (g0 + q >= ng) a = make_int4(-1, -1, -1, -1);
+            if (g0 + q >= ng) a = pad4;
             jj[4 * q + 0] = a.x;
             jj[4 * q + 1] = a.y;
             jj[4 * q + 2] = a.z;
@@ -96,15 +101,14 @@ __device__ __forceinline__ void pair_loop(const DevSys<T>& s, const V4<T>* __res
         }
         int codes = 0;
 #pragma unroll
-        for (int q = 0; q < 4 * GB; ++q) codes |= jj[q] > NBR_INDEX_MASK ? jj[q] : 0;
+        for (int q = 0; q < 4 * GB; ++q) codes |= jj[q];
         V4<T> xj[4 * GB];
 #pragma unroll
-        for (int q = 0; q < 4 * GB; ++q) xj[q] = jj[q] >= 0 ? ld4<T>(P + nbr_slot(jj[q])) : xi;
-        if (codes == 0) {
+        for (int q = 0; q < 4 * GB; ++q) xj[q] = ld4<T>(P + nbr_slot(jj[q]));
+        if ((codes & ~NBR_INDEX_MASK) == 0) {
             // no pair of this batch crosses a face (the common case)
 #pragma unroll
             for (int q = 0; q < 4 * GB; ++q) {
-                if (jj[q] < 0) continue;
                 const T dx = xi.x - xj[q].x, dy = xi.y - xj[q].y, dz = xi.z - xj[q].z;
                 pair_term<T, ENERGY, MULTI, FAST>(s, ti, pr1, dx, dy, dz, bits_as_int(xj[q].w), fx, fy, fz, pe,
                                                   vir, vxz);
@@ -117,7 +121,6 @@ __device__ __forceinline__ void pair_loop(const DevSys<T>& s, const V4<T>* __res
         } else {
 #pragma unroll
             for (int q = 0; q < 4 * GB; ++q) {
-                if (jj[q] < 0) continue;
                 const int code = nbr_code(jj[q]);
                 int nz = 0;
                 T dx;

@@ -72,11 +72,14 @@ template <class T> struct DevSys {
     int* in_cell;       // per old slot: arrival index in its cell
     // Verlet list in groups of four: entry k of particle i sits at
     // nbr[4 * ((k / 4) * stride + i) + k % 4]; k < nbr_cnt[i] <= cap; the last
-    // group is padded with -1
+    // group is padded with nbr_pad, the slot after the last particle, whose
+    // position (in both position buffers) lies far outside every box, so a
+    // padding entry is a pair beyond every cutoff
     int* nbr;
     int* nbr_cnt;
     int cap;
     int stride;
+    int nbr_pad;
     // cells, all replicas concatenated; cell index cell_off + (cz * ny + cy) * nx + cx
     int* cell_cnt;
     // compact entries (position, storage slot in the w lane): those of cell h

@@ -295,7 +295,7 @@ class System : public SystemBase {
         // device buffers
         int rc = ESPP_OK;
         const size_t n = (size_t)N;
-        if ((rc = alloc(&d.pos[0], n, allocs)) || (rc = alloc(&d.pos[1], n, allocs)) ||
+        if ((rc = alloc(&d.pos[0], n + 1, allocs)) || (rc = alloc(&d.pos[1], n + 1, allocs)) ||
             (rc = alloc(&d.vel, n, allocs)) || (rc = alloc(&d.vel_alt, n, allocs)) ||
             (rc = alloc(&d.frc, n, allocs)) || (rc = alloc(&d.frc_alt, n, allocs)) ||
             (rc = alloc(&d.xb, n, allocs)) || (rc = alloc(&d.img, n, allocs)) ||
@@ -328,6 +328,16 @@ class System : public SystemBase {
             return rc;
         d.le_clk = d_le_clk;
         d.mlp = d_mlp;
+        // the list's padding slot: one position past the particles, far
+        // outside every box (type 0), in both position buffers
+        {
+            V4<T> far;
+            far.x = far.y = far.z = (T)1e15;
+            far.w = (T)0;
+            CK(cudaMemcpy(d.pos[0] + n, &far, sizeof(far), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(d.pos[1] + n, &far, sizeof(far), cudaMemcpyHostToDevice));
+            d.nbr_pad = N;
+        }
         // host-side fault injection for tests: the tensor-core kernel's wait runs out
         if (const char* f = getenv("ESPP_FAULT_TC_TIMEOUT")) d.tc_fault = atoi(f) > 0 ? 1 : 0;
         d.bond_gid = bg;
