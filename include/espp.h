@@ -305,8 +305,8 @@ int espp_tune_force_method(espp_h h, int32_t nsteps, double dt, double gamma, do
  * paper's "Performance optimizations" name data sorting).  Shapes of the
  * FP32 step kernel on the plain list path (one particle type, Lennard-Jones,
  * no Lees-Edwards or DPD), as (int4 list groups per batch, resident blocks per
- * SM the registers are fitted to, 128-particle tiles per block): 0 = (1, 10,
- * 1) (the default), 1 = (2, 8, 1), 2 = (1, 12, 1), 3 = (1, 8, 1), 4 = (1, 5,
+ * SM the registers are fitted to, 128-particle tiles per block): 0 = (1, 8,
+ * 1) (the default), 1 = (2, 8, 1), 2 = (1, 12, 1), 3 = (1, 10, 1), 4 = (1, 5,
  * 2), 5 = (1, 3, 3), 6 = (1, 2, 4), 7 = (1, 2, 5).  Every shape computes the
  * same forces bit for bit; they differ in speed only.  espp_set_step_shape selects one (ESPP_ERR_ARG outside
  * [0, ESPP_STEP_SHAPES)).  espp_tune_step_shape times nsteps integrate steps

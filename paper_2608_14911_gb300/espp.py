@@ -46,7 +46,7 @@ ESPP_FORCES_CELLS = 1
 STEP_SHAPES = 8
 # (int4 list groups per batch, resident blocks per SM, tiles per block) of each
 # step-kernel shape, as include/espp.h lists them
-STEP_SHAPE_TABLE = ((1, 10, 1), (2, 8, 1), (1, 12, 1), (1, 8, 1), (1, 5, 2), (1, 3, 3), (1, 2, 4), (1, 2, 5))
+STEP_SHAPE_TABLE = ((1, 8, 1), (2, 8, 1), (1, 12, 1), (1, 10, 1), (1, 5, 2), (1, 3, 3), (1, 2, 4), (1, 2, 5))
 
 ERROR_NAMES = {
     ESPP_ERR_ARG: "ESPP_ERR_ARG", ESPP_ERR_CUDA: "ESPP_ERR_CUDA",
