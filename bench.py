@@ -269,7 +269,7 @@ def step_kernel_bytes(n, list_entries, precision):
 def step_kernel_digest():
     """Digest of the sources the step kernel is compiled from."""
     h = hashlib.sha256()
-    for f in ("k_step.cu", "pair_terms.cuh", "kernels.cuh", "common.cuh", "philox.cuh"):
+    for f in ("k_step.cu", "pair_terms.cuh", "kernels.cuh", "common.cuh", "philox.cuh", "packed.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2608_14911_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
