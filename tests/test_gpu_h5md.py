@@ -194,3 +194,51 @@ def test_read_refuses_other_handles_and_broken_files(tmp_path):
     a.close()
     b.close()
     o.close()
+
+
+def test_resume_under_lees_edwards(tmp_path):
+    # a sheared run: the file keeps the shear rate and the simulated time (the
+    # offset delta = gdot Lz t), and the resumed run continues the trajectory;
+    # positions compared through the sheared minimum image
+    case = kg_case()
+    c = case.cfg
+
+    def make(seed):
+        s = case.system(FP64, seed=seed, build=False)
+        s.set_lees_edwards(True, 0.8, 1.25)
+        s.build_neighbors(case.rc_list, case.skin)
+        return s
+
+    a = make(9)
+    a.integrate(120, DT, 1.0, 1.0)
+    path = tmp_path / "le.h5"
+    a.h5md_write(path)
+    f = H.read(path)
+    par = f["parameters/espp"]
+    assert int(par.attrs["lees_edwards"]) == 1 and float(par.attrs["shear_rate"]) == 0.8
+    assert float(par.attrs["time"]) == pytest.approx(1.25 + 120 * DT, abs=1e-12)
+    a.integrate(40, DT, 1.0, 1.0)
+    b = make(77)
+    b.h5md_read(path)
+    assert b.step == 120 and b.lees_edwards()[2] == pytest.approx(1.25 + 120 * DT, abs=1e-12)
+    b.integrate(40, DT, 1.0, 1.0)
+    xa, va, _ = a.get_state()
+    xb, vb, _ = b.get_state()
+    delta = 0.8 * c.box[2] * (1.25 + 160 * DT)
+    d = xa - xb
+    k = np.rint(d[:, 2] / c.box[2])
+    d[:, 2] -= k * c.box[2]
+    d[:, 0] -= k * delta
+    d[:, 0] -= np.rint(d[:, 0] / c.box[0]) * c.box[0]
+    d[:, 1] -= np.rint(d[:, 1] / c.box[1]) * c.box[1]
+    assert np.abs(d).max() <= 1e-9
+    dv = va - vb
+    dv[:, 0] -= k * 0.8 * c.box[2]
+    assert np.abs(dv).max() <= 1e-8
+    # a handle without shear refuses the sheared file
+    p = case.system(FP64, seed=9)
+    with pytest.raises(espp.EsppError):
+        p.h5md_read(path)
+    a.close()
+    b.close()
+    p.close()
