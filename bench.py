@@ -49,7 +49,7 @@ def parse():
                     help="launch every kernel directly instead of through CUDA graphs (for ncu)")
     ap.add_argument("--no-suite", action="store_true",
                     help="skip the secondary workloads (4M LJ, 512 replicas, learned CG)")
-    ap.add_argument("--suite-steps", type=int, default=1000)
+    ap.add_argument("--suite-steps", type=int, default=5000)
     ap.add_argument("--suite-only", default="",
                     help="comma-separated names of the suite entries to run (default: all)")
     ap.add_argument("--cg-frames", type=int, default=2000)
@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--cg-eq", type=int, default=2000)
     ap.add_argument("--cg-snap", type=int, default=20)
     ap.add_argument("--cg-warm", type=int, default=1000)
-    ap.add_argument("--cg-steps", type=int, default=200)
+    ap.add_argument("--cg-steps", type=int, default=1000)
     ap.add_argument("--cg-probe", type=int, default=0,
                     help="only: N-site CG system with the learned potential, a few force evaluations (for ncu)")
     ap.add_argument("--train-probe", type=int, default=0,
