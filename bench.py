@@ -628,9 +628,8 @@ def suite_dpd_fluid(a, sync):
         mean = {k: float(np.mean([q[k] for q in obs])) for k in ("temperature", "pressure", "pxz")}
         part = {"value": n * steps / (ms / 1e3), "unit": "particle-steps/s", "steps": steps,
                 "ms_per_step": ms / steps, "rebuilds": rb,
-                "force_shape": ("verlet_whole_cells", "verlet_half_cells", "cells")[method],
-                "tuner_ms_per_step": {"verlet_whole_cells": tuned_ms[0], "verlet_half_cells": tuned_ms[1],
-                                      "cells": tuned_ms[2]}, **mean}
+                "force_shape": espp.FORCE_SHAPE_NAMES[method],
+                "tuner_ms_per_step": dict(zip(espp.FORCE_SHAPE_NAMES, tuned_ms)), **mean}
         if shear is not None:
             part["viscosity_estimate"] = -mean["pxz"] / shear
         out[label] = part
@@ -653,9 +652,14 @@ def suite_lj4m(a, sync, peaks):
         s.integrate(100, 0.005, 1.0, 0.72)
         tuned = None
         if prec == espp.ESPP_FP32:
-            # the autotuner picks the step kernel's launch shape and the resort interval
+            # the autotuners pick the force path (list over whole, half or
+            # third cells, or list-free cells), then the step kernel's launch
+            # shape and the resort interval
+            force_ms, force_shape = s.tune_force_method(100, 0.005, 1.0, 0.72)
             shape_ms, resort_ms, (shape, resort) = s.tune_step_shape(200, 0.005, 1.0, 0.72)
-            tuned = {"chosen": shape, "shape": espp.STEP_SHAPE_TABLE[shape], "resort_interval": resort,
+            tuned = {"force_shape": espp.FORCE_SHAPE_NAMES[force_shape],
+                     "force_tuner_ms_per_step": dict(zip(espp.FORCE_SHAPE_NAMES, force_ms)),
+                     "chosen": shape, "shape": espp.STEP_SHAPE_TABLE[shape], "resort_interval": resort,
                      "tuner_ms_per_step": {"shapes": shape_ms, "resort_250_500_1000": resort_ms}}
             s.integrate(20, 0.005, 1.0, 0.72)
         rb0 = s.n_rebuilds
@@ -716,9 +720,8 @@ def suite_batched(a, sync):
            "value": n * steps / (ms / 1e3), "unit": "particle-steps/s", "steps": steps,
            "ms_per_step": ms / steps, "rebuild_passes": s.n_rebuilds - rb0,
            "kernel_launches_per_step": (s.kernel_launches - l0) / steps,
-           "force_shape": ("verlet_whole_cells", "verlet_half_cells", "cells")[shape],
-           "tuner_ms_per_step": {"verlet_whole_cells": tuned_ms[0], "verlet_half_cells": tuned_ms[1],
-                                 "cells": tuned_ms[2]},
+           "force_shape": espp.FORCE_SHAPE_NAMES[shape],
+           "tuner_ms_per_step": dict(zip(espp.FORCE_SHAPE_NAMES, tuned_ms)),
            "step_shape": {"chosen": step_shape, "shape": espp.STEP_SHAPE_TABLE[step_shape],
                           "resort_interval": resort,
                           "tuner_ms_per_step": {"shapes": shape_ms, "resort_250_500_1000": resort_ms}},

@@ -290,13 +290,15 @@ int espp_set_thermostat(espp_h h, int32_t kind, double rc);
 #define ESPP_FORCES_CELLS 1
 int espp_set_force_method(espp_h h, int32_t method);
 /* Autotuner of the force path's shape: times nsteps integrate steps (dt,
- * gamma, kT) from the current state with each of three shapes, 0 = the
- * Verlet list over whole cells, 1 = the Verlet list over half cells
- * (subdivision 2), 2 = the list-free cell forces over whole cells; restores
- * the state (as espp_set_state would, plus the step and simulated time) and
- * keeps the fastest shape (method and subdivision).  ms_per_step[3] (may be
- * NULL) receives the times (INFINITY for a shape whose cells do not fit the
- * box), *chosen (may be NULL) the shape kept.  Synchronises. */
+ * gamma, kT) from the current state with each of ESPP_FORCE_SHAPES shapes,
+ * 0 = the Verlet list over whole cells, 1 = the Verlet list over half cells
+ * (subdivision 2), 2 = the Verlet list over third cells (subdivision 3), 3 =
+ * the list-free cell forces over whole cells; restores the state (as
+ * espp_set_state would, plus the step and simulated time) and keeps the
+ * fastest shape (method and subdivision).  ms_per_step[ESPP_FORCE_SHAPES]
+ * (may be NULL) receives the times (INFINITY for a shape whose cells do not
+ * fit the box), *chosen (may be NULL) the shape kept.  Synchronises. */
+#define ESPP_FORCE_SHAPES 4
 int espp_tune_force_method(espp_h h, int32_t nsteps, double dt, double gamma, double kT, double* ms_per_step,
                            int32_t* chosen);
 
@@ -456,15 +458,17 @@ int espp_list_stats(espp_h h, int64_t* total_entries, int32_t* max_count);
 int espp_set_resort_interval(espp_h h, int64_t steps);
 
 /* Cell sub-decomposition for the Verlet build (paper "Performance
- * optimizations": cells of rc/2 cut the volume searched per particle).
- * w = 1: cells of edge >= rc + skin and a 3x3x3 stencil; w = 2: cells of edge
- * >= (rc + skin) / 2 and a 5x5x5 stencil; w = 0 (default): chosen at each
- * espp_build_neighbors, 2 when a full cell holds ten or more particles on
- * average (and every edge holds 5 half cells), else 1.  w = 1 needs 3 cells
- * along every edge of every replica and w = 2 needs 5 (ESPP_ERR_BOX_TOO_SMALL
- * otherwise).  The list itself (its set of pairs) does not depend on w.
- * Takes effect at once when a grid exists (the list is rebuilt), else at the
- * next espp_build_neighbors.  ESPP_ERR_ARG unless 0 <= w <= 2. */
+ * optimizations": cells of rc/2 or rc/3 cut the volume searched per
+ * particle).  w = 1: cells of edge >= rc + skin and a 3x3x3 stencil; w = 2
+ * or 3: cells of edge >= (rc + skin) / w and a (2w+1)^3 stencil, each row of
+ * it searched only over the cells the list sphere reaches; w = 0 (default):
+ * chosen at each espp_build_neighbors, 2 when a full cell holds ten or more
+ * particles on average (and every edge holds 5 half cells), else 1.  w needs
+ * 2w + 1 cells along every edge of every replica (ESPP_ERR_BOX_TOO_SMALL
+ * otherwise).  The list itself (its set of pairs) does not depend on w.  The
+ * list-free mode (ESPP_FORCES_CELLS) takes w <= 2.  Takes effect at once when
+ * a grid exists (the list is rebuilt), else at the next espp_build_neighbors.
+ * ESPP_ERR_ARG unless 0 <= w <= 3, or for w = 3 in the list-free mode. */
 int espp_set_cell_subdivision(espp_h h, int32_t w);
 
 /* Steps captured per CUDA graph replay in espp_integrate (default 64).  0

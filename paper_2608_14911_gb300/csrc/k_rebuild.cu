@@ -522,10 +522,16 @@ __device__ __forceinline__ void verlet_stencil_trim(const DevSys<T>& s, const Re
         T dmz = dz > 0 ? (T)dz - fz : (dz < 0 ? fz + (T)(-dz - 1) : T(0));
         dmz = dmz > margin ? (dmz - margin) * ez : T(0);
         const T dz2 = dmz * dmz;
-        int pb[NR][2], pe[NR][2], cyc[NR];
+        // rows whose ranges are loaded together (all of a plane for W <= 2;
+        // one at a time for W = 3, whose seven rows would not fit the
+        // registers)
+        constexpr int RG = W <= 2 ? NR : 1;
+#pragma unroll 1
+        for (int r0 = 0; r0 < NR; r0 += RG) {
+        int pb[RG][2], pe[RG][2], cyc[RG];
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            const int dy = r - W;
+        for (int r = 0; r < RG; ++r) {
+            const int dy = r0 + r - W;
             int ay = cy + dy, c = 0;
             if (ay < 0) { ay += nc1; c = 2; }
             else if (ay >= nc1) { ay -= nc1; c = 1; }
@@ -572,7 +578,7 @@ __device__ __forceinline__ void verlet_stencil_trim(const DevSys<T>& s, const Re
             pe[r][1] = h1 >= s1 ? __ldg(B + base + h1 + 1) : 0;
         }
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
+        for (int r = 0; r < RG; ++r) {
             const int cyr = cyc[r] & 3;
             const T yo = (cyr & 1) ? xi.y - L1 : xi.y, yL = (cyr & 2) ? L1 : T(0);
 #pragma unroll
@@ -588,6 +594,7 @@ __device__ __forceinline__ void verlet_stencil_trim(const DevSys<T>& s, const Re
                     verlet_range<T, EXCL, true>(E, pb[r][part], pe[r][part], i, ex, xo, yo, zo, xL, yL, zL, rl2,
                                                 tag, cap, stride, s.nbr_pad, cnt, grp, out4);
             }
+        }
         }
     }
 }
@@ -670,9 +677,12 @@ int Launch<T>::rebuild(const DevSys<T>& s, int cur, bool resort, bool permute_fo
     if (s.cell_w == 1) {
         if (s.excl_bonded) ESPP_VERLET(1, true);
         else ESPP_VERLET(1, false);
-    } else {
+    } else if (s.cell_w == 2) {
         if (s.excl_bonded) ESPP_VERLET(2, true);
         else ESPP_VERLET(2, false);
+    } else {
+        if (s.excl_bonded) ESPP_VERLET(3, true);
+        else ESPP_VERLET(3, false);
     }
 #undef ESPP_VERLET
     launched += 1;

@@ -1827,6 +1827,7 @@ class System : public SystemBase {
             return fail(ESPP_ERR_ARG, "unknown force method");
         const int cells = method == ESPP_FORCES_CELLS ? 1 : 0;
         if (cells && d.mlp_on) return fail(ESPP_ERR_STATE, "the learned potential needs the Verlet list");
+        if (cells && cell_sub_req == 3) return fail(ESPP_ERR_ARG, "the list-free mode takes whole or half cells");
         if (cells == d.cells_mode) return ESPP_OK;
         if (cells && !d.cpf) {
             int rc;
@@ -1843,8 +1844,8 @@ class System : public SystemBase {
     }
 
     // Times nsteps steps of each candidate shape from the current state and
-    // keeps the fastest: the Verlet list over whole cells, the Verlet list
-    // over half cells, the list-free cell forces (whole cells).  The state is
+    // keeps the fastest: the Verlet list over whole, half or third cells, the
+    // list-free cell forces (whole cells).  The state is
     // then restored through set_state (so the next integrate recomputes the
     // force of the current step); a candidate whose cells do not fit the box
     // is skipped.  The subdivision request of the caller is replaced.
@@ -1864,20 +1865,23 @@ class System : public SystemBase {
             if ((rc = set_step(step0))) return rc;
             return set_clock(t0, dt0, step0);
         };
-        const int method_of[3] = {ESPP_FORCES_VERLET, ESPP_FORCES_VERLET, ESPP_FORCES_CELLS};
-        const int w_of[3] = {1, 2, 1};
+        constexpr int NSH = ESPP_FORCE_SHAPES;
+        const int method_of[NSH] = {ESPP_FORCES_VERLET, ESPP_FORCES_VERLET, ESPP_FORCES_VERLET, ESPP_FORCES_CELLS};
+        const int w_of[NSH] = {1, 2, 3, 1};
         auto apply = [&](int k) -> int {
-            // method first (it rebuilds the grid), then the subdivision
+            // the subdivision first (the list-free shape takes whole cells),
+            // then the method (a change of method rebuilds the grid)
+            cell_sub_req = w_of[k];
             int rc = set_force_method(method_of[k]);
             if (rc) return rc;
-            cell_sub_req = w_of[k];
             return build_neighbors(rc_list, skin);
         };
-        double t[3] = {INFINITY, INFINITY, INFINITY};
+        double t[NSH];
+        for (double& q : t) q = INFINITY;
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
-        for (int k = 0; k < 3 && !rcode; ++k) {
+        for (int k = 0; k < NSH && !rcode; ++k) {
             if (method_of[k] == ESPP_FORCES_CELLS && d.mlp_on) continue;
             const int rc = apply(k);
             if (rc == ESPP_ERR_BOX_TOO_SMALL) continue;  // this shape does not fit
@@ -1895,12 +1899,12 @@ class System : public SystemBase {
         cudaEventDestroy(e1);
         if (rcode) return rcode;
         int best = 0;
-        for (int k = 1; k < 3; ++k)
+        for (int k = 1; k < NSH; ++k)
             if (t[k] < t[best]) best = k;
         if (!std::isfinite(t[best])) return fail(ESPP_ERR_BOX_TOO_SMALL, "no cell shape fits the box");
         if ((rcode = apply(best)) || (rcode = restore())) return rcode;
         if (ms)
-            for (int k = 0; k < 3; ++k) ms[k] = t[k];
+            for (int k = 0; k < NSH; ++k) ms[k] = t[k];
         if (chosen) *chosen = best;
         return ESPP_OK;
     }
@@ -2088,7 +2092,8 @@ class System : public SystemBase {
     }
 
     int set_cell_subdivision(int w) override {
-        if (w < 0 || w > 2) return fail(ESPP_ERR_ARG, "cell subdivision must be 0, 1 or 2");
+        if (w < 0 || w > 3) return fail(ESPP_ERR_ARG, "cell subdivision must be 0, 1, 2 or 3");
+        if (w == 3 && d.cells_mode) return fail(ESPP_ERR_ARG, "the list-free mode takes whole or half cells");
         cell_sub_req = w;
         // an existing grid is rebuilt with the new cells
         return cells_ready ? build_neighbors(rc_list, skin) : ESPP_OK;

@@ -44,6 +44,8 @@ ESPP_THERMO_DPD = 1
 ESPP_FORCES_VERLET = 0
 ESPP_FORCES_CELLS = 1
 STEP_SHAPES = 8
+FORCE_SHAPES = 4
+FORCE_SHAPE_NAMES = ("verlet_whole_cells", "verlet_half_cells", "verlet_third_cells", "cells")
 # (int4 list groups per batch, resident blocks per SM, tiles per block) of each
 # step-kernel shape, as include/espp.h lists them
 STEP_SHAPE_TABLE = ((1, 8, 1), (2, 8, 1), (1, 12, 1), (1, 10, 1), (1, 5, 2), (1, 3, 3), (1, 2, 4), (1, 2, 5))
@@ -478,14 +480,14 @@ class System:
         self._c(lib().espp_set_force_method(self._h, int(method)))
 
     def tune_force_method(self, nsteps, dt, gamma, kT):
-        """Time the three shapes (Verlet/whole cells, Verlet/half cells,
-        list-free cells) from the current state and keep the fastest;
+        """Time the FORCE_SHAPES shapes (Verlet over whole, half or third
+        cells, list-free cells) from the current state and keep the fastest;
         returns (ms per step of each, chosen shape index)."""
-        ms = (ctypes.c_double * 3)()
+        ms = (ctypes.c_double * FORCE_SHAPES)()
         ch = ctypes.c_int32()
         self._c(lib().espp_tune_force_method(self._h, int(nsteps), float(dt), float(gamma), float(kT), ms,
                                              ctypes.byref(ch)))
-        return [ms[0], ms[1], ms[2]], int(ch.value)
+        return list(ms), int(ch.value)
 
     def set_step_shape(self, shape):
         self._c(lib().espp_set_step_shape(self._h, int(shape)))

@@ -187,7 +187,7 @@ def test_tuner_times_both_and_keeps_the_state():
     before = s.get_state()
     step = s.step
     ms, chosen = s.tune_force_method(40, 0.005, 1.0, 1.0)
-    assert len(ms) == 3 and np.isfinite(ms[0]) and np.isfinite(ms[2]) and min(ms) > 0
+    assert len(ms) == espp.FORCE_SHAPES and np.isfinite(ms[0]) and np.isfinite(ms[3]) and min(ms) > 0
     assert chosen == int(np.argmin(ms))
     assert s.step == step
     for p, q in zip(before, s.get_state()):

@@ -253,7 +253,7 @@ def test_list_overflow_is_retried(monkeypatch):
     assert np.abs(_unwrapped(x, img, case.cfg.box) - _unwrapped(st.x, st.img, case.cfg.box)).max() < 1e-10
 
 
-@pytest.mark.parametrize("w", [2])
+@pytest.mark.parametrize("w", [2, 3])
 @pytest.mark.parametrize("case", [kg_case(), lj_case(), two_type_case()], ids=lambda c: c.name)
 def test_cell_subdivision_keeps_the_list(case, w):
     # sub-cells (paper: cell sub-decomposition) change the search, not the list
@@ -275,8 +275,40 @@ def test_cell_subdivision_keeps_the_list(case, w):
     O.integrate(case.model, st, 60, 0.005, 1.0, 0.72, seed=42)
     assert np.abs(_unwrapped(x, img, case.cfg.box) - _unwrapped(st.x, st.img, case.cfg.box)).max() < 1e-10
     with pytest.raises(espp.EsppError) as e:
-        b.set_cell_subdivision(3)
+        b.set_cell_subdivision(4)
     assert e.value.code == espp.ESPP_ERR_ARG
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_third_cells_keep_the_neighbour_sets(prec):
+    # cells of (rc + skin) / 3, rows trimmed to the list sphere: the same
+    # pairs as brute force (FP32: outside a 1e-6 band at the list radius)
+    case = lj_case()
+    s = case.system(prec, build=False)
+    s.set_cell_subdivision(3)
+    s.build_neighbors(case.rc_list, case.skin)
+    row, cols = s.get_neighbors()
+    c = case.cfg
+    rl = case.rc_list + case.skin
+    orow, ocols = O.neighbors(c.box, c.x, rl, method="brute")
+    band = 1e-6 if prec == FP32 else 0.0
+    for i in range(c.n):
+        got = set(cols[row[i]:row[i + 1]].tolist())
+        exp = set(ocols[orow[i]:orow[i + 1]].tolist())
+        for j in got ^ exp:
+            d = c.x[i] - c.x[j]
+            d -= c.box * np.round(d / c.box)
+            assert abs(np.linalg.norm(d) - rl) <= band, (i, j, np.linalg.norm(d))
+    # the list-free mode takes whole or half cells only
+    with pytest.raises(espp.EsppError) as e:
+        s.set_force_method(espp.ESPP_FORCES_CELLS)
+    assert e.value.code == espp.ESPP_ERR_ARG
+    s.set_cell_subdivision(0)
+    s.set_force_method(espp.ESPP_FORCES_CELLS)
+    with pytest.raises(espp.EsppError) as e:
+        s.set_cell_subdivision(3)
+    assert e.value.code == espp.ESPP_ERR_ARG
+    s.close()
 
 
 def test_cell_subdivision_in_batches():
@@ -295,6 +327,8 @@ def test_cell_subdivision_in_batches():
     b.set_cell_subdivision(1)
     f1 = b.compute_forces()
     assert rel_rms(f3, f1) <= 1e-13
+    b.set_cell_subdivision(3)
+    assert rel_rms(b.compute_forces(), f1) <= 1e-13
     off = 0
     for c in cases_:
         fo, _ = O.forces(c.model, c.cfg.box, c.cfg.x, c.cfg.types, c.cfg.bonds)
