@@ -15,10 +15,22 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "h5md.h"
 #include "kernels.cuh"
 
 namespace espp {
+
+// NVTX range over a host call (shown by ncu's --nvtx filters and by
+// timeline profilers; a no-op unless a tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 void hilbert_ranks(int nx, int ny, int nz, int* rank);
 int scan_blocks_for(int ncells);
 
@@ -826,6 +838,7 @@ class System : public SystemBase {
     // evaluation of the current weights over all frames (epochs == 0).
     int mlp_train(const double* X, const double* Y, int nframes, int batch, int epochs, double lr, uint64_t seed,
                   double* loss_hist, float* grad_out) override {
+        NvtxRange nvtx_range("espp_mlp_train");
         if (!X || !Y || nframes < 1 || epochs < 0 || (epochs > 0 && (batch < 1 || !(lr > 0))))
             return fail(ESPP_ERR_ARG, "bad training arguments");
         if (!d.mlp_on || mlp_bits.empty()) return fail(ESPP_ERR_STATE, "select the learned potential and set weights first");
@@ -1051,6 +1064,7 @@ class System : public SystemBase {
     }
 
     int build_neighbors(double rc, double sk) override {
+        NvtxRange nvtx_range("espp_build_neighbors");
         if (!(rc > 0) || !(sk >= 0) || !std::isfinite(rc) || !std::isfinite(sk))
             return fail(ESPP_ERR_ARG, "rc must be positive and skin non-negative");
         const double rc_old = rc_list, sk_old = skin;
@@ -1131,6 +1145,7 @@ class System : public SystemBase {
     // an overflow the list or the cell array is reallocated and every replica
     // is rebuilt (the old buffers of the other replicas are gone).
     int rebuild_now(bool permute_force, bool resort = true) {
+        NvtxRange nvtx_range("espp_rebuild");
         if (!cells_ready) return fail(ESPP_ERR_STATE, "call espp_build_neighbors first");
         for (int attempt = 0; attempt < 6; ++attempt) {
             launches += Launch<T>::rebuild(d, cur, resort, permute_force, st);
@@ -1238,6 +1253,7 @@ class System : public SystemBase {
 
     // ------------------------------------------------------------------ forces
     int compute_forces(double* f, int where) override {
+        NvtxRange nvtx_range("espp_compute_forces");
         int rcode = ensure_list();
         if (rcode) return rcode;
         double* target = f;
@@ -1387,6 +1403,7 @@ class System : public SystemBase {
     }
 
     int integrate(int64_t nsteps, double dt, double gamma, double kT) override {
+        NvtxRange nvtx_range("espp_integrate");
         if (nsteps < 0 || !(dt > 0) || !(gamma >= 0) || !(kT >= 0) || !std::isfinite(dt) || !std::isfinite(gamma) ||
             !std::isfinite(kT))
             return fail(ESPP_ERR_ARG, "need nsteps >= 0 and finite dt > 0, gamma >= 0, kT >= 0");
@@ -1494,6 +1511,7 @@ class System : public SystemBase {
 
     // ------------------------------------------------------------ observables
     int observables(espp_obs_t* out, int Rq) override {
+        NvtxRange nvtx_range("espp_observables");
         if (!out || Rq < 1 || Rq > R) return fail(ESPP_ERR_ARG, "bad output");
         int rcode = ensure_list();
         if (rcode) return rcode;
@@ -1605,6 +1623,7 @@ class System : public SystemBase {
     }
 
     int checkpoint_save(const char* path) override {
+        NvtxRange nvtx_range("espp_checkpoint_save");
         if (!path) return fail(ESPP_ERR_ARG, "path is required");
         if (!state_set) return fail(ESPP_ERR_STATE, "no state set");
         CK(cudaStreamSynchronize(st));
@@ -1664,6 +1683,7 @@ class System : public SystemBase {
     }
 
     int checkpoint_load(const char* path) override {
+        NvtxRange nvtx_range("espp_checkpoint_load");
         if (!path) return fail(ESPP_ERR_ARG, "path is required");
         if (!cells_ready) return fail(ESPP_ERR_STATE, "call espp_build_neighbors before loading");
         FILE* fh = fopen(path, "rb");
@@ -1850,6 +1870,7 @@ class System : public SystemBase {
     // force of the current step); a candidate whose cells do not fit the box
     // is skipped.  The subdivision request of the caller is replaced.
     int tune_force_method(int nsteps, double dt, double gamma, double kT, double* ms, int* chosen) override {
+        NvtxRange nvtx_range("espp_tune_force_method");
         if (nsteps < 1) return fail(ESPP_ERR_ARG, "nsteps must be positive");
         if (!state_set || !cells_ready) return fail(ESPP_ERR_STATE, "set the state and build the cells first");
         const size_t n3 = 3 * (size_t)N;
@@ -1911,6 +1932,7 @@ class System : public SystemBase {
 
     // ---- H5MD files ----------------------------------------------------------
     int h5md_write(const char* path) override {
+        NvtxRange nvtx_range("espp_h5md_write");
         if (!path) return fail(ESPP_ERR_ARG, "path is required");
         if (!state_set) return fail(ESPP_ERR_STATE, "no state set");
         const size_t n3 = 3 * (size_t)N;
@@ -1964,6 +1986,7 @@ class System : public SystemBase {
     }
 
     int h5md_read(const char* path) override {
+        NvtxRange nvtx_range("espp_h5md_read");
         if (!path) return fail(ESPP_ERR_ARG, "path is required");
         H5mdState hs;
         std::string err;
@@ -2026,6 +2049,7 @@ class System : public SystemBase {
     // current state (restored after each trial and at the end), keeping the
     // fastest of each.
     int tune_step_shape(int nsteps, double dt, double gamma, double kT, double* ms, int* chosen) override {
+        NvtxRange nvtx_range("espp_tune_step_shape");
         if (nsteps < 1) return fail(ESPP_ERR_ARG, "nsteps must be positive");
         if (!state_set || !cells_ready) return fail(ESPP_ERR_STATE, "set the state and build the cells first");
         const size_t n3 = 3 * (size_t)N;
