@@ -763,6 +763,9 @@ def _bond_table_boltzmann(xs, nchains, sites_per_chain, box, kT=1.0, dr=0.02, rm
 
 
 RCM, SKIN_CG, DR_G = 3.5, 0.5, 0.02
+# handles that evaluate independent frames (training, held-out forces) build
+# a fresh list for every frame, so a skin would only lengthen it
+SKIN_FRAMES = 0.0
 
 
 def _gofr(counts, n, box, dr=DR_G):
@@ -796,7 +799,7 @@ def _sampled_rdf(h, x0, v0, eq, nsnap, every):
     """Mean unique non-bonded pair counts (bins of DR_G up to RCM) over nsnap
     snapshots every `every` steps after `eq` steps from (x0, v0)."""
     h.set_state(x0, v0)
-    h.build_neighbors(RCM, SKIN_CG)
+    h.build_neighbors(RCM, SKIN_FRAMES)
     h.integrate(eq, 0.005, 1.0, 1.0)
     counts = np.zeros(int(round(RCM / DR_G)))
     for _ in range(nsnap):
@@ -944,7 +947,7 @@ def suite_learned_cg(a, sync, out):
     for k in tframes:
         probe.set_state(X[k])
         if k == 0:
-            probe.build_neighbors(RCM, SKIN_CG)
+            probe.build_neighbors(RCM, SKIN_FRAMES)
         tgt_total += probe.rdf_counts(RCM, nbin)
     g_t = _gofr(tgt_total / len(tframes), ns, cfg.box)
     # ---- judge table: Boltzmann inversion + iterative Boltzmann inversion -----
@@ -981,7 +984,7 @@ def suite_learned_cg(a, sync, out):
     bits = espp.to_bf16_bits(w0)
     c = _cg_handle(cfg.box, ns, cg_bonds, bond_tab, ("mlp", bits), 43)
     c.set_state(X[0])
-    c.build_neighbors(RCM, SKIN_CG)
+    c.build_neighbors(RCM, SKIN_FRAMES)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     sync()
@@ -1010,7 +1013,7 @@ def suite_learned_cg(a, sync, out):
         for q in range(n_hold):
             h.set_state(X[n_train + q])
             if q == 0:
-                h.build_neighbors(RCM, SKIN_CG)
+                h.build_neighbors(RCM, SKIN_FRAMES)
             h.compute_forces(fq)
             yq = Y[n_train + q]
             se += float(((fq - yq) ** 2).sum())
@@ -1086,7 +1089,7 @@ def suite_learned_cg(a, sync, out):
             for k in range(n_ref):
                 h.set_state(Xr[k])
                 if k == 0:
-                    h.build_neighbors(RCM, SKIN_CG)
+                    h.build_neighbors(RCM, SKIN_FRAMES)
                 h.compute_forces(fk)
                 Yc[k] += fk
             lh = h.mlp_train(Xr, Yc, batch_frames=a.cg_batch, epochs=a.refine_epochs, lr=1e-3, seed=5 + it)
@@ -1111,7 +1114,7 @@ def suite_learned_cg(a, sync, out):
         for q in range(n_hold):
             h.set_state(X[n_train + q])
             if q == 0:
-                h.build_neighbors(RCM, SKIN_CG)
+                h.build_neighbors(RCM, SKIN_FRAMES)
             h.compute_forces(fq)
             yq = Y[n_train + q]
             se += float(((fq - yq) ** 2).sum())
