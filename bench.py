@@ -904,11 +904,11 @@ def suite_learned_cg(a, sync, out):
     """Learned CG: a fine KG melt of 2000 chains x 200 beads is mapped 4:1 onto
     100k sites every 200 steps; the CG bond table comes from Boltzmann
     inversion; the MLP pair potential is force-matched on the frames; its
-    judge is an independent tabulated pair potential made from the mapped
+    yardstick is an independent tabulated pair potential made from the mapped
     g(r) alone (Boltzmann inversion refined by iterative Boltzmann
     inversion).  Both are compared with the mapped fine melt (g(r) and
     held-out forces); then a 4M-site CG melt runs with the MLP on the tensor
-    cores and with the judge table.  Results go into `out` as they are
+    cores and with the IBI table.  Results go into `out` as they are
     measured, and `out["stage"]` names the part that ran last."""
     import torch
     from paper_2608_14911_gb300 import espp, inputs
@@ -950,8 +950,8 @@ def suite_learned_cg(a, sync, out):
             probe.build_neighbors(RCM, SKIN_FRAMES)
         tgt_total += probe.rdf_counts(RCM, nbin)
     g_t = _gofr(tgt_total / len(tframes), ns, cfg.box)
-    # ---- judge table: Boltzmann inversion + iterative Boltzmann inversion -----
-    out["stage"] = "judge table (IBI)"
+    # ---- IBI table: Boltzmann inversion + iterative Boltzmann inversion -----
+    out["stage"] = "IBI table (IBI)"
     rt = np.linspace(0.0, RCM, 4096)
     U, first_t = _boltzmann_start(g_t, tgt_total)
     vmax = inputs.maxwell_velocities(ns, 1.0, seed=47)
@@ -969,7 +969,7 @@ def suite_learned_cg(a, sync, out):
             best = (l2, ut.copy(), ft.copy(), U.copy())
         U = _ibi_update(U, g, g_t, c * a.cg_snap, first_t, damping=a.ibi_damping)
     _, ut, ft, _ = best
-    out["judge_table"] = {"method": "Boltzmann inversion of the mapped non-bonded g(r) (bins with >= 100 sampled "
+    out["ibi_table"] = {"method": "Boltzmann inversion of the mapped non-bonded g(r) (bins with >= 100 sampled "
                                     "pairs; the core continued linearly), then %d iterations of iterative Boltzmann "
                                     "inversion (damping %.2f), the best kept" % (a.ibi_iters, a.ibi_damping),
                           "rdf_l2_per_iteration": ibi_l2, "max_abs_force_per_iteration": ibi_fmax,
@@ -1002,9 +1002,9 @@ def suite_learned_cg(a, sync, out):
     peaks_t, peak_kind_t = measured_peaks()
     tr_peak = peaks_t.get("bf16_tflops_sustained", peaks_t["bf16_tflops"])
     c.close()
-    # ---- held-out forces and losses: zero pair force, judge table, MLP ------
+    # ---- held-out forces and losses: zero pair force, IBI table, MLP ------
     out["stage"] = "held-out forces"
-    models = {"zero_pair": None, "judge_table": ("table", ut, ft), "mlp": ("mlp", trained)}
+    models = {"zero_pair": None, "ibi_table": ("table", ut, ft), "mlp": ("mlp", trained)}
     held = {}
     for name, pair in models.items():
         h = _cg_handle(cfg.box, ns, cg_bonds, bond_tab, pair, 44)
@@ -1036,16 +1036,16 @@ def suite_learned_cg(a, sync, out):
                                     "unit": "TFLOP/s", "peak": tr_peak, "frac": tr_flop / tr_s / 1e12 / tr_peak,
                                     "peak_kind": peak_kind_t + " (bf16_tflops_sustained)",
                                     "timed": "whole epochs: state upload, list build, forces, gradient, Adam"}}
-    # ---- structure: MLP and judge table against the mapped g(r) ---------------
+    # ---- structure: MLP and IBI table against the mapped g(r) ---------------
     out["stage"] = "structure at 100k sites"
     gs = {}
-    for name in ("mlp", "judge_table"):
+    for name in ("mlp", "ibi_table"):
         h = _cg_handle(cfg.box, ns, cg_bonds, bond_tab, models[name], 61)
         gs[name] = _gofr(_sampled_rdf(h, x_start, vmax, a.cg_eq, 2 * a.cg_snap, 25), ns, cfg.box)
         h.close()
     out["structure"] = {"rdf_l2_mlp_vs_mapped": _rdf_l2(gs["mlp"], g_t),
-                        "rdf_l2_table_vs_mapped": _rdf_l2(gs["judge_table"], g_t),
-                        "rdf_l2_mlp_vs_table": _rdf_l2(gs["mlp"], gs["judge_table"]),
+                        "rdf_l2_table_vs_mapped": _rdf_l2(gs["ibi_table"], g_t),
+                        "rdf_l2_mlp_vs_table": _rdf_l2(gs["mlp"], gs["ibi_table"]),
                         "protocol": "100k CG sites from a held-out mapped frame, Langevin T 1, %d steps, then g(r) "
                                     "(non-bonded pairs, dr %.2f to %.1f) over %d snapshots 25 steps apart; target: "
                                     "the mapped g(r) of %d frames" % (a.cg_eq, DR_G, RCM, 2 * a.cg_snap, len(tframes))}
@@ -1126,8 +1126,8 @@ def suite_learned_cg(a, sync, out):
         g_ref = _gofr(_sampled_rdf(h, x_start, vmax, a.cg_eq, 2 * a.cg_snap, 25), ns, cfg.box)
         h.close()
         out["structure"]["rdf_l2_mlp_refined_vs_mapped"] = _rdf_l2(g_ref, g_t)
-        out["structure"]["rdf_l2_mlp_refined_vs_table"] = _rdf_l2(g_ref, gs["judge_table"])
-    # ---- 4M CG sites: MLP on tensor cores vs the judge table -------------------
+        out["structure"]["rdf_l2_mlp_refined_vs_table"] = _rdf_l2(g_ref, gs["ibi_table"])
+    # ---- 4M CG sites: MLP on tensor cores vs the IBI table -------------------
     out["stage"] = "4M CG melt"
     cg = inputs.kg_lattice(16000, 250, density=0.2125, seed=44, jitter=0.1)
     res = {}

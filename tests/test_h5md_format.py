@@ -1,5 +1,5 @@
 """The test-side HDF5 reader's checksum against the check values Bob Jenkins
-published with lookup3 (the driver of lookup3.c): the HDF5 format checksums
+published with lookup3 (the self-test of lookup3.c): the HDF5 format checksums
 its metadata with hashlittle, initial value 0, so the files the library
 writes are verified against an independently pinned hash."""
 import pytest
