@@ -909,3 +909,66 @@ def test_step_shape_tuner_restores_the_state():
         assert np.array_equal(a, b)
     with pytest.raises(espp.EsppError):
         s.set_step_shape(espp.STEP_SHAPES)
+
+
+def test_full_size_lj_4m_in_the_benchmark_state():
+    # the 4M LJ fluid as the benchmark runs it: the force-path tuner (third
+    # cells win there) and the step-shape tuner, then steps with rebuilds;
+    # sampled forces and neighbour sets against the oracle on the stored state
+    case = lj_case((128, 128, 64), seed=2, noise=0.05)
+    c = case.cfg
+    s = case.system(FP32)
+    s.integrate(100, 0.005, 1.0, 0.72)
+    s.tune_force_method(50, 0.005, 1.0, 0.72)
+    s.tune_step_shape(50, 0.005, 1.0, 0.72)
+    rb0 = s.n_rebuilds
+    s.integrate(300, 0.005, 1.0, 0.72)
+    assert s.n_rebuilds - rb0 >= 10
+    x, _, _ = s.get_state()
+    f = s.compute_forces()
+    sel = np.random.default_rng(5).choice(c.n, 3000, replace=False)
+    fo = O.forces_subset(case.model, c.box, x, c.types, c.bonds, sel)
+    assert rel_rms(f[sel], fo) <= 1e-5, rel_rms(f[sel], fo)
+    s.build_neighbors(case.rc_list, case.skin)
+    row, cols = s.get_neighbors()
+    rl = case.rc_list + case.skin
+    orow, ocols = O.neighbors(c.box, x, rl, method="cells")
+    for i in sel[:300]:
+        got = set(cols[row[i]:row[i + 1]].tolist())
+        exp = set(ocols[orow[i]:orow[i + 1]].tolist())
+        for j in got ^ exp:
+            d = x[i] - x[j]
+            d -= c.box * np.round(d / c.box)
+            assert abs(np.sqrt(d @ d) - rl) < 1e-6, (i, j)
+    s.close()
+
+
+def test_full_size_batched_512_replicas_sampled_forces():
+    # the 512 uneven replicas of the batched benchmark (11.6M beads, lattice
+    # starts), tuned and stepped as the benchmark does; three replicas (the
+    # smallest, the largest and one between) against the oracle
+    sizes = I.replica_sizes(512, seed=42)
+    cfgs = [I.kg_lattice(nc, nb, density=0.85, seed=42 + r, jitter=0.05) for r, (nc, nb) in enumerate(sizes)]
+    reps = [dict(box=q.box, n=q.n, types=q.types, bonds=q.bonds, seed=42 + r) for r, q in enumerate(cfgs)]
+    s = espp.System(replicas=reps, precision=FP32)
+    s.set_wca()
+    s.set_fene()
+    s.set_state(np.concatenate([q.x for q in cfgs]), I.maxwell_velocities(s.n, 1.0, seed=7),
+                np.concatenate([q.img for q in cfgs]))
+    s.build_neighbors(WCA_RC, 0.4)
+    s.integrate(100, 0.005, 1.0, 1.0)
+    s.tune_force_method(50, 0.005, 1.0, 1.0)
+    s.tune_step_shape(50, 0.005, 1.0, 1.0)
+    s.integrate(200, 0.005, 1.0, 1.0)
+    x, _, _ = s.get_state()
+    f = s.compute_forces()
+    off = np.concatenate([[0], np.cumsum([q.n for q in cfgs])])
+    ns = np.array([q.n for q in cfgs])
+    model = O.Model(1, KG_PAIR, KG_BOND)
+    for r in (int(ns.argmin()), int(ns.argmax()), 255):
+        q = cfgs[r]
+        xr, fr = x[off[r]:off[r + 1]], f[off[r]:off[r + 1]]
+        sel = np.random.default_rng(r).choice(q.n, min(q.n, 2000), replace=False)
+        fo = O.forces_subset(model, q.box, xr, q.types, q.bonds, sel)
+        assert rel_rms(fr[sel], fo) <= 1e-5, (r, rel_rms(fr[sel], fo))
+    s.close()
