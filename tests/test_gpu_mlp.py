@@ -362,3 +362,33 @@ def test_mlp_refuses_sheared_and_list_free_modes():
             call()
         assert e.value.code == espp.ESPP_ERR_STATE
     s.compute_forces()
+
+
+def test_full_size_cg_4m_sampled_forces():
+    # the 4M-site CG melt of the learned-potential benchmark (16,000 chains of
+    # 250 sites at density 0.2125), stepped with the learned potential on the
+    # tensor cores; sampled summed forces against the oracle's double
+    # evaluation of the same BF16 weights on the stored positions
+    c = I.kg_lattice(16000, 250, density=0.2125, seed=44, jitter=0.1)
+    bits, wd = _weights(4)
+    rmax, ub, fb = _bond_table()
+    s = espp.System(c.box, c.n, None, c.bonds, precision=espp.ESPP_FP32, seed=45)
+    s.set_mlp(RC, bits)
+    s.set_table_bond(rmax, ub, fb)
+    s.set_exclude_bonded(True)
+    s.set_state(c.x, I.maxwell_velocities(c.n, 1.0, seed=46), c.img)
+    s.build_neighbors(RC, SKIN)
+    s.integrate(100, 0.005, 1.0, 1.0)
+    x, _, _ = s.get_state()
+    f = s.compute_forces()
+    s.close()
+    O.set_mlp(wd, RC)
+    O.set_table(7, rmax, ub, fb)
+    O.set_exclude_bonded(True)
+    try:
+        model = O.Model(1, {(0, 0): ("mlp", RC)}, ("table", 7))
+        sel = np.random.default_rng(8).choice(c.n, 1500, replace=False)
+        fo = O.forces_subset(model, c.box, x, c.types, c.bonds, sel)
+    finally:
+        O.set_exclude_bonded(False)
+    assert rel_rms(f[sel], fo) <= MLP_SUM_TOL, rel_rms(f[sel], fo)
