@@ -392,3 +392,36 @@ def test_full_size_cg_4m_sampled_forces():
     finally:
         O.set_exclude_bonded(False)
     assert rel_rms(f[sel], fo) <= MLP_SUM_TOL, rel_rms(f[sel], fo)
+
+
+def test_training_gradient_over_many_tiles_matches_oracle():
+    # a frame of 10k sites (200 chains of 50 at density 0.2125): about 180k
+    # pairs, so every gradient CTA accumulates several 128-pair tiles in tensor
+    # memory (the small case above gives each CTA at most one); the loss and
+    # its weight gradient against the oracle's double evaluation (the oracle
+    # needs minutes for a whole 100k-site frame, whose gradient is a sum over
+    # every pair and cannot be sampled)
+    import torch
+    c = I.kg_lattice(200, 50, density=0.2125, seed=31, jitter=0.3)
+    bits, wd = _weights(5)
+    rmax, ub, fb = _bond_table()
+    X = _frames(c, 1, 32)
+    Y = np.random.default_rng(33).normal(0, 1.0, X.shape)
+    s = espp.System(c.box, c.n, c.types, c.bonds, precision=espp.ESPP_FP32, seed=5)
+    s.set_mlp(RC, bits)
+    s.set_table_bond(rmax, ub, fb)
+    s.set_exclude_bonded(True)
+    s.set_state(X[0], None, None)
+    s.build_neighbors(RC, 0.0)
+    loss, grad = s.mlp_loss_grad(torch.tensor(X, device="cuda"), torch.tensor(Y, device="cuda"))
+    s.close()
+    O.set_mlp(wd, RC)
+    O.set_table(8, rmax, ub, fb)
+    O.set_exclude_bonded(True)
+    try:
+        lo, go = O.mlp_loss_grad(O.Model(1, {}, ("table", 8)), c.box, X, Y, c.types, c.bonds)
+    finally:
+        O.set_exclude_bonded(False)
+    go = go[:-1]  # b3 has no gradient
+    assert abs(loss - lo) <= 2e-2 * lo
+    assert np.linalg.norm(grad - go) <= 5e-2 * np.linalg.norm(go), np.linalg.norm(grad - go) / np.linalg.norm(go)
