@@ -972,3 +972,21 @@ def test_full_size_batched_512_replicas_sampled_forces():
         fo = O.forces_subset(model, q.box, xr, q.types, q.bonds, sel)
         assert rel_rms(fr[sel], fo) <= 1e-5, (r, rel_rms(fr[sel], fo))
     s.close()
+
+
+def test_largest_handle_2_to_the_25_minus_1_particles():
+    # the most particles a handle addresses (2^25 - 1 = 31 x 601 x 1801): the
+    # list's padding slot is then the largest index an entry can hold; forces
+    # of sampled particles against the oracle, then steps with rebuilds
+    n_chains, n_beads = 31 * 601, 1801
+    c = I.kg_lattice(n_chains, n_beads, density=0.85, seed=13, jitter=0.05)
+    assert c.n == (1 << 25) - 1
+    case = Case("kg_max", c, KG_PAIR, KG_BOND, WCA_RC, 0.4)
+    s = case.system(FP32)
+    f = s.compute_forces()
+    sel = np.random.default_rng(13).choice(c.n, 1000, replace=False)
+    fo = O.forces_subset(case.model, c.box, c.x, c.types, c.bonds, sel)
+    assert rel_rms(f[sel], fo) <= FORCE_TOL[FP32], rel_rms(f[sel], fo)
+    s.integrate(20, 0.002, 1.0, 1.0)
+    assert s.error_word == 0 and s.step == 20
+    s.close()
