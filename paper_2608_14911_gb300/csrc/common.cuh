@@ -167,6 +167,18 @@ struct Tile {
     int pad;
 };
 
+// A tile record read ahead of a test that may end the block (an abort flag,
+// a replica flag): the load is issued in program order before that test (a
+// volatile read is never moved under the branch), so its round trip overlaps
+// the flag's instead of following it.
+__device__ __forceinline__ Tile ld_tile_early(const Tile* p) {
+    Tile t;
+    asm volatile("ld.global.nc.v4.s32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(t.start), "=r"(t.count), "=r"(t.rep), "=r"(t.pad)
+                 : "l"(p));
+    return t;
+}
+
 // Pair potential record for one (type_i, type_j), derived on the host.
 template <class T> struct PairRec {
     int kind;   // 0 none, ESPP_LJ, ESPP_LJ_CAPPED (WCA is LJ)

@@ -75,6 +75,9 @@ __global__ void __launch_bounds__(256) k_prep(DevSys<T> s) {
 // at list builds only.
 template <class T>
 __global__ void __launch_bounds__(TILE) k_bin(DevSys<T> s, int cur) {
+    // the first tile's record is requested together with the abort flag
+    Tile tl0 = {0, 0, 0, 0};
+    if ((int)blockIdx.x < s.ntiles) tl0 = ld_tile_early(s.tiles + blockIdx.x);
     if (s.ctrl->abort) return;
     if (blockIdx.x == 0) {
         for (int r = threadIdx.x; r < s.R; r += blockDim.x) s.req[r] = 0;
@@ -82,7 +85,7 @@ __global__ void __launch_bounds__(TILE) k_bin(DevSys<T> s, int cur) {
     }
     V4<T>* __restrict__ P = s.pos[cur];
     for (int t = blockIdx.x; t < s.ntiles; t += gridDim.x) {
-        const Tile tl = s.tiles[t];
+        const Tile tl = t == (int)blockIdx.x ? tl0 : s.tiles[t];
         if (!s.now[tl.rep] || (int)threadIdx.x >= tl.count) continue;
         const int i = tl.start + threadIdx.x;
         V4<T> p = P[i];
@@ -132,10 +135,13 @@ __global__ void __launch_bounds__(TILE) k_bin(DevSys<T> s, int cur) {
 // flagged replica at its cell's first entry + its arrival index.
 template <class T>
 __global__ void __launch_bounds__(TILE) k_place(DevSys<T> s, int cur) {
+    // the first tile's record is requested together with the abort flag
+    Tile tl0 = {0, 0, 0, 0};
+    if ((int)blockIdx.x < s.ntiles) tl0 = ld_tile_early(s.tiles + blockIdx.x);
     if (s.ctrl->abort) return;
     const V4<T>* __restrict__ P = s.pos[cur];
     for (int t = blockIdx.x; t < s.ntiles; t += gridDim.x) {
-        const Tile tl = s.tiles[t];
+        const Tile tl = t == (int)blockIdx.x ? tl0 : s.tiles[t];
         if (!s.now[tl.rep] || (int)threadIdx.x >= tl.count) continue;
         const int i = tl.start + threadIdx.x;
         V4<T> p = ld4<T>(P + i);
@@ -601,9 +607,12 @@ __device__ __forceinline__ void verlet_stencil_trim(const DevSys<T>& s, const Re
 
 template <class T, int W, bool EXCL, bool LE>
 __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (W > 1 ? 8 : (EXCL || LE ? 7 : 9)) : 5) k_verlet(DevSys<T> s, int cur) {
+    // the first tile's record is requested together with the abort flag
+    Tile tl0 = {0, 0, 0, 0};
+    if ((int)blockIdx.x < s.ntiles) tl0 = ld_tile_early(s.tiles + blockIdx.x);
     if (s.ctrl->abort) return;
     for (int t = blockIdx.x; t < s.ntiles; t += gridDim.x) {
-        const Tile tl = s.tiles[t];
+        const Tile tl = t == (int)blockIdx.x ? tl0 : s.tiles[t];
         if (!s.now[tl.rep]) continue;  // uniform over the block
         int cnt = 0;
         if ((int)threadIdx.x < tl.count) {

@@ -275,6 +275,10 @@ __global__ void __launch_bounds__(TILE * STEP_SHAPES[SH].tpb,
     static_assert(TPB == 1 || !ENERGY, "energy reductions take one tile per block");
     const int lt = TPB > 1 ? (int)threadIdx.x % TILE : (int)threadIdx.x;  // index inside the tile
     Ctrl* c = s.ctrl;
+    const int t0 = blockIdx.x * TPB + (TPB > 1 ? (int)threadIdx.x / TILE : 0);
+    // the first tile's record is requested together with the abort flag
+    Tile tl0 = {0, 0, 0, 0};
+    if (t0 < s.ntiles) tl0 = ld_tile_early(s.tiles + t0);
     if (MODE != MODE_FORCES && c->abort) return;
     const long long step = c->step + (MODE >= MODE_STEP ? 1 : 0);
     const V4<T>* __restrict__ P = s.pos[cur];
@@ -282,8 +286,8 @@ __global__ void __launch_bounds__(TILE * STEP_SHAPES[SH].tpb,
     const IntParams<T>* __restrict__ ip = s.ip;
     __shared__ double red[NPART][TILE / 32];
 
-    for (int t = blockIdx.x * TPB + (TPB > 1 ? (int)threadIdx.x / TILE : 0); t < s.ntiles; t += gridDim.x * TPB) {
-        const Tile tl = s.tiles[t];
+    for (int t = t0; t < s.ntiles; t += gridDim.x * TPB) {
+        const Tile tl = t == t0 ? tl0 : s.tiles[t];
         const bool active = lt < tl.count;
         const RepGeom<T>& g = s.reps[tl.rep];
         double acc[NPART];
