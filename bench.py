@@ -70,6 +70,9 @@ def parse():
                     help="only: N-site CG system with the learned potential, a few force evaluations (for ncu)")
     ap.add_argument("--train-probe", type=int, default=0,
                     help="time force-matching training on this many CG sites and exit (for ncu)")
+    ap.add_argument("--step-shape", type=int, default=-1,
+                    help="launch shape of the headline's step kernel after the tuner has run (for profiling; "
+                         "default: the tuner's pick)")
     ap.add_argument("--quick-start", action="store_true",
                     help="lattice start with a short equilibration (for profiler runs)")
     return ap.parse_args()
@@ -382,6 +385,9 @@ def run_ours(a):
     # the autotuner picks the step kernel's launch shape and the resort
     # interval for this melt (untimed; the state is restored afterwards)
     shape_ms, resort_ms, (shape, resort) = s.tune_step_shape(200, 0.005, 1.0, 1.0)
+    if a.step_shape >= 0:
+        shape = a.step_shape
+        s.set_step_shape(shape)
     if a.direct:
         s.set_graph_chunk(0)
     n = cfg.n
