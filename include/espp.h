@@ -12,7 +12,9 @@
  *
  * General rules
  *  - Every call returns an int status: ESPP_OK (0) or a negative ESPP_ERR_*.
- *    espp_last_error() gives a message for the last failing call on a handle.
+ *    espp_last_error() gives a message for the last failing call on a handle;
+ *    espp_last_error(NULL), for the calling thread's last failing call made
+ *    without one (creation, espp_h5md_inspect).
  *  - Inputs are copied; the caller keeps ownership of every buffer it passes.
  *    Outputs are written into caller-allocated buffers.
  *  - Buffers tagged "where" are host pointers when where == ESPP_HOST and
@@ -423,6 +425,16 @@ int espp_checkpoint_load(espp_h h, const char* path);
  * (write without a state), ESPP_ERR_IO. */
 int espp_h5md_write(espp_h h, const char* path);
 int espp_h5md_read(espp_h h, const char* path);
+/* What an H5MD file written by espp_h5md_write holds, without a handle (host
+ * code only; no GPU is touched): the number of replicas, their particles in
+ * total, the step and the precision of the handle that wrote it.  The file is
+ * parsed and checked as espp_h5md_read does (every checksum, every address
+ * and length against the file's size, each object reached once, every
+ * particle array of the size its shape says).  Any output pointer may be NULL.
+ * Errors: ESPP_ERR_ARG (null path), ESPP_ERR_IO (a file that cannot be opened
+ * or is refused); the message is espp_last_error(NULL). */
+int espp_h5md_inspect(const char* path, int32_t* n_replicas, int64_t* n_particles, int64_t* step,
+                      int32_t* precision);
 
 /* ---- diagnostics ----------------------------------------------------------- */
 const char* espp_last_error(espp_h h);

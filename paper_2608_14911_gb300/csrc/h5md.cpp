@@ -341,16 +341,25 @@ bool parse_space(In& in, std::vector<uint64_t>& dims, bool& scalar) {
     return in.ok && type <= 1;
 }
 
+// Every address and length read from the file is checked against the file's
+// size without overflow; each object may be reached once only (the writer
+// links every object from one parent), so a file whose links form a cycle or
+// reach one object twice is refused rather than walked again.
 bool parse_node(const std::vector<uint8_t>& b, uint64_t addr, const std::string& name, Node& n, int depth,
-                std::string& err) {
+                std::vector<uint64_t>& seen, std::string& err) {
     if (depth > 16) {
         err = "groups nested too deep";
         return false;
     }
-    if (addr + 16 > b.size() || memcmp(b.data() + addr, "OHDR", 4) != 0) {
+    if (addr > b.size() || b.size() - addr < 16 || memcmp(b.data() + addr, "OHDR", 4) != 0) {
         err = "not a version-2 object header at " + std::to_string(addr);
         return false;
     }
+    if (std::find(seen.begin(), seen.end(), addr) != seen.end()) {
+        err = "an object reached twice";
+        return false;
+    }
+    seen.push_back(addr);
     In in{b, (size_t)addr + 4};
     const uint32_t ver = (uint32_t)in.get(1), flags = (uint32_t)in.get(1);
     if (ver != 2 || (flags & ~3u) != 0) {
@@ -358,11 +367,12 @@ bool parse_node(const std::vector<uint8_t>& b, uint64_t addr, const std::string&
         return false;
     }
     const uint64_t chunk = in.get(1 << (flags & 3));
-    const size_t start = in.p, end = start + (size_t)chunk;
-    if (!in.ok || end + 4 > b.size()) {
+    const size_t start = in.p;
+    if (!in.ok || chunk > b.size() || b.size() - start < chunk + 4) {
         err = "truncated object header";
         return false;
     }
+    const size_t end = start + (size_t)chunk;
     const uint32_t sum = (uint32_t)(b[end] | (b[end + 1] << 8) | (b[end + 2] << 16) | ((uint32_t)b[end + 3] << 24));
     if (sum != lookup3(b.data() + addr, end - addr, 0)) {
         err = "object header checksum mismatch";
@@ -451,11 +461,11 @@ bool parse_node(const std::vector<uint8_t>& b, uint64_t addr, const std::string&
     if (n.is_group) {
         for (const auto& l : links) {
             Node c;
-            if (!parse_node(b, l.second, l.first, c, depth + 1, err)) return false;
+            if (!parse_node(b, l.second, l.first, c, depth + 1, seen, err)) return false;
             n.children.push_back(std::move(c));
         }
     } else {
-        if (!have_layout || data_addr == UNDEF || data_addr + data_size > b.size()) {
+        if (!have_layout || data_addr > b.size() || data_size > b.size() - data_addr) {
             err = "dataset without readable data";
             return false;
         }
@@ -488,7 +498,8 @@ int read_file(const char* path, Node& root, std::string& err) {
     }
     In in{b, 36};
     const uint64_t root_addr = in.get(8);
-    return parse_node(b, root_addr, "", root, 0, err) ? 0 : -1;
+    std::vector<uint64_t> seen;
+    return parse_node(b, root_addr, "", root, 0, seen, err) ? 0 : -1;
 }
 
 // ---- tree helpers ----------------------------------------------------------------------

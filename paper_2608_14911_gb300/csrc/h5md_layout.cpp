@@ -81,10 +81,18 @@ Node element(const std::string& name, int64_t step, double time, Node value) {
 
 std::string group_name(size_t r, size_t R) { return R == 1 ? "all" : "replica_" + std::to_string(r); }
 
+// a dataset of the given class, element size and shape whose data hold exactly
+// that many elements (the element count formed without overflow: every
+// partial product stays within the data's size)
 bool shaped(const Node* n, Type::Cls cls, uint32_t size, const std::vector<uint64_t>& dims) {
-    if (!n || n->is_group || n->type.cls != cls || n->type.size != size || n->dims != dims) return false;
+    if (!n || n->is_group || n->type.cls != cls || n->type.size != size || n->dims != dims || size == 0)
+        return false;
+    const uint64_t cap = n->data.size() / size;
     uint64_t count = 1;
-    for (uint64_t d : dims) count *= d;
+    for (uint64_t d : dims) {
+        if (d != 0 && count > cap / d) return false;
+        count *= d;
+    }
     return n->data.size() == count * size;
 }
 
@@ -198,7 +206,8 @@ int h5md_read(const char* path, H5mdState& st, std::string& err) {
         return -1;
     }
     const Node* seeds = e->find("seeds");
-    if (!seeds || seeds->is_group || seeds->dims.size() != 1 || seeds->type.size != 8) {
+    if (!seeds || seeds->dims.size() != 1 || !shaped(seeds, Type::INT, 8, {seeds->dims[0]}) ||
+        seeds->dims[0] == 0) {
         err = "missing replica seeds";
         return -1;
     }
@@ -242,9 +251,9 @@ int h5md_read(const char* path, H5mdState& st, std::string& err) {
             memcpy(rp.f.data(), f->data.data(), f->data.size());
         }
         const Node* bonds = root.find("connectivity/" + group_name(r, R) + "/bonds");
-        if (bonds && !bonds->is_group && bonds->type.size == 8) {
-            rp.bonds.resize(bonds->data.size() / 8);
-            memcpy(rp.bonds.data(), bonds->data.data(), bonds->data.size());
+        if (bonds && bonds->dims.size() == 2 && shaped(bonds, Type::INT, 8, {bonds->dims[0], 2})) {
+            rp.bonds.resize(2 * (size_t)bonds->dims[0]);
+            if (!rp.bonds.empty()) memcpy(rp.bonds.data(), bonds->data.data(), bonds->data.size());
         }
     }
     return 0;

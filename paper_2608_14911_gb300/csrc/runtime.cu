@@ -2321,6 +2321,32 @@ int espp_h5md_write(espp_h h, const char* path) {
 int espp_h5md_read(espp_h h, const char* path) {
     return guarded(h, [&](espp::SystemBase& s) { return s.h5md_read(path); });
 }
+int espp_h5md_inspect(const char* path, int32_t* n_replicas, int64_t* n_particles, int64_t* step,
+                      int32_t* precision) {
+    espp::NvtxRange nvtx_range("espp_h5md_inspect");
+    if (!path) {
+        g_create_error = "path is required";
+        return ESPP_ERR_ARG;
+    }
+    try {
+        espp::H5mdState hs;
+        std::string err;
+        if (espp::h5md_read(path, hs, err)) {
+            g_create_error = "H5MD read: " + err;
+            return ESPP_ERR_IO;
+        }
+        int64_t n = 0;
+        for (const espp::H5mdReplica& r : hs.reps) n += r.n;
+        if (n_replicas) *n_replicas = (int32_t)hs.reps.size();
+        if (n_particles) *n_particles = n;
+        if (step) *step = hs.step;
+        if (precision) *precision = hs.precision;
+        return ESPP_OK;
+    } catch (const std::exception& e) {
+        g_create_error = std::string("H5MD read: ") + e.what();
+        return ESPP_ERR_IO;
+    }
+}
 int espp_set_step_shape(espp_h h, int32_t shape) {
     return guarded(h, [&](espp::SystemBase& s) { return s.set_step_shape(shape); });
 }

@@ -73,7 +73,7 @@ EXPORTS = (
     "espp_cg_map", "espp_set_cell_subdivision", "espp_set_thermostat",
     "espp_set_lees_edwards", "espp_get_lees_edwards", "espp_set_force_method",
     "espp_tune_force_method", "espp_set_step_shape", "espp_tune_step_shape",
-    "espp_h5md_write", "espp_h5md_read",
+    "espp_h5md_write", "espp_h5md_read", "espp_h5md_inspect",
 )
 NOALLOC_MAX_BINS = 4096
 NOALLOC_MAX_N = 200000
@@ -162,6 +162,8 @@ def lib(path: str = LIB_PATH):
         "espp_set_step_shape": ([vp, ctypes.c_int32], ctypes.c_int),
         "espp_h5md_write": ([vp, ctypes.c_char_p], ctypes.c_int),
         "espp_h5md_read": ([vp, ctypes.c_char_p], ctypes.c_int),
+        "espp_h5md_inspect": ([ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
+                               ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "espp_tune_step_shape": ([vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp,
                                   ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "espp_mlp_set_weights": ([vp, vp, i64], ctypes.c_int),
@@ -197,6 +199,17 @@ def _ptr(a):
 
 
 # ---- the C calls, by name --------------------------------------------------------
+def h5md_inspect(path):
+    """What an H5MD file written by the library holds, without a handle (host
+    only): {"replicas", "particles" (in total), "step", "precision"}.  A file
+    the reader refuses raises EsppError (ESPP_ERR_IO)."""
+    r, p = ctypes.c_int32(0), ctypes.c_int32(0)
+    n, st = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib().espp_h5md_inspect(os.fspath(path).encode(), ctypes.byref(r), ctypes.byref(n), ctypes.byref(st),
+                                   ctypes.byref(p)))
+    return {"replicas": r.value, "particles": n.value, "step": st.value, "precision": p.value}
+
+
 def espp_hilbert_ranks(nx, ny, nz):
     out = np.zeros(nx * ny * nz, dtype=np.int32)
     _check(lib().espp_hilbert_ranks(nx, ny, nz, out.ctypes.data_as(ctypes.c_void_p)))

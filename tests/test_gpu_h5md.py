@@ -63,6 +63,8 @@ def test_written_file_holds_the_state_in_the_h5md_layout(prec, tmp_path):
     assert _bond_set(f["connectivity/all/bonds"].value) == _bond_set(c.bonds)
     par = f["parameters/espp"]
     assert int(par.attrs["step"]) == 113 and float(par.attrs["time"]) == 113 * DT
+    # the handle-free inspection reads the same file
+    assert espp.h5md_inspect(path) == {"replicas": 1, "particles": c.n, "step": 113, "precision": prec}
     assert int(par.attrs["precision"]) == prec and int(par.attrs["lees_edwards"]) == 0
     assert par["seeds"].value.tolist() == [23]
     # the wrapped positions lie in the box; unwrapping restores the chains
@@ -121,6 +123,8 @@ def test_batched_replicas_write_one_group_each(tmp_path):
         assert _bond_set(f["connectivity/replica_%d/bonds" % r].value) == _bond_set(k.cfg.bonds)
         off += n
     assert f["parameters/espp/seeds"].value.tolist() == [500, 501]
+    info = espp.h5md_inspect(path)
+    assert info["replicas"] == 2 and info["particles"] == sum(k.cfg.n for k in cases_) and info["step"] == 40
     b.close()
 
 
