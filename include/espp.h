@@ -291,16 +291,29 @@ int espp_set_thermostat(espp_h h, int32_t kind, double rc);
 #define ESPP_FORCES_VERLET 0
 #define ESPP_FORCES_CELLS 1
 int espp_set_force_method(espp_h h, int32_t method);
+/* How the Verlet build stores a particle's hits (a tuning knob; the list, its
+ * order included, is the same either way): ESPP_LIST_STORE_PLACE (default)
+ * writes each hit at its place in a 4-entry group held in registers,
+ * ESPP_LIST_STORE_PUSH pushes it in at the group's end (the others move down
+ * one place), which saves the per-place select on builds with many hits per
+ * candidate.  Taken by builds over whole and third cells; half cells always
+ * place.  Takes effect at the next list build.  ESPP_ERR_ARG for another
+ * value. */
+#define ESPP_LIST_STORE_PLACE 0
+#define ESPP_LIST_STORE_PUSH 1
+int espp_set_list_store(espp_h h, int32_t push);
 /* Autotuner of the force path's shape: times nsteps integrate steps (dt,
  * gamma, kT) from the current state with each of ESPP_FORCE_SHAPES shapes,
  * 0 = the Verlet list over whole cells, 1 = the Verlet list over half cells
  * (subdivision 2), 2 = the Verlet list over third cells (subdivision 3), 3 =
- * the list-free cell forces over whole cells; restores the state (as
+ * the list-free cell forces over whole cells, 4 and 5 = shapes 0 and 2 with
+ * ESPP_LIST_STORE_PUSH (the others place); restores the state (as
  * espp_set_state would, plus the step and simulated time) and keeps the
- * fastest shape (method and subdivision).  ms_per_step[ESPP_FORCE_SHAPES]
- * (may be NULL) receives the times (INFINITY for a shape whose cells do not
- * fit the box), *chosen (may be NULL) the shape kept.  Synchronises. */
-#define ESPP_FORCE_SHAPES 4
+ * fastest shape (method, subdivision and list store).
+ * ms_per_step[ESPP_FORCE_SHAPES] (may be NULL) receives the times (INFINITY
+ * for a shape whose cells do not fit the box), *chosen (may be NULL) the
+ * shape kept.  Synchronises. */
+#define ESPP_FORCE_SHAPES 6
 int espp_tune_force_method(espp_h h, int32_t nsteps, double dt, double gamma, double kT, double* ms_per_step,
                            int32_t* chosen);
 

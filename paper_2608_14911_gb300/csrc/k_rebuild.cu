@@ -303,7 +303,13 @@ __global__ void __launch_bounds__(TILE) k_copyback(DevSys<T> s, int cur, int per
 // difference is the plain one, which equals the shifted form with zero shifts.
 // LE: a row across a sheared face (Lees-Edwards): x is the nearest image of
 // x_i - nz delta - x_j (xL holds nz delta, yL/zL the usual shifts).
-template <class T, bool EXCL, bool SHIFT, bool LE = false>
+// PUSH: how a hit enters the int4 group in registers.  false: at its place
+// (cnt % 4), the group reset to padding once stored; true: pushed in at w,
+// the others moving down one place, so a full group holds its four in order
+// with no per-place select (the last, partial group is moved into place by
+// verlet_last_group).  The lists are the same; which is faster depends on the
+// hits per candidate and the registers left (the force-path tuner times both).
+template <class T, bool EXCL, bool SHIFT, bool LE = false, bool PUSH = false>
 __device__ __forceinline__ void verlet_range(const V4<T>* __restrict__ E, int p, int e, int i, int2 ex, T xo, T yo,
                                              T zo, T xL, T yL, T zL, T rl2, int tag, int cap, size_t stride,
                                              int pad, int& cnt, int4& grp, int4* __restrict__ out4, T Lx = T(0),
@@ -323,18 +329,42 @@ __device__ __forceinline__ void verlet_range(const V4<T>* __restrict__ E, int p,
         bool hit = dx * dx + dy * dy + dz * dz < rl2 && j != i;
         if (EXCL) hit = hit && j != ex.x && j != ex.y;
         if (hit) {
-            const int l = cnt & 3;
-            const int en = j | tag;
-            if (l == 0) grp.x = en;
-            else if (l == 1) grp.y = en;
-            else if (l == 2) grp.z = en;
-            else grp.w = en;
-            ++cnt;
-            if ((cnt & 3) == 0) {
-                if (cnt <= cap) out4[(size_t)((cnt >> 2) - 1) * stride] = grp;
-                grp = make_int4(pad, pad, pad, pad);
+            if constexpr (PUSH) {
+                grp = make_int4(grp.y, grp.z, grp.w, j | tag);
+                ++cnt;
+                if ((cnt & 3) == 0 && cnt <= cap) out4[(size_t)((cnt >> 2) - 1) * stride] = grp;
+            } else {
+                const int l = cnt & 3;
+                const int en = j | tag;
+                if (l == 0) grp.x = en;
+                else if (l == 1) grp.y = en;
+                else if (l == 2) grp.z = en;
+                else grp.w = en;
+                ++cnt;
+                if ((cnt & 3) == 0) {
+                    if (cnt <= cap) out4[(size_t)((cnt >> 2) - 1) * stride] = grp;
+                    grp = make_int4(pad, pad, pad, pad);
+                }
             }
         }
+    }
+}
+
+// The last, partial group of a list of cnt entries (cnt % 4 != 0) as stored:
+// its entries first, in order, then the padding slot.
+template <bool PUSH>
+__device__ __forceinline__ int4 verlet_last_group(int4 grp, int cnt, int pad) {
+    if constexpr (PUSH) {
+        // the group's cnt % 4 entries sit at its top (w last)
+        switch (cnt & 3) {
+            case 1: return make_int4(grp.w, pad, pad, pad);
+            case 2: return make_int4(grp.z, grp.w, pad, pad);
+            default: return make_int4(grp.y, grp.z, grp.w, pad);
+        }
+    } else {
+        (void)cnt;
+        (void)pad;
+        return grp;
     }
 }
 
@@ -347,7 +377,7 @@ __device__ __forceinline__ int g_rep(const DevSys<T>& s, const RepGeom<T>& g) {
 // One plane of rows across a sheared face (Lees-Edwards): x cells
 // cxs - W .. cxs + W (cyclic) of rows cy - W .. cy + W, entries tagged with x
 // code 3 (the x image is taken at evaluation time from the current delta).
-template <class T, int W, bool EXCL>
+template <class T, int W, bool EXCL, bool PUSH>
 __device__ __forceinline__ void verlet_le_plane(const DevSys<T>& s, const RepGeom<T>& g, int i, const V4<T>& xi,
                                              int2 ex, int cxs, int az, int cy, T nd, T zo, T zL, T L0, T inv_L0,
                                              int czc, int& cnt, int4& grp, int4* __restrict__ out4) {
@@ -379,9 +409,9 @@ __device__ __forceinline__ void verlet_le_plane(const DevSys<T>& s, const RepGeo
             p0b = __ldg(B + base + lo);
             p0e = __ldg(B + base + hi + 1);
         }
-        verlet_range<T, EXCL, true, true>(E, p0b, p0e, i, ex, xi.x, yo, zo, nd, yL, zL, s.rlist2, tag, s.cap,
+        verlet_range<T, EXCL, true, true, PUSH>(E, p0b, p0e, i, ex, xi.x, yo, zo, nd, yL, zL, s.rlist2, tag, s.cap,
                                           (size_t)s.stride, s.nbr_pad, cnt, grp, out4, L0, inv_L0);
-        verlet_range<T, EXCL, true, true>(E, p1b, p1e, i, ex, xi.x, yo, zo, nd, yL, zL, s.rlist2, tag, s.cap,
+        verlet_range<T, EXCL, true, true, PUSH>(E, p1b, p1e, i, ex, xi.x, yo, zo, nd, yL, zL, s.rlist2, tag, s.cap,
                                           (size_t)s.stride, s.nbr_pad, cnt, grp, out4, L0, inv_L0);
     }
 }
@@ -389,7 +419,7 @@ __device__ __forceinline__ void verlet_le_plane(const DevSys<T>& s, const RepGeo
 // The full stencil of particle i: every row over the same x cells cx - W ..
 // cx + W (whole cells: the trimmed form below costs more in registers and
 // per-row work than the quarter of the candidates it saves).
-template <class T, int W, bool EXCL, bool LE>
+template <class T, int W, bool EXCL, bool LE, bool PUSH>
 __device__ __forceinline__ void verlet_stencil_full(const DevSys<T>& s, const RepGeom<T>& g, int i,
                                                const V4<T>& xi, int2 ex, int& cnt, int4& grp,
                                                int4* __restrict__ out4) {
@@ -439,7 +469,7 @@ __device__ __forceinline__ void verlet_stencil_full(const DevSys<T>& s, const Re
             if (xs < T(0)) xs += L0;
             if (xs >= L0) xs -= L0;
             const int cxs = cell_coord(xs, g.cells_per_len[0], nc0);
-            verlet_le_plane<T, W, EXCL>(s, g, i, xi, ex, cxs, az, cy, nd, zo, zL, L0, inv_L0, czc, cnt, grp, out4);
+            verlet_le_plane<T, W, EXCL, PUSH>(s, g, i, xi, ex, cxs, az, cy, nd, zo, zL, L0, inv_L0, czc, cnt, grp, out4);
             continue;
         }
         int pb[NR][2], pe[NR][2], cyc[NR];
@@ -464,10 +494,10 @@ __device__ __forceinline__ void verlet_stencil_full(const DevSys<T>& s, const Re
                 const int tag = ((part ? cxc1 : cxc0) | (cyc[r] << 2) | (czc << 4)) << NBR_INDEX_BITS;
                 // a range that crosses no face (the common case) needs no shift
                 if (tag == 0)
-                    verlet_range<T, EXCL, false>(E, pb[r][part], pe[r][part], i, ex, xo, yo, zo, xL, yL, zL, rl2,
+                    verlet_range<T, EXCL, false, false, PUSH>(E, pb[r][part], pe[r][part], i, ex, xo, yo, zo, xL, yL, zL, rl2,
                                                  tag, cap, stride, s.nbr_pad, cnt, grp, out4);
                 else
-                    verlet_range<T, EXCL, true>(E, pb[r][part], pe[r][part], i, ex, xo, yo, zo, xL, yL, zL, rl2,
+                    verlet_range<T, EXCL, true, false, PUSH>(E, pb[r][part], pe[r][part], i, ex, xo, yo, zo, xL, yL, zL, rl2,
                                                 tag, cap, stride, s.nbr_pad, cnt, grp, out4);
             }
         }
@@ -484,7 +514,7 @@ __device__ __forceinline__ void verlet_stencil_full(const DevSys<T>& s, const Re
 // is unchanged); about a quarter (whole cells) to a third (half cells) of the
 // candidates of the full stencil go.  Used with sub-cells (W >= 2), where
 // rows are many and short; with whole cells the full stencil is faster.
-template <class T, int W, bool EXCL, bool LE>
+template <class T, int W, bool EXCL, bool LE, bool PUSH>
 __device__ __forceinline__ void verlet_stencil_trim(const DevSys<T>& s, const RepGeom<T>& g, int i,
                                                const V4<T>& xi, int2 ex, int& cnt, int4& grp,
                                                int4* __restrict__ out4) {
@@ -522,7 +552,7 @@ __device__ __forceinline__ void verlet_stencil_trim(const DevSys<T>& s, const Re
             if (xs < T(0)) xs += L0;
             if (xs >= L0) xs -= L0;
             const int cxs = cell_coord(xs, g.cells_per_len[0], nc0);
-            verlet_le_plane<T, W, EXCL>(s, g, i, xi, ex, cxs, az, cy, nd, zo, zL, L0, inv_L0, czc, cnt, grp, out4);
+            verlet_le_plane<T, W, EXCL, PUSH>(s, g, i, xi, ex, cxs, az, cy, nd, zo, zL, L0, inv_L0, czc, cnt, grp, out4);
             continue;
         }
         T dmz = dz > 0 ? (T)dz - fz : (dz < 0 ? fz + (T)(-dz - 1) : T(0));
@@ -594,10 +624,10 @@ __device__ __forceinline__ void verlet_stencil_trim(const DevSys<T>& s, const Re
                 const int tag = (cxc | (cyr << 2) | (czc << 4)) << NBR_INDEX_BITS;
                 // a range that crosses no face (the common case) needs no shift
                 if (tag == 0)
-                    verlet_range<T, EXCL, false>(E, pb[r][part], pe[r][part], i, ex, xo, yo, zo, xL, yL, zL, rl2,
+                    verlet_range<T, EXCL, false, false, PUSH>(E, pb[r][part], pe[r][part], i, ex, xo, yo, zo, xL, yL, zL, rl2,
                                                  tag, cap, stride, s.nbr_pad, cnt, grp, out4);
                 else
-                    verlet_range<T, EXCL, true>(E, pb[r][part], pe[r][part], i, ex, xo, yo, zo, xL, yL, zL, rl2,
+                    verlet_range<T, EXCL, true, false, PUSH>(E, pb[r][part], pe[r][part], i, ex, xo, yo, zo, xL, yL, zL, rl2,
                                                 tag, cap, stride, s.nbr_pad, cnt, grp, out4);
             }
         }
@@ -605,7 +635,7 @@ __device__ __forceinline__ void verlet_stencil_trim(const DevSys<T>& s, const Re
     }
 }
 
-template <class T, int W, bool EXCL, bool LE>
+template <class T, int W, bool EXCL, bool LE, bool PUSH>
 __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (W > 1 ? 8 : (EXCL || LE ? 7 : 9)) : 5) k_verlet(DevSys<T> s, int cur) {
     // the first tile's record is requested together with the abort flag
     Tile tl0 = {0, 0, 0, 0};
@@ -627,10 +657,10 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? (W > 1 ? 8 : (EXCL || L
             const int2 ex = EXCL ? s.bond_slot[i] : make_int2(-1, -1);
             int4* __restrict__ out4 = reinterpret_cast<int4*>(s.nbr) + i;
             int4 grp = make_int4(s.nbr_pad, s.nbr_pad, s.nbr_pad, s.nbr_pad);
-            if constexpr (W == 1) verlet_stencil_full<T, W, EXCL, LE>(s, g, i, xi, ex, cnt, grp, out4);
-            else verlet_stencil_trim<T, W, EXCL, LE>(s, g, i, xi, ex, cnt, grp, out4);
+            if constexpr (W == 1) verlet_stencil_full<T, W, EXCL, LE, PUSH>(s, g, i, xi, ex, cnt, grp, out4);
+            else verlet_stencil_trim<T, W, EXCL, LE, PUSH>(s, g, i, xi, ex, cnt, grp, out4);
             const int cap = s.cap;
-            if ((cnt & 3) != 0 && cnt <= cap) out4[(size_t)(cnt >> 2) * s.stride] = grp;
+            if ((cnt & 3) != 0 && cnt <= cap) out4[(size_t)(cnt >> 2) * s.stride] = verlet_last_group<PUSH>(grp, cnt, s.nbr_pad);
             s.nbr_cnt[i] = cnt < cap ? cnt : cap;
             if (cnt > cap) {
                 atomicMax(&s.ctrl->need_cap, (unsigned int)cnt);
@@ -678,21 +708,28 @@ int Launch<T>::rebuild(const DevSys<T>& s, int cur, bool resort, bool permute_fo
     }
     // list-free mode: the binning is all that is needed
     if (s.cells_mode) return launched;
-#define ESPP_VERLET(W, E)                                                  \
-    do {                                                                   \
-        if (s.le_on) k_verlet<T, W, E, true><<<gt, TILE, 0, st>>>(s, cur);  \
-        else k_verlet<T, W, E, false><<<gt, TILE, 0, st>>>(s, cur);        \
+#define ESPP_VERLET(W, E, P)                                                  \
+    do {                                                                      \
+        if (s.le_on) k_verlet<T, W, E, true, P><<<gt, TILE, 0, st>>>(s, cur);  \
+        else k_verlet<T, W, E, false, P><<<gt, TILE, 0, st>>>(s, cur);        \
     } while (0)
+#define ESPP_VERLET_P(W, P)                       \
+    do {                                         \
+        if (s.excl_bonded) ESPP_VERLET(W, true, P);  \
+        else ESPP_VERLET(W, false, P);            \
+    } while (0)
+    // the pushed stores are built for whole and third cells (on half cells
+    // they only cost registers)
     if (s.cell_w == 1) {
-        if (s.excl_bonded) ESPP_VERLET(1, true);
-        else ESPP_VERLET(1, false);
+        if (s.list_push) ESPP_VERLET_P(1, true);
+        else ESPP_VERLET_P(1, false);
     } else if (s.cell_w == 2) {
-        if (s.excl_bonded) ESPP_VERLET(2, true);
-        else ESPP_VERLET(2, false);
+        ESPP_VERLET_P(2, false);
     } else {
-        if (s.excl_bonded) ESPP_VERLET(3, true);
-        else ESPP_VERLET(3, false);
+        if (s.list_push) ESPP_VERLET_P(3, true);
+        else ESPP_VERLET_P(3, false);
     }
+#undef ESPP_VERLET_P
 #undef ESPP_VERLET
     launched += 1;
     // mirrored entries for the learned potential's pair-once evaluation

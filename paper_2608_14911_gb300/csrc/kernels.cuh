@@ -88,6 +88,7 @@ template <class T> struct DevSys {
     int* cell_beg;          // ncells + 1; cell_beg[ncells] = N
     int* rank_start;        // first new slot of each cell in Hilbert-rank order (resort only)
     int cell_w;             // cell subdivision: cells of edge >= (rc + skin) / cell_w (1, 2 or 3)
+    int list_push;          // Verlet build: hits pushed into the list group (1) or placed (0)
     const int* cell_by_rank;  // global Hilbert rank -> cell index
     const int* cell_rep;
     int ncells;

@@ -87,6 +87,7 @@ struct SystemBase {
     virtual int set_force_method(int method) = 0;
     virtual int tune_force_method(int nsteps, double dt, double gamma, double kT, double* ms, int* chosen) = 0;
     virtual int set_step_shape(int shape) = 0;
+    virtual int set_list_store(int push) = 0;
     virtual int h5md_write(const char* path) = 0;
     virtual int h5md_read(const char* path) = 0;
     virtual int tune_step_shape(int nsteps, double dt, double gamma, double kT, double* ms, int* chosen) = 0;
@@ -1887,14 +1888,18 @@ class System : public SystemBase {
             return set_clock(t0, dt0, step0);
         };
         constexpr int NSH = ESPP_FORCE_SHAPES;
-        const int method_of[NSH] = {ESPP_FORCES_VERLET, ESPP_FORCES_VERLET, ESPP_FORCES_VERLET, ESPP_FORCES_CELLS};
-        const int w_of[NSH] = {1, 2, 3, 1};
+        const int method_of[NSH] = {ESPP_FORCES_VERLET, ESPP_FORCES_VERLET, ESPP_FORCES_VERLET,
+                                    ESPP_FORCES_CELLS,  ESPP_FORCES_VERLET, ESPP_FORCES_VERLET};
+        const int w_of[NSH] = {1, 2, 3, 1, 1, 3};
+        const int push_of[NSH] = {0, 0, 0, 0, 1, 1};
         auto apply = [&](int k) -> int {
-            // the subdivision first (the list-free shape takes whole cells),
-            // then the method (a change of method rebuilds the grid)
+            // the subdivision and the list store first (the list-free shape
+            // takes whole cells), then the method (a change of method
+            // rebuilds the grid)
             cell_sub_req = w_of[k];
-            int rc = set_force_method(method_of[k]);
+            int rc = set_list_store(push_of[k]);
             if (rc) return rc;
+            if ((rc = set_force_method(method_of[k]))) return rc;
             return build_neighbors(rc_list, skin);
         };
         double t[NSH];
@@ -2041,6 +2046,14 @@ class System : public SystemBase {
     int set_step_shape(int shape) override {
         if (shape < 0 || shape >= ESPP_STEP_SHAPES) return fail(ESPP_ERR_ARG, "unknown step shape");
         d.step_shape = shape;
+        clear_graphs();  // a kernel argument of the captured graphs
+        return ESPP_OK;
+    }
+
+    int set_list_store(int push) override {
+        if (push != ESPP_LIST_STORE_PLACE && push != ESPP_LIST_STORE_PUSH)
+            return fail(ESPP_ERR_ARG, "unknown list store");
+        d.list_push = push;
         clear_graphs();  // a kernel argument of the captured graphs
         return ESPP_OK;
     }
@@ -2346,6 +2359,9 @@ int espp_h5md_inspect(const char* path, int32_t* n_replicas, int64_t* n_particle
         g_create_error = std::string("H5MD read: ") + e.what();
         return ESPP_ERR_IO;
     }
+}
+int espp_set_list_store(espp_h h, int32_t push) {
+    return guarded(h, [&](espp::SystemBase& s) { return s.set_list_store(push); });
 }
 int espp_set_step_shape(espp_h h, int32_t shape) {
     return guarded(h, [&](espp::SystemBase& s) { return s.set_step_shape(shape); });

@@ -44,8 +44,10 @@ ESPP_THERMO_DPD = 1
 ESPP_FORCES_VERLET = 0
 ESPP_FORCES_CELLS = 1
 STEP_SHAPES = 8
-FORCE_SHAPES = 4
-FORCE_SHAPE_NAMES = ("verlet_whole_cells", "verlet_half_cells", "verlet_third_cells", "cells")
+FORCE_SHAPES = 6
+FORCE_SHAPE_NAMES = ("verlet_whole_cells", "verlet_half_cells", "verlet_third_cells", "cells",
+                     "verlet_whole_cells_push", "verlet_third_cells_push")
+ESPP_LIST_STORE_PLACE, ESPP_LIST_STORE_PUSH = 0, 1
 # (int4 list groups per batch, resident blocks per SM, tiles per block) of each
 # step-kernel shape, as include/espp.h lists them
 STEP_SHAPE_TABLE = ((1, 8, 1), (2, 8, 1), (1, 12, 1), (1, 10, 1), (1, 5, 2), (1, 3, 3), (1, 2, 4), (1, 2, 5))
@@ -73,7 +75,7 @@ EXPORTS = (
     "espp_cg_map", "espp_set_cell_subdivision", "espp_set_thermostat",
     "espp_set_lees_edwards", "espp_get_lees_edwards", "espp_set_force_method",
     "espp_tune_force_method", "espp_set_step_shape", "espp_tune_step_shape",
-    "espp_h5md_write", "espp_h5md_read", "espp_h5md_inspect",
+    "espp_h5md_write", "espp_h5md_read", "espp_h5md_inspect", "espp_set_list_store",
 )
 NOALLOC_MAX_BINS = 4096
 NOALLOC_MAX_N = 200000
@@ -160,6 +162,7 @@ def lib(path: str = LIB_PATH):
         "espp_tune_force_method": ([vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp,
                                     ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "espp_set_step_shape": ([vp, ctypes.c_int32], ctypes.c_int),
+        "espp_set_list_store": ([vp, ctypes.c_int32], ctypes.c_int),
         "espp_h5md_write": ([vp, ctypes.c_char_p], ctypes.c_int),
         "espp_h5md_read": ([vp, ctypes.c_char_p], ctypes.c_int),
         "espp_h5md_inspect": ([ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
@@ -494,8 +497,9 @@ class System:
 
     def tune_force_method(self, nsteps, dt, gamma, kT):
         """Time the FORCE_SHAPES shapes (Verlet over whole, half or third
-        cells, list-free cells) from the current state and keep the fastest;
-        returns (ms per step of each, chosen shape index)."""
+        cells, list-free cells, whole and third cells with pushed list
+        stores) from the current state and keep the fastest; returns (ms per
+        step of each, chosen shape index)."""
         ms = (ctypes.c_double * FORCE_SHAPES)()
         ch = ctypes.c_int32()
         self._c(lib().espp_tune_force_method(self._h, int(nsteps), float(dt), float(gamma), float(kT), ms,
@@ -504,6 +508,10 @@ class System:
 
     def set_step_shape(self, shape):
         self._c(lib().espp_set_step_shape(self._h, int(shape)))
+
+    def set_list_store(self, push):
+        """ESPP_LIST_STORE_PLACE or ESPP_LIST_STORE_PUSH (the same lists)."""
+        self._c(lib().espp_set_list_store(self._h, int(push)))
 
     def tune_step_shape(self, nsteps, dt, gamma, kT):
         """Time the step kernel's launch shapes, then the resort intervals

@@ -311,6 +311,45 @@ def test_third_cells_keep_the_neighbour_sets(prec):
     s.close()
 
 
+def _store_pair(case, w, push, prec=FP32, le=False, excl=False):
+    s = case.system(prec, build=False)
+    s.set_cell_subdivision(w)
+    s.set_list_store(push)
+    if excl:
+        s.set_exclude_bonded(True)
+    if le:
+        s.set_lees_edwards(True, 0.5, 0.25)
+    s.build_neighbors(case.rc_list, case.skin)
+    return s
+
+
+@pytest.mark.parametrize("w", [1, 3])
+@pytest.mark.parametrize("variant", ["plain", "lees_edwards", "exclusions"])
+@pytest.mark.parametrize("case", [kg_case(), lj_case()], ids=lambda c: c.name)
+def test_pushed_list_store_builds_the_same_lists(case, w, variant):
+    # the two ways of storing hits in the build give the same lists in the
+    # same order: FP32 force sums and trajectories (with rebuilds) bit for bit
+    if variant != "plain" and case.name != kg_case().name:
+        pytest.skip("sheared and excluded builds on the bonded melt")
+    kw = dict(le=variant == "lees_edwards", excl=variant == "exclusions")
+    a = _store_pair(case, w, espp.ESPP_LIST_STORE_PLACE, **kw)
+    b = _store_pair(case, w, espp.ESPP_LIST_STORE_PUSH, **kw)
+    ra, ca = a.get_neighbors()
+    rb, cb = b.get_neighbors()
+    assert np.array_equal(ra, rb) and np.array_equal(ca, cb)
+    assert np.array_equal(a.compute_forces(), b.compute_forces())
+    a.integrate(60, 0.005, 1.0, 1.0)
+    b.integrate(60, 0.005, 1.0, 1.0)
+    assert a.n_rebuilds == b.n_rebuilds and a.n_rebuilds >= 2
+    for qa, qb in zip(a.get_state(), b.get_state()):
+        assert np.array_equal(qa, qb)
+    with pytest.raises(espp.EsppError) as e:
+        b.set_list_store(2)
+    assert e.value.code == espp.ESPP_ERR_ARG
+    a.close()
+    b.close()
+
+
 def test_cell_subdivision_in_batches():
     # replicas of different sizes, each with its own sub-cell grid
     cases_ = [kg_case(), kg_case(4, 30, seed=3, jitter=0.08), kg_case(7, 23, seed=5, jitter=0.1)]
