@@ -33,6 +33,28 @@ def test_library_exports_every_declared_symbol(lib):
     assert sorted(espp.EXPORTS) == syms
 
 
+def header_constants():
+    txt = open(os.path.join(ROOT, "include", "espp.h")).read()
+    return {k: int(v) for k, v in re.findall(r"#define\s+(ESPP_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", txt)}
+
+
+def test_binding_constants_equal_the_header():
+    # every integer the header defines and the binding names has one value;
+    # the shape tables have as many rows as the header's shape counts
+    consts = header_constants()
+    assert len(consts) >= 30
+    matched = 0
+    for name, value in consts.items():
+        for alias in (name, name[len("ESPP_"):]):
+            if hasattr(espp, alias):
+                assert getattr(espp, alias) == value, (name, alias)
+                matched += 1
+    assert matched >= 30
+    assert len(espp.FORCE_SHAPE_NAMES) == consts["ESPP_FORCE_SHAPES"] == espp.FORCE_SHAPES
+    assert len(espp.STEP_SHAPE_TABLE) == consts["ESPP_STEP_SHAPES"] == espp.STEP_SHAPES
+    assert espp.MLP_NPARAMS == consts["ESPP_MLP_NPARAMS"]
+
+
 @pytest.mark.parametrize("n", [2, 4, 8, 16])
 def test_hilbert_ranks_bijective_and_adjacent(lib, n):
     rank = espp.espp_hilbert_ranks(n, n, n)
