@@ -41,7 +41,7 @@ constexpr StepShape STEP_SHAPES[ESPP_STEP_SHAPES] = {{1, 8, 1}, {2, 8, 1}, {1, 1
 #define ESPP_STEP_MINB32_DPD 10
 #endif
 #ifndef ESPP_STEP_LATE  // loads issued after the pair loop: 1 bond partners, 2 velocity and build position
-#define ESPP_STEP_LATE 1  // KG 1M FP32: 64.0 us (1), 65.8 (0), 66.9 (3) at 10 blocks per SM
+#define ESPP_STEP_LATE 3  // KG 1M FP32 at 8 blocks per SM: 58.7 us (3), 61.5 (1); fewer values live across the loop
 #endif
 #ifndef ESPP_STEP_PREFETCH
 #define ESPP_STEP_PREFETCH 2  // request the next batch's list groups early (see pair_loop)
